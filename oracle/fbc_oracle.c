@@ -196,12 +196,15 @@ static void green_barnett(const double Cr[81], int nquad, const double r[3], dou
         double psi = M_PI * (double)q / (double)nquad;
         double cp = cos(psi), sp = sin(psi);
         double z[3] = {cp * e1[0] + sp * e2[0], cp * e1[1] + sp * e2[1], cp * e1[2] + sp * e2[2]};
+        double zz[9];
+        for (int j = 0; j < 3; j++)
+            for (int l = 0; l < 3; l++) zz[3 * j + l] = z[j] * z[l];
         double M[9], Mi[9];
         for (int i = 0; i < 3; i++)
             for (int k = 0; k < 3; k++) {
                 double v = 0.0;
                 for (int j = 0; j < 3; j++)
-                    for (int l = 0; l < 3; l++) v += Cr[27 * i + 9 * j + 3 * k + l] * z[j] * z[l];
+                    for (int l = 0; l < 3; l++) v += Cr[27 * i + 9 * j + 3 * k + l] * zz[3 * j + l];
                 M[3 * i + k] = v;
             }
         inv3(M, Mi);
@@ -271,12 +274,27 @@ int orc_richardson_weights(int n, int N, double* w) {
     return ORC_OK;
 }
 
+/* G(0, 0, m l3) + G(0, 0, -m l3) for m = 1..n+N: the terms Eq. 32 subtracts,
+ * which do not depend on the evaluation point. */
+static void reference_terms(const green_ctx* g, double l3, int m_last, double* ref /* [m_last][9] */) {
+    double Gp[9], Gm[9];
+    for (int m = 1; m <= m_last; m++) {
+        double zp[3] = {0.0, 0.0, (double)m * l3};
+        double zm[3] = {0.0, 0.0, -(double)m * l3};
+        green_eval(g, zp, Gp);
+        green_eval(g, zm, Gm);
+        for (int t = 0; t < 9; t++) ref[(m - 1) * 9 + t] = Gp[t] + Gm[t];
+    }
+}
+
 /* Q0 of Eq. 36 at point r for period l3, from the partial sums of Eq. 35.
- * Partial sums and the extrapolation are carried in double-double. */
-static void periodic_q0(const green_ctx* g, double l3, int n, int N, const double r[3], double out[9]) {
+ * Partial sums and the extrapolation are carried in double-double.  `ref`
+ * holds the subtracted terms from reference_terms(). */
+static void periodic_q0(const green_ctx* g, double l3, int n, int N, const double* ref, const double r[3],
+                        double out[9]) {
     dd part[9];
     dd acc[9];
-    double G[9], Gr[9];
+    double G[9];
     for (int t = 0; t < 9; t++) { acc[t] = dd_from(0.0); }
     /* i = 0 term: G(r), nothing subtracted */
     green_eval(g, r, G);
@@ -285,16 +303,11 @@ static void periodic_q0(const green_ctx* g, double l3, int n, int N, const doubl
     for (int m = 1; m <= m_last; m++) {
         double rp[3] = {r[0], r[1], r[2] + (double)m * l3};
         double rm[3] = {r[0], r[1], r[2] - (double)m * l3};
-        double zp[3] = {0.0, 0.0, (double)m * l3};
-        double zm[3] = {0.0, 0.0, -(double)m * l3};
         green_eval(g, rp, G);
         for (int t = 0; t < 9; t++) part[t] = dd_add_d(part[t], G[t]);
         green_eval(g, rm, G);
         for (int t = 0; t < 9; t++) part[t] = dd_add_d(part[t], G[t]);
-        green_eval(g, zp, Gr);
-        for (int t = 0; t < 9; t++) part[t] = dd_add_d(part[t], -Gr[t]);
-        green_eval(g, zm, Gr);
-        for (int t = 0; t < 9; t++) part[t] = dd_add_d(part[t], -Gr[t]);
+        for (int t = 0; t < 9; t++) part[t] = dd_add_d(part[t], -ref[(m - 1) * 9 + t]);
         if (m >= n) {
             /* part now holds G_m; add its Richardson term (i = m - n) */
             int i = m - n;
@@ -316,9 +329,11 @@ int orc_periodic(const orc_material* m, double l3, int n, int N, const double r[
     green_ctx g;
     int st = green_ctx_init(m, &g);
     if (st) return st;
-    if (!(l3 > 0.0) || n < 1 || N < 0 || N > 16) return ORC_EINVAL;
+    if (!(l3 > 0.0) || n < 1 || N < 0 || N > 16 || n + N > 32) return ORC_EINVAL;
     if (r[0] == 0.0 && r[1] == 0.0) return ORC_EINVAL; /* on-axis: singular image */
-    periodic_q0(&g, l3, n, N, r, out);
+    double ref[32 * 9];
+    reference_terms(&g, l3, n + N, ref);
+    periodic_q0(&g, l3, n, N, ref, r, out);
     return ORC_OK;
 }
 
@@ -378,6 +393,7 @@ typedef struct {
     double c;
     int n, N;
     const int32_t* d;
+    const double* ref; /* [n+N][9] */
     double* out; /* [nd][L][9] */
 } table_ctx;
 
@@ -392,14 +408,14 @@ static void table_task(void* vctx, long item) {
     if (2 * s == L) {
         double a[9], b[9];
         r[2] = 0.5 * l3;
-        periodic_q0(&t->g, l3, t->n, t->N, r, a);
+        periodic_q0(&t->g, l3, t->n, t->N, t->ref, r, a);
         r[2] = -0.5 * l3;
-        periodic_q0(&t->g, l3, t->n, t->N, r, b);
+        periodic_q0(&t->g, l3, t->n, t->N, t->ref, r, b);
         for (int k = 0; k < 9; k++) o[k] = 0.5 * (a[k] + b[k]);
     } else {
         int sc = (2 * s < L) ? s : s - L;
         r[2] = (double)sc * t->c;
-        periodic_q0(&t->g, l3, t->n, t->N, r, o);
+        periodic_q0(&t->g, l3, t->n, t->N, t->ref, r, o);
     }
 }
 
@@ -408,7 +424,7 @@ int orc_kernel_table(const orc_material* m, int L, double c, int n, int N, int n
     table_ctx t;
     int st = green_ctx_init(m, &t.g);
     if (st) return st;
-    if (L < 2 || (L % 2) || !(c > 0.0) || n < 1 || N < 0 || N > 16 || nd < 0) return ORC_EINVAL;
+    if (L < 2 || (L % 2) || !(c > 0.0) || n < 1 || N < 0 || N > 16 || n + N > 32 || nd < 0) return ORC_EINVAL;
     for (int i = 0; i < nd; i++)
         if (d[2 * i] == 0 && d[2 * i + 1] == 0) return ORC_EINVAL;
     t.L = L;
@@ -417,6 +433,9 @@ int orc_kernel_table(const orc_material* m, int L, double c, int n, int N, int n
     t.N = N;
     t.d = d;
     t.out = out;
+    double ref[32 * 9];
+    reference_terms(&t.g, (double)L * c, n + N, ref);
+    t.ref = ref;
     run_parallel(table_task, &t, (long)nd * L, nthreads);
     return ORC_OK;
 }
