@@ -1,0 +1,370 @@
+"""Benchmark of the FBC Green's-function pad update on GB300.
+
+One step = one pad update u <- G f (forward line transform with the neutral
+projection, per-mode contraction, inverse transform) of the paper-scale
+single instance: N_I = 4000 interface and N_P = 6000 pad columns on
+concentric rings, L = 256 repeats, cubic medium C11 = 1.5, C12 = 1.0,
+C44 = 0.9, one right-hand side of N(0, 1) forces (seed 1).  Metric: pad
+updates as Gpair-modes/s, one pair-mode being one (pad column, interface
+column, wavenumber k = 0..L/2, right-hand side) 3x3 block product.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints ONE JSON line on rank 0.  ``--impl reference`` times the CPU oracle
+(the plain FP64 real-space sum) on the host cores instead; see the design
+notes for how its sample is extrapolated.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2105_08798_gb300 import inputs  # noqa: E402
+
+WORKLOAD = "ring4000x6000_L256_cubic"
+METRIC = "FBC pad updates/sec (Gpair-modes/s) at stated error vs FP64 oracle; roofline fraction"
+UNIT = "Gpair-modes/s"
+FLOPS_PER_PAIR_MODE = 36  # two real 3x3 matrix-vector products (x and y' halves)
+X2_OPS_PER_MAC = 12       # double-float MAC: 1 FMUL + 3 FFMA + 8 FADD (design notes)
+L2_BYTES = 129 * 1024 * 1024
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    out = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0, "source": "fallback"}
+    if os.path.exists(path):
+        with open(path) as fh:
+            m = json.load(fh)
+        out.update({k: m[k] for k in ("hbm_gbs", "bf16_tflops", "sm_max_mhz") if k in m})
+        out["source"] = "measured"
+    # plain-ALU peaks from unit counts and the maximum SM clock: 152 SMs,
+    # 128 FP32 FMA lanes per SM per clock; FP64 at the GB300 nominal 1.25 TFLOP/s
+    clk = out["sm_max_mhz"] * 1e6
+    out["fp32_tflops"] = 152 * 128 * 2 * clk / 1e12
+    out["fp64_tflops"] = 1.25 * clk / 2.07e9
+    return out
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.fh,
+                                         stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if self.proc is None or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def oracle_sample(w, xy_i, xy_p, f, n_cols: int = 1):
+    """The oracle's bounded sample: every repeat of the first n_cols pad columns
+    (all of their differences are tabulated first, as setup)."""
+    import oracle
+
+    oracle.build()
+    cols = np.arange(n_cols)
+    samples = np.array([[a, p] for a in cols for p in range(w.L)], dtype=np.int64)
+    fp = oracle.project_neutral(f)
+    d_list, d_index = oracle.difference_index(xy_i, xy_p[cols])
+    t0 = time.perf_counter()
+    table = oracle.kernel_table(w.material, w.L, w.c, d_list, nquad=64)
+    t_table = time.perf_counter() - t0
+    samp_col = np.repeat(np.arange(n_cols), w.L).astype(np.int32)
+    samp_p = np.tile(np.arange(w.L), n_cols).astype(np.int32)
+    return samples, fp, d_index, table, samp_col, samp_p, t_table
+
+
+def run_reference(args, w):
+    """CPU oracle arm: time the plain real-space sum on a bounded sample."""
+    import oracle
+
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    xy_i, xy_p = w.geometry()
+    f = w.forces()
+    samples, fp, d_index, table, samp_col, samp_p, t_table = oracle_sample(w, xy_i, xy_p, f)
+    for _ in range(args.warmup):
+        oracle.real_space_sum(d_index, table, fp, samp_col, samp_p)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.real_space_sum(d_index, table, fp, samp_col, samp_p)
+    dt = (time.perf_counter() - t0) / args.steps
+    # extrapolate one sampled step (len(samples) pad atoms) to the whole update (N_P L pad atoms)
+    t_full = dt * (w.n_p * w.L) / len(samples)
+    value = w.pair_modes / t_full / 1e9
+    info = oracle.sys_info()
+    sample = (f"{len(samples)} pad atoms (all {w.L} repeats of 1 pad column) per step, full real-space sum over "
+              f"{w.n_i} x {w.L} interface atoms; extrapolated x{w.n_p * w.L // len(samples)} to the whole update; "
+              f"kernel tabulation for the sample ({t_table:.1f} s) is setup and untimed")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_full * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": w.name, "n_i": w.n_i, "n_p": w.n_p, "L": w.L, "n_rhs": w.n_rhs, "material": "cubic",
+                   "sampled": True},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": info["cores"], "kind": "oracle", "sample": sample,
+                         "cpu": info["cpu"]},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def time_device_steps(torch, plan, fd, ud, steps, warmup, flush_buf, project=True):
+    """Per-step CUDA events around the apply on the launching stream; L2 flushed between steps."""
+    stream = torch.cuda.current_stream()
+    for _ in range(warmup):
+        flush_buf.zero_()
+        plan.apply(fd, ud, project=project, stream=stream)
+    torch.cuda.synchronize()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    stage = np.zeros(3)
+    plan.set_timing(True)
+    for i in range(steps):
+        flush_buf.zero_()
+        starts[i].record(stream)
+        plan.apply(fd, ud, project=project, stream=stream)
+        ends[i].record(stream)
+        stage += np.asarray(plan.stage_times())  # waits for this step's events
+    plan.set_timing(False)
+    torch.cuda.synchronize()
+    ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    return ms, stage / steps
+
+
+def run_ours(args, w):
+    import torch
+
+    from paper_2105_08798_gb300 import build as fbc_build
+    from paper_2105_08798_gb300 import fbc
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    fbc_build.build()
+    fbc.load()
+    pk = peaks()
+    xy_i, xy_p = w.geometry()
+    f = w.forces(seed=w.seed + rank)  # replicas: each rank updates its own instance
+    t0 = time.perf_counter()
+    plan = fbc.Plan(xy_i, xy_p, w.L, w.material, precision=args.precision)
+    plan.tabulate()
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t0
+    info = plan.info()
+    fd = torch.from_numpy(f).cuda()
+    ud = torch.zeros((1, w.n_p, w.L, 3), dtype=torch.float64, device="cuda")
+    flush_buf = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
+
+    # headline precision
+    plan.set_precision(args.precision)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        ms, stage = time_device_steps(torch, plan, fd, ud, args.steps, args.warmup, flush_buf)
+    torch.cuda.synchronize()
+    step_ms = float(np.sum(ms)) / args.steps
+    if world > 1:
+        t = torch.tensor([step_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        step_ms = float(t.item())
+    value = world * w.pair_modes / (step_ms * 1e-3) / 1e9
+    u_main = ud.cpu().numpy()
+
+    # the other precisions (same plan, same inputs)
+    variants = {}
+    outputs = {args.precision: u_main}
+    for prec in ("fp64", "f32x2", "fp32"):
+        if prec == args.precision:
+            continue
+        plan.set_precision(prec)
+        vms, vstage = time_device_steps(torch, plan, fd, ud, max(2, args.steps // 2), 2, flush_buf)
+        torch.cuda.synchronize()
+        outputs[prec] = ud.cpu().numpy()
+        variants[prec] = {"ms_per_step": float(np.mean(vms)), "value": w.pair_modes / (np.mean(vms) * 1e-3) / 1e9,
+                          "contract_ms": float(vstage[1])}
+    plan.set_precision(args.precision)
+
+    # end-to-end through the host entry point: pinned host f in, host u out
+    fh = torch.from_numpy(f).pin_memory()
+    uh = torch.zeros((1, w.n_p, w.L, 3), dtype=torch.float64).pin_memory()
+    for _ in range(2):
+        plan.apply_host(fh, uh)
+    torch.cuda.synchronize()
+    e2e_t = []
+    for _ in range(max(3, args.steps // 2)):
+        flush_buf.zero_()
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        plan.apply_host(fh, uh)
+        e2e_t.append(time.perf_counter() - t1)
+    e2e_s = float(np.mean(e2e_t))
+    h2d = f.nbytes
+    d2h = uh.numel() * 8
+
+    # error against the FP64 oracle at the sampled pad atoms, and the CPU baseline
+    errors, cpu = {}, None
+    if rank == 0 and not args.skip_oracle:
+        import oracle
+
+        samples, fp, d_index, table, samp_col, samp_p, t_table = oracle_sample(w, xy_i, xy_p, f)
+        ref = oracle.real_space_sum(d_index, table, fp, samp_col, samp_p)[0]
+        for prec, u in outputs.items():
+            got = u[0, samples[:, 0], samples[:, 1]]
+            errors[prec] = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+        # timed oracle sum on the same sample, repeated to ~10 s of CPU work
+        reps, t_cpu = 0, 0.0
+        while t_cpu < 10.0 and reps < 200:
+            t1 = time.perf_counter()
+            oracle.real_space_sum(d_index, table, fp, samp_col, samp_p)
+            t_cpu += time.perf_counter() - t1
+            reps += 1
+        t_full = (t_cpu / reps) * (w.n_p * w.L) / len(samples)
+        sinfo = oracle.sys_info()
+        cpu = {"value": w.pair_modes / t_full / 1e9, "unit": UNIT, "cores": sinfo["cores"], "kind": "oracle",
+               "sample": (f"real-space sum at {len(samples)} pad atoms (1 pad column, all repeats) x {reps} "
+                          f"repetitions ({t_cpu:.1f} s), extrapolated to N_P L = {w.n_p * w.L} pad atoms; kernel "
+                          f"tabulation for the sample ({t_table:.1f} s) untimed"),
+               "cpu": sinfo["cpu"]}
+        for prec in variants:
+            variants[prec]["rel_l2_vs_oracle"] = errors.get(prec)
+
+    # roofline of the dominant kernel (the per-mode contraction)
+    contract_ms = float(stage[1])
+    pm = w.pair_modes
+    if args.precision == "fp64":
+        achieved = FLOPS_PER_PAIR_MODE * pm / (contract_ms * 1e-3) / 1e12
+        peak, peak_name = pk["fp64_tflops"], "fp64 nominal 1.25 TFLOP/s scaled to max SM clock"
+    elif args.precision == "f32x2":
+        achieved = FLOPS_PER_PAIR_MODE // 2 * X2_OPS_PER_MAC * pm / (contract_ms * 1e-3) / 1e12
+        peak, peak_name = pk["fp32_tflops"], "fp32 FMA pipes: 152 SM x 128 lanes x 2 x max SM clock"
+    else:
+        achieved = FLOPS_PER_PAIR_MODE * pm / (contract_ms * 1e-3) / 1e12
+        peak, peak_name = pk["fp32_tflops"], "fp32 FMA pipes: 152 SM x 128 lanes x 2 x max SM clock"
+    traffic = None
+    tpath = os.path.join(ROOT, "profiles", "contract_traffic.json")
+    if os.path.exists(tpath):
+        with open(tpath) as fh:
+            tr = json.load(fh)
+        if tr.get("precision") == args.precision and tr.get("workload") == w.name and tr.get("valid", False):
+            traffic = tr.get("dram_bytes_per_launch")
+    n_launch_per_step = 1 + 1 + (2 if args.precision == "fp32" else 1) + 1  # forward, project, contract, inverse
+    clocks = clk.summary()
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": {"fp64": "f64", "f32x2": "f32x2 (double-float, FP64-accurate)", "fp32": "f32"}[args.precision],
+        "data": "synthetic",
+        "config": {"workload": w.name, "n_i": w.n_i, "n_p": w.n_p, "L": w.L, "n_rhs": w.n_rhs, "material": "cubic",
+                   "precision": args.precision, "l2": "flushed between steps (256 MB write)",
+                   "parallelism": "replicas" if world > 1 else "single"},
+        "rel_l2_vs_oracle": errors.get(args.precision),
+        "setup_s": setup_s,
+        "stage_ms": {"forward": float(stage[0]), "contract": contract_ms, "inverse": float(stage[2])},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                     "traffic": traffic, "peak_source": peak_name},
+        "variants": variants,
+        "e2e": {"value": world * pm / e2e_s / 1e9, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "ms_per_step": e2e_s * 1e3},
+        "gpu_launches": n_launch_per_step * args.steps,
+        "clocks": clocks,
+        "plan": {k: info[k] for k in ("n_tiles_a", "n_tiles_b", "sub_w", "sub_h", "n_used_d", "table_bytes",
+                                      "workspace_bytes")},
+    }
+    if cpu is not None:
+        line["cpu_baseline"] = cpu
+    plan.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--precision", choices=["fp64", "f32x2", "fp32"], default="f32x2")
+    ap.add_argument("--skip-oracle", action="store_true", help="no oracle error check / CPU baseline")
+    args = ap.parse_args(argv)
+    w = inputs.WORKLOADS[WORKLOAD]
+    if args.impl == "reference":
+        return run_reference(args, w)
+    return run_ours(args, w)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

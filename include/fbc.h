@@ -1,0 +1,218 @@
+/*
+ * fbc.h -- C ABI of the GB300 (sm_103a) Green's-function pad update of the
+ * flexible boundary condition (FBC) method for line-periodic dislocations.
+ *
+ * The operation (Sec. 1, Eq. 1; Sec. 2.3.2, Eq. 22 and Algorithm 1;
+ * Sec. 3.2, Eqs. 37-38): given the forces f on the interface atoms, update
+ * the displacements u of the pad atoms,
+ *
+ *     u(a, p) <- beta * u(a, p) + alpha * sum_{b, q} G~(x_a - x_b, (p - q) c) f(b, q),
+ *
+ * where a runs over the pad columns, b over the interface columns, p, q over
+ * the L repeats of each column along the periodic line (spacing c, period
+ * l3 = L c), and G~ is the regularised periodic Green function of Sec. 3.1,
+ * Eqs. 32-36 (image sum with Richardson extrapolation).  The paper's own
+ * update is alpha = -1 (or the relaxation factor of Algorithm 1), beta = 1.
+ *
+ * Because G~ is l3-periodic along the line, the sum over q is a circular
+ * convolution.  The library evaluates it exactly by a DFT along the line:
+ * forward FFT of f, an independent dense complex 3x3-block contraction per
+ * wavenumber k = 0..L/2 against a table g^k(d) indexed by the in-plane
+ * lattice difference d = x_a - x_b, and an inverse FFT.
+ *
+ * Conventions shared by every entry point
+ *   - Sites are integer lattice sites x in Z^2 (one per atom column).
+ *   - Force and displacement arrays are row-major [n_rhs][N][L][3] (FP64
+ *     unless the name says f32), resident in DEVICE memory unless the entry
+ *     point says host; the caller owns them.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Calls that take a stream are asynchronous on it, do not
+ *     synchronise the host and do not allocate.
+ *   - Every call returns an fbc status code; the message of the last failure
+ *     on the calling thread is available from fbc_last_error().  No call
+ *     exits or aborts the process.
+ */
+#ifndef FBC_H
+#define FBC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------- */
+#define FBC_OK 0
+#define FBC_ERR_INVALID_ARG 1   /* a pointer, size or option is out of range */
+#define FBC_ERR_OOM 2           /* device or host allocation failed */
+#define FBC_ERR_CUDA 3          /* a CUDA runtime call or kernel launch failed */
+#define FBC_ERR_NOT_TABULATED 4 /* fbc_apply before fbc_tabulate_kernel */
+#define FBC_ERR_TIMEOUT 5       /* a bounded device wait gave up */
+#define FBC_ERR_UNSUPPORTED 6   /* valid request this build does not implement */
+
+/* ---- material kinds -------------------------------------------------- */
+#define FBC_MATERIAL_ISOTROPIC 0 /* Kelvin's closed form (mu, nu) */
+#define FBC_MATERIAL_CUBIC 1     /* Barnett's line integral (C11, C12, C44, Q) */
+
+/* ---- contraction precisions (fbc_options.precision) ------------------ */
+#define FBC_PREC_FP64 0  /* FP64 fused multiply-add throughout */
+#define FBC_PREC_FP32 1  /* FP32 products and sums; k = 0 mode kept in FP64 */
+#define FBC_PREC_F32X2 2 /* double-float: FP64-accurate products/sums built from FP32 pairs */
+
+/* ---- plan flags (fbc_options.flags) ----------------------------------- */
+#define FBC_PLAN_HOST_ONLY 1 /* validate and lay out on the host only: no device memory,
+                                tabulate/apply are refused; for inspecting the layout */
+
+/* ---- fbc_apply flags ------------------------------------------------- */
+#define FBC_APPLY_PROJECT_NEUTRAL 1u /* remove the net interface force first */
+#define FBC_APPLY_ZERO_MEAN_U 2u     /* set the mean pad displacement to zero after (Eq. 23) */
+
+/* Column geometry (Sec. 2.1: line-periodic slab of a Bravais lattice).
+ * The interface columns are the force sources (the paper's Lambda^{i+}),
+ * the pad columns the targets (Lambda^p).  The two site lists are copied at
+ * plan creation; they must be disjoint and free of duplicates. */
+typedef struct fbc_geometry {
+    int32_t n_i;          /* number of interface columns, >= 1 */
+    int32_t n_p;          /* number of pad columns, >= 1 */
+    int32_t L;            /* repeats along the line: a power of two in [2, 4096] */
+    double c;             /* spacing along the line, > 0 (period l3 = L c) */
+    const int32_t* xy_i;  /* HOST [n_i][2] integer in-plane sites */
+    const int32_t* xy_p;  /* HOST [n_p][2] integer in-plane sites */
+} fbc_geometry;
+
+/* Elastic medium of the continuum Green function (Sec. 3.1, Eq. 33).
+ * Q is the row-major rotation from the computational frame to the crystal
+ * frame (r_crystal = Q r); the Green function in the computational frame is
+ * Q^T G(Q r) Q (App. B).  Only media symmetric under the mirror x3 -> -x3
+ * (isotropic media, or a cubic crystal with a cube axis along the line) are
+ * accepted; other rotations return FBC_ERR_UNSUPPORTED. */
+typedef struct fbc_material {
+    int32_t kind;             /* FBC_MATERIAL_* */
+    double mu, nu;            /* isotropic: shear modulus > 0, -1 < nu < 0.5 */
+    double C11, C12, C44;     /* cubic constants, crystal frame (stable medium) */
+    double Q[9];              /* rotation; all zero is read as the identity */
+} fbc_material;
+
+/* Plan options; fbc_default_options() fills the defaults. */
+typedef struct fbc_options {
+    int32_t precision;  /* FBC_PREC_*, default FBC_PREC_FP64 */
+    int32_t rich_n;     /* Richardson n (Eq. 36), default 4 */
+    int32_t rich_N;     /* Richardson order N (Eq. 36), default 6; n_img = n + N */
+    int32_t quad;       /* Barnett trapezoid nodes on [0, pi), default 64 */
+    int32_t max_rhs;    /* largest n_rhs fbc_apply will accept, default 1 */
+    int32_t flags;      /* FBC_PLAN_* bits, default 0 */
+} fbc_options;
+
+typedef struct fbc_plan fbc_plan;
+
+/* Read-only description of a plan (sizes and the layout the kernels use). */
+typedef struct fbc_plan_info {
+    int32_t n_i, n_p, L, K;     /* K = L/2 + 1 wavenumbers */
+    int32_t max_rhs, precision;
+    int32_t tile_a, tile_b;     /* pad / interface columns per tile */
+    int32_t n_tiles_a, n_tiles_b;
+    int32_t box_x0, box_y0;     /* in-plane origin of the difference table */
+    int32_t box_nx, box_ny;     /* its extent (columns of d_x, rows of d_y) */
+    int32_t sub_w, sub_h;       /* largest per-tile-pair sub-box */
+    int32_t n_used_d;           /* differences that occur between the two sets */
+    int32_t tabulated;          /* 1 after fbc_tabulate_kernel */
+    double pair_modes_per_rhs;  /* n_p * n_i * K */
+    size_t table_bytes;         /* FP64 mode table */
+    size_t workspace_bytes;     /* everything else the plan owns on the device */
+} fbc_plan_info;
+
+/* Defaults listed in fbc_options. */
+void fbc_default_options(fbc_options* opt);
+
+/* Validate the geometry and medium, sort the columns into spatially compact
+ * tiles and allocate every device buffer the plan will need (tables and the
+ * workspace for max_rhs right-hand sides).  Rejects: non-power-of-two L,
+ * coincident interface/pad sites (d = 0, where the continuum kernel is
+ * singular), duplicate sites, unsupported media.  On success *out owns the
+ * plan; on failure *out is NULL.  Synchronous; uses the current device. */
+int fbc_plan_create(const fbc_geometry* geom, const fbc_material* mat, const fbc_options* opt,
+                    fbc_plan** out);
+
+/* Tabulate the periodic kernel and its per-mode table (Sec. 3.1, Eqs. 32-36,
+ * then a DFT along the line): for every in-plane difference d that occurs and
+ * every wavenumber k, g^k(d) = sum_s G~(d, s c) exp(-2 pi i k s / L), stored as
+ * six reals [Re g11, Re g12, Re g22, Re g33, Im g13, Im g23] (the other
+ * parts vanish by the mirror symmetry).  Runs once per plan; the table is
+ * reused by every apply (Sec. 3.2: the setup is reused across runs).
+ * Asynchronous on `stream`. */
+int fbc_tabulate_kernel(fbc_plan* plan, void* stream);
+
+/* The pad update (see the top of this file) for n_rhs right-hand sides:
+ *   f: DEVICE const double [n_rhs][n_i][L][3], interface forces (original order);
+ *   u: DEVICE double [n_rhs][n_p][L][3], pad displacements, updated in place
+ *      (read only when beta != 0);
+ *   flags: FBC_APPLY_PROJECT_NEUTRAL removes the per-component mean of f over
+ *      all n_i * L interface atoms (per right-hand side) before the update;
+ *      FBC_APPLY_ZERO_MEAN_U subtracts the per-component mean of the updated u
+ *      over all n_p * L pad atoms (Sec. 2.3.2, Eq. 23).
+ * 1 <= n_rhs <= max_rhs.  f and u must not overlap.  The contraction runs in
+ * the plan's precision.  Asynchronous on `stream`; concurrent applies of one
+ * plan on different streams race on its workspace. */
+int fbc_apply(fbc_plan* plan, const double* f, double* u, int32_t n_rhs, double alpha, double beta,
+              uint32_t flags, void* stream);
+
+/* Same as fbc_apply with f and u in HOST memory (pinned memory makes the
+ * copies asynchronous): copies f (and u when beta != 0) to the plan's device
+ * staging buffers, applies, copies u back and synchronises `stream`. */
+int fbc_apply_host(fbc_plan* plan, const double* f_host, double* u_host, int32_t n_rhs, double alpha,
+                   double beta, uint32_t flags, void* stream);
+
+/* Switch the contraction precision of an existing plan.  Builds the
+ * precision's derived table from the FP64 table on first use (allocates;
+ * call outside stream capture).  Synchronous. */
+int fbc_plan_set_precision(fbc_plan* plan, int32_t precision);
+
+/* Stage timing for profiling.  While enabled, every fbc_apply records CUDA
+ * events on its stream before the forward transform, after it, after the
+ * per-mode contraction and after the inverse transform.  Synchronous. */
+int fbc_plan_set_timing(fbc_plan* plan, int32_t enable);
+
+/* Durations of the last timed apply, in milliseconds: ms[0] forward
+ * transform (and projection), ms[1] contraction, ms[2] inverse transform
+ * (and zero mean).  Waits for that apply's events. */
+int fbc_plan_stage_times(fbc_plan* plan, float* ms);
+
+/* Fill *info.  Host only. */
+int fbc_plan_info_get(const fbc_plan* plan, fbc_plan_info* info);
+
+/* Host copy of the tile-sorted layout the kernels use (host only, works on a
+ * FBC_PLAN_HOST_ONLY plan).  With NIpad = n_tiles_b * tile_b and
+ * NPpad = n_tiles_a * tile_a from fbc_plan_info:
+ *   perm_i: [NIpad] original interface column of each sorted slot, -1 = padding;
+ *   perm_p: [NPpad] same for the pad columns;
+ *   xy_i:   [NIpad][2] site of each sorted interface slot (padding repeats
+ *           the first site of its tile);
+ *   xy_p:   [NPpad][2] same for the pad slots.
+ * Any output pointer may be NULL. */
+int fbc_plan_layout(const fbc_plan* plan, int32_t* perm_i, int32_t* perm_p, int32_t* xy_i, int32_t* xy_p);
+
+/* Copy rows of the FP64 mode table to the host (synchronous):
+ *   d:   HOST [nd][2] in-plane differences (each must lie in the table box);
+ *   out: HOST double [nd][K][6] in the six-real layout of fbc_tabulate_kernel. */
+int fbc_get_mode_table(const fbc_plan* plan, const int32_t* d, int32_t nd, double* out);
+
+/* Wait for the plan's work on `stream` and report a device-side error word
+ * (FBC_ERR_TIMEOUT if a bounded wait gave up).  Clears the word. */
+int fbc_plan_sync_status(fbc_plan* plan, void* stream);
+
+/* Release every resource of the plan (synchronises the device first).
+ * NULL is ignored. */
+void fbc_destroy(fbc_plan* plan);
+
+/* Message of the last failing call on this thread ("" if none).  The
+ * string is owned by the library and valid until the next call. */
+const char* fbc_last_error(void);
+
+/* Library version string. */
+const char* fbc_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FBC_H */

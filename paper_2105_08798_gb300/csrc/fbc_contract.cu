@@ -1,0 +1,305 @@
+// Per-mode contraction (the hot loop):
+//     U(a, k) = sum_b g^k(x_a - x_b) F(b, k)
+// for every pad column a, wavenumber k and right-hand side (Sec. 3.2,
+// Eqs. 37-38, diagonalised along the line).  In the six-vector form each
+// pair-mode is one real 3x3 matrix M (built from the six table reals) applied
+// to two real 3-vectors x and y' (18 fused multiply-adds).
+//
+// Blocking: a CTA owns one tile of TA spatially compact pad columns at one
+// wavenumber and one right-hand side, one thread per pad column.  It walks
+// the TB-column interface tiles; for each, the table entries of every
+// difference the tile pair can produce form a small rectangle of the
+// difference box (at most W x H entries), which the CTA stages in shared
+// memory together with the tile's transformed forces.  Each thread then
+// gathers its entries at  idx = base_a - off_b  with base_a fixed per tile
+// pair and off_b = x_b + W y_b fixed per interface column.
+//
+// Precisions: FP64 (DFMA); FP32 (FFMA; the logarithmic k = 0 mode stays on
+// the FP64 kernel); F32X2 (double-float: every product and sum carried as an
+// unevaluated pair of FP32 numbers -- Dekker's exact product via FMA, Knuth's
+// two-sum -- and each interface tile's partial folded into a double-float
+// running total, FP64-accurate on the FP32 pipes).
+#include "fbc_internal.cuh"
+
+namespace fbc {
+namespace {
+
+struct ContractArgs {
+    const double* tab;   // [K][Dy][Dx][6]
+    const float* tab32;  // [K][Dy][Dx][6]
+    const float* tabx2;  // [K][Dy][Dx][12] (hi[6], lo[6])
+    const double* fh;    // [rhs][K][NIpad][6]
+    double* uh;          // [rhs][K][NPpad][6]
+    const int2* xy_p;
+    const int* off_i;
+    const int4* bbox_a;
+    const int4* bbox_b;
+    int n_tb, K, Dx, Dy, box_x0, box_y0, W, H, NIpad, NPpad, k0;
+};
+
+template <int TA, int TB>
+__global__ void __launch_bounds__(TA) k_contract_fp64(ContractArgs A) {
+    extern __shared__ double smem64[];
+    const int HW = A.H * A.W;
+    double* s_tab = smem64;              // [6][HW]
+    double* s_f = s_tab + 6 * HW;        // [TB][6]
+    int* s_off = (int*)(s_f + TB * 6);   // [TB]
+    const int tA = blockIdx.x;
+    const int k = A.k0 + blockIdx.y;
+    const int r = blockIdx.z;
+    const int a = tA * TA + threadIdx.x;
+    const int2 xa = A.xy_p[a];
+    const int4 bA = A.bbox_a[tA];
+    double acc0 = 0, acc1 = 0, acc2 = 0, acc3 = 0, acc4 = 0, acc5 = 0;
+    const double* fk = A.fh + ((size_t)r * A.K + k) * A.NIpad * 6;
+    const double* tk = A.tab + (size_t)k * A.Dy * A.Dx * 6;
+    for (int tB = 0; tB < A.n_tb; tB++) {
+        const int4 bB = A.bbox_b[tB];
+        const int ox = bA.x - bB.y, oy = bA.z - bB.w;
+        __syncthreads();
+        for (int e = threadIdx.x; e < HW; e += TA) {
+            const int iy = e / A.W, ix = e - iy * A.W;
+            const int gx = ox + ix - A.box_x0, gy = oy + iy - A.box_y0;
+            double2 v0 = make_double2(0, 0), v1 = v0, v2 = v0;
+            if (gx < A.Dx && gy < A.Dy) {
+                const double2* src = (const double2*)(tk + ((size_t)gy * A.Dx + gx) * 6);
+                v0 = __ldg(src), v1 = __ldg(src + 1), v2 = __ldg(src + 2);
+            }
+            s_tab[0 * HW + e] = v0.x, s_tab[1 * HW + e] = v0.y;
+            s_tab[2 * HW + e] = v1.x, s_tab[3 * HW + e] = v1.y;
+            s_tab[4 * HW + e] = v2.x, s_tab[5 * HW + e] = v2.y;
+        }
+        for (int e = threadIdx.x; e < TB * 6; e += TA) s_f[e] = fk[(size_t)tB * TB * 6 + e];
+        for (int e = threadIdx.x; e < TB; e += TA) s_off[e] = A.off_i[tB * TB + e];
+        __syncthreads();
+        const int base = (xa.x - ox) + A.W * (xa.y - oy);
+#pragma unroll 4
+        for (int j = 0; j < TB; j++) {
+            const int idx = base - s_off[j];
+            const double a11 = s_tab[idx], a12 = s_tab[HW + idx], a22 = s_tab[2 * HW + idx];
+            const double a33 = s_tab[3 * HW + idx], b13 = s_tab[4 * HW + idx], b23 = s_tab[5 * HW + idx];
+            const double* fj = s_f + j * 6;
+            const double x0 = fj[0], x1 = fj[1], x2 = fj[2], y0 = fj[3], y1 = fj[4], y2 = fj[5];
+            acc0 = fma(a11, x0, fma(a12, x1, fma(-b13, x2, acc0)));
+            acc1 = fma(a12, x0, fma(a22, x1, fma(-b23, x2, acc1)));
+            acc2 = fma(b13, x0, fma(b23, x1, fma(a33, x2, acc2)));
+            acc3 = fma(a11, y0, fma(a12, y1, fma(-b13, y2, acc3)));
+            acc4 = fma(a12, y0, fma(a22, y1, fma(-b23, y2, acc4)));
+            acc5 = fma(b13, y0, fma(b23, y1, fma(a33, y2, acc5)));
+        }
+    }
+    double* o = A.uh + (((size_t)r * A.K + k) * A.NPpad + a) * 6;
+    o[0] = acc0, o[1] = acc1, o[2] = acc2, o[3] = acc3, o[4] = acc4, o[5] = acc5;
+}
+
+template <int TA, int TB>
+__global__ void __launch_bounds__(TA) k_contract_fp32(ContractArgs A) {
+    extern __shared__ float smem32[];
+    const int HW = A.H * A.W;
+    float* s_tab = smem32;              // [6][HW]
+    float* s_f = s_tab + 6 * HW;        // [TB][6]
+    int* s_off = (int*)(s_f + TB * 6);  // [TB]
+    const int tA = blockIdx.x;
+    const int k = A.k0 + blockIdx.y;
+    const int r = blockIdx.z;
+    const int a = tA * TA + threadIdx.x;
+    const int2 xa = A.xy_p[a];
+    const int4 bA = A.bbox_a[tA];
+    float acc0 = 0, acc1 = 0, acc2 = 0, acc3 = 0, acc4 = 0, acc5 = 0;
+    const double* fk = A.fh + ((size_t)r * A.K + k) * A.NIpad * 6;
+    const float* tk = A.tab32 + (size_t)k * A.Dy * A.Dx * 6;
+    for (int tB = 0; tB < A.n_tb; tB++) {
+        const int4 bB = A.bbox_b[tB];
+        const int ox = bA.x - bB.y, oy = bA.z - bB.w;
+        __syncthreads();
+        for (int e = threadIdx.x; e < HW; e += TA) {
+            const int iy = e / A.W, ix = e - iy * A.W;
+            const int gx = ox + ix - A.box_x0, gy = oy + iy - A.box_y0;
+            float2 v0 = make_float2(0, 0), v1 = v0, v2 = v0;
+            if (gx < A.Dx && gy < A.Dy) {
+                const float2* src = (const float2*)(tk + ((size_t)gy * A.Dx + gx) * 6);
+                v0 = __ldg(src), v1 = __ldg(src + 1), v2 = __ldg(src + 2);
+            }
+            s_tab[0 * HW + e] = v0.x, s_tab[1 * HW + e] = v0.y;
+            s_tab[2 * HW + e] = v1.x, s_tab[3 * HW + e] = v1.y;
+            s_tab[4 * HW + e] = v2.x, s_tab[5 * HW + e] = v2.y;
+        }
+        for (int e = threadIdx.x; e < TB * 6; e += TA) s_f[e] = (float)fk[(size_t)tB * TB * 6 + e];
+        for (int e = threadIdx.x; e < TB; e += TA) s_off[e] = A.off_i[tB * TB + e];
+        __syncthreads();
+        const int base = (xa.x - ox) + A.W * (xa.y - oy);
+#pragma unroll 8
+        for (int j = 0; j < TB; j++) {
+            const int idx = base - s_off[j];
+            const float a11 = s_tab[idx], a12 = s_tab[HW + idx], a22 = s_tab[2 * HW + idx];
+            const float a33 = s_tab[3 * HW + idx], b13 = s_tab[4 * HW + idx], b23 = s_tab[5 * HW + idx];
+            const float* fj = s_f + j * 6;
+            const float x0 = fj[0], x1 = fj[1], x2 = fj[2], y0 = fj[3], y1 = fj[4], y2 = fj[5];
+            acc0 = fmaf(a11, x0, fmaf(a12, x1, fmaf(-b13, x2, acc0)));
+            acc1 = fmaf(a12, x0, fmaf(a22, x1, fmaf(-b23, x2, acc1)));
+            acc2 = fmaf(b13, x0, fmaf(b23, x1, fmaf(a33, x2, acc2)));
+            acc3 = fmaf(a11, y0, fmaf(a12, y1, fmaf(-b13, y2, acc3)));
+            acc4 = fmaf(a12, y0, fmaf(a22, y1, fmaf(-b23, y2, acc4)));
+            acc5 = fmaf(b13, y0, fmaf(b23, y1, fmaf(a33, y2, acc5)));
+        }
+    }
+    double* o = A.uh + (((size_t)r * A.K + k) * A.NPpad + a) * 6;
+    o[0] = acc0, o[1] = acc1, o[2] = acc2, o[3] = acc3, o[4] = acc4, o[5] = acc5;
+}
+
+// ---- double-float helpers -------------------------------------------------
+struct df {
+    float hi, lo;
+};
+
+// s + e = a + b exactly (Knuth).
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// Accumulate the product (ah + al)(xh + xl) into the running pair (S, E):
+// the leading product ah*xh is split exactly into p + e with one FMA, the
+// cross terms (relative size 2^-24) are folded into e, p is added to S with
+// an exact two-sum and every low-order piece lands in E.
+__device__ __forceinline__ void df_mac(float ah, float al, float xh, float xl, float& S, float& E) {
+    const float p = __fmul_rn(ah, xh);
+    float e = __fmaf_rn(ah, xh, -p);
+    e = __fmaf_rn(ah, xl, e);
+    e = __fmaf_rn(al, xh, e);
+    float s, err;
+    two_sum(S, p, s, err);
+    S = s;
+    E = __fadd_rn(E, __fadd_rn(err, e));
+}
+
+// T += (S + E) in double-float arithmetic (accurate sum of two pairs).
+__device__ __forceinline__ void df_fold(float& Thi, float& Tlo, float S, float E) {
+    float s, e;
+    two_sum(Thi, S, s, e);
+    e = __fadd_rn(e, __fadd_rn(Tlo, E));
+    Thi = __fadd_rn(s, e);
+    Tlo = __fsub_rn(e, __fsub_rn(Thi, s));
+}
+
+template <int TA, int TB>
+__global__ void __launch_bounds__(TA) k_contract_x2(ContractArgs A) {
+    extern __shared__ float2 smemx2[];
+    const int HW = A.H * A.W;
+    float2* s_tab = smemx2;             // [6][HW] (hi, lo)
+    float2* s_f = s_tab + 6 * HW;       // [TB][6] (hi, lo)
+    int* s_off = (int*)(s_f + TB * 6);  // [TB]
+    const int tA = blockIdx.x;
+    const int k = A.k0 + blockIdx.y;
+    const int r = blockIdx.z;
+    const int a = tA * TA + threadIdx.x;
+    const int2 xa = A.xy_p[a];
+    const int4 bA = A.bbox_a[tA];
+    float Th[6] = {0, 0, 0, 0, 0, 0}, Tl[6] = {0, 0, 0, 0, 0, 0};
+    const double* fk = A.fh + ((size_t)r * A.K + k) * A.NIpad * 6;
+    const float* tk = A.tabx2 + (size_t)k * A.Dy * A.Dx * 12;
+    for (int tB = 0; tB < A.n_tb; tB++) {
+        const int4 bB = A.bbox_b[tB];
+        const int ox = bA.x - bB.y, oy = bA.z - bB.w;
+        __syncthreads();
+        for (int e = threadIdx.x; e < HW; e += TA) {
+            const int iy = e / A.W, ix = e - iy * A.W;
+            const int gx = ox + ix - A.box_x0, gy = oy + iy - A.box_y0;
+            float h[6] = {0, 0, 0, 0, 0, 0}, l[6] = {0, 0, 0, 0, 0, 0};
+            if (gx < A.Dx && gy < A.Dy) {
+                const float2* src = (const float2*)(tk + ((size_t)gy * A.Dx + gx) * 12);
+#pragma unroll
+                for (int c = 0; c < 3; c++) {
+                    const float2 vh = __ldg(src + c), vl = __ldg(src + 3 + c);
+                    h[2 * c] = vh.x, h[2 * c + 1] = vh.y, l[2 * c] = vl.x, l[2 * c + 1] = vl.y;
+                }
+            }
+#pragma unroll
+            for (int c = 0; c < 6; c++) s_tab[c * HW + e] = make_float2(h[c], l[c]);
+        }
+        for (int e = threadIdx.x; e < TB * 6; e += TA) {
+            const double v = fk[(size_t)tB * TB * 6 + e];
+            const float hi = (float)v;
+            s_f[e] = make_float2(hi, (float)(v - (double)hi));
+        }
+        for (int e = threadIdx.x; e < TB; e += TA) s_off[e] = A.off_i[tB * TB + e];
+        __syncthreads();
+        const int base = (xa.x - ox) + A.W * (xa.y - oy);
+        float S[6] = {0, 0, 0, 0, 0, 0}, E[6] = {0, 0, 0, 0, 0, 0};
+#pragma unroll 2
+        for (int j = 0; j < TB; j++) {
+            const int idx = base - s_off[j];
+            const float2 a11 = s_tab[idx], a12 = s_tab[HW + idx], a22 = s_tab[2 * HW + idx];
+            const float2 a33 = s_tab[3 * HW + idx], b13 = s_tab[4 * HW + idx], b23 = s_tab[5 * HW + idx];
+            const float2* fj = s_f + j * 6;
+#pragma unroll
+            for (int v = 0; v < 2; v++) {
+                const float2 x0 = fj[3 * v], x1 = fj[3 * v + 1], x2 = fj[3 * v + 2];
+                float* Sv = S + 3 * v;
+                float* Ev = E + 3 * v;
+                df_mac(a11.x, a11.y, x0.x, x0.y, Sv[0], Ev[0]);
+                df_mac(a12.x, a12.y, x1.x, x1.y, Sv[0], Ev[0]);
+                df_mac(-b13.x, -b13.y, x2.x, x2.y, Sv[0], Ev[0]);
+                df_mac(a12.x, a12.y, x0.x, x0.y, Sv[1], Ev[1]);
+                df_mac(a22.x, a22.y, x1.x, x1.y, Sv[1], Ev[1]);
+                df_mac(-b23.x, -b23.y, x2.x, x2.y, Sv[1], Ev[1]);
+                df_mac(b13.x, b13.y, x0.x, x0.y, Sv[2], Ev[2]);
+                df_mac(b23.x, b23.y, x1.x, x1.y, Sv[2], Ev[2]);
+                df_mac(a33.x, a33.y, x2.x, x2.y, Sv[2], Ev[2]);
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < 6; c++) df_fold(Th[c], Tl[c], S[c], E[c]);
+    }
+    double* o = A.uh + (((size_t)r * A.K + k) * A.NPpad + a) * 6;
+#pragma unroll
+    for (int c = 0; c < 6; c++) o[c] = (double)Th[c] + (double)Tl[c];
+}
+
+template <class T>
+size_t contract_smem(const Plan& P, int TB, int per_entry) {
+    return (size_t)6 * P.H * P.W * per_entry + (size_t)TB * 6 * per_entry + (size_t)TB * sizeof(int) + 16;
+}
+
+template <typename KernelT>
+cudaError_t launch_one(KernelT kern, const ContractArgs& A, dim3 grid, int threads, size_t smem, cudaStream_t st) {
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e) return e;
+    }
+    kern<<<grid, threads, smem, st>>>(A);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_contract(Plan& P, int n_rhs, cudaStream_t st) {
+    static_assert(kTileA == 128 && kTileB == 64, "tile sizes are compiled in");
+    ContractArgs A;
+    A.tab = P.d_table, A.tab32 = P.d_table32, A.tabx2 = P.d_table_x2;
+    A.fh = P.d_fh, A.uh = P.d_uh, A.xy_p = P.d_xy_p, A.off_i = P.d_off_i;
+    A.bbox_a = P.d_bbox_a, A.bbox_b = P.d_bbox_b;
+    A.n_tb = P.n_tb, A.K = P.K, A.Dx = P.Dx, A.Dy = P.Dy, A.box_x0 = P.box_x0, A.box_y0 = P.box_y0;
+    A.W = P.W, A.H = P.H, A.NIpad = P.NIpad, A.NPpad = P.NPpad, A.k0 = 0;
+    const size_t s64 = contract_smem<double>(P, kTileB, 8);
+    if (s64 > 220 * 1024) return cudaErrorInvalidConfiguration;
+    if (P.precision == FBC_PREC_FP64) {
+        return launch_one(k_contract_fp64<kTileA, kTileB>, A, dim3(P.n_ta, P.K, n_rhs), kTileA, s64, st);
+    }
+    if (P.precision == FBC_PREC_FP32) {
+        // logarithmic k = 0 mode in FP64, the rest in FP32
+        cudaError_t e = launch_one(k_contract_fp64<kTileA, kTileB>, A, dim3(P.n_ta, 1, n_rhs), kTileA, s64, st);
+        if (e || P.K < 2) return e;
+        A.k0 = 1;
+        return launch_one(k_contract_fp32<kTileA, kTileB>, A, dim3(P.n_ta, P.K - 1, n_rhs), kTileA,
+                          contract_smem<float>(P, kTileB, 4), st);
+    }
+    if (P.precision == FBC_PREC_F32X2) {
+        return launch_one(k_contract_x2<kTileA, kTileB>, A, dim3(P.n_ta, P.K, n_rhs), kTileA,
+                          contract_smem<float2>(P, kTileB, 8), st);
+    }
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace fbc

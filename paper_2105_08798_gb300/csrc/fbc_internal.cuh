@@ -1,0 +1,115 @@
+// Internal declarations of the FBC pad-update library (not part of the ABI).
+//
+// Data layout in device memory (FP64 unless noted):
+//   f   [n_rhs][n_i][L][3]        caller's interface forces (original column order)
+//   u   [n_rhs][n_p][L][3]        caller's pad displacements
+//   fh  [max_rhs][K][NIpad][6]    forward transform of f, tile-sorted columns
+//   uh  [max_rhs][K][NPpad][6]    contracted modes, tile-sorted pad columns
+//   tab [K][Dy][Dx][6]            mode table g^k(d), d = (box_x0 + ix, box_y0 + iy)
+// with K = L/2 + 1.  A "six-vector" of a complex 3-vector V is
+//   (Re V1, Re V2, Im V3, Im V1, Im V2, -Re V3):
+// the first half is x, the second half y'.  For a mirror-symmetric medium the
+// per-mode 3x3 block is  g = A + iB  with A even (11, 12, 22, 33) and B odd
+// (13, 23), and U = g F becomes the same real 3x3 matrix
+//   M = [[A11, A12, -B13], [A12, A22, -B23], [B13, B23, A33]]
+// acting on x and on y' separately (two real right-hand sides per mode).
+// The table stores (A11, A12, A22, A33, B13, B23).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "fbc.h"
+
+namespace fbc {
+
+constexpr int kMaxRichImages = 40;  // n + N upper bound
+constexpr int kMaxQuad = 512;       // Barnett nodes on [0, pi)
+constexpr int kTileA = 128;         // pad columns per contraction tile
+constexpr int kTileB = 64;          // interface columns per contraction tile
+
+// Material constants as the tabulation kernels read them.
+struct MaterialDev {
+    int kind;          // FBC_MATERIAL_*
+    double kelvin_pre; // 1 / (16 pi mu (1 - nu))
+    double kelvin_a;   // 3 - 4 nu
+    double K[36];      // Christoffel form: M_I = sum_J K[I][J] zz_J, I, J over symmetric pairs
+    int nquad;
+};
+
+struct TabulateParams {
+    int L, K, Lh;           // Lh = L / 2
+    double c;
+    int rich_n, rich_N;
+    double W[kMaxRichImages];  // cumulative Richardson weights of images n+1 .. n+N
+    int box_x0, box_y0, Dx, Dy;
+};
+
+struct Plan {
+    int device = 0;
+    int n_i = 0, n_p = 0, L = 0, K = 0, logL = 0;
+    double c = 1.0;
+    int TA = kTileA, TB = kTileB;
+    int n_ta = 0, n_tb = 0, NIpad = 0, NPpad = 0;
+    int box_x0 = 0, box_y0 = 0, Dx = 0, Dy = 0;  // difference table box
+    int W = 0, H = 0;                             // largest tile-pair sub-box
+    int n_used = 0;
+    fbc_options opt{};
+    MaterialDev mat{};
+    TabulateParams tp{};
+    bool tabulated = false;
+    int precision = FBC_PREC_FP64;
+
+    // host copies of the sorted layout
+    std::vector<int> perm_i, perm_p;  // sorted slot -> original column (-1 = padding)
+    std::vector<int2> xy_i_sorted, xy_p_sorted;
+    bool host_only = false;
+
+    // device buffers (owned)
+    int2* d_xy_p = nullptr;      // [NPpad] sorted pad sites (padding: first site of its tile)
+    int* d_off_i = nullptr;      // [NIpad] x_b + W * y_b of the sorted interface sites
+    int4* d_bbox_a = nullptr;    // [n_ta] (minx, maxx, miny, maxy)
+    int4* d_bbox_b = nullptr;    // [n_tb]
+    int* d_perm_i = nullptr;     // [NIpad]
+    int* d_perm_p = nullptr;     // [NPpad]
+    int2* d_used = nullptr;      // [n_used] differences that occur
+    double2* d_tw = nullptr;     // [L/2] exp(-2 pi i t / L)
+    double2* d_twL = nullptr;    // [L] (cos, sin)(2 pi t / L) for the table DFT
+    double* d_table = nullptr;   // [K][Dy][Dx][6] FP64
+    float* d_table32 = nullptr;  // [K][Dy][Dx][6] FP32 (FBC_PREC_FP32)
+    float* d_table_x2 = nullptr; // [K][Dy][Dx][12] hi/lo pairs (FBC_PREC_F32X2)
+    double* d_fh = nullptr;      // [max_rhs][K][NIpad][6]
+    double* d_uh = nullptr;      // [max_rhs][K][NPpad][6]
+    double* d_part = nullptr;    // [max_rhs][n_line_blocks_p][3] zero-mean partial sums
+    double* d_stage_f = nullptr; // host-apply staging
+    double* d_stage_u = nullptr;
+    int* d_status = nullptr;     // device error word
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};  // stage timing (optional)
+    bool timing = false, timed_once = false;
+    size_t table_bytes = 0, workspace_bytes = 0;
+};
+
+// ---- launchers (each returns the launch's cudaError_t) ---------------------
+cudaError_t launch_tabulate(Plan& P, cudaStream_t st);
+cudaError_t launch_forward(Plan& P, const double* f, int n_rhs, bool project, cudaStream_t st);
+cudaError_t launch_contract(Plan& P, int n_rhs, cudaStream_t st);
+cudaError_t launch_inverse(Plan& P, double* u, int n_rhs, double alpha, double beta, bool zero_mean,
+                           cudaStream_t st);
+cudaError_t launch_derive_tables(Plan& P, int precision, cudaStream_t st);
+
+// line-transform blocking: columns per CTA so that a CTA holds 2048 complex points
+inline int line_cols(int L) {
+    int nc = 2048 / L;
+    if (nc < 2) nc = 2;
+    if (nc > 64) nc = 64;
+    return nc;
+}
+
+}  // namespace fbc
+
+struct fbc_plan {
+    fbc::Plan p;
+};

@@ -1,0 +1,276 @@
+// Transforms along the periodic line (FP64, HBM-bound).
+//
+// Forward (before the contraction): for each interface column b the three
+// real force sequences f_c(b, q), q = 0..L-1, are transformed to
+//     F_c(b, k) = sum_q f_c(b, q) exp(-2 pi i k q / L),  k = 0..L/2,
+// and stored as six-vectors (Re F1, Re F2, Im F3, Im F1, Im F2, -Re F3) in
+// tile-sorted column order.  Two real sequences share one complex FFT:
+// z = f1 + i f2 per column, and w = f3(b) + i f3(b+1) per column pair.
+// Removing the net force (a constant over all N_I L atoms) only changes the
+// k = 0 mode, by -L * mean, which the projection kernel applies.
+//
+// Inverse (after the contraction): the contracted six-vectors give
+// U_c(a, k) for k = 0..L/2; the Hermitian extension U(L - k) = conj U(k)
+// makes the inverse transform real, and
+//     u(a, p) <- beta u(a, p) + (alpha / L) sum_k U(a, k) exp(+2 pi i k p / L).
+// Imaginary parts at k = 0 and k = L/2 are dropped (they vanish for a real
+// result), as a real inverse DFT does.  The optional zero-mean step
+// (Sec. 2.3.2, Eq. 23) subtracts the per-component mean over all pad atoms.
+//
+// The FFT is an in-place radix-2 decimation-in-time transform in shared
+// memory (bit-reversed load, log2 L butterfly stages).  A CTA holds NC
+// columns, i.e. 1.5 NC complex sequences of length L.
+#include "fbc_internal.cuh"
+
+namespace fbc {
+namespace {
+
+__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+    return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
+}
+
+__device__ __forceinline__ int bitrev(int x, int logL) { return (int)(__brev((unsigned)x) >> (32 - logL)); }
+
+// nseq sequences of length L in buf; tw[t] = exp(-2 pi i t / L); inverse uses conj.
+__device__ void fft_block(double2* buf, int nseq, int L, int logL, const double2* __restrict__ tw, bool inverse) {
+    const int half = L >> 1;
+    for (int lh = 0; lh < logL; lh++) {
+        const int h = 1 << lh;
+        const int stride_tw = half >> lh;  // L / (2h)
+        for (int t = threadIdx.x; t < nseq * half; t += blockDim.x) {
+            const int sq = t >> (logL - 1);
+            const int j = t & (half - 1);
+            const int pos = j & (h - 1);
+            const int grp = j >> lh;
+            const int i0 = (grp << (lh + 1)) + pos;
+            const int i1 = i0 + h;
+            double2 w = __ldg(&tw[pos * stride_tw]);
+            if (inverse) w.y = -w.y;
+            double2* s = buf + (size_t)sq * L;
+            const double2 a = s[i0];
+            const double2 bw = cmul(s[i1], w);
+            s[i0] = make_double2(a.x + bw.x, a.y + bw.y);
+            s[i1] = make_double2(a.x - bw.x, a.y - bw.y);
+        }
+        __syncthreads();
+    }
+}
+
+// Forward transform of NC columns per CTA.  grid = (NIpad / NC, n_rhs).
+__global__ void k_forward(const double* __restrict__ f, const int* __restrict__ perm, const double2* __restrict__ tw,
+                          double* __restrict__ fh, int n_i, int L, int logL, int K, int NIpad, int NC) {
+    extern __shared__ double2 sbuf[];  // [NC + NC/2][L]: z sequences then w sequences
+    const int r = blockIdx.y;
+    const int b0 = blockIdx.x * NC;
+    double2* zs = sbuf;
+    double2* ws = sbuf + (size_t)NC * L;
+    // load: each column's L x 3 block is contiguous in f
+    for (int t = threadIdx.x; t < NC * L; t += blockDim.x) {
+        const int j = t / L, q = t % L;
+        const int ob = perm[b0 + j];
+        double f1 = 0.0, f2 = 0.0, f3 = 0.0;
+        if (ob >= 0) {
+            const double* src = f + (((size_t)r * n_i + ob) * L + q) * 3;
+            f1 = src[0], f2 = src[1], f3 = src[2];
+        }
+        const int qr = bitrev(q, logL);
+        zs[(size_t)j * L + qr] = make_double2(f1, f2);
+        double* wp = (double*)&ws[(size_t)(j >> 1) * L + qr];
+        wp[j & 1] = f3;
+    }
+    __syncthreads();
+    fft_block(sbuf, NC + NC / 2, L, logL, tw, false);
+    // unpack and store six-vectors for k = 0..L/2
+    for (int t = threadIdx.x; t < NC * K; t += blockDim.x) {
+        const int k = t / NC, j = t % NC;
+        const int km = (L - k) & (L - 1);
+        const double2 Z = zs[(size_t)j * L + k], Zm = zs[(size_t)j * L + km];
+        const double2 Wv = ws[(size_t)(j >> 1) * L + k], Wm = ws[(size_t)(j >> 1) * L + km];
+        // F1 = (Z + conj Zm) / 2, F2 = (Z - conj Zm) / (2i)
+        const double F1r = 0.5 * (Z.x + Zm.x), F1i = 0.5 * (Z.y - Zm.y);
+        const double F2r = 0.5 * (Z.y + Zm.y), F2i = -0.5 * (Z.x - Zm.x);
+        double F3r, F3i;
+        if ((j & 1) == 0) {
+            F3r = 0.5 * (Wv.x + Wm.x), F3i = 0.5 * (Wv.y - Wm.y);
+        } else {
+            F3r = 0.5 * (Wv.y + Wm.y), F3i = -0.5 * (Wv.x - Wm.x);
+        }
+        double* o = fh + (((size_t)r * K + k) * NIpad + b0 + j) * 6;
+        if (perm[b0 + j] < 0) {
+            o[0] = o[1] = o[2] = o[3] = o[4] = o[5] = 0.0;
+            continue;
+        }
+        o[0] = F1r;
+        o[1] = F2r;
+        o[2] = F3i;
+        o[3] = F1i;
+        o[4] = F2i;
+        o[5] = -F3r;
+    }
+}
+
+// Neutral projection in the mode domain: mean_c = sum_b F_c(b, 0) / (n_i L);
+// F_c(b, 0) -= L mean_c for every real column.  One CTA per right-hand side;
+// fixed-order reduction (deterministic).
+__global__ void k_project(double* __restrict__ fh, const int* __restrict__ perm, int n_i, int L, int K, int NIpad) {
+    __shared__ double red[3][256];
+    const int r = blockIdx.y;
+    double* row = fh + (size_t)r * K * NIpad * 6;  // k = 0
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+    for (int b = threadIdx.x; b < NIpad; b += blockDim.x) {
+        s0 += row[(size_t)b * 6 + 0];
+        s1 += row[(size_t)b * 6 + 1];
+        s2 -= row[(size_t)b * 6 + 5];
+    }
+    red[0][threadIdx.x] = s0;
+    red[1][threadIdx.x] = s1;
+    red[2][threadIdx.x] = s2;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w)
+            for (int c = 0; c < 3; c++) red[c][threadIdx.x] += red[c][threadIdx.x + w];
+        __syncthreads();
+    }
+    // L * mean = sum / n_i
+    const double m0 = red[0][0] / (double)n_i, m1 = red[1][0] / (double)n_i, m2 = red[2][0] / (double)n_i;
+    for (int b = threadIdx.x; b < NIpad; b += blockDim.x) {
+        if (perm[b] < 0) continue;
+        row[(size_t)b * 6 + 0] -= m0;
+        row[(size_t)b * 6 + 1] -= m1;
+        row[(size_t)b * 6 + 5] += m2;
+    }
+}
+
+// Inverse transform + epilogue.  grid = (NPpad / NC, n_rhs).
+__global__ void k_inverse(const double* __restrict__ uh, const int* __restrict__ perm, const double2* __restrict__ tw,
+                          double* __restrict__ u, double* __restrict__ part, int n_p, int L, int logL, int K, int NPpad,
+                          int NC, double alpha_over_L, double beta, int want_part) {
+    extern __shared__ double2 sbuf[];
+    const int r = blockIdx.y;
+    const int a0 = blockIdx.x * NC;
+    double2* zs = sbuf;
+    double2* ws = sbuf + (size_t)NC * L;
+    const int Lh = L >> 1;
+    for (int t = threadIdx.x; t < NC * K; t += blockDim.x) {
+        const int k = t / NC, j = t % NC;
+        const double* src = uh + (((size_t)r * K + k) * NPpad + a0 + j) * 6;
+        const double x0 = src[0], x1 = src[1], y0 = src[3], y1 = src[4];
+        // U1 = x0 + i y0, U2 = x1 + i y1 (U3 is handled per column pair below)
+        double U1r = x0, U1i = y0, U2r = x1, U2i = y1;
+        if (k == 0 || k == Lh) U1i = U2i = 0.0;
+        // Z(k) = U1 + i U2 ; Z(L-k) = conj U1 + i conj U2
+        zs[(size_t)j * L + bitrev(k, logL)] = make_double2(U1r - U2i, U1i + U2r);
+        if (k != 0 && k != Lh) zs[(size_t)j * L + bitrev(L - k, logL)] = make_double2(U1r + U2i, U2r - U1i);
+    }
+    // W = U3(even column) + i U3(odd column), with U3 = -y2 + i x2: thread per (k, column pair)
+    for (int t = threadIdx.x; t < (NC / 2) * K; t += blockDim.x) {
+        const int k = t / (NC / 2), jp = t % (NC / 2);
+        const double* se = uh + (((size_t)r * K + k) * NPpad + a0 + 2 * jp) * 6;
+        const double* so = se + 6;
+        double Er = -se[5], Ei = se[2], Or = -so[5], Oi = so[2];
+        if (k == 0 || k == Lh) Ei = Oi = 0.0;
+        // W(k) = E + i O ; W(L-k) = conj E + i conj O
+        ws[(size_t)jp * L + bitrev(k, logL)] = make_double2(Er - Oi, Ei + Or);
+        if (k != 0 && k != Lh) ws[(size_t)jp * L + bitrev(L - k, logL)] = make_double2(Er + Oi, Or - Ei);
+    }
+    __syncthreads();
+    fft_block(sbuf, NC + NC / 2, L, logL, tw, true);
+    double ps0 = 0.0, ps1 = 0.0, ps2 = 0.0;
+    for (int t = threadIdx.x; t < NC * L; t += blockDim.x) {
+        const int j = t / L, p = t % L;
+        const int oa = perm[a0 + j];
+        if (oa < 0) continue;
+        const double2 z = zs[(size_t)j * L + p];
+        const double2 w = ws[(size_t)(j >> 1) * L + p];
+        const double v3 = (j & 1) ? w.y : w.x;
+        double* dst = u + (((size_t)r * n_p + oa) * L + p) * 3;
+        double o0 = alpha_over_L * z.x, o1 = alpha_over_L * z.y, o2 = alpha_over_L * v3;
+        if (beta != 0.0) {
+            o0 = fma(beta, dst[0], o0);
+            o1 = fma(beta, dst[1], o1);
+            o2 = fma(beta, dst[2], o2);
+        }
+        dst[0] = o0;
+        dst[1] = o1;
+        dst[2] = o2;
+        ps0 += o0, ps1 += o1, ps2 += o2;
+    }
+    if (want_part) {
+        __shared__ double red[3][256];
+        red[0][threadIdx.x] = ps0;
+        red[1][threadIdx.x] = ps1;
+        red[2][threadIdx.x] = ps2;
+        __syncthreads();
+        for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+            if ((int)threadIdx.x < w)
+                for (int c = 0; c < 3; c++) red[c][threadIdx.x] += red[c][threadIdx.x + w];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) {
+            double* pp = part + ((size_t)r * gridDim.x + blockIdx.x) * 3;
+            pp[0] = red[0][0], pp[1] = red[1][0], pp[2] = red[2][0];
+        }
+    }
+}
+
+// Zero mean of the pad displacements (Eq. 23): every CTA reduces the per-CTA
+// partial sums in the same fixed order, then subtracts from its chunk of u.
+__global__ void k_zero_mean(double* __restrict__ u, const double* __restrict__ part, int n_part, int n_p, int L) {
+    __shared__ double mean[3];
+    const int r = blockIdx.y;
+    if (threadIdx.x == 0) {
+        double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+        const double* pp = part + (size_t)r * n_part * 3;
+        for (int t = 0; t < n_part; t++) s0 += pp[3 * t], s1 += pp[3 * t + 1], s2 += pp[3 * t + 2];
+        const double inv = 1.0 / ((double)n_p * (double)L);
+        mean[0] = s0 * inv, mean[1] = s1 * inv, mean[2] = s2 * inv;
+    }
+    __syncthreads();
+    const size_t n = (size_t)n_p * L * 3;
+    double* ur = u + (size_t)r * n;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        ur[i] -= mean[i % 3];
+}
+
+size_t line_smem(int L, int NC) { return (size_t)(NC + NC / 2) * L * sizeof(double2); }
+
+}  // namespace
+
+cudaError_t launch_forward(Plan& P, const double* f, int n_rhs, bool project, cudaStream_t st) {
+    const int NC = line_cols(P.L);
+    const size_t smem = line_smem(P.L, NC);
+    cudaError_t e;
+    if (smem > 48 * 1024 && (e = cudaFuncSetAttribute(k_forward, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)))
+        return e;
+    dim3 grid(P.NIpad / NC, n_rhs);
+    k_forward<<<grid, 256, smem, st>>>(f, P.d_perm_i, P.d_tw, P.d_fh, P.n_i, P.L, P.logL, P.K, P.NIpad, NC);
+    if ((e = cudaGetLastError())) return e;
+    if (project) {
+        k_project<<<dim3(1, n_rhs), 256, 0, st>>>(P.d_fh, P.d_perm_i, P.n_i, P.L, P.K, P.NIpad);
+        if ((e = cudaGetLastError())) return e;
+    }
+    return cudaSuccess;
+}
+
+cudaError_t launch_inverse(Plan& P, double* u, int n_rhs, double alpha, double beta, bool zero_mean,
+                           cudaStream_t st) {
+    const int NC = line_cols(P.L);
+    const size_t smem = line_smem(P.L, NC);
+    cudaError_t e;
+    if (smem > 48 * 1024 && (e = cudaFuncSetAttribute(k_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)))
+        return e;
+    const int nb = P.NPpad / NC;
+    dim3 grid(nb, n_rhs);
+    k_inverse<<<grid, 256, smem, st>>>(P.d_uh, P.d_perm_p, P.d_tw, u, P.d_part, P.n_p, P.L, P.logL, P.K, P.NPpad, NC,
+                                       alpha / (double)P.L, beta, zero_mean ? 1 : 0);
+    if ((e = cudaGetLastError())) return e;
+    if (zero_mean) {
+        const size_t n = (size_t)P.n_p * P.L * 3;
+        int blocks = (int)std::min<size_t>((n + 255) / 256, 4 * 152);
+        k_zero_mean<<<dim3(blocks, n_rhs), 256, 0, st>>>(u, P.d_part, nb, P.n_p, P.L);
+        if ((e = cudaGetLastError())) return e;
+    }
+    return cudaSuccess;
+}
+
+}  // namespace fbc

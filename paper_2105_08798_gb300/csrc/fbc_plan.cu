@@ -1,0 +1,646 @@
+// Host side of the FBC pad-update library: argument validation, the
+// spatially compact tiling of the column sets, the difference-table box,
+// device memory ownership and the C ABI entry points declared in fbc.h.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <numeric>
+
+#include "fbc_internal.cuh"
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+    return fail(e == cudaErrorMemoryAllocation ? FBC_ERR_OOM : FBC_ERR_CUDA, "%s: %s", what,
+                cudaGetErrorString(e));
+}
+
+#define FBC_CUDA(call)                                    \
+    do {                                                  \
+        cudaError_t e_ = (call);                          \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+    } while (0)
+
+bool is_pow2(int x) { return x > 0 && (x & (x - 1)) == 0; }
+
+// Recursive bisection along the longer side of the bounding box.  The left
+// part always holds a multiple of T sites, so every tile is full except the
+// last one.  Ties are broken by the other coordinate and then the index, so
+// the order is deterministic on every host.
+void bisect(const int32_t* xy, std::vector<int>& idx, int lo, int hi, int T) {
+    int n = hi - lo;
+    if (n <= T) return;
+    int minx = INT32_MAX, maxx = INT32_MIN, miny = INT32_MAX, maxy = INT32_MIN;
+    for (int t = lo; t < hi; t++) {
+        int x = xy[2 * idx[t]], y = xy[2 * idx[t] + 1];
+        minx = std::min(minx, x), maxx = std::max(maxx, x);
+        miny = std::min(miny, y), maxy = std::max(maxy, y);
+    }
+    int ax = (maxx - minx >= maxy - miny) ? 0 : 1;
+    std::sort(idx.begin() + lo, idx.begin() + hi, [&](int a, int b) {
+        int pa = xy[2 * a + ax], pb = xy[2 * b + ax];
+        if (pa != pb) return pa < pb;
+        int qa = xy[2 * a + 1 - ax], qb = xy[2 * b + 1 - ax];
+        if (qa != qb) return qa < qb;
+        return a < b;
+    });
+    int n_left = T * ((n + 2 * T - 1) / (2 * T));
+    if (n_left >= n) n_left = T * ((n - 1) / T);
+    bisect(xy, idx, lo, lo + n_left, T);
+    bisect(xy, idx, lo + n_left, hi, T);
+}
+
+struct Tiling {
+    std::vector<int> perm;      // slot -> original index or -1
+    std::vector<int2> xy;       // slot -> site (padding: first site of the tile)
+    std::vector<int4> bbox;     // tile -> (minx, maxx, miny, maxy)
+    int n_tiles = 0, n_pad = 0, max_w = 0, max_h = 0;
+};
+
+Tiling make_tiling(const int32_t* xy, int n, int T) {
+    Tiling t;
+    std::vector<int> idx(n);
+    std::iota(idx.begin(), idx.end(), 0);
+    bisect(xy, idx, 0, n, T);
+    t.n_tiles = (n + T - 1) / T;
+    t.n_pad = t.n_tiles * T;
+    t.perm.assign(t.n_pad, -1);
+    t.xy.resize(t.n_pad);
+    t.bbox.resize(t.n_tiles);
+    for (int tile = 0; tile < t.n_tiles; tile++) {
+        int4 bb = make_int4(INT32_MAX, INT32_MIN, INT32_MAX, INT32_MIN);
+        int first = idx[tile * T];
+        for (int s = 0; s < T; s++) {
+            int slot = tile * T + s;
+            int o = (slot < n) ? idx[slot] : -1;
+            t.perm[slot] = o;
+            int src = (o >= 0) ? o : first;
+            int x = xy[2 * src], y = xy[2 * src + 1];
+            t.xy[slot] = make_int2(x, y);
+            bb.x = std::min(bb.x, x), bb.y = std::max(bb.y, x);
+            bb.z = std::min(bb.z, y), bb.w = std::max(bb.w, y);
+        }
+        t.bbox[tile] = bb;
+        t.max_w = std::max(t.max_w, bb.y - bb.x + 1);
+        t.max_h = std::max(t.max_h, bb.w - bb.z + 1);
+    }
+    return t;
+}
+
+// Cumulative Richardson weights: with w_i = (n+i)^N (-1)^(i+N) / (i! (N-i)!)
+// (Eq. 36), Q0 = sum_i w_i G_{n+i} = G_n + sum_{m=n+1}^{n+N} W_m t_m where
+// t_m is the m-th paired image increment and W_m = sum_{i >= m-n} w_i.  The
+// increments are small, so this arrangement keeps the rounding of G_n out of
+// the large alternating weights.
+void richardson_cumulative(int n, int N, double* W) {
+    std::vector<double> w(N + 1);
+    for (int i = 0; i <= N; i++) {
+        double num = 1.0;
+        for (int e = 0; e < N; e++) num *= (double)(n + i);
+        double den = 1.0;
+        for (int t = 2; t <= i; t++) den *= t;
+        for (int t = 2; t <= N - i; t++) den *= t;
+        w[i] = (((i + N) & 1) ? -num : num) / den;
+    }
+    for (int m = n + 1; m <= n + N; m++) {
+        double s = 0.0;
+        for (int i = N; i >= m - n; i--) s += w[i];
+        W[m - n - 1] = s;
+    }
+}
+
+// Full stiffness C_ijkl of the medium in the computational frame and its
+// Christoffel form K[I][J] with M_ik = sum_J K[I][J] z_j z_l over the
+// symmetric index pairs I = (i, k), J = (j, l).
+void christoffel_form(const fbc_material& m, const double Q[9], double K[36]) {
+    static const int pr[6][2] = {{0, 0}, {1, 1}, {2, 2}, {1, 2}, {0, 2}, {0, 1}};
+    double C[3][3][3][3];
+    for (int i = 0; i < 3; i++)
+        for (int j = 0; j < 3; j++)
+            for (int k = 0; k < 3; k++)
+                for (int l = 0; l < 3; l++) {
+                    double v = 0.0;
+                    if (i == j && k == l) v += m.C12;
+                    if (i == k && j == l) v += m.C44;
+                    if (i == l && j == k) v += m.C44;
+                    if (i == j && j == k && k == l) v += m.C11 - m.C12 - 2.0 * m.C44;
+                    C[i][j][k][l] = v;
+                }
+    double R[3][3][3][3];
+    for (int i = 0; i < 3; i++)
+        for (int j = 0; j < 3; j++)
+            for (int k = 0; k < 3; k++)
+                for (int l = 0; l < 3; l++) {
+                    double v = 0.0;
+                    for (int a = 0; a < 3; a++)
+                        for (int b = 0; b < 3; b++)
+                            for (int c = 0; c < 3; c++)
+                                for (int d = 0; d < 3; d++)
+                                    v += Q[3 * a + i] * Q[3 * b + j] * Q[3 * c + k] * Q[3 * d + l] * C[a][b][c][d];
+                    R[i][j][k][l] = v;
+                }
+    for (int I = 0; I < 6; I++)
+        for (int J = 0; J < 6; J++) {
+            int i = pr[I][0], k = pr[I][1], j = pr[J][0], l = pr[J][1];
+            K[6 * I + J] = (j == l) ? R[i][j][k][l] : R[i][j][k][l] + R[i][l][k][j];
+        }
+}
+
+size_t align_up(size_t x) { return (x + 255) & ~size_t(255); }
+
+template <class T>
+int dev_alloc(T** p, size_t count, size_t& acc, const char* what) {
+    size_t bytes = count * sizeof(T);
+    if (bytes == 0) bytes = sizeof(T);
+    if (getenv("FBC_TEST_FAIL_ALLOC") && strcmp(getenv("FBC_TEST_FAIL_ALLOC"), what) == 0)
+        return fail(FBC_ERR_OOM, "injected allocation failure: %s", what);
+    cudaError_t e = cudaMalloc((void**)p, bytes);
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        return cuda_fail(e, what);
+    }
+    acc += align_up(bytes);
+    return FBC_OK;
+}
+
+void free_plan(fbc::Plan& P) {
+    void* bufs[] = {P.d_xy_p,  P.d_off_i,    P.d_bbox_a, P.d_bbox_b, P.d_perm_i, P.d_perm_p,
+                    P.d_used,  P.d_tw,       P.d_twL,    P.d_table,  P.d_table32, P.d_table_x2,
+                    P.d_fh,    P.d_uh,       P.d_part,   P.d_stage_f, P.d_stage_u, P.d_status};
+    for (void* b : bufs)
+        if (b) cudaFree(b);
+    for (auto& e : P.ev)
+        if (e) cudaEventDestroy(e), e = nullptr;
+}
+
+int validate_material(const fbc_material& m, double Q[9]) {
+    bool allzero = true;
+    for (int t = 0; t < 9; t++) allzero = allzero && m.Q[t] == 0.0;
+    for (int t = 0; t < 9; t++) Q[t] = allzero ? ((t % 4 == 0) ? 1.0 : 0.0) : m.Q[t];
+    for (int t = 0; t < 9; t++)
+        if (!std::isfinite(Q[t])) return fail(FBC_ERR_INVALID_ARG, "material Q has a non-finite entry");
+    for (int i = 0; i < 3; i++)
+        for (int j = 0; j < 3; j++) {
+            double s = 0.0;
+            for (int k = 0; k < 3; k++) s += Q[3 * k + i] * Q[3 * k + j];
+            if (std::fabs(s - (i == j ? 1.0 : 0.0)) > 1e-12)
+                return fail(FBC_ERR_INVALID_ARG, "material Q is not orthogonal");
+        }
+    if (m.kind == FBC_MATERIAL_ISOTROPIC) {
+        if (!(m.mu > 0.0) || !(m.nu > -1.0) || !(m.nu < 0.5) || !std::isfinite(m.mu))
+            return fail(FBC_ERR_INVALID_ARG, "isotropic medium needs mu > 0 and -1 < nu < 0.5");
+        return FBC_OK;
+    }
+    if (m.kind == FBC_MATERIAL_CUBIC) {
+        if (!(m.C44 > 0.0) || !(m.C11 - m.C12 > 0.0) || !(m.C11 + 2.0 * m.C12 > 0.0) || !std::isfinite(m.C11))
+            return fail(FBC_ERR_INVALID_ARG, "cubic medium is not stable (C44 > 0, C11 > |C12|, C11 + 2 C12 > 0)");
+        // the line direction must map onto a cube axis (mirror x3 -> -x3 preserved)
+        bool ok = false;
+        for (int j = 0; j < 3; j++) ok = ok || std::fabs(std::fabs(Q[3 * j + 2]) - 1.0) < 1e-12;
+        if (!ok)
+            return fail(FBC_ERR_UNSUPPORTED,
+                        "cubic medium: the line direction must lie along a cube axis (mirror symmetry)");
+        return FBC_OK;
+    }
+    return fail(FBC_ERR_INVALID_ARG, "unknown material kind %d", m.kind);
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* fbc_last_error(void) { return g_last_error.c_str(); }
+
+const char* fbc_version(void) { return "fbc-gb300 0.1 (sm_103a)"; }
+
+void fbc_default_options(fbc_options* opt) {
+    if (!opt) return;
+    opt->precision = FBC_PREC_FP64;
+    opt->rich_n = 4;
+    opt->rich_N = 6;
+    opt->quad = 64;
+    opt->max_rhs = 1;
+    opt->flags = 0;
+}
+
+int fbc_plan_create(const fbc_geometry* geom, const fbc_material* mat, const fbc_options* opt_in,
+                    fbc_plan** out) {
+    g_last_error.clear();
+    if (!out) return fail(FBC_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (!geom || !mat) return fail(FBC_ERR_INVALID_ARG, "geometry or material is NULL");
+    fbc_options opt;
+    if (opt_in)
+        opt = *opt_in;
+    else
+        fbc_default_options(&opt);
+    const int n_i = geom->n_i, n_p = geom->n_p, L = geom->L;
+    if (n_i < 1 || n_p < 1) return fail(FBC_ERR_INVALID_ARG, "n_i and n_p must be >= 1");
+    if (n_i > (1 << 24) || n_p > (1 << 24)) return fail(FBC_ERR_INVALID_ARG, "too many columns");
+    if (!is_pow2(L) || L < 2 || L > 4096) return fail(FBC_ERR_INVALID_ARG, "L must be a power of two in [2, 4096]");
+    if (!(geom->c > 0.0) || !std::isfinite(geom->c)) return fail(FBC_ERR_INVALID_ARG, "c must be positive");
+    if (!geom->xy_i || !geom->xy_p) return fail(FBC_ERR_INVALID_ARG, "site lists are NULL");
+    if (opt.rich_n < 1 || opt.rich_N < 0 || opt.rich_n + opt.rich_N > fbc::kMaxRichImages || opt.rich_N > 12)
+        return fail(FBC_ERR_INVALID_ARG, "Richardson needs n >= 1, 0 <= N <= 12, n + N <= %d", fbc::kMaxRichImages);
+    if (opt.quad < 8 || opt.quad > fbc::kMaxQuad) return fail(FBC_ERR_INVALID_ARG, "quad must be in [8, %d]", fbc::kMaxQuad);
+    if (opt.max_rhs < 1 || opt.max_rhs > 4096) return fail(FBC_ERR_INVALID_ARG, "max_rhs must be in [1, 4096]");
+    if (opt.precision < FBC_PREC_FP64 || opt.precision > FBC_PREC_F32X2)
+        return fail(FBC_ERR_INVALID_ARG, "unknown precision %d", opt.precision);
+    if (opt.flags & ~FBC_PLAN_HOST_ONLY) return fail(FBC_ERR_INVALID_ARG, "unknown options.flags bits 0x%x", opt.flags);
+    const int32_t coord_lim = 1 << 20;
+    for (int t = 0; t < 2 * n_i; t++)
+        if (geom->xy_i[t] < -coord_lim || geom->xy_i[t] > coord_lim)
+            return fail(FBC_ERR_INVALID_ARG, "interface site coordinate out of range");
+    for (int t = 0; t < 2 * n_p; t++)
+        if (geom->xy_p[t] < -coord_lim || geom->xy_p[t] > coord_lim)
+            return fail(FBC_ERR_INVALID_ARG, "pad site coordinate out of range");
+    double Q[9];
+    int st = validate_material(*mat, Q);
+    if (st) return st;
+
+    // duplicates within each set
+    auto has_dup = [](const int32_t* xy, int n) {
+        std::vector<int64_t> keys(n);
+        for (int t = 0; t < n; t++) keys[t] = ((int64_t)xy[2 * t] << 32) ^ (uint32_t)xy[2 * t + 1];
+        std::sort(keys.begin(), keys.end());
+        return std::adjacent_find(keys.begin(), keys.end()) != keys.end();
+    };
+    if (has_dup(geom->xy_i, n_i)) return fail(FBC_ERR_INVALID_ARG, "duplicate interface site");
+    if (has_dup(geom->xy_p, n_p)) return fail(FBC_ERR_INVALID_ARG, "duplicate pad site");
+
+    fbc_plan* plan = new (std::nothrow) fbc_plan();
+    if (!plan) return fail(FBC_ERR_OOM, "host allocation of the plan failed");
+    fbc::Plan& P = plan->p;
+    P.host_only = (opt.flags & FBC_PLAN_HOST_ONLY) != 0;
+    if (!P.host_only) cudaGetDevice(&P.device);
+    P.n_i = n_i, P.n_p = n_p, P.L = L, P.K = L / 2 + 1, P.c = geom->c;
+    P.logL = 0;
+    while ((1 << P.logL) < L) P.logL++;
+    P.opt = opt;
+    P.precision = opt.precision;
+
+    // tiling
+    fbc::Plan* pp = &P;
+    Tiling ta = make_tiling(geom->xy_p, n_p, P.TA);
+    Tiling tb = make_tiling(geom->xy_i, n_i, P.TB);
+    P.n_ta = ta.n_tiles, P.n_tb = tb.n_tiles, P.NPpad = ta.n_pad, P.NIpad = tb.n_pad;
+    P.W = ta.max_w + tb.max_w - 1;
+    P.H = ta.max_h + tb.max_h - 1;
+    P.perm_p = ta.perm;
+    P.perm_i = tb.perm;
+    P.xy_p_sorted = ta.xy;
+    P.xy_i_sorted = tb.xy;
+
+    // difference box and the differences that occur
+    int pminx = INT32_MAX, pmaxx = INT32_MIN, pminy = INT32_MAX, pmaxy = INT32_MIN;
+    int iminx = INT32_MAX, imaxx = INT32_MIN, iminy = INT32_MAX, imaxy = INT32_MIN;
+    for (int t = 0; t < n_p; t++) {
+        pminx = std::min(pminx, geom->xy_p[2 * t]), pmaxx = std::max(pmaxx, geom->xy_p[2 * t]);
+        pminy = std::min(pminy, geom->xy_p[2 * t + 1]), pmaxy = std::max(pmaxy, geom->xy_p[2 * t + 1]);
+    }
+    for (int t = 0; t < n_i; t++) {
+        iminx = std::min(iminx, geom->xy_i[2 * t]), imaxx = std::max(imaxx, geom->xy_i[2 * t]);
+        iminy = std::min(iminy, geom->xy_i[2 * t + 1]), imaxy = std::max(imaxy, geom->xy_i[2 * t + 1]);
+    }
+    P.box_x0 = pminx - imaxx;
+    P.box_y0 = pminy - imaxy;
+    P.Dx = (pmaxx - iminx) - P.box_x0 + 1;
+    P.Dy = (pmaxy - iminy) - P.box_y0 + 1;
+    if ((double)P.Dx * P.Dy > 64.0 * 1024 * 1024) {
+        delete plan;
+        return fail(FBC_ERR_INVALID_ARG, "difference box %d x %d is too large", pp->Dx, pp->Dy);
+    }
+    std::vector<uint8_t> used((size_t)P.Dx * P.Dy, 0);
+    for (int a = 0; a < n_p; a++) {
+        int xa = geom->xy_p[2 * a] - P.box_x0, ya = geom->xy_p[2 * a + 1] - P.box_y0;
+        for (int b = 0; b < n_i; b++) {
+            int ix = xa - geom->xy_i[2 * b], iy = ya - geom->xy_i[2 * b + 1];
+            used[(size_t)iy * P.Dx + ix] = 1;
+        }
+    }
+    int zx = -P.box_x0, zy = -P.box_y0;
+    if (zx >= 0 && zx < P.Dx && zy >= 0 && zy < P.Dy && used[(size_t)zy * P.Dx + zx]) {
+        delete plan;
+        return fail(FBC_ERR_INVALID_ARG, "an interface site coincides with a pad site (d = 0 is singular)");
+    }
+    std::vector<int2> used_list;
+    for (int iy = 0; iy < P.Dy; iy++)
+        for (int ix = 0; ix < P.Dx; ix++)
+            if (used[(size_t)iy * P.Dx + ix]) used_list.push_back(make_int2(ix + P.box_x0, iy + P.box_y0));
+    P.n_used = (int)used_list.size();
+
+    // material for the device
+    P.mat.kind = mat->kind;
+    P.mat.nquad = opt.quad;
+    if (mat->kind == FBC_MATERIAL_ISOTROPIC) {
+        P.mat.kelvin_pre = 1.0 / (16.0 * M_PI * mat->mu * (1.0 - mat->nu));
+        P.mat.kelvin_a = 3.0 - 4.0 * mat->nu;
+    } else {
+        christoffel_form(*mat, Q, P.mat.K);
+    }
+    P.tp.L = L, P.tp.K = P.K, P.tp.Lh = L / 2, P.tp.c = P.c;
+    P.tp.rich_n = opt.rich_n, P.tp.rich_N = opt.rich_N;
+    richardson_cumulative(opt.rich_n, opt.rich_N, P.tp.W);
+    P.tp.box_x0 = P.box_x0, P.tp.box_y0 = P.box_y0, P.tp.Dx = P.Dx, P.tp.Dy = P.Dy;
+
+    if (P.host_only) {
+        *out = plan;
+        return FBC_OK;
+    }
+
+    // device buffers
+    size_t acc = 0;
+    std::vector<int> off_i(P.NIpad);
+    for (int s = 0; s < P.NIpad; s++) off_i[s] = tb.xy[s].x + P.W * tb.xy[s].y;
+    const size_t cells = (size_t)P.K * P.Dy * P.Dx;
+    const int nlb = P.NPpad / fbc::line_cols(L);
+#define ALLOC(ptr, n, what)                                  \
+    do {                                                     \
+        int s_ = dev_alloc(&(ptr), (n), acc, what);          \
+        if (s_) {                                            \
+            free_plan(P);                                    \
+            delete plan;                                     \
+            return s_;                                       \
+        }                                                    \
+    } while (0)
+    ALLOC(P.d_xy_p, P.NPpad, "xy_p");
+    ALLOC(P.d_off_i, P.NIpad, "off_i");
+    ALLOC(P.d_bbox_a, P.n_ta, "bbox_a");
+    ALLOC(P.d_bbox_b, P.n_tb, "bbox_b");
+    ALLOC(P.d_perm_i, P.NIpad, "perm_i");
+    ALLOC(P.d_perm_p, P.NPpad, "perm_p");
+    ALLOC(P.d_used, P.n_used, "used");
+    ALLOC(P.d_tw, L / 2, "twiddles");
+    ALLOC(P.d_twL, L, "table_twiddles");
+    size_t ws_before_table = acc;
+    ALLOC(P.d_table, cells * 6, "table");
+    P.table_bytes = acc - ws_before_table;
+    ALLOC(P.d_fh, (size_t)opt.max_rhs * P.K * P.NIpad * 6, "fh");
+    ALLOC(P.d_uh, (size_t)opt.max_rhs * P.K * P.NPpad * 6, "uh");
+    ALLOC(P.d_part, (size_t)opt.max_rhs * nlb * 3, "partials");
+    ALLOC(P.d_status, 1, "status");
+#undef ALLOC
+    P.workspace_bytes = acc - P.table_bytes;
+
+    std::vector<double2> tw(L / 2), twL(L);
+    for (int t = 0; t < L / 2; t++) {
+        double ang = 2.0 * M_PI * (double)t / (double)L;
+        tw[t] = make_double2(cos(ang), -sin(ang));
+    }
+    for (int t = 0; t < L; t++) {
+        double ang = 2.0 * M_PI * (double)t / (double)L;
+        twL[t] = make_double2(cos(ang), sin(ang));
+    }
+    cudaError_t e = cudaSuccess;
+#define UP(dst, src, n)                                                                   \
+    if (e == cudaSuccess) e = cudaMemcpy((dst), (src), sizeof(*(dst)) * (size_t)(n), cudaMemcpyHostToDevice)
+    UP(P.d_xy_p, ta.xy.data(), P.NPpad);
+    UP(P.d_off_i, off_i.data(), P.NIpad);
+    UP(P.d_bbox_a, ta.bbox.data(), P.n_ta);
+    UP(P.d_bbox_b, tb.bbox.data(), P.n_tb);
+    UP(P.d_perm_i, tb.perm.data(), P.NIpad);
+    UP(P.d_perm_p, ta.perm.data(), P.NPpad);
+    if (P.n_used) UP(P.d_used, used_list.data(), P.n_used);
+    UP(P.d_tw, tw.data(), L / 2);
+    UP(P.d_twL, twL.data(), L);
+#undef UP
+    if (e == cudaSuccess) e = cudaMemset(P.d_table, 0, cells * 6 * sizeof(double));
+    // padding columns of fh stay zero for ever: the forward transform never writes them
+    if (e == cudaSuccess) e = cudaMemset(P.d_fh, 0, (size_t)opt.max_rhs * P.K * P.NIpad * 6 * sizeof(double));
+    if (e == cudaSuccess) e = cudaMemset(P.d_status, 0, sizeof(int));
+    if (e != cudaSuccess) {
+        int s = cuda_fail(e, "plan upload");
+        free_plan(P);
+        delete plan;
+        return s;
+    }
+    *out = plan;
+    return FBC_OK;
+}
+
+int fbc_tabulate_kernel(fbc_plan* plan, void* stream) {
+    g_last_error.clear();
+    if (!plan) return fail(FBC_ERR_INVALID_ARG, "plan is NULL");
+    fbc::Plan& P = plan->p;
+    if (P.host_only) return fail(FBC_ERR_INVALID_ARG, "host-only plan");
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = fbc::launch_tabulate(P, st);
+    if (e != cudaSuccess) return cuda_fail(e, "tabulate");
+    P.tabulated = true;
+    if (P.precision != FBC_PREC_FP64) {
+        e = fbc::launch_derive_tables(P, P.precision, st);
+        if (e != cudaSuccess) return cuda_fail(e, "derive tables");
+    }
+    return FBC_OK;
+}
+
+int fbc_plan_set_precision(fbc_plan* plan, int32_t precision) {
+    g_last_error.clear();
+    if (!plan) return fail(FBC_ERR_INVALID_ARG, "plan is NULL");
+    if (precision < FBC_PREC_FP64 || precision > FBC_PREC_F32X2)
+        return fail(FBC_ERR_INVALID_ARG, "unknown precision %d", precision);
+    fbc::Plan& P = plan->p;
+    if (P.host_only) return fail(FBC_ERR_INVALID_ARG, "host-only plan");
+    const size_t cells = (size_t)P.K * P.Dy * P.Dx;
+    size_t acc = 0;
+    if (precision == FBC_PREC_FP32 && !P.d_table32) {
+        int s = dev_alloc(&P.d_table32, cells * 6, acc, "table32");
+        if (s) return s;
+    }
+    if (precision == FBC_PREC_F32X2 && !P.d_table_x2) {
+        int s = dev_alloc(&P.d_table_x2, cells * 12, acc, "table_x2");
+        if (s) return s;
+    }
+    P.workspace_bytes += acc;
+    P.precision = precision;
+    if (P.tabulated && precision != FBC_PREC_FP64) {
+        cudaError_t e = fbc::launch_derive_tables(P, precision, 0);
+        if (e == cudaSuccess) e = cudaDeviceSynchronize();
+        if (e != cudaSuccess) return cuda_fail(e, "derive tables");
+    }
+    return FBC_OK;
+}
+
+static int apply_common(fbc::Plan& P, const double* f, double* u, int32_t n_rhs, double alpha, double beta,
+                        uint32_t flags, cudaStream_t st) {
+    if (P.host_only) return fail(FBC_ERR_INVALID_ARG, "host-only plan");
+    if (!P.tabulated) return fail(FBC_ERR_NOT_TABULATED, "fbc_apply before fbc_tabulate_kernel");
+    if (!f || !u) return fail(FBC_ERR_INVALID_ARG, "f or u is NULL");
+    if (n_rhs < 1 || n_rhs > P.opt.max_rhs)
+        return fail(FBC_ERR_INVALID_ARG, "n_rhs = %d outside [1, max_rhs = %d]", n_rhs, P.opt.max_rhs);
+    if (flags & ~(FBC_APPLY_PROJECT_NEUTRAL | FBC_APPLY_ZERO_MEAN_U))
+        return fail(FBC_ERR_INVALID_ARG, "unknown apply flags 0x%x", flags);
+    if (!std::isfinite(alpha) || !std::isfinite(beta)) return fail(FBC_ERR_INVALID_ARG, "alpha/beta not finite");
+    const size_t fb = (size_t)n_rhs * P.n_i * P.L * 3 * sizeof(double);
+    const size_t ub = (size_t)n_rhs * P.n_p * P.L * 3 * sizeof(double);
+    const char* fc = (const char*)f;
+    const char* uc = (const char*)u;
+    if (fc < uc + ub && uc < fc + fb) return fail(FBC_ERR_INVALID_ARG, "f and u overlap");
+    if (P.precision == FBC_PREC_FP32 && !P.d_table32) return fail(FBC_ERR_INVALID_ARG, "FP32 table missing");
+    if (P.precision == FBC_PREC_F32X2 && !P.d_table_x2) return fail(FBC_ERR_INVALID_ARG, "F32X2 table missing");
+    if (P.timing) FBC_CUDA(cudaEventRecord(P.ev[0], st));
+    cudaError_t e = fbc::launch_forward(P, f, n_rhs, (flags & FBC_APPLY_PROJECT_NEUTRAL) != 0, st);
+    if (e != cudaSuccess) return cuda_fail(e, "forward transform");
+    if (P.timing) FBC_CUDA(cudaEventRecord(P.ev[1], st));
+    e = fbc::launch_contract(P, n_rhs, st);
+    if (e != cudaSuccess) return cuda_fail(e, "mode contraction");
+    if (P.timing) FBC_CUDA(cudaEventRecord(P.ev[2], st));
+    e = fbc::launch_inverse(P, u, n_rhs, alpha, beta, (flags & FBC_APPLY_ZERO_MEAN_U) != 0, st);
+    if (e != cudaSuccess) return cuda_fail(e, "inverse transform");
+    if (P.timing) {
+        FBC_CUDA(cudaEventRecord(P.ev[3], st));
+        P.timed_once = true;
+    }
+    return FBC_OK;
+}
+
+int fbc_apply(fbc_plan* plan, const double* f, double* u, int32_t n_rhs, double alpha, double beta,
+              uint32_t flags, void* stream) {
+    g_last_error.clear();
+    if (!plan) return fail(FBC_ERR_INVALID_ARG, "plan is NULL");
+    return apply_common(plan->p, f, u, n_rhs, alpha, beta, flags, (cudaStream_t)stream);
+}
+
+int fbc_apply_host(fbc_plan* plan, const double* f_host, double* u_host, int32_t n_rhs, double alpha, double beta,
+                   uint32_t flags, void* stream) {
+    g_last_error.clear();
+    if (!plan) return fail(FBC_ERR_INVALID_ARG, "plan is NULL");
+    fbc::Plan& P = plan->p;
+    if (P.host_only) return fail(FBC_ERR_INVALID_ARG, "host-only plan");
+    if (!f_host || !u_host) return fail(FBC_ERR_INVALID_ARG, "f or u is NULL");
+    if (n_rhs < 1 || n_rhs > P.opt.max_rhs)
+        return fail(FBC_ERR_INVALID_ARG, "n_rhs = %d outside [1, max_rhs = %d]", n_rhs, P.opt.max_rhs);
+    cudaStream_t st = (cudaStream_t)stream;
+    size_t acc = 0;
+    if (!P.d_stage_f) {
+        int s = dev_alloc(&P.d_stage_f, (size_t)P.opt.max_rhs * P.n_i * P.L * 3, acc, "stage_f");
+        if (s) return s;
+    }
+    if (!P.d_stage_u) {
+        int s = dev_alloc(&P.d_stage_u, (size_t)P.opt.max_rhs * P.n_p * P.L * 3, acc, "stage_u");
+        if (s) return s;
+    }
+    P.workspace_bytes += acc;
+    const size_t fb = (size_t)n_rhs * P.n_i * P.L * 3 * sizeof(double);
+    const size_t ub = (size_t)n_rhs * P.n_p * P.L * 3 * sizeof(double);
+    FBC_CUDA(cudaMemcpyAsync(P.d_stage_f, f_host, fb, cudaMemcpyHostToDevice, st));
+    if (beta != 0.0) FBC_CUDA(cudaMemcpyAsync(P.d_stage_u, u_host, ub, cudaMemcpyHostToDevice, st));
+    int s = apply_common(P, P.d_stage_f, P.d_stage_u, n_rhs, alpha, beta, flags, st);
+    if (s) return s;
+    FBC_CUDA(cudaMemcpyAsync(u_host, P.d_stage_u, ub, cudaMemcpyDeviceToHost, st));
+    FBC_CUDA(cudaStreamSynchronize(st));
+    return FBC_OK;
+}
+
+int fbc_plan_set_timing(fbc_plan* plan, int32_t enable) {
+    g_last_error.clear();
+    if (!plan) return fail(FBC_ERR_INVALID_ARG, "plan is NULL");
+    fbc::Plan& P = plan->p;
+    if (P.host_only) return fail(FBC_ERR_INVALID_ARG, "host-only plan");
+    if (enable && !P.ev[0])
+        for (auto& e : P.ev) FBC_CUDA(cudaEventCreate(&e));
+    P.timing = enable != 0;
+    P.timed_once = false;
+    return FBC_OK;
+}
+
+int fbc_plan_stage_times(fbc_plan* plan, float* ms) {
+    g_last_error.clear();
+    if (!plan || !ms) return fail(FBC_ERR_INVALID_ARG, "plan or ms is NULL");
+    fbc::Plan& P = plan->p;
+    if (!P.timed_once) return fail(FBC_ERR_INVALID_ARG, "no timed apply since timing was enabled");
+    FBC_CUDA(cudaEventSynchronize(P.ev[3]));
+    for (int t = 0; t < 3; t++) FBC_CUDA(cudaEventElapsedTime(&ms[t], P.ev[t], P.ev[t + 1]));
+    return FBC_OK;
+}
+
+int fbc_plan_info_get(const fbc_plan* plan, fbc_plan_info* info) {
+    g_last_error.clear();
+    if (!plan || !info) return fail(FBC_ERR_INVALID_ARG, "plan or info is NULL");
+    const fbc::Plan& P = plan->p;
+    info->n_i = P.n_i, info->n_p = P.n_p, info->L = P.L, info->K = P.K;
+    info->max_rhs = P.opt.max_rhs, info->precision = P.precision;
+    info->tile_a = P.TA, info->tile_b = P.TB, info->n_tiles_a = P.n_ta, info->n_tiles_b = P.n_tb;
+    info->box_x0 = P.box_x0, info->box_y0 = P.box_y0, info->box_nx = P.Dx, info->box_ny = P.Dy;
+    info->sub_w = P.W, info->sub_h = P.H, info->n_used_d = P.n_used;
+    info->tabulated = P.tabulated ? 1 : 0;
+    info->pair_modes_per_rhs = (double)P.n_p * (double)P.n_i * (double)P.K;
+    info->table_bytes = P.table_bytes;
+    info->workspace_bytes = P.workspace_bytes;
+    return FBC_OK;
+}
+
+int fbc_plan_layout(const fbc_plan* plan, int32_t* perm_i, int32_t* perm_p, int32_t* xy_i, int32_t* xy_p) {
+    g_last_error.clear();
+    if (!plan) return fail(FBC_ERR_INVALID_ARG, "plan is NULL");
+    const fbc::Plan& P = plan->p;
+    for (int s = 0; s < P.NIpad; s++) {
+        if (perm_i) perm_i[s] = P.perm_i[s];
+        if (xy_i) xy_i[2 * s] = P.xy_i_sorted[s].x, xy_i[2 * s + 1] = P.xy_i_sorted[s].y;
+    }
+    for (int s = 0; s < P.NPpad; s++) {
+        if (perm_p) perm_p[s] = P.perm_p[s];
+        if (xy_p) xy_p[2 * s] = P.xy_p_sorted[s].x, xy_p[2 * s + 1] = P.xy_p_sorted[s].y;
+    }
+    return FBC_OK;
+}
+
+int fbc_get_mode_table(const fbc_plan* plan, const int32_t* d, int32_t nd, double* out) {
+    g_last_error.clear();
+    if (!plan || (!d && nd) || (!out && nd) || nd < 0) return fail(FBC_ERR_INVALID_ARG, "bad arguments");
+    const fbc::Plan& P = plan->p;
+    if (P.host_only) return fail(FBC_ERR_INVALID_ARG, "host-only plan");
+    if (!P.tabulated) return fail(FBC_ERR_NOT_TABULATED, "table not tabulated");
+    FBC_CUDA(cudaDeviceSynchronize());
+    for (int t = 0; t < nd; t++) {
+        int ix = d[2 * t] - P.box_x0, iy = d[2 * t + 1] - P.box_y0;
+        if (ix < 0 || ix >= P.Dx || iy < 0 || iy >= P.Dy)
+            return fail(FBC_ERR_INVALID_ARG, "difference (%d, %d) outside the table box", d[2 * t], d[2 * t + 1]);
+        for (int k = 0; k < P.K; k++) {
+            const double* src = P.d_table + (((size_t)k * P.Dy + iy) * P.Dx + ix) * 6;
+            FBC_CUDA(cudaMemcpy(out + ((size_t)t * P.K + k) * 6, src, 6 * sizeof(double), cudaMemcpyDeviceToHost));
+        }
+    }
+    return FBC_OK;
+}
+
+int fbc_plan_sync_status(fbc_plan* plan, void* stream) {
+    g_last_error.clear();
+    if (!plan) return fail(FBC_ERR_INVALID_ARG, "plan is NULL");
+    fbc::Plan& P = plan->p;
+    if (P.host_only) return fail(FBC_ERR_INVALID_ARG, "host-only plan");
+    cudaStream_t st = (cudaStream_t)stream;
+    int h = 0;
+    FBC_CUDA(cudaMemcpyAsync(&h, P.d_status, sizeof(int), cudaMemcpyDeviceToHost, st));
+    FBC_CUDA(cudaStreamSynchronize(st));
+    if (h != 0) {
+        FBC_CUDA(cudaMemsetAsync(P.d_status, 0, sizeof(int), st));
+        FBC_CUDA(cudaStreamSynchronize(st));
+        return fail(FBC_ERR_TIMEOUT, "device status word %d", h);
+    }
+    return FBC_OK;
+}
+
+void fbc_destroy(fbc_plan* plan) {
+    if (!plan) return;
+    if (!plan->p.host_only) cudaDeviceSynchronize();
+    free_plan(plan->p);
+    delete plan;
+}
+
+}  // extern "C"

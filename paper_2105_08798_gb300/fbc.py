@@ -1,0 +1,340 @@
+"""Thin ctypes binding of ``libfbc.so`` (the C ABI declared in ``include/fbc.h``).
+
+Every entry point of the header has a function of the same name here that
+only marshals arguments (structures, raw device pointers, the CUDA stream
+handle) and turns a non-zero status into ``FBCError``.  All arithmetic runs in
+the library's CUDA kernels; there is no CPU fallback: ``load()`` raises if the
+library is missing, and every call raises if it fails.
+
+``Plan`` is a convenience wrapper over the same calls that accepts torch
+tensors (device memory, ``data_ptr``) and numpy arrays (host memory).
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libfbc.so")
+
+FBC_OK = 0
+FBC_ERR_INVALID_ARG = 1
+FBC_ERR_OOM = 2
+FBC_ERR_CUDA = 3
+FBC_ERR_NOT_TABULATED = 4
+FBC_ERR_TIMEOUT = 5
+FBC_ERR_UNSUPPORTED = 6
+
+FBC_MATERIAL_ISOTROPIC = 0
+FBC_MATERIAL_CUBIC = 1
+
+FBC_PREC_FP64 = 0
+FBC_PREC_FP32 = 1
+FBC_PREC_F32X2 = 2
+PRECISIONS = {"fp64": FBC_PREC_FP64, "fp32": FBC_PREC_FP32, "f32x2": FBC_PREC_F32X2}
+
+FBC_PLAN_HOST_ONLY = 1
+
+FBC_APPLY_PROJECT_NEUTRAL = 1
+FBC_APPLY_ZERO_MEAN_U = 2
+
+
+class FBCError(RuntimeError):
+    def __init__(self, status: int, where: str, message: str):
+        super().__init__(f"{where} failed with status {status}: {message}")
+        self.status = status
+
+
+class fbc_geometry(ctypes.Structure):
+    _fields_ = [("n_i", ctypes.c_int32), ("n_p", ctypes.c_int32), ("L", ctypes.c_int32), ("c", ctypes.c_double),
+                ("xy_i", ctypes.POINTER(ctypes.c_int32)), ("xy_p", ctypes.POINTER(ctypes.c_int32))]
+
+
+class fbc_material(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("mu", ctypes.c_double), ("nu", ctypes.c_double),
+                ("C11", ctypes.c_double), ("C12", ctypes.c_double), ("C44", ctypes.c_double),
+                ("Q", ctypes.c_double * 9)]
+
+
+class fbc_options(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int32), ("rich_n", ctypes.c_int32), ("rich_N", ctypes.c_int32),
+                ("quad", ctypes.c_int32), ("max_rhs", ctypes.c_int32), ("flags", ctypes.c_int32)]
+
+
+class fbc_plan_info(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int32) for n in ("n_i", "n_p", "L", "K", "max_rhs", "precision", "tile_a", "tile_b",
+                                              "n_tiles_a", "n_tiles_b", "box_x0", "box_y0", "box_nx", "box_ny",
+                                              "sub_w", "sub_h", "n_used_d", "tabulated")] + [
+        ("pair_modes_per_rhs", ctypes.c_double), ("table_bytes", ctypes.c_size_t),
+        ("workspace_bytes", ctypes.c_size_t)]
+
+    def as_dict(self) -> dict:
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+_lock = threading.Lock()
+_lib = None
+
+_P = ctypes.POINTER
+_vp = ctypes.c_void_p
+_SIGNATURES = {
+    "fbc_default_options": (None, [_P(fbc_options)]),
+    "fbc_plan_create": (ctypes.c_int, [_P(fbc_geometry), _P(fbc_material), _P(fbc_options), _P(_vp)]),
+    "fbc_tabulate_kernel": (ctypes.c_int, [_vp, _vp]),
+    "fbc_apply": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int32, ctypes.c_double, ctypes.c_double, ctypes.c_uint32,
+                                 _vp]),
+    "fbc_apply_host": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int32, ctypes.c_double, ctypes.c_double,
+                                      ctypes.c_uint32, _vp]),
+    "fbc_plan_set_precision": (ctypes.c_int, [_vp, ctypes.c_int32]),
+    "fbc_plan_info_get": (ctypes.c_int, [_vp, _P(fbc_plan_info)]),
+    "fbc_get_mode_table": (ctypes.c_int, [_vp, _P(ctypes.c_int32), ctypes.c_int32, _P(ctypes.c_double)]),
+    "fbc_plan_layout": (ctypes.c_int, [_vp, _P(ctypes.c_int32), _P(ctypes.c_int32), _P(ctypes.c_int32),
+                                       _P(ctypes.c_int32)]),
+    "fbc_plan_sync_status": (ctypes.c_int, [_vp, _vp]),
+    "fbc_plan_set_timing": (ctypes.c_int, [_vp, ctypes.c_int32]),
+    "fbc_plan_stage_times": (ctypes.c_int, [_vp, _P(ctypes.c_float)]),
+    "fbc_destroy": (None, [_vp]),
+    "fbc_last_error": (ctypes.c_char_p, []),
+    "fbc_version": (ctypes.c_char_p, []),
+}
+
+
+def load(path: str | None = None) -> ctypes.CDLL:
+    """Load ``libfbc.so`` (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            p = path or LIB_PATH
+            if not os.path.exists(p):
+                raise FBCError(-1, "load", f"{p} is missing: run `python -m paper_2105_08798_gb300.build`")
+            lib = ctypes.CDLL(p)
+            for name, (res, args) in _SIGNATURES.items():
+                fn = getattr(lib, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = lib
+    return _lib
+
+
+def _check(status: int, where: str):
+    if status != FBC_OK:
+        raise FBCError(status, where, load().fbc_last_error().decode(errors="replace"))
+
+
+def _stream_handle(stream) -> int | None:
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return int(stream.cuda_stream)  # torch.cuda.Stream
+
+
+# ---- same-name wrappers of the C ABI ---------------------------------------
+def fbc_default_options() -> fbc_options:
+    o = fbc_options()
+    load().fbc_default_options(ctypes.byref(o))
+    return o
+
+
+def fbc_plan_create(geom: fbc_geometry, mat: fbc_material, opt: fbc_options | None) -> int:
+    h = _vp()
+    _check(load().fbc_plan_create(ctypes.byref(geom), ctypes.byref(mat), ctypes.byref(opt) if opt else None,
+                                  ctypes.byref(h)), "fbc_plan_create")
+    return h.value
+
+
+def fbc_tabulate_kernel(plan: int, stream=None):
+    _check(load().fbc_tabulate_kernel(plan, _stream_handle(stream)), "fbc_tabulate_kernel")
+
+
+def fbc_apply(plan: int, f_ptr: int, u_ptr: int, n_rhs: int, alpha: float, beta: float, flags: int, stream=None):
+    _check(load().fbc_apply(plan, f_ptr, u_ptr, n_rhs, alpha, beta, flags, _stream_handle(stream)), "fbc_apply")
+
+
+def fbc_apply_host(plan: int, f_ptr: int, u_ptr: int, n_rhs: int, alpha: float, beta: float, flags: int,
+                   stream=None):
+    _check(load().fbc_apply_host(plan, f_ptr, u_ptr, n_rhs, alpha, beta, flags, _stream_handle(stream)),
+           "fbc_apply_host")
+
+
+def fbc_plan_set_precision(plan: int, precision: int):
+    _check(load().fbc_plan_set_precision(plan, precision), "fbc_plan_set_precision")
+
+
+def fbc_plan_info_get(plan: int) -> fbc_plan_info:
+    info = fbc_plan_info()
+    _check(load().fbc_plan_info_get(plan, ctypes.byref(info)), "fbc_plan_info_get")
+    return info
+
+
+def fbc_plan_layout(plan: int) -> dict:
+    info = fbc_plan_info_get(plan)
+    nip, npp = info.n_tiles_b * info.tile_b, info.n_tiles_a * info.tile_a
+    perm_i = np.zeros(nip, np.int32)
+    perm_p = np.zeros(npp, np.int32)
+    xy_i = np.zeros((nip, 2), np.int32)
+    xy_p = np.zeros((npp, 2), np.int32)
+    P32 = _P(ctypes.c_int32)
+    _check(load().fbc_plan_layout(plan, perm_i.ctypes.data_as(P32), perm_p.ctypes.data_as(P32),
+                                  xy_i.ctypes.data_as(P32), xy_p.ctypes.data_as(P32)), "fbc_plan_layout")
+    return {"perm_i": perm_i, "perm_p": perm_p, "xy_i": xy_i, "xy_p": xy_p}
+
+
+def fbc_get_mode_table(plan: int, d: np.ndarray, K: int) -> np.ndarray:
+    d = np.ascontiguousarray(d, dtype=np.int32).reshape(-1, 2)
+    out = np.zeros((len(d), K, 6))
+    _check(load().fbc_get_mode_table(plan, d.ctypes.data_as(_P(ctypes.c_int32)), len(d),
+                                     out.ctypes.data_as(_P(ctypes.c_double))), "fbc_get_mode_table")
+    return out
+
+
+def fbc_plan_sync_status(plan: int, stream=None):
+    _check(load().fbc_plan_sync_status(plan, _stream_handle(stream)), "fbc_plan_sync_status")
+
+
+def fbc_plan_set_timing(plan: int, enable: bool):
+    _check(load().fbc_plan_set_timing(plan, 1 if enable else 0), "fbc_plan_set_timing")
+
+
+def fbc_plan_stage_times(plan: int) -> list[float]:
+    ms = (ctypes.c_float * 3)()
+    _check(load().fbc_plan_stage_times(plan, ms), "fbc_plan_stage_times")
+    return [float(x) for x in ms]
+
+
+def fbc_destroy(plan: int):
+    load().fbc_destroy(plan)
+
+
+def fbc_last_error() -> str:
+    return load().fbc_last_error().decode(errors="replace")
+
+
+def fbc_version() -> str:
+    return load().fbc_version().decode()
+
+
+# ---- convenience wrapper -----------------------------------------------------
+def material_struct(material: dict) -> fbc_material:
+    m = fbc_material()
+    kind = material.get("kind", "isotropic")
+    Q = np.asarray(material.get("Q", np.eye(3)), dtype=np.float64).reshape(9)
+    for t in range(9):
+        m.Q[t] = float(Q[t])
+    if kind == "isotropic":
+        m.kind = FBC_MATERIAL_ISOTROPIC
+        m.mu, m.nu = float(material["mu"]), float(material["nu"])
+    elif kind == "cubic":
+        m.kind = FBC_MATERIAL_CUBIC
+        m.C11, m.C12, m.C44 = float(material["C11"]), float(material["C12"]), float(material["C44"])
+    else:
+        raise ValueError(f"unknown material kind {kind!r}")
+    return m
+
+
+class Plan:
+    """Owning handle of one ``fbc_plan`` (tables + workspace on the current device)."""
+
+    def __init__(self, xy_i, xy_p, L: int, material: dict, c: float = 1.0, precision: str | int = "fp64",
+                 rich_n: int | None = None, rich_N: int | None = None, quad: int | None = None, max_rhs: int = 1,
+                 host_only: bool = False):
+        self._h = None
+        xy_i = np.ascontiguousarray(xy_i, dtype=np.int32)
+        xy_p = np.ascontiguousarray(xy_p, dtype=np.int32)
+        g = fbc_geometry(len(xy_i), len(xy_p), int(L), float(c), xy_i.ctypes.data_as(_P(ctypes.c_int32)),
+                         xy_p.ctypes.data_as(_P(ctypes.c_int32)))
+        o = fbc_default_options()
+        o.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        if rich_n is not None:
+            o.rich_n = rich_n
+        if rich_N is not None:
+            o.rich_N = rich_N
+        if quad is not None:
+            o.quad = quad
+        o.max_rhs = int(max_rhs)
+        o.flags = FBC_PLAN_HOST_ONLY if host_only else 0
+        self._h = fbc_plan_create(g, material_struct(material), o)
+        self.n_i, self.n_p, self.L, self.K = len(xy_i), len(xy_p), int(L), int(L) // 2 + 1
+        self.max_rhs = int(max_rhs)
+
+    @property
+    def handle(self) -> int:
+        if self._h is None:
+            raise FBCError(FBC_ERR_INVALID_ARG, "Plan", "plan is closed")
+        return self._h
+
+    def tabulate(self, stream=None):
+        fbc_tabulate_kernel(self.handle, stream)
+
+    def set_precision(self, precision: str | int):
+        fbc_plan_set_precision(self.handle, PRECISIONS[precision] if isinstance(precision, str) else int(precision))
+
+    def info(self) -> dict:
+        return fbc_plan_info_get(self.handle).as_dict()
+
+    def layout(self) -> dict:
+        return fbc_plan_layout(self.handle)
+
+    def mode_table(self, d) -> np.ndarray:
+        return fbc_get_mode_table(self.handle, d, self.K)
+
+    @staticmethod
+    def flags(project: bool = True, zero_mean: bool = False) -> int:
+        return (FBC_APPLY_PROJECT_NEUTRAL if project else 0) | (FBC_APPLY_ZERO_MEAN_U if zero_mean else 0)
+
+    def apply(self, f, u, alpha: float = 1.0, beta: float = 0.0, project: bool = True, zero_mean: bool = False,
+              stream=None):
+        """u <- beta u + alpha G f on device tensors ``f [n_rhs][n_i][L][3]``, ``u [n_rhs][n_p][L][3]`` (float64)."""
+        import torch
+
+        n_rhs = f.shape[0]
+        if f.dtype != torch.float64 or u.dtype != torch.float64 or not f.is_cuda or not u.is_cuda:
+            raise TypeError("f and u must be float64 CUDA tensors")
+        if tuple(f.shape) != (n_rhs, self.n_i, self.L, 3) or tuple(u.shape) != (n_rhs, self.n_p, self.L, 3):
+            raise ValueError(f"shape mismatch: f {tuple(f.shape)}, u {tuple(u.shape)}")
+        if not f.is_contiguous() or not u.is_contiguous():
+            raise ValueError("f and u must be contiguous")
+        if stream is None:
+            stream = torch.cuda.current_stream(f.device)
+        fbc_apply(self.handle, f.data_ptr(), u.data_ptr(), n_rhs, alpha, beta, self.flags(project, zero_mean), stream)
+        return u
+
+    def apply_host(self, f: np.ndarray, u: np.ndarray, alpha: float = 1.0, beta: float = 0.0, project: bool = True,
+                   zero_mean: bool = False, stream=None):
+        """Host-memory form: numpy (or pinned torch CPU) arrays in, ``u`` updated in place."""
+        fp = f.data_ptr() if hasattr(f, "data_ptr") else f.ctypes.data
+        up = u.data_ptr() if hasattr(u, "data_ptr") else u.ctypes.data
+        n_rhs = f.shape[0]
+        fbc_apply_host(self.handle, fp, up, n_rhs, alpha, beta, self.flags(project, zero_mean), stream)
+        return u
+
+    def set_timing(self, enable: bool = True):
+        fbc_plan_set_timing(self.handle, enable)
+
+    def stage_times(self) -> list[float]:
+        """[forward, contraction, inverse] milliseconds of the last timed apply."""
+        return fbc_plan_stage_times(self.handle)
+
+    def sync_status(self, stream=None):
+        fbc_plan_sync_status(self.handle, stream)
+
+    def close(self):
+        if self._h is not None:
+            fbc_destroy(self._h)
+            self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
