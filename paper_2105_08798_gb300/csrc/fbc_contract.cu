@@ -264,7 +264,7 @@ size_t contract_smem(const Plan& P, int TB, int per_entry) {
 
 template <typename KernelT>
 cudaError_t launch_one(KernelT kern, const ContractArgs& A, dim3 grid, int threads, size_t smem, cudaStream_t st) {
-    if (smem > 48 * 1024) {
+    if (smem > 32 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e) return e;
     }

@@ -240,7 +240,8 @@ cudaError_t launch_forward(Plan& P, const double* f, int n_rhs, bool project, cu
     const int NC = line_cols(P.L);
     const size_t smem = line_smem(P.L, NC);
     cudaError_t e;
-    if (smem > 48 * 1024 && (e = cudaFuncSetAttribute(k_forward, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)))
+    // opt in above the default dynamic limit (the kernel's static arrays count towards 48 KB)
+    if (smem > 32 * 1024 && (e = cudaFuncSetAttribute(k_forward, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)))
         return e;
     dim3 grid(P.NIpad / NC, n_rhs);
     k_forward<<<grid, 256, smem, st>>>(f, P.d_perm_i, P.d_tw, P.d_fh, P.n_i, P.L, P.logL, P.K, P.NIpad, NC);
@@ -257,7 +258,7 @@ cudaError_t launch_inverse(Plan& P, double* u, int n_rhs, double alpha, double b
     const int NC = line_cols(P.L);
     const size_t smem = line_smem(P.L, NC);
     cudaError_t e;
-    if (smem > 48 * 1024 && (e = cudaFuncSetAttribute(k_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)))
+    if (smem > 32 * 1024 && (e = cudaFuncSetAttribute(k_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)))
         return e;
     const int nb = P.NPpad / NC;
     dim3 grid(nb, n_rhs);

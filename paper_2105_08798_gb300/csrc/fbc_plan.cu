@@ -188,6 +188,22 @@ void free_plan(fbc::Plan& P) {
         if (e) cudaEventDestroy(e), e = nullptr;
 }
 
+// Allocate the derived table a reduced-precision contraction reads (once).
+int ensure_derived(fbc::Plan& P, int precision) {
+    const size_t cells = (size_t)P.K * P.Dy * P.Dx;
+    size_t acc = 0;
+    if (precision == FBC_PREC_FP32 && !P.d_table32) {
+        int s = dev_alloc(&P.d_table32, cells * 6, acc, "table32");
+        if (s) return s;
+    }
+    if (precision == FBC_PREC_F32X2 && !P.d_table_x2) {
+        int s = dev_alloc(&P.d_table_x2, cells * 12, acc, "table_x2");
+        if (s) return s;
+    }
+    P.workspace_bytes += acc;
+    return FBC_OK;
+}
+
 int validate_material(const fbc_material& m, double Q[9]) {
     bool allzero = true;
     for (int t = 0; t < 9; t++) allzero = allzero && m.Q[t] == 0.0;
@@ -396,6 +412,11 @@ int fbc_plan_create(const fbc_geometry* geom, const fbc_material* mat, const fbc
     ALLOC(P.d_status, 1, "status");
 #undef ALLOC
     P.workspace_bytes = acc - P.table_bytes;
+    if (int s_ = ensure_derived(P, P.precision)) {
+        free_plan(P);
+        delete plan;
+        return s_;
+    }
 
     std::vector<double2> tw(L / 2), twL(L);
     for (int t = 0; t < L / 2; t++) {
@@ -456,17 +477,7 @@ int fbc_plan_set_precision(fbc_plan* plan, int32_t precision) {
         return fail(FBC_ERR_INVALID_ARG, "unknown precision %d", precision);
     fbc::Plan& P = plan->p;
     if (P.host_only) return fail(FBC_ERR_INVALID_ARG, "host-only plan");
-    const size_t cells = (size_t)P.K * P.Dy * P.Dx;
-    size_t acc = 0;
-    if (precision == FBC_PREC_FP32 && !P.d_table32) {
-        int s = dev_alloc(&P.d_table32, cells * 6, acc, "table32");
-        if (s) return s;
-    }
-    if (precision == FBC_PREC_F32X2 && !P.d_table_x2) {
-        int s = dev_alloc(&P.d_table_x2, cells * 12, acc, "table_x2");
-        if (s) return s;
-    }
-    P.workspace_bytes += acc;
+    if (int st = ensure_derived(P, precision)) return st;
     P.precision = precision;
     if (P.tabulated && precision != FBC_PREC_FP64) {
         cudaError_t e = fbc::launch_derive_tables(P, precision, 0);

@@ -243,7 +243,7 @@ cudaError_t launch_tabulate(Plan& P, cudaStream_t st) {
     double* gs = nullptr;
     if ((e = cudaMallocAsync((void**)&gs, per_d * chunk, st))) return e;
     const size_t smem = per_d;
-    if (smem > 48 * 1024) {
+    if (smem > 32 * 1024) {
         if ((e = cudaFuncSetAttribute(k_line_dft, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem))) {
             cudaFreeAsync(gs, st);
             return e;
