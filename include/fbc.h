@@ -212,6 +212,22 @@ const char* fbc_last_error(void);
 /* Library version string. */
 const char* fbc_version(void);
 
+/* Allocation-free zero-mean step.  The paper has no counterpart of this
+ * call: it exists for callers that cannot call cudaMalloc where they need
+ * it -- an atomistic engine that owns the whole device through its own
+ * memory pool, code running while a CUDA graph is captured, or a relaxation
+ * loop that must not take the allocator's device-wide lock.
+ *   u: DEVICE double [n_rhs][n_p][L][3]; for every right-hand side and
+ *      component the mean over all n_p * L pad atoms is subtracted in place
+ *      (the same result as the FBC_APPLY_ZERO_MEAN_U step of fbc_apply).
+ * 1 <= n_rhs <= 64; larger n_rhs returns FBC_ERR_INVALID_ARG.  Needs no
+ * plan.  The reduction scratch is a fixed 384 KiB array inside the library
+ * that every GPU loading the library keeps until the process exits; all
+ * calls share it, so calls that overlap on the GPU race.  The first call on
+ * a device looks up the array's device address (make it before any stream
+ * capture).  Asynchronous on `stream`; allocates nothing. */
+int fbc_zero_mean_static(double* u, int32_t n_rhs, int32_t n_p, int32_t L, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -100,6 +100,9 @@ cudaError_t launch_inverse(Plan& P, double* u, int n_rhs, double alpha, double b
                            cudaStream_t st);
 cudaError_t launch_derive_tables(Plan& P, int precision, cudaStream_t st);
 
+// Record the message fbc_last_error() returns for this thread; returns code.
+int report_error(int code, const char* msg);
+
 // line-transform blocking: columns per CTA so that a CTA holds 2048 complex points
 inline int line_cols(int L) {
     int nc = 2048 / L;

@@ -238,6 +238,11 @@ int validate_material(const fbc_material& m, double Q[9]) {
 
 }  // namespace
 
+int fbc::report_error(int code, const char* msg) {
+    g_last_error = msg ? msg : "";
+    return code;
+}
+
 extern "C" {
 
 const char* fbc_last_error(void) { return g_last_error.c_str(); }

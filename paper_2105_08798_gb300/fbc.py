@@ -100,6 +100,7 @@ _SIGNATURES = {
     "fbc_destroy": (None, [_vp]),
     "fbc_last_error": (ctypes.c_char_p, []),
     "fbc_version": (ctypes.c_char_p, []),
+    "fbc_zero_mean_static": (ctypes.c_int, [_vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _vp]),
 }
 
 
@@ -216,6 +217,10 @@ def fbc_last_error() -> str:
 
 def fbc_version() -> str:
     return load().fbc_version().decode()
+
+
+def fbc_zero_mean_static(u_ptr: int, n_rhs: int, n_p: int, L: int, stream=None):
+    _check(load().fbc_zero_mean_static(u_ptr, n_rhs, n_p, L, _stream_handle(stream)), "fbc_zero_mean_static")
 
 
 # ---- convenience wrapper -----------------------------------------------------
