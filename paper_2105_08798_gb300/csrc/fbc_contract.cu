@@ -183,13 +183,15 @@ __device__ __forceinline__ void df_fold(float& Thi, float& Tlo, float S, float E
     Tlo = __fsub_rn(e, __fsub_rn(Thi, s));
 }
 
+// Double-float: each table entry is staged as three 16-byte records
+// (a11h, a11l, a12h, a12l), (a22h, a22l, a33h, a33l), (b13h, b13l, b23h, b23l)
+// and each interface column as four: the (hi, lo) pairs of x and y' and off_b.
 template <int TA, int TB>
 __global__ void __launch_bounds__(TA) k_contract_x2(ContractArgs A) {
-    extern __shared__ float2 smemx2[];
+    extern __shared__ float4 smemx2[];
     const int HW = A.H * A.W;
-    float2* s_tab = smemx2;             // [6][HW] (hi, lo)
-    float2* s_f = s_tab + 6 * HW;       // [TB][6] (hi, lo)
-    int* s_off = (int*)(s_f + TB * 6);  // [TB]
+    float4* s_tab = smemx2;            // [HW][3]
+    float4* s_f = s_tab + 3 * HW;      // [TB][4]
     const int tA = blockIdx.x;
     const int k = A.k0 + blockIdx.y;
     const int r = blockIdx.z;
@@ -206,48 +208,57 @@ __global__ void __launch_bounds__(TA) k_contract_x2(ContractArgs A) {
         for (int e = threadIdx.x; e < HW; e += TA) {
             const int iy = e / A.W, ix = e - iy * A.W;
             const int gx = ox + ix - A.box_x0, gy = oy + iy - A.box_y0;
-            float h[6] = {0, 0, 0, 0, 0, 0}, l[6] = {0, 0, 0, 0, 0, 0};
+            float4 q0 = make_float4(0, 0, 0, 0), q1 = q0, q2 = q0;
             if (gx < A.Dx && gy < A.Dy) {
                 const float2* src = (const float2*)(tk + ((size_t)gy * A.Dx + gx) * 12);
-#pragma unroll
-                for (int c = 0; c < 3; c++) {
-                    const float2 vh = __ldg(src + c), vl = __ldg(src + 3 + c);
-                    h[2 * c] = vh.x, h[2 * c + 1] = vh.y, l[2 * c] = vl.x, l[2 * c + 1] = vl.y;
-                }
+                const float2 h01 = __ldg(src), h23 = __ldg(src + 1), h45 = __ldg(src + 2);
+                const float2 l01 = __ldg(src + 3), l23 = __ldg(src + 4), l45 = __ldg(src + 5);
+                q0 = make_float4(h01.x, l01.x, h01.y, l01.y);
+                q1 = make_float4(h23.x, l23.x, h23.y, l23.y);
+                q2 = make_float4(h45.x, l45.x, h45.y, l45.y);
             }
+            s_tab[3 * e] = q0, s_tab[3 * e + 1] = q1, s_tab[3 * e + 2] = q2;
+        }
+        for (int j = threadIdx.x; j < TB; j += TA) {
+            float h[6], l[6];
 #pragma unroll
-            for (int c = 0; c < 6; c++) s_tab[c * HW + e] = make_float2(h[c], l[c]);
+            for (int c = 0; c < 6; c++) {
+                const double v = fk[(size_t)(tB * TB + j) * 6 + c];
+                h[c] = (float)v;
+                l[c] = (float)(v - (double)h[c]);
+            }
+            s_f[4 * j + 0] = make_float4(h[0], l[0], h[1], l[1]);
+            s_f[4 * j + 1] = make_float4(h[2], l[2], h[3], l[3]);
+            s_f[4 * j + 2] = make_float4(h[4], l[4], h[5], l[5]);
+            s_f[4 * j + 3] = make_float4(__int_as_float(A.off_i[tB * TB + j]), 0.f, 0.f, 0.f);
         }
-        for (int e = threadIdx.x; e < TB * 6; e += TA) {
-            const double v = fk[(size_t)tB * TB * 6 + e];
-            const float hi = (float)v;
-            s_f[e] = make_float2(hi, (float)(v - (double)hi));
-        }
-        for (int e = threadIdx.x; e < TB; e += TA) s_off[e] = A.off_i[tB * TB + e];
         __syncthreads();
         const int base = (xa.x - ox) + A.W * (xa.y - oy);
         float S[6] = {0, 0, 0, 0, 0, 0}, E[6] = {0, 0, 0, 0, 0, 0};
 #pragma unroll 2
         for (int j = 0; j < TB; j++) {
-            const int idx = base - s_off[j];
-            const float2 a11 = s_tab[idx], a12 = s_tab[HW + idx], a22 = s_tab[2 * HW + idx];
-            const float2 a33 = s_tab[3 * HW + idx], b13 = s_tab[4 * HW + idx], b23 = s_tab[5 * HW + idx];
-            const float2* fj = s_f + j * 6;
-#pragma unroll
-            for (int v = 0; v < 2; v++) {
-                const float2 x0 = fj[3 * v], x1 = fj[3 * v + 1], x2 = fj[3 * v + 2];
-                float* Sv = S + 3 * v;
-                float* Ev = E + 3 * v;
-                df_mac(a11.x, a11.y, x0.x, x0.y, Sv[0], Ev[0]);
-                df_mac(a12.x, a12.y, x1.x, x1.y, Sv[0], Ev[0]);
-                df_mac(-b13.x, -b13.y, x2.x, x2.y, Sv[0], Ev[0]);
-                df_mac(a12.x, a12.y, x0.x, x0.y, Sv[1], Ev[1]);
-                df_mac(a22.x, a22.y, x1.x, x1.y, Sv[1], Ev[1]);
-                df_mac(-b23.x, -b23.y, x2.x, x2.y, Sv[1], Ev[1]);
-                df_mac(b13.x, b13.y, x0.x, x0.y, Sv[2], Ev[2]);
-                df_mac(b23.x, b23.y, x1.x, x1.y, Sv[2], Ev[2]);
-                df_mac(a33.x, a33.y, x2.x, x2.y, Sv[2], Ev[2]);
-            }
+            const float4 f0 = s_f[4 * j], f1 = s_f[4 * j + 1], f2 = s_f[4 * j + 2], f3 = s_f[4 * j + 3];
+            const int idx = base - __float_as_int(f3.x);
+            const float4 t0 = s_tab[3 * idx], t1 = s_tab[3 * idx + 1], t2 = s_tab[3 * idx + 2];
+            // x = (f0.x, f0.y) (f0.z, f0.w) (f1.x, f1.y); y' = (f1.z, f1.w) (f2.x, f2.y) (f2.z, f2.w)
+            df_mac(t0.x, t0.y, f0.x, f0.y, S[0], E[0]);
+            df_mac(t0.z, t0.w, f0.z, f0.w, S[0], E[0]);
+            df_mac(-t2.x, -t2.y, f1.x, f1.y, S[0], E[0]);
+            df_mac(t0.z, t0.w, f0.x, f0.y, S[1], E[1]);
+            df_mac(t1.x, t1.y, f0.z, f0.w, S[1], E[1]);
+            df_mac(-t2.z, -t2.w, f1.x, f1.y, S[1], E[1]);
+            df_mac(t2.x, t2.y, f0.x, f0.y, S[2], E[2]);
+            df_mac(t2.z, t2.w, f0.z, f0.w, S[2], E[2]);
+            df_mac(t1.z, t1.w, f1.x, f1.y, S[2], E[2]);
+            df_mac(t0.x, t0.y, f1.z, f1.w, S[3], E[3]);
+            df_mac(t0.z, t0.w, f2.x, f2.y, S[3], E[3]);
+            df_mac(-t2.x, -t2.y, f2.z, f2.w, S[3], E[3]);
+            df_mac(t0.z, t0.w, f1.z, f1.w, S[4], E[4]);
+            df_mac(t1.x, t1.y, f2.x, f2.y, S[4], E[4]);
+            df_mac(-t2.z, -t2.w, f2.z, f2.w, S[4], E[4]);
+            df_mac(t2.x, t2.y, f1.z, f1.w, S[5], E[5]);
+            df_mac(t2.z, t2.w, f2.x, f2.y, S[5], E[5]);
+            df_mac(t1.z, t1.w, f2.z, f2.w, S[5], E[5]);
         }
 #pragma unroll
         for (int c = 0; c < 6; c++) df_fold(Th[c], Tl[c], S[c], E[c]);
@@ -296,8 +307,8 @@ cudaError_t launch_contract(Plan& P, int n_rhs, cudaStream_t st) {
                           contract_smem<float>(P, kTileB, 4), st);
     }
     if (P.precision == FBC_PREC_F32X2) {
-        return launch_one(k_contract_x2<kTileA, kTileB>, A, dim3(P.n_ta, P.K, n_rhs), kTileA,
-                          contract_smem<float2>(P, kTileB, 8), st);
+        const size_t sx2 = (size_t)P.H * P.W * 48 + (size_t)kTileB * 64 + 16;
+        return launch_one(k_contract_x2<kTileA, kTileB>, A, dim3(P.n_ta, P.K, n_rhs), kTileA, sx2, st);
     }
     return cudaErrorInvalidValue;
 }
