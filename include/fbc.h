@@ -67,6 +67,7 @@ extern "C" {
 /* ---- fbc_apply flags ------------------------------------------------- */
 #define FBC_APPLY_PROJECT_NEUTRAL 1u /* remove the net interface force first */
 #define FBC_APPLY_ZERO_MEAN_U 2u     /* set the mean pad displacement to zero after (Eq. 23) */
+#define FBC_APPLY_NO_GRAPH 4u        /* fbc_batch_apply only: launch directly instead of replaying a graph */
 
 /* Column geometry (Sec. 2.1: line-periodic slab of a Bravais lattice).
  * The interface columns are the force sources (the paper's Lambda^{i+}),
@@ -211,6 +212,50 @@ const char* fbc_last_error(void);
 
 /* Library version string. */
 const char* fbc_version(void);
+
+/* ---- batches of plans ------------------------------------------------
+ * Many independent FBC instances (uneven sizes, each with its own right-hand
+ * sides) updated together -- the pad update of Eqs. 1, 22, 37-38 for each
+ * instance -- by one fixed sequence of launches: batched line transforms and
+ * ONE persistent contraction launch that drains a cost-sorted tile queue over
+ * all instances (no CTA ever waits for another), captured into a CUDA graph
+ * on first use and replayed. */
+typedef struct fbc_batch fbc_batch;
+
+typedef struct fbc_batch_info {
+    int32_t n_plans, precision;
+    int32_t n_contract_items;   /* (instance, mode, pad tile, rhs block) work items */
+    int32_t grid;               /* persistent contraction CTAs */
+    int32_t occupancy;          /* resident contraction CTAs per SM */
+    int32_t lpt_order;          /* 1: longest-first queue, 0: instance-major */
+    int32_t kernel_launches;    /* launches per apply (with both flags) */
+    size_t smem_contract;       /* dynamic shared memory of the contraction CTAs */
+    double pair_modes;          /* sum over instances of n_p n_i K n_rhs */
+} fbc_batch_info;
+
+/* Bind n_plans tabulated plans (same precision, each at most once) to their
+ * DEVICE buffers: f[i] [n_rhs[i]][n_i][L][3], u[i] [n_rhs[i]][n_p][L][3].
+ * The buffers are fixed for the batch's lifetime (the graph refers to them).
+ * Allocates the work lists; synchronous. */
+int fbc_batch_create(fbc_plan* const* plans, int32_t n_plans, const double* const* f, double* const* u,
+                     const int32_t* n_rhs, fbc_batch** out);
+
+/* u_i <- beta u_i + alpha G_i f_i for every instance (flags as fbc_apply, plus
+ * FBC_APPLY_NO_GRAPH).  The first call with a new (alpha, beta, flags)
+ * captures the launch sequence into a CUDA graph (on an internal stream);
+ * later calls replay it on `stream`.  Asynchronous; do not run two applies of
+ * one batch, or of batches sharing a plan, concurrently. */
+int fbc_batch_apply(fbc_batch* batch, double alpha, double beta, uint32_t flags, void* stream);
+
+/* Time the contraction launch for a few persistent grid sizes and both queue
+ * orders and keep the fastest (synchronous; reallocates the queue).  *best_ms
+ * (may be NULL) receives the chosen configuration's contraction time. */
+int fbc_batch_autotune(fbc_batch* batch, void* stream, double* best_ms);
+
+int fbc_batch_info_get(const fbc_batch* batch, fbc_batch_info* info);
+
+/* Release the batch (not its plans).  NULL is ignored. */
+void fbc_batch_destroy(fbc_batch* batch);
 
 /* Allocation-free zero-mean step.  The paper has no counterpart of this
  * call: it exists for callers that cannot call cudaMalloc where they need

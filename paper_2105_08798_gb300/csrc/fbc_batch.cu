@@ -1,0 +1,303 @@
+// Batches of plans: many FBC instances of uneven size, each with its own
+// right-hand sides, updated by one fixed sequence of launches -- batched
+// forward transforms, projections, ONE persistent contraction launch that
+// drains a cost-sorted (longest processing time first) tile queue over all
+// instances, batched inverse transforms and zero-mean steps -- captured once
+// into a CUDA graph and replayed.
+//
+// The persistent kernel's CTAs take work with atomicAdd on a counter that is
+// reset by the graph; no CTA waits for another, so nothing can spin.
+//
+// Autotuning: the persistent grid size (resident CTAs per SM times the SM
+// count, or fewer) and the order of the contraction queue (LPT or the natural
+// instance-major order) are chosen by timing the contraction launch.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <numeric>
+#include <vector>
+
+#include "fbc_internal.cuh"
+
+namespace {
+
+struct Item {
+    int4 w;
+    double cost;
+};
+
+}  // namespace
+
+struct fbc_batch {
+    int n = 0;
+    int precision = 0;
+    int device = 0;
+    std::vector<fbc_plan*> plans;
+    std::vector<int> n_rhs;
+    std::vector<Item> con_items;  // natural order
+    std::vector<int4> fwd, proj, inv, zm;
+    fbc::LineArgs* d_largs = nullptr;
+    fbc::ContractArgs* d_cargs = nullptr;
+    int* d_nrhs = nullptr;
+    int4* d_fwd = nullptr;
+    int4* d_proj = nullptr;
+    int4* d_con = nullptr;
+    int4* d_inv = nullptr;
+    int4* d_zm = nullptr;
+    int* d_counter = nullptr;
+    size_t smem_con = 0, smem_line = 0;
+    int sm_count = 152, occupancy = 1, grid = 152;
+    int lpt = 1;
+    cudaStream_t cap = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    double g_alpha = 0.0, g_beta = 0.0;
+    uint32_t g_flags = 0;
+    bool graph_valid = false;
+    double pair_modes = 0.0;
+};
+
+namespace {
+
+int bfail(int code, const char* msg) { return fbc::report_error(code, msg); }
+
+int bcuda(cudaError_t e, const char* what) {
+    char buf[256];
+    snprintf(buf, sizeof(buf), "%s: %s", what, cudaGetErrorString(e));
+    return fbc::report_error(e == cudaErrorMemoryAllocation ? FBC_ERR_OOM : FBC_ERR_CUDA, buf);
+}
+
+void free_batch(fbc_batch* b) {
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    if (b->cap) cudaStreamDestroy(b->cap);
+    void* bufs[] = {b->d_largs, b->d_cargs, b->d_nrhs, b->d_fwd, b->d_proj, b->d_con, b->d_inv, b->d_zm, b->d_counter};
+    for (void* p : bufs)
+        if (p) cudaFree(p);
+}
+
+template <class T>
+cudaError_t upload(T** dst, const std::vector<T>& src) {
+    if (*dst) cudaFree(*dst), *dst = nullptr;
+    size_t bytes = std::max<size_t>(1, src.size()) * sizeof(T);
+    cudaError_t e = cudaMalloc((void**)dst, bytes);
+    if (e) return e;
+    if (!src.empty()) e = cudaMemcpy(*dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice);
+    return e;
+}
+
+std::vector<int4> ordered_items(const fbc_batch* b, bool lpt) {
+    std::vector<Item> it = b->con_items;
+    if (lpt) std::stable_sort(it.begin(), it.end(), [](const Item& x, const Item& y) { return x.cost > y.cost; });
+    std::vector<int4> out(it.size());
+    for (size_t t = 0; t < it.size(); t++) out[t] = it[t].w;
+    return out;
+}
+
+// Enqueue the whole batched update on `st` (direct launches, no graph).
+cudaError_t enqueue(fbc_batch* b, double alpha, double beta, uint32_t flags, cudaStream_t st) {
+    cudaError_t e;
+    const bool project = flags & FBC_APPLY_PROJECT_NEUTRAL, zmean = flags & FBC_APPLY_ZERO_MEAN_U;
+    if ((e = fbc::launch_batch_line(0, b->d_largs, b->d_fwd, (int)b->fwd.size(), b->smem_line, 0, 0, 0, st))) return e;
+    if (project && (e = fbc::launch_batch_line(1, b->d_largs, b->d_proj, (int)b->proj.size(), 0, 0, 0, 0, st))) return e;
+    if ((e = cudaMemsetAsync(b->d_counter, 0, sizeof(int), st))) return e;
+    if ((e = fbc::launch_batch_contract(b->precision, b->d_cargs, b->d_nrhs, b->d_con, (int)b->con_items.size(),
+                                        b->d_counter, b->grid, b->smem_con, st)))
+        return e;
+    if ((e = fbc::launch_batch_line(2, b->d_largs, b->d_inv, (int)b->inv.size(), b->smem_line, alpha, beta,
+                                    zmean ? 1 : 0, st)))
+        return e;
+    if (zmean && (e = fbc::launch_batch_line(3, b->d_largs, b->d_zm, (int)b->zm.size(), 0, 0, 0, 0, st))) return e;
+    return cudaSuccess;
+}
+
+}  // namespace
+
+extern "C" {
+
+int fbc_batch_create(fbc_plan* const* plans, int32_t n_plans, const double* const* f, double* const* u,
+                     const int32_t* n_rhs, fbc_batch** out) {
+    fbc::report_error(FBC_OK, "");
+    if (!out) return bfail(FBC_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (!plans || !f || !u || !n_rhs || n_plans < 1) return bfail(FBC_ERR_INVALID_ARG, "bad batch arguments");
+    int prec = -1;
+    for (int i = 0; i < n_plans; i++) {
+        if (!plans[i]) return bfail(FBC_ERR_INVALID_ARG, "a plan is NULL");
+        const fbc::Plan& P = plans[i]->p;
+        if (P.host_only) return bfail(FBC_ERR_INVALID_ARG, "host-only plan in a batch");
+        if (!P.tabulated) return bfail(FBC_ERR_NOT_TABULATED, "every plan of a batch must be tabulated");
+        if (prec < 0) prec = P.precision;
+        if (P.precision != prec) return bfail(FBC_ERR_INVALID_ARG, "all plans of a batch need the same precision");
+        if (n_rhs[i] < 1 || n_rhs[i] > P.opt.max_rhs) return bfail(FBC_ERR_INVALID_ARG, "n_rhs outside [1, max_rhs]");
+        if (!f[i] || !u[i]) return bfail(FBC_ERR_INVALID_ARG, "f or u of an instance is NULL");
+        for (int j = 0; j < i; j++)
+            if (plans[j] == plans[i]) return bfail(FBC_ERR_INVALID_ARG, "a plan appears twice (its workspace would race)");
+    }
+    fbc_batch* b = new (std::nothrow) fbc_batch();
+    if (!b) return bfail(FBC_ERR_OOM, "host allocation failed");
+    b->n = n_plans;
+    b->precision = prec;
+    b->plans.assign(plans, plans + n_plans);
+    b->n_rhs.assign(n_rhs, n_rhs + n_plans);
+    cudaGetDevice(&b->device);
+    cudaDeviceGetAttribute(&b->sm_count, cudaDevAttrMultiProcessorCount, b->device);
+    std::vector<fbc::LineArgs> la(n_plans);
+    std::vector<fbc::ContractArgs> ca(n_plans);
+    const int RB = fbc::batch_rhs_block();
+    int max_L = 2;
+    for (int i = 0; i < n_plans; i++) {
+        const fbc::Plan& P = plans[i]->p;
+        la[i] = fbc::make_line_args(P, f[i], u[i]);
+        ca[i] = fbc::make_contract_args(P);
+        max_L = std::max(max_L, P.L);
+        b->smem_con = std::max(b->smem_con, fbc::batch_contract_smem(prec, P.W, P.H));
+        const int R = n_rhs[i];
+        const int NC = la[i].NC;
+        for (int r = 0; r < R; r++) {
+            for (int blk = 0; blk < P.NIpad / NC; blk++) b->fwd.push_back(make_int4(i, blk, r, 0));
+            b->proj.push_back(make_int4(i, 0, r, 0));
+            for (int blk = 0; blk < P.NPpad / NC; blk++) b->inv.push_back(make_int4(i, blk, r, 0));
+            const size_t n_el = (size_t)P.n_p * P.L * 3;
+            const int nch = (int)std::max<size_t>(1, std::min<size_t>(64, (n_el + 4095) / 4096));
+            for (int c = 0; c < nch; c++) b->zm.push_back(make_int4(i, c, r, nch));
+        }
+        // contraction items; cost ~ pair-modes / measured rate of the tile kind
+        const double per_tile = (double)P.n_tb * P.TA * P.TB;
+        for (int k = 0; k < P.K; k++)
+            for (int tA = 0; tA < P.n_ta; tA++) {
+                if (prec == FBC_PREC_FP32 && k > 0) {
+                    for (int rb = 0; rb < (R + RB - 1) / RB; rb++) {
+                        const int cnt = std::min(RB, R - rb * RB);
+                        b->con_items.push_back({make_int4(i, k, tA, rb), per_tile * cnt / 1500.0});
+                    }
+                } else {
+                    const double rate = (prec == FBC_PREC_F32X2) ? 130.0 : 34.0;
+                    for (int r = 0; r < R; r++) b->con_items.push_back({make_int4(i, k, tA, r), per_tile / rate});
+                }
+            }
+        b->pair_modes += (double)P.n_p * P.n_i * P.K * R;
+    }
+    if (b->smem_con > 227 * 1024) {
+        free_batch(b);
+        delete b;
+        return bfail(FBC_ERR_UNSUPPORTED, "an instance's staged sub-box exceeds shared memory");
+    }
+    b->smem_line = fbc::batch_line_smem(max_L);
+    std::vector<int> nr(b->n_rhs);
+    cudaError_t e = cudaSuccess;
+    if (!e) e = upload(&b->d_largs, la);
+    if (!e) e = upload(&b->d_cargs, ca);
+    if (!e) e = upload(&b->d_nrhs, nr);
+    if (!e) e = upload(&b->d_fwd, b->fwd);
+    if (!e) e = upload(&b->d_proj, b->proj);
+    if (!e) e = upload(&b->d_inv, b->inv);
+    if (!e) e = upload(&b->d_zm, b->zm);
+    if (!e) e = upload(&b->d_con, ordered_items(b, true));
+    if (!e) e = cudaMalloc((void**)&b->d_counter, sizeof(int));
+    if (!e) e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
+    if (e) {
+        int st = bcuda(e, "batch setup");
+        free_batch(b);
+        delete b;
+        return st;
+    }
+    b->occupancy = fbc::batch_contract_occupancy(prec, b->smem_con);
+    b->grid = b->occupancy * b->sm_count;
+    *out = b;
+    return FBC_OK;
+}
+
+int fbc_batch_apply(fbc_batch* b, double alpha, double beta, uint32_t flags, void* stream) {
+    fbc::report_error(FBC_OK, "");
+    if (!b) return bfail(FBC_ERR_INVALID_ARG, "batch is NULL");
+    if (flags & ~(FBC_APPLY_PROJECT_NEUTRAL | FBC_APPLY_ZERO_MEAN_U | FBC_APPLY_NO_GRAPH))
+        return bfail(FBC_ERR_INVALID_ARG, "unknown apply flags");
+    if (!std::isfinite(alpha) || !std::isfinite(beta)) return bfail(FBC_ERR_INVALID_ARG, "alpha/beta not finite");
+    cudaStream_t st = (cudaStream_t)stream;
+    const uint32_t gflags = flags & ~FBC_APPLY_NO_GRAPH;
+    if (flags & FBC_APPLY_NO_GRAPH) {
+        cudaError_t e = enqueue(b, alpha, beta, gflags, st);
+        return e ? bcuda(e, "batched apply") : FBC_OK;
+    }
+    if (!b->graph_valid || b->g_alpha != alpha || b->g_beta != beta || b->g_flags != gflags) {
+        if (b->exec) cudaGraphExecDestroy(b->exec), b->exec = nullptr;
+        if (b->graph) cudaGraphDestroy(b->graph), b->graph = nullptr;
+        cudaError_t e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeRelaxed);
+        if (e) return bcuda(e, "begin capture");
+        cudaError_t e1 = enqueue(b, alpha, beta, gflags, b->cap);
+        e = cudaStreamEndCapture(b->cap, &b->graph);
+        if (e1) return bcuda(e1, "capture of the batched apply");
+        if (e) return bcuda(e, "end capture");
+        e = cudaGraphInstantiate(&b->exec, b->graph, 0);
+        if (e) return bcuda(e, "graph instantiate");
+        b->g_alpha = alpha, b->g_beta = beta, b->g_flags = gflags, b->graph_valid = true;
+    }
+    cudaError_t e = cudaGraphLaunch(b->exec, st);
+    return e ? bcuda(e, "graph launch") : FBC_OK;
+}
+
+int fbc_batch_autotune(fbc_batch* b, void* stream, double* best_ms) {
+    fbc::report_error(FBC_OK, "");
+    if (!b) return bfail(FBC_ERR_INVALID_ARG, "batch is NULL");
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) || cudaEventCreate(&e1)) return bfail(FBC_ERR_CUDA, "event creation failed");
+    // the transforms run once so the contraction sees real inputs
+    cudaError_t e = fbc::launch_batch_line(0, b->d_largs, b->d_fwd, (int)b->fwd.size(), b->smem_line, 0, 0, 0, st);
+    double best = 1e300;
+    int best_grid = b->grid, best_lpt = b->lpt;
+    const int grids[] = {b->occupancy * b->sm_count, std::max(1, b->occupancy - 1) * b->sm_count, b->sm_count};
+    for (int lpt = 1; lpt >= 0 && !e; lpt--) {
+        if ((e = upload(&b->d_con, ordered_items(b, lpt == 1)))) break;
+        for (int g : grids) {
+            float ms_sum = 0.0f;
+            for (int rep = 0; rep < 2 && !e; rep++) {
+                if ((e = cudaMemsetAsync(b->d_counter, 0, sizeof(int), st))) break;
+                cudaEventRecord(e0, st);
+                e = fbc::launch_batch_contract(b->precision, b->d_cargs, b->d_nrhs, b->d_con,
+                                               (int)b->con_items.size(), b->d_counter, g, b->smem_con, st);
+                cudaEventRecord(e1, st);
+                if (!e) e = cudaEventSynchronize(e1);
+                float ms = 0.0f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (rep == 1) ms_sum += ms;  // the first repetition warms caches
+            }
+            if (!e && ms_sum < best) best = ms_sum, best_grid = g, best_lpt = lpt;
+        }
+    }
+    if (!e) e = upload(&b->d_con, ordered_items(b, best_lpt == 1));
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (e) return bcuda(e, "autotune");
+    b->grid = best_grid;
+    b->lpt = best_lpt;
+    b->graph_valid = false;
+    if (best_ms) *best_ms = best;
+    return FBC_OK;
+}
+
+int fbc_batch_info_get(const fbc_batch* b, fbc_batch_info* info) {
+    fbc::report_error(FBC_OK, "");
+    if (!b || !info) return bfail(FBC_ERR_INVALID_ARG, "batch or info is NULL");
+    info->n_plans = b->n;
+    info->precision = b->precision;
+    info->n_contract_items = (int32_t)b->con_items.size();
+    info->grid = b->grid;
+    info->occupancy = b->occupancy;
+    info->lpt_order = b->lpt;
+    info->kernel_launches = 3 + 2;  // forward, projection, contraction, inverse, zero mean (when flagged)
+    info->smem_contract = b->smem_con;
+    info->pair_modes = b->pair_modes;
+    return FBC_OK;
+}
+
+void fbc_batch_destroy(fbc_batch* b) {
+    if (!b) return;
+    cudaDeviceSynchronize();
+    free_batch(b);
+    delete b;
+}
+
+}  // extern "C"

@@ -24,29 +24,14 @@
 namespace fbc {
 namespace {
 
-struct ContractArgs {
-    const double* tab;   // [K][Dy][Dx][6]
-    const float* tab32;  // [K][Dy][Dx][6]
-    const float* tabx2;  // [K][Dy][Dx][12] (hi[6], lo[6])
-    const double* fh;    // [rhs][K][NIpad][6]
-    double* uh;          // [rhs][K][NPpad][6]
-    const int2* xy_p;
-    const int* off_i;
-    const int4* bbox_a;
-    const int4* bbox_b;
-    int n_tb, K, Dx, Dy, box_x0, box_y0, W, H, NIpad, NPpad, k0;
-};
 
 template <int TA, int TB>
-__global__ void __launch_bounds__(TA) k_contract_fp64(ContractArgs A) {
-    extern __shared__ double smem64[];
+__device__ __forceinline__ void tile_fp64(const ContractArgs& A, int tA, int k, int r, void* smem_raw) {
+    double* smem64 = (double*)smem_raw;
     const int HW = A.H * A.W;
     double* s_tab = smem64;              // [6][HW]
     double* s_f = s_tab + 6 * HW;        // [TB][6]
     int* s_off = (int*)(s_f + TB * 6);   // [TB]
-    const int tA = blockIdx.x;
-    const int k = A.k0 + blockIdx.y;
-    const int r = blockIdx.z;
     const int a = tA * TA + threadIdx.x;
     const int2 xa = A.xy_p[a];
     const int4 bA = A.bbox_a[tA];
@@ -93,15 +78,12 @@ __global__ void __launch_bounds__(TA) k_contract_fp64(ContractArgs A) {
 }
 
 template <int TA, int TB>
-__global__ void __launch_bounds__(TA) k_contract_fp32(ContractArgs A) {
-    extern __shared__ float smem32[];
+__device__ __forceinline__ void tile_fp32(const ContractArgs& A, int tA, int k, int r, void* smem_raw) {
+    float* smem32 = (float*)smem_raw;
     const int HW = A.H * A.W;
     float* s_tab = smem32;              // [6][HW]
     float* s_f = s_tab + 6 * HW;        // [TB][6]
     int* s_off = (int*)(s_f + TB * 6);  // [TB]
-    const int tA = blockIdx.x;
-    const int k = A.k0 + blockIdx.y;
-    const int r = blockIdx.z;
     const int a = tA * TA + threadIdx.x;
     const int2 xa = A.xy_p[a];
     const int4 bA = A.bbox_a[tA];
@@ -147,6 +129,88 @@ __global__ void __launch_bounds__(TA) k_contract_fp32(ContractArgs A) {
     o[0] = acc0, o[1] = acc1, o[2] = acc2, o[3] = acc3, o[4] = acc4, o[5] = acc5;
 }
 
+
+// FP32 with RB right-hand sides per thread: the staged table entries of a
+// (pad column, interface column) pair are read once and applied to RB
+// transformed force columns held in shared memory, so the gathers amortise
+// over the right-hand sides and the loop is FFMA-bound.  grid.z = ceil(n_rhs / RB).
+template <int TA, int TB, int RB>
+__device__ __forceinline__ void tile_fp32_rb(const ContractArgs& A, int tA, int k, int rb, int n_rhs, void* smem_raw) {
+    float* smem32rb = (float*)smem_raw;
+    const int HW = A.H * A.W;
+    float* s_tab = smem32rb;                          // [6][HW]
+    // the force records start at the next 16-byte boundary after the table (HW may be odd)
+    float4* s_fx = (float4*)((char*)smem32rb + (((size_t)6 * HW * 4 + 15) & ~(size_t)15));  // [RB][TB]: (x0, x1, x2, y0)
+    float2* s_fy = (float2*)(s_fx + RB * TB);         // [RB][TB]: (y1, y2)
+    int* s_off = (int*)(s_fy + RB * TB);              // [TB]
+    const int r0 = rb * RB;
+    const int a = tA * TA + threadIdx.x;
+    const int2 xa = A.xy_p[a];
+    const int4 bA = A.bbox_a[tA];
+    float acc[RB][6];
+#pragma unroll
+    for (int q = 0; q < RB; q++)
+#pragma unroll
+        for (int c = 0; c < 6; c++) acc[q][c] = 0.f;
+    const float* tk = A.tab32 + (size_t)k * A.Dy * A.Dx * 6;
+    for (int tB = 0; tB < A.n_tb; tB++) {
+        const int4 bB = A.bbox_b[tB];
+        const int ox = bA.x - bB.y, oy = bA.z - bB.w;
+        __syncthreads();
+        for (int e = threadIdx.x; e < HW; e += TA) {
+            const int iy = e / A.W, ix = e - iy * A.W;
+            const int gx = ox + ix - A.box_x0, gy = oy + iy - A.box_y0;
+            float2 v0 = make_float2(0, 0), v1 = v0, v2 = v0;
+            if (gx < A.Dx && gy < A.Dy) {
+                const float2* src = (const float2*)(tk + ((size_t)gy * A.Dx + gx) * 6);
+                v0 = __ldg(src), v1 = __ldg(src + 1), v2 = __ldg(src + 2);
+            }
+            s_tab[0 * HW + e] = v0.x, s_tab[1 * HW + e] = v0.y;
+            s_tab[2 * HW + e] = v1.x, s_tab[3 * HW + e] = v1.y;
+            s_tab[4 * HW + e] = v2.x, s_tab[5 * HW + e] = v2.y;
+        }
+        for (int e = threadIdx.x; e < RB * TB; e += TA) {
+            const int q = e / TB, j = e - q * TB;
+            float v[6] = {0, 0, 0, 0, 0, 0};
+            if (r0 + q < n_rhs) {
+                const double* src = A.fh + (((size_t)(r0 + q) * A.K + k) * A.NIpad + (size_t)tB * TB + j) * 6;
+#pragma unroll
+                for (int c = 0; c < 6; c++) v[c] = (float)src[c];
+            }
+            s_fx[e] = make_float4(v[0], v[1], v[2], v[3]);
+            s_fy[e] = make_float2(v[4], v[5]);
+        }
+        for (int e = threadIdx.x; e < TB; e += TA) s_off[e] = A.off_i[tB * TB + e];
+        __syncthreads();
+        const int base = (xa.x - ox) + A.W * (xa.y - oy);
+#pragma unroll 2
+        for (int j = 0; j < TB; j++) {
+            const int idx = base - s_off[j];
+            const float a11 = s_tab[idx], a12 = s_tab[HW + idx], a22 = s_tab[2 * HW + idx];
+            const float a33 = s_tab[3 * HW + idx], b13 = s_tab[4 * HW + idx], b23 = s_tab[5 * HW + idx];
+#pragma unroll
+            for (int q = 0; q < RB; q++) {
+                const float4 fx = s_fx[q * TB + j];
+                const float2 fy = s_fy[q * TB + j];
+                float* c = acc[q];
+                c[0] = fmaf(a11, fx.x, fmaf(a12, fx.y, fmaf(-b13, fx.z, c[0])));
+                c[1] = fmaf(a12, fx.x, fmaf(a22, fx.y, fmaf(-b23, fx.z, c[1])));
+                c[2] = fmaf(b13, fx.x, fmaf(b23, fx.y, fmaf(a33, fx.z, c[2])));
+                c[3] = fmaf(a11, fx.w, fmaf(a12, fy.x, fmaf(-b13, fy.y, c[3])));
+                c[4] = fmaf(a12, fx.w, fmaf(a22, fy.x, fmaf(-b23, fy.y, c[4])));
+                c[5] = fmaf(b13, fx.w, fmaf(b23, fy.x, fmaf(a33, fy.y, c[5])));
+            }
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < RB; q++) {
+        if (r0 + q >= n_rhs) break;
+        double* o = A.uh + (((size_t)(r0 + q) * A.K + k) * A.NPpad + a) * 6;
+#pragma unroll
+        for (int c = 0; c < 6; c++) o[c] = acc[q][c];
+    }
+}
+
 // ---- double-float helpers -------------------------------------------------
 struct df {
     float hi, lo;
@@ -187,14 +251,11 @@ __device__ __forceinline__ void df_fold(float& Thi, float& Tlo, float S, float E
 // (a11h, a11l, a12h, a12l), (a22h, a22l, a33h, a33l), (b13h, b13l, b23h, b23l)
 // and each interface column as four: the (hi, lo) pairs of x and y' and off_b.
 template <int TA, int TB>
-__global__ void __launch_bounds__(TA) k_contract_x2(ContractArgs A) {
-    extern __shared__ float4 smemx2[];
+__device__ __forceinline__ void tile_x2(const ContractArgs& A, int tA, int k, int r, void* smem_raw) {
+    float4* smemx2 = (float4*)smem_raw;
     const int HW = A.H * A.W;
     float4* s_tab = smemx2;            // [HW][3]
     float4* s_f = s_tab + 3 * HW;      // [TB][4]
-    const int tA = blockIdx.x;
-    const int k = A.k0 + blockIdx.y;
-    const int r = blockIdx.z;
     const int a = tA * TA + threadIdx.x;
     const int2 xa = A.xy_p[a];
     const int4 bA = A.bbox_a[tA];
@@ -268,18 +329,75 @@ __global__ void __launch_bounds__(TA) k_contract_x2(ContractArgs A) {
     for (int c = 0; c < 6; c++) o[c] = (double)Th[c] + (double)Tl[c];
 }
 
+
+// ---- one launch per plan: grid (pad tiles, modes, right-hand sides) ----------
+template <int TA, int TB>
+__global__ void __launch_bounds__(TA) k_contract_fp64(ContractArgs A) {
+    extern __shared__ float4 smem_raw[];
+    tile_fp64<TA, TB>(A, blockIdx.x, A.k0 + blockIdx.y, blockIdx.z, smem_raw);
+}
+template <int TA, int TB>
+__global__ void __launch_bounds__(TA) k_contract_fp32(ContractArgs A) {
+    extern __shared__ float4 smem_raw[];
+    tile_fp32<TA, TB>(A, blockIdx.x, A.k0 + blockIdx.y, blockIdx.z, smem_raw);
+}
+template <int TA, int TB, int RB>
+__global__ void __launch_bounds__(TA) k_contract_fp32_rb(ContractArgs A, int n_rhs) {
+    extern __shared__ float4 smem_raw[];
+    tile_fp32_rb<TA, TB, RB>(A, blockIdx.x, A.k0 + blockIdx.y, blockIdx.z, n_rhs, smem_raw);
+}
+template <int TA, int TB>
+__global__ void __launch_bounds__(TA) k_contract_x2(ContractArgs A) {
+    extern __shared__ float4 smem_raw[];
+    tile_x2<TA, TB>(A, blockIdx.x, A.k0 + blockIdx.y, blockIdx.z, smem_raw);
+}
+
+// ---- batched: one persistent launch drains a cost-sorted work list ----------
+// Item (inst, k, pad tile, r): r is a right-hand side, or a block of RB
+// right-hand sides for the multi-rhs FP32 tile (k >= 1).  CTAs take items
+// from a global counter with atomicAdd; no CTA ever waits for another.
+constexpr int kBatchRB = 8;
+template <int TA, int TB, int PREC>
+__global__ void __launch_bounds__(TA) k_batch_contract(const ContractArgs* __restrict__ args,
+                                                       const int* __restrict__ n_rhs_arr,
+                                                       const int4* __restrict__ items, int n_items,
+                                                       int* __restrict__ counter) {
+    extern __shared__ float4 smem_raw[];
+    __shared__ int s_item;
+    for (;;) {
+        __syncthreads();  // everyone has read s_item and left the previous tile's shared memory
+        if (threadIdx.x == 0) s_item = atomicAdd(counter, 1);
+        __syncthreads();
+        const int it = s_item;
+        if (it >= n_items) return;
+        const int4 w = items[it];
+        const ContractArgs A = args[w.x];
+        if (PREC == FBC_PREC_FP64) {
+            tile_fp64<TA, TB>(A, w.z, w.y, w.w, smem_raw);
+        } else if (PREC == FBC_PREC_F32X2) {
+            tile_x2<TA, TB>(A, w.z, w.y, w.w, smem_raw);
+        } else {
+            if (w.y == 0)
+                tile_fp64<TA, TB>(A, w.z, 0, w.w, smem_raw);
+            else
+                tile_fp32_rb<TA, TB, kBatchRB>(A, w.z, w.y, w.w, n_rhs_arr[w.x], smem_raw);
+        }
+    }
+}
+
 template <class T>
 size_t contract_smem(const Plan& P, int TB, int per_entry) {
     return (size_t)6 * P.H * P.W * per_entry + (size_t)TB * 6 * per_entry + (size_t)TB * sizeof(int) + 16;
 }
 
-template <typename KernelT>
-cudaError_t launch_one(KernelT kern, const ContractArgs& A, dim3 grid, int threads, size_t smem, cudaStream_t st) {
+template <typename KernelT, typename... Extra>
+cudaError_t launch_one(KernelT kern, const ContractArgs& A, dim3 grid, int threads, size_t smem, cudaStream_t st,
+                       Extra... extra) {
     if (smem > 32 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e) return e;
     }
-    kern<<<grid, threads, smem, st>>>(A);
+    kern<<<grid, threads, smem, st>>>(A, extra...);
     return cudaGetLastError();
 }
 
@@ -287,12 +405,7 @@ cudaError_t launch_one(KernelT kern, const ContractArgs& A, dim3 grid, int threa
 
 cudaError_t launch_contract(Plan& P, int n_rhs, cudaStream_t st) {
     static_assert(kTileA == 128 && kTileB == 64, "tile sizes are compiled in");
-    ContractArgs A;
-    A.tab = P.d_table, A.tab32 = P.d_table32, A.tabx2 = P.d_table_x2;
-    A.fh = P.d_fh, A.uh = P.d_uh, A.xy_p = P.d_xy_p, A.off_i = P.d_off_i;
-    A.bbox_a = P.d_bbox_a, A.bbox_b = P.d_bbox_b;
-    A.n_tb = P.n_tb, A.K = P.K, A.Dx = P.Dx, A.Dy = P.Dy, A.box_x0 = P.box_x0, A.box_y0 = P.box_y0;
-    A.W = P.W, A.H = P.H, A.NIpad = P.NIpad, A.NPpad = P.NPpad, A.k0 = 0;
+    ContractArgs A = make_contract_args(P);
     const size_t s64 = contract_smem<double>(P, kTileB, 8);
     if (s64 > 220 * 1024) return cudaErrorInvalidConfiguration;
     if (P.precision == FBC_PREC_FP64) {
@@ -303,6 +416,12 @@ cudaError_t launch_contract(Plan& P, int n_rhs, cudaStream_t st) {
         cudaError_t e = launch_one(k_contract_fp64<kTileA, kTileB>, A, dim3(P.n_ta, 1, n_rhs), kTileA, s64, st);
         if (e || P.K < 2) return e;
         A.k0 = 1;
+        if (n_rhs >= 2) {
+            constexpr int RB = 8;
+            const size_t srb = (size_t)6 * P.H * P.W * 4 + (size_t)RB * kTileB * 24 + (size_t)kTileB * 4 + 16;
+            return launch_one(k_contract_fp32_rb<kTileA, kTileB, RB>, A, dim3(P.n_ta, P.K - 1, (n_rhs + RB - 1) / RB),
+                              kTileA, srb, st, n_rhs);
+        }
         return launch_one(k_contract_fp32<kTileA, kTileB>, A, dim3(P.n_ta, P.K - 1, n_rhs), kTileA,
                           contract_smem<float>(P, kTileB, 4), st);
     }
@@ -311,6 +430,64 @@ cudaError_t launch_contract(Plan& P, int n_rhs, cudaStream_t st) {
         return launch_one(k_contract_x2<kTileA, kTileB>, A, dim3(P.n_ta, P.K, n_rhs), kTileA, sx2, st);
     }
     return cudaErrorInvalidValue;
+}
+
+ContractArgs make_contract_args(const Plan& P) {
+    ContractArgs A;
+    A.tab = P.d_table, A.tab32 = P.d_table32, A.tabx2 = P.d_table_x2;
+    A.fh = P.d_fh, A.uh = P.d_uh, A.xy_p = P.d_xy_p, A.off_i = P.d_off_i;
+    A.bbox_a = P.d_bbox_a, A.bbox_b = P.d_bbox_b;
+    A.n_tb = P.n_tb, A.K = P.K, A.Dx = P.Dx, A.Dy = P.Dy, A.box_x0 = P.box_x0, A.box_y0 = P.box_y0;
+    A.W = P.W, A.H = P.H, A.NIpad = P.NIpad, A.NPpad = P.NPpad, A.k0 = 0;
+    return A;
+}
+
+size_t batch_contract_smem(int precision, int W, int H) {
+    const size_t HW = (size_t)W * H;
+    const size_t s64 = HW * 48 + (size_t)kTileB * 52 + 16;
+    const size_t sx2 = HW * 48 + (size_t)kTileB * 64 + 16;
+    const size_t srb = ((HW * 24 + 15) & ~(size_t)15) + (size_t)kBatchRB * kTileB * 24 + (size_t)kTileB * 4 + 16;
+    if (precision == FBC_PREC_FP64) return s64;
+    if (precision == FBC_PREC_F32X2) return sx2;
+    return s64 > srb ? s64 : srb;
+}
+
+int batch_rhs_block() { return kBatchRB; }
+
+cudaError_t launch_batch_contract(int precision, const ContractArgs* d_args, const int* d_n_rhs, const int4* d_items,
+                                  int n_items, int* d_counter, int grid, size_t smem, cudaStream_t st) {
+    cudaError_t e = cudaSuccess;
+    auto go = [&](auto kern) {
+        if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem))) return;
+        kern<<<grid, kTileA, smem, st>>>(d_args, d_n_rhs, d_items, n_items, d_counter);
+        e = cudaGetLastError();
+    };
+    if (precision == FBC_PREC_FP64)
+        go(k_batch_contract<kTileA, kTileB, FBC_PREC_FP64>);
+    else if (precision == FBC_PREC_F32X2)
+        go(k_batch_contract<kTileA, kTileB, FBC_PREC_F32X2>);
+    else
+        go(k_batch_contract<kTileA, kTileB, FBC_PREC_FP32>);
+    return e;
+}
+
+int batch_contract_occupancy(int precision, size_t smem) {
+    int nb = 0;
+    cudaError_t e;
+    if (precision == FBC_PREC_FP64) {
+        cudaFuncSetAttribute(k_batch_contract<kTileA, kTileB, FBC_PREC_FP64>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch_contract<kTileA, kTileB, FBC_PREC_FP64>, kTileA, smem);
+    } else if (precision == FBC_PREC_F32X2) {
+        cudaFuncSetAttribute(k_batch_contract<kTileA, kTileB, FBC_PREC_F32X2>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch_contract<kTileA, kTileB, FBC_PREC_F32X2>, kTileA, smem);
+    } else {
+        cudaFuncSetAttribute(k_batch_contract<kTileA, kTileB, FBC_PREC_FP32>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch_contract<kTileA, kTileB, FBC_PREC_FP32>, kTileA, smem);
+    }
+    return (e == cudaSuccess && nb > 0) ? nb : 1;
 }
 
 }  // namespace fbc

@@ -92,6 +92,33 @@ struct Plan {
     size_t table_bytes = 0, workspace_bytes = 0;
 };
 
+// Everything a contraction tile needs about one plan (one instance of a batch).
+struct ContractArgs {
+    const double* tab;   // [K][Dy][Dx][6]
+    const float* tab32;  // [K][Dy][Dx][6]
+    const float* tabx2;  // [K][Dy][Dx][12] (hi[6], lo[6])
+    const double* fh;    // [rhs][K][NIpad][6]
+    double* uh;          // [rhs][K][NPpad][6]
+    const int2* xy_p;
+    const int* off_i;
+    const int4* bbox_a;
+    const int4* bbox_b;
+    int n_tb, K, Dx, Dy, box_x0, box_y0, W, H, NIpad, NPpad, k0;
+};
+
+// Everything the line transforms need about one plan (one instance of a batch).
+struct LineArgs {
+    const double* f;   // caller forces [n_rhs][n_i][L][3]
+    double* u;         // caller displacements [n_rhs][n_p][L][3]
+    double* fh;
+    double* uh;
+    const int* perm_i;
+    const int* perm_p;
+    const double2* tw;
+    double* part;
+    int n_i, n_p, L, logL, K, NIpad, NPpad, NC;
+};
+
 // ---- launchers (each returns the launch's cudaError_t) ---------------------
 cudaError_t launch_tabulate(Plan& P, cudaStream_t st);
 cudaError_t launch_forward(Plan& P, const double* f, int n_rhs, bool project, cudaStream_t st);
@@ -99,6 +126,17 @@ cudaError_t launch_contract(Plan& P, int n_rhs, cudaStream_t st);
 cudaError_t launch_inverse(Plan& P, double* u, int n_rhs, double alpha, double beta, bool zero_mean,
                            cudaStream_t st);
 cudaError_t launch_derive_tables(Plan& P, int precision, cudaStream_t st);
+ContractArgs make_contract_args(const Plan& P);
+size_t batch_contract_smem(int precision, int W, int H);
+int batch_rhs_block();
+int batch_contract_occupancy(int precision, size_t smem);
+LineArgs make_line_args(const Plan& P, const double* f, double* u);
+size_t batch_line_smem(int max_L);
+// stage 0 forward, 1 projection, 2 inverse, 3 zero mean; items as documented in fbc_line.cu
+cudaError_t launch_batch_line(int stage, const LineArgs* d_args, const int4* d_items, int n_items, size_t smem,
+                              double alpha, double beta, int want_part, cudaStream_t st);
+cudaError_t launch_batch_contract(int precision, const ContractArgs* d_args, const int* d_n_rhs, const int4* d_items,
+                                  int n_items, int* d_counter, int grid, size_t smem, cudaStream_t st);
 
 // Record the message fbc_last_error() returns for this thread; returns code.
 int report_error(int code, const char* msg);

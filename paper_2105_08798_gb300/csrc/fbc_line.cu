@@ -56,12 +56,12 @@ __device__ void fft_block(double2* buf, int nseq, int L, int logL, const double2
     }
 }
 
-// Forward transform of NC columns per CTA.  grid = (NIpad / NC, n_rhs).
-__global__ void k_forward(const double* __restrict__ f, const int* __restrict__ perm, const double2* __restrict__ tw,
-                          double* __restrict__ fh, int n_i, int L, int logL, int K, int NIpad, int NC) {
-    extern __shared__ double2 sbuf[];  // [NC + NC/2][L]: z sequences then w sequences
-    const int r = blockIdx.y;
-    const int b0 = blockIdx.x * NC;
+// Forward transform of NC columns (block blk of right-hand side r).
+__device__ __forceinline__ void fwd_block(const double* __restrict__ f, const int* __restrict__ perm,
+                                          const double2* __restrict__ tw, double* __restrict__ fh, int n_i, int L,
+                                          int logL, int K, int NIpad, int NC, int blk, int r, double2* sbuf) {
+    // sbuf: [NC + NC/2][L], z sequences then w sequences
+    const int b0 = blk * NC;
     double2* zs = sbuf;
     double2* ws = sbuf + (size_t)NC * L;
     // load: each column's L x 3 block is contiguous in f
@@ -110,11 +110,11 @@ __global__ void k_forward(const double* __restrict__ f, const int* __restrict__ 
 }
 
 // Neutral projection in the mode domain: mean_c = sum_b F_c(b, 0) / (n_i L);
-// F_c(b, 0) -= L mean_c for every real column.  One CTA per right-hand side;
-// fixed-order reduction (deterministic).
-__global__ void k_project(double* __restrict__ fh, const int* __restrict__ perm, int n_i, int L, int K, int NIpad) {
+// F_c(b, 0) -= L mean_c for every real column.  One CTA of 256 threads per
+// right-hand side; fixed-order reduction (deterministic).
+__device__ __forceinline__ void project_rhs(double* __restrict__ fh, const int* __restrict__ perm, int n_i, int K,
+                                            int NIpad, int r) {
     __shared__ double red[3][256];
-    const int r = blockIdx.y;
     double* row = fh + (size_t)r * K * NIpad * 6;  // k = 0
     double s0 = 0.0, s1 = 0.0, s2 = 0.0;
     for (int b = threadIdx.x; b < NIpad; b += blockDim.x) {
@@ -141,13 +141,14 @@ __global__ void k_project(double* __restrict__ fh, const int* __restrict__ perm,
     }
 }
 
-// Inverse transform + epilogue.  grid = (NPpad / NC, n_rhs).
-__global__ void k_inverse(const double* __restrict__ uh, const int* __restrict__ perm, const double2* __restrict__ tw,
-                          double* __restrict__ u, double* __restrict__ part, int n_p, int L, int logL, int K, int NPpad,
-                          int NC, double alpha_over_L, double beta, int want_part) {
-    extern __shared__ double2 sbuf[];
-    const int r = blockIdx.y;
-    const int a0 = blockIdx.x * NC;
+// Inverse transform + epilogue of NC pad columns (block blk of right-hand side
+// r); with want_part the block's per-component sums go to part[r][blk].
+__device__ __forceinline__ void inv_block(const double* __restrict__ uh, const int* __restrict__ perm,
+                                          const double2* __restrict__ tw, double* __restrict__ u,
+                                          double* __restrict__ part, int n_p, int L, int logL, int K, int NPpad,
+                                          int NC, double alpha_over_L, double beta, int want_part, int blk, int n_blk,
+                                          int r, double2* sbuf) {
+    const int a0 = blk * NC;
     double2* zs = sbuf;
     double2* ws = sbuf + (size_t)NC * L;
     const int Lh = L >> 1;
@@ -207,17 +208,17 @@ __global__ void k_inverse(const double* __restrict__ uh, const int* __restrict__
             __syncthreads();
         }
         if (threadIdx.x == 0) {
-            double* pp = part + ((size_t)r * gridDim.x + blockIdx.x) * 3;
+            double* pp = part + ((size_t)r * n_blk + blk) * 3;
             pp[0] = red[0][0], pp[1] = red[1][0], pp[2] = red[2][0];
         }
     }
 }
 
 // Zero mean of the pad displacements (Eq. 23): every CTA reduces the per-CTA
-// partial sums in the same fixed order, then subtracts from its chunk of u.
-__global__ void k_zero_mean(double* __restrict__ u, const double* __restrict__ part, int n_part, int n_p, int L) {
+// partial sums in the same fixed order, then subtracts from chunk c of n_chunk.
+__device__ __forceinline__ void zero_mean_chunk(double* __restrict__ u, const double* __restrict__ part, int n_part,
+                                                int n_p, int L, int r, int c, int n_chunk) {
     __shared__ double mean[3];
-    const int r = blockIdx.y;
     if (threadIdx.x == 0) {
         double s0 = 0.0, s1 = 0.0, s2 = 0.0;
         const double* pp = part + (size_t)r * n_part * 3;
@@ -228,8 +229,54 @@ __global__ void k_zero_mean(double* __restrict__ u, const double* __restrict__ p
     __syncthreads();
     const size_t n = (size_t)n_p * L * 3;
     double* ur = u + (size_t)r * n;
-    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    for (size_t i = (size_t)c * blockDim.x + threadIdx.x; i < n; i += (size_t)n_chunk * blockDim.x)
         ur[i] -= mean[i % 3];
+}
+
+// ---- one launch per plan ------------------------------------------------------
+__global__ void k_forward(const double* __restrict__ f, const int* __restrict__ perm, const double2* __restrict__ tw,
+                          double* __restrict__ fh, int n_i, int L, int logL, int K, int NIpad, int NC) {
+    extern __shared__ double2 sbuf[];
+    fwd_block(f, perm, tw, fh, n_i, L, logL, K, NIpad, NC, blockIdx.x, blockIdx.y, sbuf);
+}
+__global__ void k_project(double* __restrict__ fh, const int* __restrict__ perm, int n_i, int K, int NIpad) {
+    project_rhs(fh, perm, n_i, K, NIpad, blockIdx.y);
+}
+__global__ void k_inverse(const double* __restrict__ uh, const int* __restrict__ perm, const double2* __restrict__ tw,
+                          double* __restrict__ u, double* __restrict__ part, int n_p, int L, int logL, int K, int NPpad,
+                          int NC, double alpha_over_L, double beta, int want_part) {
+    extern __shared__ double2 sbuf[];
+    inv_block(uh, perm, tw, u, part, n_p, L, logL, K, NPpad, NC, alpha_over_L, beta, want_part, blockIdx.x, gridDim.x,
+              blockIdx.y, sbuf);
+}
+__global__ void k_zero_mean(double* __restrict__ u, const double* __restrict__ part, int n_part, int n_p, int L) {
+    zero_mean_chunk(u, part, n_part, n_p, L, blockIdx.y, blockIdx.x, gridDim.x);
+}
+
+// ---- batched over plans: items (instance, block, right-hand side) ---------------
+__global__ void k_batch_forward(const LineArgs* __restrict__ la, const int4* __restrict__ items) {
+    extern __shared__ double2 sbuf[];
+    const int4 w = items[blockIdx.x];
+    const LineArgs A = la[w.x];
+    fwd_block(A.f, A.perm_i, A.tw, A.fh, A.n_i, A.L, A.logL, A.K, A.NIpad, A.NC, w.y, w.z, sbuf);
+}
+__global__ void k_batch_project(const LineArgs* __restrict__ la, const int4* __restrict__ items) {
+    const int4 w = items[blockIdx.x];
+    const LineArgs A = la[w.x];
+    project_rhs(A.fh, A.perm_i, A.n_i, A.K, A.NIpad, w.z);
+}
+__global__ void k_batch_inverse(const LineArgs* __restrict__ la, const int4* __restrict__ items, double alpha,
+                                double beta, int want_part) {
+    extern __shared__ double2 sbuf[];
+    const int4 w = items[blockIdx.x];
+    const LineArgs A = la[w.x];
+    inv_block(A.uh, A.perm_p, A.tw, A.u, A.part, A.n_p, A.L, A.logL, A.K, A.NPpad, A.NC, alpha / (double)A.L, beta,
+              want_part, w.y, A.NPpad / A.NC, w.z, sbuf);
+}
+__global__ void k_batch_zero_mean(const LineArgs* __restrict__ la, const int4* __restrict__ items) {
+    const int4 w = items[blockIdx.x];  // (instance, chunk, r, n_chunk)
+    const LineArgs A = la[w.x];
+    zero_mean_chunk(A.u, A.part, A.NPpad / A.NC, A.n_p, A.L, w.z, w.y, w.w);
 }
 
 size_t line_smem(int L, int NC) { return (size_t)(NC + NC / 2) * L * sizeof(double2); }
@@ -247,7 +294,7 @@ cudaError_t launch_forward(Plan& P, const double* f, int n_rhs, bool project, cu
     k_forward<<<grid, 256, smem, st>>>(f, P.d_perm_i, P.d_tw, P.d_fh, P.n_i, P.L, P.logL, P.K, P.NIpad, NC);
     if ((e = cudaGetLastError())) return e;
     if (project) {
-        k_project<<<dim3(1, n_rhs), 256, 0, st>>>(P.d_fh, P.d_perm_i, P.n_i, P.L, P.K, P.NIpad);
+        k_project<<<dim3(1, n_rhs), 256, 0, st>>>(P.d_fh, P.d_perm_i, P.n_i, P.K, P.NIpad);
         if ((e = cudaGetLastError())) return e;
     }
     return cudaSuccess;
@@ -272,6 +319,42 @@ cudaError_t launch_inverse(Plan& P, double* u, int n_rhs, double alpha, double b
         if ((e = cudaGetLastError())) return e;
     }
     return cudaSuccess;
+}
+
+LineArgs make_line_args(const Plan& P, const double* f, double* u) {
+    LineArgs A;
+    A.f = f, A.u = u, A.fh = P.d_fh, A.uh = P.d_uh, A.perm_i = P.d_perm_i, A.perm_p = P.d_perm_p, A.tw = P.d_tw;
+    A.part = P.d_part;
+    A.n_i = P.n_i, A.n_p = P.n_p, A.L = P.L, A.logL = P.logL, A.K = P.K, A.NIpad = P.NIpad, A.NPpad = P.NPpad;
+    A.NC = line_cols(P.L);
+    return A;
+}
+
+size_t batch_line_smem(int max_L) { return line_smem(max_L, line_cols(max_L)); }
+
+cudaError_t launch_batch_line(int stage, const LineArgs* d_args, const int4* d_items, int n_items, size_t smem,
+                              double alpha, double beta, int want_part, cudaStream_t st) {
+    if (n_items == 0) return cudaSuccess;
+    cudaError_t e;
+    switch (stage) {
+        case 0:
+            if ((e = cudaFuncSetAttribute(k_batch_forward, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)))
+                return e;
+            k_batch_forward<<<n_items, 256, smem, st>>>(d_args, d_items);
+            break;
+        case 1:
+            k_batch_project<<<n_items, 256, 0, st>>>(d_args, d_items);
+            break;
+        case 2:
+            if ((e = cudaFuncSetAttribute(k_batch_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)))
+                return e;
+            k_batch_inverse<<<n_items, 256, smem, st>>>(d_args, d_items, alpha, beta, want_part);
+            break;
+        default:
+            k_batch_zero_mean<<<n_items, 256, 0, st>>>(d_args, d_items);
+            break;
+    }
+    return cudaGetLastError();
 }
 
 }  // namespace fbc

@@ -41,6 +41,7 @@ FBC_PLAN_HOST_ONLY = 1
 
 FBC_APPLY_PROJECT_NEUTRAL = 1
 FBC_APPLY_ZERO_MEAN_U = 2
+FBC_APPLY_NO_GRAPH = 4
 
 
 class FBCError(RuntimeError):
@@ -76,6 +77,15 @@ class fbc_plan_info(ctypes.Structure):
         return {name: getattr(self, name) for name, _ in self._fields_}
 
 
+class fbc_batch_info(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int32) for n in ("n_plans", "precision", "n_contract_items", "grid", "occupancy",
+                                              "lpt_order", "kernel_launches")] + [
+        ("smem_contract", ctypes.c_size_t), ("pair_modes", ctypes.c_double)]
+
+    def as_dict(self) -> dict:
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
 _lock = threading.Lock()
 _lib = None
 
@@ -101,6 +111,11 @@ _SIGNATURES = {
     "fbc_last_error": (ctypes.c_char_p, []),
     "fbc_version": (ctypes.c_char_p, []),
     "fbc_zero_mean_static": (ctypes.c_int, [_vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _vp]),
+    "fbc_batch_create": (ctypes.c_int, [_P(_vp), ctypes.c_int32, _P(_vp), _P(_vp), _P(ctypes.c_int32), _P(_vp)]),
+    "fbc_batch_apply": (ctypes.c_int, [_vp, ctypes.c_double, ctypes.c_double, ctypes.c_uint32, _vp]),
+    "fbc_batch_autotune": (ctypes.c_int, [_vp, _vp, _P(ctypes.c_double)]),
+    "fbc_batch_info_get": (ctypes.c_int, [_vp, _P(fbc_batch_info)]),
+    "fbc_batch_destroy": (None, [_vp]),
 }
 
 
@@ -223,6 +238,37 @@ def fbc_zero_mean_static(u_ptr: int, n_rhs: int, n_p: int, L: int, stream=None):
     _check(load().fbc_zero_mean_static(u_ptr, n_rhs, n_p, L, _stream_handle(stream)), "fbc_zero_mean_static")
 
 
+def fbc_batch_create(plans: list[int], f_ptrs: list[int], u_ptrs: list[int], n_rhs: list[int]) -> int:
+    n = len(plans)
+    P = (_vp * n)(*plans)
+    F = (_vp * n)(*f_ptrs)
+    U = (_vp * n)(*u_ptrs)
+    R = (ctypes.c_int32 * n)(*n_rhs)
+    h = _vp()
+    _check(load().fbc_batch_create(P, n, F, U, R, ctypes.byref(h)), "fbc_batch_create")
+    return h.value
+
+
+def fbc_batch_apply(batch: int, alpha: float, beta: float, flags: int, stream=None):
+    _check(load().fbc_batch_apply(batch, alpha, beta, flags, _stream_handle(stream)), "fbc_batch_apply")
+
+
+def fbc_batch_autotune(batch: int, stream=None) -> float:
+    best = ctypes.c_double()
+    _check(load().fbc_batch_autotune(batch, _stream_handle(stream), ctypes.byref(best)), "fbc_batch_autotune")
+    return best.value
+
+
+def fbc_batch_info_get(batch: int) -> dict:
+    info = fbc_batch_info()
+    _check(load().fbc_batch_info_get(batch, ctypes.byref(info)), "fbc_batch_info_get")
+    return info.as_dict()
+
+
+def fbc_batch_destroy(batch: int):
+    load().fbc_batch_destroy(batch)
+
+
 # ---- convenience wrapper -----------------------------------------------------
 def material_struct(material: dict) -> fbc_material:
     m = fbc_material()
@@ -330,6 +376,55 @@ class Plan:
     def close(self):
         if self._h is not None:
             fbc_destroy(self._h)
+            self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Owning handle of one ``fbc_batch`` over existing plans and device tensors."""
+
+    def __init__(self, plans: list, f_list: list, u_list: list):
+        import torch
+
+        for f, u, p in zip(f_list, u_list, plans):
+            if f.dtype != torch.float64 or u.dtype != torch.float64 or not f.is_cuda or not u.is_cuda:
+                raise TypeError("f and u must be float64 CUDA tensors")
+            if tuple(f.shape[1:]) != (p.n_i, p.L, 3) or tuple(u.shape[1:]) != (p.n_p, p.L, 3) or f.shape[0] != u.shape[0]:
+                raise ValueError("shape mismatch between a plan and its buffers")
+        self._plans = list(plans)
+        self._keep = (list(f_list), list(u_list))
+        self._h = fbc_batch_create([p.handle for p in plans], [f.data_ptr() for f in f_list],
+                                   [u.data_ptr() for u in u_list], [int(f.shape[0]) for f in f_list])
+
+    def apply(self, alpha: float = 1.0, beta: float = 0.0, project: bool = True, zero_mean: bool = False,
+              graph: bool = True, stream=None):
+        import torch
+
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        flags = Plan.flags(project, zero_mean) | (0 if graph else FBC_APPLY_NO_GRAPH)
+        fbc_batch_apply(self._h, alpha, beta, flags, stream)
+
+    def autotune(self, stream=None) -> float:
+        return fbc_batch_autotune(self._h, stream)
+
+    def info(self) -> dict:
+        return fbc_batch_info_get(self._h)
+
+    def close(self):
+        if self._h is not None:
+            fbc_batch_destroy(self._h)
             self._h = None
 
     def __enter__(self):
