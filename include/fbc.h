@@ -59,6 +59,9 @@ extern "C" {
 #define FBC_PREC_FP64 0  /* FP64 fused multiply-add throughout */
 #define FBC_PREC_FP32 1  /* FP32 products and sums; k = 0 mode kept in FP64 */
 #define FBC_PREC_F32X2 2 /* double-float: FP64-accurate products/sums built from FP32 pairs */
+#define FBC_PREC_TF32 3   /* tensor cores (tcgen05): tf32 operands, FP32 accumulation; k = 0 in FP64 */
+#define FBC_PREC_BF16X2 4 /* tensor cores: bf16 split x = h + m, 3 products, FP32 accumulation; k = 0 in FP64 */
+#define FBC_PREC_BF16X3 5 /* tensor cores: bf16 split x = h + m + l, 6 products, FP32 accumulation; k = 0 in FP64 */
 
 /* ---- plan flags (fbc_options.flags) ----------------------------------- */
 #define FBC_PLAN_HOST_ONLY 1 /* validate and lay out on the host only: no device memory,

@@ -130,6 +130,8 @@ int fbc_batch_create(fbc_plan* const* plans, int32_t n_plans, const double* cons
         if (!P.tabulated) return bfail(FBC_ERR_NOT_TABULATED, "every plan of a batch must be tabulated");
         if (prec < 0) prec = P.precision;
         if (P.precision != prec) return bfail(FBC_ERR_INVALID_ARG, "all plans of a batch need the same precision");
+        if (fbc::is_tensor_precision(prec))
+            return bfail(FBC_ERR_UNSUPPORTED, "batches run the CUDA-core precisions (FP64, FP32, double-float)");
         if (n_rhs[i] < 1 || n_rhs[i] > P.opt.max_rhs) return bfail(FBC_ERR_INVALID_ARG, "n_rhs outside [1, max_rhs]");
         if (!f[i] || !u[i]) return bfail(FBC_ERR_INVALID_ARG, "f or u of an instance is NULL");
         for (int j = 0; j < i; j++)

@@ -425,6 +425,13 @@ cudaError_t launch_contract(Plan& P, int n_rhs, cudaStream_t st) {
         return launch_one(k_contract_fp32<kTileA, kTileB>, A, dim3(P.n_ta, P.K - 1, n_rhs), kTileA,
                           contract_smem<float>(P, kTileB, 4), st);
     }
+    if (is_tensor_precision(P.precision)) {
+        // logarithmic k = 0 mode in FP64 on the CUDA cores, k >= 1 on the tensor cores
+        cudaError_t e = launch_one(k_contract_fp64<kTileA, kTileB>, A, dim3(P.n_ta, 1, n_rhs), kTileA, s64, st);
+        if (e || P.K < 2) return e;
+        A.k0 = 1;
+        return launch_contract_tc(A, P, n_rhs, st);
+    }
     if (P.precision == FBC_PREC_F32X2) {
         const size_t sx2 = (size_t)P.H * P.W * 48 + (size_t)kTileB * 64 + 16;
         return launch_one(k_contract_x2<kTileA, kTileB>, A, dim3(P.n_ta, P.K, n_rhs), kTileA, sx2, st);

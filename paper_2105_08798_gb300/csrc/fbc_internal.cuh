@@ -128,6 +128,9 @@ cudaError_t launch_inverse(Plan& P, double* u, int n_rhs, double alpha, double b
 cudaError_t launch_derive_tables(Plan& P, int precision, cudaStream_t st);
 ContractArgs make_contract_args(const Plan& P);
 size_t batch_contract_smem(int precision, int W, int H);
+cudaError_t launch_contract_tc(const ContractArgs& A, const Plan& P, int n_rhs, cudaStream_t st);
+size_t contract_tc_smem(int precision, int HW);
+inline bool is_tensor_precision(int p) { return p == FBC_PREC_TF32 || p == FBC_PREC_BF16X2 || p == FBC_PREC_BF16X3; }
 int batch_rhs_block();
 int batch_contract_occupancy(int precision, size_t smem);
 LineArgs make_line_args(const Plan& P, const double* f, double* u);

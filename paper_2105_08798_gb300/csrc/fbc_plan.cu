@@ -192,7 +192,7 @@ void free_plan(fbc::Plan& P) {
 int ensure_derived(fbc::Plan& P, int precision) {
     const size_t cells = (size_t)P.K * P.Dy * P.Dx;
     size_t acc = 0;
-    if (precision == FBC_PREC_FP32 && !P.d_table32) {
+    if ((precision == FBC_PREC_FP32 || fbc::is_tensor_precision(precision)) && !P.d_table32) {
         int s = dev_alloc(&P.d_table32, cells * 6, acc, "table32");
         if (s) return s;
     }
@@ -280,7 +280,7 @@ int fbc_plan_create(const fbc_geometry* geom, const fbc_material* mat, const fbc
         return fail(FBC_ERR_INVALID_ARG, "Richardson needs n >= 1, 0 <= N <= 12, n + N <= %d", fbc::kMaxRichImages);
     if (opt.quad < 8 || opt.quad > fbc::kMaxQuad) return fail(FBC_ERR_INVALID_ARG, "quad must be in [8, %d]", fbc::kMaxQuad);
     if (opt.max_rhs < 1 || opt.max_rhs > 4096) return fail(FBC_ERR_INVALID_ARG, "max_rhs must be in [1, 4096]");
-    if (opt.precision < FBC_PREC_FP64 || opt.precision > FBC_PREC_F32X2)
+    if (opt.precision < FBC_PREC_FP64 || opt.precision > FBC_PREC_BF16X3)
         return fail(FBC_ERR_INVALID_ARG, "unknown precision %d", opt.precision);
     if (opt.flags & ~FBC_PLAN_HOST_ONLY) return fail(FBC_ERR_INVALID_ARG, "unknown options.flags bits 0x%x", opt.flags);
     const int32_t coord_lim = 1 << 20;
@@ -478,7 +478,7 @@ int fbc_tabulate_kernel(fbc_plan* plan, void* stream) {
 int fbc_plan_set_precision(fbc_plan* plan, int32_t precision) {
     g_last_error.clear();
     if (!plan) return fail(FBC_ERR_INVALID_ARG, "plan is NULL");
-    if (precision < FBC_PREC_FP64 || precision > FBC_PREC_F32X2)
+    if (precision < FBC_PREC_FP64 || precision > FBC_PREC_BF16X3)
         return fail(FBC_ERR_INVALID_ARG, "unknown precision %d", precision);
     fbc::Plan& P = plan->p;
     if (P.host_only) return fail(FBC_ERR_INVALID_ARG, "host-only plan");
@@ -507,7 +507,10 @@ static int apply_common(fbc::Plan& P, const double* f, double* u, int32_t n_rhs,
     const char* fc = (const char*)f;
     const char* uc = (const char*)u;
     if (fc < uc + ub && uc < fc + fb) return fail(FBC_ERR_INVALID_ARG, "f and u overlap");
-    if (P.precision == FBC_PREC_FP32 && !P.d_table32) return fail(FBC_ERR_INVALID_ARG, "FP32 table missing");
+    if ((P.precision == FBC_PREC_FP32 || fbc::is_tensor_precision(P.precision)) && !P.d_table32)
+        return fail(FBC_ERR_INVALID_ARG, "FP32 table missing");
+    if (fbc::is_tensor_precision(P.precision) && fbc::contract_tc_smem(P.precision, P.W * P.H) > 227 * 1024)
+        return fail(FBC_ERR_UNSUPPORTED, "tensor-core contraction: staged sub-box too large for shared memory");
     if (P.precision == FBC_PREC_F32X2 && !P.d_table_x2) return fail(FBC_ERR_INVALID_ARG, "F32X2 table missing");
     if (P.timing) FBC_CUDA(cudaEventRecord(P.ev[0], st));
     cudaError_t e = fbc::launch_forward(P, f, n_rhs, (flags & FBC_APPLY_PROJECT_NEUTRAL) != 0, st);

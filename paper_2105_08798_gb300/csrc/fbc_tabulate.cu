@@ -265,7 +265,7 @@ cudaError_t launch_tabulate(Plan& P, cudaStream_t st) {
 
 cudaError_t launch_derive_tables(Plan& P, int precision, cudaStream_t st) {
     const size_t cells = (size_t)P.K * P.Dy * P.Dx;
-    if (precision == FBC_PREC_FP32) {
+    if (precision == FBC_PREC_FP32 || is_tensor_precision(precision)) {
         if (!P.d_table32) return cudaErrorInvalidValue;
         k_derive_fp32<<<1216, 256, 0, st>>>(P.d_table, P.d_table32, cells * 6);
         return cudaGetLastError();

@@ -35,7 +35,11 @@ FBC_MATERIAL_CUBIC = 1
 FBC_PREC_FP64 = 0
 FBC_PREC_FP32 = 1
 FBC_PREC_F32X2 = 2
-PRECISIONS = {"fp64": FBC_PREC_FP64, "fp32": FBC_PREC_FP32, "f32x2": FBC_PREC_F32X2}
+FBC_PREC_TF32 = 3
+FBC_PREC_BF16X2 = 4
+FBC_PREC_BF16X3 = 5
+PRECISIONS = {"fp64": FBC_PREC_FP64, "fp32": FBC_PREC_FP32, "f32x2": FBC_PREC_F32X2, "tf32": FBC_PREC_TF32,
+              "bf16x2": FBC_PREC_BF16X2, "bf16x3": FBC_PREC_BF16X3}
 
 FBC_PLAN_HOST_ONLY = 1
 

@@ -1,0 +1,70 @@
+"""Tensor-core (tcgen05) contraction for plans with several right-hand sides.
+
+The TF32, BF16x2 and BF16x3 forms (k >= 1 on the tensor cores with FP32
+accumulation in tensor memory, k = 0 in FP64) are compared with the FP64 GPU
+path, which is itself at 1e-12 of the oracle.  Expected accuracy from the
+operand precision and FP32 accumulation over 3 N_I terms: TF32 ~1e-3,
+BF16x2 ~1e-5, BF16x3 ~1e-6.  Also checked: ragged right-hand-side counts
+(padding of the GEMM's N dimension), more than 64 right-hand sides (two CTA
+groups along N), and agreement with the oracle on one right-hand side.
+"""
+
+import numpy as np
+import pytest
+
+from conftest import ISO
+from paper_2105_08798_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+BOUNDS = {"tf32": 5e-3, "bf16x2": 1e-4, "bf16x3": 1e-5}
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm((np.asarray(a) - np.asarray(b)).ravel()) / np.linalg.norm(np.asarray(b).ravel()))
+
+
+@pytest.fixture(scope="module")
+def fbc():
+    from paper_2105_08798_gb300 import build, fbc as binding
+
+    build.build()
+    binding.load()
+    return binding
+
+
+def _run_all(fbc, n_i, n_p, L, R, seed):
+    xy_i, xy_p = inputs.ring_geometry(n_i, n_p)
+    f = inputs.forces(R, n_i, L, seed=seed)
+    out = {}
+    with fbc.Plan(xy_i, xy_p, L, ISO, max_rhs=R) as plan:
+        plan.tabulate()
+        fd = torch.from_numpy(f).cuda()
+        for prec in ("fp64", "tf32", "bf16x2", "bf16x3"):
+            plan.set_precision(prec)
+            ud = torch.full((R, n_p, L, 3), float("nan"), dtype=torch.float64, device="cuda")
+            plan.apply(fd, ud)
+            torch.cuda.synchronize()
+            plan.sync_status()
+            out[prec] = ud.cpu().numpy()
+    return xy_i, xy_p, f, out
+
+
+@pytest.mark.parametrize("n_i,n_p,L,R", [(300, 450, 32, 16), (150, 220, 16, 3), (100, 140, 8, 70)])
+def test_tensor_forms_against_fp64(fbc, n_i, n_p, L, R):
+    _, _, _, out = _run_all(fbc, n_i, n_p, L, R, seed=n_i + R)
+    assert np.isfinite(out["fp64"]).all()
+    errs = {}
+    for prec, bound in BOUNDS.items():
+        assert np.isfinite(out[prec]).all(), prec
+        errs[prec] = rel_l2(out[prec], out["fp64"])
+        assert errs[prec] <= bound, (prec, errs[prec])
+    assert errs["bf16x3"] < errs["bf16x2"] < errs["tf32"], errs
+
+
+def test_tensor_form_against_oracle(fbc, oracle_mod):
+    xy_i, xy_p, f, out = _run_all(fbc, 200, 300, 16, 8, seed=3)
+    ref = oracle_mod.pad_update(xy_i, xy_p, 16, 1.0, ISO, f[:1])
+    assert rel_l2(out["fp64"][:1], ref) <= 1e-12
+    assert rel_l2(out["bf16x3"][:1], ref) <= BOUNDS["bf16x3"]
