@@ -35,19 +35,19 @@ struct fbc_batch {
     int device = 0;
     std::vector<fbc_plan*> plans;
     std::vector<int> n_rhs;
-    std::vector<Item> con_items;  // natural order
+    std::vector<Item> con_items[2];  // natural order; [0]: k = 0 items of an FP32 batch, [1]: the rest
     std::vector<int4> fwd, proj, inv, zm;
     fbc::LineArgs* d_largs = nullptr;
     fbc::ContractArgs* d_cargs = nullptr;
     int* d_nrhs = nullptr;
     int4* d_fwd = nullptr;
     int4* d_proj = nullptr;
-    int4* d_con = nullptr;
+    int4* d_con[2] = {nullptr, nullptr};
     int4* d_inv = nullptr;
     int4* d_zm = nullptr;
     int* d_counter = nullptr;
-    size_t smem_con = 0, smem_line = 0;
-    int sm_count = 152, occupancy = 1, grid = 152;
+    size_t smem_con[2] = {0, 0}, smem_line = 0;
+    int sm_count = 152, occupancy[2] = {1, 1}, grid[2] = {152, 152};
     int lpt = 1;
     cudaStream_t cap = nullptr;
     cudaGraph_t graph = nullptr;
@@ -72,7 +72,8 @@ void free_batch(fbc_batch* b) {
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->graph) cudaGraphDestroy(b->graph);
     if (b->cap) cudaStreamDestroy(b->cap);
-    void* bufs[] = {b->d_largs, b->d_cargs, b->d_nrhs, b->d_fwd, b->d_proj, b->d_con, b->d_inv, b->d_zm, b->d_counter};
+    void* bufs[] = {b->d_largs, b->d_cargs, b->d_nrhs, b->d_fwd, b->d_proj, b->d_con[0], b->d_con[1], b->d_inv, b->d_zm,
+                    b->d_counter};
     for (void* p : bufs)
         if (p) cudaFree(p);
 }
@@ -87,8 +88,8 @@ cudaError_t upload(T** dst, const std::vector<T>& src) {
     return e;
 }
 
-std::vector<int4> ordered_items(const fbc_batch* b, bool lpt) {
-    std::vector<Item> it = b->con_items;
+std::vector<int4> ordered_items(const fbc_batch* b, int phase, bool lpt) {
+    std::vector<Item> it = b->con_items[phase];
     if (lpt) std::stable_sort(it.begin(), it.end(), [](const Item& x, const Item& y) { return x.cost > y.cost; });
     std::vector<int4> out(it.size());
     for (size_t t = 0; t < it.size(); t++) out[t] = it[t].w;
@@ -101,10 +102,12 @@ cudaError_t enqueue(fbc_batch* b, double alpha, double beta, uint32_t flags, cud
     const bool project = flags & FBC_APPLY_PROJECT_NEUTRAL, zmean = flags & FBC_APPLY_ZERO_MEAN_U;
     if ((e = fbc::launch_batch_line(0, b->d_largs, b->d_fwd, (int)b->fwd.size(), b->smem_line, 0, 0, 0, st))) return e;
     if (project && (e = fbc::launch_batch_line(1, b->d_largs, b->d_proj, (int)b->proj.size(), 0, 0, 0, 0, st))) return e;
-    if ((e = cudaMemsetAsync(b->d_counter, 0, sizeof(int), st))) return e;
-    if ((e = fbc::launch_batch_contract(b->precision, b->d_cargs, b->d_nrhs, b->d_con, (int)b->con_items.size(),
-                                        b->d_counter, b->grid, b->smem_con, st)))
-        return e;
+    if ((e = cudaMemsetAsync(b->d_counter, 0, 2 * sizeof(int), st))) return e;
+    for (int ph = 0; ph < 2; ph++)
+        if ((e = fbc::launch_batch_contract(b->precision, ph, b->d_cargs, b->d_nrhs, b->d_con[ph],
+                                            (int)b->con_items[ph].size(), b->d_counter + ph, b->grid[ph],
+                                            b->smem_con[ph], st)))
+            return e;
     if ((e = fbc::launch_batch_line(2, b->d_largs, b->d_inv, (int)b->inv.size(), b->smem_line, alpha, beta,
                                     zmean ? 1 : 0, st)))
         return e;
@@ -154,7 +157,8 @@ int fbc_batch_create(fbc_plan* const* plans, int32_t n_plans, const double* cons
         la[i] = fbc::make_line_args(P, f[i], u[i]);
         ca[i] = fbc::make_contract_args(P);
         max_L = std::max(max_L, P.L);
-        b->smem_con = std::max(b->smem_con, fbc::batch_contract_smem(prec, P.W, P.H));
+        for (int ph = 0; ph < 2; ph++)
+            b->smem_con[ph] = std::max(b->smem_con[ph], fbc::batch_contract_smem_phase(prec, ph, P.W, P.H));
         const int R = n_rhs[i];
         const int NC = la[i].NC;
         for (int r = 0; r < R; r++) {
@@ -172,16 +176,18 @@ int fbc_batch_create(fbc_plan* const* plans, int32_t n_plans, const double* cons
                 if (prec == FBC_PREC_FP32 && k > 0) {
                     for (int rb = 0; rb < (R + RB - 1) / RB; rb++) {
                         const int cnt = std::min(RB, R - rb * RB);
-                        b->con_items.push_back({make_int4(i, k, tA, rb), per_tile * cnt / 1500.0});
+                        b->con_items[1].push_back({make_int4(i, k, tA, rb), per_tile * cnt / 1500.0});
                     }
+                } else if (prec == FBC_PREC_FP32) {  // k = 0 in double-float
+                    for (int r = 0; r < R; r++) b->con_items[0].push_back({make_int4(i, k, tA, r), per_tile / 130.0});
                 } else {
                     const double rate = (prec == FBC_PREC_F32X2) ? 130.0 : 34.0;
-                    for (int r = 0; r < R; r++) b->con_items.push_back({make_int4(i, k, tA, r), per_tile / rate});
+                    for (int r = 0; r < R; r++) b->con_items[1].push_back({make_int4(i, k, tA, r), per_tile / rate});
                 }
             }
         b->pair_modes += (double)P.n_p * P.n_i * P.K * R;
     }
-    if (b->smem_con > 227 * 1024) {
+    if (std::max(b->smem_con[0], b->smem_con[1]) > 227 * 1024) {
         free_batch(b);
         delete b;
         return bfail(FBC_ERR_UNSUPPORTED, "an instance's staged sub-box exceeds shared memory");
@@ -196,8 +202,9 @@ int fbc_batch_create(fbc_plan* const* plans, int32_t n_plans, const double* cons
     if (!e) e = upload(&b->d_proj, b->proj);
     if (!e) e = upload(&b->d_inv, b->inv);
     if (!e) e = upload(&b->d_zm, b->zm);
-    if (!e) e = upload(&b->d_con, ordered_items(b, true));
-    if (!e) e = cudaMalloc((void**)&b->d_counter, sizeof(int));
+    if (!e) e = upload(&b->d_con[0], ordered_items(b, 0, true));
+    if (!e) e = upload(&b->d_con[1], ordered_items(b, 1, true));
+    if (!e) e = cudaMalloc((void**)&b->d_counter, 2 * sizeof(int));
     if (!e) e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
     if (e) {
         int st = bcuda(e, "batch setup");
@@ -205,8 +212,10 @@ int fbc_batch_create(fbc_plan* const* plans, int32_t n_plans, const double* cons
         delete b;
         return st;
     }
-    b->occupancy = fbc::batch_contract_occupancy(prec, b->smem_con);
-    b->grid = b->occupancy * b->sm_count;
+    for (int ph = 0; ph < 2; ph++) {
+        b->occupancy[ph] = fbc::batch_contract_occupancy_phase(prec, ph, b->smem_con[ph]);
+        b->grid[ph] = b->occupancy[ph] * b->sm_count;
+    }
     *out = b;
     return FBC_OK;
 }
@@ -246,20 +255,22 @@ int fbc_batch_autotune(fbc_batch* b, void* stream, double* best_ms) {
     cudaStream_t st = (cudaStream_t)stream;
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) || cudaEventCreate(&e1)) return bfail(FBC_ERR_CUDA, "event creation failed");
-    // the transforms run once so the contraction sees real inputs
+    // the transforms run once so the contraction sees real inputs; the dominant launch (phase 1) is tuned
     cudaError_t e = fbc::launch_batch_line(0, b->d_largs, b->d_fwd, (int)b->fwd.size(), b->smem_line, 0, 0, 0, st);
+    const int ph = 1;
     double best = 1e300;
-    int best_grid = b->grid, best_lpt = b->lpt;
-    const int grids[] = {b->occupancy * b->sm_count, std::max(1, b->occupancy - 1) * b->sm_count, b->sm_count};
+    int best_grid = b->grid[ph], best_lpt = b->lpt;
+    const int occ = b->occupancy[ph];
+    const int grids[] = {occ * b->sm_count, std::max(1, occ - 1) * b->sm_count, b->sm_count};
     for (int lpt = 1; lpt >= 0 && !e; lpt--) {
-        if ((e = upload(&b->d_con, ordered_items(b, lpt == 1)))) break;
+        if ((e = upload(&b->d_con[ph], ordered_items(b, ph, lpt == 1)))) break;
         for (int g : grids) {
             float ms_sum = 0.0f;
             for (int rep = 0; rep < 2 && !e; rep++) {
-                if ((e = cudaMemsetAsync(b->d_counter, 0, sizeof(int), st))) break;
+                if ((e = cudaMemsetAsync(b->d_counter + ph, 0, sizeof(int), st))) break;
                 cudaEventRecord(e0, st);
-                e = fbc::launch_batch_contract(b->precision, b->d_cargs, b->d_nrhs, b->d_con,
-                                               (int)b->con_items.size(), b->d_counter, g, b->smem_con, st);
+                e = fbc::launch_batch_contract(b->precision, ph, b->d_cargs, b->d_nrhs, b->d_con[ph],
+                                               (int)b->con_items[ph].size(), b->d_counter + ph, g, b->smem_con[ph], st);
                 cudaEventRecord(e1, st);
                 if (!e) e = cudaEventSynchronize(e1);
                 float ms = 0.0f;
@@ -269,11 +280,11 @@ int fbc_batch_autotune(fbc_batch* b, void* stream, double* best_ms) {
             if (!e && ms_sum < best) best = ms_sum, best_grid = g, best_lpt = lpt;
         }
     }
-    if (!e) e = upload(&b->d_con, ordered_items(b, best_lpt == 1));
+    if (!e) e = upload(&b->d_con[ph], ordered_items(b, ph, best_lpt == 1));
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (e) return bcuda(e, "autotune");
-    b->grid = best_grid;
+    b->grid[ph] = best_grid;
     b->lpt = best_lpt;
     b->graph_valid = false;
     if (best_ms) *best_ms = best;
@@ -285,12 +296,13 @@ int fbc_batch_info_get(const fbc_batch* b, fbc_batch_info* info) {
     if (!b || !info) return bfail(FBC_ERR_INVALID_ARG, "batch or info is NULL");
     info->n_plans = b->n;
     info->precision = b->precision;
-    info->n_contract_items = (int32_t)b->con_items.size();
-    info->grid = b->grid;
-    info->occupancy = b->occupancy;
+    info->n_contract_items = (int32_t)(b->con_items[0].size() + b->con_items[1].size());
+    info->grid = b->grid[1];
+    info->occupancy = b->occupancy[1];
     info->lpt_order = b->lpt;
-    info->kernel_launches = 3 + 2;  // forward, projection, contraction, inverse, zero mean (when flagged)
-    info->smem_contract = b->smem_con;
+    // forward, projection, contraction (one launch per non-empty phase), inverse, zero mean (when flagged)
+    info->kernel_launches = 4 + (b->con_items[0].empty() ? 0 : 1) + (b->con_items[1].empty() ? 0 : 1);
+    info->smem_contract = b->smem_con[1];
     info->pair_modes = b->pair_modes;
     return FBC_OK;
 }

@@ -357,7 +357,7 @@ __global__ void __launch_bounds__(TA) k_contract_x2(ContractArgs A) {
 // right-hand sides for the multi-rhs FP32 tile (k >= 1).  CTAs take items
 // from a global counter with atomicAdd; no CTA ever waits for another.
 constexpr int kBatchRB = 8;
-template <int TA, int TB, int PREC>
+template <int TA, int TB, int PREC, int PHASE>
 __global__ void __launch_bounds__(TA) k_batch_contract(const ContractArgs* __restrict__ args,
                                                        const int* __restrict__ n_rhs_arr,
                                                        const int4* __restrict__ items, int n_items,
@@ -374,13 +374,10 @@ __global__ void __launch_bounds__(TA) k_batch_contract(const ContractArgs* __res
         const ContractArgs A = args[w.x];
         if (PREC == FBC_PREC_FP64) {
             tile_fp64<TA, TB>(A, w.z, w.y, w.w, smem_raw);
-        } else if (PREC == FBC_PREC_F32X2) {
+        } else if (PREC == FBC_PREC_F32X2 || PHASE == 0) {
             tile_x2<TA, TB>(A, w.z, w.y, w.w, smem_raw);
         } else {
-            if (w.y == 0)
-                tile_fp64<TA, TB>(A, w.z, 0, w.w, smem_raw);
-            else
-                tile_fp32_rb<TA, TB, kBatchRB>(A, w.z, w.y, w.w, n_rhs_arr[w.x], smem_raw);
+            tile_fp32_rb<TA, TB, kBatchRB>(A, w.z, w.y, w.w, n_rhs_arr[w.x], smem_raw);
         }
     }
 }
@@ -408,12 +405,13 @@ cudaError_t launch_contract(Plan& P, int n_rhs, cudaStream_t st) {
     ContractArgs A = make_contract_args(P);
     const size_t s64 = contract_smem<double>(P, kTileB, 8);
     if (s64 > 220 * 1024) return cudaErrorInvalidConfiguration;
+    const size_t sx2 = (size_t)P.H * P.W * 48 + (size_t)kTileB * 64 + 16;
     if (P.precision == FBC_PREC_FP64) {
         return launch_one(k_contract_fp64<kTileA, kTileB>, A, dim3(P.n_ta, P.K, n_rhs), kTileA, s64, st);
     }
     if (P.precision == FBC_PREC_FP32) {
-        // logarithmic k = 0 mode in FP64, the rest in FP32
-        cudaError_t e = launch_one(k_contract_fp64<kTileA, kTileB>, A, dim3(P.n_ta, 1, n_rhs), kTileA, s64, st);
+        // logarithmic k = 0 mode in double-float (FP64-accurate), the rest in FP32
+        cudaError_t e = launch_one(k_contract_x2<kTileA, kTileB>, A, dim3(P.n_ta, 1, n_rhs), kTileA, sx2, st);
         if (e || P.K < 2) return e;
         A.k0 = 1;
         if (n_rhs >= 2) {
@@ -426,14 +424,13 @@ cudaError_t launch_contract(Plan& P, int n_rhs, cudaStream_t st) {
                           contract_smem<float>(P, kTileB, 4), st);
     }
     if (is_tensor_precision(P.precision)) {
-        // logarithmic k = 0 mode in FP64 on the CUDA cores, k >= 1 on the tensor cores
-        cudaError_t e = launch_one(k_contract_fp64<kTileA, kTileB>, A, dim3(P.n_ta, 1, n_rhs), kTileA, s64, st);
+        // logarithmic k = 0 mode in double-float (FP64-accurate) on the CUDA cores, k >= 1 on the tensor cores
+        cudaError_t e = launch_one(k_contract_x2<kTileA, kTileB>, A, dim3(P.n_ta, 1, n_rhs), kTileA, sx2, st);
         if (e || P.K < 2) return e;
         A.k0 = 1;
         return launch_contract_tc(A, P, n_rhs, st);
     }
     if (P.precision == FBC_PREC_F32X2) {
-        const size_t sx2 = (size_t)P.H * P.W * 48 + (size_t)kTileB * 64 + 16;
         return launch_one(k_contract_x2<kTileA, kTileB>, A, dim3(P.n_ta, P.K, n_rhs), kTileA, sx2, st);
     }
     return cudaErrorInvalidValue;
@@ -441,7 +438,9 @@ cudaError_t launch_contract(Plan& P, int n_rhs, cudaStream_t st) {
 
 ContractArgs make_contract_args(const Plan& P) {
     ContractArgs A;
-    A.tab = P.d_table, A.tab32 = P.d_table32, A.tabx2 = P.d_table_x2;
+    A.tab = P.d_table, A.tab32 = P.d_table32;
+    // the double-float kernel of an FP32 or tensor-core plan only reads k = 0: the k = 0 slice suffices
+    A.tabx2 = P.d_table_x2 ? P.d_table_x2 : P.d_table_x2_k0;
     A.fh = P.d_fh, A.uh = P.d_uh, A.xy_p = P.d_xy_p, A.off_i = P.d_off_i;
     A.bbox_a = P.d_bbox_a, A.bbox_b = P.d_bbox_b;
     A.n_tb = P.n_tb, A.K = P.K, A.Dx = P.Dx, A.Dy = P.Dy, A.box_x0 = P.box_x0, A.box_y0 = P.box_y0;
@@ -449,52 +448,52 @@ ContractArgs make_contract_args(const Plan& P) {
     return A;
 }
 
-size_t batch_contract_smem(int precision, int W, int H) {
+size_t batch_contract_smem_phase(int precision, int phase, int W, int H) {
     const size_t HW = (size_t)W * H;
     const size_t s64 = HW * 48 + (size_t)kTileB * 52 + 16;
     const size_t sx2 = HW * 48 + (size_t)kTileB * 64 + 16;
     const size_t srb = ((HW * 24 + 15) & ~(size_t)15) + (size_t)kBatchRB * kTileB * 24 + (size_t)kTileB * 4 + 16;
     if (precision == FBC_PREC_FP64) return s64;
-    if (precision == FBC_PREC_F32X2) return sx2;
-    return s64 > srb ? s64 : srb;
+    if (precision == FBC_PREC_F32X2 || phase == 0) return sx2;
+    return srb;
 }
 
 int batch_rhs_block() { return kBatchRB; }
 
-cudaError_t launch_batch_contract(int precision, const ContractArgs* d_args, const int* d_n_rhs, const int4* d_items,
-                                  int n_items, int* d_counter, int grid, size_t smem, cudaStream_t st) {
-    cudaError_t e = cudaSuccess;
-    auto go = [&](auto kern) {
-        if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem))) return;
-        kern<<<grid, kTileA, smem, st>>>(d_args, d_n_rhs, d_items, n_items, d_counter);
-        e = cudaGetLastError();
-    };
-    if (precision == FBC_PREC_FP64)
-        go(k_batch_contract<kTileA, kTileB, FBC_PREC_FP64>);
-    else if (precision == FBC_PREC_F32X2)
-        go(k_batch_contract<kTileA, kTileB, FBC_PREC_F32X2>);
-    else
-        go(k_batch_contract<kTileA, kTileB, FBC_PREC_FP32>);
-    return e;
+template <int PREC, int PHASE>
+static cudaError_t go_batch(const ContractArgs* d_args, const int* d_n_rhs, const int4* d_items, int n_items,
+                            int* d_counter, int grid, size_t smem, cudaStream_t st) {
+    auto kern = k_batch_contract<kTileA, kTileB, PREC, PHASE>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e) return e;
+    kern<<<grid, kTileA, smem, st>>>(d_args, d_n_rhs, d_items, n_items, d_counter);
+    return cudaGetLastError();
 }
 
-int batch_contract_occupancy(int precision, size_t smem) {
+template <int PREC, int PHASE>
+static int occ_batch(size_t smem) {
+    auto kern = k_batch_contract<kTileA, kTileB, PREC, PHASE>;
     int nb = 0;
-    cudaError_t e;
-    if (precision == FBC_PREC_FP64) {
-        cudaFuncSetAttribute(k_batch_contract<kTileA, kTileB, FBC_PREC_FP64>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch_contract<kTileA, kTileB, FBC_PREC_FP64>, kTileA, smem);
-    } else if (precision == FBC_PREC_F32X2) {
-        cudaFuncSetAttribute(k_batch_contract<kTileA, kTileB, FBC_PREC_F32X2>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch_contract<kTileA, kTileB, FBC_PREC_F32X2>, kTileA, smem);
-    } else {
-        cudaFuncSetAttribute(k_batch_contract<kTileA, kTileB, FBC_PREC_FP32>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch_contract<kTileA, kTileB, FBC_PREC_FP32>, kTileA, smem);
-    }
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, kTileA, smem);
     return (e == cudaSuccess && nb > 0) ? nb : 1;
+}
+
+cudaError_t launch_batch_contract(int precision, int phase, const ContractArgs* d_args, const int* d_n_rhs,
+                                  const int4* d_items, int n_items, int* d_counter, int grid, size_t smem,
+                                  cudaStream_t st) {
+    if (n_items == 0) return cudaSuccess;
+    if (precision == FBC_PREC_FP64) return go_batch<FBC_PREC_FP64, 1>(d_args, d_n_rhs, d_items, n_items, d_counter, grid, smem, st);
+    if (precision == FBC_PREC_F32X2) return go_batch<FBC_PREC_F32X2, 1>(d_args, d_n_rhs, d_items, n_items, d_counter, grid, smem, st);
+    if (phase == 0) return go_batch<FBC_PREC_FP32, 0>(d_args, d_n_rhs, d_items, n_items, d_counter, grid, smem, st);
+    return go_batch<FBC_PREC_FP32, 1>(d_args, d_n_rhs, d_items, n_items, d_counter, grid, smem, st);
+}
+
+int batch_contract_occupancy_phase(int precision, int phase, size_t smem) {
+    if (precision == FBC_PREC_FP64) return occ_batch<FBC_PREC_FP64, 1>(smem);
+    if (precision == FBC_PREC_F32X2) return occ_batch<FBC_PREC_F32X2, 1>(smem);
+    if (phase == 0) return occ_batch<FBC_PREC_FP32, 0>(smem);
+    return occ_batch<FBC_PREC_FP32, 1>(smem);
 }
 
 }  // namespace fbc

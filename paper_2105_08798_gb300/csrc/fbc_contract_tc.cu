@@ -77,22 +77,27 @@ struct TcCfg<FBC_PREC_BF16X3> {
 // (piece of A, piece of B) for each split product, by decreasing magnitude
 __constant__ int c_prod_a[6] = {0, 0, 1, 0, 2, 1};
 __constant__ int c_prod_b[6] = {0, 1, 0, 2, 0, 1};
+// table component of M for (c_out, c_in), and the force block it multiplies (3 = -X2)
+__constant__ int c_ent[3][3] = {{0, 1, 4}, {1, 2, 5}, {4, 5, 3}};
+__constant__ int c_bsel[3][3] = {{0, 1, 3}, {0, 1, 3}, {0, 1, 2}};
 
 // Split x into NS pieces of the operand type; returned as raw bits (bf16 in
-// the low 16 bits, or the tf32 bit pattern).
+// the low 16 bits, or the tf32 bit pattern).  FP32 arithmetic throughout: each
+// remainder x - bf16(x) is exact in FP32, and three bf16 pieces hold all 24
+// bits of an FP32 value.
 template <int PREC>
-__device__ __forceinline__ void split(double x, uint32_t (&out)[TcCfg<PREC>::NS]) {
+__device__ __forceinline__ void split(float x, uint32_t (&out)[TcCfg<PREC>::NS]) {
     if (PREC == FBC_PREC_TF32) {
         uint32_t t;
-        asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(t) : "f"((float)x));
+        asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(t) : "f"(x));
         out[0] = t;
     } else {
-        double r = x;
+        float r = x;
 #pragma unroll
         for (int s = 0; s < TcCfg<PREC>::NS; s++) {
-            const __nv_bfloat16 h = __float2bfloat16_rn((float)r);
+            const __nv_bfloat16 h = __float2bfloat16_rn(r);
             out[s] = (uint32_t)__bfloat16_as_ushort(h);
-            r -= (double)__bfloat162float(h);
+            r = __fsub_rn(r, __bfloat162float(h));
         }
     }
 }
@@ -221,7 +226,7 @@ __global__ void __launch_bounds__(kTileA, 1) k_contract_tc(ContractArgs A, int n
 #pragma unroll
                     for (int i = 0; i < KPC; i++) {
                         uint32_t sp[C::NS];
-                        split<PREC>((double)s_tab[eidx * HW + idx[i]], sp);
+                        split<PREC>(s_tab[eidx * HW + idx[i]], sp);
 #pragma unroll
                         for (int s2 = 0; s2 < C::NS; s2++) pk[s2][i] = sp[s2];
                     }
@@ -242,7 +247,7 @@ __global__ void __launch_bounds__(kTileA, 1) k_contract_tc(ContractArgs A, int n
                     uint32_t pk[C::NS][KPC];
 #pragma unroll
                     for (int i = 0; i < KPC; i++) {
-                        double v = (r < RG) ? src[i * 6 + (c < 3 ? c : 2)] : 0.0;
+                        float v = (r < RG) ? (float)src[i * 6 + (c < 3 ? c : 2)] : 0.0f;
                         if (c == 3) v = -v;
                         uint32_t sp[C::NS];
                         split<PREC>(v, sp);
@@ -258,9 +263,6 @@ __global__ void __launch_bounds__(kTileA, 1) k_contract_tc(ContractArgs A, int n
             __syncthreads();
             if (threadIdx.x == 0) {
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                // entry of M for (c_out, c_in); B block 3 holds -X2
-                const int ent[3][3] = {{0, 1, 4}, {1, 2, 5}, {4, 5, 3}};
-                const int bsel[3][3] = {{0, 1, 3}, {0, 1, 3}, {0, 1, 2}};
 #pragma unroll 1
                 for (int co = 0; co < 3; co++) {
 #pragma unroll 1
@@ -269,8 +271,8 @@ __global__ void __launch_bounds__(kTileA, 1) k_contract_tc(ContractArgs A, int n
                         for (int pr = 0; pr < C::NPROD; pr++)
 #pragma unroll 1
                             for (int s = 0; s < C::KB / C::KMMA; s++) {
-                                const uint32_t aa = smem_u32(sA) + (ent[co][ci] * C::NS + c_prod_a[pr]) * ABLK + 256 * s;
-                                const uint32_t bb = smem_u32(sB) + (bsel[co][ci] * C::NS + c_prod_b[pr]) * BBLK + 256 * s;
+                                const uint32_t aa = smem_u32(sA) + (c_ent[co][ci] * C::NS + c_prod_a[pr]) * ABLK + 256 * s;
+                                const uint32_t bb = smem_u32(sB) + (c_bsel[co][ci] * C::NS + c_prod_b[pr]) * BBLK + 256 * s;
                                 const uint64_t da = sdesc(aa, 128, SBO_A), db = sdesc(bb, 128, SBO_A);
                                 const uint32_t accum = acc[co] ? 1u : 0u;
                                 const uint32_t dt = tmem + (uint32_t)(co * NP);

@@ -81,6 +81,7 @@ struct Plan {
     double* d_table = nullptr;   // [K][Dy][Dx][6] FP64
     float* d_table32 = nullptr;  // [K][Dy][Dx][6] FP32 (FBC_PREC_FP32)
     float* d_table_x2 = nullptr; // [K][Dy][Dx][12] hi/lo pairs (FBC_PREC_F32X2)
+    float* d_table_x2_k0 = nullptr; // [Dy][Dx][12]: the k = 0 slice as hi/lo pairs (FP32 and tensor-core plans)
     double* d_fh = nullptr;      // [max_rhs][K][NIpad][6]
     double* d_uh = nullptr;      // [max_rhs][K][NPpad][6]
     double* d_part = nullptr;    // [max_rhs][n_line_blocks_p][3] zero-mean partial sums
@@ -127,19 +128,22 @@ cudaError_t launch_inverse(Plan& P, double* u, int n_rhs, double alpha, double b
                            cudaStream_t st);
 cudaError_t launch_derive_tables(Plan& P, int precision, cudaStream_t st);
 ContractArgs make_contract_args(const Plan& P);
-size_t batch_contract_smem(int precision, int W, int H);
 cudaError_t launch_contract_tc(const ContractArgs& A, const Plan& P, int n_rhs, cudaStream_t st);
 size_t contract_tc_smem(int precision, int HW);
 inline bool is_tensor_precision(int p) { return p == FBC_PREC_TF32 || p == FBC_PREC_BF16X2 || p == FBC_PREC_BF16X3; }
 int batch_rhs_block();
-int batch_contract_occupancy(int precision, size_t smem);
 LineArgs make_line_args(const Plan& P, const double* f, double* u);
 size_t batch_line_smem(int max_L);
 // stage 0 forward, 1 projection, 2 inverse, 3 zero mean; items as documented in fbc_line.cu
 cudaError_t launch_batch_line(int stage, const LineArgs* d_args, const int4* d_items, int n_items, size_t smem,
                               double alpha, double beta, int want_part, cudaStream_t st);
-cudaError_t launch_batch_contract(int precision, const ContractArgs* d_args, const int* d_n_rhs, const int4* d_items,
-                                  int n_items, int* d_counter, int grid, size_t smem, cudaStream_t st);
+// phase 0: k = 0 items (double-float tile), phase 1: k >= 1 items of an FP32 batch (8-rhs FP32 tile);
+// FP64 and double-float batches use phase 1 with their own tile for every item
+cudaError_t launch_batch_contract(int precision, int phase, const ContractArgs* d_args, const int* d_n_rhs,
+                                  const int4* d_items, int n_items, int* d_counter, int grid, size_t smem,
+                                  cudaStream_t st);
+size_t batch_contract_smem_phase(int precision, int phase, int W, int H);
+int batch_contract_occupancy_phase(int precision, int phase, size_t smem);
 
 // Record the message fbc_last_error() returns for this thread; returns code.
 int report_error(int code, const char* msg);

@@ -180,7 +180,7 @@ int dev_alloc(T** p, size_t count, size_t& acc, const char* what) {
 
 void free_plan(fbc::Plan& P) {
     void* bufs[] = {P.d_xy_p,  P.d_off_i,    P.d_bbox_a, P.d_bbox_b, P.d_perm_i, P.d_perm_p,
-                    P.d_used,  P.d_tw,       P.d_twL,    P.d_table,  P.d_table32, P.d_table_x2,
+                    P.d_used,  P.d_tw,       P.d_twL,    P.d_table,  P.d_table32, P.d_table_x2, P.d_table_x2_k0,
                     P.d_fh,    P.d_uh,       P.d_part,   P.d_stage_f, P.d_stage_u, P.d_status};
     for (void* b : bufs)
         if (b) cudaFree(b);
@@ -198,6 +198,11 @@ int ensure_derived(fbc::Plan& P, int precision) {
     }
     if (precision == FBC_PREC_F32X2 && !P.d_table_x2) {
         int s = dev_alloc(&P.d_table_x2, cells * 12, acc, "table_x2");
+        if (s) return s;
+    }
+    // the k = 0 mode of the FP32 and tensor-core forms runs in double-float
+    if ((precision == FBC_PREC_FP32 || fbc::is_tensor_precision(precision)) && !P.d_table_x2_k0) {
+        int s = dev_alloc(&P.d_table_x2_k0, (size_t)P.Dy * P.Dx * 12, acc, "table_x2_k0");
         if (s) return s;
     }
     P.workspace_bytes += acc;

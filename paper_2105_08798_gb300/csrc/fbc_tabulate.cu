@@ -266,8 +266,11 @@ cudaError_t launch_tabulate(Plan& P, cudaStream_t st) {
 cudaError_t launch_derive_tables(Plan& P, int precision, cudaStream_t st) {
     const size_t cells = (size_t)P.K * P.Dy * P.Dx;
     if (precision == FBC_PREC_FP32 || is_tensor_precision(precision)) {
-        if (!P.d_table32) return cudaErrorInvalidValue;
+        if (!P.d_table32 || !P.d_table_x2_k0) return cudaErrorInvalidValue;
         k_derive_fp32<<<1216, 256, 0, st>>>(P.d_table, P.d_table32, cells * 6);
+        cudaError_t e = cudaGetLastError();
+        if (e) return e;
+        k_derive_x2<<<1216, 256, 0, st>>>(P.d_table, P.d_table_x2_k0, (size_t)P.Dy * P.Dx);  // k = 0 slice
         return cudaGetLastError();
     }
     if (precision == FBC_PREC_F32X2) {
