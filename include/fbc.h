@@ -124,6 +124,9 @@ typedef struct fbc_plan_info {
     double pair_modes_per_rhs;  /* n_p * n_i * K */
     size_t table_bytes;         /* FP64 mode table */
     size_t workspace_bytes;     /* everything else the plan owns on the device */
+    size_t surrogate_bytes;     /* buffers of an attached surrogate (slice, near copy, lists, activations) */
+    int32_t surrogate_attached; /* 1 while a surrogate is attached */
+    int32_t n_far_d;            /* used differences the surrogate serves (|d| >= r_min) */
 } fbc_plan_info;
 
 /* Defaults listed in fbc_options. */
@@ -275,6 +278,79 @@ void fbc_batch_destroy(fbc_batch* batch);
  * a device looks up the array's device address (make it before any stream
  * capture).  Asynchronous on `stream`; allocates nothing. */
 int fbc_zero_mean_static(double* u, int32_t n_rhs, int32_t n_p, int32_t L, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * Learned surrogate of the mode table (an extension; the paper tabulates the
+ * kernel exactly and has no learned model).  For a difference d != 0 and a
+ * mode k >= 1 a multilayer perceptron 4 -> H -> H -> H -> 6 with SiLU
+ * activations maps the features
+ *     x = (q r / 32, d_x / r, d_y / r, ln(r) / 5),  r = |d|,  q = 2 pi k / (L c)
+ * to the six reals [A11, A12, A22, A33, B13, B23] of the mode table (the
+ * layout fbc_get_mode_table returns), divided by the scale
+ *     s(q, r) = exp(-q r) / (c sqrt(1 + q r)),
+ * the decay of the modified Bessel functions K_0, K_1 that the line sum of
+ * the Green function (Eqs. 32-36) becomes for k >= 1.  Entries with
+ * q r > 16 (below exp(-16) of the entry at q r -> 0, and below the FP64
+ * table's own roundoff after Richardson extrapolation) are served as zero;
+ * training samples only q r <= 16.  Parameters are FP32
+ * master weights (He initialisation from `seed`), trained with Adam on
+ * samples of the plan's exact FP64 table; inference uses the weights rounded
+ * to BF16 with FP32 accumulation.  Layout of the parameter vector: W1 [4][H],
+ * b1 [H], W2 [H][H], b2 [H], W3 [H][H], b3 [H], W4 [H][6], b4 [6]
+ * (row = input).  The surrogate object owns its device buffers.
+ * ------------------------------------------------------------------------- */
+typedef struct fbc_surrogate fbc_surrogate;
+
+/* Create a surrogate of hidden width H (multiple of 8 in [8, 1024]). */
+int fbc_surrogate_create(int32_t width, uint64_t seed, fbc_surrogate** out);
+
+/* Number of parameters (4H + H + 2(H^2 + H) + 6H + 6); 0 for NULL. */
+int fbc_surrogate_n_params(const fbc_surrogate* s);
+
+/* Copy the FP32 master parameters: host_in (may be NULL) is written to the
+ * device first, then the device copy is read into host_out (may be NULL). */
+int fbc_surrogate_params(fbc_surrogate* s, float* host_out, const float* host_in);
+
+/* Network output y[n][6] = MLP(x[n][4]) (scaled units, no s(q, r)).
+ * x, y: DEVICE float.  bf16_weights != 0 uses the BF16-rounded weights. */
+int fbc_surrogate_forward(fbc_surrogate* s, const float* x, float* y, int32_t n, int32_t bf16_weights, void* stream);
+
+/* Mean squared error  loss = sum_i sum_j (y_ij - t_ij)^2 / (6 n)  over the
+ * FP32 weights and its gradient.  x[n][4], t[n][6]: DEVICE float.  loss
+ * (host double, may be NULL) and host_grad (host float[n_params], may be
+ * NULL) are written after the stream synchronises. */
+int fbc_surrogate_loss_grad(fbc_surrogate* s, const float* x, const float* t, int32_t n, double* loss,
+                            float* host_grad, void* stream);
+
+/* Train on n_samples pairs (d, k) drawn (seeded) from the plan's differences
+ * with |d| >= r_min and modes 1 <= k < K, targets from the exact FP64 table
+ * divided by s(q, r): `epochs` passes of Adam (beta 0.9, 0.999) over batches
+ * of `batch`, learning rate lr decayed by a half cosine over the epochs.
+ * final_loss (may be NULL) receives the last batch's loss.  The plan must be
+ * tabulated.  Blocks until done. */
+int fbc_surrogate_train(fbc_surrogate* s, const fbc_plan* plan, int32_t n_samples, double r_min, int32_t epochs,
+                        int32_t batch, double lr, uint64_t seed, void* stream, double* final_loss);
+
+/* Surrogate mode-table entries for n pairs: d[n][2] (host int32, d != 0),
+ * k[n] (host int32, 1 <= k < K); out[n][6] (host double) in the layout of
+ * fbc_get_mode_table, BF16 weights.  Blocks until done. */
+int fbc_surrogate_eval_table(fbc_surrogate* s, const fbc_plan* plan, const int32_t* d, const int32_t* k, int32_t n,
+                             double* out);
+
+/* Attach a trained surrogate to a plan whose precision is FBC_PREC_FP32 or
+ * a tensor-core form.  fbc_apply then builds, per mode k >= 1, one FP32 mode
+ * slice in device memory -- the surrogate for |d| >= r_min, the exact table
+ * (a compact FP32 copy of the near differences) below -- and contracts with
+ * it; mode k = 0 stays exact.  release_tables != 0 frees the plan's K-slice
+ * tables (FP64 and derived), keeping only the near copy and the k = 0 slice:
+ * the plan can then neither be re-tabulated nor switch precision, and
+ * fbc_get_mode_table fails.  s == NULL detaches (refused once tables were
+ * released).  The plan keeps a pointer to s: s must outlive the plan or be
+ * detached first; later training of s takes effect at the next attach. */
+int fbc_plan_attach_surrogate(fbc_plan* plan, fbc_surrogate* s, double r_min, int32_t release_tables);
+
+/* Release the surrogate.  NULL is ignored. */
+void fbc_surrogate_destroy(fbc_surrogate* s);
 
 #ifdef __cplusplus
 }

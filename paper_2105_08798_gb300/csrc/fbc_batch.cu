@@ -131,6 +131,7 @@ int fbc_batch_create(fbc_plan* const* plans, int32_t n_plans, const double* cons
         const fbc::Plan& P = plans[i]->p;
         if (P.host_only) return bfail(FBC_ERR_INVALID_ARG, "host-only plan in a batch");
         if (!P.tabulated) return bfail(FBC_ERR_NOT_TABULATED, "every plan of a batch must be tabulated");
+        if (P.sur) return bfail(FBC_ERR_UNSUPPORTED, "a plan with a surrogate attached runs on its own");
         if (prec < 0) prec = P.precision;
         if (P.precision != prec) return bfail(FBC_ERR_INVALID_ARG, "all plans of a batch need the same precision");
         if (fbc::is_tensor_precision(prec))
@@ -226,6 +227,10 @@ int fbc_batch_apply(fbc_batch* b, double alpha, double beta, uint32_t flags, voi
     if (flags & ~(FBC_APPLY_PROJECT_NEUTRAL | FBC_APPLY_ZERO_MEAN_U | FBC_APPLY_NO_GRAPH))
         return bfail(FBC_ERR_INVALID_ARG, "unknown apply flags");
     if (!std::isfinite(alpha) || !std::isfinite(beta)) return bfail(FBC_ERR_INVALID_ARG, "alpha/beta not finite");
+    // the batch holds the plans' table pointers as they were at creation
+    for (const fbc_plan* pl : b->plans)
+        if (pl->p.sur || pl->p.precision != b->precision)
+            return bfail(FBC_ERR_INVALID_ARG, "a plan changed precision or took a surrogate after the batch was made");
     cudaStream_t st = (cudaStream_t)stream;
     const uint32_t gflags = flags & ~FBC_APPLY_NO_GRAPH;
     if (flags & FBC_APPLY_NO_GRAPH) {

@@ -159,7 +159,7 @@ __global__ void __launch_bounds__(kTileA, 1) k_contract_tc(ContractArgs A, int n
     const int a = tA * TA + a_loc;
     const int2 xa = A.xy_p[a];
     const int4 bA = A.bbox_a[tA];
-    const float* tk = A.tab32 + (size_t)k * A.Dy * A.Dx * 6;
+    const float* tk = A.tab32 + (size_t)(k * A.kmul) * A.Dy * A.Dx * 6;
 
     if (threadIdx.x == 0) {
         s_abort = 0;
@@ -342,12 +342,12 @@ size_t tc_smem(int HW) {
 }
 
 template <int PREC>
-cudaError_t launch_tc(const ContractArgs& A, const Plan& P, int n_rhs, cudaStream_t st) {
+cudaError_t launch_tc(const ContractArgs& A, const Plan& P, int n_rhs, cudaStream_t st, int n_modes) {
     const size_t smem = tc_smem<PREC>(P.H * P.W);
     if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
     cudaError_t e = cudaFuncSetAttribute(k_contract_tc<PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e) return e;
-    dim3 grid(P.n_ta, P.K - 1, (n_rhs + kRhsPerCta - 1) / kRhsPerCta);
+    dim3 grid(P.n_ta, n_modes, (n_rhs + kRhsPerCta - 1) / kRhsPerCta);
     k_contract_tc<PREC><<<grid, kTileA, smem, st>>>(A, n_rhs, P.d_status);
     return cudaGetLastError();
 }
@@ -360,11 +360,12 @@ size_t contract_tc_smem(int precision, int HW) {
     return tc_smem<FBC_PREC_BF16X3>(HW);
 }
 
-// Modes k >= 1 on the tensor cores (A.k0 must be 1).
-cudaError_t launch_contract_tc(const ContractArgs& A, const Plan& P, int n_rhs, cudaStream_t st) {
-    if (P.precision == FBC_PREC_TF32) return launch_tc<FBC_PREC_TF32>(A, P, n_rhs, st);
-    if (P.precision == FBC_PREC_BF16X2) return launch_tc<FBC_PREC_BF16X2>(A, P, n_rhs, st);
-    if (P.precision == FBC_PREC_BF16X3) return launch_tc<FBC_PREC_BF16X3>(A, P, n_rhs, st);
+// Modes A.k0 .. A.k0 + n_modes - 1 (default: through K - 1) on the tensor cores (A.k0 >= 1).
+cudaError_t launch_contract_tc(const ContractArgs& A, const Plan& P, int n_rhs, cudaStream_t st, int n_modes) {
+    if (n_modes < 0) n_modes = P.K - A.k0;
+    if (P.precision == FBC_PREC_TF32) return launch_tc<FBC_PREC_TF32>(A, P, n_rhs, st, n_modes);
+    if (P.precision == FBC_PREC_BF16X2) return launch_tc<FBC_PREC_BF16X2>(A, P, n_rhs, st, n_modes);
+    if (P.precision == FBC_PREC_BF16X3) return launch_tc<FBC_PREC_BF16X3>(A, P, n_rhs, st, n_modes);
     return cudaErrorInvalidValue;
 }
 

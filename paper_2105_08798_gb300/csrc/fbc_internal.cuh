@@ -89,6 +89,19 @@ struct Plan {
     double* d_stage_u = nullptr;
     int* d_status = nullptr;     // device error word
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};  // stage timing (optional)
+    // learned far field (fbc_plan_attach_surrogate): streamed per-mode slices
+    fbc_surrogate* sur = nullptr;
+    double sur_rmin = 0.0;
+    size_t sur_bytes = 0;
+    bool tables_released = false;
+    int n_far = 0, n_near = 0;
+    int2* d_far = nullptr;
+    int2* d_near = nullptr;
+    float* d_near32 = nullptr;   // [K][n_near][6] exact entries of the near field
+    float* d_slice = nullptr;    // [Dy][Dx][6] one streamed mode slice (FP32)
+    float* d_sX = nullptr;       // [n_far][4] network inputs
+    float* d_sY = nullptr;       // [n_far][6] network outputs
+    float* d_sact = nullptr;     // [6][n_far][width] hidden activations
     bool timing = false, timed_once = false;
     size_t table_bytes = 0, workspace_bytes = 0;
 };
@@ -105,6 +118,7 @@ struct ContractArgs {
     const int4* bbox_a;
     const int4* bbox_b;
     int n_tb, K, Dx, Dy, box_x0, box_y0, W, H, NIpad, NPpad, k0;
+    int kmul;  // 1: the tables hold K mode slices; 0: one streamed slice serves the mode being contracted
 };
 
 // Everything the line transforms need about one plan (one instance of a batch).
@@ -128,7 +142,15 @@ cudaError_t launch_inverse(Plan& P, double* u, int n_rhs, double alpha, double b
                            cudaStream_t st);
 cudaError_t launch_derive_tables(Plan& P, int precision, cudaStream_t st);
 ContractArgs make_contract_args(const Plan& P);
-cudaError_t launch_contract_tc(const ContractArgs& A, const Plan& P, int n_rhs, cudaStream_t st);
+cudaError_t launch_contract_tc(const ContractArgs& A, const Plan& P, int n_rhs, cudaStream_t st, int n_modes = -1);
+// contraction of modes k0 .. k0 + n_modes - 1 in the plan's precision (k0 >= 1 for the FP32 and tensor forms)
+cudaError_t launch_contract_modes(Plan& P, const ContractArgs& A, int k0, int n_modes, int n_rhs, cudaStream_t st);
+cudaError_t launch_contract_x2_k0(Plan& P, const ContractArgs& A, int n_rhs, cudaStream_t st);
+cudaError_t surrogate_forward(const fbc_surrogate* S, const float* params, const float* X, int n, float* Y, float* act,
+                              int cap, cudaStream_t st);
+// streamed contraction of a plan with an attached surrogate (modes k >= 1)
+cudaError_t launch_contract_streamed(Plan& P, int n_rhs, cudaStream_t st);
+void release_surrogate_buffers(Plan& P);
 size_t contract_tc_smem(int precision, int HW);
 inline bool is_tensor_precision(int p) { return p == FBC_PREC_TF32 || p == FBC_PREC_BF16X2 || p == FBC_PREC_BF16X3; }
 int batch_rhs_block();
@@ -161,3 +183,4 @@ inline int line_cols(int L) {
 struct fbc_plan {
     fbc::Plan p;
 };
+

@@ -186,6 +186,7 @@ void free_plan(fbc::Plan& P) {
         if (b) cudaFree(b);
     for (auto& e : P.ev)
         if (e) cudaEventDestroy(e), e = nullptr;
+    fbc::release_surrogate_buffers(P);
 }
 
 // Allocate the derived table a reduced-precision contraction reads (once).
@@ -469,6 +470,7 @@ int fbc_tabulate_kernel(fbc_plan* plan, void* stream) {
     if (!plan) return fail(FBC_ERR_INVALID_ARG, "plan is NULL");
     fbc::Plan& P = plan->p;
     if (P.host_only) return fail(FBC_ERR_INVALID_ARG, "host-only plan");
+    if (P.tables_released) return fail(FBC_ERR_UNSUPPORTED, "the plan's tables were released for its surrogate");
     cudaStream_t st = (cudaStream_t)stream;
     cudaError_t e = fbc::launch_tabulate(P, st);
     if (e != cudaSuccess) return cuda_fail(e, "tabulate");
@@ -487,6 +489,9 @@ int fbc_plan_set_precision(fbc_plan* plan, int32_t precision) {
         return fail(FBC_ERR_INVALID_ARG, "unknown precision %d", precision);
     fbc::Plan& P = plan->p;
     if (P.host_only) return fail(FBC_ERR_INVALID_ARG, "host-only plan");
+    if (P.tables_released) return fail(FBC_ERR_UNSUPPORTED, "the plan's tables were released for its surrogate");
+    if (P.sur && precision != FBC_PREC_FP32 && !fbc::is_tensor_precision(precision))
+        return fail(FBC_ERR_UNSUPPORTED, "detach the surrogate before switching to this precision");
     if (int st = ensure_derived(P, precision)) return st;
     P.precision = precision;
     if (P.tabulated && precision != FBC_PREC_FP64) {
@@ -501,6 +506,7 @@ static int apply_common(fbc::Plan& P, const double* f, double* u, int32_t n_rhs,
                         uint32_t flags, cudaStream_t st) {
     if (P.host_only) return fail(FBC_ERR_INVALID_ARG, "host-only plan");
     if (!P.tabulated) return fail(FBC_ERR_NOT_TABULATED, "fbc_apply before fbc_tabulate_kernel");
+    if (P.tables_released && !P.sur) return fail(FBC_ERR_INVALID_ARG, "tables released without a surrogate");
     if (!f || !u) return fail(FBC_ERR_INVALID_ARG, "f or u is NULL");
     if (n_rhs < 1 || n_rhs > P.opt.max_rhs)
         return fail(FBC_ERR_INVALID_ARG, "n_rhs = %d outside [1, max_rhs = %d]", n_rhs, P.opt.max_rhs);
@@ -512,7 +518,7 @@ static int apply_common(fbc::Plan& P, const double* f, double* u, int32_t n_rhs,
     const char* fc = (const char*)f;
     const char* uc = (const char*)u;
     if (fc < uc + ub && uc < fc + fb) return fail(FBC_ERR_INVALID_ARG, "f and u overlap");
-    if ((P.precision == FBC_PREC_FP32 || fbc::is_tensor_precision(P.precision)) && !P.d_table32)
+    if ((P.precision == FBC_PREC_FP32 || fbc::is_tensor_precision(P.precision)) && !P.d_table32 && !P.sur)
         return fail(FBC_ERR_INVALID_ARG, "FP32 table missing");
     if (fbc::is_tensor_precision(P.precision) && fbc::contract_tc_smem(P.precision, P.W * P.H) > 227 * 1024)
         return fail(FBC_ERR_UNSUPPORTED, "tensor-core contraction: staged sub-box too large for shared memory");
@@ -521,7 +527,14 @@ static int apply_common(fbc::Plan& P, const double* f, double* u, int32_t n_rhs,
     cudaError_t e = fbc::launch_forward(P, f, n_rhs, (flags & FBC_APPLY_PROJECT_NEUTRAL) != 0, st);
     if (e != cudaSuccess) return cuda_fail(e, "forward transform");
     if (P.timing) FBC_CUDA(cudaEventRecord(P.ev[1], st));
-    e = fbc::launch_contract(P, n_rhs, st);
+    if (P.sur) {
+        // k = 0 exact (double-float slice), modes k >= 1 from streamed slices
+        fbc::ContractArgs A0 = fbc::make_contract_args(P);
+        e = fbc::launch_contract_x2_k0(P, A0, n_rhs, st);
+        if (e == cudaSuccess) e = fbc::launch_contract_streamed(P, n_rhs, st);
+    } else {
+        e = fbc::launch_contract(P, n_rhs, st);
+    }
     if (e != cudaSuccess) return cuda_fail(e, "mode contraction");
     if (P.timing) FBC_CUDA(cudaEventRecord(P.ev[2], st));
     e = fbc::launch_inverse(P, u, n_rhs, alpha, beta, (flags & FBC_APPLY_ZERO_MEAN_U) != 0, st);
@@ -605,6 +618,9 @@ int fbc_plan_info_get(const fbc_plan* plan, fbc_plan_info* info) {
     info->tabulated = P.tabulated ? 1 : 0;
     info->pair_modes_per_rhs = (double)P.n_p * (double)P.n_i * (double)P.K;
     info->table_bytes = P.table_bytes;
+    info->surrogate_bytes = P.sur_bytes;
+    info->surrogate_attached = P.sur ? 1 : 0;
+    info->n_far_d = P.n_far;
     info->workspace_bytes = P.workspace_bytes;
     return FBC_OK;
 }
@@ -630,6 +646,7 @@ int fbc_get_mode_table(const fbc_plan* plan, const int32_t* d, int32_t nd, doubl
     const fbc::Plan& P = plan->p;
     if (P.host_only) return fail(FBC_ERR_INVALID_ARG, "host-only plan");
     if (!P.tabulated) return fail(FBC_ERR_NOT_TABULATED, "table not tabulated");
+    if (!P.d_table) return fail(FBC_ERR_UNSUPPORTED, "the plan's tables were released for its surrogate");
     FBC_CUDA(cudaDeviceSynchronize());
     for (int t = 0; t < nd; t++) {
         int ix = d[2 * t] - P.box_x0, iy = d[2 * t + 1] - P.box_y0;

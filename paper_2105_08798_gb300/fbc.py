@@ -75,7 +75,8 @@ class fbc_plan_info(ctypes.Structure):
                                               "n_tiles_a", "n_tiles_b", "box_x0", "box_y0", "box_nx", "box_ny",
                                               "sub_w", "sub_h", "n_used_d", "tabulated")] + [
         ("pair_modes_per_rhs", ctypes.c_double), ("table_bytes", ctypes.c_size_t),
-        ("workspace_bytes", ctypes.c_size_t)]
+        ("workspace_bytes", ctypes.c_size_t), ("surrogate_bytes", ctypes.c_size_t),
+        ("surrogate_attached", ctypes.c_int32), ("n_far_d", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
         return {name: getattr(self, name) for name, _ in self._fields_}
@@ -120,6 +121,17 @@ _SIGNATURES = {
     "fbc_batch_autotune": (ctypes.c_int, [_vp, _vp, _P(ctypes.c_double)]),
     "fbc_batch_info_get": (ctypes.c_int, [_vp, _P(fbc_batch_info)]),
     "fbc_batch_destroy": (None, [_vp]),
+    "fbc_surrogate_create": (ctypes.c_int, [ctypes.c_int32, ctypes.c_uint64, _P(_vp)]),
+    "fbc_surrogate_n_params": (ctypes.c_int, [_vp]),
+    "fbc_surrogate_params": (ctypes.c_int, [_vp, _vp, _vp]),
+    "fbc_surrogate_forward": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int32, ctypes.c_int32, _vp]),
+    "fbc_surrogate_loss_grad": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int32, _P(ctypes.c_double), _vp, _vp]),
+    "fbc_surrogate_train": (ctypes.c_int, [_vp, _vp, ctypes.c_int32, ctypes.c_double, ctypes.c_int32, ctypes.c_int32,
+                                           ctypes.c_double, ctypes.c_uint64, _vp, _P(ctypes.c_double)]),
+    "fbc_surrogate_eval_table": (ctypes.c_int, [_vp, _vp, _P(ctypes.c_int32), _P(ctypes.c_int32), ctypes.c_int32,
+                                                _P(ctypes.c_double)]),
+    "fbc_plan_attach_surrogate": (ctypes.c_int, [_vp, _vp, ctypes.c_double, ctypes.c_int32]),
+    "fbc_surrogate_destroy": (None, [_vp]),
 }
 
 
@@ -273,6 +285,65 @@ def fbc_batch_destroy(batch: int):
     load().fbc_batch_destroy(batch)
 
 
+def fbc_surrogate_create(width: int, seed: int) -> int:
+    h = _vp()
+    _check(load().fbc_surrogate_create(width, seed, ctypes.byref(h)), "fbc_surrogate_create")
+    return h.value
+
+
+def fbc_surrogate_n_params(sur: int) -> int:
+    return load().fbc_surrogate_n_params(sur)
+
+
+def fbc_surrogate_params(sur: int, host_out: np.ndarray | None, host_in: np.ndarray | None):
+    for a in (host_out, host_in):
+        if a is not None and (a.dtype != np.float32 or not a.flags.c_contiguous or a.size != fbc_surrogate_n_params(sur)):
+            raise ValueError("parameter arrays must be contiguous float32 of n_params")
+    _check(load().fbc_surrogate_params(sur, None if host_out is None else host_out.ctypes.data,
+                                       None if host_in is None else host_in.ctypes.data), "fbc_surrogate_params")
+
+
+def fbc_surrogate_forward(sur: int, x_ptr: int, y_ptr: int, n: int, bf16_weights: bool, stream=None):
+    _check(load().fbc_surrogate_forward(sur, x_ptr, y_ptr, n, int(bf16_weights), _stream_handle(stream)),
+           "fbc_surrogate_forward")
+
+
+def fbc_surrogate_loss_grad(sur: int, x_ptr: int, t_ptr: int, n: int, stream=None) -> tuple[float, np.ndarray]:
+    loss = ctypes.c_double()
+    g = np.empty(fbc_surrogate_n_params(sur), dtype=np.float32)
+    _check(load().fbc_surrogate_loss_grad(sur, x_ptr, t_ptr, n, ctypes.byref(loss), g.ctypes.data,
+                                          _stream_handle(stream)), "fbc_surrogate_loss_grad")
+    return loss.value, g
+
+
+def fbc_surrogate_train(sur: int, plan: int, n_samples: int, r_min: float, epochs: int, batch: int, lr: float,
+                        seed: int, stream=None) -> float:
+    loss = ctypes.c_double()
+    _check(load().fbc_surrogate_train(sur, plan, n_samples, r_min, epochs, batch, lr, seed, _stream_handle(stream),
+                                      ctypes.byref(loss)), "fbc_surrogate_train")
+    return loss.value
+
+
+def fbc_surrogate_eval_table(sur: int, plan: int, d: np.ndarray, k: np.ndarray) -> np.ndarray:
+    d = np.ascontiguousarray(d, dtype=np.int32).reshape(-1, 2)
+    k = np.ascontiguousarray(k, dtype=np.int32).reshape(-1)
+    if d.shape[0] != k.shape[0]:
+        raise ValueError("d and k differ in length")
+    out = np.empty((k.shape[0], 6), dtype=np.float64)
+    _check(load().fbc_surrogate_eval_table(sur, plan, d.ctypes.data_as(_P(ctypes.c_int32)),
+                                           k.ctypes.data_as(_P(ctypes.c_int32)), k.shape[0],
+                                           out.ctypes.data_as(_P(ctypes.c_double))), "fbc_surrogate_eval_table")
+    return out
+
+
+def fbc_plan_attach_surrogate(plan: int, sur: int | None, r_min: float, release_tables: bool):
+    _check(load().fbc_plan_attach_surrogate(plan, sur, r_min, int(release_tables)), "fbc_plan_attach_surrogate")
+
+
+def fbc_surrogate_destroy(sur: int):
+    load().fbc_surrogate_destroy(sur)
+
+
 # ---- convenience wrapper -----------------------------------------------------
 def material_struct(material: dict) -> fbc_material:
     m = fbc_material()
@@ -298,6 +369,7 @@ class Plan:
                  rich_n: int | None = None, rich_N: int | None = None, quad: int | None = None, max_rhs: int = 1,
                  host_only: bool = False):
         self._h = None
+        self._sur = None
         xy_i = np.ascontiguousarray(xy_i, dtype=np.int32)
         xy_p = np.ascontiguousarray(xy_p, dtype=np.int32)
         g = fbc_geometry(len(xy_i), len(xy_p), int(L), float(c), xy_i.ctypes.data_as(_P(ctypes.c_int32)),
@@ -377,9 +449,86 @@ class Plan:
     def sync_status(self, stream=None):
         fbc_plan_sync_status(self.handle, stream)
 
+    def attach_surrogate(self, sur: "Surrogate | None", r_min: float = 8.0, release_tables: bool = False):
+        """Serve modes k >= 1 at |d| >= r_min from ``sur`` (None detaches); see fbc_plan_attach_surrogate."""
+        fbc_plan_attach_surrogate(self.handle, None if sur is None else sur.handle, r_min, release_tables)
+        self._sur = sur  # keep the surrogate alive while attached
+
     def close(self):
         if self._h is not None:
             fbc_destroy(self._h)
+            self._h = None
+        self._sur = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Surrogate:
+    """Owning handle of one ``fbc_surrogate`` (MLP 4 -> H -> H -> H -> 6 of the scaled mode table)."""
+
+    def __init__(self, width: int = 128, seed: int = 0):
+        self._h = None
+        self._h = fbc_surrogate_create(width, seed)
+        self.width = width
+
+    @property
+    def handle(self) -> int:
+        if self._h is None:
+            raise ValueError("surrogate is closed")
+        return self._h
+
+    @property
+    def n_params(self) -> int:
+        return fbc_surrogate_n_params(self.handle)
+
+    def params(self) -> np.ndarray:
+        out = np.empty(self.n_params, dtype=np.float32)
+        fbc_surrogate_params(self.handle, out, None)
+        return out
+
+    def set_params(self, p: np.ndarray):
+        fbc_surrogate_params(self.handle, None, np.ascontiguousarray(p, dtype=np.float32))
+
+    def forward(self, x, bf16_weights: bool = False):
+        """y [n][6] = MLP(x [n][4]) on float32 CUDA tensors."""
+        import torch
+
+        if x.dtype != torch.float32 or not x.is_cuda or x.dim() != 2 or x.shape[1] != 4 or not x.is_contiguous():
+            raise TypeError("x must be a contiguous float32 CUDA tensor [n][4]")
+        y = torch.empty((x.shape[0], 6), dtype=torch.float32, device=x.device)
+        fbc_surrogate_forward(self.handle, x.data_ptr(), y.data_ptr(), x.shape[0], bf16_weights,
+                              torch.cuda.current_stream(x.device))
+        return y
+
+    def loss_grad(self, x, t) -> tuple[float, np.ndarray]:
+        import torch
+
+        for a, w in ((x, 4), (t, 6)):
+            if a.dtype != torch.float32 or not a.is_cuda or a.dim() != 2 or a.shape[1] != w or not a.is_contiguous():
+                raise TypeError("x [n][4] and t [n][6] must be contiguous float32 CUDA tensors")
+        return fbc_surrogate_loss_grad(self.handle, x.data_ptr(), t.data_ptr(), x.shape[0],
+                                       torch.cuda.current_stream(x.device))
+
+    def train(self, plan: Plan, n_samples: int = 1 << 20, r_min: float = 8.0, epochs: int = 50, batch: int = 4096,
+              lr: float = 2e-3, seed: int = 0) -> float:
+        return fbc_surrogate_train(self.handle, plan.handle, n_samples, r_min, epochs, batch, lr, seed)
+
+    def table(self, plan: Plan, d, k) -> np.ndarray:
+        return fbc_surrogate_eval_table(self.handle, plan.handle, d, k)
+
+    def close(self):
+        if self._h is not None:
+            fbc_surrogate_destroy(self._h)
             self._h = None
 
     def __enter__(self):
