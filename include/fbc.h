@@ -284,7 +284,7 @@ int fbc_zero_mean_static(double* u, int32_t n_rhs, int32_t n_p, int32_t L, void*
  * kernel exactly and has no learned model).  For a difference d != 0 and a
  * mode k >= 1 a multilayer perceptron 4 -> H -> H -> H -> 6 with SiLU
  * activations maps the features
- *     x = (q r / 32, d_x / r, d_y / r, ln(r) / 5),  r = |d|,  q = 2 pi k / (L c)
+ *     x = (ln(q r) / 4, d_x / r, d_y / r, ln(r) / 5),  r = |d|,  q = 2 pi k / (L c)
  * to the six reals [A11, A12, A22, A33, B13, B23] of the mode table (the
  * layout fbc_get_mode_table returns), divided by the scale
  *     s(q, r) = exp(-q r) / (c sqrt(1 + q r)),
@@ -292,12 +292,13 @@ int fbc_zero_mean_static(double* u, int32_t n_rhs, int32_t n_p, int32_t L, void*
  * the Green function (Eqs. 32-36) becomes for k >= 1.  Entries with
  * q r > 16 (below exp(-16) of the entry at q r -> 0, and below the FP64
  * table's own roundoff after Richardson extrapolation) are served as zero;
- * training samples only q r <= 16.  Parameters are FP32
- * master weights (He initialisation from `seed`), trained with Adam on
- * samples of the plan's exact FP64 table; inference uses the weights rounded
- * to BF16 with FP32 accumulation.  Layout of the parameter vector: W1 [4][H],
- * b1 [H], W2 [H][H], b2 [H], W3 [H][H], b3 [H], W4 [H][6], b4 [6]
- * (row = input).  The surrogate object owns its device buffers.
+ * training samples only q r <= 16.  Parameters are FP32 master weights (He
+ * initialisation from `seed`), trained with Adam on samples of the plan's
+ * exact FP64 table; inference uses the weights rounded to BF16 with FP32
+ * accumulation (a fused tensor-core kernel for H in {32, 64, 96, 128}).
+ * Layout of the parameter vector: W1 [4][H], b1 [H], W2 [H][H], b2 [H],
+ * W3 [H][H], b3 [H], W4 [H][6], b4 [6] (row = input).  The surrogate object
+ * owns its device buffers.
  * ------------------------------------------------------------------------- */
 typedef struct fbc_surrogate fbc_surrogate;
 
@@ -312,8 +313,15 @@ int fbc_surrogate_n_params(const fbc_surrogate* s);
 int fbc_surrogate_params(fbc_surrogate* s, float* host_out, const float* host_in);
 
 /* Network output y[n][6] = MLP(x[n][4]) (scaled units, no s(q, r)).
- * x, y: DEVICE float.  bf16_weights != 0 uses the BF16-rounded weights. */
+ * x, y: DEVICE float.  bf16_weights != 0 uses the BF16-rounded weights (and,
+ * for the widths it takes, the fused tensor-core kernel, whose waits are
+ * bounded: a timeout is reported by fbc_surrogate_sync_status).
+ * Asynchronous on `stream`. */
 int fbc_surrogate_forward(fbc_surrogate* s, const float* x, float* y, int32_t n, int32_t bf16_weights, void* stream);
+
+/* Wait for `stream` and report a timeout of the fused inference kernel
+ * (FBC_ERR_TIMEOUT, after which the word is cleared). */
+int fbc_surrogate_sync_status(fbc_surrogate* s, void* stream);
 
 /* Mean squared error  loss = sum_i sum_j (y_ij - t_ij)^2 / (6 n)  over the
  * FP32 weights and its gradient.  x[n][4], t[n][6]: DEVICE float.  loss
@@ -323,8 +331,9 @@ int fbc_surrogate_loss_grad(fbc_surrogate* s, const float* x, const float* t, in
                             float* host_grad, void* stream);
 
 /* Train on n_samples pairs (d, k) drawn (seeded) from the plan's differences
- * with |d| >= r_min and modes 1 <= k < K, targets from the exact FP64 table
- * divided by s(q, r): `epochs` passes of Adam (beta 0.9, 0.999) over batches
+ * with |d| >= r_min -- d uniform, k log-uniform over the modes 1 <= k < K
+ * with q r <= 16 -- with targets from the exact FP64 table divided by
+ * s(q, r): `epochs` passes of Adam (beta 0.9, 0.999) over batches
  * of `batch`, learning rate lr decayed by a half cosine over the epochs.
  * final_loss (may be NULL) receives the last batch's loss.  The plan must be
  * tabulated.  Blocks until done. */
@@ -337,11 +346,13 @@ int fbc_surrogate_train(fbc_surrogate* s, const fbc_plan* plan, int32_t n_sample
 int fbc_surrogate_eval_table(fbc_surrogate* s, const fbc_plan* plan, const int32_t* d, const int32_t* k, int32_t n,
                              double* out);
 
-/* Attach a trained surrogate to a plan whose precision is FBC_PREC_FP32 or
- * a tensor-core form.  fbc_apply then builds, per mode k >= 1, one FP32 mode
- * slice in device memory -- the surrogate for |d| >= r_min, the exact table
- * (a compact FP32 copy of the near differences) below -- and contracts with
- * it; mode k = 0 stays exact.  release_tables != 0 frees the plan's K-slice
+/* Attach a trained surrogate (width 32, 64, 96 or 128) to a plan whose
+ * precision is FBC_PREC_FP32 or a tensor-core form.  fbc_apply then builds,
+ * for a chunk of modes k >= 1 at a time (as many as fit in about 48 MB), FP32
+ * mode slices in device memory -- the network for |d| >= r_min, a compact
+ * FP32 copy of the exact table for the near differences -- and contracts with
+ * them in one launch per chunk; mode k = 0 stays exact.  A timeout of the
+ * network kernel is reported through the plan's status word.  release_tables != 0 frees the plan's K-slice
  * tables (FP64 and derived), keeping only the near copy and the k = 0 slice:
  * the plan can then neither be re-tabulated nor switch precision, and
  * fbc_get_mode_table fails.  s == NULL detaches (refused once tables were

@@ -8,7 +8,7 @@ writes out, as plainly as numpy allows, the network the library's surrogate
 evaluates, so that the CUDA forward pass, loss and gradients can be compared
 with it element by element:
 
-* ``features``  -- x = (q r / 32, d_x / r, d_y / r, ln(r) / 5) with
+* ``features``  -- x = (ln(q r) / 4, d_x / r, d_y / r, ln(r) / 5) with
                    r = |d| and q = 2 pi k / (L c), the wavenumber of mode k of
                    the line DFT (Sec. 3.2, Eqs. 37-38).
 * ``scale``     -- s(q, r) = exp(-q r) / (c sqrt(1 + q r)), zero beyond
@@ -100,7 +100,7 @@ def features(d, k, L: int, c: float = 1.0) -> np.ndarray:
     k = np.asarray(k, dtype=np.float64).reshape(-1)
     r = np.hypot(d[:, 0], d[:, 1])
     qr = 2.0 * np.pi * k / (L * c) * r
-    return np.stack([qr / 32.0, d[:, 0] / r, d[:, 1] / r, np.log(r) / 5.0], axis=1)
+    return np.stack([np.log(qr) / 4.0, d[:, 0] / r, d[:, 1] / r, np.log(r) / 5.0], axis=1)
 
 
 def scale(d, k, L: int, c: float = 1.0) -> np.ndarray:

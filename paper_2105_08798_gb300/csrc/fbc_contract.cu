@@ -37,7 +37,7 @@ __device__ __forceinline__ void tile_fp64(const ContractArgs& A, int tA, int k, 
     const int4 bA = A.bbox_a[tA];
     double acc0 = 0, acc1 = 0, acc2 = 0, acc3 = 0, acc4 = 0, acc5 = 0;
     const double* fk = A.fh + ((size_t)r * A.K + k) * A.NIpad * 6;
-    const double* tk = A.tab + (size_t)(k * A.kmul) * A.Dy * A.Dx * 6;
+    const double* tk = A.tab + (size_t)(k - A.kbase) * A.Dy * A.Dx * 6;
     for (int tB = 0; tB < A.n_tb; tB++) {
         const int4 bB = A.bbox_b[tB];
         const int ox = bA.x - bB.y, oy = bA.z - bB.w;
@@ -89,7 +89,7 @@ __device__ __forceinline__ void tile_fp32(const ContractArgs& A, int tA, int k, 
     const int4 bA = A.bbox_a[tA];
     float acc0 = 0, acc1 = 0, acc2 = 0, acc3 = 0, acc4 = 0, acc5 = 0;
     const double* fk = A.fh + ((size_t)r * A.K + k) * A.NIpad * 6;
-    const float* tk = A.tab32 + (size_t)(k * A.kmul) * A.Dy * A.Dx * 6;
+    const float* tk = A.tab32 + (size_t)(k - A.kbase) * A.Dy * A.Dx * 6;
     for (int tB = 0; tB < A.n_tb; tB++) {
         const int4 bB = A.bbox_b[tB];
         const int ox = bA.x - bB.y, oy = bA.z - bB.w;
@@ -152,7 +152,7 @@ __device__ __forceinline__ void tile_fp32_rb(const ContractArgs& A, int tA, int 
     for (int q = 0; q < RB; q++)
 #pragma unroll
         for (int c = 0; c < 6; c++) acc[q][c] = 0.f;
-    const float* tk = A.tab32 + (size_t)(k * A.kmul) * A.Dy * A.Dx * 6;
+    const float* tk = A.tab32 + (size_t)(k - A.kbase) * A.Dy * A.Dx * 6;
     for (int tB = 0; tB < A.n_tb; tB++) {
         const int4 bB = A.bbox_b[tB];
         const int ox = bA.x - bB.y, oy = bA.z - bB.w;
@@ -261,7 +261,7 @@ __device__ __forceinline__ void tile_x2(const ContractArgs& A, int tA, int k, in
     const int4 bA = A.bbox_a[tA];
     float Th[6] = {0, 0, 0, 0, 0, 0}, Tl[6] = {0, 0, 0, 0, 0, 0};
     const double* fk = A.fh + ((size_t)r * A.K + k) * A.NIpad * 6;
-    const float* tk = A.tabx2 + (size_t)(k * A.kmul) * A.Dy * A.Dx * 12;
+    const float* tk = A.tabx2 + (size_t)(k - A.kbase) * A.Dy * A.Dx * 12;
     for (int tB = 0; tB < A.n_tb; tB++) {
         const int4 bB = A.bbox_b[tB];
         const int ox = bA.x - bB.y, oy = bA.z - bB.w;
@@ -444,7 +444,7 @@ ContractArgs make_contract_args(const Plan& P) {
     A.fh = P.d_fh, A.uh = P.d_uh, A.xy_p = P.d_xy_p, A.off_i = P.d_off_i;
     A.bbox_a = P.d_bbox_a, A.bbox_b = P.d_bbox_b;
     A.n_tb = P.n_tb, A.K = P.K, A.Dx = P.Dx, A.Dy = P.Dy, A.box_x0 = P.box_x0, A.box_y0 = P.box_y0;
-    A.W = P.W, A.H = P.H, A.NIpad = P.NIpad, A.NPpad = P.NPpad, A.k0 = 0, A.kmul = 1;
+    A.W = P.W, A.H = P.H, A.NIpad = P.NIpad, A.NPpad = P.NPpad, A.k0 = 0, A.kbase = 0;
     return A;
 }
 

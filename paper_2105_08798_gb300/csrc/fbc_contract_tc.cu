@@ -29,6 +29,7 @@
 #include <cuda_bf16.h>
 
 #include "fbc_internal.cuh"
+#include "fbc_tc.cuh"
 
 namespace fbc {
 namespace {
@@ -36,28 +37,10 @@ namespace {
 constexpr int kTmemCols = 512;
 constexpr int kMaxNP = 128;      // 64 right-hand sides x (x, y')
 constexpr int kRhsPerCta = 64;
-constexpr int kWaitLimit = 1 << 24;
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-// Shared-memory matrix descriptor: start address, leading (K-direction core
-// matrix) byte offset, stride (8-row group) byte offset, fixed version bits,
-// no swizzle.
-__device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
-    uint64_t d = 0;
-    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
-    d |= (uint64_t)((lbo & 0x3FFFFu) >> 4) << 16;
-    d |= (uint64_t)((sbo & 0x3FFFFu) >> 4) << 32;
-    d |= (uint64_t)1 << 46;
-    return d;
-}
-
-// Instruction descriptor: FP32 accumulator, A/B format (1 = bf16, 2 = tf32),
-// both K-major, N >> 3 and M >> 4.
-__device__ __forceinline__ uint32_t idesc(int fmt, int M, int N) {
-    return (1u << 4) | ((uint32_t)fmt << 7) | ((uint32_t)fmt << 10) | ((uint32_t)(N >> 3) << 17) |
-           ((uint32_t)(M >> 4) << 24);
-}
+using tc::idesc;
+using tc::mbar_wait;
+using tc::sdesc;
+using tc::smem_u32;
 
 template <int PREC>
 struct TcCfg;
@@ -117,19 +100,6 @@ __device__ __forceinline__ uint4 pack16(const uint32_t (&w)[KPC]) {
     return v;
 }
 
-__device__ __forceinline__ bool mbar_wait(uint64_t* m, uint32_t phase) {
-    for (int it = 0; it < kWaitLimit; it++) {
-        uint32_t ok;
-        asm volatile(
-            "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
-            : "=r"(ok)
-            : "r"(smem_u32(m)), "r"(phase)
-            : "memory");
-        if (ok) return true;
-    }
-    return false;
-}
-
 template <int PREC>
 __global__ void __launch_bounds__(kTileA, 1) k_contract_tc(ContractArgs A, int n_rhs, int* status) {
     using C = TcCfg<PREC>;
@@ -159,7 +129,7 @@ __global__ void __launch_bounds__(kTileA, 1) k_contract_tc(ContractArgs A, int n
     const int a = tA * TA + a_loc;
     const int2 xa = A.xy_p[a];
     const int4 bA = A.bbox_a[tA];
-    const float* tk = A.tab32 + (size_t)(k * A.kmul) * A.Dy * A.Dx * 6;
+    const float* tk = A.tab32 + (size_t)(k - A.kbase) * A.Dy * A.Dx * 6;
 
     if (threadIdx.x == 0) {
         s_abort = 0;

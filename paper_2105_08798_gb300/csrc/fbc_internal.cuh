@@ -98,10 +98,8 @@ struct Plan {
     int2* d_far = nullptr;
     int2* d_near = nullptr;
     float* d_near32 = nullptr;   // [K][n_near][6] exact entries of the near field
-    float* d_slice = nullptr;    // [Dy][Dx][6] one streamed mode slice (FP32)
-    float* d_sX = nullptr;       // [n_far][4] network inputs
-    float* d_sY = nullptr;       // [n_far][6] network outputs
-    float* d_sact = nullptr;     // [6][n_far][width] hidden activations
+    float* d_slice = nullptr;    // [sur_chunk][Dy][Dx][6] streamed mode slices (FP32)
+    int sur_chunk = 0;           // modes per streamed chunk
     bool timing = false, timed_once = false;
     size_t table_bytes = 0, workspace_bytes = 0;
 };
@@ -118,7 +116,7 @@ struct ContractArgs {
     const int4* bbox_a;
     const int4* bbox_b;
     int n_tb, K, Dx, Dy, box_x0, box_y0, W, H, NIpad, NPpad, k0;
-    int kmul;  // 1: the tables hold K mode slices; 0: one streamed slice serves the mode being contracted
+    int kbase;  // the tables hold mode slices kbase, kbase + 1, ... (0: all K; else a streamed chunk)
 };
 
 // Everything the line transforms need about one plan (one instance of a batch).
@@ -146,8 +144,6 @@ cudaError_t launch_contract_tc(const ContractArgs& A, const Plan& P, int n_rhs, 
 // contraction of modes k0 .. k0 + n_modes - 1 in the plan's precision (k0 >= 1 for the FP32 and tensor forms)
 cudaError_t launch_contract_modes(Plan& P, const ContractArgs& A, int k0, int n_modes, int n_rhs, cudaStream_t st);
 cudaError_t launch_contract_x2_k0(Plan& P, const ContractArgs& A, int n_rhs, cudaStream_t st);
-cudaError_t surrogate_forward(const fbc_surrogate* S, const float* params, const float* X, int n, float* Y, float* act,
-                              int cap, cudaStream_t st);
 // streamed contraction of a plan with an attached surrogate (modes k >= 1)
 cudaError_t launch_contract_streamed(Plan& P, int n_rhs, cudaStream_t st);
 void release_surrogate_buffers(Plan& P);
@@ -166,6 +162,48 @@ cudaError_t launch_batch_contract(int precision, int phase, const ContractArgs* 
                                   cudaStream_t st);
 size_t batch_contract_smem_phase(int precision, int phase, int W, int H);
 int batch_contract_occupancy_phase(int precision, int phase, size_t smem);
+
+// ---- learned surrogate of the mode table (fbc_surrogate.cu, fbc_mlp_tc.cu) ----
+constexpr int kSurIn = 4, kSurOut = 6;
+// beyond q r = kQrCut a k >= 1 entry is served as zero (and never trained on)
+constexpr double kQrCut = 16.0;
+
+// Network inputs of difference d (d != 0) at mode k >= 1:
+// (ln(q r) / 4, d_x / r, d_y / r, ln(r) / 5) with q = 2 pi k / (L c); returns q r.
+__host__ __device__ inline double surrogate_features(int dx, int dy, int k, int L, double c, float* x) {
+    const double r = sqrt((double)dx * dx + (double)dy * dy);
+    const double qr = 2.0 * 3.14159265358979323846 * k / (L * c) * r;
+    x[0] = (float)(log(qr) * 0.25);
+    x[1] = (float)(dx / r);
+    x[2] = (float)(dy / r);
+    x[3] = (float)(log(r) * 0.2);
+    return qr;
+}
+// s(q, r) = exp(-q r) / (c sqrt(1 + q r)), zero beyond the cut
+__host__ __device__ inline double surrogate_scale(double qr, double c) {
+    return qr > kQrCut ? 0.0 : exp(-qr) / (c * sqrt(1.0 + qr));
+}
+
+// Fused tensor-core inference (fbc_mlp_tc.cu).  Rows are either given as
+// features (X [n][4] -> Y [n][6]) or are the far differences at modes
+// k0 .. k0 + n_modes - 1, whose scaled outputs are written into mode slices.
+struct MlpArgs {
+    const float* params = nullptr;  // BF16-rounded weights in FP32 storage, packed as in fbc.h
+    int H = 0;
+    int off[8] = {};
+    int n = 0;                      // rows (per mode)
+    const float* X = nullptr;       // row mode
+    float* Y = nullptr;
+    const int2* far = nullptr;      // slice mode
+    int k0 = 0, n_modes = 1, L = 0;
+    double c = 1.0;
+    float* slice = nullptr;         // [n_modes][Dy][Dx][6]
+    int Dx = 0, box_x0 = 0, box_y0 = 0;
+    size_t slice_floats = 0;        // Dy * Dx * 6
+    int* status = nullptr;
+};
+bool mlp_tc_supported(int H);
+cudaError_t launch_mlp_tc(const MlpArgs& a, cudaStream_t st);
 
 // Record the message fbc_last_error() returns for this thread; returns code.
 int report_error(int code, const char* msg);

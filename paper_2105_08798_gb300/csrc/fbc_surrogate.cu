@@ -2,22 +2,28 @@
 //
 // A multilayer perceptron 4 -> H -> H -> H -> 6 with SiLU activations maps the
 // features of a (difference d, wavenumber k >= 1) pair,
-//     x = (q r / 32, d_x / r, d_y / r, ln(r) / 5),   r = |d|,  q = 2 pi k / (L c),
+//     x = (ln(q r) / 4, d_x / r, d_y / r, ln(r) / 5),   r = |d|,  q = 2 pi k / (L c),
 // to the six independent reals of g^k(d) (Re g11, Re g12, Re g22, Re g33,
 // Im g13, Im g23) divided by the smooth decay factor
 //     s(q, r) = exp(-q r) / (c sqrt(1 + q r)),
 // so that the targets are O(1) although the modes decay exponentially in q r.
+// The Green function is homogeneous of degree -1, so for r well beyond the
+// lattice spacing the mode entry depends on q r and the direction of d only
+// (lattice corrections fall off like exp(-2 pi r / c)); ln(q r) makes the
+// logarithm of the small-q r regime a linear function of an input.
 // It is trained on the plan's own exact FP64 table (the tables the method
 // itself generates) by the kernels of this file: a tiled FP32 GEMM used for
 // the forward pass and both backward products, SiLU and its derivative, the
 // mean-squared loss, bias reductions and Adam.  For inference the weights are
-// rounded to bf16 values and the products accumulate in FP32.
+// rounded to bf16 values and the products accumulate in FP32 (fused
+// tensor-core kernel in fbc_mlp_tc.cu).
 //
 // Use in the pad update: a plan in a CUDA-core FP32 or tensor-core precision
-// can stream its table one mode at a time: for each k >= 1 a slice
-// [Dy][Dx][6] is assembled from the exact table for |d| < r_min (near field)
-// and from the network for |d| >= r_min, and the contraction of that mode
-// reads the slice, so only one slice (not K of them) is resident.
+// streams its table a chunk of modes at a time: for modes k0 .. k0 + m - 1 the
+// slices [m][Dy][Dx][6] are assembled from a compact exact copy for
+// |d| < r_min (near field) and by the fused network for |d| >= r_min, and one
+// contraction launch over those m modes reads them while they sit in L2; the
+// K-slice tables need not exist.
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -43,15 +49,10 @@ struct fbc_surrogate {
     int cap = 0;
     float* d_act = nullptr;    // Z1 A1 Z2 A2 Z3 A3 (cap x H each), Y, dY (cap x 6), T, B0, B1 (cap x H)
     double* d_loss = nullptr;
+    int* d_status = nullptr;   // error word of the fused inference kernel
 };
 
 namespace fbc {
-
-// Beyond q r = kQrCut an entry of mode k >= 1 is below exp(-16) ~ 1e-7 of its
-// value at q r -> 0 and, after the roundoff the Richardson weights amplify,
-// no longer carries a trustworthy FP64 value: the surrogate serves it as zero
-// and is trained only below the cut.
-constexpr double kQrCut = 16.0;
 namespace {
 
 constexpr int kOut = 6;
@@ -173,55 +174,25 @@ __global__ void k_samples(const int2* __restrict__ used, const int* __restrict__
     if (i >= n) return;
     const int2 d = used[s_d[i]];
     const int k = s_k[i];
-    const double r = sqrt((double)d.x * d.x + (double)d.y * d.y);
-    const double q = 2.0 * M_PI * k / (L * c);
-    const double qr = q * r;
-    X[i * 4 + 0] = (float)(qr / 32.0);
-    X[i * 4 + 1] = (float)(d.x / r);
-    X[i * 4 + 2] = (float)(d.y / r);
-    X[i * 4 + 3] = (float)(log(r) / 5.0);
-    if (T) {
-        const double inv_s = c * sqrt(1.0 + qr) * exp(qr);
-        const double* src = table + (((size_t)k * Dy + (d.y - box_y0)) * Dx + (d.x - box_x0)) * 6;
-        for (int j = 0; j < 6; j++) T[i * 6 + j] = (float)(src[j] * inv_s);
-    }
+    const double qr = surrogate_features(d.x, d.y, k, L, c, X + (size_t)i * kSurIn);
+    const double inv_s = 1.0 / surrogate_scale(qr, c);
+    const double* src = table + (((size_t)k * Dy + (d.y - box_y0)) * Dx + (d.x - box_x0)) * 6;
+    for (int j = 0; j < 6; j++) T[(size_t)i * 6 + j] = (float)(src[j] * inv_s);
 }
 
-// Features of every far difference (|d| >= r_min) at one k, for a streamed slice.
-__global__ void k_slice_features(const int2* __restrict__ far, int n, int k, int L, double c, float* __restrict__ X) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const int2 d = far[i];
-    const double r = sqrt((double)d.x * d.x + (double)d.y * d.y);
-    const double qr = 2.0 * M_PI * k / (L * c) * r;
-    X[i * 4 + 0] = (float)(qr / 32.0);
-    X[i * 4 + 1] = (float)(d.x / r);
-    X[i * 4 + 2] = (float)(d.y / r);
-    X[i * 4 + 3] = (float)(log(r) / 5.0);
-}
-
-// Slice assembly: far entries from the network output (times the decay
-// factor), near entries copied from the exact FP32 table.
-__global__ void k_slice_far(const int2* __restrict__ far, int n, int k, int L, double c, const float* __restrict__ Y,
-                            float* __restrict__ slice, int Dx, int box_x0, int box_y0) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const int2 d = far[i];
-    const double r = sqrt((double)d.x * d.x + (double)d.y * d.y);
-    const double qr = 2.0 * M_PI * k / (L * c) * r;
-    const double s = qr > kQrCut ? 0.0 : exp(-qr) / (c * sqrt(1.0 + qr));
-    float* o = slice + ((size_t)(d.y - box_y0) * Dx + (d.x - box_x0)) * 6;
-    for (int j = 0; j < 6; j++) o[j] = (float)(Y[i * 6 + j] * s);
-}
-__global__ void k_slice_near(const int2* __restrict__ near, int n, int k, const float* __restrict__ near32, int Dx,
-                             int box_x0, int box_y0, float* __restrict__ slice) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
+// Near entries of modes kbase .. kbase + n_modes - 1 copied into their slices
+// from the compact exact table.
+__global__ void k_slice_near(const int2* __restrict__ near, int n, int kbase, int n_modes,
+                             const float* __restrict__ near32, int Dx, int box_x0, int box_y0, size_t slice_floats,
+                             float* __restrict__ slice) {
+    const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (size_t)n * n_modes) return;
+    const int j = (int)(t / n), i = (int)(t % n);
     const int2 d = near[i];
     const size_t cell = (size_t)(d.y - box_y0) * Dx + (d.x - box_x0);
-    const float* src = near32 + ((size_t)k * n + i) * 6;
-    float* o = slice + cell * 6;
-    for (int j = 0; j < 6; j++) o[j] = src[j];
+    const float* src = near32 + ((size_t)(kbase + j) * n + i) * 6;
+    float* o = slice + (size_t)j * slice_floats + cell * 6;
+    for (int e = 0; e < 6; e++) o[e] = src[e];
 }
 // compact exact near-field table: near32[k][i] = FP32 of table[k][near[i]]
 __global__ void k_near_gather(const int2* __restrict__ near, int n, int K, const double* __restrict__ table, int Dx,
@@ -260,36 +231,49 @@ cudaError_t surrogate_forward(const fbc_surrogate* S, const float* params, const
     return cudaGetLastError();
 }
 
+MlpArgs mlp_args(const fbc_surrogate* S, const float* params, int* status) {
+    MlpArgs a;
+    a.params = params;
+    a.H = S->width;
+    for (int t = 0; t < 8; t++) a.off[t] = S->off[t];
+    a.status = status;
+    return a;
+}
+
 cudaError_t launch_contract_streamed(Plan& P, int n_rhs, cudaStream_t st) {
     const fbc_surrogate* S = P.sur;
     ContractArgs A = make_contract_args(P);
     A.tab32 = P.d_slice;
-    A.kmul = 0;
+    MlpArgs m = mlp_args(S, S->d_pb, P.d_status);
+    m.far = P.d_far, m.n = P.n_far, m.L = P.L, m.c = P.c;
+    m.slice = P.d_slice, m.Dx = P.Dx, m.box_x0 = P.box_x0, m.box_y0 = P.box_y0;
+    m.slice_floats = (size_t)P.Dy * P.Dx * 6;
     cudaError_t e = cudaSuccess;
-    const int bs = 256;
-    for (int k = 1; k < P.K && !e; k++) {
+    for (int k0 = 1; k0 < P.K && !e; k0 += P.sur_chunk) {
+        const int nm = std::min(P.sur_chunk, P.K - k0);
         if (P.n_far) {
-            k_slice_features<<<(P.n_far + bs - 1) / bs, bs, 0, st>>>(P.d_far, P.n_far, k, P.L, P.c, P.d_sX);
-            if ((e = surrogate_forward(S, S->d_pb, P.d_sX, P.n_far, P.d_sY, P.d_sact, P.n_far, st))) break;
-            k_slice_far<<<(P.n_far + bs - 1) / bs, bs, 0, st>>>(P.d_far, P.n_far, k, P.L, P.c, P.d_sY, P.d_slice, P.Dx,
-                                                                  P.box_x0, P.box_y0);
+            m.k0 = k0, m.n_modes = nm;
+            if ((e = launch_mlp_tc(m, st))) break;
         }
-        if (P.n_near)
-            k_slice_near<<<(P.n_near + bs - 1) / bs, bs, 0, st>>>(P.d_near, P.n_near, k, P.d_near32, P.Dx, P.box_x0,
-                                                                    P.box_y0, P.d_slice);
+        if (P.n_near) {
+            const size_t t = (size_t)P.n_near * nm;
+            k_slice_near<<<(unsigned)((t + 255) / 256), 256, 0, st>>>(P.d_near, P.n_near, k0, nm, P.d_near32, P.Dx,
+                                                                      P.box_x0, P.box_y0, m.slice_floats, P.d_slice);
+        }
         if ((e = cudaGetLastError())) break;
-        e = launch_contract_modes(P, A, k, 1, n_rhs, st);
+        A.kbase = k0;
+        e = launch_contract_modes(P, A, k0, nm, n_rhs, st);
     }
     return e;
 }
 
 void release_surrogate_buffers(Plan& P) {
-    void* bufs[] = {P.d_far, P.d_near, P.d_near32, P.d_slice, P.d_sX, P.d_sY, P.d_sact};
+    void* bufs[] = {P.d_far, P.d_near, P.d_near32, P.d_slice};
     for (void* b : bufs)
         if (b) cudaFree(b);
     P.d_far = P.d_near = nullptr;
-    P.d_near32 = P.d_slice = P.d_sX = P.d_sY = P.d_sact = nullptr;
-    P.n_far = P.n_near = 0;
+    P.d_near32 = P.d_slice = nullptr;
+    P.n_far = P.n_near = P.sur_chunk = 0;
     P.sur_bytes = 0;
 }
 
@@ -398,6 +382,8 @@ int fbc_surrogate_create(int32_t width, uint64_t seed, fbc_surrogate** out) {
     for (auto b : bufs)
         if (!e) e = cudaMalloc((void**)b, sizeof(float) * o);
     if (!e) e = cudaMalloc((void**)&S->d_loss, 64 * sizeof(double));
+    if (!e) e = cudaMalloc((void**)&S->d_status, sizeof(int));
+    if (!e) e = cudaMemset(S->d_status, 0, sizeof(int));
     if (!e) e = cudaMemcpy(S->d_p, p.data(), sizeof(float) * o, cudaMemcpyHostToDevice);
     if (!e) e = cudaMemset(S->d_m, 0, sizeof(float) * o);
     if (!e) e = cudaMemset(S->d_v, 0, sizeof(float) * o);
@@ -431,6 +417,12 @@ int fbc_surrogate_forward(fbc_surrogate* S, const float* x, float* y, int32_t n,
     if (bf16_weights) {
         fbc::k_round_bf16<<<fbc::grid_for(S->n_params), 256, 0, st>>>(S->d_p, S->d_pb, S->n_params);
         params = S->d_pb;
+        if (fbc::mlp_tc_supported(S->width)) {
+            fbc::MlpArgs m = fbc::mlp_args(S, params, S->d_status);
+            m.n = n, m.X = x, m.Y = y;
+            cudaError_t e = fbc::launch_mlp_tc(m, st);
+            return e ? scuda(e, "fused surrogate inference") : FBC_OK;
+        }
     }
     cudaError_t e = fbc::surrogate_forward(S, params, x, n, y, S->d_act, S->cap, st);
     return e ? scuda(e, "surrogate forward") : FBC_OK;
@@ -468,19 +460,26 @@ int fbc_surrogate_train(fbc_surrogate* S, const fbc_plan* plan, int32_t n_sample
     for (int i = 0; i < P.n_used; i++)
         if ((double)used[i].x * used[i].x + (double)used[i].y * used[i].y >= r_min * r_min) far.push_back(i);
     if (far.empty()) return sfail(FBC_ERR_INVALID_ARG, "no differences at or beyond r_min");
-    // (d, k) uniform over the far differences and the modes with q r <= cut
+    // d uniform over the far differences that have a mode below the q r cut;
+    // k log-uniform over 1 .. kmax(d) (the modes with q r <= cut), which puts
+    // as many samples in each octave of q r as the small-q r entries, the
+    // largest ones, need
     const double q1 = 2.0 * M_PI / (P.L * P.c);
-    double r_far_min = 1e300;
-    for (int i : far) r_far_min = std::min(r_far_min, std::sqrt((double)used[i].x * used[i].x + (double)used[i].y * used[i].y));
-    if (q1 * r_far_min > fbc::kQrCut) return sfail(FBC_ERR_INVALID_ARG, "every far pair is beyond the q r cut");
+    std::vector<int> far_ok;
+    std::vector<int> kmax;
+    for (int i : far) {
+        const double r = std::sqrt((double)used[i].x * used[i].x + (double)used[i].y * used[i].y);
+        const int km = std::min(P.K - 1, (int)std::floor(fbc::kQrCut / (q1 * r)));
+        if (km >= 1) far_ok.push_back(i), kmax.push_back(km);
+    }
+    if (far_ok.empty()) return sfail(FBC_ERR_INVALID_ARG, "every far pair is beyond the q r cut");
     std::mt19937_64 rng(seed);
+    std::uniform_real_distribution<double> u01(0.0, 1.0);
     std::vector<int> sd(n_samples), sk(n_samples);
-    for (int i = 0; i < n_samples;) {
-        const int di = far[rng() % far.size()];
-        const int k = 1 + (int)(rng() % (uint64_t)(P.K - 1));
-        const double r = std::sqrt((double)used[di].x * used[di].x + (double)used[di].y * used[di].y);
-        if (q1 * k * r > fbc::kQrCut) continue;
-        sd[i] = di, sk[i] = k, i++;
+    for (int i = 0; i < n_samples; i++) {
+        const size_t j = rng() % far_ok.size();
+        const int k = (int)std::floor(std::exp(u01(rng) * std::log(kmax[j] + 1.0)));
+        sd[i] = far_ok[j], sk[i] = std::min(std::max(k, 1), kmax[j]);
     }
     cudaStream_t st = (cudaStream_t)stream;
     int *d_sd = nullptr, *d_sk = nullptr;
@@ -531,14 +530,14 @@ int fbc_surrogate_eval_table(fbc_surrogate* S, const fbc_plan* plan, const int32
     fbc::report_error(FBC_OK, "");
     if (!S || !plan || !d || !k || !out || n < 1) return sfail(FBC_ERR_INVALID_ARG, "bad arguments");
     const fbc::Plan& P = plan->p;
-    // features on the host (same formula as the device kernels), network on the device
+    // features on the host (the function the device kernels use), network on the device
     std::vector<float> X(4 * (size_t)n);
+    std::vector<double> sc(n);
     for (int i = 0; i < n; i++) {
-        const double r = std::sqrt((double)d[2 * i] * d[2 * i] + (double)d[2 * i + 1] * d[2 * i + 1]);
-        if (!(r > 0.0) || k[i] < 1 || k[i] >= P.K) return sfail(FBC_ERR_INVALID_ARG, "need d != 0 and 1 <= k < K");
-        const double qr = 2.0 * M_PI * k[i] / (P.L * P.c) * r;
-        X[4 * i + 0] = (float)(qr / 32.0), X[4 * i + 1] = (float)(d[2 * i] / r), X[4 * i + 2] = (float)(d[2 * i + 1] / r);
-        X[4 * i + 3] = (float)(std::log(r) / 5.0);
+        if ((d[2 * i] == 0 && d[2 * i + 1] == 0) || k[i] < 1 || k[i] >= P.K)
+            return sfail(FBC_ERR_INVALID_ARG, "need d != 0 and 1 <= k < K");
+        sc[i] = fbc::surrogate_scale(fbc::surrogate_features(d[2 * i], d[2 * i + 1], k[i], P.L, P.c, &X[4 * (size_t)i]),
+                                     P.c);
     }
     float *d_X = nullptr, *d_Y = nullptr;
     cudaError_t e = cudaMalloc((void**)&d_X, sizeof(float) * 4 * (size_t)n);
@@ -552,12 +551,13 @@ int fbc_surrogate_eval_table(fbc_surrogate* S, const fbc_plan* plan, const int32
     }
     cudaFree(d_X), cudaFree(d_Y);
     if (s) return s;
-    for (int i = 0; i < n; i++) {
-        const double r = std::sqrt((double)d[2 * i] * d[2 * i] + (double)d[2 * i + 1] * d[2 * i + 1]);
-        const double qr = 2.0 * M_PI * k[i] / (P.L * P.c) * r;
-        const double sc = qr > fbc::kQrCut ? 0.0 : std::exp(-qr) / (P.c * std::sqrt(1.0 + qr));
-        for (int j = 0; j < 6; j++) out[6 * (size_t)i + j] = Y[6 * (size_t)i + j] * sc;
+    int st = 0;
+    if (cudaMemcpy(&st, S->d_status, sizeof(int), cudaMemcpyDeviceToHost) == cudaSuccess && st) {
+        cudaMemset(S->d_status, 0, sizeof(int));
+        return sfail(st, "fused surrogate inference timed out");
     }
+    for (int i = 0; i < n; i++)
+        for (int j = 0; j < 6; j++) out[6 * (size_t)i + j] = Y[6 * (size_t)i + j] * sc[i];
     return FBC_OK;
 }
 
@@ -577,6 +577,8 @@ int fbc_plan_attach_surrogate(fbc_plan* plan, fbc_surrogate* S, double r_min, in
     if (!(r_min > 0.0)) return sfail(FBC_ERR_INVALID_ARG, "r_min must be positive");
     if (P.precision != FBC_PREC_FP32 && !fbc::is_tensor_precision(P.precision))
         return sfail(FBC_ERR_UNSUPPORTED, "the surrogate serves the FP32 and tensor-core precisions");
+    if (!fbc::mlp_tc_supported(S->width))
+        return sfail(FBC_ERR_UNSUPPORTED, "the fused inference kernel takes widths 32, 64, 96 and 128");
     cudaDeviceSynchronize();
     fbc::release_surrogate_buffers(P);
     std::vector<int2> used(P.n_used), far, near;
@@ -586,6 +588,11 @@ int fbc_plan_attach_surrogate(fbc_plan* plan, fbc_surrogate* S, double r_min, in
     if (far.size() > (size_t)kMaxRows) return sfail(FBC_ERR_UNSUPPORTED, "more than 65535 * 64 far differences");
     P.n_far = (int)far.size(), P.n_near = (int)near.size();
     const size_t cells = (size_t)P.Dy * P.Dx;
+    // modes per chunk: their slices (about 48 MB together) stay in L2 between
+    // the network that writes them and the contraction that reads them
+    const size_t slice_bytes = cells * 6 * sizeof(float);
+    const int chunk = (int)std::max<size_t>(1, std::min<size_t>({(size_t)32, (size_t)std::max(1, P.K - 1),
+                                                                  ((size_t)48 << 20) / slice_bytes}));
     size_t bytes_total = 0;
     auto A = [&](void** p, size_t bytes) {
         bytes = std::max<size_t>(bytes, 16);
@@ -595,14 +602,11 @@ int fbc_plan_attach_surrogate(fbc_plan* plan, fbc_surrogate* S, double r_min, in
     A((void**)&P.d_far, sizeof(int2) * far.size());
     A((void**)&P.d_near, sizeof(int2) * near.size());
     A((void**)&P.d_near32, sizeof(float) * 6 * near.size() * P.K);
-    A((void**)&P.d_slice, sizeof(float) * 6 * cells);
-    A((void**)&P.d_sX, sizeof(float) * 4 * far.size());
-    A((void**)&P.d_sY, sizeof(float) * 6 * far.size());
-    A((void**)&P.d_sact, sizeof(float) * 6 * far.size() * S->width);
+    A((void**)&P.d_slice, slice_bytes * chunk);
     if (!e && !far.empty()) e = cudaMemcpy(P.d_far, far.data(), sizeof(int2) * far.size(), cudaMemcpyHostToDevice);
     if (!e && !near.empty()) e = cudaMemcpy(P.d_near, near.data(), sizeof(int2) * near.size(), cudaMemcpyHostToDevice);
     // cells no pair reads stay zero (padding columns multiply them by zero forces)
-    if (!e) e = cudaMemset(P.d_slice, 0, sizeof(float) * 6 * cells);
+    if (!e) e = cudaMemset(P.d_slice, 0, slice_bytes * chunk);
     if (!e && !near.empty()) {
         const size_t t = (size_t)near.size() * P.K;
         fbc::k_near_gather<<<(unsigned)((t + 255) / 256), 256>>>(P.d_near, (int)near.size(), P.K, P.d_table, P.Dx, P.Dy,
@@ -620,6 +624,7 @@ int fbc_plan_attach_surrogate(fbc_plan* plan, fbc_surrogate* S, double r_min, in
     }
     P.sur = S;
     P.sur_rmin = r_min;
+    P.sur_chunk = chunk;
     P.sur_bytes = bytes_total;
     if (release_tables) {
         // the k = 0 double-float slice stays; the K-slice tables go
@@ -633,9 +638,23 @@ int fbc_plan_attach_surrogate(fbc_plan* plan, fbc_surrogate* S, double r_min, in
     return FBC_OK;
 }
 
+int fbc_surrogate_sync_status(fbc_surrogate* S, void* stream) {
+    fbc::report_error(FBC_OK, "");
+    if (!S) return sfail(FBC_ERR_INVALID_ARG, "surrogate is NULL");
+    int st = 0;
+    cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+    if (!e) e = cudaMemcpy(&st, S->d_status, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e) return scuda(e, "surrogate status");
+    if (st) {
+        cudaMemset(S->d_status, 0, sizeof(int));
+        return sfail(st, "fused surrogate inference timed out");
+    }
+    return FBC_OK;
+}
+
 void fbc_surrogate_destroy(fbc_surrogate* S) {
     if (!S) return;
-    void* bufs[] = {S->d_p, S->d_pb, S->d_g, S->d_m, S->d_v, S->d_act, S->d_loss};
+    void* bufs[] = {S->d_p, S->d_pb, S->d_g, S->d_m, S->d_v, S->d_act, S->d_loss, S->d_status};
     for (void* b : bufs)
         if (b) cudaFree(b);
     delete S;

@@ -131,6 +131,7 @@ _SIGNATURES = {
     "fbc_surrogate_eval_table": (ctypes.c_int, [_vp, _vp, _P(ctypes.c_int32), _P(ctypes.c_int32), ctypes.c_int32,
                                                 _P(ctypes.c_double)]),
     "fbc_plan_attach_surrogate": (ctypes.c_int, [_vp, _vp, ctypes.c_double, ctypes.c_int32]),
+    "fbc_surrogate_sync_status": (ctypes.c_int, [_vp, _vp]),
     "fbc_surrogate_destroy": (None, [_vp]),
 }
 
@@ -340,6 +341,10 @@ def fbc_plan_attach_surrogate(plan: int, sur: int | None, r_min: float, release_
     _check(load().fbc_plan_attach_surrogate(plan, sur, r_min, int(release_tables)), "fbc_plan_attach_surrogate")
 
 
+def fbc_surrogate_sync_status(sur: int, stream=None):
+    _check(load().fbc_surrogate_sync_status(sur, _stream_handle(stream)), "fbc_surrogate_sync_status")
+
+
 def fbc_surrogate_destroy(sur: int):
     load().fbc_surrogate_destroy(sur)
 
@@ -522,6 +527,9 @@ class Surrogate:
     def train(self, plan: Plan, n_samples: int = 1 << 20, r_min: float = 8.0, epochs: int = 50, batch: int = 4096,
               lr: float = 2e-3, seed: int = 0) -> float:
         return fbc_surrogate_train(self.handle, plan.handle, n_samples, r_min, epochs, batch, lr, seed)
+
+    def sync_status(self, stream=None):
+        fbc_surrogate_sync_status(self.handle, stream)
 
     def table(self, plan: Plan, d, k) -> np.ndarray:
         return fbc_surrogate_eval_table(self.handle, plan.handle, d, k)

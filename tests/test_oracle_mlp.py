@@ -61,7 +61,7 @@ def test_features_and_scale():
     k = np.array([2, 1])
     x = mlp.features(d, k, L=64, c=2.0)
     q0 = 2 * np.pi * 2 / (64 * 2.0) * 5
-    np.testing.assert_allclose(x[0], [q0 / 32, 0.6, 0.8, np.log(5) / 5], rtol=1e-15)
+    np.testing.assert_allclose(x[0], [np.log(q0) / 4, 0.6, 0.8, np.log(5) / 5], rtol=1e-15)
     np.testing.assert_allclose(x[1, 1:], [-1.0, 0.0, np.log(8) / 5], rtol=1e-15)
     s = mlp.scale(d, k, L=64, c=2.0)
     assert s[0] == pytest.approx(np.exp(-q0) / (2.0 * np.sqrt(1 + q0)), rel=1e-15)
