@@ -36,7 +36,7 @@ WORKLOAD = "ring4000x6000_L256_cubic"
 METRIC = "FBC pad updates/sec (Gpair-modes/s) at stated error vs FP64 oracle; roofline fraction"
 UNIT = "Gpair-modes/s"
 FLOPS_PER_PAIR_MODE = 36  # two real 3x3 matrix-vector products (x and y' halves)
-X2_FLOPS_PER_MAC = 15     # double-float MAC: 1 FMUL + 3 FFMA (2 flops each) + 8 FADD
+X2_INSTR_PER_MAC = 12     # double-float MAC: 1 FMUL + 3 FFMA + 8 FADD (each one FP32-pipe lane slot)
 L2_BYTES = 129 * 1024 * 1024
 
 
@@ -46,12 +46,13 @@ def peaks():
     if os.path.exists(path):
         with open(path) as fh:
             m = json.load(fh)
-        out.update({k: m[k] for k in ("hbm_gbs", "bf16_tflops", "sm_max_mhz") if k in m})
+        out.update({k: m[k] for k in ("hbm_gbs", "bf16_tflops", "bf16_tflops_sustained", "sm_max_mhz") if k in m})
         out["source"] = "measured"
     # plain-ALU peaks from unit counts and the maximum SM clock: 152 SMs,
     # 128 FP32 FMA lanes per SM per clock; FP64 at the GB300 nominal 1.25 TFLOP/s
     clk = out["sm_max_mhz"] * 1e6
     out["fp32_tflops"] = 152 * 128 * 2 * clk / 1e12
+    out["fp32_tinstr"] = 152 * 128 * clk / 1e12
     out["fp64_tflops"] = 1.25 * clk / 2.07e9
     return out
 
@@ -145,7 +146,7 @@ def run_reference(args, w):
     if rank != 0:
         return 0
     xy_i, xy_p = w.geometry()
-    f = w.forces()
+    f = w.forces()[:1]  # one right-hand side per sampled step; extrapolated over all of them below
     samples, fp, d_index, table, samp_col, samp_p, t_table = oracle_sample(w, xy_i, xy_p, f)
     for _ in range(args.warmup):
         oracle.real_space_sum(d_index, table, fp, samp_col, samp_p)
@@ -153,19 +154,21 @@ def run_reference(args, w):
     for _ in range(args.steps):
         oracle.real_space_sum(d_index, table, fp, samp_col, samp_p)
     dt = (time.perf_counter() - t0) / args.steps
-    # extrapolate one sampled step (len(samples) pad atoms) to the whole update (N_P L pad atoms)
-    t_full = dt * (w.n_p * w.L) / len(samples)
+    # extrapolate one sampled step (len(samples) pad atoms, one right-hand side) to the whole update
+    # (N_P L pad atoms for each of the n_rhs right-hand sides)
+    t_full = dt * (w.n_p * w.L * w.n_rhs) / len(samples)
     value = w.pair_modes / t_full / 1e9
     info = oracle.sys_info()
-    sample = (f"{len(samples)} pad atoms (all {w.L} repeats of 1 pad column) per step, full real-space sum over "
-              f"{w.n_i} x {w.L} interface atoms; extrapolated x{w.n_p * w.L // len(samples)} to the whole update; "
+    sample = (f"{len(samples)} pad atoms (all {w.L} repeats of 1 pad column, 1 right-hand side) per step, full "
+              f"real-space sum over {w.n_i} x {w.L} interface atoms; extrapolated "
+              f"x{w.n_p * w.L * w.n_rhs // len(samples)} to the whole update; "
               f"kernel tabulation for the sample ({t_table:.1f} s) is setup and untimed")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_full * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": w.name, "n_i": w.n_i, "n_p": w.n_p, "L": w.L, "n_rhs": w.n_rhs, "material": "cubic",
-                   "sampled": True},
+        "config": {"workload": w.name, "n_i": w.n_i, "n_p": w.n_p, "L": w.L, "n_rhs": w.n_rhs,
+                   "material": w.material.get("kind"), "sampled": True},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": info["cores"], "kind": "oracle", "sample": sample,
                          "cpu": info["cpu"]},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -193,8 +196,45 @@ def time_device_steps(torch, plan, fd, ud, steps, warmup, flush_buf, project=Tru
         stage += np.asarray(plan.stage_times())  # waits for this step's events
     plan.set_timing(False)
     torch.cuda.synchronize()
+    plan.sync_status()
     ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     return ms, stage / steps
+
+
+TENSOR = {"tf32": 1, "bf16x2": 3, "bf16x3": 6}  # tensor-core products per block product (split terms)
+DTYPE = {"fp64": "f64", "f32x2": "f32x2 (double-float, FP64-accurate)", "fp32": "f32",
+         "tf32": "tf32 x f32-accumulate (k = 0 in double-float)",
+         "bf16x2": "bf16 2-term split x f32-accumulate (k = 0 in double-float)",
+         "bf16x3": "bf16 3-term split x f32-accumulate (k = 0 in double-float)"}
+
+
+def mode_bands(L):
+    """k = 0, low 1..L/8, high L/8+1..L/2 (reading of the mode bands)."""
+    return {"k0": (0, 0), "low": (1, L // 8), "high": (L // 8 + 1, L // 2)}
+
+
+def band_errors(got, ref, L):
+    """Relative L2 error per mode band of one pad column's line (got, ref: [L][3])."""
+    E = np.fft.rfft(got - ref, axis=0)
+    R = np.fft.rfft(ref, axis=0)
+    out = {}
+    for name, (lo, hi) in mode_bands(L).items():
+        out[name] = float(np.linalg.norm(E[lo:hi + 1]) / max(np.linalg.norm(R[lo:hi + 1]), 1e-300))
+    return out
+
+
+def launches_per_apply(precision, info):
+    """Kernels one apply launches: forward, projection, contraction (k = 0 separately for the FP32 and
+    tensor forms; per streamed chunk: network, near copy, contraction), inverse."""
+    K = info["K"]
+    if info.get("surrogate_attached"):
+        chunks = -(-(K - 1) // max(1, info["surrogate_chunk"]))
+        contract = 1 + 3 * chunks
+    elif precision in ("fp64", "f32x2"):
+        contract = 1
+    else:
+        contract = 2
+    return 2 + contract + 1
 
 
 def run_ours(args, w):
@@ -212,20 +252,58 @@ def run_ours(args, w):
     fbc_build.build()
     fbc.load()
     pk = peaks()
+    R = w.n_rhs
     xy_i, xy_p = w.geometry()
     f = w.forces(seed=w.seed + rank)  # replicas: each rank updates its own instance
     t0 = time.perf_counter()
-    plan = fbc.Plan(xy_i, xy_p, w.L, w.material, precision=args.precision)
+    plan = fbc.Plan(xy_i, xy_p, w.L, w.material, precision=args.precision, max_rhs=R)
     plan.tabulate()
     torch.cuda.synchronize()
     setup_s = time.perf_counter() - t0
-    info = plan.info()
     fd = torch.from_numpy(f).cuda()
-    ud = torch.zeros((1, w.n_p, w.L, 3), dtype=torch.float64, device="cuda")
+    ud = torch.zeros((R, w.n_p, w.L, 3), dtype=torch.float64, device="cuda")
     flush_buf = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
+    pm = w.pair_modes
+    keep = 2  # pad columns whose outputs are kept for the error check (all rhs 0 and R-1 repeats)
+    rows = sorted({0, R - 1})
 
-    # headline precision
-    plan.set_precision(args.precision)
+    def snap():
+        return ud[rows, :keep].cpu().numpy()
+
+    variants, outputs = {}, {}
+
+    def variant(prec, steps):
+        plan.set_precision(prec)
+        vms, vstage = time_device_steps(torch, plan, fd, ud, steps, 2, flush_buf)
+        outputs[prec] = snap()
+        variants[prec] = {"ms_per_step": float(np.mean(vms)), "value": pm / (np.mean(vms) * 1e-3) / 1e9,
+                          "contract_ms": float(vstage[1])}
+
+    surrogate = None
+    if args.surrogate:
+        # ablation: the same plan with its exact tables first, then with the learned far field
+        variant(args.precision, max(2, args.steps // 2))
+        variants["exact_table"] = variants.pop(args.precision)
+        outputs["exact_table"] = outputs.pop(args.precision)
+        t1 = time.perf_counter()
+        S = fbc.Surrogate(width=128, seed=1)
+        loss = S.train(plan, n_samples=1 << 20, r_min=8.0, epochs=50, batch=4096, lr=2e-3, seed=2)
+        torch.cuda.synchronize()
+        train_s = time.perf_counter() - t1
+        before = plan.info()
+        plan.attach_surrogate(S, r_min=8.0, release_tables=True)
+        after = plan.info()
+        surrogate = {"width": 128, "r_min": 8.0, "train_samples": 1 << 20, "epochs": 50, "train_s": train_s,
+                     "final_loss": loss, "far_differences": after["n_far_d"], "used_differences": after["n_used_d"],
+                     "chunk_modes": after["surrogate_chunk"],
+                     "table_bytes_released": before["table_bytes"] + before["workspace_bytes"]
+                     - after["workspace_bytes"],
+                     "surrogate_bytes": after["surrogate_bytes"]}
+
+    # headline (a plan with released tables keeps its precision)
+    if not args.surrogate:
+        plan.set_precision(args.precision)
+    info = plan.info()
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
@@ -237,26 +315,21 @@ def run_ours(args, w):
         t = torch.tensor([step_ms], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         step_ms = float(t.item())
-    value = world * w.pair_modes / (step_ms * 1e-3) / 1e9
-    u_main = ud.cpu().numpy()
+    value = world * pm / (step_ms * 1e-3) / 1e9
+    outputs["headline"] = snap()
 
-    # the other precisions (same plan, same inputs)
-    variants = {}
-    outputs = {args.precision: u_main}
-    for prec in ("fp64", "f32x2", "fp32"):
-        if prec == args.precision:
-            continue
-        plan.set_precision(prec)
-        vms, vstage = time_device_steps(torch, plan, fd, ud, max(2, args.steps // 2), 2, flush_buf)
-        torch.cuda.synchronize()
-        outputs[prec] = ud.cpu().numpy()
-        variants[prec] = {"ms_per_step": float(np.mean(vms)), "value": w.pair_modes / (np.mean(vms) * 1e-3) / 1e9,
-                          "contract_ms": float(vstage[1])}
-    plan.set_precision(args.precision)
+    # the other precisions on the same plan and inputs (not after the tables were released); at the
+    # multi-rhs sizes the FP64 and double-float forms (tens of seconds per step) are left out
+    if not args.surrogate:
+        others = ("fp64", "f32x2", "fp32") if R == 1 else ("fp32", "tf32", "bf16x2", "bf16x3")
+        for prec in others:
+            if prec != args.precision:
+                variant(prec, max(2, args.steps // 2))
+        plan.set_precision(args.precision)
 
     # end-to-end through the host entry point: pinned host f in, host u out
     fh = torch.from_numpy(f).pin_memory()
-    uh = torch.zeros((1, w.n_p, w.L, 3), dtype=torch.float64).pin_memory()
+    uh = torch.zeros((R, w.n_p, w.L, 3), dtype=torch.float64).pin_memory()
     for _ in range(2):
         plan.apply_host(fh, uh)
     torch.cuda.synchronize()
@@ -270,76 +343,99 @@ def run_ours(args, w):
     e2e_s = float(np.mean(e2e_t))
     h2d = f.nbytes
     d2h = uh.numel() * 8
+    del fh, uh
 
-    # error against the FP64 oracle at the sampled pad atoms, and the CPU baseline
-    errors, cpu = {}, None
+    # error against the FP64 oracle at the sampled pad atoms (all repeats of the first pad column, right-hand
+    # sides 0 and R-1), per mode band, and the CPU baseline
+    errors, bands, cpu = {}, {}, None
     if rank == 0 and not args.skip_oracle:
         import oracle
 
-        samples, fp, d_index, table, samp_col, samp_p, t_table = oracle_sample(w, xy_i, xy_p, f)
-        ref = oracle.real_space_sum(d_index, table, fp, samp_col, samp_p)[0]
-        for prec, u in outputs.items():
-            got = u[0, samples[:, 0], samples[:, 1]]
-            errors[prec] = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
-        # timed oracle sum on the same sample, repeated to ~10 s of CPU work
+        samples, fp, d_index, table, samp_col, samp_p, t_table = oracle_sample(w, xy_i, xy_p, f[rows])
+        ref = oracle.real_space_sum(d_index, table, fp, samp_col, samp_p)  # [len(rows)][L][3]
+        for name, u in outputs.items():
+            got = u[:, samples[:, 0], samples[:, 1]]
+            errors[name] = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+            bands[name] = band_errors(got[0], ref[0], w.L)
+        # timed oracle sum on the same sample (one right-hand side), repeated to ~10 s of CPU work
+        fp1 = np.ascontiguousarray(fp[:1])
         reps, t_cpu = 0, 0.0
         while t_cpu < 10.0 and reps < 200:
             t1 = time.perf_counter()
-            oracle.real_space_sum(d_index, table, fp, samp_col, samp_p)
+            oracle.real_space_sum(d_index, table, fp1, samp_col, samp_p)
             t_cpu += time.perf_counter() - t1
             reps += 1
-        t_full = (t_cpu / reps) * (w.n_p * w.L) / len(samples)
+        t_full = (t_cpu / reps) * (w.n_p * w.L * R) / len(samples)
         sinfo = oracle.sys_info()
-        cpu = {"value": w.pair_modes / t_full / 1e9, "unit": UNIT, "cores": sinfo["cores"], "kind": "oracle",
-               "sample": (f"real-space sum at {len(samples)} pad atoms (1 pad column, all repeats) x {reps} "
-                          f"repetitions ({t_cpu:.1f} s), extrapolated to N_P L = {w.n_p * w.L} pad atoms; kernel "
-                          f"tabulation for the sample ({t_table:.1f} s) untimed"),
+        cpu = {"value": pm / t_full / 1e9, "unit": UNIT, "cores": sinfo["cores"], "kind": "oracle",
+               "sample": (f"real-space sum at {len(samples)} pad atoms (1 pad column, all repeats, 1 right-hand "
+                          f"side) x {reps} repetitions ({t_cpu:.1f} s), extrapolated to N_P L n_rhs = "
+                          f"{w.n_p * w.L * R} pad-atom updates; kernel tabulation for the sample ({t_table:.1f} s) "
+                          f"untimed"),
                "cpu": sinfo["cpu"]}
-        for prec in variants:
-            variants[prec]["rel_l2_vs_oracle"] = errors.get(prec)
+        for name in variants:
+            variants[name]["rel_l2_vs_oracle"] = errors.get(name)
+            variants[name]["rel_l2_by_band"] = bands.get(name)
 
-    # roofline of the dominant kernel (the per-mode contraction)
+    # roofline of the dominant kernel (the per-mode contraction stage, timed by the plan's events on the
+    # launching stream over the timed steps)
     contract_ms = float(stage[1])
-    pm = w.pair_modes
-    if args.precision == "fp64":
+    p = args.precision
+    if p in TENSOR:
+        # issued split products (TENSOR[p] bf16/tf32 products per block product), 36 flops each
+        achieved = TENSOR[p] * FLOPS_PER_PAIR_MODE * pm / (contract_ms * 1e-3) / 1e12
+        base = pk.get("bf16_tflops_sustained", pk["bf16_tflops"])
+        peak = base * (1.1 / 2.25 if p == "tf32" else 1.0)
+        peak_name = ("measured sustained bf16 dense" + (" x nominal tf32/bf16 ratio 1.1/2.25" if p == "tf32" else "")
+                     + f" ({pk['source']})")
+        bound = "tensor"
+    elif p == "fp64":
         achieved = FLOPS_PER_PAIR_MODE * pm / (contract_ms * 1e-3) / 1e12
-        peak, peak_name = pk["fp64_tflops"], "fp64 nominal 1.25 TFLOP/s scaled to max SM clock"
-    elif args.precision == "f32x2":
-        achieved = FLOPS_PER_PAIR_MODE // 2 * X2_FLOPS_PER_MAC * pm / (contract_ms * 1e-3) / 1e12
-        peak, peak_name = pk["fp32_tflops"], "fp32 FMA pipes: 152 SM x 128 lanes x 2 x max SM clock"
+        peak, peak_name, bound = pk["fp64_tflops"], "fp64 nominal 1.25 TFLOP/s scaled to max SM clock", "alu"
     else:
-        achieved = FLOPS_PER_PAIR_MODE * pm / (contract_ms * 1e-3) / 1e12
-        peak, peak_name = pk["fp32_tflops"], "fp32 FMA pipes: 152 SM x 128 lanes x 2 x max SM clock"
+        # CUDA-core FP32-pipe work: FFMA, FMUL and FADD each take one lane-slot of the FMA pipes, so the
+        # ceiling is an instruction rate: 152 SMs x 128 lanes x max SM clock
+        per_pm = (FLOPS_PER_PAIR_MODE // 2) * (X2_INSTR_PER_MAC if p == "f32x2" else 1)
+        achieved = per_pm * pm / (contract_ms * 1e-3) / 1e12
+        peak, bound = pk["fp32_tinstr"], "alu"
+        peak_name = ("FP32-pipe lane instructions: 152 SM x 128 lanes x max SM clock; "
+                     f"{per_pm} per pair-mode ({'12 per double-float MAC' if p == 'f32x2' else '1 FFMA per MAC'})")
     traffic = None
     tpath = os.path.join(ROOT, "profiles", "contract_traffic.json")
-    if os.path.exists(tpath):
-        with open(tpath) as fh:
-            tr = json.load(fh)
-        if tr.get("precision") == args.precision and tr.get("workload") == w.name and tr.get("valid", False):
-            traffic = tr.get("dram_bytes_per_launch")
-    n_launch_per_step = 1 + 1 + (2 if args.precision == "fp32" else 1) + 1  # forward, project, contract, inverse
+    if os.path.exists(tpath) and not args.surrogate:
+        with open(tpath) as fh_:
+            tr = json.load(fh_)
+        ent = tr.get(f"{w.name}/{p}")
+        if ent and ent.get("source_sha256") == source_digest(ent.get("sources", [])):
+            traffic = ent.get("dram_bytes_per_apply_contraction")
     clocks = clk.summary()
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": {"fp64": "f64", "f32x2": "f32x2 (double-float, FP64-accurate)", "fp32": "f32"}[args.precision],
+        "dtype": DTYPE[p] + (" with learned far field" if args.surrogate else ""),
         "data": "synthetic",
-        "config": {"workload": w.name, "n_i": w.n_i, "n_p": w.n_p, "L": w.L, "n_rhs": w.n_rhs, "material": "cubic",
-                   "precision": args.precision, "l2": "flushed between steps (256 MB write)",
+        "config": {"workload": w.name, "n_i": w.n_i, "n_p": w.n_p, "L": w.L, "n_rhs": R,
+                   "material": w.material.get("kind"), "precision": p, "surrogate": bool(args.surrogate),
+                   "l2": "flushed between steps (256 MB write)",
                    "parallelism": "replicas" if world > 1 else "single"},
-        "rel_l2_vs_oracle": errors.get(args.precision),
+        "rel_l2_vs_oracle": errors.get("headline"),
+        "rel_l2_by_band": bands.get("headline"),
         "setup_s": setup_s,
         "stage_ms": {"forward": float(stage[0]), "contract": contract_ms, "inverse": float(stage[2])},
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                     "traffic": traffic, "peak_source": peak_name},
+        "roofline": {"bound": bound, "achieved": achieved, "peak": peak,
+                     "unit": "TFLOP/s" if p in TENSOR or p == "fp64" else "T FP32-pipe instr/s",
+                     "frac": achieved / peak, "traffic": traffic, "peak_source": peak_name,
+                     "useful_tflops": FLOPS_PER_PAIR_MODE * pm / (contract_ms * 1e-3) / 1e12},
         "variants": variants,
         "e2e": {"value": world * pm / e2e_s / 1e9, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "ms_per_step": e2e_s * 1e3},
-        "gpu_launches": n_launch_per_step * args.steps,
+        "gpu_launches": launches_per_apply(p, info) * args.steps,
         "clocks": clocks,
         "plan": {k: info[k] for k in ("n_tiles_a", "n_tiles_b", "sub_w", "sub_h", "n_used_d", "table_bytes",
                                       "workspace_bytes")},
     }
+    if surrogate is not None:
+        line["surrogate"] = surrogate
     if cpu is not None:
         line["cpu_baseline"] = cpu
     plan.close()
@@ -351,16 +447,39 @@ def run_ours(args, w):
     return 0
 
 
+def source_digest(files):
+    """SHA-256 over the named source files (relative to the repository root); '' if any is missing."""
+    import hashlib
+
+    h = hashlib.sha256()
+    for rel in files:
+        path = os.path.join(ROOT, rel)
+        if not os.path.exists(path):
+            return ""
+        with open(path, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--precision", choices=["fp64", "f32x2", "fp32"], default="f32x2")
+    ap.add_argument("--precision", choices=["fp64", "f32x2", "fp32", "tf32", "bf16x2", "bf16x3"], default=None,
+                    help="contraction precision (default: f32x2 for one right-hand side, bf16x2 for several)")
+    ap.add_argument("--workload", choices=sorted(inputs.WORKLOADS), default=WORKLOAD)
+    ap.add_argument("--surrogate", action="store_true",
+                    help="train the learned far field (width 128, 2^20 samples, 50 epochs), attach it with "
+                         "r_min = 8 and release the K-slice tables; the exact-table path is timed first")
     ap.add_argument("--skip-oracle", action="store_true", help="no oracle error check / CPU baseline")
     args = ap.parse_args(argv)
-    w = inputs.WORKLOADS[WORKLOAD]
+    w = inputs.WORKLOADS[args.workload]
+    if args.precision is None:
+        args.precision = "f32x2" if w.n_rhs == 1 else "bf16x2"
+    if args.surrogate and args.precision not in ("fp32", "tf32", "bf16x2", "bf16x3"):
+        ap.error("--surrogate serves the FP32 and tensor-core precisions")
     if args.impl == "reference":
         return run_reference(args, w)
     return run_ours(args, w)

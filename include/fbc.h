@@ -127,6 +127,8 @@ typedef struct fbc_plan_info {
     size_t surrogate_bytes;     /* buffers of an attached surrogate (slice, near copy, lists, activations) */
     int32_t surrogate_attached; /* 1 while a surrogate is attached */
     int32_t n_far_d;            /* used differences the surrogate serves (|d| >= r_min) */
+    int32_t surrogate_chunk;    /* modes per streamed chunk (one network, near-copy and contraction launch each) */
+    int32_t reserved;
 } fbc_plan_info;
 
 /* Defaults listed in fbc_options. */

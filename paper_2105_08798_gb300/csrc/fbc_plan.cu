@@ -621,6 +621,8 @@ int fbc_plan_info_get(const fbc_plan* plan, fbc_plan_info* info) {
     info->surrogate_bytes = P.sur_bytes;
     info->surrogate_attached = P.sur ? 1 : 0;
     info->n_far_d = P.n_far;
+    info->surrogate_chunk = P.sur_chunk;
+    info->reserved = 0;
     info->workspace_bytes = P.workspace_bytes;
     return FBC_OK;
 }

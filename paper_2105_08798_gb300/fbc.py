@@ -76,7 +76,8 @@ class fbc_plan_info(ctypes.Structure):
                                               "sub_w", "sub_h", "n_used_d", "tabulated")] + [
         ("pair_modes_per_rhs", ctypes.c_double), ("table_bytes", ctypes.c_size_t),
         ("workspace_bytes", ctypes.c_size_t), ("surrogate_bytes", ctypes.c_size_t),
-        ("surrogate_attached", ctypes.c_int32), ("n_far_d", ctypes.c_int32)]
+        ("surrogate_attached", ctypes.c_int32), ("n_far_d", ctypes.c_int32), ("surrogate_chunk", ctypes.c_int32),
+        ("reserved", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
         return {name: getattr(self, name) for name, _ in self._fields_}

@@ -127,6 +127,8 @@ WORKLOADS = {
     "ring4000x6000_L256_cubic": Workload("ring4000x6000_L256_cubic", 4000, 6000, 256, 1, CUBIC, 1),
     # precision sweep size: 64 right-hand sides, isotropic
     "ring8000x12000_L1024_rhs64_iso": Workload("ring8000x12000_L1024_rhs64_iso", 8000, 12000, 1024, 64, ISO, 4),
+    # the same kind of case at a size a profiler capture can hold (a few GB on the device)
+    "ring4000x6000_L256_rhs64_iso": Workload("ring4000x6000_L256_rhs64_iso", 4000, 6000, 256, 64, ISO, 5),
 }
 
 

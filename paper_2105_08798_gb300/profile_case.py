@@ -1,0 +1,62 @@
+"""Run one configuration of the pad update (or of the surrogate network) a
+few times, for a profiler to capture.
+
+    python -m paper_2105_08798_gb300.profile_case --workload NAME --precision P [--applies N]
+    python -m paper_2105_08798_gb300.profile_case --mlp-rows N [--width H] [--applies N]
+
+The first form builds a plan for a named workload, tabulates it and runs
+``--applies`` pad updates at the given precision on device-resident inputs;
+the second runs the fused surrogate network on N rows of random features.
+Exits non-zero on any error; prints one line of timings.
+"""
+
+from __future__ import annotations
+
+import argparse
+import sys
+import time
+
+
+def main(argv=None) -> int:
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--workload", default="ring4000x6000_L256_rhs64_iso")
+    ap.add_argument("--precision", default="bf16x2")
+    ap.add_argument("--applies", type=int, default=2)
+    ap.add_argument("--mlp-rows", type=int, default=0)
+    ap.add_argument("--width", type=int, default=128)
+    args = ap.parse_args(argv)
+
+    import torch
+
+    from . import build, fbc, inputs
+
+    build.build()
+    fbc.load()
+    if args.mlp_rows:
+        with fbc.Surrogate(width=args.width, seed=1) as S:
+            x = torch.rand((args.mlp_rows, 4), device="cuda") * 2 - 1
+            for _ in range(args.applies):
+                S.forward(x, bf16_weights=True)
+            S.sync_status()
+        print(f"surrogate forward: {args.applies} x {args.mlp_rows} rows, width {args.width}")
+        return 0
+    w = inputs.WORKLOADS[args.workload]
+    xy_i, xy_p = w.geometry()
+    with fbc.Plan(xy_i, xy_p, w.L, w.material, precision=args.precision, max_rhs=w.n_rhs) as plan:
+        plan.tabulate()
+        fd = torch.from_numpy(w.forces()).cuda()
+        ud = torch.zeros((w.n_rhs, w.n_p, w.L, 3), dtype=torch.float64, device="cuda")
+        torch.cuda.synchronize()
+        times = []
+        for _ in range(args.applies):
+            t0 = time.perf_counter()
+            plan.apply(fd, ud)
+            torch.cuda.synchronize()
+            times.append(time.perf_counter() - t0)
+        plan.sync_status()
+    print(f"{w.name} {args.precision}: applies " + " ".join(f"{t * 1e3:.1f} ms" for t in times))
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())
