@@ -8,25 +8,32 @@
 // where the columns ':' are the x and y' halves of all right-hand sides and
 // M = [[A11, A12, -B13], [A12, A22, -B23], [B13, B23, A33]] comes from the six
 // table reals.  A CTA owns 128 pad columns (GEMM rows) at one k and up to 64
-// right-hand sides (N = 2 R columns); it walks the interface tiles in steps
-// of KB columns, and for each step
-//   * gathers the six 128 x KB blocks A_e(a, b) = T_e(x_a - x_b) from the
-//     staged table sub-box and splits them into bf16 pieces (h, m, l) or
-//     rounds them to tf32, written in the K-major no-swizzle canonical layout
-//     (8-row x 16-byte core matrices);
-//   * converts the transformed forces X_0, X_1, X_2 and -X_2 (the sign of the
-//     13/23 entries is carried by this negated copy) the same way;
+// right-hand sides (N = 2 R columns) and walks the interface columns in
+// stages of 16, through a ring of shared-memory stages:
+//   * eight builder warps gather the six 128 x 16 blocks A_e(a, b) =
+//     T_e(x_a - x_b) from the staged table sub-box, split them into bf16
+//     pieces (h, m, l) or round them to tf32, and store them in the K-major
+//     no-swizzle canonical layout (8-row x 16-byte core matrices);
+//   * the force operand X_0, X_1, X_2 was split once per apply by k_prep_b
+//     into the same layout, one contiguous chunk per (k, rhs group, stage);
+//     one thread streams each chunk in with a bulk copy (cp.async.bulk);
 //   * one thread issues the 9 block products per split-product pair with
 //     tcgen05.mma (M = 128, N = 2 R, K = 16 bf16 / 8 tf32) into three TMEM
-//     accumulators (one per output component) and commits to an mbarrier.
+//     accumulators (one per output component); the -B13, -B23 entries use
+//     the instruction's negate-A bit; a commit to the stage's "empty" barrier
+//     hands the stage back to the builders and the copy thread.
 // Split products: TF32 (1), BF16X2 (hh + hm + mh), BF16X3 (+ hl + lh + mm),
 // pieces h = bf16(x), m = bf16(x - h), l = bf16(x - h - m), all rounded to
-// nearest.  The logarithmic k = 0 mode is left to the FP64 kernel.
+// nearest.  The logarithmic k = 0 mode is left to the double-float kernel.
 //
-// Every wait on the mbarrier is bounded; when a bound is hit the CTA records
-// the status word, stops issuing work, waits once more (bounded) for its own
-// tensor-core work, frees its tensor memory and returns.
+// Every wait is bounded and gives up at once when another role has given up;
+// on a timeout the CTA records the status word, stops, waits (bounded) for
+// its own bulk copies and tensor-core work, frees its tensor memory and
+// returns.  Warps that synchronise on a named barrier decide to stop only
+// right after it, so none is left waiting there.
 #include <cuda_bf16.h>
+
+#include <algorithm>
 
 #include "fbc_internal.cuh"
 #include "fbc_tc.cuh"
@@ -35,10 +42,17 @@ namespace fbc {
 namespace {
 
 constexpr int kTmemCols = 512;
-constexpr int kMaxNP = 128;      // 64 right-hand sides x (x, y')
+constexpr int kRows = kTileA;    // GEMM rows (pad columns) per CTA
 constexpr int kRhsPerCta = 64;
+constexpr int kNPB = 128;        // force-operand rows per CTA (64 rhs x (x, y'))
+constexpr int kKC = 16;          // interface columns per stage
+constexpr int kBuilderWarps = 8;
+constexpr int kBuilders = kBuilderWarps * 32;
+constexpr int kMmaWarp = 8, kCopyWarp = 9;
+constexpr int kThreads = 10 * 32;
+constexpr int kStagesPerTile = kTileB / kKC;
+
 using tc::idesc;
-using tc::mbar_wait;
 using tc::sdesc;
 using tc::smem_u32;
 
@@ -46,23 +60,32 @@ template <int PREC>
 struct TcCfg;
 template <>
 struct TcCfg<FBC_PREC_TF32> {
-    static constexpr int ES = 4, NS = 1, NPROD = 1, KB = 32, KMMA = 8, FMT = 2;
+    static constexpr int ES = 4, NS = 1, NPROD = 1, KMMA = 8, FMT = 2, S = 2;
 };
 template <>
 struct TcCfg<FBC_PREC_BF16X2> {
-    static constexpr int ES = 2, NS = 2, NPROD = 3, KB = 32, KMMA = 16, FMT = 1;
+    static constexpr int ES = 2, NS = 2, NPROD = 3, KMMA = 16, FMT = 1, S = 2;
 };
 template <>
 struct TcCfg<FBC_PREC_BF16X3> {
-    static constexpr int ES = 2, NS = 3, NPROD = 6, KB = 16, KMMA = 16, FMT = 1;
+    static constexpr int ES = 2, NS = 3, NPROD = 6, KMMA = 16, FMT = 1, S = 1;
+};
+
+template <int PREC>
+struct TcLayout {
+    using C = TcCfg<PREC>;
+    static constexpr int KPC = 16 / C::ES;                    // K elements per 16-byte core row
+    static constexpr uint32_t SBO = (kKC / KPC) * 128;        // bytes per 8-row group of a [rows][16] block
+    static constexpr size_t ABLK = (size_t)kRows * kKC * C::ES;
+    static constexpr size_t A_STAGE = 6 * C::NS * ABLK;
+    static constexpr size_t B_STAGE = 3 * C::NS * (size_t)kNPB * kKC * C::ES;  // allocated for 128 rows
 };
 
 // (piece of A, piece of B) for each split product, by decreasing magnitude
 __constant__ int c_prod_a[6] = {0, 0, 1, 0, 2, 1};
 __constant__ int c_prod_b[6] = {0, 1, 0, 2, 0, 1};
-// table component of M for (c_out, c_in), and the force block it multiplies (3 = -X2)
+// table component of M for (c_out, c_in); the (0, 2) and (1, 2) entries are negated
 __constant__ int c_ent[3][3] = {{0, 1, 4}, {1, 2, 5}, {4, 5, 3}};
-__constant__ int c_bsel[3][3] = {{0, 1, 3}, {0, 1, 3}, {0, 1, 2}};
 
 // Split x into NS pieces of the operand type; returned as raw bits (bf16 in
 // the low 16 bits, or the tf32 bit pattern).  FP32 arithmetic throughout: each
@@ -85,58 +108,146 @@ __device__ __forceinline__ void split(float x, uint32_t (&out)[TcCfg<PREC>::NS])
     }
 }
 
-// 16 bytes of one core-matrix row: eight bf16 (low halves) or four tf32 words.
+// 16 bytes of one core-matrix row from KPC elements
 template <int ES, int KPC>
-__device__ __forceinline__ uint4 pack16(const uint32_t (&w)[KPC]) {
+__device__ __forceinline__ uint4 pack16(const uint32_t* w) {
     uint4 v;
     if (ES == 2) {
-        v.x = w[0] | (w[1 % KPC] << 16);
-        v.y = w[2 % KPC] | (w[3 % KPC] << 16);
-        v.z = w[4 % KPC] | (w[5 % KPC] << 16);
-        v.w = w[6 % KPC] | (w[7 % KPC] << 16);
+        v.x = w[0] | (w[1] << 16), v.y = w[2] | (w[3] << 16);
+        v.z = w[4] | (w[5] << 16), v.w = w[6] | (w[7] << 16);
     } else {
-        v.x = w[0], v.y = w[1 % KPC], v.z = w[2 % KPC], v.w = w[3 % KPC];
+        v.x = w[0], v.y = w[1], v.z = w[2], v.w = w[3];
     }
     return v;
 }
 
+// Bounded wait that also gives up as soon as another role has set *abort.
+__device__ __forceinline__ bool wait_or_abort(uint64_t* m, uint32_t parity, volatile int* abort) {
+    for (int it = 0; it < tc::kWaitLimit; it++) {
+        uint32_t ok;
+        asm volatile(
+            "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(ok)
+            : "r"(smem_u32(m)), "r"(parity)
+            : "memory");
+        if (ok) return true;
+        if ((it & 255) == 255 && *abort) return false;
+    }
+    return false;
+}
+
+// Named barrier among the builder warps that also returns, to every one of
+// them, whether any passed flag != 0: a decision all of them take alike.
+__device__ __forceinline__ bool builders_sync_any(int flag) {
+    uint32_t r;
+    asm volatile(
+        "{\n.reg .pred p, q;\nsetp.ne.s32 p, %1, 0;\nbar.red.or.pred q, 1, %2, p;\nselp.u32 %0, 1, 0, q;\n}\n"
+        : "=r"(r)
+        : "r"(flag), "n"(kBuilders)
+        : "memory");
+    return r != 0;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* m, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(m)), "r"(count));
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* m) {
+    asm volatile("{\n.reg .b64 st;\nmbarrier.arrive.shared::cta.b64 st, [%0];\n}\n" ::"r"(smem_u32(m)) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* m, uint32_t bytes) {
+    asm volatile("{\n.reg .b64 st;\nmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n}\n" ::"r"(smem_u32(m)),
+                 "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* m) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(m))
+        : "memory");
+}
+
+// Chunk of the split force operand for (k, rhs group g, interface tile tB, stage st).
+__host__ __device__ __forceinline__ size_t bchunk_index(int k, int g, int tB, int st, int G, int n_tb) {
+    return (((size_t)k * G + g) * n_tb + tB) * kStagesPerTile + st;
+}
+
+// One thread per 16-byte core row (block c, row n, core column kc) of a chunk:
+// X_c(b, n = 2 r + h) = fh[r][k][b][3 h + c], zero for r beyond the group.
 template <int PREC>
-__global__ void __launch_bounds__(kTileA, 1) k_contract_tc(ContractArgs A, int n_rhs, int* status) {
+__global__ void k_prep_b(const double* __restrict__ fh, int K, int NIpad, int n_tb, int G, int npb, int n_rhs,
+                         int k0, int n_modes, unsigned char* __restrict__ out) {
     using C = TcCfg<PREC>;
-    constexpr int TA = kTileA, TB = kTileB;
-    constexpr int KPC = 16 / C::ES;              // K elements per 16-byte core row
-    constexpr int KCOL = C::KB / KPC;            // core matrices along K per block
-    constexpr int SBO_A = KCOL * 128;            // bytes per 8-row group
-    constexpr int ABLK = TA * C::KB * C::ES;     // bytes per A block
-    constexpr int BBLK = kMaxNP * C::KB * C::ES; // bytes per B block (allocated for N = 128)
+    using Lt = TcLayout<PREC>;
+    constexpr int KPC = Lt::KPC, NKC = kKC / KPC;
+    const size_t chunk_bytes = (size_t)3 * C::NS * npb * kKC * C::ES;
+    const size_t per_chunk = (size_t)3 * npb * NKC;
+    const size_t total = (size_t)n_modes * G * n_tb * kStagesPerTile * per_chunk;
+    for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
+        size_t q = t / per_chunk;
+        const int rem = (int)(t % per_chunk);
+        const int c = rem / (npb * NKC), n = (rem / NKC) % npb, kc = rem % NKC;
+        const int st = (int)(q % kStagesPerTile);
+        q /= kStagesPerTile;
+        const int tB = (int)(q % n_tb);
+        q /= n_tb;
+        const int g = (int)(q % G);
+        const int k = k0 + (int)(q / G);
+        const int RG = min(kRhsPerCta, n_rhs - g * kRhsPerCta);
+        const int r = n >> 1, h = n & 1;
+        const int b0 = tB * kTileB + st * kKC + kc * KPC;
+        uint32_t w[C::NS][KPC];
+#pragma unroll
+        for (int i = 0; i < KPC; i++) {
+            float v = 0.f;
+            if (r < RG) v = (float)fh[(((size_t)(g * kRhsPerCta + r) * K + k) * NIpad + b0 + i) * 6 + h * 3 + c];
+            uint32_t sp[C::NS];
+            split<PREC>(v, sp);
+#pragma unroll
+            for (int p = 0; p < C::NS; p++) w[p][i] = sp[p];
+        }
+        unsigned char* base = out + bchunk_index(k, g, tB, st, G, n_tb) * chunk_bytes;
+        const uint32_t off = (uint32_t)(n / 8) * Lt::SBO + kc * 128 + (n % 8) * 16;
+#pragma unroll
+        for (int p = 0; p < C::NS; p++)
+            *(uint4*)(base + (size_t)(c * C::NS + p) * npb * kKC * C::ES + off) = pack16<C::ES, KPC>(w[p]);
+    }
+}
+
+template <int PREC>
+__global__ void __launch_bounds__(kThreads, 1)
+    k_contract_tc(ContractArgs A, int n_rhs, int G, int npb, const unsigned char* __restrict__ bprep, int* status) {
+    using C = TcCfg<PREC>;
+    using Lt = TcLayout<PREC>;
+    constexpr int S = C::S, KPC = Lt::KPC;
     extern __shared__ __align__(1024) unsigned char smem[];
-    __shared__ uint64_t mbar;
+    __shared__ uint64_t full[S], bfull[S], empty[S], done;
     __shared__ uint32_t tbase;
-    __shared__ int s_abort;
+    __shared__ volatile int s_abort;
 
     const int HW = A.H * A.W;
-    unsigned char* sA = smem;                                  // [6][NS] blocks
-    unsigned char* sB = sA + 6 * C::NS * ABLK;                  // [4][NS] blocks: X0, X1, X2, -X2
-    float* s_tab = (float*)(sB + 4 * C::NS * BBLK);             // [6][HW]
+    unsigned char* sA = smem;                                   // [S][6][NS][128][16]
+    unsigned char* sB = sA + S * Lt::A_STAGE;                   // [S][3][NS][npb][16]
+    float* s_tab = (float*)(sB + S * Lt::B_STAGE);              // [HW][6]
     int* s_off = (int*)(s_tab + 6 * HW);                        // [TB]
 
     const int tA = blockIdx.x;
     const int k = A.k0 + blockIdx.y;
-    const int r0 = blockIdx.z * kRhsPerCta;
+    const int g = blockIdx.z;
+    const int r0 = g * kRhsPerCta;
     const int RG = min(kRhsPerCta, n_rhs - r0);
     const int NP = ((2 * RG + 15) / 16) * 16;
-    const int a_loc = threadIdx.x;
-    const int a = tA * TA + a_loc;
-    const int2 xa = A.xy_p[a];
-    const int4 bA = A.bbox_a[tA];
-    const float* tk = A.tab32 + (size_t)(k - A.kbase) * A.Dy * A.Dx * 6;
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const int n_it = A.n_tb * kStagesPerTile;
+    const uint32_t chunk_bytes = (uint32_t)(3 * C::NS * npb * kKC * C::ES);
+    const size_t bblk = (size_t)npb * kKC * C::ES;              // one (block, piece) of a chunk
 
     if (threadIdx.x == 0) {
         s_abort = 0;
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&mbar)), "r"(1));
+        for (int s = 0; s < S; s++) mbar_init(&full[s], kBuilderWarps), mbar_init(&bfull[s], 1), mbar_init(&empty[s], 1);
+        mbar_init(&done, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (threadIdx.x < 32) {
+    if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tbase)),
                      "r"(kTmemCols));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
@@ -145,180 +256,204 @@ __global__ void __launch_bounds__(kTileA, 1) k_contract_tc(ContractArgs A, int n
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = tbase;
-    const uint32_t id = idesc(C::FMT, TA, NP);
-    uint32_t phase = 0;
-    bool acc[3] = {false, false, false};
-    bool pending = false;  // MMAs committed but not yet waited for
 
-    for (int tB = 0; tB < A.n_tb && !s_abort; tB++) {
-        const int4 bB = A.bbox_b[tB];
-        const int ox = bA.x - bB.y, oy = bA.z - bB.w;
-        __syncthreads();
-        for (int e = threadIdx.x; e < HW; e += TA) {
-            const int iy = e / A.W, ix = e - iy * A.W;
-            const int gx = ox + ix - A.box_x0, gy = oy + iy - A.box_y0;
-            float2 v0 = make_float2(0, 0), v1 = v0, v2 = v0;
-            if (gx < A.Dx && gy < A.Dy) {
-                const float2* src = (const float2*)(tk + ((size_t)gy * A.Dx + gx) * 6);
-                v0 = __ldg(src), v1 = __ldg(src + 1), v2 = __ldg(src + 2);
-            }
-            s_tab[0 * HW + e] = v0.x, s_tab[1 * HW + e] = v0.y;
-            s_tab[2 * HW + e] = v1.x, s_tab[3 * HW + e] = v1.y;
-            s_tab[4 * HW + e] = v2.x, s_tab[5 * HW + e] = v2.y;
-        }
-        for (int e = threadIdx.x; e < TB; e += TA) s_off[e] = A.off_i[tB * TB + e];
-        __syncthreads();
-        const int base = (xa.x - ox) + A.W * (xa.y - oy);
-        for (int j0 = 0; j0 < TB; j0 += C::KB) {
-            // the previous step's MMAs read the operand blocks: wait before overwriting them
-            if (pending) {
-                if (mbar_wait(&mbar, phase)) {
-                    phase ^= 1u;
-                    pending = false;
-                } else if (threadIdx.x == 0) {
-                    atomicExch(status, FBC_ERR_TIMEOUT);
+    if (warp == kCopyWarp) {
+        // ---- force operand: one bulk copy per stage ----
+        if (lane == 0) {
+            int it = 0;
+            for (; it < n_it; it++) {
+                const int s = it % S;
+                const uint32_t u = (uint32_t)(it / S);
+                if (!wait_or_abort(&empty[s], (u & 1u) ^ 1u, &s_abort)) {
                     s_abort = 1;
+                    break;
+                }
+                const int tB = it / kStagesPerTile, st = it % kStagesPerTile;
+                mbar_expect_tx(&bfull[s], chunk_bytes);
+                bulk_g2s(sB + s * Lt::B_STAGE, bprep + bchunk_index(k, g, tB, st, G, A.n_tb) * chunk_bytes,
+                         chunk_bytes, &bfull[s]);
+            }
+            // copies still in flight land before the CTA may exit (bounded)
+            for (int j = max(0, it - S); j < it; j++) wait_or_abort(&bfull[j % S], (uint32_t)(j / S) & 1u, &s_abort);
+        }
+    } else if (warp == kMmaWarp) {
+        // ---- tensor-core issue ----
+        if (lane == 0) {
+            const uint32_t id = idesc(C::FMT, kRows, NP), idn = id | (1u << 13);  // bit 13: negate A
+            bool acc[3] = {false, false, false};
+            for (int it = 0; it < n_it; it++) {
+                const int s = it % S;
+                const uint32_t par = (uint32_t)(it / S) & 1u;
+                if (!wait_or_abort(&full[s], par, &s_abort) || !wait_or_abort(&bfull[s], par, &s_abort)) {
+                    s_abort = 1;
+                    break;
                 }
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            }
-            __syncthreads();
-            if (s_abort) break;
-            // A blocks: row a_loc, columns j0 .. j0 + KB - 1, one table component at a time
+                const uint32_t a0 = smem_u32(sA + s * Lt::A_STAGE), b0 = smem_u32(sB + s * Lt::B_STAGE);
 #pragma unroll 1
-            for (int kc = 0; kc < KCOL; kc++) {
-                int idx[KPC];
-#pragma unroll
-                for (int i = 0; i < KPC; i++) idx[i] = base - s_off[j0 + kc * KPC + i];
-                const uint32_t off = (a_loc / 8) * SBO_A + kc * 128 + (a_loc % 8) * 16;
+                for (int co = 0; co < 3; co++)
 #pragma unroll 1
-                for (int eidx = 0; eidx < 6; eidx++) {
-                    uint32_t pk[C::NS][KPC];
-#pragma unroll
-                    for (int i = 0; i < KPC; i++) {
-                        uint32_t sp[C::NS];
-                        split<PREC>(s_tab[eidx * HW + idx[i]], sp);
-#pragma unroll
-                        for (int s2 = 0; s2 < C::NS; s2++) pk[s2][i] = sp[s2];
-                    }
-#pragma unroll
-                    for (int s2 = 0; s2 < C::NS; s2++)
-                        *(uint4*)(sA + (eidx * C::NS + s2) * ABLK + off) = pack16<C::ES, KPC>(pk[s2]);
-                }
-            }
-            // B blocks: rows n = 2 r + h (h = 0: x, 1: y'), columns j0 .. j0 + KB - 1; block 3 = -X2
-            for (int p = threadIdx.x; p < NP * KCOL; p += TA) {
-                const int n = p / KCOL, kc = p % KCOL;
-                const int r = n >> 1, h = n & 1;
-                const uint32_t off = (n / 8) * SBO_A + kc * 128 + (n % 8) * 16;
-                const double* src = A.fh + (((size_t)(r0 + min(r, RG - 1)) * A.K + k) * A.NIpad +
-                                            (size_t)tB * TB + j0 + kc * KPC) * 6 + h * 3;
-#pragma unroll 1
-                for (int c = 0; c < 4; c++) {
-                    uint32_t pk[C::NS][KPC];
-#pragma unroll
-                    for (int i = 0; i < KPC; i++) {
-                        float v = (r < RG) ? (float)src[i * 6 + (c < 3 ? c : 2)] : 0.0f;
-                        if (c == 3) v = -v;
-                        uint32_t sp[C::NS];
-                        split<PREC>(v, sp);
-#pragma unroll
-                        for (int s2 = 0; s2 < C::NS; s2++) pk[s2][i] = sp[s2];
-                    }
-#pragma unroll
-                    for (int s2 = 0; s2 < C::NS; s2++)
-                        *(uint4*)(sB + (c * C::NS + s2) * BBLK + off) = pack16<C::ES, KPC>(pk[s2]);
-                }
-            }
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            __syncthreads();
-            if (threadIdx.x == 0) {
-                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-#pragma unroll 1
-                for (int co = 0; co < 3; co++) {
-#pragma unroll 1
-                    for (int ci = 0; ci < 3; ci++)
+                    for (int ci = 0; ci < 3; ci++) {
+                        const uint32_t idd = (ci == 2 && co < 2) ? idn : id;
 #pragma unroll 1
                         for (int pr = 0; pr < C::NPROD; pr++)
-#pragma unroll 1
-                            for (int s = 0; s < C::KB / C::KMMA; s++) {
-                                const uint32_t aa = smem_u32(sA) + (c_ent[co][ci] * C::NS + c_prod_a[pr]) * ABLK + 256 * s;
-                                const uint32_t bb = smem_u32(sB) + (c_bsel[co][ci] * C::NS + c_prod_b[pr]) * BBLK + 256 * s;
-                                const uint64_t da = sdesc(aa, 128, SBO_A), db = sdesc(bb, 128, SBO_A);
-                                const uint32_t accum = acc[co] ? 1u : 0u;
+#pragma unroll
+                            for (int ks = 0; ks < kKC / C::KMMA; ks++) {
+                                const uint32_t aa =
+                                    a0 + (uint32_t)((c_ent[co][ci] * C::NS + c_prod_a[pr]) * Lt::ABLK) + 256 * ks;
+                                const uint32_t bb = b0 + (uint32_t)((ci * C::NS + c_prod_b[pr]) * bblk) + 256 * ks;
+                                const uint64_t da = sdesc(aa, 128, Lt::SBO), db = sdesc(bb, 128, Lt::SBO);
                                 const uint32_t dt = tmem + (uint32_t)(co * NP);
                                 if (C::FMT == 2)
                                     asm volatile(
                                         "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
                                         "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(dt),
-                                        "l"(da), "l"(db), "r"(id), "r"(accum));
+                                        "l"(da), "l"(db), "r"(idd), "r"(acc[co] ? 1u : 0u));
                                 else
-                                    asm volatile(
-                                        "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-                                        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dt),
-                                        "l"(da), "l"(db), "r"(id), "r"(accum));
+                                    tc::mma_bf16(dt, da, db, idd, acc[co] ? 1u : 0u);
                                 acc[co] = true;
                             }
-                }
-                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                    smem_u32(&mbar)));
+                    }
+                tc::commit(&empty[s]);
             }
-            pending = true;
+            tc::commit(&done);  // also after a stop: fires once the issued products are complete
         }
-    }
-    // drain the last commit (bounded; after a timeout this is the second, last
-    // bounded wait for our own tensor-core work), then read the accumulators
-    bool ok = true;
-    if (pending) {
-        ok = mbar_wait(&mbar, phase);
-        if (!ok && threadIdx.x == 0) atomicExch(status, FBC_ERR_TIMEOUT);
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    }
-    __syncthreads();
-    if (ok && !s_abort) {
-        const int warp = threadIdx.x / 32;
-        for (int co = 0; co < 3; co++)
-            for (int c0 = 0; c0 < NP; c0 += 16) {
-                uint32_t v[16];
-                const uint32_t ta = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(co * NP + c0);
-                asm volatile(
-                    "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
-                    "[%16];"
-                    : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-                      "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
-                      "=r"(v[15])
-                    : "r"(ta));
-                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+    } else {
+        // ---- builders (warps 0..7) ----
+        const int tid = threadIdx.x;                  // 0 .. 255
+        const int a_loc = (warp & 3) * 32 + lane;     // TMEM lane = GEMM row
+        const int hb = warp >> 2;                     // which 8 of the stage's 16 columns
+        const int a = tA * kRows + a_loc;
+        const int2 xa = A.xy_p[a];
+        const int4 bA = A.bbox_a[tA];
+        const float* tk = A.tab32 + (size_t)(k - A.kbase) * A.Dy * A.Dx * 6;
+        int it = 0;
+        for (int tB = 0; tB < A.n_tb; tB++) {
+            if (builders_sync_any(s_abort)) break;  // the same decision in every builder
+            const int4 bB = A.bbox_b[tB];
+            const int ox = bA.x - bB.y, oy = bA.z - bB.w;
+            for (int e = tid; e < HW; e += kBuilders) {
+                const int iy = e / A.W, ix = e - iy * A.W;
+                const int gx = ox + ix - A.box_x0, gy = oy + iy - A.box_y0;
+                float2 v0 = make_float2(0, 0), v1 = v0, v2 = v0;
+                if (gx < A.Dx && gy < A.Dy) {
+                    const float2* src = (const float2*)(tk + ((size_t)gy * A.Dx + gx) * 6);
+                    v0 = __ldg(src), v1 = __ldg(src + 1), v2 = __ldg(src + 2);
+                }
+                float2* dst = (float2*)(s_tab + (size_t)e * 6);
+                dst[0] = v0, dst[1] = v1, dst[2] = v2;
+            }
+            for (int e = tid; e < kTileB; e += kBuilders) s_off[e] = A.off_i[tB * kTileB + e];
+            asm volatile("bar.sync 1, %0;" ::"n"(kBuilders) : "memory");
+            const int base = (xa.x - ox) + A.W * (xa.y - oy);
+            for (int st = 0; st < kStagesPerTile; st++, it++) {
+                const int s = it % S;
+                const uint32_t u = (uint32_t)(it / S);
+                if (s_abort || !wait_or_abort(&empty[s], (u & 1u) ^ 1u, &s_abort)) {
+                    s_abort = 1;
+                    continue;  // keep the barrier count of the other builders
+                }
+                // row a_loc, columns st*16 + hb*8 .. + 7 of this tile: six entries, NS pieces each
+                float v[8][6];
 #pragma unroll
-                for (int i = 0; i < 16; i++) {
-                    const int n = c0 + i, r = n >> 1, h = n & 1;
+                for (int i = 0; i < 8; i++) {
+                    const int idx = base - s_off[st * kKC + hb * 8 + i];
+                    const float2* src = (const float2*)(s_tab + (size_t)idx * 6);
+                    const float2 p0 = src[0], p1 = src[1], p2 = src[2];
+                    v[i][0] = p0.x, v[i][1] = p0.y, v[i][2] = p1.x, v[i][3] = p1.y, v[i][4] = p2.x, v[i][5] = p2.y;
+                }
+                unsigned char* dstA = sA + s * Lt::A_STAGE;
+#pragma unroll
+                for (int e = 0; e < 6; e++) {
+                    uint32_t w[C::NS][8];
+#pragma unroll
+                    for (int i = 0; i < 8; i++) {
+                        uint32_t sp[C::NS];
+                        split<PREC>(v[i][e], sp);
+#pragma unroll
+                        for (int p = 0; p < C::NS; p++) w[p][i] = sp[p];
+                    }
+#pragma unroll
+                    for (int p = 0; p < C::NS; p++)
+#pragma unroll
+                        for (int q = 0; q < 8 / KPC; q++) {
+                            const int kc = (hb * 8) / KPC + q;
+                            const uint32_t off = (uint32_t)(a_loc / 8) * Lt::SBO + kc * 128 + (a_loc % 8) * 16;
+                            *(uint4*)(dstA + (size_t)(e * C::NS + p) * Lt::ABLK + off) =
+                                pack16<C::ES, KPC>(&w[p][q * KPC]);
+                        }
+                }
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&full[s]);
+            }
+        }
+        // ---- epilogue: accumulators -> uh (FP64) ----
+        const bool ok = wait_or_abort(&done, 0u, &s_abort) && !s_abort;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (ok) {
+            const uint32_t trow = tmem + ((uint32_t)((warp & 3) * 32) << 16);
+            for (int c0 = hb * 16; c0 < NP; c0 += 32) {
+                float v0[16], v1[16], v2[16];
+                tc::ld16(trow + (uint32_t)c0, v0);
+                tc::ld16(trow + (uint32_t)(NP + c0), v1);
+                tc::ld16(trow + (uint32_t)(2 * NP + c0), v2);
+#pragma unroll
+                for (int j = 0; j < 8; j++) {
+                    const int r = c0 / 2 + j;
                     if (r < RG) {
-                        double* o = A.uh + (((size_t)(r0 + r) * A.K + k) * A.NPpad + a) * 6 + h * 3 + co;
-                        *o = (double)__uint_as_float(v[i]);
+                        double2* o = (double2*)(A.uh + (((size_t)(r0 + r) * A.K + k) * A.NPpad + a) * 6);
+                        o[0] = make_double2(v0[2 * j], v1[2 * j]);
+                        o[1] = make_double2(v2[2 * j], v0[2 * j + 1]);
+                        o[2] = make_double2(v1[2 * j + 1], v2[2 * j + 1]);
                     }
                 }
             }
+        }
     }
+    __syncthreads();
+    if (threadIdx.x == 0 && s_abort) atomicExch(status, FBC_ERR_TIMEOUT);
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
-    if (threadIdx.x < 32)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols));
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols));
 }
 
 template <int PREC>
 size_t tc_smem(int HW) {
+    using Lt = TcLayout<PREC>;
+    return TcCfg<PREC>::S * (Lt::A_STAGE + Lt::B_STAGE) + (size_t)6 * HW * 4 + (size_t)kTileB * 4 + 1024;
+}
+
+int prep_groups(const Plan& P) { return (P.opt.max_rhs + kRhsPerCta - 1) / kRhsPerCta; }
+int prep_rows(const Plan& P) { return ((2 * std::min(kRhsPerCta, P.opt.max_rhs) + 15) / 16) * 16; }
+
+template <int PREC>
+size_t prep_bytes(const Plan& P) {
     using C = TcCfg<PREC>;
-    return (size_t)6 * C::NS * kTileA * C::KB * C::ES + (size_t)4 * C::NS * kMaxNP * C::KB * C::ES +
-           (size_t)6 * HW * 4 + (size_t)kTileB * 4 + 1024;
+    return (size_t)P.K * prep_groups(P) * P.n_tb * kStagesPerTile * 3 * C::NS * prep_rows(P) * kKC * C::ES;
 }
 
 template <int PREC>
 cudaError_t launch_tc(const ContractArgs& A, const Plan& P, int n_rhs, cudaStream_t st, int n_modes) {
     const size_t smem = tc_smem<PREC>(P.H * P.W);
     if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
+    if (!P.d_bprep || P.bprep_prec != PREC || n_rhs > P.opt.max_rhs) return cudaErrorInvalidValue;
+    const int G = (n_rhs + kRhsPerCta - 1) / kRhsPerCta;
+    const int Galloc = prep_groups(P), npb = prep_rows(P);
+    // split the force operand of these modes once
+    {
+        using Lt = TcLayout<PREC>;
+        const size_t total = (size_t)n_modes * Galloc * P.n_tb * kStagesPerTile * 3 * npb * (kKC / Lt::KPC);
+        const int grid = (int)std::min<size_t>((total + 255) / 256, (size_t)152 * 32);
+        k_prep_b<PREC><<<grid, 256, 0, st>>>(A.fh, P.K, P.NIpad, P.n_tb, Galloc, npb, n_rhs, A.k0, n_modes,
+                                             (unsigned char*)P.d_bprep);
+        if (cudaError_t e = cudaGetLastError()) return e;
+    }
     cudaError_t e = cudaFuncSetAttribute(k_contract_tc<PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e) return e;
-    dim3 grid(P.n_ta, n_modes, (n_rhs + kRhsPerCta - 1) / kRhsPerCta);
-    k_contract_tc<PREC><<<grid, kTileA, smem, st>>>(A, n_rhs, P.d_status);
+    dim3 grid(P.n_ta, n_modes, G);
+    k_contract_tc<PREC><<<grid, kThreads, smem, st>>>(A, n_rhs, Galloc, npb, (const unsigned char*)P.d_bprep,
+                                                      P.d_status);
     return cudaGetLastError();
 }
 
@@ -328,6 +463,12 @@ size_t contract_tc_smem(int precision, int HW) {
     if (precision == FBC_PREC_TF32) return tc_smem<FBC_PREC_TF32>(HW);
     if (precision == FBC_PREC_BF16X2) return tc_smem<FBC_PREC_BF16X2>(HW);
     return tc_smem<FBC_PREC_BF16X3>(HW);
+}
+
+size_t contract_tc_prep_bytes(const Plan& P, int precision) {
+    if (precision == FBC_PREC_TF32) return prep_bytes<FBC_PREC_TF32>(P);
+    if (precision == FBC_PREC_BF16X2) return prep_bytes<FBC_PREC_BF16X2>(P);
+    return prep_bytes<FBC_PREC_BF16X3>(P);
 }
 
 // Modes A.k0 .. A.k0 + n_modes - 1 (default: through K - 1) on the tensor cores (A.k0 >= 1).

@@ -100,6 +100,10 @@ struct Plan {
     float* d_near32 = nullptr;   // [K][n_near][6] exact entries of the near field
     float* d_slice = nullptr;    // [sur_chunk][Dy][Dx][6] streamed mode slices (FP32)
     int sur_chunk = 0;           // modes per streamed chunk
+    // tensor-core forms: the force operand split once per apply (fbc_contract_tc.cu)
+    void* d_bprep = nullptr;
+    size_t bprep_bytes = 0;
+    int bprep_prec = -1;
     bool timing = false, timed_once = false;
     size_t table_bytes = 0, workspace_bytes = 0;
 };
@@ -148,6 +152,7 @@ cudaError_t launch_contract_x2_k0(Plan& P, const ContractArgs& A, int n_rhs, cud
 cudaError_t launch_contract_streamed(Plan& P, int n_rhs, cudaStream_t st);
 void release_surrogate_buffers(Plan& P);
 size_t contract_tc_smem(int precision, int HW);
+size_t contract_tc_prep_bytes(const Plan& P, int precision);
 inline bool is_tensor_precision(int p) { return p == FBC_PREC_TF32 || p == FBC_PREC_BF16X2 || p == FBC_PREC_BF16X3; }
 int batch_rhs_block();
 LineArgs make_line_args(const Plan& P, const double* f, double* u);

@@ -181,7 +181,7 @@ int dev_alloc(T** p, size_t count, size_t& acc, const char* what) {
 void free_plan(fbc::Plan& P) {
     void* bufs[] = {P.d_xy_p,  P.d_off_i,    P.d_bbox_a, P.d_bbox_b, P.d_perm_i, P.d_perm_p,
                     P.d_used,  P.d_tw,       P.d_twL,    P.d_table,  P.d_table32, P.d_table_x2, P.d_table_x2_k0,
-                    P.d_fh,    P.d_uh,       P.d_part,   P.d_stage_f, P.d_stage_u, P.d_status};
+                    P.d_fh,    P.d_uh,       P.d_part,   P.d_stage_f, P.d_stage_u, P.d_status, P.d_bprep};
     for (void* b : bufs)
         if (b) cudaFree(b);
     for (auto& e : P.ev)
@@ -196,6 +196,22 @@ int ensure_derived(fbc::Plan& P, int precision) {
     if ((precision == FBC_PREC_FP32 || fbc::is_tensor_precision(precision)) && !P.d_table32) {
         int s = dev_alloc(&P.d_table32, cells * 6, acc, "table32");
         if (s) return s;
+    }
+    // the tensor forms' split force operand, sized for this precision's pieces
+    if (fbc::is_tensor_precision(precision) && P.bprep_prec != precision) {
+        const size_t want = fbc::contract_tc_prep_bytes(P, precision);
+        if (P.d_bprep && P.bprep_bytes < want) {
+            cudaFree(P.d_bprep);
+            P.workspace_bytes -= P.bprep_bytes;
+            P.d_bprep = nullptr, P.bprep_bytes = 0;
+        }
+        if (!P.d_bprep) {
+            unsigned char* q = nullptr;
+            int s = dev_alloc(&q, want, acc, "tensor force operand");
+            if (s) return s;
+            P.d_bprep = q, P.bprep_bytes = want;
+        }
+        P.bprep_prec = precision;
     }
     if (precision == FBC_PREC_F32X2 && !P.d_table_x2) {
         int s = dev_alloc(&P.d_table_x2, cells * 12, acc, "table_x2");
