@@ -100,8 +100,8 @@ std::vector<int4> ordered_items(const fbc_batch* b, int phase, bool lpt) {
 cudaError_t enqueue(fbc_batch* b, double alpha, double beta, uint32_t flags, cudaStream_t st) {
     cudaError_t e;
     const bool project = flags & FBC_APPLY_PROJECT_NEUTRAL, zmean = flags & FBC_APPLY_ZERO_MEAN_U;
-    if ((e = fbc::launch_batch_line(0, b->d_largs, b->d_fwd, (int)b->fwd.size(), b->smem_line, 0, 0, 0, st))) return e;
-    if (project && (e = fbc::launch_batch_line(1, b->d_largs, b->d_proj, (int)b->proj.size(), 0, 0, 0, 0, st))) return e;
+    if ((e = fbc::launch_batch_line(0, b->d_largs, b->d_fwd, (int)b->fwd.size(), b->smem_line, 0, 0, 0, st, fbc::line_fp32(b->precision)))) return e;
+    if (project && (e = fbc::launch_batch_line(1, b->d_largs, b->d_proj, (int)b->proj.size(), 0, 0, 0, 0, st, fbc::line_fp32(b->precision)))) return e;
     if ((e = cudaMemsetAsync(b->d_counter, 0, 2 * sizeof(int), st))) return e;
     for (int ph = 0; ph < 2; ph++)
         if ((e = fbc::launch_batch_contract(b->precision, ph, b->d_cargs, b->d_nrhs, b->d_con[ph],
@@ -109,9 +109,9 @@ cudaError_t enqueue(fbc_batch* b, double alpha, double beta, uint32_t flags, cud
                                             b->smem_con[ph], st)))
             return e;
     if ((e = fbc::launch_batch_line(2, b->d_largs, b->d_inv, (int)b->inv.size(), b->smem_line, alpha, beta,
-                                    zmean ? 1 : 0, st)))
+                                    zmean ? 1 : 0, st, fbc::line_fp32(b->precision))))
         return e;
-    if (zmean && (e = fbc::launch_batch_line(3, b->d_largs, b->d_zm, (int)b->zm.size(), 0, 0, 0, 0, st))) return e;
+    if (zmean && (e = fbc::launch_batch_line(3, b->d_largs, b->d_zm, (int)b->zm.size(), 0, 0, 0, 0, st, fbc::line_fp32(b->precision)))) return e;
     return cudaSuccess;
 }
 
@@ -261,7 +261,7 @@ int fbc_batch_autotune(fbc_batch* b, void* stream, double* best_ms) {
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) || cudaEventCreate(&e1)) return bfail(FBC_ERR_CUDA, "event creation failed");
     // the transforms run once so the contraction sees real inputs; the dominant launch (phase 1) is tuned
-    cudaError_t e = fbc::launch_batch_line(0, b->d_largs, b->d_fwd, (int)b->fwd.size(), b->smem_line, 0, 0, 0, st);
+    cudaError_t e = fbc::launch_batch_line(0, b->d_largs, b->d_fwd, (int)b->fwd.size(), b->smem_line, 0, 0, 0, st, fbc::line_fp32(b->precision));
     const int ph = 1;
     double best = 1e300;
     int best_grid = b->grid[ph], best_lpt = b->lpt;

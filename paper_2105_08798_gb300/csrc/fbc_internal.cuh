@@ -159,7 +159,9 @@ LineArgs make_line_args(const Plan& P, const double* f, double* u);
 size_t batch_line_smem(int max_L);
 // stage 0 forward, 1 projection, 2 inverse, 3 zero mean; items as documented in fbc_line.cu
 cudaError_t launch_batch_line(int stage, const LineArgs* d_args, const int4* d_items, int n_items, size_t smem,
-                              double alpha, double beta, int want_part, cudaStream_t st);
+                              double alpha, double beta, int want_part, cudaStream_t st, bool fp32);
+// line transforms in FP32 (k = 0 kept in FP64) for the FP32 and tensor-core contractions
+inline bool line_fp32(int precision) { return precision == FBC_PREC_FP32 || is_tensor_precision(precision); }
 // phase 0: k = 0 items (double-float tile), phase 1: k >= 1 items of an FP32 batch (8-rhs FP32 tile);
 // FP64 and double-float batches use phase 1 with their own tile for every item
 cudaError_t launch_batch_contract(int precision, int phase, const ContractArgs* d_args, const int* d_n_rhs,

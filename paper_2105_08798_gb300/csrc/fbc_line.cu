@@ -20,19 +20,46 @@
 // The FFT is an in-place radix-2 decimation-in-time transform in shared
 // memory (bit-reversed load, log2 L butterfly stages).  A CTA holds NC
 // columns, i.e. 1.5 NC complex sequences of length L.
+//
+// Two arithmetic forms.  FP64 throughout for the FP64 and double-float
+// contractions.  For the FP32 and tensor-core contractions (whose own error
+// is 3e-6 or more) the FFT runs in FP32, which on GB300 is about 30x the
+// FP64 rate, while the k = 0 mode stays FP64: the forward k = 0 entries are
+// FP64 column sums, and the inverse adds the k = 0 term (a constant along the
+// line) in FP64 after an FP32 transform of the k >= 1 modes.
 #include "fbc_internal.cuh"
 
 namespace fbc {
 namespace {
 
-__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
-    return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
+template <typename R>
+struct Cx;
+template <>
+struct Cx<double> {
+    using T = double2;
+    __device__ static T make(double x, double y) { return make_double2(x, y); }
+};
+template <>
+struct Cx<float> {
+    using T = float2;
+    __device__ static T make(float x, float y) { return make_float2(x, y); }
+};
+
+template <typename T2>
+__device__ __forceinline__ T2 cmul(T2 a, T2 b) {
+    T2 r;
+    r.x = fma(a.x, b.x, -a.y * b.y);
+    r.y = fma(a.x, b.y, a.y * b.x);
+    return r;
 }
 
 __device__ __forceinline__ int bitrev(int x, int logL) { return (int)(__brev((unsigned)x) >> (32 - logL)); }
 
 // nseq sequences of length L in buf; tw[t] = exp(-2 pi i t / L); inverse uses conj.
-__device__ void fft_block(double2* buf, int nseq, int L, int logL, const double2* __restrict__ tw, bool inverse) {
+template <typename R>
+__device__ void fft_block(typename Cx<R>::T* buf, int nseq, int L, int logL, const double2* __restrict__ tw,
+                          bool inverse) {
+    using T2 = typename Cx<R>::T;
     const int half = L >> 1;
     for (int lh = 0; lh < logL; lh++) {
         const int h = 1 << lh;
@@ -44,26 +71,30 @@ __device__ void fft_block(double2* buf, int nseq, int L, int logL, const double2
             const int grp = j >> lh;
             const int i0 = (grp << (lh + 1)) + pos;
             const int i1 = i0 + h;
-            double2 w = __ldg(&tw[pos * stride_tw]);
-            if (inverse) w.y = -w.y;
-            double2* s = buf + (size_t)sq * L;
-            const double2 a = s[i0];
-            const double2 bw = cmul(s[i1], w);
-            s[i0] = make_double2(a.x + bw.x, a.y + bw.y);
-            s[i1] = make_double2(a.x - bw.x, a.y - bw.y);
+            const double2 wd = __ldg(&tw[pos * stride_tw]);
+            const T2 w = Cx<R>::make((R)wd.x, inverse ? -(R)wd.y : (R)wd.y);
+            T2* s = buf + (size_t)sq * L;
+            const T2 a = s[i0];
+            const T2 bw = cmul(s[i1], w);
+            s[i0] = Cx<R>::make(a.x + bw.x, a.y + bw.y);
+            s[i1] = Cx<R>::make(a.x - bw.x, a.y - bw.y);
         }
         __syncthreads();
     }
 }
 
 // Forward transform of NC columns (block blk of right-hand side r).
+template <typename R>
 __device__ __forceinline__ void fwd_block(const double* __restrict__ f, const int* __restrict__ perm,
                                           const double2* __restrict__ tw, double* __restrict__ fh, int n_i, int L,
-                                          int logL, int K, int NIpad, int NC, int blk, int r, double2* sbuf) {
+                                          int logL, int K, int NIpad, int NC, int blk, int r, void* sraw) {
+    using T2 = typename Cx<R>::T;
+    constexpr bool kF32 = sizeof(R) == 4;
     // sbuf: [NC + NC/2][L], z sequences then w sequences
     const int b0 = blk * NC;
-    double2* zs = sbuf;
-    double2* ws = sbuf + (size_t)NC * L;
+    T2* zs = (T2*)sraw;
+    T2* ws = zs + (size_t)NC * L;
+    __shared__ double s0[kF32 ? 64 : 1][3];  // FP64 column sums = the k = 0 mode (FP32 form)
     // load: each column's L x 3 block is contiguous in f
     for (int t = threadIdx.x; t < NC * L; t += blockDim.x) {
         const int j = t / L, q = t % L;
@@ -74,27 +105,47 @@ __device__ __forceinline__ void fwd_block(const double* __restrict__ f, const in
             f1 = src[0], f2 = src[1], f3 = src[2];
         }
         const int qr = bitrev(q, logL);
-        zs[(size_t)j * L + qr] = make_double2(f1, f2);
-        double* wp = (double*)&ws[(size_t)(j >> 1) * L + qr];
-        wp[j & 1] = f3;
+        zs[(size_t)j * L + qr] = Cx<R>::make((R)f1, (R)f2);
+        R* wp = (R*)&ws[(size_t)(j >> 1) * L + qr];
+        wp[j & 1] = (R)f3;
+    }
+    if (kF32) {
+        // one warp per column: lane-strided FP64 sums, then a fixed shuffle tree (deterministic)
+        const int warp = threadIdx.x / 32, lane = threadIdx.x % 32, nw = blockDim.x / 32;
+        for (int j = warp; j < NC; j += nw) {
+            const int ob = perm[b0 + j];
+            double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+            if (ob >= 0)
+                for (int q = lane; q < L; q += 32) {
+                    const double* src = f + (((size_t)r * n_i + ob) * L + q) * 3;
+                    a0 += src[0], a1 += src[1], a2 += src[2];
+                }
+            for (int o = 16; o > 0; o >>= 1) {
+                a0 += __shfl_xor_sync(0xffffffffu, a0, o);
+                a1 += __shfl_xor_sync(0xffffffffu, a1, o);
+                a2 += __shfl_xor_sync(0xffffffffu, a2, o);
+            }
+            if (lane == 0) s0[j][0] = a0, s0[j][1] = a1, s0[j][2] = a2;
+        }
     }
     __syncthreads();
-    fft_block(sbuf, NC + NC / 2, L, logL, tw, false);
+    fft_block<R>(zs, NC + NC / 2, L, logL, tw, false);
     // unpack and store six-vectors for k = 0..L/2
     for (int t = threadIdx.x; t < NC * K; t += blockDim.x) {
         const int k = t / NC, j = t % NC;
         const int km = (L - k) & (L - 1);
-        const double2 Z = zs[(size_t)j * L + k], Zm = zs[(size_t)j * L + km];
-        const double2 Wv = ws[(size_t)(j >> 1) * L + k], Wm = ws[(size_t)(j >> 1) * L + km];
+        const T2 Z = zs[(size_t)j * L + k], Zm = zs[(size_t)j * L + km];
+        const T2 Wv = ws[(size_t)(j >> 1) * L + k], Wm = ws[(size_t)(j >> 1) * L + km];
         // F1 = (Z + conj Zm) / 2, F2 = (Z - conj Zm) / (2i)
-        const double F1r = 0.5 * (Z.x + Zm.x), F1i = 0.5 * (Z.y - Zm.y);
-        const double F2r = 0.5 * (Z.y + Zm.y), F2i = -0.5 * (Z.x - Zm.x);
+        double F1r = 0.5 * ((double)Z.x + Zm.x), F1i = 0.5 * ((double)Z.y - Zm.y);
+        double F2r = 0.5 * ((double)Z.y + Zm.y), F2i = -0.5 * ((double)Z.x - Zm.x);
         double F3r, F3i;
         if ((j & 1) == 0) {
-            F3r = 0.5 * (Wv.x + Wm.x), F3i = 0.5 * (Wv.y - Wm.y);
+            F3r = 0.5 * ((double)Wv.x + Wm.x), F3i = 0.5 * ((double)Wv.y - Wm.y);
         } else {
-            F3r = 0.5 * (Wv.y + Wm.y), F3i = -0.5 * (Wv.x - Wm.x);
+            F3r = 0.5 * ((double)Wv.y + Wm.y), F3i = -0.5 * ((double)Wv.x - Wm.x);
         }
+        if (kF32 && k == 0) F1r = s0[j][0], F2r = s0[j][1], F3r = s0[j][2], F1i = F2i = F3i = 0.0;
         double* o = fh + (((size_t)r * K + k) * NIpad + b0 + j) * 6;
         if (perm[b0 + j] < 0) {
             o[0] = o[1] = o[2] = o[3] = o[4] = o[5] = 0.0;
@@ -143,14 +194,18 @@ __device__ __forceinline__ void project_rhs(double* __restrict__ fh, const int* 
 
 // Inverse transform + epilogue of NC pad columns (block blk of right-hand side
 // r); with want_part the block's per-component sums go to part[r][blk].
+template <typename R>
 __device__ __forceinline__ void inv_block(const double* __restrict__ uh, const int* __restrict__ perm,
                                           const double2* __restrict__ tw, double* __restrict__ u,
                                           double* __restrict__ part, int n_p, int L, int logL, int K, int NPpad,
                                           int NC, double alpha_over_L, double beta, int want_part, int blk, int n_blk,
-                                          int r, double2* sbuf) {
+                                          int r, void* sraw) {
+    using T2 = typename Cx<R>::T;
+    constexpr bool kF32 = sizeof(R) == 4;
     const int a0 = blk * NC;
-    double2* zs = sbuf;
-    double2* ws = sbuf + (size_t)NC * L;
+    T2* zs = (T2*)sraw;
+    T2* ws = zs + (size_t)NC * L;
+    __shared__ double u0[kF32 ? 64 : 1][3];  // FP64 k = 0 term per column (FP32 form)
     const int Lh = L >> 1;
     for (int t = threadIdx.x; t < NC * K; t += blockDim.x) {
         const int k = t / NC, j = t % NC;
@@ -159,9 +214,14 @@ __device__ __forceinline__ void inv_block(const double* __restrict__ uh, const i
         // U1 = x0 + i y0, U2 = x1 + i y1 (U3 is handled per column pair below)
         double U1r = x0, U1i = y0, U2r = x1, U2i = y1;
         if (k == 0 || k == Lh) U1i = U2i = 0.0;
+        if (kF32 && k == 0) {
+            u0[j][0] = U1r, u0[j][1] = U2r;
+            U1r = U2r = 0.0;
+        }
         // Z(k) = U1 + i U2 ; Z(L-k) = conj U1 + i conj U2
-        zs[(size_t)j * L + bitrev(k, logL)] = make_double2(U1r - U2i, U1i + U2r);
-        if (k != 0 && k != Lh) zs[(size_t)j * L + bitrev(L - k, logL)] = make_double2(U1r + U2i, U2r - U1i);
+        zs[(size_t)j * L + bitrev(k, logL)] = Cx<R>::make((R)(U1r - U2i), (R)(U1i + U2r));
+        if (k != 0 && k != Lh)
+            zs[(size_t)j * L + bitrev(L - k, logL)] = Cx<R>::make((R)(U1r + U2i), (R)(U2r - U1i));
     }
     // W = U3(even column) + i U3(odd column), with U3 = -y2 + i x2: thread per (k, column pair)
     for (int t = threadIdx.x; t < (NC / 2) * K; t += blockDim.x) {
@@ -170,22 +230,54 @@ __device__ __forceinline__ void inv_block(const double* __restrict__ uh, const i
         const double* so = se + 6;
         double Er = -se[5], Ei = se[2], Or = -so[5], Oi = so[2];
         if (k == 0 || k == Lh) Ei = Oi = 0.0;
+        if (kF32 && k == 0) {
+            u0[2 * jp][2] = Er, u0[2 * jp + 1][2] = Or;
+            Er = Or = 0.0;
+        }
         // W(k) = E + i O ; W(L-k) = conj E + i conj O
-        ws[(size_t)jp * L + bitrev(k, logL)] = make_double2(Er - Oi, Ei + Or);
-        if (k != 0 && k != Lh) ws[(size_t)jp * L + bitrev(L - k, logL)] = make_double2(Er + Oi, Or - Ei);
+        ws[(size_t)jp * L + bitrev(k, logL)] = Cx<R>::make((R)(Er - Oi), (R)(Ei + Or));
+        if (k != 0 && k != Lh) ws[(size_t)jp * L + bitrev(L - k, logL)] = Cx<R>::make((R)(Er + Oi), (R)(Or - Ei));
     }
     __syncthreads();
-    fft_block(sbuf, NC + NC / 2, L, logL, tw, true);
+    fft_block<R>(zs, NC + NC / 2, L, logL, tw, true);
+    if (kF32) {
+        // the k >= 1 modes sum to zero along the line: remove the mean their FP32
+        // transform picked up, so the k = 0 band keeps FP64 accuracy
+        __shared__ double mz[64][3];
+        const int warp = threadIdx.x / 32, lane = threadIdx.x % 32, nw = blockDim.x / 32;
+        for (int j = warp; j < NC; j += nw) {
+            double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+            for (int p = lane; p < L; p += 32) {
+                const T2 z = zs[(size_t)j * L + p];
+                const T2 w = ws[(size_t)(j >> 1) * L + p];
+                a0 += z.x, a1 += z.y, a2 += (j & 1) ? w.y : w.x;
+            }
+            for (int o = 16; o > 0; o >>= 1) {
+                a0 += __shfl_xor_sync(0xffffffffu, a0, o);
+                a1 += __shfl_xor_sync(0xffffffffu, a1, o);
+                a2 += __shfl_xor_sync(0xffffffffu, a2, o);
+            }
+            if (lane == 0) mz[j][0] = a0 / L, mz[j][1] = a1 / L, mz[j][2] = a2 / L;
+        }
+        __syncthreads();
+        if (threadIdx.x < NC) {
+            u0[threadIdx.x][0] -= mz[threadIdx.x][0];
+            u0[threadIdx.x][1] -= mz[threadIdx.x][1];
+            u0[threadIdx.x][2] -= mz[threadIdx.x][2];
+        }
+        __syncthreads();
+    }
     double ps0 = 0.0, ps1 = 0.0, ps2 = 0.0;
     for (int t = threadIdx.x; t < NC * L; t += blockDim.x) {
         const int j = t / L, p = t % L;
         const int oa = perm[a0 + j];
         if (oa < 0) continue;
-        const double2 z = zs[(size_t)j * L + p];
-        const double2 w = ws[(size_t)(j >> 1) * L + p];
-        const double v3 = (j & 1) ? w.y : w.x;
+        const T2 z = zs[(size_t)j * L + p];
+        const T2 w = ws[(size_t)(j >> 1) * L + p];
+        double z0 = z.x, z1 = z.y, v3 = (j & 1) ? w.y : w.x;
+        if (kF32) z0 += u0[j][0], z1 += u0[j][1], v3 += u0[j][2];
         double* dst = u + (((size_t)r * n_p + oa) * L + p) * 3;
-        double o0 = alpha_over_L * z.x, o1 = alpha_over_L * z.y, o2 = alpha_over_L * v3;
+        double o0 = alpha_over_L * z0, o1 = alpha_over_L * z1, o2 = alpha_over_L * v3;
         if (beta != 0.0) {
             o0 = fma(beta, dst[0], o0);
             o1 = fma(beta, dst[1], o1);
@@ -234,43 +326,47 @@ __device__ __forceinline__ void zero_mean_chunk(double* __restrict__ u, const do
 }
 
 // ---- one launch per plan ------------------------------------------------------
+template <typename R>
 __global__ void k_forward(const double* __restrict__ f, const int* __restrict__ perm, const double2* __restrict__ tw,
                           double* __restrict__ fh, int n_i, int L, int logL, int K, int NIpad, int NC) {
     extern __shared__ double2 sbuf[];
-    fwd_block(f, perm, tw, fh, n_i, L, logL, K, NIpad, NC, blockIdx.x, blockIdx.y, sbuf);
+    fwd_block<R>(f, perm, tw, fh, n_i, L, logL, K, NIpad, NC, blockIdx.x, blockIdx.y, sbuf);
 }
 __global__ void k_project(double* __restrict__ fh, const int* __restrict__ perm, int n_i, int K, int NIpad) {
     project_rhs(fh, perm, n_i, K, NIpad, blockIdx.y);
 }
+template <typename R>
 __global__ void k_inverse(const double* __restrict__ uh, const int* __restrict__ perm, const double2* __restrict__ tw,
                           double* __restrict__ u, double* __restrict__ part, int n_p, int L, int logL, int K, int NPpad,
                           int NC, double alpha_over_L, double beta, int want_part) {
     extern __shared__ double2 sbuf[];
-    inv_block(uh, perm, tw, u, part, n_p, L, logL, K, NPpad, NC, alpha_over_L, beta, want_part, blockIdx.x, gridDim.x,
-              blockIdx.y, sbuf);
+    inv_block<R>(uh, perm, tw, u, part, n_p, L, logL, K, NPpad, NC, alpha_over_L, beta, want_part, blockIdx.x,
+                 gridDim.x, blockIdx.y, sbuf);
 }
 __global__ void k_zero_mean(double* __restrict__ u, const double* __restrict__ part, int n_part, int n_p, int L) {
     zero_mean_chunk(u, part, n_part, n_p, L, blockIdx.y, blockIdx.x, gridDim.x);
 }
 
 // ---- batched over plans: items (instance, block, right-hand side) ---------------
+template <typename R>
 __global__ void k_batch_forward(const LineArgs* __restrict__ la, const int4* __restrict__ items) {
     extern __shared__ double2 sbuf[];
     const int4 w = items[blockIdx.x];
     const LineArgs A = la[w.x];
-    fwd_block(A.f, A.perm_i, A.tw, A.fh, A.n_i, A.L, A.logL, A.K, A.NIpad, A.NC, w.y, w.z, sbuf);
+    fwd_block<R>(A.f, A.perm_i, A.tw, A.fh, A.n_i, A.L, A.logL, A.K, A.NIpad, A.NC, w.y, w.z, sbuf);
 }
 __global__ void k_batch_project(const LineArgs* __restrict__ la, const int4* __restrict__ items) {
     const int4 w = items[blockIdx.x];
     const LineArgs A = la[w.x];
     project_rhs(A.fh, A.perm_i, A.n_i, A.K, A.NIpad, w.z);
 }
+template <typename R>
 __global__ void k_batch_inverse(const LineArgs* __restrict__ la, const int4* __restrict__ items, double alpha,
                                 double beta, int want_part) {
     extern __shared__ double2 sbuf[];
     const int4 w = items[blockIdx.x];
     const LineArgs A = la[w.x];
-    inv_block(A.uh, A.perm_p, A.tw, A.u, A.part, A.n_p, A.L, A.logL, A.K, A.NPpad, A.NC, alpha / (double)A.L, beta,
+    inv_block<R>(A.uh, A.perm_p, A.tw, A.u, A.part, A.n_p, A.L, A.logL, A.K, A.NPpad, A.NC, alpha / (double)A.L, beta,
               want_part, w.y, A.NPpad / A.NC, w.z, sbuf);
 }
 __global__ void k_batch_zero_mean(const LineArgs* __restrict__ la, const int4* __restrict__ items) {
@@ -288,10 +384,14 @@ cudaError_t launch_forward(Plan& P, const double* f, int n_rhs, bool project, cu
     const size_t smem = line_smem(P.L, NC);
     cudaError_t e;
     // opt in above the default dynamic limit (the kernel's static arrays count towards 48 KB)
-    if (smem > 32 * 1024 && (e = cudaFuncSetAttribute(k_forward, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)))
-        return e;
     dim3 grid(P.NIpad / NC, n_rhs);
-    k_forward<<<grid, 256, smem, st>>>(f, P.d_perm_i, P.d_tw, P.d_fh, P.n_i, P.L, P.logL, P.K, P.NIpad, NC);
+    if (line_fp32(P.precision)) {
+        if ((e = cudaFuncSetAttribute(k_forward<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem))) return e;
+        k_forward<float><<<grid, 256, smem / 2, st>>>(f, P.d_perm_i, P.d_tw, P.d_fh, P.n_i, P.L, P.logL, P.K, P.NIpad, NC);
+    } else {
+        if ((e = cudaFuncSetAttribute(k_forward<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem))) return e;
+        k_forward<double><<<grid, 256, smem, st>>>(f, P.d_perm_i, P.d_tw, P.d_fh, P.n_i, P.L, P.logL, P.K, P.NIpad, NC);
+    }
     if ((e = cudaGetLastError())) return e;
     if (project) {
         k_project<<<dim3(1, n_rhs), 256, 0, st>>>(P.d_fh, P.d_perm_i, P.n_i, P.K, P.NIpad);
@@ -305,12 +405,17 @@ cudaError_t launch_inverse(Plan& P, double* u, int n_rhs, double alpha, double b
     const int NC = line_cols(P.L);
     const size_t smem = line_smem(P.L, NC);
     cudaError_t e;
-    if (smem > 32 * 1024 && (e = cudaFuncSetAttribute(k_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)))
-        return e;
     const int nb = P.NPpad / NC;
     dim3 grid(nb, n_rhs);
-    k_inverse<<<grid, 256, smem, st>>>(P.d_uh, P.d_perm_p, P.d_tw, u, P.d_part, P.n_p, P.L, P.logL, P.K, P.NPpad, NC,
-                                       alpha / (double)P.L, beta, zero_mean ? 1 : 0);
+    if (line_fp32(P.precision)) {
+        if ((e = cudaFuncSetAttribute(k_inverse<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem))) return e;
+        k_inverse<float><<<grid, 256, smem / 2, st>>>(P.d_uh, P.d_perm_p, P.d_tw, u, P.d_part, P.n_p, P.L, P.logL, P.K,
+                                                      P.NPpad, NC, alpha / (double)P.L, beta, zero_mean ? 1 : 0);
+    } else {
+        if ((e = cudaFuncSetAttribute(k_inverse<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem))) return e;
+        k_inverse<double><<<grid, 256, smem, st>>>(P.d_uh, P.d_perm_p, P.d_tw, u, P.d_part, P.n_p, P.L, P.logL, P.K,
+                                                   P.NPpad, NC, alpha / (double)P.L, beta, zero_mean ? 1 : 0);
+    }
     if ((e = cudaGetLastError())) return e;
     if (zero_mean) {
         const size_t n = (size_t)P.n_p * P.L * 3;
@@ -333,22 +438,38 @@ LineArgs make_line_args(const Plan& P, const double* f, double* u) {
 size_t batch_line_smem(int max_L) { return line_smem(max_L, line_cols(max_L)); }
 
 cudaError_t launch_batch_line(int stage, const LineArgs* d_args, const int4* d_items, int n_items, size_t smem,
-                              double alpha, double beta, int want_part, cudaStream_t st) {
+                              double alpha, double beta, int want_part, cudaStream_t st, bool fp32) {
     if (n_items == 0) return cudaSuccess;
     cudaError_t e;
     switch (stage) {
         case 0:
-            if ((e = cudaFuncSetAttribute(k_batch_forward, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)))
-                return e;
-            k_batch_forward<<<n_items, 256, smem, st>>>(d_args, d_items);
+            if (fp32) {
+                if ((e = cudaFuncSetAttribute(k_batch_forward<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              (int)smem)))
+                    return e;
+                k_batch_forward<float><<<n_items, 256, smem / 2, st>>>(d_args, d_items);
+            } else {
+                if ((e = cudaFuncSetAttribute(k_batch_forward<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              (int)smem)))
+                    return e;
+                k_batch_forward<double><<<n_items, 256, smem, st>>>(d_args, d_items);
+            }
             break;
         case 1:
             k_batch_project<<<n_items, 256, 0, st>>>(d_args, d_items);
             break;
         case 2:
-            if ((e = cudaFuncSetAttribute(k_batch_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)))
-                return e;
-            k_batch_inverse<<<n_items, 256, smem, st>>>(d_args, d_items, alpha, beta, want_part);
+            if (fp32) {
+                if ((e = cudaFuncSetAttribute(k_batch_inverse<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              (int)smem)))
+                    return e;
+                k_batch_inverse<float><<<n_items, 256, smem / 2, st>>>(d_args, d_items, alpha, beta, want_part);
+            } else {
+                if ((e = cudaFuncSetAttribute(k_batch_inverse<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              (int)smem)))
+                    return e;
+                k_batch_inverse<double><<<n_items, 256, smem, st>>>(d_args, d_items, alpha, beta, want_part);
+            }
             break;
         default:
             k_batch_zero_mean<<<n_items, 256, 0, st>>>(d_args, d_items);

@@ -68,3 +68,14 @@ def test_tensor_form_against_oracle(fbc, oracle_mod):
     ref = oracle_mod.pad_update(xy_i, xy_p, 16, 1.0, ISO, f[:1])
     assert rel_l2(out["fp64"][:1], ref) <= 1e-12
     assert rel_l2(out["bf16x3"][:1], ref) <= BOUNDS["bf16x3"]
+
+
+def test_k0_band_stays_fp64(fbc):
+    """The k = 0 mode runs in double-float and the FP32 line transforms keep it in FP64:
+    the mean along the line of every pad column matches the FP64 path to rounding."""
+    _, _, _, out = _run_all(fbc, 300, 450, 64, 8, seed=11)
+    ref = np.fft.rfft(out["fp64"], axis=2)[:, :, 0]
+    for prec in BOUNDS:
+        got = np.fft.rfft(out[prec], axis=2)[:, :, 0]
+        err = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+        assert err <= 1e-11, (prec, err)
