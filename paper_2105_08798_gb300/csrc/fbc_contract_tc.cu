@@ -148,6 +148,14 @@ __device__ __forceinline__ bool builders_sync_any(int flag) {
     return r != 0;
 }
 
+__device__ __forceinline__ void cp_async8(void* dst, const void* src, int src_bytes) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(smem_u32(dst)), "l"(src), "r"(src_bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+
 __device__ __forceinline__ void mbar_init(uint64_t* m, uint32_t count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(m)), "r"(count));
 }
@@ -215,7 +223,8 @@ __global__ void k_prep_b(const double* __restrict__ fh, int K, int NIpad, int n_
 
 template <int PREC>
 __global__ void __launch_bounds__(kThreads, 1)
-    k_contract_tc(ContractArgs A, int n_rhs, int G, int npb, const unsigned char* __restrict__ bprep, int* status) {
+    k_contract_tc(ContractArgs A, int n_rhs, int G, int npb, const unsigned char* __restrict__ bprep, int nbuf,
+                  int* status) {
     using C = TcCfg<PREC>;
     using Lt = TcLayout<PREC>;
     constexpr int S = C::S, KPC = Lt::KPC;
@@ -227,8 +236,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int HW = A.H * A.W;
     unsigned char* sA = smem;                                   // [S][6][NS][128][16]
     unsigned char* sB = sA + S * Lt::A_STAGE;                   // [S][3][NS][npb][16]
-    float* s_tab = (float*)(sB + S * Lt::B_STAGE);              // [HW][6]
-    int* s_off = (int*)(s_tab + 6 * HW);                        // [TB]
+    int* s_off = (int*)(sB + S * Lt::B_STAGE);                  // [nbuf][TB]
+    float* s_tab = (float*)(s_off + nbuf * kTileB);             // [nbuf][HW][6]
 
     const int tA = blockIdx.x;
     const int k = A.k0 + blockIdx.y;
@@ -327,24 +336,39 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int2 xa = A.xy_p[a];
         const int4 bA = A.bbox_a[tA];
         const float* tk = A.tab32 + (size_t)(k - A.kbase) * A.Dy * A.Dx * 6;
-        int it = 0;
-        for (int tB = 0; tB < A.n_tb; tB++) {
-            if (builders_sync_any(s_abort)) break;  // the same decision in every builder
+        // table sub-box and interface offsets of tile tB into buffer buf, by asynchronous copies
+        auto stage_async = [&](int buf, int tB) {
             const int4 bB = A.bbox_b[tB];
             const int ox = bA.x - bB.y, oy = bA.z - bB.w;
+            float* dt = s_tab + (size_t)buf * HW * 6;
             for (int e = tid; e < HW; e += kBuilders) {
                 const int iy = e / A.W, ix = e - iy * A.W;
                 const int gx = ox + ix - A.box_x0, gy = oy + iy - A.box_y0;
-                float2 v0 = make_float2(0, 0), v1 = v0, v2 = v0;
-                if (gx < A.Dx && gy < A.Dy) {
-                    const float2* src = (const float2*)(tk + ((size_t)gy * A.Dx + gx) * 6);
-                    v0 = __ldg(src), v1 = __ldg(src + 1), v2 = __ldg(src + 2);
-                }
-                float2* dst = (float2*)(s_tab + (size_t)e * 6);
-                dst[0] = v0, dst[1] = v1, dst[2] = v2;
+                const bool in = gx < A.Dx && gy < A.Dy;
+                const float* src = in ? tk + ((size_t)gy * A.Dx + gx) * 6 : tk;  // zero fill outside the box
+#pragma unroll
+                for (int h = 0; h < 3; h++) cp_async8(dt + (size_t)e * 6 + 2 * h, src + 2 * h, in ? 8 : 0);
             }
-            for (int e = tid; e < kTileB; e += kBuilders) s_off[e] = A.off_i[tB * kTileB + e];
-            asm volatile("bar.sync 1, %0;" ::"n"(kBuilders) : "memory");
+            if (tid < kTileB / 4) cp_async16(s_off + buf * kTileB + 4 * tid, A.off_i + tB * kTileB + 4 * tid);
+            asm volatile("cp.async.commit_group;" ::: "memory");
+        };
+        int it = 0;
+        if (nbuf == 2) stage_async(0, 0);
+        for (int tB = 0; tB < A.n_tb; tB++) {
+            if (nbuf == 1) {
+                if (builders_sync_any(s_abort)) break;  // everyone is done with the previous tile
+                stage_async(0, tB);
+            }
+            asm volatile("cp.async.wait_all;" ::: "memory");
+            // this tile's copies are visible to every builder, the previous tile is done;
+            // the same stop decision in every builder
+            if (builders_sync_any(s_abort)) break;
+            if (nbuf == 2 && tB + 1 < A.n_tb) stage_async((tB + 1) & 1, tB + 1);
+            const int buf = nbuf == 2 ? (tB & 1) : 0;
+            const float* tab_b = s_tab + (size_t)buf * HW * 6;
+            const int* off_b = s_off + buf * kTileB;
+            const int4 bB = A.bbox_b[tB];
+            const int ox = bA.x - bB.y, oy = bA.z - bB.w;
             const int base = (xa.x - ox) + A.W * (xa.y - oy);
             for (int st = 0; st < kStagesPerTile; st++, it++) {
                 const int s = it % S;
@@ -357,37 +381,51 @@ __global__ void __launch_bounds__(kThreads, 1)
                 float v[8][6];
 #pragma unroll
                 for (int i = 0; i < 8; i++) {
-                    const int idx = base - s_off[st * kKC + hb * 8 + i];
-                    const float2* src = (const float2*)(s_tab + (size_t)idx * 6);
+                    const int idx = base - off_b[st * kKC + hb * 8 + i];
+                    const float2* src = (const float2*)(tab_b + (size_t)idx * 6);
                     const float2 p0 = src[0], p1 = src[1], p2 = src[2];
                     v[i][0] = p0.x, v[i][1] = p0.y, v[i][2] = p1.x, v[i][3] = p1.y, v[i][4] = p2.x, v[i][5] = p2.y;
                 }
                 unsigned char* dstA = sA + s * Lt::A_STAGE;
 #pragma unroll
                 for (int e = 0; e < 6; e++) {
-                    uint32_t w[C::NS][8];
+                    float x[8];
 #pragma unroll
-                    for (int i = 0; i < 8; i++) {
-                        uint32_t sp[C::NS];
-                        split<PREC>(v[i][e], sp);
+                    for (int i = 0; i < 8; i++) x[i] = v[i][e];
+                    if (C::ES == 2) {
+                        // bf16 pieces two at a time: packed round-to-nearest conversion, exact FP32 remainders
 #pragma unroll
-                        for (int p = 0; p < C::NS; p++) w[p][i] = sp[p];
-                    }
+                        for (int p = 0; p < C::NS; p++) {
+                            uint32_t w[4];
 #pragma unroll
-                    for (int p = 0; p < C::NS; p++)
-#pragma unroll
-                        for (int q = 0; q < 8 / KPC; q++) {
-                            const int kc = (hb * 8) / KPC + q;
-                            const uint32_t off = (uint32_t)(a_loc / 8) * Lt::SBO + kc * 128 + (a_loc % 8) * 16;
-                            *(uint4*)(dstA + (size_t)(e * C::NS + p) * Lt::ABLK + off) =
-                                pack16<C::ES, KPC>(&w[p][q * KPC]);
+                            for (int i = 0; i < 4; i++) {
+                                asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(w[i]) : "f"(x[2 * i + 1]), "f"(x[2 * i]));
+                                if (p + 1 < C::NS) {
+                                    x[2 * i] = __fsub_rn(x[2 * i], __uint_as_float(w[i] << 16));
+                                    x[2 * i + 1] = __fsub_rn(x[2 * i + 1], __uint_as_float(w[i] & 0xffff0000u));
+                                }
+                            }
+                            const uint32_t off = (uint32_t)(a_loc / 8) * Lt::SBO + hb * 128 + (a_loc % 8) * 16;
+                            *(uint4*)(dstA + (size_t)(e * C::NS + p) * Lt::ABLK + off) = make_uint4(w[0], w[1], w[2], w[3]);
                         }
+                    } else {
+#pragma unroll
+                        for (int q = 0; q < 2; q++) {
+                            uint32_t w[4];
+#pragma unroll
+                            for (int i = 0; i < 4; i++) asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(w[i]) : "f"(x[4 * q + i]));
+                            const int kc = hb * 2 + q;
+                            const uint32_t off = (uint32_t)(a_loc / 8) * Lt::SBO + kc * 128 + (a_loc % 8) * 16;
+                            *(uint4*)(dstA + (size_t)e * Lt::ABLK + off) = make_uint4(w[0], w[1], w[2], w[3]);
+                        }
+                    }
                 }
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&full[s]);
             }
         }
+        asm volatile("cp.async.wait_all;" ::: "memory");  // a prefetch still in flight after a stop
         // ---- epilogue: accumulators -> uh (FP64) ----
         const bool ok = wait_or_abort(&done, 0u, &s_abort) && !s_abort;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -419,10 +457,15 @@ __global__ void __launch_bounds__(kThreads, 1)
 }
 
 template <int PREC>
-size_t tc_smem(int HW) {
+size_t tc_smem(int HW, int nbuf) {
     using Lt = TcLayout<PREC>;
-    return TcCfg<PREC>::S * (Lt::A_STAGE + Lt::B_STAGE) + (size_t)6 * HW * 4 + (size_t)kTileB * 4 + 1024;
+    return TcCfg<PREC>::S * (Lt::A_STAGE + Lt::B_STAGE) + nbuf * ((size_t)6 * HW * 4 + (size_t)kTileB * 4) + 1024;
 }
+// two table buffers (the next tile prefetched) when they fit, else one
+template <int PREC>
+int tc_nbuf(int HW) { return tc_smem<PREC>(HW, 2) <= 227 * 1024 ? 2 : 1; }
+template <int PREC>
+size_t tc_smem(int HW) { return tc_smem<PREC>(HW, tc_nbuf<PREC>(HW)); }
 
 int prep_groups(const Plan& P) { return (P.opt.max_rhs + kRhsPerCta - 1) / kRhsPerCta; }
 int prep_rows(const Plan& P) { return ((2 * std::min(kRhsPerCta, P.opt.max_rhs) + 15) / 16) * 16; }
@@ -453,7 +496,7 @@ cudaError_t launch_tc(const ContractArgs& A, const Plan& P, int n_rhs, cudaStrea
     if (e) return e;
     dim3 grid(P.n_ta, n_modes, G);
     k_contract_tc<PREC><<<grid, kThreads, smem, st>>>(A, n_rhs, Galloc, npb, (const unsigned char*)P.d_bprep,
-                                                      P.d_status);
+                                                      tc_nbuf<PREC>(P.H * P.W), P.d_status);
     return cudaGetLastError();
 }
 

@@ -72,11 +72,23 @@ struct Tiling {
     int n_tiles = 0, n_pad = 0, max_w = 0, max_h = 0;
 };
 
-Tiling make_tiling(const int32_t* xy, int n, int T) {
+// row_major: inside each tile, order the sites by (y, x), so that the threads
+// of a warp (consecutive rows of a pad tile) gather table cells that are
+// neighbours along x -- consecutive shared-memory records, not records a
+// sub-box width apart, which share banks.  Each pad column's sum over the
+// interface columns keeps its order, so results do not change.
+Tiling make_tiling(const int32_t* xy, int n, int T, bool row_major) {
     Tiling t;
     std::vector<int> idx(n);
     std::iota(idx.begin(), idx.end(), 0);
     bisect(xy, idx, 0, n, T);
+    if (row_major)
+        for (int lo = 0; lo < n; lo += T)
+            std::sort(idx.begin() + lo, idx.begin() + std::min(n, lo + T), [&](int a, int b) {
+                if (xy[2 * a + 1] != xy[2 * b + 1]) return xy[2 * a + 1] < xy[2 * b + 1];
+                if (xy[2 * a] != xy[2 * b]) return xy[2 * a] < xy[2 * b];
+                return a < b;
+            });
     t.n_tiles = (n + T - 1) / T;
     t.n_pad = t.n_tiles * T;
     t.perm.assign(t.n_pad, -1);
@@ -339,8 +351,8 @@ int fbc_plan_create(const fbc_geometry* geom, const fbc_material* mat, const fbc
 
     // tiling
     fbc::Plan* pp = &P;
-    Tiling ta = make_tiling(geom->xy_p, n_p, P.TA);
-    Tiling tb = make_tiling(geom->xy_i, n_i, P.TB);
+    Tiling ta = make_tiling(geom->xy_p, n_p, P.TA, true);
+    Tiling tb = make_tiling(geom->xy_i, n_i, P.TB, false);
     P.n_ta = ta.n_tiles, P.n_tb = tb.n_tiles, P.NPpad = ta.n_pad, P.NIpad = tb.n_pad;
     P.W = ta.max_w + tb.max_w - 1;
     P.H = ta.max_h + tb.max_h - 1;
