@@ -51,6 +51,7 @@ constexpr int kBuilders = kBuilderWarps * 32;
 constexpr int kMmaWarp = 8, kCopyWarp = 9;
 constexpr int kThreads = 10 * 32;
 constexpr int kStagesPerTile = kTileB / kKC;
+constexpr uint32_t kAcol = 384;  // first TMEM column of the A operand (after 3 x 128 accumulator columns)
 
 using tc::idesc;
 using tc::sdesc;
@@ -60,15 +61,18 @@ template <int PREC>
 struct TcCfg;
 template <>
 struct TcCfg<FBC_PREC_TF32> {
-    static constexpr int ES = 4, NS = 1, NPROD = 1, KMMA = 8, FMT = 2, S = 2;
+    static constexpr int ES = 4, NS = 1, NPROD = 1, KMMA = 8, FMT = 2, S = 3;
+    static constexpr bool ATM = true;  // A operand in tensor memory
 };
 template <>
 struct TcCfg<FBC_PREC_BF16X2> {
-    static constexpr int ES = 2, NS = 2, NPROD = 3, KMMA = 16, FMT = 1, S = 2;
+    static constexpr int ES = 2, NS = 2, NPROD = 3, KMMA = 16, FMT = 1, S = 3;
+    static constexpr bool ATM = true;
 };
 template <>
 struct TcCfg<FBC_PREC_BF16X3> {
     static constexpr int ES = 2, NS = 3, NPROD = 6, KMMA = 16, FMT = 1, S = 1;
+    static constexpr bool ATM = false;  // 18 A blocks do not fit beside the accumulators
 };
 
 template <int PREC>
@@ -77,15 +81,16 @@ struct TcLayout {
     static constexpr int KPC = 16 / C::ES;                    // K elements per 16-byte core row
     static constexpr uint32_t SBO = (kKC / KPC) * 128;        // bytes per 8-row group of a [rows][16] block
     static constexpr size_t ABLK = (size_t)kRows * kKC * C::ES;
-    static constexpr size_t A_STAGE = 6 * C::NS * ABLK;
+    static constexpr size_t A_STAGE = C::ATM ? 0 : 6 * C::NS * ABLK;  // shared-memory A stage
+    static constexpr uint32_t ACOLS = (uint32_t)(kKC * C::ES / 4);         // TMEM columns of one A block
     static constexpr size_t B_STAGE = 3 * C::NS * (size_t)kNPB * kKC * C::ES;  // allocated for 128 rows
 };
 
-// (piece of A, piece of B) for each split product, by decreasing magnitude
-__constant__ int c_prod_a[6] = {0, 0, 1, 0, 2, 1};
-__constant__ int c_prod_b[6] = {0, 1, 0, 2, 0, 1};
-// table component of M for (c_out, c_in); the (0, 2) and (1, 2) entries are negated
-__constant__ int c_ent[3][3] = {{0, 1, 4}, {1, 2, 5}, {4, 5, 3}};
+// Products issued per stage, fully unrolled: for output component co and
+// input component ci the table entry kEnt[co][ci] of M (the (0, 2) and (1, 2)
+// entries negated through the instruction descriptor), and for split product
+// pr the pieces (kPa[pr], kPb[pr]) of the A and B operands, by decreasing
+// magnitude: hh, hm, mh, hl, lh, mm.
 
 // Split x into NS pieces of the operand type; returned as raw bits (bf16 in
 // the low 16 bits, or the tf32 bit pattern).  FP32 arithmetic throughout: each
@@ -229,7 +234,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     using Lt = TcLayout<PREC>;
     constexpr int S = C::S, KPC = Lt::KPC;
     extern __shared__ __align__(1024) unsigned char smem[];
-    __shared__ uint64_t full[S], bfull[S], empty[S], done;
+    __shared__ uint64_t full[S], bfull[S], empty[S], done, afull, aempty;
     __shared__ uint32_t tbase;
     __shared__ volatile int s_abort;
 
@@ -254,6 +259,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         s_abort = 0;
         for (int s = 0; s < S; s++) mbar_init(&full[s], kBuilderWarps), mbar_init(&bfull[s], 1), mbar_init(&empty[s], 1);
         mbar_init(&done, 1);
+        mbar_init(&afull, kBuilderWarps), mbar_init(&aempty, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 0) {
@@ -289,40 +295,64 @@ __global__ void __launch_bounds__(kThreads, 1)
         // ---- tensor-core issue ----
         if (lane == 0) {
             const uint32_t id = idesc(C::FMT, kRows, NP), idn = id | (1u << 13);  // bit 13: negate A
-            bool acc[3] = {false, false, false};
+            // descriptor of B block 0 of stage 0; the others differ by (byte offset >> 4) in the address field
+            const uint64_t dB0 = sdesc(smem_u32(sB), 128, Lt::SBO);
+            const uint64_t dA0 = sdesc(smem_u32(sA), 128, Lt::SBO);
+            const uint32_t bblk16 = (uint32_t)(bblk >> 4);
             for (int it = 0; it < n_it; it++) {
                 const int s = it % S;
                 const uint32_t par = (uint32_t)(it / S) & 1u;
-                if (!wait_or_abort(&full[s], par, &s_abort) || !wait_or_abort(&bfull[s], par, &s_abort)) {
+                uint64_t* af = C::ATM ? &afull : &full[s];
+                const uint32_t apar = C::ATM ? ((uint32_t)it & 1u) : par;
+                if (!wait_or_abort(af, apar, &s_abort) || !wait_or_abort(&bfull[s], par, &s_abort)) {
                     s_abort = 1;
                     break;
                 }
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                const uint32_t a0 = smem_u32(sA + s * Lt::A_STAGE), b0 = smem_u32(sB + s * Lt::B_STAGE);
-#pragma unroll 1
+                const uint64_t dBs = dB0 + (uint64_t)((s * Lt::B_STAGE) >> 4);
+                const uint64_t dAs = dA0 + (uint64_t)((s * Lt::A_STAGE) >> 4);
+                const uint32_t first = it == 0 ? 0u : 1u;
+#pragma unroll
                 for (int co = 0; co < 3; co++)
-#pragma unroll 1
-                    for (int ci = 0; ci < 3; ci++) {
-                        const uint32_t idd = (ci == 2 && co < 2) ? idn : id;
-#pragma unroll 1
+#pragma unroll
+                    for (int ci = 0; ci < 3; ci++)
+#pragma unroll
                         for (int pr = 0; pr < C::NPROD; pr++)
 #pragma unroll
                             for (int ks = 0; ks < kKC / C::KMMA; ks++) {
-                                const uint32_t aa =
-                                    a0 + (uint32_t)((c_ent[co][ci] * C::NS + c_prod_a[pr]) * Lt::ABLK) + 256 * ks;
-                                const uint32_t bb = b0 + (uint32_t)((ci * C::NS + c_prod_b[pr]) * bblk) + 256 * ks;
-                                const uint64_t da = sdesc(aa, 128, Lt::SBO), db = sdesc(bb, 128, Lt::SBO);
+                                constexpr int kEnt[3][3] = {{0, 1, 4}, {1, 2, 5}, {4, 5, 3}};
+                                constexpr int kPa[6] = {0, 0, 1, 0, 2, 1}, kPb[6] = {0, 1, 0, 2, 0, 1};
+                                const int ablk = kEnt[co][ci] * C::NS + kPa[pr];
+                                const uint64_t db = dBs + (uint64_t)((ci * C::NS + kPb[pr]) * bblk16 + 16 * ks);
+                                const uint32_t idd = (ci == 2 && co < 2) ? idn : id;
                                 const uint32_t dt = tmem + (uint32_t)(co * NP);
-                                if (C::FMT == 2)
-                                    asm volatile(
-                                        "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-                                        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(dt),
-                                        "l"(da), "l"(db), "r"(idd), "r"(acc[co] ? 1u : 0u));
-                                else
-                                    tc::mma_bf16(dt, da, db, idd, acc[co] ? 1u : 0u);
-                                acc[co] = true;
+                                // the first product into each accumulator overwrites it
+                                const uint32_t en = (ci | pr | ks) ? 1u : first;
+                                if (C::ATM) {
+                                    // A from tensor memory: block ablk, K step ks (8 columns per MMA)
+                                    const uint32_t ta = tmem + kAcol + (uint32_t)ablk * Lt::ACOLS + 8u * ks;
+                                    if (C::FMT == 2)
+                                        asm volatile(
+                                            "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                                            "tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n}\n" ::"r"(dt),
+                                            "r"(ta), "l"(db), "r"(idd), "r"(en));
+                                    else
+                                        asm volatile(
+                                            "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                                            "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}\n" ::"r"(dt),
+                                            "r"(ta), "l"(db), "r"(idd), "r"(en));
+                                } else {
+                                    const uint64_t da = dAs + (uint64_t)((ablk * Lt::ABLK + 256 * ks) >> 4);
+                                    if (C::FMT == 2)
+                                        asm volatile(
+                                            "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                                            "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(dt),
+                                            "l"(da), "l"(db), "r"(idd), "r"(en));
+                                    else
+                                        tc::mma_bf16(dt, da, db, idd, en);
+                                }
                             }
-                    }
+                if (C::ATM) tc::commit(&aempty);
                 tc::commit(&empty[s]);
             }
             tc::commit(&done);  // also after a stop: fires once the issued products are complete
@@ -373,7 +403,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             for (int st = 0; st < kStagesPerTile; st++, it++) {
                 const int s = it % S;
                 const uint32_t u = (uint32_t)(it / S);
-                if (s_abort || !wait_or_abort(&empty[s], (u & 1u) ^ 1u, &s_abort)) {
+                if (!C::ATM && (s_abort || !wait_or_abort(&empty[s], (u & 1u) ^ 1u, &s_abort))) {
                     s_abort = 1;
                     continue;  // keep the barrier count of the other builders
                 }
@@ -386,7 +416,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                     const float2 p0 = src[0], p1 = src[1], p2 = src[2];
                     v[i][0] = p0.x, v[i][1] = p0.y, v[i][2] = p1.x, v[i][3] = p1.y, v[i][4] = p2.x, v[i][5] = p2.y;
                 }
-                unsigned char* dstA = sA + s * Lt::A_STAGE;
+                // split into NS pieces: four 32-bit words (eight bf16, or four tf32 twice) per entry and piece
+                uint32_t wq[6][C::NS][4], wt[6][2][4];
 #pragma unroll
                 for (int e = 0; e < 6; e++) {
                     float x[8];
@@ -395,34 +426,80 @@ __global__ void __launch_bounds__(kThreads, 1)
                     if (C::ES == 2) {
                         // bf16 pieces two at a time: packed round-to-nearest conversion, exact FP32 remainders
 #pragma unroll
-                        for (int p = 0; p < C::NS; p++) {
-                            uint32_t w[4];
+                        for (int p = 0; p < C::NS; p++)
 #pragma unroll
                             for (int i = 0; i < 4; i++) {
-                                asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(w[i]) : "f"(x[2 * i + 1]), "f"(x[2 * i]));
+                                uint32_t w;
+                                asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(w) : "f"(x[2 * i + 1]), "f"(x[2 * i]));
+                                wq[e][p][i] = w;
                                 if (p + 1 < C::NS) {
-                                    x[2 * i] = __fsub_rn(x[2 * i], __uint_as_float(w[i] << 16));
-                                    x[2 * i + 1] = __fsub_rn(x[2 * i + 1], __uint_as_float(w[i] & 0xffff0000u));
+                                    x[2 * i] = __fsub_rn(x[2 * i], __uint_as_float(w << 16));
+                                    x[2 * i + 1] = __fsub_rn(x[2 * i + 1], __uint_as_float(w & 0xffff0000u));
                                 }
                             }
-                            const uint32_t off = (uint32_t)(a_loc / 8) * Lt::SBO + hb * 128 + (a_loc % 8) * 16;
-                            *(uint4*)(dstA + (size_t)(e * C::NS + p) * Lt::ABLK + off) = make_uint4(w[0], w[1], w[2], w[3]);
-                        }
                     } else {
 #pragma unroll
-                        for (int q = 0; q < 2; q++) {
-                            uint32_t w[4];
+                        for (int q = 0; q < 2; q++)
 #pragma unroll
-                            for (int i = 0; i < 4; i++) asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(w[i]) : "f"(x[4 * q + i]));
-                            const int kc = hb * 2 + q;
-                            const uint32_t off = (uint32_t)(a_loc / 8) * Lt::SBO + kc * 128 + (a_loc % 8) * 16;
-                            *(uint4*)(dstA + (size_t)e * Lt::ABLK + off) = make_uint4(w[0], w[1], w[2], w[3]);
-                        }
+                            for (int i = 0; i < 4; i++) asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(wt[e][q][i]) : "f"(x[4 * q + i]));
                     }
                 }
-                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                __syncwarp();
-                if (lane == 0) mbar_arrive(&full[s]);
+                if (C::ATM) {
+                    // the tensor-memory A buffer is free once the previous stage's products are complete
+                    if (s_abort || !wait_or_abort(&aempty, ((uint32_t)it & 1u) ^ 1u, &s_abort)) {
+                        s_abort = 1;
+                        continue;
+                    }
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    // lane = row a_loc; columns: block * ACOLS + this thread's K half
+                    const uint32_t trow = tmem + ((uint32_t)((warp & 3) * 32) << 16) + kAcol;
+#pragma unroll
+                    for (int e = 0; e < 6; e++) {
+                        if (C::ES == 2) {
+#pragma unroll
+                            for (int p = 0; p < C::NS; p++)
+                                asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1, %2, %3, %4};" ::"r"(
+                                                 trow + (uint32_t)(e * C::NS + p) * Lt::ACOLS + 4u * hb),
+                                             "r"(wq[e][p][0]), "r"(wq[e][p][1]), "r"(wq[e][p][2]), "r"(wq[e][p][3])
+                                             : "memory");
+                        } else {
+                            asm volatile(
+                                "tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"r"(
+                                    trow + (uint32_t)e * Lt::ACOLS + 8u * hb),
+                                "r"(wt[e][0][0]), "r"(wt[e][0][1]), "r"(wt[e][0][2]), "r"(wt[e][0][3]), "r"(wt[e][1][0]),
+                                "r"(wt[e][1][1]), "r"(wt[e][1][2]), "r"(wt[e][1][3])
+                                : "memory");
+                        }
+                    }
+                    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+                    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&afull);
+                } else {
+                    unsigned char* dstA = sA + s * Lt::A_STAGE;
+#pragma unroll
+                    for (int e = 0; e < 6; e++) {
+                        if (C::ES == 2) {
+#pragma unroll
+                            for (int p = 0; p < C::NS; p++) {
+                                const uint32_t off = (uint32_t)(a_loc / 8) * Lt::SBO + hb * 128 + (a_loc % 8) * 16;
+                                *(uint4*)(dstA + (size_t)(e * C::NS + p) * Lt::ABLK + off) =
+                                    make_uint4(wq[e][p][0], wq[e][p][1], wq[e][p][2], wq[e][p][3]);
+                            }
+                        } else {
+#pragma unroll
+                            for (int q = 0; q < 2; q++) {
+                                const int kc = hb * 2 + q;
+                                const uint32_t off = (uint32_t)(a_loc / 8) * Lt::SBO + kc * 128 + (a_loc % 8) * 16;
+                                *(uint4*)(dstA + (size_t)e * Lt::ABLK + off) =
+                                    make_uint4(wt[e][q][0], wt[e][q][1], wt[e][q][2], wt[e][q][3]);
+                            }
+                        }
+                    }
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&full[s]);
+                }
             }
         }
         asm volatile("cp.async.wait_all;" ::: "memory");  // a prefetch still in flight after a stop
