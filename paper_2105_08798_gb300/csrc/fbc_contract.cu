@@ -296,6 +296,26 @@ __device__ __forceinline__ void tile_x2(const ContractArgs& A, int tA, int k, in
         __syncthreads();
         const int base = (xa.x - ox) + A.W * (xa.y - oy);
         float S[6] = {0, 0, 0, 0, 0, 0}, E[6] = {0, 0, 0, 0, 0, 0};
+        if (k == 0) {
+            // k = 0: g^0 is real (B13 = B23 = 0) and so are the k = 0 forces, so of the
+            // six outputs only x_0, x_1 and y'_2 are non-zero: 5 of the 18 products, in the
+            // order the general loop adds them (the imaginary slots, which the inverse
+            // transform discards at k = 0, are written as zeros below)
+#pragma unroll 4
+            for (int j = 0; j < TB; j++) {
+                const float4 f0 = s_f[4 * j], f2 = s_f[4 * j + 2], f3 = s_f[4 * j + 3];
+                const int idx = base - __float_as_int(f3.x);
+                const float4 t0 = s_tab[3 * idx], t1 = s_tab[3 * idx + 1];
+                df_mac(t0.x, t0.y, f0.x, f0.y, S[0], E[0]);
+                df_mac(t0.z, t0.w, f0.z, f0.w, S[0], E[0]);
+                df_mac(t0.z, t0.w, f0.x, f0.y, S[1], E[1]);
+                df_mac(t1.x, t1.y, f0.z, f0.w, S[1], E[1]);
+                df_mac(t1.z, t1.w, f2.z, f2.w, S[5], E[5]);
+            }
+#pragma unroll
+            for (int c = 0; c < 6; c++) df_fold(Th[c], Tl[c], S[c], E[c]);
+            continue;
+        }
 #pragma unroll 2
         for (int j = 0; j < TB; j++) {
             const float4 f0 = s_f[4 * j], f1 = s_f[4 * j + 1], f2 = s_f[4 * j + 2], f3 = s_f[4 * j + 3];
@@ -327,6 +347,7 @@ __device__ __forceinline__ void tile_x2(const ContractArgs& A, int tA, int k, in
     double* o = A.uh + (((size_t)r * A.K + k) * A.NPpad + a) * 6;
 #pragma unroll
     for (int c = 0; c < 6; c++) o[c] = (double)Th[c] + (double)Tl[c];
+    if (k == 0) o[2] = o[3] = o[4] = 0.0;
 }
 
 
