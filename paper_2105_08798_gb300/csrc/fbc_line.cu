@@ -45,6 +45,39 @@ struct Cx<float> {
     __device__ static T make(float x, float y) { return make_float2(x, y); }
 };
 
+// GB300's FP64 pipe runs at about 1/64 of the FP32 rate, and conversions
+// between double and float issue there too.  The FP32 forms therefore convert
+// with integer bit arithmetic and keep one FP64 add per output element (the
+// k = 0 term).
+// double -> float, rounded to nearest (ties away from zero); magnitudes below
+// 2^-126 become signed zero (no overflow for the values transformed here).
+__device__ __forceinline__ float d2f_int(double x) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const unsigned int hi = (unsigned int)(b >> 32), lo = (unsigned int)b;
+    const unsigned int sign = hi & 0x80000000u;
+    const int e = (int)((hi >> 20) & 0x7ffu) - 1023 + 127;
+    if (e <= 0) return __uint_as_float(sign);
+    unsigned int r = ((unsigned int)e << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29);
+    r += (lo >> 28) & 1u;  // a carry out of the mantissa raises the exponent, as it should
+    return __uint_as_float(sign | r);
+}
+// float -> double, exact; zero and FP32 subnormals become signed zero.
+__device__ __forceinline__ double f2d_int(float x) {
+    const unsigned int b = __float_as_uint(x);
+    const unsigned int sign = b & 0x80000000u, e = (b >> 23) & 0xffu;
+    if (e == 0) return __longlong_as_double((long long)((unsigned long long)sign << 32));
+    const unsigned int hi = sign | ((e + 896u) << 20) | ((b & 0x7fffffu) >> 3);
+    const unsigned int lo = (b & 7u) << 29;
+    return __longlong_as_double((long long)(((unsigned long long)hi << 32) | lo));
+}
+// (sh, sl) += v with an exact two-sum (double-float accumulation on the FP32 pipes)
+__device__ __forceinline__ void df_acc(float v, float& sh, float& sl) {
+    const float t = __fadd_rn(sh, v);
+    const float bb = __fsub_rn(t, sh);
+    sl = __fadd_rn(sl, __fadd_rn(__fsub_rn(sh, __fsub_rn(t, bb)), __fsub_rn(v, bb)));
+    sh = t;
+}
+
 template <typename T2>
 __device__ __forceinline__ T2 cmul(T2 a, T2 b) {
     T2 r;
@@ -105,9 +138,14 @@ __device__ __forceinline__ void fwd_block(const double* __restrict__ f, const in
             f1 = src[0], f2 = src[1], f3 = src[2];
         }
         const int qr = bitrev(q, logL);
-        zs[(size_t)j * L + qr] = Cx<R>::make((R)f1, (R)f2);
         R* wp = (R*)&ws[(size_t)(j >> 1) * L + qr];
-        wp[j & 1] = (R)f3;
+        if constexpr (kF32) {
+            zs[(size_t)j * L + qr] = Cx<R>::make(d2f_int(f1), d2f_int(f2));
+            wp[j & 1] = d2f_int(f3);
+        } else {
+            zs[(size_t)j * L + qr] = Cx<R>::make((R)f1, (R)f2);
+            wp[j & 1] = (R)f3;
+        }
     }
     if (kF32) {
         // one warp per column: lane-strided FP64 sums, then a fixed shuffle tree (deterministic)
@@ -137,15 +175,26 @@ __device__ __forceinline__ void fwd_block(const double* __restrict__ f, const in
         const T2 Z = zs[(size_t)j * L + k], Zm = zs[(size_t)j * L + km];
         const T2 Wv = ws[(size_t)(j >> 1) * L + k], Wm = ws[(size_t)(j >> 1) * L + km];
         // F1 = (Z + conj Zm) / 2, F2 = (Z - conj Zm) / (2i)
-        double F1r = 0.5 * ((double)Z.x + Zm.x), F1i = 0.5 * ((double)Z.y - Zm.y);
-        double F2r = 0.5 * ((double)Z.y + Zm.y), F2i = -0.5 * ((double)Z.x - Zm.x);
-        double F3r, F3i;
-        if ((j & 1) == 0) {
-            F3r = 0.5 * ((double)Wv.x + Wm.x), F3i = 0.5 * ((double)Wv.y - Wm.y);
+        double F1r, F1i, F2r, F2i, F3r, F3i;
+        if constexpr (kF32) {
+            // unpack in FP32, widen exactly
+            F1r = f2d_int(0.5f * (Z.x + Zm.x)), F1i = f2d_int(0.5f * (Z.y - Zm.y));
+            F2r = f2d_int(0.5f * (Z.y + Zm.y)), F2i = f2d_int(-0.5f * (Z.x - Zm.x));
+            if ((j & 1) == 0) {
+                F3r = f2d_int(0.5f * (Wv.x + Wm.x)), F3i = f2d_int(0.5f * (Wv.y - Wm.y));
+            } else {
+                F3r = f2d_int(0.5f * (Wv.y + Wm.y)), F3i = f2d_int(-0.5f * (Wv.x - Wm.x));
+            }
+            if (k == 0) F1r = s0[j][0], F2r = s0[j][1], F3r = s0[j][2], F1i = F2i = F3i = 0.0;
         } else {
-            F3r = 0.5 * ((double)Wv.y + Wm.y), F3i = -0.5 * ((double)Wv.x - Wm.x);
+            F1r = 0.5 * ((double)Z.x + Zm.x), F1i = 0.5 * ((double)Z.y - Zm.y);
+            F2r = 0.5 * ((double)Z.y + Zm.y), F2i = -0.5 * ((double)Z.x - Zm.x);
+            if ((j & 1) == 0) {
+                F3r = 0.5 * ((double)Wv.x + Wm.x), F3i = 0.5 * ((double)Wv.y - Wm.y);
+            } else {
+                F3r = 0.5 * ((double)Wv.y + Wm.y), F3i = -0.5 * ((double)Wv.x - Wm.x);
+            }
         }
-        if (kF32 && k == 0) F1r = s0[j][0], F2r = s0[j][1], F3r = s0[j][2], F1i = F2i = F3i = 0.0;
         double* o = fh + (((size_t)r * K + k) * NIpad + b0 + j) * 6;
         if (perm[b0 + j] < 0) {
             o[0] = o[1] = o[2] = o[3] = o[4] = o[5] = 0.0;
@@ -210,14 +259,25 @@ __device__ __forceinline__ void inv_block(const double* __restrict__ uh, const i
     for (int t = threadIdx.x; t < NC * K; t += blockDim.x) {
         const int k = t / NC, j = t % NC;
         const double* src = uh + (((size_t)r * K + k) * NPpad + a0 + j) * 6;
+        if constexpr (kF32) {
+            // k = 0 kept in FP64 beside the transform; the rest converted on the integer pipes
+            float U1r, U1i, U2r, U2i;
+            if (k == 0) {
+                u0[j][0] = src[0], u0[j][1] = src[1];
+                U1r = U2r = U1i = U2i = 0.f;
+            } else {
+                U1r = d2f_int(src[0]), U2r = d2f_int(src[1]);
+                U1i = k == Lh ? 0.f : d2f_int(src[3]);
+                U2i = k == Lh ? 0.f : d2f_int(src[4]);
+            }
+            zs[(size_t)j * L + bitrev(k, logL)] = Cx<R>::make(U1r - U2i, U1i + U2r);
+            if (k != 0 && k != Lh) zs[(size_t)j * L + bitrev(L - k, logL)] = Cx<R>::make(U1r + U2i, U2r - U1i);
+            continue;
+        }
         const double x0 = src[0], x1 = src[1], y0 = src[3], y1 = src[4];
         // U1 = x0 + i y0, U2 = x1 + i y1 (U3 is handled per column pair below)
         double U1r = x0, U1i = y0, U2r = x1, U2i = y1;
         if (k == 0 || k == Lh) U1i = U2i = 0.0;
-        if (kF32 && k == 0) {
-            u0[j][0] = U1r, u0[j][1] = U2r;
-            U1r = U2r = 0.0;
-        }
         // Z(k) = U1 + i U2 ; Z(L-k) = conj U1 + i conj U2
         zs[(size_t)j * L + bitrev(k, logL)] = Cx<R>::make((R)(U1r - U2i), (R)(U1i + U2r));
         if (k != 0 && k != Lh)
@@ -228,65 +288,96 @@ __device__ __forceinline__ void inv_block(const double* __restrict__ uh, const i
         const int k = t / (NC / 2), jp = t % (NC / 2);
         const double* se = uh + (((size_t)r * K + k) * NPpad + a0 + 2 * jp) * 6;
         const double* so = se + 6;
+        if constexpr (kF32) {
+            float Er, Ei, Or, Oi;
+            if (k == 0) {
+                u0[2 * jp][2] = -se[5], u0[2 * jp + 1][2] = -so[5];
+                Er = Ei = Or = Oi = 0.f;
+            } else {
+                Er = -d2f_int(se[5]), Or = -d2f_int(so[5]);
+                Ei = k == Lh ? 0.f : d2f_int(se[2]);
+                Oi = k == Lh ? 0.f : d2f_int(so[2]);
+            }
+            ws[(size_t)jp * L + bitrev(k, logL)] = Cx<R>::make(Er - Oi, Ei + Or);
+            if (k != 0 && k != Lh) ws[(size_t)jp * L + bitrev(L - k, logL)] = Cx<R>::make(Er + Oi, Or - Ei);
+            continue;
+        }
         double Er = -se[5], Ei = se[2], Or = -so[5], Oi = so[2];
         if (k == 0 || k == Lh) Ei = Oi = 0.0;
-        if (kF32 && k == 0) {
-            u0[2 * jp][2] = Er, u0[2 * jp + 1][2] = Or;
-            Er = Or = 0.0;
-        }
         // W(k) = E + i O ; W(L-k) = conj E + i conj O
         ws[(size_t)jp * L + bitrev(k, logL)] = Cx<R>::make((R)(Er - Oi), (R)(Ei + Or));
         if (k != 0 && k != Lh) ws[(size_t)jp * L + bitrev(L - k, logL)] = Cx<R>::make((R)(Er + Oi), (R)(Or - Ei));
     }
     __syncthreads();
     fft_block<R>(zs, NC + NC / 2, L, logL, tw, true);
-    if (kF32) {
+    double ps0 = 0.0, ps1 = 0.0, ps2 = 0.0;
+    if constexpr (kF32) {
         // the k >= 1 modes sum to zero along the line: remove the mean their FP32
-        // transform picked up, so the k = 0 band keeps FP64 accuracy
-        __shared__ double mz[64][3];
+        // transform picked up (summed in double-float), so the k = 0 band keeps FP64
+        // accuracy; uk[j][c] = (alpha / L) (U_c(0) - mean) in FP64
+        __shared__ double uk[64][3];
         const int warp = threadIdx.x / 32, lane = threadIdx.x % 32, nw = blockDim.x / 32;
         for (int j = warp; j < NC; j += nw) {
-            double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+            float h0 = 0.f, l0 = 0.f, h1 = 0.f, l1 = 0.f, h2 = 0.f, l2 = 0.f;
             for (int p = lane; p < L; p += 32) {
                 const T2 z = zs[(size_t)j * L + p];
                 const T2 w = ws[(size_t)(j >> 1) * L + p];
-                a0 += z.x, a1 += z.y, a2 += (j & 1) ? w.y : w.x;
+                df_acc(z.x, h0, l0), df_acc(z.y, h1, l1), df_acc((j & 1) ? w.y : w.x, h2, l2);
             }
+            double a0 = f2d_int(h0) + f2d_int(l0), a1 = f2d_int(h1) + f2d_int(l1), a2 = f2d_int(h2) + f2d_int(l2);
             for (int o = 16; o > 0; o >>= 1) {
                 a0 += __shfl_xor_sync(0xffffffffu, a0, o);
                 a1 += __shfl_xor_sync(0xffffffffu, a1, o);
                 a2 += __shfl_xor_sync(0xffffffffu, a2, o);
             }
-            if (lane == 0) mz[j][0] = a0 / L, mz[j][1] = a1 / L, mz[j][2] = a2 / L;
+            if (lane == 0) {
+                uk[j][0] = alpha_over_L * (u0[j][0] - a0 / L);
+                uk[j][1] = alpha_over_L * (u0[j][1] - a1 / L);
+                uk[j][2] = alpha_over_L * (u0[j][2] - a2 / L);
+            }
         }
         __syncthreads();
-        if (threadIdx.x < NC) {
-            u0[threadIdx.x][0] -= mz[threadIdx.x][0];
-            u0[threadIdx.x][1] -= mz[threadIdx.x][1];
-            u0[threadIdx.x][2] -= mz[threadIdx.x][2];
+        const float af = (float)alpha_over_L;
+        for (int t = threadIdx.x; t < NC * L; t += blockDim.x) {
+            const int j = t / L, p = t % L;
+            const int oa = perm[a0 + j];
+            if (oa < 0) continue;
+            const T2 z = zs[(size_t)j * L + p];
+            const T2 w = ws[(size_t)(j >> 1) * L + p];
+            double* dst = u + (((size_t)r * n_p + oa) * L + p) * 3;
+            double o0 = f2d_int(af * z.x) + uk[j][0];
+            double o1 = f2d_int(af * z.y) + uk[j][1];
+            double o2 = f2d_int(af * ((j & 1) ? w.y : w.x)) + uk[j][2];
+            if (beta != 0.0) {
+                o0 = fma(beta, dst[0], o0);
+                o1 = fma(beta, dst[1], o1);
+                o2 = fma(beta, dst[2], o2);
+            }
+            dst[0] = o0;
+            dst[1] = o1;
+            dst[2] = o2;
+            if (want_part) ps0 += o0, ps1 += o1, ps2 += o2;
         }
-        __syncthreads();
-    }
-    double ps0 = 0.0, ps1 = 0.0, ps2 = 0.0;
-    for (int t = threadIdx.x; t < NC * L; t += blockDim.x) {
-        const int j = t / L, p = t % L;
-        const int oa = perm[a0 + j];
-        if (oa < 0) continue;
-        const T2 z = zs[(size_t)j * L + p];
-        const T2 w = ws[(size_t)(j >> 1) * L + p];
-        double z0 = z.x, z1 = z.y, v3 = (j & 1) ? w.y : w.x;
-        if (kF32) z0 += u0[j][0], z1 += u0[j][1], v3 += u0[j][2];
-        double* dst = u + (((size_t)r * n_p + oa) * L + p) * 3;
-        double o0 = alpha_over_L * z0, o1 = alpha_over_L * z1, o2 = alpha_over_L * v3;
-        if (beta != 0.0) {
-            o0 = fma(beta, dst[0], o0);
-            o1 = fma(beta, dst[1], o1);
-            o2 = fma(beta, dst[2], o2);
+    } else {
+        for (int t = threadIdx.x; t < NC * L; t += blockDim.x) {
+            const int j = t / L, p = t % L;
+            const int oa = perm[a0 + j];
+            if (oa < 0) continue;
+            const T2 z = zs[(size_t)j * L + p];
+            const T2 w = ws[(size_t)(j >> 1) * L + p];
+            const double z0 = z.x, z1 = z.y, v3 = (j & 1) ? w.y : w.x;
+            double* dst = u + (((size_t)r * n_p + oa) * L + p) * 3;
+            double o0 = alpha_over_L * z0, o1 = alpha_over_L * z1, o2 = alpha_over_L * v3;
+            if (beta != 0.0) {
+                o0 = fma(beta, dst[0], o0);
+                o1 = fma(beta, dst[1], o1);
+                o2 = fma(beta, dst[2], o2);
+            }
+            dst[0] = o0;
+            dst[1] = o1;
+            dst[2] = o2;
+            ps0 += o0, ps1 += o1, ps2 += o2;
         }
-        dst[0] = o0;
-        dst[1] = o1;
-        dst[2] = o2;
-        ps0 += o0, ps1 += o1, ps2 += o2;
     }
     if (want_part) {
         __shared__ double red[3][256];
