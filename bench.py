@@ -326,6 +326,16 @@ def run_ours(args, w):
             if prec != args.precision:
                 variant(prec, max(2, args.steps // 2))
         plan.set_precision(args.precision)
+        if args.precision in TENSOR and w.n_i > 1024:
+            # the same precision with the whole interface sum in one tensor-memory accumulation group
+            with fbc.Plan(xy_i, xy_p, w.L, w.material, precision=args.precision, max_rhs=R,
+                          tc_fast_accumulate=True) as p1:
+                p1.tabulate()
+                vms, vstage = time_device_steps(torch, p1, fd, ud, max(2, args.steps // 2), 2, flush_buf)
+                outputs["fast_accumulate"] = snap()
+                variants["fast_accumulate"] = {"precision": args.precision, "ms_per_step": float(np.mean(vms)),
+                                               "value": pm / (np.mean(vms) * 1e-3) / 1e9,
+                                               "contract_ms": float(vstage[1])}
 
     # end-to-end through the host entry point: pinned host f in, host u out
     fh = torch.from_numpy(f).pin_memory()

@@ -250,7 +250,9 @@ __device__ __forceinline__ void df_fold(float& Thi, float& Tlo, float S, float E
 // Double-float: each table entry is staged as three 16-byte records
 // (a11h, a11l, a12h, a12l), (a22h, a22l, a33h, a33l), (b13h, b13l, b23h, b23l)
 // and each interface column as four: the (hi, lo) pairs of x and y' and off_b.
-template <int TA, int TB>
+// K0: the tile of the one-mode k = 0 launches (a separate instance, so that the
+// all-modes loop keeps its own code).
+template <int TA, int TB, bool K0>
 __device__ __forceinline__ void tile_x2(const ContractArgs& A, int tA, int k, int r, void* smem_raw) {
     float4* smemx2 = (float4*)smem_raw;
     const int HW = A.H * A.W;
@@ -296,7 +298,7 @@ __device__ __forceinline__ void tile_x2(const ContractArgs& A, int tA, int k, in
         __syncthreads();
         const int base = (xa.x - ox) + A.W * (xa.y - oy);
         float S[6] = {0, 0, 0, 0, 0, 0}, E[6] = {0, 0, 0, 0, 0, 0};
-        if (k == 0) {
+        if (K0) {
             // k = 0: g^0 is real (B13 = B23 = 0) and so are the k = 0 forces, so of the
             // six outputs only x_0, x_1 and y'_2 are non-zero: 5 of the 18 products, in the
             // order the general loop adds them (the imaginary slots, which the inverse
@@ -347,7 +349,7 @@ __device__ __forceinline__ void tile_x2(const ContractArgs& A, int tA, int k, in
     double* o = A.uh + (((size_t)r * A.K + k) * A.NPpad + a) * 6;
 #pragma unroll
     for (int c = 0; c < 6; c++) o[c] = (double)Th[c] + (double)Tl[c];
-    if (k == 0) o[2] = o[3] = o[4] = 0.0;
+    if (K0) o[2] = o[3] = o[4] = 0.0;
 }
 
 
@@ -367,10 +369,10 @@ __global__ void __launch_bounds__(TA) k_contract_fp32_rb(ContractArgs A, int n_r
     extern __shared__ float4 smem_raw[];
     tile_fp32_rb<TA, TB, RB>(A, blockIdx.x, A.k0 + blockIdx.y, blockIdx.z, n_rhs, smem_raw);
 }
-template <int TA, int TB>
+template <int TA, int TB, bool K0>
 __global__ void __launch_bounds__(TA) k_contract_x2(ContractArgs A) {
     extern __shared__ float4 smem_raw[];
-    tile_x2<TA, TB>(A, blockIdx.x, A.k0 + blockIdx.y, blockIdx.z, smem_raw);
+    tile_x2<TA, TB, K0>(A, blockIdx.x, A.k0 + blockIdx.y, blockIdx.z, smem_raw);
 }
 
 // ---- batched: one persistent launch drains a cost-sorted work list ----------
@@ -395,8 +397,10 @@ __global__ void __launch_bounds__(TA) k_batch_contract(const ContractArgs* __res
         const ContractArgs A = args[w.x];
         if (PREC == FBC_PREC_FP64) {
             tile_fp64<TA, TB>(A, w.z, w.y, w.w, smem_raw);
-        } else if (PREC == FBC_PREC_F32X2 || PHASE == 0) {
-            tile_x2<TA, TB>(A, w.z, w.y, w.w, smem_raw);
+        } else if (PREC == FBC_PREC_F32X2) {
+            tile_x2<TA, TB, false>(A, w.z, w.y, w.w, smem_raw);
+        } else if (PHASE == 0) {
+            tile_x2<TA, TB, true>(A, w.z, w.y, w.w, smem_raw);  // the k = 0 items
         } else {
             tile_fp32_rb<TA, TB, kBatchRB>(A, w.z, w.y, w.w, n_rhs_arr[w.x], smem_raw);
         }
@@ -432,7 +436,7 @@ cudaError_t launch_contract(Plan& P, int n_rhs, cudaStream_t st) {
     }
     if (P.precision == FBC_PREC_FP32) {
         // logarithmic k = 0 mode in double-float (FP64-accurate), the rest in FP32
-        cudaError_t e = launch_one(k_contract_x2<kTileA, kTileB>, A, dim3(P.n_ta, 1, n_rhs), kTileA, sx2, st);
+        cudaError_t e = launch_one(k_contract_x2<kTileA, kTileB, true>, A, dim3(P.n_ta, 1, n_rhs), kTileA, sx2, st);
         if (e || P.K < 2) return e;
         A.k0 = 1;
         if (n_rhs >= 2) {
@@ -446,13 +450,13 @@ cudaError_t launch_contract(Plan& P, int n_rhs, cudaStream_t st) {
     }
     if (is_tensor_precision(P.precision)) {
         // logarithmic k = 0 mode in double-float (FP64-accurate) on the CUDA cores, k >= 1 on the tensor cores
-        cudaError_t e = launch_one(k_contract_x2<kTileA, kTileB>, A, dim3(P.n_ta, 1, n_rhs), kTileA, sx2, st);
+        cudaError_t e = launch_one(k_contract_x2<kTileA, kTileB, true>, A, dim3(P.n_ta, 1, n_rhs), kTileA, sx2, st);
         if (e || P.K < 2) return e;
         A.k0 = 1;
         return launch_contract_tc(A, P, n_rhs, st);
     }
     if (P.precision == FBC_PREC_F32X2) {
-        return launch_one(k_contract_x2<kTileA, kTileB>, A, dim3(P.n_ta, P.K, n_rhs), kTileA, sx2, st);
+        return launch_one(k_contract_x2<kTileA, kTileB, false>, A, dim3(P.n_ta, P.K, n_rhs), kTileA, sx2, st);
     }
     return cudaErrorInvalidValue;
 }
@@ -471,7 +475,7 @@ ContractArgs make_contract_args(const Plan& P) {
 
 cudaError_t launch_contract_x2_k0(Plan& P, const ContractArgs& A, int n_rhs, cudaStream_t st) {
     const size_t sx2 = (size_t)P.H * P.W * 48 + (size_t)kTileB * 64 + 16;
-    return launch_one(k_contract_x2<kTileA, kTileB>, A, dim3(P.n_ta, 1, n_rhs), kTileA, sx2, st);
+    return launch_one(k_contract_x2<kTileA, kTileB, true>, A, dim3(P.n_ta, 1, n_rhs), kTileA, sx2, st);
 }
 
 cudaError_t launch_contract_modes(Plan& P, const ContractArgs& A0, int k0, int n_modes, int n_rhs, cudaStream_t st) {

@@ -51,6 +51,7 @@ constexpr int kBuilders = kBuilderWarps * 32;
 constexpr int kMmaWarp = 8, kCopyWarp = 9;
 constexpr int kThreads = 10 * 32;
 constexpr int kStagesPerTile = kTileB / kKC;
+constexpr int kDrainTiles = 16;  // interface tiles per tensor-memory accumulation group
 constexpr uint32_t kAcol = 384;  // first TMEM column of the A operand (after 3 x 128 accumulator columns)
 
 using tc::idesc;
@@ -229,7 +230,7 @@ __global__ void k_prep_b(const double* __restrict__ fh, int K, int NIpad, int n_
 template <int PREC>
 __global__ void __launch_bounds__(kThreads, 1)
     k_contract_tc(ContractArgs A, int n_rhs, int G, int npb, const unsigned char* __restrict__ bprep, int nbuf,
-                  int* status) {
+                  int gs, int* status) {
     using C = TcCfg<PREC>;
     using Lt = TcLayout<PREC>;
     constexpr int S = C::S, KPC = Lt::KPC;
@@ -299,6 +300,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             const uint64_t dB0 = sdesc(smem_u32(sB), 128, Lt::SBO);
             const uint64_t dA0 = sdesc(smem_u32(sA), 128, Lt::SBO);
             const uint32_t bblk16 = (uint32_t)(bblk >> 4);
+            int gpos = 0;  // position of the stage in its accumulation group
             for (int it = 0; it < n_it; it++) {
                 const int s = it % S;
                 const uint32_t par = (uint32_t)(it / S) & 1u;
@@ -311,7 +313,9 @@ __global__ void __launch_bounds__(kThreads, 1)
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 const uint64_t dBs = dB0 + (uint64_t)((s * Lt::B_STAGE) >> 4);
                 const uint64_t dAs = dA0 + (uint64_t)((s * Lt::A_STAGE) >> 4);
-                const uint32_t first = it == 0 ? 0u : 1u;
+                // a new accumulation group starts by overwriting the accumulators
+                const uint32_t first = gpos == 0 ? 0u : 1u;
+                if (++gpos == gs) gpos = 0;
 #pragma unroll
                 for (int co = 0; co < 3; co++)
 #pragma unroll
@@ -382,7 +386,45 @@ __global__ void __launch_bounds__(kThreads, 1)
             if (tid < kTileB / 4) cp_async16(s_off + buf * kTileB + 4 * tid, A.off_i + tB * kTileB + 4 * tid);
             asm volatile("cp.async.commit_group;" ::: "memory");
         };
-        int it = 0;
+        // Accumulators -> uh.  The FP32 accumulation in tensor memory truncates at every
+        // step, so the interface sum is split into groups of gs stages whose partial sums
+        // are added here with round-to-nearest FP32 adds (conversions on the integer
+        // pipes); the first group writes, the later ones add.
+        const uint32_t tacc = tmem + ((uint32_t)((warp & 3) * 32) << 16);
+        auto drain = [&](bool add) {
+            for (int c0 = hb * 16; c0 < NP; c0 += 32) {
+                float v0[16], v1[16], v2[16];
+                tc::ld16(tacc + (uint32_t)c0, v0);
+                tc::ld16(tacc + (uint32_t)(NP + c0), v1);
+                tc::ld16(tacc + (uint32_t)(2 * NP + c0), v2);
+#pragma unroll
+                for (int h = 0; h < 2; h++) {
+                    // four right-hand sides at a time: every load issued before any store
+                    double2 q[4][3];
+                    double2* o[4];
+#pragma unroll
+                    for (int jj = 0; jj < 4; jj++) {
+                        const int r = c0 / 2 + h * 4 + jj;
+                        o[jj] = (double2*)(A.uh + (((size_t)(r0 + min(r, RG - 1)) * A.K + k) * A.NPpad + a) * 6);
+                        if (add && r < RG) q[jj][0] = o[jj][0], q[jj][1] = o[jj][1], q[jj][2] = o[jj][2];
+                    }
+#pragma unroll
+                    for (int jj = 0; jj < 4; jj++) {
+                        const int j = h * 4 + jj, r = c0 / 2 + j;
+                        if (r >= RG) continue;
+                        float w[6] = {v0[2 * j], v1[2 * j], v2[2 * j], v0[2 * j + 1], v1[2 * j + 1], v2[2 * j + 1]};
+                        if (add) {
+                            w[0] += d2f_int(q[jj][0].x), w[1] += d2f_int(q[jj][0].y), w[2] += d2f_int(q[jj][1].x);
+                            w[3] += d2f_int(q[jj][1].y), w[4] += d2f_int(q[jj][2].x), w[5] += d2f_int(q[jj][2].y);
+                        }
+                        o[jj][0] = make_double2(f2d_int(w[0]), f2d_int(w[1]));
+                        o[jj][1] = make_double2(f2d_int(w[2]), f2d_int(w[3]));
+                        o[jj][2] = make_double2(f2d_int(w[4]), f2d_int(w[5]));
+                    }
+                }
+            }
+        };
+        int it = 0, gpos = 0;  // stage counter and its position in the accumulation group
         if (nbuf == 2) stage_async(0, 0);
         for (int tB = 0; tB < A.n_tb; tB++) {
             if (nbuf == 1) {
@@ -406,6 +448,22 @@ __global__ void __launch_bounds__(kThreads, 1)
                 if (!C::ATM && (s_abort || !wait_or_abort(&empty[s], (u & 1u) ^ 1u, &s_abort))) {
                     s_abort = 1;
                     continue;  // keep the barrier count of the other builders
+                }
+                // At a group boundary, wait for the previous stage's products first (A in tensor
+                // memory: the A buffer's release; otherwise the single stage's release above)
+                // and drain the accumulators before gathering, where few registers are live.
+                bool drained = false;
+                const bool boundary = it > 0 && gpos == 0;
+                if (++gpos == gs) gpos = 0;
+                if (boundary) {
+                    if (C::ATM && (s_abort || !wait_or_abort(&aempty, ((uint32_t)it & 1u) ^ 1u, &s_abort))) {
+                        s_abort = 1;
+                        continue;
+                    }
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    drain(it > gs);
+                    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                    drained = true;
                 }
                 // row a_loc, columns st*16 + hb*8 .. + 7 of this tile: six entries, NS pieces each
                 float v[8][6];
@@ -446,7 +504,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 }
                 if (C::ATM) {
                     // the tensor-memory A buffer is free once the previous stage's products are complete
-                    if (s_abort || !wait_or_abort(&aempty, ((uint32_t)it & 1u) ^ 1u, &s_abort)) {
+                    if (!drained && (s_abort || !wait_or_abort(&aempty, ((uint32_t)it & 1u) ^ 1u, &s_abort))) {
                         s_abort = 1;
                         continue;
                     }
@@ -506,25 +564,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         // ---- epilogue: accumulators -> uh (FP64) ----
         const bool ok = wait_or_abort(&done, 0u, &s_abort) && !s_abort;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        if (ok) {
-            const uint32_t trow = tmem + ((uint32_t)((warp & 3) * 32) << 16);
-            for (int c0 = hb * 16; c0 < NP; c0 += 32) {
-                float v0[16], v1[16], v2[16];
-                tc::ld16(trow + (uint32_t)c0, v0);
-                tc::ld16(trow + (uint32_t)(NP + c0), v1);
-                tc::ld16(trow + (uint32_t)(2 * NP + c0), v2);
-#pragma unroll
-                for (int j = 0; j < 8; j++) {
-                    const int r = c0 / 2 + j;
-                    if (r < RG) {
-                        double2* o = (double2*)(A.uh + (((size_t)(r0 + r) * A.K + k) * A.NPpad + a) * 6);
-                        o[0] = make_double2(v0[2 * j], v1[2 * j]);
-                        o[1] = make_double2(v2[2 * j], v0[2 * j + 1]);
-                        o[2] = make_double2(v1[2 * j + 1], v2[2 * j + 1]);
-                    }
-                }
-            }
-        }
+        if (ok) drain(n_it > gs);  // the last group; earlier groups were drained in the loop
     }
     __syncthreads();
     if (threadIdx.x == 0 && s_abort) atomicExch(status, FBC_ERR_TIMEOUT);
@@ -572,8 +612,11 @@ cudaError_t launch_tc(const ContractArgs& A, const Plan& P, int n_rhs, cudaStrea
     cudaError_t e = cudaFuncSetAttribute(k_contract_tc<PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e) return e;
     dim3 grid(P.n_ta, n_modes, G);
+    // accumulation groups of kDrainTiles interface tiles (1024 columns), or one group
+    const int n_it = P.n_tb * kStagesPerTile;
+    const int gs = (P.opt.flags & FBC_PLAN_TC_FAST_ACCUMULATE) ? n_it : std::min(n_it, kDrainTiles * kStagesPerTile);
     k_contract_tc<PREC><<<grid, kThreads, smem, st>>>(A, n_rhs, Galloc, npb, (const unsigned char*)P.d_bprep,
-                                                      tc_nbuf<PREC>(P.H * P.W), P.d_status);
+                                                      tc_nbuf<PREC>(P.H * P.W), gs, P.d_status);
     return cudaGetLastError();
 }
 

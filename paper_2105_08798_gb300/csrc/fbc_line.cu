@@ -47,29 +47,8 @@ struct Cx<float> {
 
 // GB300's FP64 pipe runs at about 1/64 of the FP32 rate, and conversions
 // between double and float issue there too.  The FP32 forms therefore convert
-// with integer bit arithmetic and keep one FP64 add per output element (the
-// k = 0 term).
-// double -> float, rounded to nearest (ties away from zero); magnitudes below
-// 2^-126 become signed zero (no overflow for the values transformed here).
-__device__ __forceinline__ float d2f_int(double x) {
-    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-    const unsigned int hi = (unsigned int)(b >> 32), lo = (unsigned int)b;
-    const unsigned int sign = hi & 0x80000000u;
-    const int e = (int)((hi >> 20) & 0x7ffu) - 1023 + 127;
-    if (e <= 0) return __uint_as_float(sign);
-    unsigned int r = ((unsigned int)e << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29);
-    r += (lo >> 28) & 1u;  // a carry out of the mantissa raises the exponent, as it should
-    return __uint_as_float(sign | r);
-}
-// float -> double, exact; zero and FP32 subnormals become signed zero.
-__device__ __forceinline__ double f2d_int(float x) {
-    const unsigned int b = __float_as_uint(x);
-    const unsigned int sign = b & 0x80000000u, e = (b >> 23) & 0xffu;
-    if (e == 0) return __longlong_as_double((long long)((unsigned long long)sign << 32));
-    const unsigned int hi = sign | ((e + 896u) << 20) | ((b & 0x7fffffu) >> 3);
-    const unsigned int lo = (b & 7u) << 29;
-    return __longlong_as_double((long long)(((unsigned long long)hi << 32) | lo));
-}
+// with integer bit arithmetic (d2f_int, f2d_int) and keep one FP64 add per
+// output element (the k = 0 term).
 // (sh, sl) += v with an exact two-sum (double-float accumulation on the FP32 pipes)
 __device__ __forceinline__ void df_acc(float v, float& sh, float& sl) {
     const float t = __fadd_rn(sh, v);

@@ -316,7 +316,8 @@ int fbc_plan_create(const fbc_geometry* geom, const fbc_material* mat, const fbc
     if (opt.max_rhs < 1 || opt.max_rhs > 4096) return fail(FBC_ERR_INVALID_ARG, "max_rhs must be in [1, 4096]");
     if (opt.precision < FBC_PREC_FP64 || opt.precision > FBC_PREC_BF16X3)
         return fail(FBC_ERR_INVALID_ARG, "unknown precision %d", opt.precision);
-    if (opt.flags & ~FBC_PLAN_HOST_ONLY) return fail(FBC_ERR_INVALID_ARG, "unknown options.flags bits 0x%x", opt.flags);
+    if (opt.flags & ~(FBC_PLAN_HOST_ONLY | FBC_PLAN_TC_FAST_ACCUMULATE))
+        return fail(FBC_ERR_INVALID_ARG, "unknown options.flags bits 0x%x", opt.flags);
     const int32_t coord_lim = 1 << 20;
     for (int t = 0; t < 2 * n_i; t++)
         if (geom->xy_i[t] < -coord_lim || geom->xy_i[t] > coord_lim)

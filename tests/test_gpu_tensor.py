@@ -51,7 +51,8 @@ def _run_all(fbc, n_i, n_p, L, R, seed):
     return xy_i, xy_p, f, out
 
 
-@pytest.mark.parametrize("n_i,n_p,L,R", [(300, 450, 32, 16), (150, 220, 16, 3), (100, 140, 8, 70)])
+# (1500, 2000): more than 1024 interface columns, so the accumulators are drained mid-sum
+@pytest.mark.parametrize("n_i,n_p,L,R", [(300, 450, 32, 16), (150, 220, 16, 3), (100, 140, 8, 70), (1500, 2000, 8, 8)])
 def test_tensor_forms_against_fp64(fbc, n_i, n_p, L, R):
     _, _, _, out = _run_all(fbc, n_i, n_p, L, R, seed=n_i + R)
     assert np.isfinite(out["fp64"]).all()
@@ -79,3 +80,24 @@ def test_k0_band_stays_fp64(fbc):
         got = np.fft.rfft(out[prec], axis=2)[:, :, 0]
         err = np.linalg.norm(got - ref) / np.linalg.norm(ref)
         assert err <= 1e-11, (prec, err)
+
+
+def test_fast_accumulate_flag(fbc):
+    """More than 1024 interface columns: the default splits the tensor-memory accumulation
+    into groups; FBC_PLAN_TC_FAST_ACCUMULATE keeps one group.  Both stay within the BF16x2
+    bound against FP64, and they differ (the flag changes the summation)."""
+    n_i, n_p, L, R = 1500, 2000, 8, 8
+    xy_i, xy_p = inputs.ring_geometry(n_i, n_p)
+    f = torch.from_numpy(inputs.forces(R, n_i, L, seed=2)).cuda()
+    out = {}
+    for name, prec, fast in (("fp64", "fp64", False), ("grouped", "bf16x2", False), ("one", "bf16x2", True)):
+        with fbc.Plan(xy_i, xy_p, L, ISO, precision=prec, max_rhs=R, tc_fast_accumulate=fast) as plan:
+            plan.tabulate()
+            ud = torch.full((R, n_p, L, 3), float("nan"), dtype=torch.float64, device="cuda")
+            plan.apply(f, ud)
+            torch.cuda.synchronize()
+            plan.sync_status()
+            out[name] = ud.cpu().numpy()
+    for name in ("grouped", "one"):
+        assert rel_l2(out[name], out["fp64"]) <= BOUNDS["bf16x2"], name
+    assert not np.array_equal(out["grouped"], out["one"])
