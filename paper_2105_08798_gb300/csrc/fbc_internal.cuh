@@ -76,7 +76,7 @@ struct Plan {
     int* d_perm_i = nullptr;     // [NIpad]
     int* d_perm_p = nullptr;     // [NPpad]
     int2* d_used = nullptr;      // [n_used] differences that occur
-    double2* d_tw = nullptr;     // [L/2] exp(-2 pi i t / L)
+    double2* d_tw = nullptr;     // [L/2] exp(-2 pi i t / L), then the same as [L/2] float2
     double2* d_twL = nullptr;    // [L] (cos, sin)(2 pi t / L) for the table DFT
     double* d_table = nullptr;   // [K][Dy][Dx][6] FP64
     float* d_table32 = nullptr;  // [K][Dy][Dx][6] FP32 (FBC_PREC_FP32)
@@ -216,8 +216,8 @@ cudaError_t launch_mlp_tc(const MlpArgs& a, cudaStream_t st);
 // pipe, where cvt between the two issues, runs at about 1/64 of the FP32 rate).
 // double -> float, rounded to nearest (ties away from zero); magnitudes below
 // 2^-126 become signed zero (no overflow for the values transformed here).
-__device__ __forceinline__ float d2f_int(double x) {
-    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+__device__ __forceinline__ float d2f_bits(long long bits) {
+    const unsigned long long b = (unsigned long long)bits;
     const unsigned int hi = (unsigned int)(b >> 32), lo = (unsigned int)b;
     const unsigned int sign = hi & 0x80000000u;
     const int e = (int)((hi >> 20) & 0x7ffu) - 1023 + 127;
@@ -226,6 +226,7 @@ __device__ __forceinline__ float d2f_int(double x) {
     r += (lo >> 28) & 1u;  // a carry out of the mantissa raises the exponent, as it should
     return __uint_as_float(sign | r);
 }
+__device__ __forceinline__ float d2f_int(double x) { return d2f_bits(__double_as_longlong(x)); }
 // float -> double, exact; zero and FP32 subnormals become signed zero.
 __device__ __forceinline__ double f2d_int(float x) {
     const unsigned int b = __float_as_uint(x);

@@ -67,7 +67,8 @@ __device__ __forceinline__ T2 cmul(T2 a, T2 b) {
 
 __device__ __forceinline__ int bitrev(int x, int logL) { return (int)(__brev((unsigned)x) >> (32 - logL)); }
 
-// nseq sequences of length L in buf; tw[t] = exp(-2 pi i t / L); inverse uses conj.
+// nseq sequences of length L in buf; tw[t] = exp(-2 pi i t / L) (FP32 form: the float
+// copy tw32[t] stored after the L/2 double entries); inverse uses conj.
 template <typename R>
 __device__ void fft_block(typename Cx<R>::T* buf, int nseq, int L, int logL, const double2* __restrict__ tw,
                           bool inverse) {
@@ -83,8 +84,14 @@ __device__ void fft_block(typename Cx<R>::T* buf, int nseq, int L, int logL, con
             const int grp = j >> lh;
             const int i0 = (grp << (lh + 1)) + pos;
             const int i1 = i0 + h;
-            const double2 wd = __ldg(&tw[pos * stride_tw]);
-            const T2 w = Cx<R>::make((R)wd.x, inverse ? -(R)wd.y : (R)wd.y);
+            T2 w;
+            if constexpr (sizeof(R) == 4) {
+                // the float copy after the L/2 double entries (no conversion on the FP64 pipe)
+                w = __ldg(&((const float2*)(tw + half))[pos * stride_tw]);
+            } else {
+                w = __ldg(&tw[pos * stride_tw]);
+            }
+            if (inverse) w.y = -w.y;
             T2* s = buf + (size_t)sq * L;
             const T2 a = s[i0];
             const T2 bw = cmul(s[i1], w);
@@ -102,6 +109,7 @@ __device__ __forceinline__ void fwd_block(const double* __restrict__ f, const in
                                           int logL, int K, int NIpad, int NC, int blk, int r, void* sraw) {
     using T2 = typename Cx<R>::T;
     constexpr bool kF32 = sizeof(R) == 4;
+    const int logNC = __ffs(NC) - 1;  // NC and L are powers of two: shifts, no integer division
     // sbuf: [NC + NC/2][L], z sequences then w sequences
     const int b0 = blk * NC;
     T2* zs = (T2*)sraw;
@@ -109,19 +117,26 @@ __device__ __forceinline__ void fwd_block(const double* __restrict__ f, const in
     __shared__ double s0[kF32 ? 64 : 1][3];  // FP64 column sums = the k = 0 mode (FP32 form)
     // load: each column's L x 3 block is contiguous in f
     for (int t = threadIdx.x; t < NC * L; t += blockDim.x) {
-        const int j = t / L, q = t % L;
+        const int j = t >> logL, q = t & (L - 1);
         const int ob = perm[b0 + j];
+        const int qr = bitrev(q, logL);
+        R* wp = (R*)&ws[(size_t)(j >> 1) * L + qr];
+        if constexpr (kF32) {
+            long long b1 = 0, b2 = 0, b3 = 0;  // raw FP64 words: nothing typed double on the way
+            if (ob >= 0) {
+                const long long* src = (const long long*)(f + (((size_t)r * n_i + ob) * L + q) * 3);
+                b1 = src[0], b2 = src[1], b3 = src[2];
+            }
+            zs[(size_t)j * L + qr] = Cx<R>::make(d2f_bits(b1), d2f_bits(b2));
+            wp[j & 1] = d2f_bits(b3);
+            continue;
+        }
         double f1 = 0.0, f2 = 0.0, f3 = 0.0;
         if (ob >= 0) {
             const double* src = f + (((size_t)r * n_i + ob) * L + q) * 3;
             f1 = src[0], f2 = src[1], f3 = src[2];
         }
-        const int qr = bitrev(q, logL);
-        R* wp = (R*)&ws[(size_t)(j >> 1) * L + qr];
-        if constexpr (kF32) {
-            zs[(size_t)j * L + qr] = Cx<R>::make(d2f_int(f1), d2f_int(f2));
-            wp[j & 1] = d2f_int(f3);
-        } else {
+        {
             zs[(size_t)j * L + qr] = Cx<R>::make((R)f1, (R)f2);
             wp[j & 1] = (R)f3;
         }
@@ -149,7 +164,7 @@ __device__ __forceinline__ void fwd_block(const double* __restrict__ f, const in
     fft_block<R>(zs, NC + NC / 2, L, logL, tw, false);
     // unpack and store six-vectors for k = 0..L/2
     for (int t = threadIdx.x; t < NC * K; t += blockDim.x) {
-        const int k = t / NC, j = t % NC;
+        const int k = t >> logNC, j = t & (NC - 1);
         const int km = (L - k) & (L - 1);
         const T2 Z = zs[(size_t)j * L + k], Zm = zs[(size_t)j * L + km];
         const T2 Wv = ws[(size_t)(j >> 1) * L + k], Wm = ws[(size_t)(j >> 1) * L + km];
@@ -230,13 +245,15 @@ __device__ __forceinline__ void inv_block(const double* __restrict__ uh, const i
                                           int r, void* sraw) {
     using T2 = typename Cx<R>::T;
     constexpr bool kF32 = sizeof(R) == 4;
+    const int logNC = __ffs(NC) - 1;  // NC and L are powers of two: shifts, no integer division
     const int a0 = blk * NC;
+    const bool has_beta = beta != 0.0;
     T2* zs = (T2*)sraw;
     T2* ws = zs + (size_t)NC * L;
     __shared__ double u0[kF32 ? 64 : 1][3];  // FP64 k = 0 term per column (FP32 form)
     const int Lh = L >> 1;
     for (int t = threadIdx.x; t < NC * K; t += blockDim.x) {
-        const int k = t / NC, j = t % NC;
+        const int k = t >> logNC, j = t & (NC - 1);
         const double* src = uh + (((size_t)r * K + k) * NPpad + a0 + j) * 6;
         if constexpr (kF32) {
             // k = 0 kept in FP64 beside the transform; the rest converted on the integer pipes
@@ -245,9 +262,10 @@ __device__ __forceinline__ void inv_block(const double* __restrict__ uh, const i
                 u0[j][0] = src[0], u0[j][1] = src[1];
                 U1r = U2r = U1i = U2i = 0.f;
             } else {
-                U1r = d2f_int(src[0]), U2r = d2f_int(src[1]);
-                U1i = k == Lh ? 0.f : d2f_int(src[3]);
-                U2i = k == Lh ? 0.f : d2f_int(src[4]);
+                const long long* sb = (const long long*)src;  // raw FP64 words
+                U1r = d2f_bits(sb[0]), U2r = d2f_bits(sb[1]);
+                U1i = k == Lh ? 0.f : d2f_bits(sb[3]);
+                U2i = k == Lh ? 0.f : d2f_bits(sb[4]);
             }
             zs[(size_t)j * L + bitrev(k, logL)] = Cx<R>::make(U1r - U2i, U1i + U2r);
             if (k != 0 && k != Lh) zs[(size_t)j * L + bitrev(L - k, logL)] = Cx<R>::make(U1r + U2i, U2r - U1i);
@@ -264,7 +282,7 @@ __device__ __forceinline__ void inv_block(const double* __restrict__ uh, const i
     }
     // W = U3(even column) + i U3(odd column), with U3 = -y2 + i x2: thread per (k, column pair)
     for (int t = threadIdx.x; t < (NC / 2) * K; t += blockDim.x) {
-        const int k = t / (NC / 2), jp = t % (NC / 2);
+        const int k = t >> (logNC - 1), jp = t & ((NC >> 1) - 1);
         const double* se = uh + (((size_t)r * K + k) * NPpad + a0 + 2 * jp) * 6;
         const double* so = se + 6;
         if constexpr (kF32) {
@@ -273,9 +291,10 @@ __device__ __forceinline__ void inv_block(const double* __restrict__ uh, const i
                 u0[2 * jp][2] = -se[5], u0[2 * jp + 1][2] = -so[5];
                 Er = Ei = Or = Oi = 0.f;
             } else {
-                Er = -d2f_int(se[5]), Or = -d2f_int(so[5]);
-                Ei = k == Lh ? 0.f : d2f_int(se[2]);
-                Oi = k == Lh ? 0.f : d2f_int(so[2]);
+                const long long *eb = (const long long*)se, *ob = (const long long*)so;
+                Er = -d2f_bits(eb[5]), Or = -d2f_bits(ob[5]);
+                Ei = k == Lh ? 0.f : d2f_bits(eb[2]);
+                Oi = k == Lh ? 0.f : d2f_bits(ob[2]);
             }
             ws[(size_t)jp * L + bitrev(k, logL)] = Cx<R>::make(Er - Oi, Ei + Or);
             if (k != 0 && k != Lh) ws[(size_t)jp * L + bitrev(L - k, logL)] = Cx<R>::make(Er + Oi, Or - Ei);
@@ -318,7 +337,7 @@ __device__ __forceinline__ void inv_block(const double* __restrict__ uh, const i
         __syncthreads();
         const float af = (float)alpha_over_L;
         for (int t = threadIdx.x; t < NC * L; t += blockDim.x) {
-            const int j = t / L, p = t % L;
+            const int j = t >> logL, p = t & (L - 1);
             const int oa = perm[a0 + j];
             if (oa < 0) continue;
             const T2 z = zs[(size_t)j * L + p];
@@ -327,7 +346,7 @@ __device__ __forceinline__ void inv_block(const double* __restrict__ uh, const i
             double o0 = f2d_int(af * z.x) + uk[j][0];
             double o1 = f2d_int(af * z.y) + uk[j][1];
             double o2 = f2d_int(af * ((j & 1) ? w.y : w.x)) + uk[j][2];
-            if (beta != 0.0) {
+            if (has_beta) {
                 o0 = fma(beta, dst[0], o0);
                 o1 = fma(beta, dst[1], o1);
                 o2 = fma(beta, dst[2], o2);
@@ -339,7 +358,7 @@ __device__ __forceinline__ void inv_block(const double* __restrict__ uh, const i
         }
     } else {
         for (int t = threadIdx.x; t < NC * L; t += blockDim.x) {
-            const int j = t / L, p = t % L;
+            const int j = t >> logL, p = t & (L - 1);
             const int oa = perm[a0 + j];
             if (oa < 0) continue;
             const T2 z = zs[(size_t)j * L + p];
@@ -347,7 +366,7 @@ __device__ __forceinline__ void inv_block(const double* __restrict__ uh, const i
             const double z0 = z.x, z1 = z.y, v3 = (j & 1) ? w.y : w.x;
             double* dst = u + (((size_t)r * n_p + oa) * L + p) * 3;
             double o0 = alpha_over_L * z0, o1 = alpha_over_L * z1, o2 = alpha_over_L * v3;
-            if (beta != 0.0) {
+            if (has_beta) {
                 o0 = fma(beta, dst[0], o0);
                 o1 = fma(beta, dst[1], o1);
                 o2 = fma(beta, dst[2], o2);

@@ -441,7 +441,7 @@ int fbc_plan_create(const fbc_geometry* geom, const fbc_material* mat, const fbc
     ALLOC(P.d_perm_i, P.NIpad, "perm_i");
     ALLOC(P.d_perm_p, P.NPpad, "perm_p");
     ALLOC(P.d_used, P.n_used, "used");
-    ALLOC(P.d_tw, L / 2, "twiddles");
+    ALLOC(P.d_tw, L / 2 + L / 4 + 1, "twiddles");  // L/2 double2, then L/2 float2
     ALLOC(P.d_twL, L, "table_twiddles");
     size_t ws_before_table = acc;
     ALLOC(P.d_table, cells * 6, "table");
@@ -458,10 +458,12 @@ int fbc_plan_create(const fbc_geometry* geom, const fbc_material* mat, const fbc
         return s_;
     }
 
-    std::vector<double2> tw(L / 2), twL(L);
+    std::vector<double2> tw(L / 2 + L / 4 + 1), twL(L);
+    float2* tw32 = (float2*)(tw.data() + L / 2);  // the FP32 transforms' copy, rounded from FP64
     for (int t = 0; t < L / 2; t++) {
         double ang = 2.0 * M_PI * (double)t / (double)L;
         tw[t] = make_double2(cos(ang), -sin(ang));
+        tw32[t] = make_float2((float)tw[t].x, (float)tw[t].y);
     }
     for (int t = 0; t < L; t++) {
         double ang = 2.0 * M_PI * (double)t / (double)L;
@@ -477,7 +479,7 @@ int fbc_plan_create(const fbc_geometry* geom, const fbc_material* mat, const fbc
     UP(P.d_perm_i, tb.perm.data(), P.NIpad);
     UP(P.d_perm_p, ta.perm.data(), P.NPpad);
     if (P.n_used) UP(P.d_used, used_list.data(), P.n_used);
-    UP(P.d_tw, tw.data(), L / 2);
+    UP(P.d_tw, tw.data(), L / 2 + L / 4 + 1);
     UP(P.d_twL, twL.data(), L);
 #undef UP
     if (e == cudaSuccess) e = cudaMemset(P.d_table, 0, cells * 6 * sizeof(double));
