@@ -21,6 +21,9 @@ with ``ctypes``.  Every function cites the passage of the paper it follows:
                           form u <- beta u + alpha G f (Sec. 2.3.2, Eq. 22,
                           Algorithm 1) and the optional zero mean (Eq. 23).
 * ``mode_table``       -- plain DFT of the tabulated kernel along the line.
+* ``relax_alpha``      -- the residual-based relaxation parameter (Sec. 2.3.3,
+                          Algorithm 2) and ``relaxed_update``, the pad update of
+                          Algorithm 1 that uses it.
 
 Parity is pinned by the ``-m "not gpu"`` tests in ``tests/test_oracle_*.py``.
 """
@@ -317,6 +320,46 @@ def pad_update(xy_i, xy_p, L: int, c: float, material: dict, f: np.ndarray, *, s
     if return_table:
         return out, (d_list, table)
     return out
+
+
+def relax_alpha(f_new, f_old, alpha_k, g, du_max: float = 0.0) -> np.ndarray:
+    """Relaxation parameter of Algorithm 2 (Sec. 2.3.3), one per right-hand side.
+
+    alpha = -alpha_k <f_old, f_new - f_old> / ||f_new - f_old||^2 over all interface
+    atoms and components (alpha_k kept when the denominator is zero, or when f_old
+    is None); alpha = 1 where that is negative; alpha = du_max / ||g||_inf where
+    du_max > 0 and ||alpha g||_inf > du_max, with g = G f_new.
+    """
+    f_new = np.asarray(f_new, dtype=np.float64)
+    alpha = np.array(alpha_k, dtype=np.float64).reshape(-1).copy()
+    g = np.asarray(g, dtype=np.float64)
+    for r in range(f_new.shape[0]):
+        if f_old is not None:
+            a = f_new[r].ravel()
+            b = np.asarray(f_old[r], dtype=np.float64).ravel()
+            diff = a - b
+            den = float(np.dot(diff, diff))
+            if den > 0.0:
+                alpha[r] = -alpha[r] * float(np.dot(b, diff)) / den
+            if alpha[r] < 0.0:
+                alpha[r] = 1.0
+        if du_max > 0.0:
+            gmax = float(np.max(np.abs(g[r])))
+            if gmax > 0.0 and alpha[r] * gmax > du_max:
+                alpha[r] = du_max / gmax
+    return alpha
+
+
+def relaxed_update(xy_i, xy_p, L: int, c: float, material: dict, f_new, f_old, u0, alpha_k, du_max: float = 0.0,
+                   project: bool = True, zero_mean_u: bool = False, nquad: int | None = None):
+    """One pad update of Algorithm 1 with the relaxation of Algorithm 2:
+    u = u0 - alpha G f_new (then the optional zero mean, Eq. 23).  Returns (u, alpha)."""
+    g = pad_update(xy_i, xy_p, L, c, material, f_new, project=project, nquad=nquad)
+    alpha = relax_alpha(f_new, f_old, alpha_k, g, du_max)
+    u = np.asarray(u0, dtype=np.float64) - alpha[:, None, None, None] * g
+    if zero_mean_u:
+        u = zero_mean(u)
+    return u, alpha
 
 
 def sys_info() -> dict:
