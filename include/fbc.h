@@ -174,6 +174,26 @@ int fbc_tabulate_kernel(fbc_plan* plan, void* stream);
 int fbc_apply(fbc_plan* plan, const double* f, double* u, int32_t n_rhs, double alpha, double beta,
               uint32_t flags, void* stream);
 
+/* Relaxed pad update of the FBC iteration (Algorithm 1 with the residual-based
+ * relaxation of Sec. 2.3.3, Algorithm 2), per right-hand side r:
+ *   alpha = -alpha_io[r] <f_old, f_new - f_old> / ||f_new - f_old||^2   (f_old given;
+ *           kept as alpha_io[r] if f_new == f_old),
+ *   alpha = 1 if it is negative,
+ *   alpha = du_max / ||G f_new||_inf if du_max > 0 and ||alpha G f_new||_inf > du_max,
+ *   u <- u - alpha G f_new, then the optional zero mean (FBC_APPLY_ZERO_MEAN_U),
+ * and alpha_io[r] <- alpha.  The inner products run over all n_i * L interface
+ * atoms and components of the raw inputs; the maximum over all n_p * L pad atoms
+ * and components of G f_new (after the optional neutral projection of f_new, as
+ * in fbc_apply).  f_old = NULL skips the first two steps (alpha_io is used as
+ * given, as in the iterations before the relaxation starts).
+ *   f_new, f_old: DEVICE double [n_rhs][n_i][L][3]; u: DEVICE double
+ *   [n_rhs][n_p][L][3] (updated in place); alpha_io: DEVICE double [n_rhs].
+ * Asynchronous on `stream`; no allocation and no host synchronisation (alpha is
+ * computed on the device).  The plan's contracted modes are transformed twice
+ * (once for the maximum, once for the update) when du_max > 0. */
+int fbc_apply_relaxed(fbc_plan* plan, const double* f_new, const double* f_old, double* u, int32_t n_rhs,
+                      double* alpha_io, double du_max, uint32_t flags, void* stream);
+
 /* Same as fbc_apply with f and u in HOST memory (pinned memory makes the
  * copies asynchronous): copies f (and u when beta != 0) to the plan's device
  * staging buffers, applies, copies u back and synchronises `stream`. */

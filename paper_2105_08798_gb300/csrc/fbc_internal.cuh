@@ -85,6 +85,7 @@ struct Plan {
     double* d_fh = nullptr;      // [max_rhs][K][NIpad][6]
     double* d_uh = nullptr;      // [max_rhs][K][NPpad][6]
     double* d_part = nullptr;    // [max_rhs][n_line_blocks_p][3] zero-mean partial sums
+    double* d_relax = nullptr;   // [max_rhs][kRelaxBlocks][2] dot products, then [max_rhs][n_line_blocks_p] maxima
     double* d_stage_f = nullptr; // host-apply staging
     double* d_stage_u = nullptr;
     int* d_status = nullptr;     // device error word
@@ -140,8 +141,17 @@ struct LineArgs {
 cudaError_t launch_tabulate(Plan& P, cudaStream_t st);
 cudaError_t launch_forward(Plan& P, const double* f, int n_rhs, bool project, cudaStream_t st);
 cudaError_t launch_contract(Plan& P, int n_rhs, cudaStream_t st);
+// alpha_dev (optional): per-rhs multiplier alpha_dev_scale * alpha_dev[r] in place of alpha / L;
+// gmax_part (optional): only record per (rhs, line block) the largest |value|, write nothing
 cudaError_t launch_inverse(Plan& P, double* u, int n_rhs, double alpha, double beta, bool zero_mean,
-                           cudaStream_t st);
+                           cudaStream_t st, const double* alpha_dev = nullptr, double alpha_dev_scale = 0.0,
+                           double* gmax_part = nullptr);
+// residual-based relaxation (fbc_relax.cu)
+constexpr int kRelaxBlocks = 128;  // blocks per right-hand side of the dot-product pass
+cudaError_t launch_relax_dots(const double* f_new, const double* f_old, size_t n_per_rhs, int n_rhs, double* part,
+                              cudaStream_t st);
+cudaError_t launch_relax_alpha(const double* dot_part, int has_old, const double* gmax_part, int n_gblk, int n_rhs,
+                               double du_max, double* alpha_io, cudaStream_t st);
 cudaError_t launch_derive_tables(Plan& P, int precision, cudaStream_t st);
 ContractArgs make_contract_args(const Plan& P);
 cudaError_t launch_contract_tc(const ContractArgs& A, const Plan& P, int n_rhs, cudaStream_t st, int n_modes = -1);

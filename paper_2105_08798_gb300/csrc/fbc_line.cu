@@ -242,11 +242,18 @@ __device__ __forceinline__ void inv_block(const double* __restrict__ uh, const i
                                           const double2* __restrict__ tw, double* __restrict__ u,
                                           double* __restrict__ part, int n_p, int L, int logL, int K, int NPpad,
                                           int NC, double alpha_over_L, double beta, int want_part, int blk, int n_blk,
-                                          int r, void* sraw) {
+                                          int r, void* sraw, const double* __restrict__ alpha_dev = nullptr,
+                                          double alpha_dev_scale = 0.0, double* __restrict__ gmax_part = nullptr) {
     using T2 = typename Cx<R>::T;
     constexpr bool kF32 = sizeof(R) == 4;
     const int logNC = __ffs(NC) - 1;  // NC and L are powers of two: shifts, no integer division
     const int a0 = blk * NC;
+    // per-rhs multiplier from device memory (the relaxed update), or the launch's alpha / L
+    if (alpha_dev) alpha_over_L = alpha_dev_scale * alpha_dev[r];
+    // gmax_part: only the block's largest |alpha/L sum_k ...| is recorded, nothing is written
+    const bool max_only = gmax_part != nullptr;
+    float mx32 = 0.f;
+    double mx64 = 0.0;
     const bool has_beta = beta != 0.0;
     T2* zs = (T2*)sraw;
     T2* ws = zs + (size_t)NC * L;
@@ -342,6 +349,13 @@ __device__ __forceinline__ void inv_block(const double* __restrict__ uh, const i
             if (oa < 0) continue;
             const T2 z = zs[(size_t)j * L + p];
             const T2 w = ws[(size_t)(j >> 1) * L + p];
+            if (max_only) {
+                // the cap needs |g| to FP32 accuracy: sum in FP32, no FP64 work per element
+                const float g0 = af * z.x + (float)uk[j][0], g1 = af * z.y + (float)uk[j][1];
+                const float g2 = af * ((j & 1) ? w.y : w.x) + (float)uk[j][2];
+                mx32 = fmaxf(mx32, fmaxf(fabsf(g0), fmaxf(fabsf(g1), fabsf(g2))));
+                continue;
+            }
             double* dst = u + (((size_t)r * n_p + oa) * L + p) * 3;
             double o0 = f2d_int(af * z.x) + uk[j][0];
             double o1 = f2d_int(af * z.y) + uk[j][1];
@@ -364,8 +378,12 @@ __device__ __forceinline__ void inv_block(const double* __restrict__ uh, const i
             const T2 z = zs[(size_t)j * L + p];
             const T2 w = ws[(size_t)(j >> 1) * L + p];
             const double z0 = z.x, z1 = z.y, v3 = (j & 1) ? w.y : w.x;
-            double* dst = u + (((size_t)r * n_p + oa) * L + p) * 3;
             double o0 = alpha_over_L * z0, o1 = alpha_over_L * z1, o2 = alpha_over_L * v3;
+            if (max_only) {
+                mx64 = fmax(mx64, fmax(fabs(o0), fmax(fabs(o1), fabs(o2))));
+                continue;
+            }
+            double* dst = u + (((size_t)r * n_p + oa) * L + p) * 3;
             if (has_beta) {
                 o0 = fma(beta, dst[0], o0);
                 o1 = fma(beta, dst[1], o1);
@@ -376,6 +394,17 @@ __device__ __forceinline__ void inv_block(const double* __restrict__ uh, const i
             dst[2] = o2;
             ps0 += o0, ps1 += o1, ps2 += o2;
         }
+    }
+    if (max_only) {
+        __shared__ double redm[256];
+        redm[threadIdx.x] = kF32 ? (double)mx32 : mx64;
+        __syncthreads();
+        for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+            if ((int)threadIdx.x < w) redm[threadIdx.x] = fmax(redm[threadIdx.x], redm[threadIdx.x + w]);
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) gmax_part[(size_t)r * n_blk + blk] = redm[0];
+        return;
     }
     if (want_part) {
         __shared__ double red[3][256];
@@ -427,10 +456,11 @@ __global__ void k_project(double* __restrict__ fh, const int* __restrict__ perm,
 template <typename R>
 __global__ void k_inverse(const double* __restrict__ uh, const int* __restrict__ perm, const double2* __restrict__ tw,
                           double* __restrict__ u, double* __restrict__ part, int n_p, int L, int logL, int K, int NPpad,
-                          int NC, double alpha_over_L, double beta, int want_part) {
+                          int NC, double alpha_over_L, double beta, int want_part, const double* __restrict__ alpha_dev,
+                          double alpha_dev_scale, double* __restrict__ gmax_part) {
     extern __shared__ double2 sbuf[];
     inv_block<R>(uh, perm, tw, u, part, n_p, L, logL, K, NPpad, NC, alpha_over_L, beta, want_part, blockIdx.x,
-                 gridDim.x, blockIdx.y, sbuf);
+                 gridDim.x, blockIdx.y, sbuf, alpha_dev, alpha_dev_scale, gmax_part);
 }
 __global__ void k_zero_mean(double* __restrict__ u, const double* __restrict__ part, int n_part, int n_p, int L) {
     zero_mean_chunk(u, part, n_part, n_p, L, blockIdx.y, blockIdx.x, gridDim.x);
@@ -490,7 +520,7 @@ cudaError_t launch_forward(Plan& P, const double* f, int n_rhs, bool project, cu
 }
 
 cudaError_t launch_inverse(Plan& P, double* u, int n_rhs, double alpha, double beta, bool zero_mean,
-                           cudaStream_t st) {
+                           cudaStream_t st, const double* alpha_dev, double alpha_dev_scale, double* gmax_part) {
     const int NC = line_cols(P.L);
     const size_t smem = line_smem(P.L, NC);
     cudaError_t e;
@@ -499,14 +529,16 @@ cudaError_t launch_inverse(Plan& P, double* u, int n_rhs, double alpha, double b
     if (line_fp32(P.precision)) {
         if ((e = cudaFuncSetAttribute(k_inverse<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem))) return e;
         k_inverse<float><<<grid, 256, smem / 2, st>>>(P.d_uh, P.d_perm_p, P.d_tw, u, P.d_part, P.n_p, P.L, P.logL, P.K,
-                                                      P.NPpad, NC, alpha / (double)P.L, beta, zero_mean ? 1 : 0);
+                                                      P.NPpad, NC, alpha / (double)P.L, beta, zero_mean ? 1 : 0,
+                                                      alpha_dev, alpha_dev_scale, gmax_part);
     } else {
         if ((e = cudaFuncSetAttribute(k_inverse<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem))) return e;
         k_inverse<double><<<grid, 256, smem, st>>>(P.d_uh, P.d_perm_p, P.d_tw, u, P.d_part, P.n_p, P.L, P.logL, P.K,
-                                                   P.NPpad, NC, alpha / (double)P.L, beta, zero_mean ? 1 : 0);
+                                                   P.NPpad, NC, alpha / (double)P.L, beta, zero_mean ? 1 : 0,
+                                                   alpha_dev, alpha_dev_scale, gmax_part);
     }
     if ((e = cudaGetLastError())) return e;
-    if (zero_mean) {
+    if (zero_mean && !gmax_part) {
         const size_t n = (size_t)P.n_p * P.L * 3;
         int blocks = (int)std::min<size_t>((n + 255) / 256, 4 * 152);
         k_zero_mean<<<dim3(blocks, n_rhs), 256, 0, st>>>(u, P.d_part, nb, P.n_p, P.L);

@@ -193,7 +193,8 @@ int dev_alloc(T** p, size_t count, size_t& acc, const char* what) {
 void free_plan(fbc::Plan& P) {
     void* bufs[] = {P.d_xy_p,  P.d_off_i,    P.d_bbox_a, P.d_bbox_b, P.d_perm_i, P.d_perm_p,
                     P.d_used,  P.d_tw,       P.d_twL,    P.d_table,  P.d_table32, P.d_table_x2, P.d_table_x2_k0,
-                    P.d_fh,    P.d_uh,       P.d_part,   P.d_stage_f, P.d_stage_u, P.d_status, P.d_bprep};
+                    P.d_fh,    P.d_uh,       P.d_part,   P.d_stage_f, P.d_stage_u, P.d_status, P.d_bprep,
+                    P.d_relax};
     for (void* b : bufs)
         if (b) cudaFree(b);
     for (auto& e : P.ev)
@@ -449,6 +450,7 @@ int fbc_plan_create(const fbc_geometry* geom, const fbc_material* mat, const fbc
     ALLOC(P.d_fh, (size_t)opt.max_rhs * P.K * P.NIpad * 6, "fh");
     ALLOC(P.d_uh, (size_t)opt.max_rhs * P.K * P.NPpad * 6, "uh");
     ALLOC(P.d_part, (size_t)opt.max_rhs * nlb * 3, "partials");
+    ALLOC(P.d_relax, (size_t)opt.max_rhs * (fbc::kRelaxBlocks * 2 + nlb), "relaxation");
     ALLOC(P.d_status, 1, "status");
 #undef ALLOC
     P.workspace_bytes = acc - P.table_bytes;
@@ -533,8 +535,8 @@ int fbc_plan_set_precision(fbc_plan* plan, int32_t precision) {
     return FBC_OK;
 }
 
-static int apply_common(fbc::Plan& P, const double* f, double* u, int32_t n_rhs, double alpha, double beta,
-                        uint32_t flags, cudaStream_t st) {
+// Checks shared by the apply entry points.
+static int apply_checks(fbc::Plan& P, const double* f, const double* u, int32_t n_rhs, uint32_t flags) {
     if (P.host_only) return fail(FBC_ERR_INVALID_ARG, "host-only plan");
     if (!P.tabulated) return fail(FBC_ERR_NOT_TABULATED, "fbc_apply before fbc_tabulate_kernel");
     if (P.tables_released && !P.sur) return fail(FBC_ERR_INVALID_ARG, "tables released without a surrogate");
@@ -543,7 +545,6 @@ static int apply_common(fbc::Plan& P, const double* f, double* u, int32_t n_rhs,
         return fail(FBC_ERR_INVALID_ARG, "n_rhs = %d outside [1, max_rhs = %d]", n_rhs, P.opt.max_rhs);
     if (flags & ~(FBC_APPLY_PROJECT_NEUTRAL | FBC_APPLY_ZERO_MEAN_U))
         return fail(FBC_ERR_INVALID_ARG, "unknown apply flags 0x%x", flags);
-    if (!std::isfinite(alpha) || !std::isfinite(beta)) return fail(FBC_ERR_INVALID_ARG, "alpha/beta not finite");
     const size_t fb = (size_t)n_rhs * P.n_i * P.L * 3 * sizeof(double);
     const size_t ub = (size_t)n_rhs * P.n_p * P.L * 3 * sizeof(double);
     const char* fc = (const char*)f;
@@ -554,6 +555,11 @@ static int apply_common(fbc::Plan& P, const double* f, double* u, int32_t n_rhs,
     if (fbc::is_tensor_precision(P.precision) && fbc::contract_tc_smem(P.precision, P.W * P.H) > 227 * 1024)
         return fail(FBC_ERR_UNSUPPORTED, "tensor-core contraction: staged sub-box too large for shared memory");
     if (P.precision == FBC_PREC_F32X2 && !P.d_table_x2) return fail(FBC_ERR_INVALID_ARG, "F32X2 table missing");
+    return FBC_OK;
+}
+
+// Forward transform and per-mode contraction: leaves the contracted modes in P.d_uh.
+static int apply_modes(fbc::Plan& P, const double* f, int32_t n_rhs, uint32_t flags, cudaStream_t st) {
     if (P.timing) FBC_CUDA(cudaEventRecord(P.ev[0], st));
     cudaError_t e = fbc::launch_forward(P, f, n_rhs, (flags & FBC_APPLY_PROJECT_NEUTRAL) != 0, st);
     if (e != cudaSuccess) return cuda_fail(e, "forward transform");
@@ -568,7 +574,15 @@ static int apply_common(fbc::Plan& P, const double* f, double* u, int32_t n_rhs,
     }
     if (e != cudaSuccess) return cuda_fail(e, "mode contraction");
     if (P.timing) FBC_CUDA(cudaEventRecord(P.ev[2], st));
-    e = fbc::launch_inverse(P, u, n_rhs, alpha, beta, (flags & FBC_APPLY_ZERO_MEAN_U) != 0, st);
+    return FBC_OK;
+}
+
+static int apply_common(fbc::Plan& P, const double* f, double* u, int32_t n_rhs, double alpha, double beta,
+                        uint32_t flags, cudaStream_t st) {
+    if (int s = apply_checks(P, f, u, n_rhs, flags)) return s;
+    if (!std::isfinite(alpha) || !std::isfinite(beta)) return fail(FBC_ERR_INVALID_ARG, "alpha/beta not finite");
+    if (int s = apply_modes(P, f, n_rhs, flags, st)) return s;
+    cudaError_t e = fbc::launch_inverse(P, u, n_rhs, alpha, beta, (flags & FBC_APPLY_ZERO_MEAN_U) != 0, st);
     if (e != cudaSuccess) return cuda_fail(e, "inverse transform");
     if (P.timing) {
         FBC_CUDA(cudaEventRecord(P.ev[3], st));
@@ -582,6 +596,37 @@ int fbc_apply(fbc_plan* plan, const double* f, double* u, int32_t n_rhs, double 
     g_last_error.clear();
     if (!plan) return fail(FBC_ERR_INVALID_ARG, "plan is NULL");
     return apply_common(plan->p, f, u, n_rhs, alpha, beta, flags, (cudaStream_t)stream);
+}
+
+int fbc_apply_relaxed(fbc_plan* plan, const double* f_new, const double* f_old, double* u, int32_t n_rhs,
+                      double* alpha_io, double du_max, uint32_t flags, void* stream) {
+    g_last_error.clear();
+    if (!plan) return fail(FBC_ERR_INVALID_ARG, "plan is NULL");
+    fbc::Plan& P = plan->p;
+    if (int s = apply_checks(P, f_new, u, n_rhs, flags)) return s;
+    if (!alpha_io) return fail(FBC_ERR_INVALID_ARG, "alpha_io is NULL");
+    if (!std::isfinite(du_max) || du_max < 0.0) return fail(FBC_ERR_INVALID_ARG, "du_max must be finite and >= 0");
+    if (f_old) {
+        if (f_old == f_new) return fail(FBC_ERR_INVALID_ARG, "f_old and f_new are the same buffer");
+        if (int s = apply_checks(P, f_old, u, n_rhs, flags)) return s;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    const int nlb = P.NPpad / fbc::line_cols(P.L);
+    double* dots = P.d_relax;
+    double* gmax = P.d_relax + (size_t)P.opt.max_rhs * fbc::kRelaxBlocks * 2;
+    cudaError_t e = cudaSuccess;
+    if (f_old) e = fbc::launch_relax_dots(f_new, f_old, (size_t)P.n_i * P.L * 3, n_rhs, dots, st);
+    if (e != cudaSuccess) return cuda_fail(e, "relaxation dot products");
+    if (int s = apply_modes(P, f_new, n_rhs, flags, st)) return s;
+    // ||G f_new||_inf per right-hand side (a pass of the inverse transform that writes nothing)
+    if (du_max > 0.0) e = fbc::launch_inverse(P, u, n_rhs, 1.0, 0.0, false, st, nullptr, 0.0, gmax);
+    if (e == cudaSuccess) e = fbc::launch_relax_alpha(dots, f_old ? 1 : 0, gmax, nlb, n_rhs, du_max, alpha_io, st);
+    if (e != cudaSuccess) return cuda_fail(e, "relaxation parameter");
+    // u <- u - alpha_{k+1} G f_new, then the optional zero mean
+    e = fbc::launch_inverse(P, u, n_rhs, 0.0, 1.0, (flags & FBC_APPLY_ZERO_MEAN_U) != 0, st, alpha_io,
+                            -1.0 / (double)P.L, nullptr);
+    if (e != cudaSuccess) return cuda_fail(e, "inverse transform");
+    return FBC_OK;
 }
 
 int fbc_apply_host(fbc_plan* plan, const double* f_host, double* u_host, int32_t n_rhs, double alpha, double beta,

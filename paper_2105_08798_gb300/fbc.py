@@ -106,6 +106,8 @@ _SIGNATURES = {
                                  _vp]),
     "fbc_apply_host": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int32, ctypes.c_double, ctypes.c_double,
                                       ctypes.c_uint32, _vp]),
+    "fbc_apply_relaxed": (ctypes.c_int, [_vp, _vp, _vp, _vp, ctypes.c_int32, _vp, ctypes.c_double, ctypes.c_uint32,
+                                         _vp]),
     "fbc_plan_set_precision": (ctypes.c_int, [_vp, ctypes.c_int32]),
     "fbc_plan_info_get": (ctypes.c_int, [_vp, _P(fbc_plan_info)]),
     "fbc_get_mode_table": (ctypes.c_int, [_vp, _P(ctypes.c_int32), ctypes.c_int32, _P(ctypes.c_double)]),
@@ -194,6 +196,12 @@ def fbc_apply_host(plan: int, f_ptr: int, u_ptr: int, n_rhs: int, alpha: float, 
                    stream=None):
     _check(load().fbc_apply_host(plan, f_ptr, u_ptr, n_rhs, alpha, beta, flags, _stream_handle(stream)),
            "fbc_apply_host")
+
+
+def fbc_apply_relaxed(plan: int, f_new_ptr: int, f_old_ptr: int | None, u_ptr: int, n_rhs: int, alpha_ptr: int,
+                      du_max: float, flags: int, stream=None):
+    _check(load().fbc_apply_relaxed(plan, f_new_ptr, f_old_ptr, u_ptr, n_rhs, alpha_ptr, du_max, flags,
+                                    _stream_handle(stream)), "fbc_apply_relaxed")
 
 
 def fbc_plan_set_precision(plan: int, precision: int):
@@ -435,6 +443,24 @@ class Plan:
         if stream is None:
             stream = torch.cuda.current_stream(f.device)
         fbc_apply(self.handle, f.data_ptr(), u.data_ptr(), n_rhs, alpha, beta, self.flags(project, zero_mean), stream)
+        return u
+
+    def apply_relaxed(self, f_new, f_old, u, alpha, du_max: float = 0.0, project: bool = True,
+                      zero_mean: bool = False, stream=None):
+        """One relaxed FBC update on device tensors: u <- u - alpha G f_new with alpha from the residual-based
+        relaxation (f_old may be None); ``alpha`` is a float64 CUDA tensor [n_rhs], updated in place."""
+        import torch
+
+        n_rhs = f_new.shape[0]
+        for t, n in ((f_new, self.n_i), (u, self.n_p)) + (((f_old, self.n_i),) if f_old is not None else ()):
+            if t.dtype != torch.float64 or not t.is_cuda or not t.is_contiguous() or tuple(t.shape) != (n_rhs, n, self.L, 3):
+                raise ValueError("f_new, f_old and u must be contiguous float64 CUDA tensors of the plan's shapes")
+        if alpha.dtype != torch.float64 or not alpha.is_cuda or tuple(alpha.shape) != (n_rhs,):
+            raise ValueError("alpha must be a float64 CUDA tensor [n_rhs]")
+        if stream is None:
+            stream = torch.cuda.current_stream(f_new.device)
+        fbc_apply_relaxed(self.handle, f_new.data_ptr(), None if f_old is None else f_old.data_ptr(), u.data_ptr(),
+                          n_rhs, alpha.data_ptr(), du_max, self.flags(project, zero_mean), stream)
         return u
 
     def apply_host(self, f: np.ndarray, u: np.ndarray, alpha: float = 1.0, beta: float = 0.0, project: bool = True,
