@@ -1,0 +1,88 @@
+"""Oracle of the incompatibility force (Sec. 2.3.2, Eq. 21; Algorithm 1).
+
+TEST INFRASTRUCTURE ONLY (see the package docstring).  Plain numpy, FP64,
+written from the definitions:
+
+* ``stencil_apply`` -- the harmonic operator as a local block stencil,
+  ``f(a, q) = sum_n K(n) u(x_a + (n_x, n_y), (q + n_z) mod L)``, rows restricted
+  to the interface columns, each neighbour's displacement taken from the site
+  set that holds it (the relaxed atoms with u_{k+1}, the continuum nodes with
+  u_k), which is ``L^{i+|i}[u_{k+1}] + L^{i+|i++}[u_k]``.
+* ``spring_incompat_force`` -- the same quantity for the synthetic spring
+  model written as a sum of pair forces, ``f(a) = sum_bonds k v v^T / |v|^2
+  (u(a) - u(a + n))`` (the stiffness acting on the interface site), without
+  any block table.
+* ``spring_bonds`` -- the model's bonds: central springs k1 to the neighbours
+  with |n|_1 = 1 and k2 to those with |n|_1 = 2 on the lattice with in-plane
+  spacing 1 and plane spacing c.
+"""
+
+from __future__ import annotations
+
+import itertools
+
+import numpy as np
+
+
+def spring_bonds(k1: float, k2: float, c: float):
+    """[(n, k, v)] for the 18 bonds of a site: n integer offset, k stiffness, v = (n_x, n_y, c n_z)."""
+    out = []
+    for n in itertools.product((-1, 0, 1), repeat=3):
+        l1 = sum(abs(t) for t in n)
+        if l1 in (1, 2):
+            out.append((n, k1 if l1 == 1 else k2, np.array([n[0], n[1], c * n[2]], dtype=np.float64)))
+    return out
+
+
+def _site_lookup(sources):
+    where = {}
+    for s, (xy, _) in enumerate(sources):
+        for t, (x, y) in enumerate(np.asarray(xy).reshape(-1, 2)):
+            key = (int(x), int(y))
+            if key in where:
+                raise ValueError(f"site {key} is in two source sets")
+            where[key] = (s, t)
+    return where
+
+
+def _column(sources, where, x: int, y: int):
+    """u[:, column, :, :] of the site (x, y): [R][L][3]."""
+    if (x, y) not in where:
+        raise ValueError(f"site {(x, y)} is in no source set")
+    s, t = where[(x, y)]
+    return np.asarray(sources[s][1], dtype=np.float64)[:, t]
+
+
+def stencil_apply(xy_i, sources, L: int, K) -> np.ndarray:
+    """f [R][n_i][L][3] = sum over the 27 offsets of K(n) u(x_a + n_xy, q + n_z); ``sources`` is a list of
+    (xy [n][2], u [R][n][L][3]); K [27][3][3] with offset index (n_x+1)*9 + (n_y+1)*3 + (n_z+1)."""
+    K = np.asarray(K, dtype=np.float64).reshape(27, 3, 3)
+    where = _site_lookup(sources)
+    xy_i = np.asarray(xy_i).reshape(-1, 2)
+    R = np.asarray(sources[0][1]).shape[0]
+    f = np.zeros((R, len(xy_i), L, 3))
+    for a, (x, y) in enumerate(xy_i):
+        for nx, ny, nz in itertools.product((-1, 0, 1), repeat=3):
+            Kn = K[(nx + 1) * 9 + (ny + 1) * 3 + (nz + 1)]
+            if not Kn.any():
+                continue
+            col = _column(sources, where, int(x) + nx, int(y) + ny)  # [R][L][3]
+            shifted = np.roll(col, -nz, axis=1)  # shifted[:, q] = col[:, (q + nz) mod L]
+            f[:, a] += shifted @ Kn.T
+    return f
+
+
+def spring_incompat_force(xy_i, sources, L: int, c: float, k1: float, k2: float) -> np.ndarray:
+    """f [R][n_i][L][3] of the spring model as a sum of bond forces on each interface site."""
+    where = _site_lookup(sources)
+    xy_i = np.asarray(xy_i).reshape(-1, 2)
+    R = np.asarray(sources[0][1]).shape[0]
+    f = np.zeros((R, len(xy_i), L, 3))
+    bonds = spring_bonds(k1, k2, c)
+    for a, (x, y) in enumerate(xy_i):
+        u_a = _column(sources, where, int(x), int(y))
+        for n, k, v in bonds:
+            u_b = np.roll(_column(sources, where, int(x) + n[0], int(y) + n[1]), -n[2], axis=1)
+            stretch = (u_a - u_b) @ v  # [R][L]: bond elongation times |v|
+            f[:, a] += (k / float(v @ v)) * stretch[..., None] * v
+    return f

@@ -31,6 +31,7 @@ import numpy as np
 
 __all__ = [
     "ring_geometry",
+    "core_sites",
     "forces",
     "Workload",
     "WORKLOADS",
@@ -77,6 +78,20 @@ def ring_geometry(n_i: int, n_p: int) -> tuple[np.ndarray, np.ndarray]:
     xy_i = xy_inner[n_inner - n_i:]
     xy_p = xy_outer[:n_p]
     return np.ascontiguousarray(xy_i, dtype=np.int32), np.ascontiguousarray(xy_p, dtype=np.int32)
+
+
+def core_sites(n_i: int) -> np.ndarray:
+    """The sites inside the interface ring (the atomistic core, ``Lambda^a``), ``int32 [n][2]``:
+    every site with ``2 |x|^2 <= N_I`` that ``ring_geometry`` does not put in the interface, in
+    the same tie order.  Together with the interface and a pad of at least two site layers they
+    contain every site within one lattice step (in x and y) of an interface site."""
+    r2_max = int(math.ceil(n_i / 2.0)) + 1
+    xy, r2 = _sites_sorted(r2_max)
+    inner = 2 * r2 <= n_i
+    n_inner = int(inner.sum())
+    if n_inner < n_i:
+        raise ValueError("fewer sites inside the ring than interface sites")
+    return np.ascontiguousarray(xy[inner][: n_inner - n_i], dtype=np.int32)
 
 
 def forces(n_rhs: int, n_i: int, L: int, seed: int, decay: float | None = None) -> np.ndarray:
