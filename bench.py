@@ -201,6 +201,48 @@ def time_device_steps(torch, plan, fd, ud, steps, warmup, flush_buf, project=Tru
     return ms, stage / steps
 
 
+def time_harmonic_step(torch, fbc, plan, w, xy_i, xy_p, ud, steps, flush_buf):
+    """One iteration of the harmonic half of Algorithm 1 on the device: the incompatibility force of the
+    synthetic spring model (Eq. 21) from the core, interface and pad displacements, then the relaxed pad
+    update (Algorithm 2 with the du_max cap) and the zero mean (Eq. 23).  Inputs resident, L2 flushed."""
+    R, L = w.n_rhs, w.L
+    xy_c = inputs.core_sites(w.n_i)
+    K = fbc.fbc_spring_constants(1.0, 0.4, 1.0)
+    gen = torch.Generator(device="cuda").manual_seed(7)
+    u_c = 0.05 * torch.randn((R, len(xy_c), L, 3), dtype=torch.float64, device="cuda", generator=gen)
+    u_i = 0.05 * torch.randn((R, w.n_i, L, 3), dtype=torch.float64, device="cuda", generator=gen)
+    fs = [torch.empty((R, w.n_i, L, 3), dtype=torch.float64, device="cuda") for _ in range(2)]
+    alpha = torch.ones(R, dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+    with fbc.Stencil(xy_i, [xy_c, xy_i, xy_p], L, K) as st:
+        def one(it):
+            st.incompat_force([u_c, u_i, ud], f=fs[it % 2], stream=stream)
+            plan.apply_relaxed(fs[it % 2], fs[(it + 1) % 2] if it else None, ud, alpha, du_max=0.02,
+                               zero_mean=True, stream=stream)
+
+        for it in range(3):
+            flush_buf.zero_()
+            one(it)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        ev_f = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for i in range(steps):
+            flush_buf.zero_()
+            ev[i][0].record(stream)
+            ev_f[i][0].record(stream)
+            st.incompat_force([u_c, u_i, ud], f=fs[i % 2], stream=stream)
+            ev_f[i][1].record(stream)
+            plan.apply_relaxed(fs[i % 2], fs[(i + 1) % 2], ud, alpha, du_max=0.02, zero_mean=True, stream=stream)
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+        plan.sync_status()
+    ms = float(np.mean([a.elapsed_time(b) for a, b in ev]))
+    ms_f = float(np.mean([a.elapsed_time(b) for a, b in ev_f]))
+    prec = {v: k for k, v in fbc.PRECISIONS.items()}[plan.info()["precision"]]
+    return {"precision": prec, "ms_per_step": ms, "incompat_force_ms": ms_f,
+            "value": w.pair_modes / (ms * 1e-3) / 1e9, "core_sites": len(xy_c),
+            "model": "spring k1 = 1, k2 = 0.4, c = 1; du_max = 0.02; zero mean"}
+
+
 TENSOR = {"tf32": 1, "bf16x2": 3, "bf16x3": 6}  # tensor-core products per block product (split terms)
 DTYPE = {"fp64": "f64", "f32x2": "f32x2 (double-float, FP64-accurate)", "fp32": "f32",
          "tf32": "tf32 x f32-accumulate (k = 0 in double-float)",
@@ -326,6 +368,9 @@ def run_ours(args, w):
             if prec != args.precision:
                 variant(prec, max(2, args.steps // 2))
         plan.set_precision(args.precision)
+        if R == 1:
+            variants["harmonic_step"] = time_harmonic_step(torch, fbc, plan, w, xy_i, xy_p, ud,
+                                                           max(3, args.steps // 2), flush_buf)
         if args.precision in TENSOR and w.n_i > 1024:
             # the same precision with the whole interface sum in one tensor-memory accumulation group
             with fbc.Plan(xy_i, xy_p, w.L, w.material, precision=args.precision, max_rhs=R,

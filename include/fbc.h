@@ -310,6 +310,58 @@ void fbc_batch_destroy(fbc_batch* batch);
 int fbc_zero_mean_static(double* u, int32_t n_rhs, int32_t n_p, int32_t L, void* stream);
 
 /* ---------------------------------------------------------------------------
+ * Incompatibility force (Sec. 2.3.2, Eq. 21; Algorithm 1, the step between
+ * the atomistic solve and the pad update): the harmonic operator L_h,
+ * restricted to the rows of the interface columns Lambda^{i+}, applied to
+ * the displacements of the sites around them -- the relaxed atoms with their
+ * new displacements u_{k+1}, the continuum nodes with the previous ones u_k:
+ *     f_in = L_h^{i+|i}[u_{k+1}] + L_h^{i+|i++}[u_k].
+ * L_h is a local block stencil on the line-periodic lattice,
+ *     L_h[u](x, q) = sum_{n in {-1,0,1}^3} K(n) u(x + (n_x, n_y), (q + n_z) mod L),
+ * K [27][3][3] row-major with offset index (n_x+1)*9 + (n_y+1)*3 + (n_z+1);
+ * an all-zero block is skipped.  The result feeds fbc_apply_relaxed as its
+ * f_new (and, one iteration later, as its f_old).
+ * ------------------------------------------------------------------------- */
+typedef struct fbc_stencil fbc_stencil;
+
+#define FBC_STENCIL_MAX_SOURCES 4
+
+/* Force constants of a synthetic harmonic model (the paper's EAM force
+ * constants are not available): a simple lattice with in-plane spacing 1 and
+ * plane spacing c, central springs of stiffness k1 to the 6 neighbours with
+ * |n|_1 = 1 and k2 to the 12 with |n|_1 = 2.  For a spring of stiffness k
+ * along v = (n_x, n_y, c n_z): K(n) = -k v v^T / |v|^2, and
+ * K(0) = -sum_{n != 0} K(n) (a rigid translation gives no force).  For
+ * c = 1 the long-wave limit is the cubic medium C11 = k1 + 2 k2,
+ * C12 = C44 = k2.  Host only: writes K [27][3][3]. */
+int fbc_spring_constants(double k1, double k2, double c, double* K);
+
+/* Build the stencil for the interface columns xy_i [n_i][2] (the rows) and
+ * n_src source site sets xy_src[s] [n_site[s]][2] (host arrays; ownership
+ * stays with the caller).  Every in-plane neighbour of an interface site
+ * that a non-zero block reaches, the site itself included, must be in
+ * exactly one source set: a missing site, or a site in two sets, returns
+ * FBC_ERR_INVALID_ARG before anything is allocated.  L >= 1 planes.
+ * Uploads the neighbour table (36 B per interface column) and K.
+ * Synchronous. */
+int fbc_stencil_create(int32_t n_i, const int32_t* xy_i, int32_t n_src, const int32_t* const* xy_src,
+                       const int32_t* n_site, int32_t L, const double* K, fbc_stencil** out);
+
+/* f_in[r][a][q][:] = L_h[u](x_a, q) for every right-hand side r, interface
+ * column a and plane q, with u taken from the source set holding each site:
+ *   u_src: HOST array of n_src DEVICE pointers, u_src[s] double
+ *          [n_rhs][n_site[s]][L][3] (NULL allowed for an empty set);
+ *   f_in:  DEVICE double [n_rhs][n_i][L][3], overwritten; must not alias
+ *          any u_src[s].
+ * FP64 fused multiply-adds in a fixed order.  Asynchronous on `stream`;
+ * allocates nothing. */
+int fbc_incompat_force(const fbc_stencil* st, const double* const* u_src, double* f_in, int32_t n_rhs,
+                       void* stream);
+
+/* Free the stencil's device buffers (NULL is a no-op). */
+int fbc_stencil_destroy(fbc_stencil* st);
+
+/* ---------------------------------------------------------------------------
  * Learned surrogate of the mode table (an extension; the paper tabulates the
  * kernel exactly and has no learned model).  For a difference d != 0 and a
  * mode k >= 1 a multilayer perceptron 4 -> H -> H -> H -> 6 with SiLU

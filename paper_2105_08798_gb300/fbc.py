@@ -120,6 +120,11 @@ _SIGNATURES = {
     "fbc_last_error": (ctypes.c_char_p, []),
     "fbc_version": (ctypes.c_char_p, []),
     "fbc_zero_mean_static": (ctypes.c_int, [_vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _vp]),
+    "fbc_spring_constants": (ctypes.c_int, [ctypes.c_double, ctypes.c_double, ctypes.c_double, _P(ctypes.c_double)]),
+    "fbc_stencil_create": (ctypes.c_int, [ctypes.c_int32, _P(ctypes.c_int32), ctypes.c_int32, _P(_P(ctypes.c_int32)),
+                                          _P(ctypes.c_int32), ctypes.c_int32, _P(ctypes.c_double), _P(_vp)]),
+    "fbc_incompat_force": (ctypes.c_int, [_vp, _P(_vp), _vp, ctypes.c_int32, _vp]),
+    "fbc_stencil_destroy": (ctypes.c_int, [_vp]),
     "fbc_batch_create": (ctypes.c_int, [_P(_vp), ctypes.c_int32, _P(_vp), _P(_vp), _P(ctypes.c_int32), _P(_vp)]),
     "fbc_batch_apply": (ctypes.c_int, [_vp, ctypes.c_double, ctypes.c_double, ctypes.c_uint32, _vp]),
     "fbc_batch_autotune": (ctypes.c_int, [_vp, _vp, _P(ctypes.c_double)]),
@@ -263,6 +268,37 @@ def fbc_version() -> str:
 
 def fbc_zero_mean_static(u_ptr: int, n_rhs: int, n_p: int, L: int, stream=None):
     _check(load().fbc_zero_mean_static(u_ptr, n_rhs, n_p, L, _stream_handle(stream)), "fbc_zero_mean_static")
+
+
+def fbc_spring_constants(k1: float, k2: float, c: float = 1.0) -> np.ndarray:
+    """Force-constant blocks K [27][3][3] of the synthetic spring model (host only)."""
+    K = np.empty((27, 3, 3), dtype=np.float64)
+    _check(load().fbc_spring_constants(k1, k2, c, K.ctypes.data_as(_P(ctypes.c_double))), "fbc_spring_constants")
+    return K
+
+
+def fbc_stencil_create(xy_i: np.ndarray, sources: list[np.ndarray], L: int, K: np.ndarray) -> int:
+    xy_i = np.ascontiguousarray(xy_i, dtype=np.int32)
+    srcs = [np.ascontiguousarray(x, dtype=np.int32).reshape(-1, 2) for x in sources]
+    ptrs = (_P(ctypes.c_int32) * len(srcs))(*[x.ctypes.data_as(_P(ctypes.c_int32)) for x in srcs])
+    counts = (ctypes.c_int32 * len(srcs))(*[len(x) for x in srcs])
+    K = np.ascontiguousarray(K, dtype=np.float64)
+    if K.size != 27 * 9:
+        raise ValueError("K must hold 27 blocks of 3x3")
+    h = _vp()
+    _check(load().fbc_stencil_create(len(xy_i), xy_i.ctypes.data_as(_P(ctypes.c_int32)), len(srcs), ptrs, counts,
+                                     int(L), K.ctypes.data_as(_P(ctypes.c_double)), ctypes.byref(h)),
+           "fbc_stencil_create")
+    return h.value
+
+
+def fbc_incompat_force(st: int, u_ptrs: list[int | None], f_ptr: int, n_rhs: int, stream=None):
+    arr = (_vp * len(u_ptrs))(*u_ptrs)
+    _check(load().fbc_incompat_force(st, arr, f_ptr, n_rhs, _stream_handle(stream)), "fbc_incompat_force")
+
+
+def fbc_stencil_destroy(st: int):
+    _check(load().fbc_stencil_destroy(st), "fbc_stencil_destroy")
 
 
 def fbc_batch_create(plans: list[int], f_ptrs: list[int], u_ptrs: list[int], n_rhs: list[int]) -> int:
@@ -565,6 +601,59 @@ class Surrogate:
     def close(self):
         if self._h is not None:
             fbc_surrogate_destroy(self._h)
+            self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Stencil:
+    """Owning handle of one ``fbc_stencil``: the harmonic operator restricted to the interface rows."""
+
+    def __init__(self, xy_i, sources: list, L: int, K):
+        self._h = None
+        self.n_i, self.L = len(xy_i), int(L)
+        self.n_site = [len(np.asarray(x).reshape(-1, 2)) for x in sources]
+        self._h = fbc_stencil_create(xy_i, sources, L, K)
+
+    @property
+    def handle(self) -> int:
+        if self._h is None:
+            raise ValueError("stencil is closed")
+        return self._h
+
+    def incompat_force(self, u_list: list, f=None, stream=None):
+        """f_in [n_rhs][n_i][L][3] from the displacements ``u_list[s]`` [n_rhs][n_site[s]][L][3] (float64 CUDA
+        tensors, one per source set, in the order given at construction)."""
+        import torch
+
+        if len(u_list) != len(self.n_site):
+            raise ValueError("one displacement tensor per source set")
+        n_rhs = u_list[0].shape[0]
+        for u, n in zip(u_list, self.n_site):
+            if u.dtype != torch.float64 or not u.is_cuda or not u.is_contiguous() or tuple(u.shape) != (n_rhs, n, self.L, 3):
+                raise ValueError("u tensors must be contiguous float64 CUDA tensors [n_rhs][n_site][L][3]")
+        if f is None:
+            f = torch.empty((n_rhs, self.n_i, self.L, 3), dtype=torch.float64, device=u_list[0].device)
+        elif f.dtype != torch.float64 or not f.is_cuda or not f.is_contiguous() or tuple(f.shape) != (n_rhs, self.n_i, self.L, 3):
+            raise ValueError("f must be a contiguous float64 CUDA tensor [n_rhs][n_i][L][3]")
+        if stream is None:
+            stream = torch.cuda.current_stream(f.device)
+        fbc_incompat_force(self.handle, [u.data_ptr() for u in u_list], f.data_ptr(), n_rhs, stream)
+        return f
+
+    def close(self):
+        if self._h is not None:
+            fbc_stencil_destroy(self._h)
             self._h = None
 
     def __enter__(self):
