@@ -62,6 +62,14 @@ extern "C" {
 #define FBC_PREC_TF32 3   /* tensor cores (tcgen05): tf32 operands, FP32 accumulation; k = 0 in FP64 */
 #define FBC_PREC_BF16X2 4 /* tensor cores: bf16 split x = h + m, 3 products, FP32 accumulation; k = 0 in FP64 */
 #define FBC_PREC_BF16X3 5 /* tensor cores: bf16 split x = h + m + l, 6 products, FP32 accumulation; k = 0 in FP64 */
+/* In-plane FFT form (FP64): the per-mode sum over interface columns is a 2D
+ * convolution over the lattice (the kernel depends only on x_a - x_b), done
+ * exactly as a circular convolution on a power-of-two grid of at least
+ * 2 max|d| + 1 points per side, O(M log M) per mode instead of
+ * O(N_P N_I).  Needs the grid's transformed kernel (6 reals per grid point
+ * and mode, built on first use) and a workspace of at most about 1 GiB.
+ * Not for batches or plans with a surrogate. */
+#define FBC_PREC_FFT64 6
 
 /* ---- plan flags (fbc_options.flags) ----------------------------------- */
 #define FBC_PLAN_HOST_ONLY 1 /* validate and lay out on the host only: no device memory,
@@ -137,6 +145,10 @@ typedef struct fbc_plan_info {
     int32_t n_far_d;            /* used differences the surrogate serves (|d| >= r_min) */
     int32_t surrogate_chunk;    /* modes per streamed chunk (one network, near-copy and contraction launch each) */
     int32_t reserved;
+    int32_t fft_mx, fft_my;     /* in-plane FFT form: grid (0 until built) */
+    int32_t fft_rows_i, fft_rows_p; /* grid rows holding interface / pad sites */
+    int32_t fft_chunk_items;    /* (rhs, mode) items per workspace chunk: 3 launches each */
+    int32_t reserved2;
 } fbc_plan_info;
 
 /* Defaults listed in fbc_options. */

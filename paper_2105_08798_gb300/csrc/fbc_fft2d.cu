@@ -1,0 +1,481 @@
+// In-plane FFT form of the per-mode contraction (FBC_PREC_FFT64).
+//
+// The dense contraction evaluates, for every wavenumber k and right-hand side,
+//     U(a) = sum_b M^k(x_a - x_b) z(b),
+// where z(b) = x(b) + i y'(b) packs the two real 3-vectors of the six-vector
+// form into one complex 3-vector and M^k(d) is the real 3x3 matrix built from
+// the six table reals,
+//     M = [[a11, a12, -b13], [a12, a22, -b23], [b13, b23, a33]].
+// Because the kernel depends only on the lattice difference d (translation
+// invariance of the Green function in the plane, Sec. 3.1), this is a 2D
+// convolution over the lattice.  It is evaluated exactly by a circular
+// convolution on an Mx x My grid with Mx, My powers of two of at least
+// 2 max|d| + 1: every difference d that occurs, and its mirror -d, then has a
+// residue of its own, so the circular sum at a pad site picks up exactly the
+// terms of the direct sum.  The kernel is placed at d with the table values
+// and at -d with the exact mirror relations of the Green function (a_ij even
+// and b_i3 odd in d), which makes its 2D DFT the Hermitian matrix
+//     Mhat = [[A11, A12, -i B13], [A12, A22, -i B23], [i B13, i B23, A33]]
+// with six real fields A11, A12, A22, A33 (the DFTs of the even a_ij) and
+// B13, B23 (DFT(b_i3) = i B_i3); they are computed once per plan.
+//
+// One apply, per (right-hand side, mode) item:
+//   P1  gather z of every interface row onto its grid row, forward FFT along x
+//       (only the rows that hold interface sites);
+//   P2  per grid column: forward FFT along y, multiply by Mhat, inverse FFT
+//       along y; keep only the rows that hold pad sites;
+//   P3  inverse FFT along x of every pad row, scale by 1/(Mx My) and scatter
+//       the pad sites into uh.
+// Radix-2 transforms in shared memory, FP64 throughout: decimation in time
+// with bit-reversed loads for the forward transforms (natural-order output),
+// decimation in frequency for the inverse ones (natural-order input,
+// bit-reversed output, read back at bit-reversed positions), so no pass
+// reorders data.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <new>
+#include <map>
+#include <set>
+#include <vector>
+
+#include "fbc_internal.cuh"
+
+namespace fbc {
+
+struct FftGrid {
+    int Mx = 0, My = 0, logMx = 0, logMy = 0;
+    int ny_i = 0, ny_p = 0;
+    int Q = 0;                     // (rhs, mode) items per chunk of the workspace
+    int* d_row_i = nullptr;        // [ny_i + 1] CSR of the interface rows
+    int2* d_ent_i = nullptr;       // (bit-reversed x position, fh slot)
+    int* d_row_p = nullptr;        // [ny_p + 1]
+    int2* d_ent_p = nullptr;       // (bit-reversed x position, uh slot)
+    int* d_ypos_i = nullptr;       // [ny_i] bit-reversed y position of each interface row
+    int* d_ypos_p = nullptr;       // [ny_p]
+    double2* d_twx = nullptr;      // [Mx / 2] exp(-2 pi i j / Mx)
+    double2* d_twy = nullptr;      // [My / 2]
+    double* d_mhat = nullptr;      // [K][Mx][My][6]: A11 A12 A22 A33 B13 B23
+    double2* d_T1 = nullptr;       // [Q][Mx][ny_i][3]
+    double2* d_T2 = nullptr;       // [Q][Mx][ny_p][3]
+    int2* d_used = nullptr;        // [n_used] differences placed on the grid (table entries)
+    unsigned char* d_mirror = nullptr;  // [n_used] 1: also place the mirror -d (it is not a table entry)
+    int n_used = 0;
+    size_t bytes = 0;
+};
+
+namespace {
+
+constexpr int kFftThreads = 256;
+constexpr int kRowElems = 1024;  // complex elements per component a block of P1 / P3 transforms
+
+inline int ilog2(int v) {
+    int l = 0;
+    while ((1 << l) < v) l++;
+    return l;
+}
+
+inline int brev(int v, int bits) {
+    int r = 0;
+    for (int t = 0; t < bits; t++) r |= ((v >> t) & 1) << (bits - 1 - t);
+    return r;
+}
+
+__device__ __forceinline__ int brev_dev(int v, int bits) { return (int)(__brev((unsigned)v) >> (32 - bits)); }
+
+__device__ __forceinline__ double2 cmul(double2 a, double2 w) {
+    return make_double2(fma(a.x, w.x, -a.y * w.y), fma(a.x, w.y, a.y * w.x));
+}
+
+// nseq transforms of length 2^logN, back to back in s; input bit-reversed, output natural
+template <bool INV>
+__device__ void fft_dit(double2* s, int nseq, int logN, const double2* __restrict__ tw) {
+    const int half = 1 << (logN - 1);
+    const int nb = nseq * half;
+    for (int st = 0; st < logN; st++) {
+        const int h = 1 << st, tstep = half >> st;
+        for (int t = threadIdx.x; t < nb; t += blockDim.x) {
+            const int seq = t >> (logN - 1), b = t & (half - 1), j = b & (h - 1);
+            const int i0 = (seq << logN) + ((b >> st) << (st + 1)) + j, i1 = i0 + h;
+            double2 w = __ldg(tw + j * tstep);
+            if (INV) w.y = -w.y;
+            const double2 a = s[i0], v = cmul(s[i1], w);
+            s[i0] = make_double2(a.x + v.x, a.y + v.y);
+            s[i1] = make_double2(a.x - v.x, a.y - v.y);
+        }
+        __syncthreads();
+    }
+}
+
+// input natural, output bit-reversed
+template <bool INV>
+__device__ void fft_dif(double2* s, int nseq, int logN, const double2* __restrict__ tw) {
+    const int half = 1 << (logN - 1);
+    const int nb = nseq * half;
+    for (int st = logN - 1; st >= 0; st--) {
+        const int h = 1 << st, tstep = half >> st;
+        for (int t = threadIdx.x; t < nb; t += blockDim.x) {
+            const int seq = t >> (logN - 1), b = t & (half - 1), j = b & (h - 1);
+            const int i0 = (seq << logN) + ((b >> st) << (st + 1)) + j, i1 = i0 + h;
+            double2 w = __ldg(tw + j * tstep);
+            if (INV) w.y = -w.y;
+            const double2 a = s[i0], c = s[i1];
+            s[i0] = make_double2(a.x + c.x, a.y + c.y);
+            s[i1] = cmul(make_double2(a.x - c.x, a.y - c.y), w);
+        }
+        __syncthreads();
+    }
+}
+
+struct FftArgs {
+    const double* fh;
+    double* uh;
+    const double* mhat;
+    double2* T1;
+    double2* T2;
+    const int* row_i;
+    const int2* ent_i;
+    const int* row_p;
+    const int2* ent_p;
+    const int* ypos_i;
+    const int* ypos_p;
+    const double2* twx;
+    const double2* twy;
+    int Mx, My, logMx, logMy, ny_i, ny_p, K, NIpad, NPpad, item0;
+    double scale;
+};
+
+// P1: rows of interface sites, forward FFT along x.  Block: G rows of one item.
+__global__ void __launch_bounds__(kFftThreads) k_fft_rows_fwd(FftArgs A, int G) {
+    extern __shared__ double2 s[];  // [G][3][Mx]
+    const int iq = blockIdx.y, item = A.item0 + iq, r = item / A.K, k = item - r * A.K;
+    const int row0 = blockIdx.x * G, n = G * 3 * A.Mx;
+    for (int t = threadIdx.x; t < n; t += blockDim.x) s[t] = make_double2(0.0, 0.0);
+    __syncthreads();
+    const double* fk = A.fh + ((size_t)r * A.K + k) * A.NIpad * 6;
+    for (int g = 0; g < G && row0 + g < A.ny_i; g++) {
+        const int e0 = A.row_i[row0 + g], e1 = A.row_i[row0 + g + 1];
+        for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+            const int2 en = A.ent_i[e];
+            const double* v = fk + (size_t)en.y * 6;
+            for (int c = 0; c < 3; c++) s[(g * 3 + c) * A.Mx + en.x] = make_double2(v[c], v[3 + c]);
+        }
+    }
+    __syncthreads();
+    fft_dit<false>(s, G * 3, A.logMx, A.twx);
+    const int gr = min(G, A.ny_i - row0);
+    double2* out = A.T1 + (size_t)iq * A.Mx * A.ny_i * 3;
+    for (int t = threadIdx.x; t < A.Mx * gr * 3; t += blockDim.x) {
+        const int c = t % 3, g = (t / 3) % gr, xi = t / (3 * gr);
+        out[((size_t)xi * A.ny_i + row0 + g) * 3 + c] = s[(g * 3 + c) * A.Mx + xi];
+    }
+}
+
+// P2: G grid columns of one item: forward FFT along y, Mhat, inverse FFT along y, pad rows out.
+__global__ void __launch_bounds__(kFftThreads) k_fft_cols(FftArgs A, int G) {
+    extern __shared__ double2 s[];  // [G][3][My]
+    const int iq = blockIdx.y, item = A.item0 + iq, r = item / A.K, k = item - r * A.K;
+    const int xi0 = blockIdx.x * G, n = G * 3 * A.My;
+    for (int t = threadIdx.x; t < n; t += blockDim.x) s[t] = make_double2(0.0, 0.0);
+    __syncthreads();
+    const double2* in = A.T1 + (size_t)iq * A.Mx * A.ny_i * 3;
+    for (int t = threadIdx.x; t < G * A.ny_i * 3; t += blockDim.x) {
+        const int c = t % 3, row = (t / 3) % A.ny_i, g = t / (3 * A.ny_i);
+        s[(g * 3 + c) * A.My + A.ypos_i[row]] = in[((size_t)(xi0 + g) * A.ny_i + row) * 3 + c];
+    }
+    __syncthreads();
+    fft_dit<false>(s, G * 3, A.logMy, A.twy);
+    for (int t = threadIdx.x; t < G * A.My; t += blockDim.x) {
+        const int g = t / A.My, et = t - g * A.My;
+        const double* m = A.mhat + (((size_t)k * A.Mx + xi0 + g) * A.My + et) * 6;
+        const double a11 = m[0], a12 = m[1], a22 = m[2], a33 = m[3], b13 = m[4], b23 = m[5];
+        double2* z = s + g * 3 * A.My + et;
+        const double2 z0 = z[0], z1 = z[A.My], z2 = z[2 * A.My];
+        // (-i b) z = (b z.y, -b z.x),  (i b) z = (-b z.y, b z.x)
+        z[0] = make_double2(fma(a11, z0.x, fma(a12, z1.x, b13 * z2.y)), fma(a11, z0.y, fma(a12, z1.y, -b13 * z2.x)));
+        z[A.My] = make_double2(fma(a12, z0.x, fma(a22, z1.x, b23 * z2.y)), fma(a12, z0.y, fma(a22, z1.y, -b23 * z2.x)));
+        z[2 * A.My] = make_double2(fma(a33, z2.x, -fma(b13, z0.y, b23 * z1.y)), fma(a33, z2.y, fma(b13, z0.x, b23 * z1.x)));
+    }
+    __syncthreads();
+    fft_dif<true>(s, G * 3, A.logMy, A.twy);
+    double2* out = A.T2 + (size_t)iq * A.Mx * A.ny_p * 3;
+    for (int t = threadIdx.x; t < G * A.ny_p * 3; t += blockDim.x) {
+        const int c = t % 3, row = (t / 3) % A.ny_p, g = t / (3 * A.ny_p);
+        out[((size_t)(xi0 + g) * A.ny_p + row) * 3 + c] = s[(g * 3 + c) * A.My + A.ypos_p[row]];
+    }
+}
+
+// P3: G pad rows of one item: inverse FFT along x, scale, scatter the pad sites into uh.
+__global__ void __launch_bounds__(kFftThreads) k_fft_rows_inv(FftArgs A, int G) {
+    extern __shared__ double2 s[];  // [G][3][Mx]
+    const int iq = blockIdx.y, item = A.item0 + iq, r = item / A.K, k = item - r * A.K;
+    const int row0 = blockIdx.x * G, gr = min(G, A.ny_p - row0);
+    const double2* in = A.T2 + (size_t)iq * A.Mx * A.ny_p * 3;
+    for (int t = threadIdx.x; t < A.Mx * G * 3; t += blockDim.x) {
+        const int c = t % 3, g = (t / 3) % G, xi = t / (3 * G);
+        s[(g * 3 + c) * A.Mx + xi] = g < gr ? in[((size_t)xi * A.ny_p + row0 + g) * 3 + c] : make_double2(0.0, 0.0);
+    }
+    __syncthreads();
+    fft_dif<true>(s, G * 3, A.logMx, A.twx);
+    double* uk = A.uh + ((size_t)r * A.K + k) * A.NPpad * 6;
+    for (int g = 0; g < gr; g++) {
+        const int e0 = A.row_p[row0 + g], e1 = A.row_p[row0 + g + 1];
+        for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+            const int2 en = A.ent_p[e];
+            double* o = uk + (size_t)en.y * 6;
+            for (int c = 0; c < 3; c++) {
+                const double2 v = s[(g * 3 + c) * A.Mx + en.x];
+                o[c] = v.x * A.scale, o[3 + c] = v.y * A.scale;
+            }
+        }
+    }
+}
+
+// ---- the kernel's transform (setup) ----------------------------------------
+
+// place the six table fields of modes k0 .. k0 + nk - 1 on the grid: S [nk][6][My][Mx] complex (zeroed before)
+__global__ void k_fft_place(const double* __restrict__ tab, const int2* __restrict__ used,
+                            const unsigned char* __restrict__ mirror, int n_used, int k0, int nk, int Dx, int Dy,
+                            int box_x0, int box_y0, int Mx, int My, double2* __restrict__ S) {
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (long long)n_used * nk) return;
+    const int u = (int)(t % n_used), kk = (int)(t / n_used);
+    const int2 d = used[u];
+    const double* v = tab + (((size_t)(k0 + kk) * Dy + (d.y - box_y0)) * Dx + (d.x - box_x0)) * 6;
+    const int px = ((d.x % Mx) + Mx) % Mx, py = ((d.y % My) + My) % My;
+    const int qx = (Mx - px) % Mx, qy = (My - py) % My;
+    double2* base = S + (size_t)kk * 6 * My * Mx;
+    for (int f = 0; f < 6; f++) {
+        base[((size_t)f * My + py) * Mx + px] = make_double2(v[f], 0.0);
+        if (mirror[u]) base[((size_t)f * My + qy) * Mx + qx] = make_double2(f < 4 ? v[f] : -v[f], 0.0);
+    }
+}
+
+// forward FFT along x of G rows (of length Mx) per block, in place in global memory
+__global__ void __launch_bounds__(kFftThreads) k_fft_dense_rows(double2* S, int Mx, int logMx, int G,
+                                                                 const double2* __restrict__ twx) {
+    extern __shared__ double2 s[];
+    double2* rows = S + ((size_t)blockIdx.y * gridDim.x + blockIdx.x) * G * Mx;
+    for (int t = threadIdx.x; t < G * Mx; t += blockDim.x) {
+        const int g = t / Mx, x = t - g * Mx;
+        s[g * Mx + brev_dev(x, logMx)] = rows[t];
+    }
+    __syncthreads();
+    fft_dit<false>(s, G, logMx, twx);
+    for (int t = threadIdx.x; t < G * Mx; t += blockDim.x) rows[t] = s[t];
+}
+
+// forward FFT along y of G columns of all six fields of one mode, then Mhat [k][Mx][My][6]
+__global__ void __launch_bounds__(kFftThreads) k_fft_dense_cols(const double2* __restrict__ S, int Mx, int My,
+                                                                 int logMy, int G, int k0,
+                                                                 const double2* __restrict__ twy,
+                                                                 double* __restrict__ mhat) {
+    extern __shared__ double2 s[];  // [6][G][My]
+    const int kk = blockIdx.y, xi0 = blockIdx.x * G;
+    const double2* base = S + (size_t)kk * 6 * My * Mx;
+    for (int t = threadIdx.x; t < 6 * G * My; t += blockDim.x) {
+        const int g = t % G, y = (t / G) % My, f = t / (G * My);
+        s[(f * G + g) * My + brev_dev(y, logMy)] = base[((size_t)f * My + y) * Mx + xi0 + g];
+    }
+    __syncthreads();
+    fft_dit<false>(s, 6 * G, logMy, twy);
+    for (int t = threadIdx.x; t < G * My * 6; t += blockDim.x) {
+        const int f = t % 6, et = (t / 6) % My, g = t / (6 * My);
+        const double2 v = s[(f * G + g) * My + et];
+        mhat[(((size_t)(k0 + kk) * Mx + xi0 + g) * My + et) * 6 + f] = f < 4 ? v.x : v.y;
+    }
+}
+
+}  // namespace
+
+void fft_free(Plan& P) {
+    FftGrid* F = P.fft;
+    if (!F) return;
+    void* bufs[] = {F->d_row_i, F->d_ent_i, F->d_row_p, F->d_ent_p, F->d_ypos_i, F->d_ypos_p, F->d_twx,
+                    F->d_twy,   F->d_mhat,  F->d_T1,    F->d_T2,    F->d_used,   F->d_mirror};
+    for (void* b : bufs)
+        if (b) cudaFree(b);
+    delete F;
+    P.fft = nullptr;
+}
+
+void fft_info(const Plan& P, int* mx, int* my, int* rows_i, int* rows_p, int* chunk_items) {
+    const FftGrid* F = P.fft;
+    *mx = F ? F->Mx : 0, *my = F ? F->My : 0;
+    *rows_i = F ? F->ny_i : 0, *rows_p = F ? F->ny_p : 0;
+    *chunk_items = F ? F->Q : 0;
+}
+
+int fft_prepare(Plan& P) {
+    if (P.fft) return FBC_OK;
+    char msg[256];
+    // the differences that occur (device list of the plan)
+    std::vector<int2> used(P.n_used);
+    if (P.n_used && cudaMemcpy(used.data(), P.d_used, sizeof(int2) * P.n_used, cudaMemcpyDeviceToHost))
+        return report_error(FBC_ERR_CUDA, "in-plane FFT: copy of the difference list failed");
+    int ex = 0, ey = 0;
+    std::set<std::pair<int, int>> uset;
+    for (const int2& d : used) {
+        ex = std::max(ex, std::abs(d.x)), ey = std::max(ey, std::abs(d.y));
+        uset.insert({d.x, d.y});
+    }
+    FftGrid* F = new (std::nothrow) FftGrid();
+    if (!F) return report_error(FBC_ERR_OOM, "host allocation failed");
+    F->logMx = std::max(1, ilog2(2 * ex + 1)), F->logMy = std::max(1, ilog2(2 * ey + 1));
+    F->Mx = 1 << F->logMx, F->My = 1 << F->logMy;
+    if (F->Mx > 2048 || F->My > 2048) {
+        delete F;
+        snprintf(msg, sizeof(msg), "in-plane FFT: grid %d x %d above 2048 per side", 1 << F->logMx, 1 << F->logMy);
+        return report_error(FBC_ERR_UNSUPPORTED, msg);
+    }
+    const int Mx = F->Mx, My = F->My;
+    int ox = 1 << 30, oy = 1 << 30;
+    for (int s = 0; s < P.NIpad; s++)
+        if (P.perm_i[s] >= 0) ox = std::min(ox, P.xy_i_sorted[s].x), oy = std::min(oy, P.xy_i_sorted[s].y);
+    auto rows_of = [&](const std::vector<int>& perm, const std::vector<int2>& xy, int npad, std::vector<int>& row,
+                       std::vector<int2>& ent, std::vector<int>& ypos) -> bool {
+        std::map<int, std::vector<int2>> by_y;
+        for (int s = 0; s < npad; s++)
+            if (perm[s] >= 0) by_y[xy[s].y].push_back(make_int2(xy[s].x, s));
+        std::set<int> yres;
+        row.assign(1, 0);
+        for (auto& kv : by_y) {
+            const int yr = (((kv.first - oy) % My) + My) % My;
+            if (!yres.insert(yr).second) return false;
+            std::set<int> xres;
+            for (const int2& e : kv.second) {
+                const int xr = (((e.x - ox) % Mx) + Mx) % Mx;
+                if (!xres.insert(xr).second) return false;
+                ent.push_back(make_int2(brev(xr, F->logMx), e.y));
+            }
+            row.push_back((int)ent.size());
+            ypos.push_back(brev(yr, F->logMy));
+        }
+        return true;
+    };
+    std::vector<int> row_i, row_p, ypos_i, ypos_p;
+    std::vector<int2> ent_i, ent_p;
+    if (!rows_of(P.perm_i, P.xy_i_sorted, P.NIpad, row_i, ent_i, ypos_i) ||
+        !rows_of(P.perm_p, P.xy_p_sorted, P.NPpad, row_p, ent_p, ypos_p)) {
+        delete F;
+        return report_error(FBC_ERR_UNSUPPORTED, "in-plane FFT: two sites share a grid residue");
+    }
+    F->ny_i = (int)ypos_i.size(), F->ny_p = (int)ypos_p.size();
+    std::vector<unsigned char> mirror(used.size());
+    for (size_t u = 0; u < used.size(); u++) mirror[u] = uset.count({-used[u].x, -used[u].y}) ? 0 : 1;
+    // workspace for Q (rhs, mode) items at a time, at most about 1 GiB
+    const size_t per_item = (size_t)Mx * (F->ny_i + F->ny_p) * 3 * sizeof(double2);
+    const size_t items = (size_t)P.opt.max_rhs * P.K;
+    F->Q = (int)std::max<size_t>(1, std::min<size_t>({items, (size_t)65535, ((size_t)1 << 30) / per_item}));
+    std::vector<double2> twx(Mx / 2), twy(My / 2);
+    for (int j = 0; j < Mx / 2; j++) twx[j] = make_double2(cos(2.0 * M_PI * j / Mx), -sin(2.0 * M_PI * j / Mx));
+    for (int j = 0; j < My / 2; j++) twy[j] = make_double2(cos(2.0 * M_PI * j / My), -sin(2.0 * M_PI * j / My));
+    cudaError_t e = cudaSuccess;
+    size_t bytes = 0;
+    auto alloc = [&](auto** p, size_t n) {
+        if (e) return;
+        e = cudaMalloc((void**)p, std::max<size_t>(1, n) * sizeof(**p));
+        bytes += n * sizeof(**p);
+    };
+    auto up = [&](auto* dst, const auto& src) {
+        if (!e && !src.empty()) e = cudaMemcpy(dst, src.data(), src.size() * sizeof(src[0]), cudaMemcpyHostToDevice);
+    };
+    alloc(&F->d_row_i, row_i.size());
+    alloc(&F->d_ent_i, ent_i.size());
+    alloc(&F->d_row_p, row_p.size());
+    alloc(&F->d_ent_p, ent_p.size());
+    alloc(&F->d_ypos_i, ypos_i.size());
+    alloc(&F->d_ypos_p, ypos_p.size());
+    alloc(&F->d_twx, twx.size());
+    alloc(&F->d_twy, twy.size());
+    alloc(&F->d_mhat, (size_t)P.K * Mx * My * 6);
+    alloc(&F->d_T1, (size_t)F->Q * Mx * F->ny_i * 3);
+    alloc(&F->d_T2, (size_t)F->Q * Mx * F->ny_p * 3);
+    alloc(&F->d_used, used.size());
+    alloc(&F->d_mirror, mirror.size());
+    up(F->d_row_i, row_i), up(F->d_ent_i, ent_i), up(F->d_row_p, row_p), up(F->d_ent_p, ent_p);
+    up(F->d_ypos_i, ypos_i), up(F->d_ypos_p, ypos_p), up(F->d_twx, twx), up(F->d_twy, twy);
+    up(F->d_used, used), up(F->d_mirror, mirror);
+    F->n_used = (int)used.size();
+    F->bytes = bytes;
+    P.fft = F;
+    if (e) {
+        fft_free(P);
+        snprintf(msg, sizeof(msg), "in-plane FFT setup: %s", cudaGetErrorString(e));
+        return report_error(e == cudaErrorMemoryAllocation ? FBC_ERR_OOM : FBC_ERR_CUDA, msg);
+    }
+    P.workspace_bytes += bytes;
+    return FBC_OK;
+}
+
+cudaError_t launch_fft_tables(Plan& P, cudaStream_t st) {
+    FftGrid* F = P.fft;
+    if (!F) return cudaErrorInvalidValue;
+    const int Mx = F->Mx, My = F->My;
+    const size_t per_k = (size_t)6 * Mx * My * sizeof(double2);
+    const int nk = (int)std::max<size_t>(1, std::min<size_t>(P.K, ((size_t)512 << 20) / per_k));
+    double2* S = nullptr;
+    cudaError_t e = cudaMallocAsync((void**)&S, per_k * nk, st);
+    if (e) return e;
+    const int Gr = std::max(1, std::min(My, kRowElems / Mx));
+    const int Gc = std::max(1, std::min(Mx, (kRowElems / 4) / My));  // six fields per column group
+    const size_t smem_dc = (size_t)6 * Gc * My * sizeof(double2);
+    if (smem_dc > 48 * 1024)
+        cudaFuncSetAttribute(k_fft_dense_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_dc);
+    for (int k0 = 0; k0 < P.K && !e; k0 += nk) {
+        const int n = std::min(nk, P.K - k0);
+        e = cudaMemsetAsync(S, 0, per_k * n, st);
+        if (e) break;
+        const long long threads = (long long)F->n_used * n;
+        if (threads > 0) {
+            k_fft_place<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(P.d_table, F->d_used, F->d_mirror,
+                                                                           F->n_used, k0, n, P.Dx, P.Dy, P.box_x0,
+                                                                           P.box_y0, Mx, My, S);
+            if ((e = cudaGetLastError())) break;
+        }
+        k_fft_dense_rows<<<dim3(My / Gr, n * 6), kFftThreads, (size_t)Gr * Mx * sizeof(double2), st>>>(
+            S, Mx, F->logMx, Gr, F->d_twx);
+        if ((e = cudaGetLastError())) break;
+        k_fft_dense_cols<<<dim3(Mx / Gc, n), kFftThreads, smem_dc, st>>>(
+            S, Mx, My, F->logMy, Gc, k0, F->d_twy, F->d_mhat);
+        e = cudaGetLastError();
+    }
+    cudaError_t e2 = cudaFreeAsync(S, st);
+    return e ? e : e2;
+}
+
+cudaError_t launch_contract_fft(Plan& P, int n_rhs, cudaStream_t st) {
+    FftGrid* F = P.fft;
+    if (!F || !F->d_mhat) return cudaErrorInvalidValue;
+    FftArgs A{};
+    A.fh = P.d_fh, A.uh = P.d_uh, A.mhat = F->d_mhat, A.T1 = F->d_T1, A.T2 = F->d_T2;
+    A.row_i = F->d_row_i, A.ent_i = F->d_ent_i, A.row_p = F->d_row_p, A.ent_p = F->d_ent_p;
+    A.ypos_i = F->d_ypos_i, A.ypos_p = F->d_ypos_p, A.twx = F->d_twx, A.twy = F->d_twy;
+    A.Mx = F->Mx, A.My = F->My, A.logMx = F->logMx, A.logMy = F->logMy, A.ny_i = F->ny_i, A.ny_p = F->ny_p;
+    A.K = P.K, A.NIpad = P.NIpad, A.NPpad = P.NPpad;
+    A.scale = 1.0 / ((double)F->Mx * (double)F->My);
+    const int Gr = std::max(1, kRowElems / F->Mx);
+    const int Gc = std::max(1, std::min(F->Mx, kRowElems / F->My));
+    const size_t smem_r = (size_t)Gr * 3 * F->Mx * sizeof(double2);
+    const size_t smem_c = (size_t)Gc * 3 * F->My * sizeof(double2);
+    if (smem_r > 48 * 1024) {
+        cudaFuncSetAttribute(k_fft_rows_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_r);
+        cudaFuncSetAttribute(k_fft_rows_inv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_r);
+    }
+    if (smem_c > 48 * 1024) cudaFuncSetAttribute(k_fft_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_c);
+    const int items = n_rhs * P.K;
+    for (int i0 = 0; i0 < items; i0 += F->Q) {
+        const int q = std::min(F->Q, items - i0);
+        A.item0 = i0;
+        k_fft_rows_fwd<<<dim3((F->ny_i + Gr - 1) / Gr, q), kFftThreads, smem_r, st>>>(A, Gr);
+        cudaError_t e = cudaGetLastError();
+        if (e) return e;
+        k_fft_cols<<<dim3(F->Mx / Gc, q), kFftThreads, smem_c, st>>>(A, Gc);
+        if ((e = cudaGetLastError())) return e;
+        k_fft_rows_inv<<<dim3((F->ny_p + Gr - 1) / Gr, q), kFftThreads, smem_r, st>>>(A, Gr);
+        if ((e = cudaGetLastError())) return e;
+    }
+    return cudaSuccess;
+}
+
+}  // namespace fbc

@@ -48,6 +48,8 @@ struct TabulateParams {
     int box_x0, box_y0, Dx, Dy;
 };
 
+struct FftGrid;  // in-plane FFT form (fbc_fft2d.cu)
+
 struct Plan {
     int device = 0;
     int n_i = 0, n_p = 0, L = 0, K = 0, logL = 0;
@@ -107,6 +109,7 @@ struct Plan {
     int bprep_prec = -1;
     bool timing = false, timed_once = false;
     size_t table_bytes = 0, workspace_bytes = 0;
+    FftGrid* fft = nullptr;  // in-plane FFT form: grid, transformed kernel, workspace
 };
 
 // Everything a contraction tile needs about one plan (one instance of a batch).
@@ -153,6 +156,13 @@ cudaError_t launch_relax_dots(const double* f_new, const double* f_old, size_t n
 cudaError_t launch_relax_alpha(const double* dot_part, int has_old, const double* gmax_part, int n_gblk, int n_rhs,
                                double du_max, double* alpha_io, cudaStream_t st);
 cudaError_t launch_derive_tables(Plan& P, int precision, cudaStream_t st);
+// in-plane FFT form (fbc_fft2d.cu): host structures and buffers (once; needs the uploaded difference
+// list), the grid's transformed kernel from the FP64 table, the contraction, release
+int fft_prepare(Plan& P);
+cudaError_t launch_fft_tables(Plan& P, cudaStream_t st);
+cudaError_t launch_contract_fft(Plan& P, int n_rhs, cudaStream_t st);
+void fft_free(Plan& P);
+void fft_info(const Plan& P, int* mx, int* my, int* rows_i, int* rows_p, int* chunk_items);
 ContractArgs make_contract_args(const Plan& P);
 cudaError_t launch_contract_tc(const ContractArgs& A, const Plan& P, int n_rhs, cudaStream_t st, int n_modes = -1);
 // contraction of modes k0 .. k0 + n_modes - 1 in the plan's precision (k0 >= 1 for the FP32 and tensor forms)

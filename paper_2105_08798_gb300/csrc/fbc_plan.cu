@@ -200,6 +200,7 @@ void free_plan(fbc::Plan& P) {
     for (auto& e : P.ev)
         if (e) cudaEventDestroy(e), e = nullptr;
     fbc::release_surrogate_buffers(P);
+    fbc::fft_free(P);
 }
 
 // Allocate the derived table a reduced-precision contraction reads (once).
@@ -315,7 +316,7 @@ int fbc_plan_create(const fbc_geometry* geom, const fbc_material* mat, const fbc
         return fail(FBC_ERR_INVALID_ARG, "Richardson needs n >= 1, 0 <= N <= 12, n + N <= %d", fbc::kMaxRichImages);
     if (opt.quad < 8 || opt.quad > fbc::kMaxQuad) return fail(FBC_ERR_INVALID_ARG, "quad must be in [8, %d]", fbc::kMaxQuad);
     if (opt.max_rhs < 1 || opt.max_rhs > 4096) return fail(FBC_ERR_INVALID_ARG, "max_rhs must be in [1, 4096]");
-    if (opt.precision < FBC_PREC_FP64 || opt.precision > FBC_PREC_BF16X3)
+    if (opt.precision < FBC_PREC_FP64 || opt.precision > FBC_PREC_FFT64)
         return fail(FBC_ERR_INVALID_ARG, "unknown precision %d", opt.precision);
     if (opt.flags & ~(FBC_PLAN_HOST_ONLY | FBC_PLAN_TC_FAST_ACCUMULATE))
         return fail(FBC_ERR_INVALID_ARG, "unknown options.flags bits 0x%x", opt.flags);
@@ -508,6 +509,9 @@ int fbc_tabulate_kernel(fbc_plan* plan, void* stream) {
     cudaError_t e = fbc::launch_tabulate(P, st);
     if (e != cudaSuccess) return cuda_fail(e, "tabulate");
     P.tabulated = true;
+    if (P.precision == FBC_PREC_FFT64) {
+        if (int s = fbc::fft_prepare(P)) return s;
+    }
     if (P.precision != FBC_PREC_FP64) {
         e = fbc::launch_derive_tables(P, P.precision, st);
         if (e != cudaSuccess) return cuda_fail(e, "derive tables");
@@ -518,7 +522,7 @@ int fbc_tabulate_kernel(fbc_plan* plan, void* stream) {
 int fbc_plan_set_precision(fbc_plan* plan, int32_t precision) {
     g_last_error.clear();
     if (!plan) return fail(FBC_ERR_INVALID_ARG, "plan is NULL");
-    if (precision < FBC_PREC_FP64 || precision > FBC_PREC_BF16X3)
+    if (precision < FBC_PREC_FP64 || precision > FBC_PREC_FFT64)
         return fail(FBC_ERR_INVALID_ARG, "unknown precision %d", precision);
     fbc::Plan& P = plan->p;
     if (P.host_only) return fail(FBC_ERR_INVALID_ARG, "host-only plan");
@@ -526,6 +530,9 @@ int fbc_plan_set_precision(fbc_plan* plan, int32_t precision) {
     if (P.sur && precision != FBC_PREC_FP32 && !fbc::is_tensor_precision(precision))
         return fail(FBC_ERR_UNSUPPORTED, "detach the surrogate before switching to this precision");
     if (int st = ensure_derived(P, precision)) return st;
+    if (precision == FBC_PREC_FFT64 && P.tabulated) {
+        if (int st = fbc::fft_prepare(P)) return st;
+    }
     P.precision = precision;
     if (P.tabulated && precision != FBC_PREC_FP64) {
         cudaError_t e = fbc::launch_derive_tables(P, precision, 0);
@@ -555,6 +562,7 @@ static int apply_checks(fbc::Plan& P, const double* f, const double* u, int32_t 
     if (fbc::is_tensor_precision(P.precision) && fbc::contract_tc_smem(P.precision, P.W * P.H) > 227 * 1024)
         return fail(FBC_ERR_UNSUPPORTED, "tensor-core contraction: staged sub-box too large for shared memory");
     if (P.precision == FBC_PREC_F32X2 && !P.d_table_x2) return fail(FBC_ERR_INVALID_ARG, "F32X2 table missing");
+    if (P.precision == FBC_PREC_FFT64 && !P.fft) return fail(FBC_ERR_INVALID_ARG, "in-plane FFT grid missing");
     return FBC_OK;
 }
 
@@ -699,6 +707,8 @@ int fbc_plan_info_get(const fbc_plan* plan, fbc_plan_info* info) {
     info->n_far_d = P.n_far;
     info->surrogate_chunk = P.sur_chunk;
     info->reserved = 0;
+    fbc::fft_info(P, &info->fft_mx, &info->fft_my, &info->fft_rows_i, &info->fft_rows_p, &info->fft_chunk_items);
+    info->reserved2 = 0;
     info->workspace_bytes = P.workspace_bytes;
     return FBC_OK;
 }

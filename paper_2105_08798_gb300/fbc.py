@@ -38,8 +38,9 @@ FBC_PREC_F32X2 = 2
 FBC_PREC_TF32 = 3
 FBC_PREC_BF16X2 = 4
 FBC_PREC_BF16X3 = 5
+FBC_PREC_FFT64 = 6
 PRECISIONS = {"fp64": FBC_PREC_FP64, "fp32": FBC_PREC_FP32, "f32x2": FBC_PREC_F32X2, "tf32": FBC_PREC_TF32,
-              "bf16x2": FBC_PREC_BF16X2, "bf16x3": FBC_PREC_BF16X3}
+              "bf16x2": FBC_PREC_BF16X2, "bf16x3": FBC_PREC_BF16X3, "fft64": FBC_PREC_FFT64}
 
 FBC_PLAN_HOST_ONLY = 1
 FBC_PLAN_TC_FAST_ACCUMULATE = 2
@@ -78,7 +79,8 @@ class fbc_plan_info(ctypes.Structure):
         ("pair_modes_per_rhs", ctypes.c_double), ("table_bytes", ctypes.c_size_t),
         ("workspace_bytes", ctypes.c_size_t), ("surrogate_bytes", ctypes.c_size_t),
         ("surrogate_attached", ctypes.c_int32), ("n_far_d", ctypes.c_int32), ("surrogate_chunk", ctypes.c_int32),
-        ("reserved", ctypes.c_int32)]
+        ("reserved", ctypes.c_int32)] + [(n, ctypes.c_int32) for n in ("fft_mx", "fft_my", "fft_rows_i", "fft_rows_p",
+                                                                     "fft_chunk_items", "reserved2")]
 
     def as_dict(self) -> dict:
         return {name: getattr(self, name) for name, _ in self._fields_}
