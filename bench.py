@@ -248,7 +248,8 @@ DTYPE = {"fp64": "f64", "f32x2": "f32x2 (double-float, FP64-accurate)", "fp32": 
          "tf32": "tf32 x f32-accumulate (k = 0 in double-float)",
          "bf16x2": "bf16 2-term split x f32-accumulate (k = 0 in double-float)",
          "bf16x3": "bf16 3-term split x f32-accumulate (k = 0 in double-float)",
-         "fft64": "f64 (in-plane FFT form)"}
+         "fft64": "f64 (in-plane FFT form)",
+         "fft32": "f32 (in-plane FFT form; k = 0 in f64)"}
 
 
 def mode_bands(L):
@@ -270,9 +271,11 @@ def launches_per_apply(precision, info):
     """Kernels one apply launches: forward, projection, contraction (k = 0 separately for the FP32 and
     tensor forms; per streamed chunk: network, near copy, contraction), inverse."""
     K = info["K"]
-    if precision == "fft64":
-        items = info["max_rhs"] * K
-        return 2 + 3 * -(-items // max(1, info["fft_chunk_items"])) + 1
+    if precision in ("fft64", "fft32"):
+        R, Q = info["max_rhs"], max(1, info["fft_chunk_items"])
+        if precision == "fft64":
+            return 2 + 3 * -(-(R * K) // Q) + 1
+        return 2 + 3 * (-(-R // Q) - (-(R * (K - 1)) // min(2 * Q, 65535))) + 1
     if info.get("surrogate_attached"):
         chunks = -(-(K - 1) // max(1, info["surrogate_chunk"]))
         contract = 1 + 3 * chunks
@@ -367,7 +370,8 @@ def run_ours(args, w):
     # the other precisions on the same plan and inputs (not after the tables were released); at the
     # multi-rhs sizes the FP64 and double-float forms (tens of seconds per step) are left out
     if not args.surrogate:
-        others = ("fp64", "f32x2", "fp32", "fft64") if R == 1 else ("fp32", "tf32", "bf16x2", "bf16x3", "fft64")
+        others = (("fp64", "f32x2", "fp32", "fft64", "fft32") if R == 1
+                  else ("fp32", "tf32", "bf16x2", "bf16x3", "fft64", "fft32"))
         for prec in others:
             if prec != args.precision:
                 variant(prec, max(2, args.steps // 2))

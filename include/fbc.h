@@ -70,6 +70,10 @@ extern "C" {
  * and mode, built on first use) and a workspace of at most about 1 GiB.
  * Not for batches or plans with a surrogate. */
 #define FBC_PREC_FFT64 6
+/* The in-plane FFT form with FP32 transforms and kernel for the modes k >= 1
+ * and FP32 line transforms; the logarithmic k = 0 mode stays on the FP64
+ * grid transforms (as the other FP32 forms keep it FP64-accurate). */
+#define FBC_PREC_FFT32 7
 
 /* ---- plan flags (fbc_options.flags) ----------------------------------- */
 #define FBC_PLAN_HOST_ONLY 1 /* validate and lay out on the host only: no device memory,

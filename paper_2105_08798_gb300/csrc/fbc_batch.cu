@@ -134,7 +134,7 @@ int fbc_batch_create(fbc_plan* const* plans, int32_t n_plans, const double* cons
         if (P.sur) return bfail(FBC_ERR_UNSUPPORTED, "a plan with a surrogate attached runs on its own");
         if (prec < 0) prec = P.precision;
         if (P.precision != prec) return bfail(FBC_ERR_INVALID_ARG, "all plans of a batch need the same precision");
-        if (prec == FBC_PREC_FFT64)
+        if (fbc::is_fft_precision(prec))
             return bfail(FBC_ERR_UNSUPPORTED, "batches run the dense per-mode contraction, not the in-plane FFT form");
         if (fbc::is_tensor_precision(prec))
             return bfail(FBC_ERR_UNSUPPORTED, "batches run the CUDA-core precisions (FP64, FP32, double-float)");

@@ -458,7 +458,7 @@ cudaError_t launch_contract(Plan& P, int n_rhs, cudaStream_t st) {
     if (P.precision == FBC_PREC_F32X2) {
         return launch_one(k_contract_x2<kTileA, kTileB, false>, A, dim3(P.n_ta, P.K, n_rhs), kTileA, sx2, st);
     }
-    if (P.precision == FBC_PREC_FFT64) return launch_contract_fft(P, n_rhs, st);
+    if (is_fft_precision(P.precision)) return launch_contract_fft(P, n_rhs, st);
     return cudaErrorInvalidValue;
 }
 

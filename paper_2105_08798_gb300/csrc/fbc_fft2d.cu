@@ -56,7 +56,10 @@ struct FftGrid {
     double2* d_twx = nullptr;      // [Mx / 2] exp(-2 pi i j / Mx)
     double2* d_twy = nullptr;      // [My / 2]
     double* d_mhat = nullptr;      // [K][Mx][My][6]: A11 A12 A22 A33 B13 B23
-    double2* d_T1 = nullptr;       // [Q][Mx][ny_i][3]
+    float* d_mhat32 = nullptr;     // the same rounded to FP32 (FBC_PREC_FFT32)
+    float2* d_twx32 = nullptr;     // twiddles rounded to FP32
+    float2* d_twy32 = nullptr;
+    double2* d_T1 = nullptr;       // [Q][Mx][ny_i][3] (2Q items when complex FP32)
     double2* d_T2 = nullptr;       // [Q][Mx][ny_p][3]
     int2* d_used = nullptr;        // [n_used] differences placed on the grid (table entries)
     unsigned char* d_mirror = nullptr;  // [n_used] 1: also place the mirror -d (it is not a table entry)
@@ -83,13 +86,27 @@ inline int brev(int v, int bits) {
 
 __device__ __forceinline__ int brev_dev(int v, int bits) { return (int)(__brev((unsigned)v) >> (32 - bits)); }
 
-__device__ __forceinline__ double2 cmul(double2 a, double2 w) {
-    return make_double2(fma(a.x, w.x, -a.y * w.y), fma(a.x, w.y, a.y * w.x));
+template <typename R> struct CxOf;
+template <> struct CxOf<float> { using T = float2; };
+template <> struct CxOf<double> { using T = double2; };
+template <typename R> using Cx = typename CxOf<R>::T;
+
+__device__ __forceinline__ float fmx(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fmx(double a, double b, double c) { return __fma_rn(a, b, c); }
+
+template <typename C> __device__ __forceinline__ C mkc(decltype(C::x) x, decltype(C::x) y) {
+    C c;
+    c.x = x, c.y = y;
+    return c;
+}
+
+template <typename C> __device__ __forceinline__ C cmul(C a, C w) {
+    return mkc<C>(fmx(a.x, w.x, -a.y * w.y), fmx(a.x, w.y, a.y * w.x));
 }
 
 // nseq transforms of length 2^logN, back to back in s; input bit-reversed, output natural
-template <bool INV>
-__device__ void fft_dit(double2* s, int nseq, int logN, const double2* __restrict__ tw) {
+template <bool INV, typename C>
+__device__ void fft_dit(C* s, int nseq, int logN, const C* __restrict__ tw) {
     const int half = 1 << (logN - 1);
     const int nb = nseq * half;
     for (int st = 0; st < logN; st++) {
@@ -97,19 +114,19 @@ __device__ void fft_dit(double2* s, int nseq, int logN, const double2* __restric
         for (int t = threadIdx.x; t < nb; t += blockDim.x) {
             const int seq = t >> (logN - 1), b = t & (half - 1), j = b & (h - 1);
             const int i0 = (seq << logN) + ((b >> st) << (st + 1)) + j, i1 = i0 + h;
-            double2 w = __ldg(tw + j * tstep);
+            C w = __ldg(tw + j * tstep);
             if (INV) w.y = -w.y;
-            const double2 a = s[i0], v = cmul(s[i1], w);
-            s[i0] = make_double2(a.x + v.x, a.y + v.y);
-            s[i1] = make_double2(a.x - v.x, a.y - v.y);
+            const C a = s[i0], v = cmul(s[i1], w);
+            s[i0] = mkc<C>(a.x + v.x, a.y + v.y);
+            s[i1] = mkc<C>(a.x - v.x, a.y - v.y);
         }
         __syncthreads();
     }
 }
 
 // input natural, output bit-reversed
-template <bool INV>
-__device__ void fft_dif(double2* s, int nseq, int logN, const double2* __restrict__ tw) {
+template <bool INV, typename C>
+__device__ void fft_dif(C* s, int nseq, int logN, const C* __restrict__ tw) {
     const int half = 1 << (logN - 1);
     const int nb = nseq * half;
     for (int st = logN - 1; st >= 0; st--) {
@@ -117,40 +134,45 @@ __device__ void fft_dif(double2* s, int nseq, int logN, const double2* __restric
         for (int t = threadIdx.x; t < nb; t += blockDim.x) {
             const int seq = t >> (logN - 1), b = t & (half - 1), j = b & (h - 1);
             const int i0 = (seq << logN) + ((b >> st) << (st + 1)) + j, i1 = i0 + h;
-            double2 w = __ldg(tw + j * tstep);
+            C w = __ldg(tw + j * tstep);
             if (INV) w.y = -w.y;
-            const double2 a = s[i0], c = s[i1];
-            s[i0] = make_double2(a.x + c.x, a.y + c.y);
-            s[i1] = cmul(make_double2(a.x - c.x, a.y - c.y), w);
+            const C a = s[i0], c = s[i1];
+            s[i0] = mkc<C>(a.x + c.x, a.y + c.y);
+            s[i1] = cmul(mkc<C>(a.x - c.x, a.y - c.y), w);
         }
         __syncthreads();
     }
 }
 
+// Items are (rhs, mode) pairs in mode-major order, item = k * R + r, so that the items of one
+// workspace chunk share few modes and each mode's Mhat slice is read from L2 by all its rhs.
 struct FftArgs {
     const double* fh;
     double* uh;
-    const double* mhat;
-    double2* T1;
-    double2* T2;
+    const void* mhat;  // [K][Mx][My][6] of the transform's real type
+    void* T1;          // [Q][Mx][ny_i][3] complex
+    void* T2;          // [Q][Mx][ny_p][3] complex
     const int* row_i;
     const int2* ent_i;
     const int* row_p;
     const int2* ent_p;
     const int* ypos_i;
     const int* ypos_p;
-    const double2* twx;
-    const double2* twy;
-    int Mx, My, logMx, logMy, ny_i, ny_p, K, NIpad, NPpad, item0;
+    const void* twx;
+    const void* twy;
+    int Mx, My, logMx, logMy, ny_i, ny_p, R, K, NIpad, NPpad, item0;
     double scale;
 };
 
 // P1: rows of interface sites, forward FFT along x.  Block: G rows of one item.
+template <typename R>
 __global__ void __launch_bounds__(kFftThreads) k_fft_rows_fwd(FftArgs A, int G) {
-    extern __shared__ double2 s[];  // [G][3][Mx]
-    const int iq = blockIdx.y, item = A.item0 + iq, r = item / A.K, k = item - r * A.K;
+    using C = Cx<R>;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    C* s = (C*)smraw;  // [G][3][Mx]
+    const int iq = blockIdx.y, item = A.item0 + iq, k = item / A.R, r = item - k * A.R;
     const int row0 = blockIdx.x * G, n = G * 3 * A.Mx;
-    for (int t = threadIdx.x; t < n; t += blockDim.x) s[t] = make_double2(0.0, 0.0);
+    for (int t = threadIdx.x; t < n; t += blockDim.x) s[t] = mkc<C>(0, 0);
     __syncthreads();
     const double* fk = A.fh + ((size_t)r * A.K + k) * A.NIpad * 6;
     for (int g = 0; g < G && row0 + g < A.ny_i; g++) {
@@ -158,13 +180,13 @@ __global__ void __launch_bounds__(kFftThreads) k_fft_rows_fwd(FftArgs A, int G) 
         for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
             const int2 en = A.ent_i[e];
             const double* v = fk + (size_t)en.y * 6;
-            for (int c = 0; c < 3; c++) s[(g * 3 + c) * A.Mx + en.x] = make_double2(v[c], v[3 + c]);
+            for (int c = 0; c < 3; c++) s[(g * 3 + c) * A.Mx + en.x] = mkc<C>((R)v[c], (R)v[3 + c]);
         }
     }
     __syncthreads();
-    fft_dit<false>(s, G * 3, A.logMx, A.twx);
+    fft_dit<false>(s, G * 3, A.logMx, (const C*)A.twx);
     const int gr = min(G, A.ny_i - row0);
-    double2* out = A.T1 + (size_t)iq * A.Mx * A.ny_i * 3;
+    C* out = (C*)A.T1 + (size_t)iq * A.Mx * A.ny_i * 3;
     for (int t = threadIdx.x; t < A.Mx * gr * 3; t += blockDim.x) {
         const int c = t % 3, g = (t / 3) % gr, xi = t / (3 * gr);
         out[((size_t)xi * A.ny_i + row0 + g) * 3 + c] = s[(g * 3 + c) * A.Mx + xi];
@@ -172,33 +194,36 @@ __global__ void __launch_bounds__(kFftThreads) k_fft_rows_fwd(FftArgs A, int G) 
 }
 
 // P2: G grid columns of one item: forward FFT along y, Mhat, inverse FFT along y, pad rows out.
+template <typename R>
 __global__ void __launch_bounds__(kFftThreads) k_fft_cols(FftArgs A, int G) {
-    extern __shared__ double2 s[];  // [G][3][My]
-    const int iq = blockIdx.y, item = A.item0 + iq, r = item / A.K, k = item - r * A.K;
+    using C = Cx<R>;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    C* s = (C*)smraw;  // [G][3][My]
+    const int iq = blockIdx.y, item = A.item0 + iq, k = item / A.R;
     const int xi0 = blockIdx.x * G, n = G * 3 * A.My;
-    for (int t = threadIdx.x; t < n; t += blockDim.x) s[t] = make_double2(0.0, 0.0);
+    for (int t = threadIdx.x; t < n; t += blockDim.x) s[t] = mkc<C>(0, 0);
     __syncthreads();
-    const double2* in = A.T1 + (size_t)iq * A.Mx * A.ny_i * 3;
+    const C* in = (const C*)A.T1 + (size_t)iq * A.Mx * A.ny_i * 3;
     for (int t = threadIdx.x; t < G * A.ny_i * 3; t += blockDim.x) {
         const int c = t % 3, row = (t / 3) % A.ny_i, g = t / (3 * A.ny_i);
         s[(g * 3 + c) * A.My + A.ypos_i[row]] = in[((size_t)(xi0 + g) * A.ny_i + row) * 3 + c];
     }
     __syncthreads();
-    fft_dit<false>(s, G * 3, A.logMy, A.twy);
+    fft_dit<false>(s, G * 3, A.logMy, (const C*)A.twy);
     for (int t = threadIdx.x; t < G * A.My; t += blockDim.x) {
         const int g = t / A.My, et = t - g * A.My;
-        const double* m = A.mhat + (((size_t)k * A.Mx + xi0 + g) * A.My + et) * 6;
-        const double a11 = m[0], a12 = m[1], a22 = m[2], a33 = m[3], b13 = m[4], b23 = m[5];
-        double2* z = s + g * 3 * A.My + et;
-        const double2 z0 = z[0], z1 = z[A.My], z2 = z[2 * A.My];
+        const R* m = (const R*)A.mhat + (((size_t)k * A.Mx + xi0 + g) * A.My + et) * 6;
+        const R a11 = m[0], a12 = m[1], a22 = m[2], a33 = m[3], b13 = m[4], b23 = m[5];
+        C* z = s + g * 3 * A.My + et;
+        const C z0 = z[0], z1 = z[A.My], z2 = z[2 * A.My];
         // (-i b) z = (b z.y, -b z.x),  (i b) z = (-b z.y, b z.x)
-        z[0] = make_double2(fma(a11, z0.x, fma(a12, z1.x, b13 * z2.y)), fma(a11, z0.y, fma(a12, z1.y, -b13 * z2.x)));
-        z[A.My] = make_double2(fma(a12, z0.x, fma(a22, z1.x, b23 * z2.y)), fma(a12, z0.y, fma(a22, z1.y, -b23 * z2.x)));
-        z[2 * A.My] = make_double2(fma(a33, z2.x, -fma(b13, z0.y, b23 * z1.y)), fma(a33, z2.y, fma(b13, z0.x, b23 * z1.x)));
+        z[0] = mkc<C>(fmx(a11, z0.x, fmx(a12, z1.x, b13 * z2.y)), fmx(a11, z0.y, fmx(a12, z1.y, -b13 * z2.x)));
+        z[A.My] = mkc<C>(fmx(a12, z0.x, fmx(a22, z1.x, b23 * z2.y)), fmx(a12, z0.y, fmx(a22, z1.y, -b23 * z2.x)));
+        z[2 * A.My] = mkc<C>(fmx(a33, z2.x, -fmx(b13, z0.y, b23 * z1.y)), fmx(a33, z2.y, fmx(b13, z0.x, b23 * z1.x)));
     }
     __syncthreads();
-    fft_dif<true>(s, G * 3, A.logMy, A.twy);
-    double2* out = A.T2 + (size_t)iq * A.Mx * A.ny_p * 3;
+    fft_dif<true>(s, G * 3, A.logMy, (const C*)A.twy);
+    C* out = (C*)A.T2 + (size_t)iq * A.Mx * A.ny_p * 3;
     for (int t = threadIdx.x; t < G * A.ny_p * 3; t += blockDim.x) {
         const int c = t % 3, row = (t / 3) % A.ny_p, g = t / (3 * A.ny_p);
         out[((size_t)(xi0 + g) * A.ny_p + row) * 3 + c] = s[(g * 3 + c) * A.My + A.ypos_p[row]];
@@ -206,17 +231,20 @@ __global__ void __launch_bounds__(kFftThreads) k_fft_cols(FftArgs A, int G) {
 }
 
 // P3: G pad rows of one item: inverse FFT along x, scale, scatter the pad sites into uh.
+template <typename R>
 __global__ void __launch_bounds__(kFftThreads) k_fft_rows_inv(FftArgs A, int G) {
-    extern __shared__ double2 s[];  // [G][3][Mx]
-    const int iq = blockIdx.y, item = A.item0 + iq, r = item / A.K, k = item - r * A.K;
+    using C = Cx<R>;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    C* s = (C*)smraw;  // [G][3][Mx]
+    const int iq = blockIdx.y, item = A.item0 + iq, k = item / A.R, r = item - k * A.R;
     const int row0 = blockIdx.x * G, gr = min(G, A.ny_p - row0);
-    const double2* in = A.T2 + (size_t)iq * A.Mx * A.ny_p * 3;
+    const C* in = (const C*)A.T2 + (size_t)iq * A.Mx * A.ny_p * 3;
     for (int t = threadIdx.x; t < A.Mx * G * 3; t += blockDim.x) {
         const int c = t % 3, g = (t / 3) % G, xi = t / (3 * G);
-        s[(g * 3 + c) * A.Mx + xi] = g < gr ? in[((size_t)xi * A.ny_p + row0 + g) * 3 + c] : make_double2(0.0, 0.0);
+        s[(g * 3 + c) * A.Mx + xi] = g < gr ? in[((size_t)xi * A.ny_p + row0 + g) * 3 + c] : mkc<C>(0, 0);
     }
     __syncthreads();
-    fft_dif<true>(s, G * 3, A.logMx, A.twx);
+    fft_dif<true>(s, G * 3, A.logMx, (const C*)A.twx);
     double* uk = A.uh + ((size_t)r * A.K + k) * A.NPpad * 6;
     for (int g = 0; g < gr; g++) {
         const int e0 = A.row_p[row0 + g], e1 = A.row_p[row0 + g + 1];
@@ -224,11 +252,16 @@ __global__ void __launch_bounds__(kFftThreads) k_fft_rows_inv(FftArgs A, int G) 
             const int2 en = A.ent_p[e];
             double* o = uk + (size_t)en.y * 6;
             for (int c = 0; c < 3; c++) {
-                const double2 v = s[(g * 3 + c) * A.Mx + en.x];
-                o[c] = v.x * A.scale, o[3 + c] = v.y * A.scale;
+                const C v = s[(g * 3 + c) * A.Mx + en.x];
+                o[c] = (double)v.x * A.scale, o[3 + c] = (double)v.y * A.scale;
             }
         }
     }
+}
+
+__global__ void k_fft_to_f32(const double* __restrict__ src, float* __restrict__ dst, size_t n) {
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        dst[i] = (float)src[i];
 }
 
 // ---- the kernel's transform (setup) ----------------------------------------
@@ -291,8 +324,9 @@ __global__ void __launch_bounds__(kFftThreads) k_fft_dense_cols(const double2* _
 void fft_free(Plan& P) {
     FftGrid* F = P.fft;
     if (!F) return;
-    void* bufs[] = {F->d_row_i, F->d_ent_i, F->d_row_p, F->d_ent_p, F->d_ypos_i, F->d_ypos_p, F->d_twx,
-                    F->d_twy,   F->d_mhat,  F->d_T1,    F->d_T2,    F->d_used,   F->d_mirror};
+    void* bufs[] = {F->d_row_i, F->d_ent_i,  F->d_row_p, F->d_ent_p,   F->d_ypos_i,  F->d_ypos_p, F->d_twx,
+                    F->d_twy,   F->d_mhat,   F->d_T1,    F->d_T2,      F->d_used,    F->d_mirror, F->d_mhat32,
+                    F->d_twx32, F->d_twy32};
     for (void* b : bufs)
         if (b) cudaFree(b);
     delete F;
@@ -306,8 +340,37 @@ void fft_info(const Plan& P, int* mx, int* my, int* rows_i, int* rows_p, int* ch
     *chunk_items = F ? F->Q : 0;
 }
 
-int fft_prepare(Plan& P) {
-    if (P.fft) return FBC_OK;
+// the FP32 copies of the transformed kernel and the twiddles (FBC_PREC_FFT32), once
+static int fft_prepare32(Plan& P) {
+    FftGrid* F = P.fft;
+    if (F->d_mhat32) return FBC_OK;
+    const size_t n = (size_t)P.K * F->Mx * F->My * 6;
+    std::vector<float2> twx(F->Mx / 2), twy(F->My / 2);
+    for (int j = 0; j < F->Mx / 2; j++)
+        twx[j] = make_float2((float)cos(2.0 * M_PI * j / F->Mx), (float)-sin(2.0 * M_PI * j / F->Mx));
+    for (int j = 0; j < F->My / 2; j++)
+        twy[j] = make_float2((float)cos(2.0 * M_PI * j / F->My), (float)-sin(2.0 * M_PI * j / F->My));
+    cudaError_t e = cudaMalloc((void**)&F->d_mhat32, n * sizeof(float));
+    if (!e) e = cudaMalloc((void**)&F->d_twx32, twx.size() * sizeof(float2));
+    if (!e) e = cudaMalloc((void**)&F->d_twy32, twy.size() * sizeof(float2));
+    if (!e) e = cudaMemcpy(F->d_twx32, twx.data(), twx.size() * sizeof(float2), cudaMemcpyHostToDevice);
+    if (!e) e = cudaMemcpy(F->d_twy32, twy.data(), twy.size() * sizeof(float2), cudaMemcpyHostToDevice);
+    if (e) {
+        for (void* b : {(void*)F->d_mhat32, (void*)F->d_twx32, (void*)F->d_twy32})
+            if (b) cudaFree(b);
+        F->d_mhat32 = nullptr, F->d_twx32 = F->d_twy32 = nullptr;
+        char msg[256];
+        snprintf(msg, sizeof(msg), "in-plane FFT (FP32) setup: %s", cudaGetErrorString(e));
+        return report_error(e == cudaErrorMemoryAllocation ? FBC_ERR_OOM : FBC_ERR_CUDA, msg);
+    }
+    const size_t b = n * sizeof(float) + (twx.size() + twy.size()) * sizeof(float2);
+    F->bytes += b;
+    P.workspace_bytes += b;
+    return FBC_OK;
+}
+
+int fft_prepare(Plan& P, int precision) {
+    if (P.fft) return precision == FBC_PREC_FFT32 ? fft_prepare32(P) : FBC_OK;
     char msg[256];
     // the differences that occur (device list of the plan)
     std::vector<int2> used(P.n_used);
@@ -405,12 +468,16 @@ int fft_prepare(Plan& P) {
         return report_error(e == cudaErrorMemoryAllocation ? FBC_ERR_OOM : FBC_ERR_CUDA, msg);
     }
     P.workspace_bytes += bytes;
-    return FBC_OK;
+    return precision == FBC_PREC_FFT32 ? fft_prepare32(P) : FBC_OK;
 }
 
-cudaError_t launch_fft_tables(Plan& P, cudaStream_t st) {
+bool fft_ready(const Plan& P, int precision) {
+    return P.fft && P.fft->d_mhat && (precision != FBC_PREC_FFT32 || P.fft->d_mhat32);
+}
+
+cudaError_t launch_fft_tables(Plan& P, int precision, cudaStream_t st) {
     FftGrid* F = P.fft;
-    if (!F) return cudaErrorInvalidValue;
+    if (!fft_ready(P, precision)) return cudaErrorInvalidValue;
     const int Mx = F->Mx, My = F->My;
     const size_t per_k = (size_t)6 * Mx * My * sizeof(double2);
     const int nk = (int)std::max<size_t>(1, std::min<size_t>(P.K, ((size_t)512 << 20) / per_k));
@@ -441,41 +508,58 @@ cudaError_t launch_fft_tables(Plan& P, cudaStream_t st) {
         e = cudaGetLastError();
     }
     cudaError_t e2 = cudaFreeAsync(S, st);
+    if (!e && !e2 && precision == FBC_PREC_FFT32) {
+        k_fft_to_f32<<<1216, 256, 0, st>>>(F->d_mhat, F->d_mhat32, (size_t)P.K * Mx * My * 6);
+        e = cudaGetLastError();
+    }
     return e ? e : e2;
+}
+
+// P1, P2, P3 over items [i_begin, i_end) in chunks of q_max items, complex type of R
+template <typename R>
+static cudaError_t run_fft_items(FftArgs A, const FftGrid* F, int i_begin, int i_end, int q_max, cudaStream_t st) {
+    const int Gr = std::max(1, kRowElems / F->Mx);
+    const int Gc = std::max(1, std::min(F->Mx, kRowElems / F->My));
+    const size_t smem_r = (size_t)Gr * 3 * F->Mx * sizeof(Cx<R>);
+    const size_t smem_c = (size_t)Gc * 3 * F->My * sizeof(Cx<R>);
+    if (smem_r > 48 * 1024) {
+        cudaFuncSetAttribute(k_fft_rows_fwd<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_r);
+        cudaFuncSetAttribute(k_fft_rows_inv<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_r);
+    }
+    if (smem_c > 48 * 1024)
+        cudaFuncSetAttribute(k_fft_cols<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_c);
+    for (int i0 = i_begin; i0 < i_end; i0 += q_max) {
+        const int q = std::min(q_max, i_end - i0);
+        A.item0 = i0;
+        k_fft_rows_fwd<R><<<dim3((F->ny_i + Gr - 1) / Gr, q), kFftThreads, smem_r, st>>>(A, Gr);
+        cudaError_t e = cudaGetLastError();
+        if (e) return e;
+        k_fft_cols<R><<<dim3(F->Mx / Gc, q), kFftThreads, smem_c, st>>>(A, Gc);
+        if ((e = cudaGetLastError())) return e;
+        k_fft_rows_inv<R><<<dim3((F->ny_p + Gr - 1) / Gr, q), kFftThreads, smem_r, st>>>(A, Gr);
+        if ((e = cudaGetLastError())) return e;
+    }
+    return cudaSuccess;
 }
 
 cudaError_t launch_contract_fft(Plan& P, int n_rhs, cudaStream_t st) {
     FftGrid* F = P.fft;
-    if (!F || !F->d_mhat) return cudaErrorInvalidValue;
+    if (!fft_ready(P, P.precision)) return cudaErrorInvalidValue;
     FftArgs A{};
-    A.fh = P.d_fh, A.uh = P.d_uh, A.mhat = F->d_mhat, A.T1 = F->d_T1, A.T2 = F->d_T2;
+    A.fh = P.d_fh, A.uh = P.d_uh, A.T1 = F->d_T1, A.T2 = F->d_T2;
     A.row_i = F->d_row_i, A.ent_i = F->d_ent_i, A.row_p = F->d_row_p, A.ent_p = F->d_ent_p;
-    A.ypos_i = F->d_ypos_i, A.ypos_p = F->d_ypos_p, A.twx = F->d_twx, A.twy = F->d_twy;
+    A.ypos_i = F->d_ypos_i, A.ypos_p = F->d_ypos_p;
     A.Mx = F->Mx, A.My = F->My, A.logMx = F->logMx, A.logMy = F->logMy, A.ny_i = F->ny_i, A.ny_p = F->ny_p;
-    A.K = P.K, A.NIpad = P.NIpad, A.NPpad = P.NPpad;
+    A.R = n_rhs, A.K = P.K, A.NIpad = P.NIpad, A.NPpad = P.NPpad;
     A.scale = 1.0 / ((double)F->Mx * (double)F->My);
-    const int Gr = std::max(1, kRowElems / F->Mx);
-    const int Gc = std::max(1, std::min(F->Mx, kRowElems / F->My));
-    const size_t smem_r = (size_t)Gr * 3 * F->Mx * sizeof(double2);
-    const size_t smem_c = (size_t)Gc * 3 * F->My * sizeof(double2);
-    if (smem_r > 48 * 1024) {
-        cudaFuncSetAttribute(k_fft_rows_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_r);
-        cudaFuncSetAttribute(k_fft_rows_inv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_r);
-    }
-    if (smem_c > 48 * 1024) cudaFuncSetAttribute(k_fft_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_c);
     const int items = n_rhs * P.K;
-    for (int i0 = 0; i0 < items; i0 += F->Q) {
-        const int q = std::min(F->Q, items - i0);
-        A.item0 = i0;
-        k_fft_rows_fwd<<<dim3((F->ny_i + Gr - 1) / Gr, q), kFftThreads, smem_r, st>>>(A, Gr);
-        cudaError_t e = cudaGetLastError();
-        if (e) return e;
-        k_fft_cols<<<dim3(F->Mx / Gc, q), kFftThreads, smem_c, st>>>(A, Gc);
-        if ((e = cudaGetLastError())) return e;
-        k_fft_rows_inv<<<dim3((F->ny_p + Gr - 1) / Gr, q), kFftThreads, smem_r, st>>>(A, Gr);
-        if ((e = cudaGetLastError())) return e;
-    }
-    return cudaSuccess;
+    // FP64: every mode; FP32 form: the logarithmic k = 0 mode (items 0 .. n_rhs - 1) stays FP64
+    const int n64 = P.precision == FBC_PREC_FFT32 ? n_rhs : items;
+    A.mhat = F->d_mhat, A.twx = F->d_twx, A.twy = F->d_twy;
+    cudaError_t e = run_fft_items<double>(A, F, 0, n64, F->Q, st);
+    if (e || n64 == items) return e;
+    A.mhat = F->d_mhat32, A.twx = F->d_twx32, A.twy = F->d_twy32;
+    return run_fft_items<float>(A, F, n64, items, std::min(2 * F->Q, 65535), st);
 }
 
 }  // namespace fbc

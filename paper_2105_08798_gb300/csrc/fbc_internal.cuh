@@ -158,8 +158,9 @@ cudaError_t launch_relax_alpha(const double* dot_part, int has_old, const double
 cudaError_t launch_derive_tables(Plan& P, int precision, cudaStream_t st);
 // in-plane FFT form (fbc_fft2d.cu): host structures and buffers (once; needs the uploaded difference
 // list), the grid's transformed kernel from the FP64 table, the contraction, release
-int fft_prepare(Plan& P);
-cudaError_t launch_fft_tables(Plan& P, cudaStream_t st);
+int fft_prepare(Plan& P, int precision);
+bool fft_ready(const Plan& P, int precision);
+cudaError_t launch_fft_tables(Plan& P, int precision, cudaStream_t st);
 cudaError_t launch_contract_fft(Plan& P, int n_rhs, cudaStream_t st);
 void fft_free(Plan& P);
 void fft_info(const Plan& P, int* mx, int* my, int* rows_i, int* rows_p, int* chunk_items);
@@ -181,7 +182,10 @@ size_t batch_line_smem(int max_L);
 cudaError_t launch_batch_line(int stage, const LineArgs* d_args, const int4* d_items, int n_items, size_t smem,
                               double alpha, double beta, int want_part, cudaStream_t st, bool fp32);
 // line transforms in FP32 (k = 0 kept in FP64) for the FP32 and tensor-core contractions
-inline bool line_fp32(int precision) { return precision == FBC_PREC_FP32 || is_tensor_precision(precision); }
+inline bool is_fft_precision(int p) { return p == FBC_PREC_FFT64 || p == FBC_PREC_FFT32; }
+inline bool line_fp32(int precision) {
+    return precision == FBC_PREC_FP32 || is_tensor_precision(precision) || precision == FBC_PREC_FFT32;
+}
 // phase 0: k = 0 items (double-float tile), phase 1: k >= 1 items of an FP32 batch (8-rhs FP32 tile);
 // FP64 and double-float batches use phase 1 with their own tile for every item
 cudaError_t launch_batch_contract(int precision, int phase, const ContractArgs* d_args, const int* d_n_rhs,

@@ -316,7 +316,7 @@ int fbc_plan_create(const fbc_geometry* geom, const fbc_material* mat, const fbc
         return fail(FBC_ERR_INVALID_ARG, "Richardson needs n >= 1, 0 <= N <= 12, n + N <= %d", fbc::kMaxRichImages);
     if (opt.quad < 8 || opt.quad > fbc::kMaxQuad) return fail(FBC_ERR_INVALID_ARG, "quad must be in [8, %d]", fbc::kMaxQuad);
     if (opt.max_rhs < 1 || opt.max_rhs > 4096) return fail(FBC_ERR_INVALID_ARG, "max_rhs must be in [1, 4096]");
-    if (opt.precision < FBC_PREC_FP64 || opt.precision > FBC_PREC_FFT64)
+    if (opt.precision < FBC_PREC_FP64 || opt.precision > FBC_PREC_FFT32)
         return fail(FBC_ERR_INVALID_ARG, "unknown precision %d", opt.precision);
     if (opt.flags & ~(FBC_PLAN_HOST_ONLY | FBC_PLAN_TC_FAST_ACCUMULATE))
         return fail(FBC_ERR_INVALID_ARG, "unknown options.flags bits 0x%x", opt.flags);
@@ -509,8 +509,8 @@ int fbc_tabulate_kernel(fbc_plan* plan, void* stream) {
     cudaError_t e = fbc::launch_tabulate(P, st);
     if (e != cudaSuccess) return cuda_fail(e, "tabulate");
     P.tabulated = true;
-    if (P.precision == FBC_PREC_FFT64) {
-        if (int s = fbc::fft_prepare(P)) return s;
+    if (fbc::is_fft_precision(P.precision)) {
+        if (int s = fbc::fft_prepare(P, P.precision)) return s;
     }
     if (P.precision != FBC_PREC_FP64) {
         e = fbc::launch_derive_tables(P, P.precision, st);
@@ -522,7 +522,7 @@ int fbc_tabulate_kernel(fbc_plan* plan, void* stream) {
 int fbc_plan_set_precision(fbc_plan* plan, int32_t precision) {
     g_last_error.clear();
     if (!plan) return fail(FBC_ERR_INVALID_ARG, "plan is NULL");
-    if (precision < FBC_PREC_FP64 || precision > FBC_PREC_FFT64)
+    if (precision < FBC_PREC_FP64 || precision > FBC_PREC_FFT32)
         return fail(FBC_ERR_INVALID_ARG, "unknown precision %d", precision);
     fbc::Plan& P = plan->p;
     if (P.host_only) return fail(FBC_ERR_INVALID_ARG, "host-only plan");
@@ -530,8 +530,8 @@ int fbc_plan_set_precision(fbc_plan* plan, int32_t precision) {
     if (P.sur && precision != FBC_PREC_FP32 && !fbc::is_tensor_precision(precision))
         return fail(FBC_ERR_UNSUPPORTED, "detach the surrogate before switching to this precision");
     if (int st = ensure_derived(P, precision)) return st;
-    if (precision == FBC_PREC_FFT64 && P.tabulated) {
-        if (int st = fbc::fft_prepare(P)) return st;
+    if (fbc::is_fft_precision(precision) && P.tabulated) {
+        if (int st = fbc::fft_prepare(P, precision)) return st;
     }
     P.precision = precision;
     if (P.tabulated && precision != FBC_PREC_FP64) {
@@ -562,7 +562,8 @@ static int apply_checks(fbc::Plan& P, const double* f, const double* u, int32_t 
     if (fbc::is_tensor_precision(P.precision) && fbc::contract_tc_smem(P.precision, P.W * P.H) > 227 * 1024)
         return fail(FBC_ERR_UNSUPPORTED, "tensor-core contraction: staged sub-box too large for shared memory");
     if (P.precision == FBC_PREC_F32X2 && !P.d_table_x2) return fail(FBC_ERR_INVALID_ARG, "F32X2 table missing");
-    if (P.precision == FBC_PREC_FFT64 && !P.fft) return fail(FBC_ERR_INVALID_ARG, "in-plane FFT grid missing");
+    if (fbc::is_fft_precision(P.precision) && !fbc::fft_ready(P, P.precision))
+        return fail(FBC_ERR_INVALID_ARG, "in-plane FFT grid missing");
     return FBC_OK;
 }
 

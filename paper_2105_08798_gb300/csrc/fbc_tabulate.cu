@@ -273,7 +273,7 @@ cudaError_t launch_derive_tables(Plan& P, int precision, cudaStream_t st) {
         k_derive_x2<<<1216, 256, 0, st>>>(P.d_table, P.d_table_x2_k0, (size_t)P.Dy * P.Dx);  // k = 0 slice
         return cudaGetLastError();
     }
-    if (precision == FBC_PREC_FFT64) return launch_fft_tables(P, st);
+    if (is_fft_precision(precision)) return launch_fft_tables(P, precision, st);
     if (precision == FBC_PREC_F32X2) {
         if (!P.d_table_x2) return cudaErrorInvalidValue;
         k_derive_x2<<<1216, 256, 0, st>>>(P.d_table, P.d_table_x2, cells);

@@ -93,3 +93,25 @@ def test_fft_rejected_for_batches(fbc):
         plan.tabulate()
         with pytest.raises(fbc.FBCError):
             fbc.Batch([plan], [f], [u])
+
+
+@pytest.mark.parametrize("n_i,n_p,L,R", [(200, 300, 16, 1), (300, 450, 8, 3), (1500, 2000, 8, 2)])
+def test_fft32_against_fp64(fbc, n_i, n_p, L, R):
+    """FP32 transforms for k >= 1 (error at the FP32 level, as the dense FP32 form), FP64 for k = 0."""
+    xy_i, xy_p = inputs.ring_geometry(n_i, n_p)
+    f = torch.from_numpy(inputs.forces(R, n_i, L, seed=n_i + R)).cuda()
+    out = {}
+    with fbc.Plan(xy_i, xy_p, L, ISO, max_rhs=R) as plan:
+        plan.tabulate()
+        for prec in ("fp64", "fft32", "fp32"):
+            plan.set_precision(prec)
+            u = torch.full((R, n_p, L, 3), float("nan"), dtype=torch.float64, device="cuda")
+            plan.apply(f, u)
+            torch.cuda.synchronize()
+            plan.sync_status()
+            out[prec] = u.cpu().numpy()
+    ref = out["fp64"]
+    assert np.isfinite(out["fft32"]).all()
+    assert rel_l2(out["fft32"], ref) <= 1e-5, rel_l2(out["fft32"], ref)
+    # the k = 0 band (the mean along the line) keeps FP64 accuracy
+    assert rel_l2(out["fft32"].mean(axis=2), ref.mean(axis=2)) <= 1e-11
