@@ -26,11 +26,11 @@
 //       along y; keep only the rows that hold pad sites;
 //   P3  inverse FFT along x of every pad row, scale by 1/(Mx My) and scatter
 //       the pad sites into uh.
-// Radix-2 transforms in shared memory, FP64 throughout: decimation in time
-// with bit-reversed loads for the forward transforms (natural-order output),
-// decimation in frequency for the inverse ones (natural-order input,
-// bit-reversed output, read back at bit-reversed positions), so no pass
-// reorders data.
+// Transforms in shared memory in the Stockham form (natural order in and
+// out, two buffers used in turn): radix-8 passes, each thread holding one
+// 8-point sub-transform in registers, and one radix-4 or radix-2 pass for
+// the remaining factor, so a 512-point transform takes three passes through
+// shared memory.
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
@@ -48,13 +48,13 @@ struct FftGrid {
     int ny_i = 0, ny_p = 0;
     int Q = 0;                     // (rhs, mode) items per chunk of the workspace
     int* d_row_i = nullptr;        // [ny_i + 1] CSR of the interface rows
-    int2* d_ent_i = nullptr;       // (bit-reversed x position, fh slot)
+    int2* d_ent_i = nullptr;       // (x position on the grid, fh slot)
     int* d_row_p = nullptr;        // [ny_p + 1]
-    int2* d_ent_p = nullptr;       // (bit-reversed x position, uh slot)
-    int* d_ypos_i = nullptr;       // [ny_i] bit-reversed y position of each interface row
+    int2* d_ent_p = nullptr;       // (x position on the grid, uh slot)
+    int* d_ypos_i = nullptr;       // [ny_i] y position on the grid of each interface row
     int* d_ypos_p = nullptr;       // [ny_p]
-    double2* d_twx = nullptr;      // [Mx / 2] exp(-2 pi i j / Mx)
-    double2* d_twy = nullptr;      // [My / 2]
+    double2* d_twx = nullptr;      // [Mx] exp(-2 pi i j / Mx)
+    double2* d_twy = nullptr;      // [My]
     double* d_mhat = nullptr;      // [K][Mx][My][6]: A11 A12 A22 A33 B13 B23
     float* d_mhat32 = nullptr;     // the same rounded to FP32 (FBC_PREC_FFT32)
     float2* d_twx32 = nullptr;     // twiddles rounded to FP32
@@ -78,13 +78,6 @@ inline int ilog2(int v) {
     return l;
 }
 
-inline int brev(int v, int bits) {
-    int r = 0;
-    for (int t = 0; t < bits; t++) r |= ((v >> t) & 1) << (bits - 1 - t);
-    return r;
-}
-
-__device__ __forceinline__ int brev_dev(int v, int bits) { return (int)(__brev((unsigned)v) >> (32 - bits)); }
 
 template <typename R> struct CxOf;
 template <> struct CxOf<float> { using T = float2; };
@@ -104,44 +97,86 @@ template <typename C> __device__ __forceinline__ C cmul(C a, C w) {
     return mkc<C>(fmx(a.x, w.x, -a.y * w.y), fmx(a.x, w.y, a.y * w.x));
 }
 
-// nseq transforms of length 2^logN, back to back in s; input bit-reversed, output natural
-template <bool INV, typename C>
-__device__ void fft_dit(C* s, int nseq, int logN, const C* __restrict__ tw) {
-    const int half = 1 << (logN - 1);
-    const int nb = nseq * half;
-    for (int st = 0; st < logN; st++) {
-        const int h = 1 << st, tstep = half >> st;
-        for (int t = threadIdx.x; t < nb; t += blockDim.x) {
-            const int seq = t >> (logN - 1), b = t & (half - 1), j = b & (h - 1);
-            const int i0 = (seq << logN) + ((b >> st) << (st + 1)) + j, i1 = i0 + h;
-            C w = __ldg(tw + j * tstep);
-            if (INV) w.y = -w.y;
-            const C a = s[i0], v = cmul(s[i1], w);
-            s[i0] = mkc<C>(a.x + v.x, a.y + v.y);
-            s[i1] = mkc<C>(a.x - v.x, a.y - v.y);
+template <bool INV, typename C> __device__ __forceinline__ C add(C a, C b) { return mkc<C>(a.x + b.x, a.y + b.y); }
+template <bool INV, typename C> __device__ __forceinline__ C sub(C a, C b) { return mkc<C>(a.x - b.x, a.y - b.y); }
+// times -i (forward) or +i (inverse)
+template <bool INV, typename C> __device__ __forceinline__ C rot(C a) {
+    return INV ? mkc<C>(-a.y, a.x) : mkc<C>(a.y, -a.x);
+}
+
+template <bool INV, typename C> __device__ __forceinline__ void dft2(C* v) {
+    const C t = v[0];
+    v[0] = add<INV>(t, v[1]), v[1] = sub<INV>(t, v[1]);
+}
+
+template <bool INV, typename C> __device__ __forceinline__ void dft4(C& v0, C& v1, C& v2, C& v3) {
+    const C a0 = add<INV>(v0, v2), a1 = sub<INV>(v0, v2), a2 = add<INV>(v1, v3), a3 = rot<INV>(sub<INV>(v1, v3));
+    v0 = add<INV>(a0, a2), v1 = add<INV>(a1, a3), v2 = sub<INV>(a0, a2), v3 = sub<INV>(a1, a3);
+}
+
+// 8-point transform from two 4-point ones (even and odd inputs) and the factors exp(-+ i pi k / 4)
+template <bool INV, typename C> __device__ __forceinline__ void dft8(C* v) {
+    using R = decltype(C::x);
+    const R h = (R)0.70710678118654752440;
+    C e0 = v[0], e1 = v[2], e2 = v[4], e3 = v[6], o0 = v[1], o1 = v[3], o2 = v[5], o3 = v[7];
+    dft4<INV>(e0, e1, e2, e3);
+    dft4<INV>(o0, o1, o2, o3);
+    o1 = INV ? mkc<C>((o1.x - o1.y) * h, (o1.x + o1.y) * h) : mkc<C>((o1.x + o1.y) * h, (o1.y - o1.x) * h);
+    o2 = rot<INV>(o2);
+    o3 = INV ? mkc<C>(-(o3.x + o3.y) * h, (o3.x - o3.y) * h) : mkc<C>((o3.y - o3.x) * h, -(o3.x + o3.y) * h);
+    v[0] = add<INV>(e0, o0), v[4] = sub<INV>(e0, o0);
+    v[1] = add<INV>(e1, o1), v[5] = sub<INV>(e1, o1);
+    v[2] = add<INV>(e2, o2), v[6] = sub<INV>(e2, o2);
+    v[3] = add<INV>(e3, o3), v[7] = sub<INV>(e3, o3);
+}
+
+// One Stockham pass of radix 2^LR over nseq sequences of length 2^logN: work item j of a sequence
+// reads x[j + r N/R], twiddles by exp(-+2 pi i r k / (Ns R)) with k = j mod Ns, transforms in
+// registers and writes y[(j - k) R + k + r Ns].  tw[m] = exp(-2 pi i m / N), m < N.
+template <int LR, bool INV, typename C>
+__device__ __forceinline__ void stockham_pass(const C* in, C* out, int nseq, int logN, int logNs,
+                                              const C* __restrict__ tw) {
+    constexpr int R = 1 << LR;
+    const int NR = 1 << (logN - LR), Ns = 1 << logNs, tsh = logN - logNs - LR;
+    for (int t = threadIdx.x; t < nseq * NR; t += blockDim.x) {
+        const int seq = t >> (logN - LR), j = t & (NR - 1), k = j & (Ns - 1);
+        const C* x = in + (seq << logN);
+        C v[R];
+#pragma unroll
+        for (int r = 0; r < R; r++) v[r] = x[j + r * NR];
+        if (Ns > 1) {
+#pragma unroll
+            for (int r = 1; r < R; r++) {
+                C w = __ldg(tw + ((r * k) << tsh));
+                if (INV) w.y = -w.y;
+                v[r] = cmul(v[r], w);
+            }
         }
-        __syncthreads();
+        if (LR == 3) dft8<INV>(v);
+        else if (LR == 2) dft4<INV>(v[0], v[1], v[2], v[3]);
+        else dft2<INV>(v);
+        C* y = out + (seq << logN) + ((j - k) << LR) + k;
+#pragma unroll
+        for (int r = 0; r < R; r++) y[r * Ns] = v[r];
     }
 }
 
-// input natural, output bit-reversed
+// nseq transforms of length 2^logN in a (natural order); b is scratch of the same size.  Returns the
+// buffer that holds the result.  Starts and ends at a barrier.
 template <bool INV, typename C>
-__device__ void fft_dif(C* s, int nseq, int logN, const C* __restrict__ tw) {
-    const int half = 1 << (logN - 1);
-    const int nb = nseq * half;
-    for (int st = logN - 1; st >= 0; st--) {
-        const int h = 1 << st, tstep = half >> st;
-        for (int t = threadIdx.x; t < nb; t += blockDim.x) {
-            const int seq = t >> (logN - 1), b = t & (half - 1), j = b & (h - 1);
-            const int i0 = (seq << logN) + ((b >> st) << (st + 1)) + j, i1 = i0 + h;
-            C w = __ldg(tw + j * tstep);
-            if (INV) w.y = -w.y;
-            const C a = s[i0], c = s[i1];
-            s[i0] = mkc<C>(a.x + c.x, a.y + c.y);
-            s[i1] = cmul(mkc<C>(a.x - c.x, a.y - c.y), w);
-        }
+__device__ C* fft_smem(C* a, C* b, int nseq, int logN, const C* __restrict__ tw) {
+    int logNs = 0;
+    while (logNs < logN) {
+        const int lr = min(3, logN - logNs);
+        if (lr == 3) stockham_pass<3, INV>(a, b, nseq, logN, logNs, tw);
+        else if (lr == 2) stockham_pass<2, INV>(a, b, nseq, logN, logNs, tw);
+        else stockham_pass<1, INV>(a, b, nseq, logN, logNs, tw);
         __syncthreads();
+        C* t = a;
+        a = b, b = t;
+        logNs += lr;
     }
+    return a;
 }
 
 // Items are (rhs, mode) pairs in mode-major order, item = k * R + r, so that the items of one
@@ -169,7 +204,7 @@ template <typename R>
 __global__ void __launch_bounds__(kFftThreads) k_fft_rows_fwd(FftArgs A, int G) {
     using C = Cx<R>;
     extern __shared__ __align__(16) unsigned char smraw[];
-    C* s = (C*)smraw;  // [G][3][Mx]
+    C* s = (C*)smraw;  // [G][3][Mx], then the same again as scratch
     const int iq = blockIdx.y, item = A.item0 + iq, k = item / A.R, r = item - k * A.R;
     const int row0 = blockIdx.x * G, n = G * 3 * A.Mx;
     for (int t = threadIdx.x; t < n; t += blockDim.x) s[t] = mkc<C>(0, 0);
@@ -184,12 +219,12 @@ __global__ void __launch_bounds__(kFftThreads) k_fft_rows_fwd(FftArgs A, int G) 
         }
     }
     __syncthreads();
-    fft_dit<false>(s, G * 3, A.logMx, (const C*)A.twx);
+    const C* res = fft_smem<false>(s, s + n, G * 3, A.logMx, (const C*)A.twx);
     const int gr = min(G, A.ny_i - row0);
     C* out = (C*)A.T1 + (size_t)iq * A.Mx * A.ny_i * 3;
     for (int t = threadIdx.x; t < A.Mx * gr * 3; t += blockDim.x) {
         const int c = t % 3, g = (t / 3) % gr, xi = t / (3 * gr);
-        out[((size_t)xi * A.ny_i + row0 + g) * 3 + c] = s[(g * 3 + c) * A.Mx + xi];
+        out[((size_t)xi * A.ny_i + row0 + g) * 3 + c] = res[(g * 3 + c) * A.Mx + xi];
     }
 }
 
@@ -198,7 +233,7 @@ template <typename R>
 __global__ void __launch_bounds__(kFftThreads) k_fft_cols(FftArgs A, int G) {
     using C = Cx<R>;
     extern __shared__ __align__(16) unsigned char smraw[];
-    C* s = (C*)smraw;  // [G][3][My]
+    C* s = (C*)smraw;  // [G][3][My], then the same again as scratch
     const int iq = blockIdx.y, item = A.item0 + iq, k = item / A.R;
     const int xi0 = blockIdx.x * G, n = G * 3 * A.My;
     for (int t = threadIdx.x; t < n; t += blockDim.x) s[t] = mkc<C>(0, 0);
@@ -209,12 +244,12 @@ __global__ void __launch_bounds__(kFftThreads) k_fft_cols(FftArgs A, int G) {
         s[(g * 3 + c) * A.My + A.ypos_i[row]] = in[((size_t)(xi0 + g) * A.ny_i + row) * 3 + c];
     }
     __syncthreads();
-    fft_dit<false>(s, G * 3, A.logMy, (const C*)A.twy);
+    C* z0p = fft_smem<false>(s, s + n, G * 3, A.logMy, (const C*)A.twy);
     for (int t = threadIdx.x; t < G * A.My; t += blockDim.x) {
         const int g = t / A.My, et = t - g * A.My;
         const R* m = (const R*)A.mhat + (((size_t)k * A.Mx + xi0 + g) * A.My + et) * 6;
         const R a11 = m[0], a12 = m[1], a22 = m[2], a33 = m[3], b13 = m[4], b23 = m[5];
-        C* z = s + g * 3 * A.My + et;
+        C* z = z0p + g * 3 * A.My + et;
         const C z0 = z[0], z1 = z[A.My], z2 = z[2 * A.My];
         // (-i b) z = (b z.y, -b z.x),  (i b) z = (-b z.y, b z.x)
         z[0] = mkc<C>(fmx(a11, z0.x, fmx(a12, z1.x, b13 * z2.y)), fmx(a11, z0.y, fmx(a12, z1.y, -b13 * z2.x)));
@@ -222,11 +257,11 @@ __global__ void __launch_bounds__(kFftThreads) k_fft_cols(FftArgs A, int G) {
         z[2 * A.My] = mkc<C>(fmx(a33, z2.x, -fmx(b13, z0.y, b23 * z1.y)), fmx(a33, z2.y, fmx(b13, z0.x, b23 * z1.x)));
     }
     __syncthreads();
-    fft_dif<true>(s, G * 3, A.logMy, (const C*)A.twy);
+    const C* res = fft_smem<true>(z0p, z0p == s ? s + n : s, G * 3, A.logMy, (const C*)A.twy);
     C* out = (C*)A.T2 + (size_t)iq * A.Mx * A.ny_p * 3;
     for (int t = threadIdx.x; t < G * A.ny_p * 3; t += blockDim.x) {
         const int c = t % 3, row = (t / 3) % A.ny_p, g = t / (3 * A.ny_p);
-        out[((size_t)(xi0 + g) * A.ny_p + row) * 3 + c] = s[(g * 3 + c) * A.My + A.ypos_p[row]];
+        out[((size_t)(xi0 + g) * A.ny_p + row) * 3 + c] = res[(g * 3 + c) * A.My + A.ypos_p[row]];
     }
 }
 
@@ -235,16 +270,16 @@ template <typename R>
 __global__ void __launch_bounds__(kFftThreads) k_fft_rows_inv(FftArgs A, int G) {
     using C = Cx<R>;
     extern __shared__ __align__(16) unsigned char smraw[];
-    C* s = (C*)smraw;  // [G][3][Mx]
+    C* s = (C*)smraw;  // [G][3][Mx], then the same again as scratch
     const int iq = blockIdx.y, item = A.item0 + iq, k = item / A.R, r = item - k * A.R;
-    const int row0 = blockIdx.x * G, gr = min(G, A.ny_p - row0);
+    const int row0 = blockIdx.x * G, gr = min(G, A.ny_p - row0), n = G * 3 * A.Mx;
     const C* in = (const C*)A.T2 + (size_t)iq * A.Mx * A.ny_p * 3;
     for (int t = threadIdx.x; t < A.Mx * G * 3; t += blockDim.x) {
         const int c = t % 3, g = (t / 3) % G, xi = t / (3 * G);
         s[(g * 3 + c) * A.Mx + xi] = g < gr ? in[((size_t)xi * A.ny_p + row0 + g) * 3 + c] : mkc<C>(0, 0);
     }
     __syncthreads();
-    fft_dif<true>(s, G * 3, A.logMx, (const C*)A.twx);
+    const C* res = fft_smem<true>(s, s + n, G * 3, A.logMx, (const C*)A.twx);
     double* uk = A.uh + ((size_t)r * A.K + k) * A.NPpad * 6;
     for (int g = 0; g < gr; g++) {
         const int e0 = A.row_p[row0 + g], e1 = A.row_p[row0 + g + 1];
@@ -252,7 +287,7 @@ __global__ void __launch_bounds__(kFftThreads) k_fft_rows_inv(FftArgs A, int G) 
             const int2 en = A.ent_p[e];
             double* o = uk + (size_t)en.y * 6;
             for (int c = 0; c < 3; c++) {
-                const C v = s[(g * 3 + c) * A.Mx + en.x];
+                const C v = res[(g * 3 + c) * A.Mx + en.x];
                 o[c] = (double)v.x * A.scale, o[3 + c] = (double)v.y * A.scale;
             }
         }
@@ -287,34 +322,32 @@ __global__ void k_fft_place(const double* __restrict__ tab, const int2* __restri
 // forward FFT along x of G rows (of length Mx) per block, in place in global memory
 __global__ void __launch_bounds__(kFftThreads) k_fft_dense_rows(double2* S, int Mx, int logMx, int G,
                                                                  const double2* __restrict__ twx) {
-    extern __shared__ double2 s[];
+    extern __shared__ double2 sd[];  // [G][Mx] twice
     double2* rows = S + ((size_t)blockIdx.y * gridDim.x + blockIdx.x) * G * Mx;
-    for (int t = threadIdx.x; t < G * Mx; t += blockDim.x) {
-        const int g = t / Mx, x = t - g * Mx;
-        s[g * Mx + brev_dev(x, logMx)] = rows[t];
-    }
+    for (int t = threadIdx.x; t < G * Mx; t += blockDim.x) sd[t] = rows[t];
     __syncthreads();
-    fft_dit<false>(s, G, logMx, twx);
-    for (int t = threadIdx.x; t < G * Mx; t += blockDim.x) rows[t] = s[t];
+    const double2* res = fft_smem<false>(sd, sd + G * Mx, G, logMx, twx);
+    for (int t = threadIdx.x; t < G * Mx; t += blockDim.x) rows[t] = res[t];
 }
 
-// forward FFT along y of G columns of all six fields of one mode, then Mhat [k][Mx][My][6]
+// forward FFT along y of G columns of one of the six fields of one mode, into Mhat [k][Mx][My][6]
+// (the real part of the even fields a_ij, the imaginary part of the odd fields b_i3)
 __global__ void __launch_bounds__(kFftThreads) k_fft_dense_cols(const double2* __restrict__ S, int Mx, int My,
                                                                  int logMy, int G, int k0,
                                                                  const double2* __restrict__ twy,
                                                                  double* __restrict__ mhat) {
-    extern __shared__ double2 s[];  // [6][G][My]
-    const int kk = blockIdx.y, xi0 = blockIdx.x * G;
-    const double2* base = S + (size_t)kk * 6 * My * Mx;
-    for (int t = threadIdx.x; t < 6 * G * My; t += blockDim.x) {
-        const int g = t % G, y = (t / G) % My, f = t / (G * My);
-        s[(f * G + g) * My + brev_dev(y, logMy)] = base[((size_t)f * My + y) * Mx + xi0 + g];
+    extern __shared__ double2 sd[];  // [G][My] twice
+    const int kk = blockIdx.y / 6, f = blockIdx.y - 6 * kk, xi0 = blockIdx.x * G;
+    const double2* base = S + ((size_t)kk * 6 + f) * My * Mx;
+    for (int t = threadIdx.x; t < G * My; t += blockDim.x) {
+        const int g = t % G, y = t / G;
+        sd[g * My + y] = base[(size_t)y * Mx + xi0 + g];
     }
     __syncthreads();
-    fft_dit<false>(s, 6 * G, logMy, twy);
-    for (int t = threadIdx.x; t < G * My * 6; t += blockDim.x) {
-        const int f = t % 6, et = (t / 6) % My, g = t / (6 * My);
-        const double2 v = s[(f * G + g) * My + et];
+    const double2* res = fft_smem<false>(sd, sd + G * My, G, logMy, twy);
+    for (int t = threadIdx.x; t < G * My; t += blockDim.x) {
+        const int et = t % My, g = t / My;
+        const double2 v = res[g * My + et];
         mhat[(((size_t)(k0 + kk) * Mx + xi0 + g) * My + et) * 6 + f] = f < 4 ? v.x : v.y;
     }
 }
@@ -345,10 +378,10 @@ static int fft_prepare32(Plan& P) {
     FftGrid* F = P.fft;
     if (F->d_mhat32) return FBC_OK;
     const size_t n = (size_t)P.K * F->Mx * F->My * 6;
-    std::vector<float2> twx(F->Mx / 2), twy(F->My / 2);
-    for (int j = 0; j < F->Mx / 2; j++)
+    std::vector<float2> twx(F->Mx), twy(F->My);
+    for (int j = 0; j < F->Mx; j++)
         twx[j] = make_float2((float)cos(2.0 * M_PI * j / F->Mx), (float)-sin(2.0 * M_PI * j / F->Mx));
-    for (int j = 0; j < F->My / 2; j++)
+    for (int j = 0; j < F->My; j++)
         twy[j] = make_float2((float)cos(2.0 * M_PI * j / F->My), (float)-sin(2.0 * M_PI * j / F->My));
     cudaError_t e = cudaMalloc((void**)&F->d_mhat32, n * sizeof(float));
     if (!e) e = cudaMalloc((void**)&F->d_twx32, twx.size() * sizeof(float2));
@@ -409,10 +442,10 @@ int fft_prepare(Plan& P, int precision) {
             for (const int2& e : kv.second) {
                 const int xr = (((e.x - ox) % Mx) + Mx) % Mx;
                 if (!xres.insert(xr).second) return false;
-                ent.push_back(make_int2(brev(xr, F->logMx), e.y));
+                ent.push_back(make_int2(xr, e.y));
             }
             row.push_back((int)ent.size());
-            ypos.push_back(brev(yr, F->logMy));
+            ypos.push_back(yr);
         }
         return true;
     };
@@ -430,9 +463,9 @@ int fft_prepare(Plan& P, int precision) {
     const size_t per_item = (size_t)Mx * (F->ny_i + F->ny_p) * 3 * sizeof(double2);
     const size_t items = (size_t)P.opt.max_rhs * P.K;
     F->Q = (int)std::max<size_t>(1, std::min<size_t>({items, (size_t)65535, ((size_t)1 << 30) / per_item}));
-    std::vector<double2> twx(Mx / 2), twy(My / 2);
-    for (int j = 0; j < Mx / 2; j++) twx[j] = make_double2(cos(2.0 * M_PI * j / Mx), -sin(2.0 * M_PI * j / Mx));
-    for (int j = 0; j < My / 2; j++) twy[j] = make_double2(cos(2.0 * M_PI * j / My), -sin(2.0 * M_PI * j / My));
+    std::vector<double2> twx(Mx), twy(My);
+    for (int j = 0; j < Mx; j++) twx[j] = make_double2(cos(2.0 * M_PI * j / Mx), -sin(2.0 * M_PI * j / Mx));
+    for (int j = 0; j < My; j++) twy[j] = make_double2(cos(2.0 * M_PI * j / My), -sin(2.0 * M_PI * j / My));
     cudaError_t e = cudaSuccess;
     size_t bytes = 0;
     auto alloc = [&](auto** p, size_t n) {
@@ -485,8 +518,11 @@ cudaError_t launch_fft_tables(Plan& P, int precision, cudaStream_t st) {
     cudaError_t e = cudaMallocAsync((void**)&S, per_k * nk, st);
     if (e) return e;
     const int Gr = std::max(1, std::min(My, kRowElems / Mx));
-    const int Gc = std::max(1, std::min(Mx, (kRowElems / 4) / My));  // six fields per column group
-    const size_t smem_dc = (size_t)6 * Gc * My * sizeof(double2);
+    const int Gc = std::max(1, std::min(Mx, kRowElems / My));
+    const size_t smem_dr = (size_t)2 * Gr * Mx * sizeof(double2);
+    const size_t smem_dc = (size_t)2 * Gc * My * sizeof(double2);
+    if (smem_dr > 48 * 1024)
+        cudaFuncSetAttribute(k_fft_dense_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_dr);
     if (smem_dc > 48 * 1024)
         cudaFuncSetAttribute(k_fft_dense_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_dc);
     for (int k0 = 0; k0 < P.K && !e; k0 += nk) {
@@ -500,10 +536,10 @@ cudaError_t launch_fft_tables(Plan& P, int precision, cudaStream_t st) {
                                                                            P.box_y0, Mx, My, S);
             if ((e = cudaGetLastError())) break;
         }
-        k_fft_dense_rows<<<dim3(My / Gr, n * 6), kFftThreads, (size_t)Gr * Mx * sizeof(double2), st>>>(
+        k_fft_dense_rows<<<dim3(My / Gr, n * 6), kFftThreads, smem_dr, st>>>(
             S, Mx, F->logMx, Gr, F->d_twx);
         if ((e = cudaGetLastError())) break;
-        k_fft_dense_cols<<<dim3(Mx / Gc, n), kFftThreads, smem_dc, st>>>(
+        k_fft_dense_cols<<<dim3(Mx / Gc, n * 6), kFftThreads, smem_dc, st>>>(
             S, Mx, My, F->logMy, Gc, k0, F->d_twy, F->d_mhat);
         e = cudaGetLastError();
     }
@@ -520,8 +556,8 @@ template <typename R>
 static cudaError_t run_fft_items(FftArgs A, const FftGrid* F, int i_begin, int i_end, int q_max, cudaStream_t st) {
     const int Gr = std::max(1, kRowElems / F->Mx);
     const int Gc = std::max(1, std::min(F->Mx, kRowElems / F->My));
-    const size_t smem_r = (size_t)Gr * 3 * F->Mx * sizeof(Cx<R>);
-    const size_t smem_c = (size_t)Gc * 3 * F->My * sizeof(Cx<R>);
+    const size_t smem_r = (size_t)2 * Gr * 3 * F->Mx * sizeof(Cx<R>);  // data and scratch
+    const size_t smem_c = (size_t)2 * Gc * 3 * F->My * sizeof(Cx<R>);
     if (smem_r > 48 * 1024) {
         cudaFuncSetAttribute(k_fft_rows_fwd<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_r);
         cudaFuncSetAttribute(k_fft_rows_inv<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_r);
