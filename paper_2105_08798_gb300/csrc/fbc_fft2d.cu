@@ -69,7 +69,8 @@ struct FftGrid {
 
 namespace {
 
-constexpr int kFftThreads = 256;
+constexpr int kFftThreads = 384;  // one radix-8 work item per thread when a block holds 3 x 1024 points
+constexpr int kSetupThreads = 256;
 constexpr int kRowElems = 1024;  // complex elements per component a block of P1 / P3 transforms
 
 inline int ilog2(int v) {
@@ -96,6 +97,11 @@ template <typename C> __device__ __forceinline__ C mkc(decltype(C::x) x, decltyp
 template <typename C> __device__ __forceinline__ C cmul(C a, C w) {
     return mkc<C>(fmx(a.x, w.x, -a.y * w.y), fmx(a.x, w.y, a.y * w.x));
 }
+
+// Shared-memory index with one pad slot after every 8 complex numbers: the early Stockham passes store
+// with strides of 8 and 64 elements, which would otherwise hit the same banks.
+__device__ __forceinline__ int sx(int i) { return i + (i >> 3); }
+__host__ __device__ inline int padded(int n) { return n + (n >> 3) + 1; }
 
 template <bool INV, typename C> __device__ __forceinline__ C add(C a, C b) { return mkc<C>(a.x + b.x, a.y + b.y); }
 template <bool INV, typename C> __device__ __forceinline__ C sub(C a, C b) { return mkc<C>(a.x - b.x, a.y - b.y); }
@@ -140,10 +146,10 @@ __device__ __forceinline__ void stockham_pass(const C* in, C* out, int nseq, int
     const int NR = 1 << (logN - LR), Ns = 1 << logNs, tsh = logN - logNs - LR;
     for (int t = threadIdx.x; t < nseq * NR; t += blockDim.x) {
         const int seq = t >> (logN - LR), j = t & (NR - 1), k = j & (Ns - 1);
-        const C* x = in + (seq << logN);
+        const int x0 = (seq << logN) + j;
         C v[R];
 #pragma unroll
-        for (int r = 0; r < R; r++) v[r] = x[j + r * NR];
+        for (int r = 0; r < R; r++) v[r] = in[sx(x0 + r * NR)];
         if (Ns > 1) {
 #pragma unroll
             for (int r = 1; r < R; r++) {
@@ -155,13 +161,13 @@ __device__ __forceinline__ void stockham_pass(const C* in, C* out, int nseq, int
         if (LR == 3) dft8<INV>(v);
         else if (LR == 2) dft4<INV>(v[0], v[1], v[2], v[3]);
         else dft2<INV>(v);
-        C* y = out + (seq << logN) + ((j - k) << LR) + k;
+        const int y0 = (seq << logN) + ((j - k) << LR) + k;
 #pragma unroll
-        for (int r = 0; r < R; r++) y[r * Ns] = v[r];
+        for (int r = 0; r < R; r++) out[sx(y0 + r * Ns)] = v[r];
     }
 }
 
-// nseq transforms of length 2^logN in a (natural order); b is scratch of the same size.  Returns the
+// nseq transforms of length 2^logN in a (natural order, padded index); b is scratch of the same size.  Returns the
 // buffer that holds the result.  Starts and ends at a barrier.
 template <bool INV, typename C>
 __device__ C* fft_smem(C* a, C* b, int nseq, int logN, const C* __restrict__ tw) {
@@ -204,9 +210,9 @@ template <typename R>
 __global__ void __launch_bounds__(kFftThreads) k_fft_rows_fwd(FftArgs A, int G) {
     using C = Cx<R>;
     extern __shared__ __align__(16) unsigned char smraw[];
-    C* s = (C*)smraw;  // [G][3][Mx], then the same again as scratch
+    C* s = (C*)smraw;  // [G][3][Mx] (padded index), then the same again as scratch
     const int iq = blockIdx.y, item = A.item0 + iq, k = item / A.R, r = item - k * A.R;
-    const int row0 = blockIdx.x * G, n = G * 3 * A.Mx;
+    const int row0 = blockIdx.x * G, n = padded(G * 3 * A.Mx);
     for (int t = threadIdx.x; t < n; t += blockDim.x) s[t] = mkc<C>(0, 0);
     __syncthreads();
     const double* fk = A.fh + ((size_t)r * A.K + k) * A.NIpad * 6;
@@ -215,7 +221,7 @@ __global__ void __launch_bounds__(kFftThreads) k_fft_rows_fwd(FftArgs A, int G) 
         for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
             const int2 en = A.ent_i[e];
             const double* v = fk + (size_t)en.y * 6;
-            for (int c = 0; c < 3; c++) s[(g * 3 + c) * A.Mx + en.x] = mkc<C>((R)v[c], (R)v[3 + c]);
+            for (int c = 0; c < 3; c++) s[sx((g * 3 + c) * A.Mx + en.x)] = mkc<C>((R)v[c], (R)v[3 + c]);
         }
     }
     __syncthreads();
@@ -224,7 +230,7 @@ __global__ void __launch_bounds__(kFftThreads) k_fft_rows_fwd(FftArgs A, int G) 
     C* out = (C*)A.T1 + (size_t)iq * A.Mx * A.ny_i * 3;
     for (int t = threadIdx.x; t < A.Mx * gr * 3; t += blockDim.x) {
         const int c = t % 3, g = (t / 3) % gr, xi = t / (3 * gr);
-        out[((size_t)xi * A.ny_i + row0 + g) * 3 + c] = res[(g * 3 + c) * A.Mx + xi];
+        out[((size_t)xi * A.ny_i + row0 + g) * 3 + c] = res[sx((g * 3 + c) * A.Mx + xi)];
     }
 }
 
@@ -233,15 +239,15 @@ template <typename R>
 __global__ void __launch_bounds__(kFftThreads) k_fft_cols(FftArgs A, int G) {
     using C = Cx<R>;
     extern __shared__ __align__(16) unsigned char smraw[];
-    C* s = (C*)smraw;  // [G][3][My], then the same again as scratch
+    C* s = (C*)smraw;  // [G][3][My] (padded index), then the same again as scratch
     const int iq = blockIdx.y, item = A.item0 + iq, k = item / A.R;
-    const int xi0 = blockIdx.x * G, n = G * 3 * A.My;
+    const int xi0 = blockIdx.x * G, n = padded(G * 3 * A.My);
     for (int t = threadIdx.x; t < n; t += blockDim.x) s[t] = mkc<C>(0, 0);
     __syncthreads();
     const C* in = (const C*)A.T1 + (size_t)iq * A.Mx * A.ny_i * 3;
     for (int t = threadIdx.x; t < G * A.ny_i * 3; t += blockDim.x) {
         const int c = t % 3, row = (t / 3) % A.ny_i, g = t / (3 * A.ny_i);
-        s[(g * 3 + c) * A.My + A.ypos_i[row]] = in[((size_t)(xi0 + g) * A.ny_i + row) * 3 + c];
+        s[sx((g * 3 + c) * A.My + A.ypos_i[row])] = in[((size_t)(xi0 + g) * A.ny_i + row) * 3 + c];
     }
     __syncthreads();
     C* z0p = fft_smem<false>(s, s + n, G * 3, A.logMy, (const C*)A.twy);
@@ -249,19 +255,19 @@ __global__ void __launch_bounds__(kFftThreads) k_fft_cols(FftArgs A, int G) {
         const int g = t / A.My, et = t - g * A.My;
         const R* m = (const R*)A.mhat + (((size_t)k * A.Mx + xi0 + g) * A.My + et) * 6;
         const R a11 = m[0], a12 = m[1], a22 = m[2], a33 = m[3], b13 = m[4], b23 = m[5];
-        C* z = z0p + g * 3 * A.My + et;
-        const C z0 = z[0], z1 = z[A.My], z2 = z[2 * A.My];
+        const int i0 = sx(g * 3 * A.My + et), i1 = sx((g * 3 + 1) * A.My + et), i2 = sx((g * 3 + 2) * A.My + et);
+        const C z0 = z0p[i0], z1 = z0p[i1], z2 = z0p[i2];
         // (-i b) z = (b z.y, -b z.x),  (i b) z = (-b z.y, b z.x)
-        z[0] = mkc<C>(fmx(a11, z0.x, fmx(a12, z1.x, b13 * z2.y)), fmx(a11, z0.y, fmx(a12, z1.y, -b13 * z2.x)));
-        z[A.My] = mkc<C>(fmx(a12, z0.x, fmx(a22, z1.x, b23 * z2.y)), fmx(a12, z0.y, fmx(a22, z1.y, -b23 * z2.x)));
-        z[2 * A.My] = mkc<C>(fmx(a33, z2.x, -fmx(b13, z0.y, b23 * z1.y)), fmx(a33, z2.y, fmx(b13, z0.x, b23 * z1.x)));
+        z0p[i0] = mkc<C>(fmx(a11, z0.x, fmx(a12, z1.x, b13 * z2.y)), fmx(a11, z0.y, fmx(a12, z1.y, -b13 * z2.x)));
+        z0p[i1] = mkc<C>(fmx(a12, z0.x, fmx(a22, z1.x, b23 * z2.y)), fmx(a12, z0.y, fmx(a22, z1.y, -b23 * z2.x)));
+        z0p[i2] = mkc<C>(fmx(a33, z2.x, -fmx(b13, z0.y, b23 * z1.y)), fmx(a33, z2.y, fmx(b13, z0.x, b23 * z1.x)));
     }
     __syncthreads();
     const C* res = fft_smem<true>(z0p, z0p == s ? s + n : s, G * 3, A.logMy, (const C*)A.twy);
     C* out = (C*)A.T2 + (size_t)iq * A.Mx * A.ny_p * 3;
     for (int t = threadIdx.x; t < G * A.ny_p * 3; t += blockDim.x) {
         const int c = t % 3, row = (t / 3) % A.ny_p, g = t / (3 * A.ny_p);
-        out[((size_t)(xi0 + g) * A.ny_p + row) * 3 + c] = res[(g * 3 + c) * A.My + A.ypos_p[row]];
+        out[((size_t)(xi0 + g) * A.ny_p + row) * 3 + c] = res[sx((g * 3 + c) * A.My + A.ypos_p[row])];
     }
 }
 
@@ -270,13 +276,13 @@ template <typename R>
 __global__ void __launch_bounds__(kFftThreads) k_fft_rows_inv(FftArgs A, int G) {
     using C = Cx<R>;
     extern __shared__ __align__(16) unsigned char smraw[];
-    C* s = (C*)smraw;  // [G][3][Mx], then the same again as scratch
+    C* s = (C*)smraw;  // [G][3][Mx] (padded index), then the same again as scratch
     const int iq = blockIdx.y, item = A.item0 + iq, k = item / A.R, r = item - k * A.R;
-    const int row0 = blockIdx.x * G, gr = min(G, A.ny_p - row0), n = G * 3 * A.Mx;
+    const int row0 = blockIdx.x * G, gr = min(G, A.ny_p - row0), n = padded(G * 3 * A.Mx);
     const C* in = (const C*)A.T2 + (size_t)iq * A.Mx * A.ny_p * 3;
     for (int t = threadIdx.x; t < A.Mx * G * 3; t += blockDim.x) {
         const int c = t % 3, g = (t / 3) % G, xi = t / (3 * G);
-        s[(g * 3 + c) * A.Mx + xi] = g < gr ? in[((size_t)xi * A.ny_p + row0 + g) * 3 + c] : mkc<C>(0, 0);
+        s[sx((g * 3 + c) * A.Mx + xi)] = g < gr ? in[((size_t)xi * A.ny_p + row0 + g) * 3 + c] : mkc<C>(0, 0);
     }
     __syncthreads();
     const C* res = fft_smem<true>(s, s + n, G * 3, A.logMx, (const C*)A.twx);
@@ -287,7 +293,7 @@ __global__ void __launch_bounds__(kFftThreads) k_fft_rows_inv(FftArgs A, int G) 
             const int2 en = A.ent_p[e];
             double* o = uk + (size_t)en.y * 6;
             for (int c = 0; c < 3; c++) {
-                const C v = res[(g * 3 + c) * A.Mx + en.x];
+                const C v = res[sx((g * 3 + c) * A.Mx + en.x)];
                 o[c] = (double)v.x * A.scale, o[3 + c] = (double)v.y * A.scale;
             }
         }
@@ -320,34 +326,34 @@ __global__ void k_fft_place(const double* __restrict__ tab, const int2* __restri
 }
 
 // forward FFT along x of G rows (of length Mx) per block, in place in global memory
-__global__ void __launch_bounds__(kFftThreads) k_fft_dense_rows(double2* S, int Mx, int logMx, int G,
-                                                                 const double2* __restrict__ twx) {
-    extern __shared__ double2 sd[];  // [G][Mx] twice
+__global__ void __launch_bounds__(kSetupThreads) k_fft_dense_rows(double2* S, int Mx, int logMx, int G,
+                                                                   const double2* __restrict__ twx) {
+    extern __shared__ double2 sd[];  // [G][Mx] (padded index) twice
     double2* rows = S + ((size_t)blockIdx.y * gridDim.x + blockIdx.x) * G * Mx;
-    for (int t = threadIdx.x; t < G * Mx; t += blockDim.x) sd[t] = rows[t];
+    for (int t = threadIdx.x; t < G * Mx; t += blockDim.x) sd[sx(t)] = rows[t];
     __syncthreads();
-    const double2* res = fft_smem<false>(sd, sd + G * Mx, G, logMx, twx);
-    for (int t = threadIdx.x; t < G * Mx; t += blockDim.x) rows[t] = res[t];
+    const double2* res = fft_smem<false>(sd, sd + padded(G * Mx), G, logMx, twx);
+    for (int t = threadIdx.x; t < G * Mx; t += blockDim.x) rows[t] = res[sx(t)];
 }
 
 // forward FFT along y of G columns of one of the six fields of one mode, into Mhat [k][Mx][My][6]
 // (the real part of the even fields a_ij, the imaginary part of the odd fields b_i3)
-__global__ void __launch_bounds__(kFftThreads) k_fft_dense_cols(const double2* __restrict__ S, int Mx, int My,
-                                                                 int logMy, int G, int k0,
-                                                                 const double2* __restrict__ twy,
-                                                                 double* __restrict__ mhat) {
-    extern __shared__ double2 sd[];  // [G][My] twice
+__global__ void __launch_bounds__(kSetupThreads) k_fft_dense_cols(const double2* __restrict__ S, int Mx, int My,
+                                                                   int logMy, int G, int k0,
+                                                                   const double2* __restrict__ twy,
+                                                                   double* __restrict__ mhat) {
+    extern __shared__ double2 sd[];  // [G][My] (padded index) twice
     const int kk = blockIdx.y / 6, f = blockIdx.y - 6 * kk, xi0 = blockIdx.x * G;
     const double2* base = S + ((size_t)kk * 6 + f) * My * Mx;
     for (int t = threadIdx.x; t < G * My; t += blockDim.x) {
         const int g = t % G, y = t / G;
-        sd[g * My + y] = base[(size_t)y * Mx + xi0 + g];
+        sd[sx(g * My + y)] = base[(size_t)y * Mx + xi0 + g];
     }
     __syncthreads();
-    const double2* res = fft_smem<false>(sd, sd + G * My, G, logMy, twy);
+    const double2* res = fft_smem<false>(sd, sd + padded(G * My), G, logMy, twy);
     for (int t = threadIdx.x; t < G * My; t += blockDim.x) {
         const int et = t % My, g = t / My;
-        const double2 v = res[g * My + et];
+        const double2 v = res[sx(g * My + et)];
         mhat[(((size_t)(k0 + kk) * Mx + xi0 + g) * My + et) * 6 + f] = f < 4 ? v.x : v.y;
     }
 }
@@ -519,8 +525,8 @@ cudaError_t launch_fft_tables(Plan& P, int precision, cudaStream_t st) {
     if (e) return e;
     const int Gr = std::max(1, std::min(My, kRowElems / Mx));
     const int Gc = std::max(1, std::min(Mx, kRowElems / My));
-    const size_t smem_dr = (size_t)2 * Gr * Mx * sizeof(double2);
-    const size_t smem_dc = (size_t)2 * Gc * My * sizeof(double2);
+    const size_t smem_dr = (size_t)2 * padded(Gr * Mx) * sizeof(double2);
+    const size_t smem_dc = (size_t)2 * padded(Gc * My) * sizeof(double2);
     if (smem_dr > 48 * 1024)
         cudaFuncSetAttribute(k_fft_dense_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_dr);
     if (smem_dc > 48 * 1024)
@@ -536,10 +542,10 @@ cudaError_t launch_fft_tables(Plan& P, int precision, cudaStream_t st) {
                                                                            P.box_y0, Mx, My, S);
             if ((e = cudaGetLastError())) break;
         }
-        k_fft_dense_rows<<<dim3(My / Gr, n * 6), kFftThreads, smem_dr, st>>>(
+        k_fft_dense_rows<<<dim3(My / Gr, n * 6), kSetupThreads, smem_dr, st>>>(
             S, Mx, F->logMx, Gr, F->d_twx);
         if ((e = cudaGetLastError())) break;
-        k_fft_dense_cols<<<dim3(Mx / Gc, n * 6), kFftThreads, smem_dc, st>>>(
+        k_fft_dense_cols<<<dim3(Mx / Gc, n * 6), kSetupThreads, smem_dc, st>>>(
             S, Mx, My, F->logMy, Gc, k0, F->d_twy, F->d_mhat);
         e = cudaGetLastError();
     }
@@ -556,8 +562,8 @@ template <typename R>
 static cudaError_t run_fft_items(FftArgs A, const FftGrid* F, int i_begin, int i_end, int q_max, cudaStream_t st) {
     const int Gr = std::max(1, kRowElems / F->Mx);
     const int Gc = std::max(1, std::min(F->Mx, kRowElems / F->My));
-    const size_t smem_r = (size_t)2 * Gr * 3 * F->Mx * sizeof(Cx<R>);  // data and scratch
-    const size_t smem_c = (size_t)2 * Gc * 3 * F->My * sizeof(Cx<R>);
+    const size_t smem_r = (size_t)2 * padded(Gr * 3 * F->Mx) * sizeof(Cx<R>);  // data and scratch
+    const size_t smem_c = (size_t)2 * padded(Gc * 3 * F->My) * sizeof(Cx<R>);
     if (smem_r > 48 * 1024) {
         cudaFuncSetAttribute(k_fft_rows_fwd<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_r);
         cudaFuncSetAttribute(k_fft_rows_inv<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_r);
