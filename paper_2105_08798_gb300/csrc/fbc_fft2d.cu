@@ -9,8 +9,9 @@
 // Because the kernel depends only on the lattice difference d (translation
 // invariance of the Green function in the plane, Sec. 3.1), this is a 2D
 // convolution over the lattice.  It is evaluated exactly by a circular
-// convolution on an Mx x My grid with Mx, My powers of two of at least
-// 2 max|d| + 1: every difference d that occurs, and its mirror -d, then has a
+// convolution on an Mx x My grid with at least 2 max|d| + 1 points per side
+// (each side 2^a 3^b 5^c, the cheapest such length): every difference d that
+// occurs, and its mirror -d, then has a
 // residue of its own, so the circular sum at a pad site picks up exactly the
 // terms of the direct sum.  The kernel is placed at d with the table values
 // and at -d with the exact mirror relations of the Green function (a_ij even
@@ -27,10 +28,10 @@
 //   P3  inverse FFT along x of every pad row, scale by 1/(Mx My) and scatter
 //       the pad sites into uh.
 // Transforms in shared memory in the Stockham form (natural order in and
-// out, two buffers used in turn): radix-8 passes, each thread holding one
-// 8-point sub-transform in registers, and one radix-4 or radix-2 pass for
-// the remaining factor, so a 512-point transform takes three passes through
-// shared memory.
+// out, two buffers used in turn): each pass gives every thread one
+// sub-transform of radix 8, 6, 5, 4, 3 or 2 in registers; the lengths are
+// chosen for the fewest passes (216 = 6 x 6 x 6, 320 = 5 x 8 x 8: three
+// passes through shared memory each).
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
@@ -43,8 +44,21 @@
 
 namespace fbc {
 
+constexpr int kMaxPass = 8;
+
+// One transform length and its passes: pass p has radix R[p], Ns[p] = the product of the earlier
+// radices, NR[p] = N / R[p] work items per sequence, twiddle step N / (Ns R); divisions by NR and Ns
+// as multiply-high, add and shift (m, l).
+struct Fft1D {
+    int N = 0, np = 0;
+    int R[kMaxPass], Ns[kMaxPass], NR[kMaxPass], tstep[kMaxPass];
+    unsigned mNR[kMaxPass], mNs[kMaxPass];
+    int lNR[kMaxPass], lNs[kMaxPass];
+};
+
 struct FftGrid {
-    int Mx = 0, My = 0, logMx = 0, logMy = 0;
+    int Mx = 0, My = 0;
+    Fft1D fx, fy;
     int ny_i = 0, ny_p = 0;
     int Q = 0;                     // (rhs, mode) items per chunk of the workspace
     int* d_row_i = nullptr;        // [ny_i + 1] CSR of the interface rows
@@ -73,10 +87,57 @@ constexpr int kFftThreads = 384;  // one radix-8 work item per thread when a blo
 constexpr int kSetupThreads = 256;
 constexpr int kRowElems = 1024;  // complex elements per component a block of P1 / P3 transforms
 
-inline int ilog2(int v) {
-    int l = 0;
-    while ((1 << l) < v) l++;
-    return l;
+// n / d for 0 <= n < 2^31 with (m, l) from div_magic(d)
+__device__ __forceinline__ int fdiv(int n, unsigned m, int l) {
+    return (int)((__umulhi((unsigned)n, m) + (unsigned)n) >> l);
+}
+
+void div_magic(int d, unsigned* m, int* l) {
+    int s = 0;
+    while ((1LL << s) < d) s++;
+    *l = s;
+    *m = (unsigned)((((unsigned long long)1 << 32) * (((unsigned long long)1 << s) - (unsigned long long)d)) /
+                    (unsigned long long)d + 1ULL);
+}
+
+// fewest passes of radix 8, 6, 5, 4, 3, 2 with product n (empty if n has another prime factor)
+std::vector<int> radix_passes(int n) {
+    static const int kRad[6] = {8, 6, 5, 4, 3, 2};
+    std::vector<std::vector<int>> best(n + 1);
+    std::vector<bool> ok(n + 1, false);
+    ok[1] = true;
+    for (int m = 2; m <= n; m++) {
+        if (n % m) continue;
+        for (int R : kRad)
+            if (m % R == 0 && ok[m / R] && (!ok[m] || best[m / R].size() + 1 < best[m].size())) {
+                best[m] = best[m / R];
+                best[m].push_back(R);
+                ok[m] = true;
+            }
+    }
+    return ok[n] ? best[n] : std::vector<int>();
+}
+
+// the cheapest length >= need (cost: points x (passes + 1)), and its passes
+Fft1D choose_length(int need) {
+    Fft1D F;
+    long long best_cost = -1;
+    std::vector<int> best;
+    for (int N = std::max(2, need); N <= std::max(4, 2 * need); N++) {
+        std::vector<int> p = radix_passes(N);
+        if (p.empty() || (int)p.size() > kMaxPass) continue;
+        const long long cost = (long long)N * (long long)(p.size() + 1);
+        if (best_cost < 0 || cost < best_cost) best_cost = cost, best = p, F.N = N;
+    }
+    F.np = (int)best.size();
+    int Ns = 1;
+    for (int q = 0; q < F.np; q++) {
+        F.R[q] = best[q], F.Ns[q] = Ns, F.NR[q] = F.N / best[q], F.tstep[q] = F.N / (Ns * best[q]);
+        div_magic(F.NR[q], &F.mNR[q], &F.lNR[q]);
+        div_magic(Ns, &F.mNs[q], &F.lNs[q]);
+        Ns *= best[q];
+    }
+    return F;
 }
 
 
@@ -136,51 +197,98 @@ template <bool INV, typename C> __device__ __forceinline__ void dft8(C* v) {
     v[3] = add<INV>(e3, o3), v[7] = sub<INV>(e3, o3);
 }
 
-// One Stockham pass of radix 2^LR over nseq sequences of length 2^logN: work item j of a sequence
-// reads x[j + r N/R], twiddles by exp(-+2 pi i r k / (Ns R)) with k = j mod Ns, transforms in
-// registers and writes y[(j - k) R + k + r Ns].  tw[m] = exp(-2 pi i m / N), m < N.
-template <int LR, bool INV, typename C>
-__device__ __forceinline__ void stockham_pass(const C* in, C* out, int nseq, int logN, int logNs,
+template <bool INV, typename C> __device__ __forceinline__ void dft3(C& v0, C& v1, C& v2) {
+    using R = decltype(C::x);
+    const R h = (R)0.86602540378443864676;  // sin(2 pi / 3)
+    const C t1 = add<INV>(v1, v2), d = sub<INV>(v1, v2);
+    const C t2 = INV ? mkc<C>(-d.y * h, d.x * h) : mkc<C>(d.y * h, -d.x * h);  // -+ i h (v1 - v2)
+    const C m = mkc<C>(v0.x - (R)0.5 * t1.x, v0.y - (R)0.5 * t1.y);
+    v0 = add<INV>(v0, t1), v1 = add<INV>(m, t2), v2 = sub<INV>(m, t2);
+}
+
+template <bool INV, typename C> __device__ __forceinline__ void dft5(C* v) {
+    using R = decltype(C::x);
+    const R c1 = (R)0.30901699437494742410, c2 = (R)-0.80901699437494742410;  // cos(2 pi / 5), cos(4 pi / 5)
+    const R s1 = (R)0.95105651629515357212, s2 = (R)0.58778525229247312917;   // sin(2 pi / 5), sin(4 pi / 5)
+    const C t1 = add<INV>(v[1], v[4]), t2 = add<INV>(v[2], v[3]), t3 = sub<INV>(v[1], v[4]), t4 = sub<INV>(v[2], v[3]);
+    const C a1 = mkc<C>(v[0].x + c1 * t1.x + c2 * t2.x, v[0].y + c1 * t1.y + c2 * t2.y);
+    const C a2 = mkc<C>(v[0].x + c2 * t1.x + c1 * t2.x, v[0].y + c2 * t1.y + c1 * t2.y);
+    const C b1 = mkc<C>(s1 * t3.x + s2 * t4.x, s1 * t3.y + s2 * t4.y);
+    const C b2 = mkc<C>(s2 * t3.x - s1 * t4.x, s2 * t3.y - s1 * t4.y);
+    // forward: y1 = a1 - i b1, y2 = a2 - i b2, y3 = a2 + i b2, y4 = a1 + i b1 (inverse: i -> -i)
+    const C ib1 = rot<INV>(b1), ib2 = rot<INV>(b2);
+    v[0] = mkc<C>(v[0].x + t1.x + t2.x, v[0].y + t1.y + t2.y);
+    v[1] = add<INV>(a1, ib1), v[4] = sub<INV>(a1, ib1);
+    v[2] = add<INV>(a2, ib2), v[3] = sub<INV>(a2, ib2);
+}
+
+// 6 points from two 3-point transforms (even and odd inputs) and the factors exp(-+ i pi k / 3)
+template <bool INV, typename C> __device__ __forceinline__ void dft6(C* v) {
+    using R = decltype(C::x);
+    const R h = (R)0.86602540378443864676;
+    C e0 = v[0], e1 = v[2], e2 = v[4], o0 = v[1], o1 = v[3], o2 = v[5];
+    dft3<INV>(e0, e1, e2);
+    dft3<INV>(o0, o1, o2);
+    // w1 = 1/2 -+ i h, w2 = -1/2 -+ i h
+    const R sg = INV ? (R)1 : (R)-1;
+    o1 = mkc<C>((R)0.5 * o1.x - sg * h * o1.y, (R)0.5 * o1.y + sg * h * o1.x);
+    o2 = mkc<C>((R)-0.5 * o2.x - sg * h * o2.y, (R)-0.5 * o2.y + sg * h * o2.x);
+    v[0] = add<INV>(e0, o0), v[3] = sub<INV>(e0, o0);
+    v[1] = add<INV>(e1, o1), v[4] = sub<INV>(e1, o1);
+    v[2] = add<INV>(e2, o2), v[5] = sub<INV>(e2, o2);
+}
+
+// One Stockham pass (pass q of F, radix R) over nseq sequences of length N: work item j of a
+// sequence reads x[j + r N/R], twiddles by exp(-+2 pi i r k / (Ns R)) with k = j mod Ns, transforms
+// in registers and writes y[(j - k) R + k + r Ns].  tw[m] = exp(-2 pi i m / N), m < N.
+template <int R, bool INV, typename C>
+__device__ __forceinline__ void stockham_pass(const C* in, C* out, int nseq, const Fft1D& F, int q,
                                               const C* __restrict__ tw) {
-    constexpr int R = 1 << LR;
-    const int NR = 1 << (logN - LR), Ns = 1 << logNs, tsh = logN - logNs - LR;
+    const int N = F.N, NR = F.NR[q], Ns = F.Ns[q], tstep = F.tstep[q];
+    const unsigned mNR = F.mNR[q], mNs = F.mNs[q];
+    const int lNR = F.lNR[q], lNs = F.lNs[q];
     for (int t = threadIdx.x; t < nseq * NR; t += blockDim.x) {
-        const int seq = t >> (logN - LR), j = t & (NR - 1), k = j & (Ns - 1);
-        const int x0 = (seq << logN) + j;
+        const int seq = fdiv(t, mNR, lNR), j = t - seq * NR, k = j - fdiv(j, mNs, lNs) * Ns;
+        const int x0 = seq * N + j;
         C v[R];
 #pragma unroll
         for (int r = 0; r < R; r++) v[r] = in[sx(x0 + r * NR)];
         if (Ns > 1) {
 #pragma unroll
             for (int r = 1; r < R; r++) {
-                C w = __ldg(tw + ((r * k) << tsh));
+                C w = __ldg(tw + r * k * tstep);
                 if (INV) w.y = -w.y;
                 v[r] = cmul(v[r], w);
             }
         }
-        if (LR == 3) dft8<INV>(v);
-        else if (LR == 2) dft4<INV>(v[0], v[1], v[2], v[3]);
+        if (R == 8) dft8<INV>(v);
+        else if (R == 6) dft6<INV>(v);
+        else if (R == 5) dft5<INV>(v);
+        else if (R == 4) dft4<INV>(v[0], v[1], v[2], v[3]);
+        else if (R == 3) dft3<INV>(v[0], v[1], v[2]);
         else dft2<INV>(v);
-        const int y0 = (seq << logN) + ((j - k) << LR) + k;
+        const int y0 = seq * N + (j - k) * R + k;
 #pragma unroll
         for (int r = 0; r < R; r++) out[sx(y0 + r * Ns)] = v[r];
     }
 }
 
-// nseq transforms of length 2^logN in a (natural order, padded index); b is scratch of the same size.  Returns the
-// buffer that holds the result.  Starts and ends at a barrier.
+// nseq transforms of length F.N in a (natural order, padded index); b is scratch of the same size.
+// Returns the buffer that holds the result.  Starts and ends at a barrier.
 template <bool INV, typename C>
-__device__ C* fft_smem(C* a, C* b, int nseq, int logN, const C* __restrict__ tw) {
-    int logNs = 0;
-    while (logNs < logN) {
-        const int lr = min(3, logN - logNs);
-        if (lr == 3) stockham_pass<3, INV>(a, b, nseq, logN, logNs, tw);
-        else if (lr == 2) stockham_pass<2, INV>(a, b, nseq, logN, logNs, tw);
-        else stockham_pass<1, INV>(a, b, nseq, logN, logNs, tw);
+__device__ C* fft_smem(C* a, C* b, int nseq, const Fft1D& F, const C* __restrict__ tw) {
+    for (int q = 0; q < F.np; q++) {
+        switch (F.R[q]) {
+            case 8: stockham_pass<8, INV>(a, b, nseq, F, q, tw); break;
+            case 6: stockham_pass<6, INV>(a, b, nseq, F, q, tw); break;
+            case 5: stockham_pass<5, INV>(a, b, nseq, F, q, tw); break;
+            case 4: stockham_pass<4, INV>(a, b, nseq, F, q, tw); break;
+            case 3: stockham_pass<3, INV>(a, b, nseq, F, q, tw); break;
+            default: stockham_pass<2, INV>(a, b, nseq, F, q, tw); break;
+        }
         __syncthreads();
         C* t = a;
         a = b, b = t;
-        logNs += lr;
     }
     return a;
 }
@@ -201,7 +309,8 @@ struct FftArgs {
     const int* ypos_p;
     const void* twx;
     const void* twy;
-    int Mx, My, logMx, logMy, ny_i, ny_p, R, K, NIpad, NPpad, item0;
+    Fft1D fx, fy;
+    int Mx, My, ny_i, ny_p, R, K, NIpad, NPpad, item0;
     double scale;
 };
 
@@ -225,7 +334,7 @@ __global__ void __launch_bounds__(kFftThreads) k_fft_rows_fwd(FftArgs A, int G) 
         }
     }
     __syncthreads();
-    const C* res = fft_smem<false>(s, s + n, G * 3, A.logMx, (const C*)A.twx);
+    const C* res = fft_smem<false>(s, s + n, G * 3, A.fx, (const C*)A.twx);
     const int gr = min(G, A.ny_i - row0);
     C* out = (C*)A.T1 + (size_t)iq * A.Mx * A.ny_i * 3;
     for (int t = threadIdx.x; t < A.Mx * gr * 3; t += blockDim.x) {
@@ -241,17 +350,17 @@ __global__ void __launch_bounds__(kFftThreads) k_fft_cols(FftArgs A, int G) {
     extern __shared__ __align__(16) unsigned char smraw[];
     C* s = (C*)smraw;  // [G][3][My] (padded index), then the same again as scratch
     const int iq = blockIdx.y, item = A.item0 + iq, k = item / A.R;
-    const int xi0 = blockIdx.x * G, n = padded(G * 3 * A.My);
+    const int xi0 = blockIdx.x * G, gc = min(G, A.Mx - xi0), n = padded(G * 3 * A.My);
     for (int t = threadIdx.x; t < n; t += blockDim.x) s[t] = mkc<C>(0, 0);
     __syncthreads();
     const C* in = (const C*)A.T1 + (size_t)iq * A.Mx * A.ny_i * 3;
-    for (int t = threadIdx.x; t < G * A.ny_i * 3; t += blockDim.x) {
+    for (int t = threadIdx.x; t < gc * A.ny_i * 3; t += blockDim.x) {
         const int c = t % 3, row = (t / 3) % A.ny_i, g = t / (3 * A.ny_i);
         s[sx((g * 3 + c) * A.My + A.ypos_i[row])] = in[((size_t)(xi0 + g) * A.ny_i + row) * 3 + c];
     }
     __syncthreads();
-    C* z0p = fft_smem<false>(s, s + n, G * 3, A.logMy, (const C*)A.twy);
-    for (int t = threadIdx.x; t < G * A.My; t += blockDim.x) {
+    C* z0p = fft_smem<false>(s, s + n, G * 3, A.fy, (const C*)A.twy);
+    for (int t = threadIdx.x; t < gc * A.My; t += blockDim.x) {
         const int g = t / A.My, et = t - g * A.My;
         const R* m = (const R*)A.mhat + (((size_t)k * A.Mx + xi0 + g) * A.My + et) * 6;
         const R a11 = m[0], a12 = m[1], a22 = m[2], a33 = m[3], b13 = m[4], b23 = m[5];
@@ -263,9 +372,9 @@ __global__ void __launch_bounds__(kFftThreads) k_fft_cols(FftArgs A, int G) {
         z0p[i2] = mkc<C>(fmx(a33, z2.x, -fmx(b13, z0.y, b23 * z1.y)), fmx(a33, z2.y, fmx(b13, z0.x, b23 * z1.x)));
     }
     __syncthreads();
-    const C* res = fft_smem<true>(z0p, z0p == s ? s + n : s, G * 3, A.logMy, (const C*)A.twy);
+    const C* res = fft_smem<true>(z0p, z0p == s ? s + n : s, G * 3, A.fy, (const C*)A.twy);
     C* out = (C*)A.T2 + (size_t)iq * A.Mx * A.ny_p * 3;
-    for (int t = threadIdx.x; t < G * A.ny_p * 3; t += blockDim.x) {
+    for (int t = threadIdx.x; t < gc * A.ny_p * 3; t += blockDim.x) {
         const int c = t % 3, row = (t / 3) % A.ny_p, g = t / (3 * A.ny_p);
         out[((size_t)(xi0 + g) * A.ny_p + row) * 3 + c] = res[sx((g * 3 + c) * A.My + A.ypos_p[row])];
     }
@@ -285,7 +394,7 @@ __global__ void __launch_bounds__(kFftThreads) k_fft_rows_inv(FftArgs A, int G) 
         s[sx((g * 3 + c) * A.Mx + xi)] = g < gr ? in[((size_t)xi * A.ny_p + row0 + g) * 3 + c] : mkc<C>(0, 0);
     }
     __syncthreads();
-    const C* res = fft_smem<true>(s, s + n, G * 3, A.logMx, (const C*)A.twx);
+    const C* res = fft_smem<true>(s, s + n, G * 3, A.fx, (const C*)A.twx);
     double* uk = A.uh + ((size_t)r * A.K + k) * A.NPpad * 6;
     for (int g = 0; g < gr; g++) {
         const int e0 = A.row_p[row0 + g], e1 = A.row_p[row0 + g + 1];
@@ -325,33 +434,35 @@ __global__ void k_fft_place(const double* __restrict__ tab, const int2* __restri
     }
 }
 
-// forward FFT along x of G rows (of length Mx) per block, in place in global memory
-__global__ void __launch_bounds__(kSetupThreads) k_fft_dense_rows(double2* S, int Mx, int logMx, int G,
+// forward FFT along x of G rows (of length Mx) of one field per block, in place in global memory;
+// S holds nf fields of My rows each, block (bx, f) takes rows bx G .. bx G + G - 1 of field f
+__global__ void __launch_bounds__(kSetupThreads) k_fft_dense_rows(double2* S, int Mx, int My, Fft1D fx, int G,
                                                                    const double2* __restrict__ twx) {
     extern __shared__ double2 sd[];  // [G][Mx] (padded index) twice
-    double2* rows = S + ((size_t)blockIdx.y * gridDim.x + blockIdx.x) * G * Mx;
-    for (int t = threadIdx.x; t < G * Mx; t += blockDim.x) sd[sx(t)] = rows[t];
+    const int row0 = blockIdx.x * G, gr = min(G, My - row0);
+    double2* rows = S + ((size_t)blockIdx.y * My + row0) * Mx;
+    for (int t = threadIdx.x; t < G * Mx; t += blockDim.x) sd[sx(t)] = t < gr * Mx ? rows[t] : make_double2(0, 0);
     __syncthreads();
-    const double2* res = fft_smem<false>(sd, sd + padded(G * Mx), G, logMx, twx);
-    for (int t = threadIdx.x; t < G * Mx; t += blockDim.x) rows[t] = res[sx(t)];
+    const double2* res = fft_smem<false>(sd, sd + padded(G * Mx), G, fx, twx);
+    for (int t = threadIdx.x; t < gr * Mx; t += blockDim.x) rows[t] = res[sx(t)];
 }
 
 // forward FFT along y of G columns of one of the six fields of one mode, into Mhat [k][Mx][My][6]
 // (the real part of the even fields a_ij, the imaginary part of the odd fields b_i3)
 __global__ void __launch_bounds__(kSetupThreads) k_fft_dense_cols(const double2* __restrict__ S, int Mx, int My,
-                                                                   int logMy, int G, int k0,
+                                                                   Fft1D fy, int G, int k0,
                                                                    const double2* __restrict__ twy,
                                                                    double* __restrict__ mhat) {
     extern __shared__ double2 sd[];  // [G][My] (padded index) twice
-    const int kk = blockIdx.y / 6, f = blockIdx.y - 6 * kk, xi0 = blockIdx.x * G;
+    const int kk = blockIdx.y / 6, f = blockIdx.y - 6 * kk, xi0 = blockIdx.x * G, gc = min(G, Mx - xi0);
     const double2* base = S + ((size_t)kk * 6 + f) * My * Mx;
     for (int t = threadIdx.x; t < G * My; t += blockDim.x) {
         const int g = t % G, y = t / G;
-        sd[sx(g * My + y)] = base[(size_t)y * Mx + xi0 + g];
+        sd[sx(g * My + y)] = g < gc ? base[(size_t)y * Mx + xi0 + g] : make_double2(0, 0);
     }
     __syncthreads();
-    const double2* res = fft_smem<false>(sd, sd + padded(G * My), G, logMy, twy);
-    for (int t = threadIdx.x; t < G * My; t += blockDim.x) {
+    const double2* res = fft_smem<false>(sd, sd + padded(G * My), G, fy, twy);
+    for (int t = threadIdx.x; t < gc * My; t += blockDim.x) {
         const int et = t % My, g = t / My;
         const double2 v = res[sx(g * My + et)];
         mhat[(((size_t)(k0 + kk) * Mx + xi0 + g) * My + et) * 6 + f] = f < 4 ? v.x : v.y;
@@ -423,13 +534,14 @@ int fft_prepare(Plan& P, int precision) {
     }
     FftGrid* F = new (std::nothrow) FftGrid();
     if (!F) return report_error(FBC_ERR_OOM, "host allocation failed");
-    F->logMx = std::max(1, ilog2(2 * ex + 1)), F->logMy = std::max(1, ilog2(2 * ey + 1));
-    F->Mx = 1 << F->logMx, F->My = 1 << F->logMy;
-    if (F->Mx > 2048 || F->My > 2048) {
+    if (2 * ex + 1 > 2048 || 2 * ey + 1 > 2048) {
         delete F;
-        snprintf(msg, sizeof(msg), "in-plane FFT: grid %d x %d above 2048 per side", 1 << F->logMx, 1 << F->logMy);
+        snprintf(msg, sizeof(msg), "in-plane FFT: differences span %d x %d, above 2048 per side", 2 * ex + 1,
+                 2 * ey + 1);
         return report_error(FBC_ERR_UNSUPPORTED, msg);
     }
+    F->fx = choose_length(2 * ex + 1), F->fy = choose_length(2 * ey + 1);
+    F->Mx = F->fx.N, F->My = F->fy.N;
     const int Mx = F->Mx, My = F->My;
     int ox = 1 << 30, oy = 1 << 30;
     for (int s = 0; s < P.NIpad; s++)
@@ -542,11 +654,11 @@ cudaError_t launch_fft_tables(Plan& P, int precision, cudaStream_t st) {
                                                                            P.box_y0, Mx, My, S);
             if ((e = cudaGetLastError())) break;
         }
-        k_fft_dense_rows<<<dim3(My / Gr, n * 6), kSetupThreads, smem_dr, st>>>(
-            S, Mx, F->logMx, Gr, F->d_twx);
+        k_fft_dense_rows<<<dim3((My + Gr - 1) / Gr, n * 6), kSetupThreads, smem_dr, st>>>(
+            S, Mx, My, F->fx, Gr, F->d_twx);
         if ((e = cudaGetLastError())) break;
-        k_fft_dense_cols<<<dim3(Mx / Gc, n * 6), kSetupThreads, smem_dc, st>>>(
-            S, Mx, My, F->logMy, Gc, k0, F->d_twy, F->d_mhat);
+        k_fft_dense_cols<<<dim3((Mx + Gc - 1) / Gc, n * 6), kSetupThreads, smem_dc, st>>>(
+            S, Mx, My, F->fy, Gc, k0, F->d_twy, F->d_mhat);
         e = cudaGetLastError();
     }
     cudaError_t e2 = cudaFreeAsync(S, st);
@@ -576,7 +688,7 @@ static cudaError_t run_fft_items(FftArgs A, const FftGrid* F, int i_begin, int i
         k_fft_rows_fwd<R><<<dim3((F->ny_i + Gr - 1) / Gr, q), kFftThreads, smem_r, st>>>(A, Gr);
         cudaError_t e = cudaGetLastError();
         if (e) return e;
-        k_fft_cols<R><<<dim3(F->Mx / Gc, q), kFftThreads, smem_c, st>>>(A, Gc);
+        k_fft_cols<R><<<dim3((F->Mx + Gc - 1) / Gc, q), kFftThreads, smem_c, st>>>(A, Gc);
         if ((e = cudaGetLastError())) return e;
         k_fft_rows_inv<R><<<dim3((F->ny_p + Gr - 1) / Gr, q), kFftThreads, smem_r, st>>>(A, Gr);
         if ((e = cudaGetLastError())) return e;
@@ -591,7 +703,8 @@ cudaError_t launch_contract_fft(Plan& P, int n_rhs, cudaStream_t st) {
     A.fh = P.d_fh, A.uh = P.d_uh, A.T1 = F->d_T1, A.T2 = F->d_T2;
     A.row_i = F->d_row_i, A.ent_i = F->d_ent_i, A.row_p = F->d_row_p, A.ent_p = F->d_ent_p;
     A.ypos_i = F->d_ypos_i, A.ypos_p = F->d_ypos_p;
-    A.Mx = F->Mx, A.My = F->My, A.logMx = F->logMx, A.logMy = F->logMy, A.ny_i = F->ny_i, A.ny_p = F->ny_p;
+    A.fx = F->fx, A.fy = F->fy;
+    A.Mx = F->Mx, A.My = F->My, A.ny_i = F->ny_i, A.ny_p = F->ny_p;
     A.R = n_rhs, A.K = P.K, A.NIpad = P.NIpad, A.NPpad = P.NPpad;
     A.scale = 1.0 / ((double)F->Mx * (double)F->My);
     const int items = n_rhs * P.K;

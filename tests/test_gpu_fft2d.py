@@ -77,12 +77,12 @@ def test_fft_multi_rhs_flags_and_switching(fbc):
 
 
 def test_fft_chunked_workspace(fbc):
-    # 8000 x 12000 columns: a 512 x 512 grid, about 7.5 MB of workspace per (rhs, mode) item, so the
-    # 2 x 129 items run in two chunks
+    # 8000 x 12000 columns: differences span 305 per side, a 320 x 320 grid (radices 5, 8, 8), about
+    # 4.7 MB of workspace per (rhs, mode) item, so the 2 x 129 items run in two chunks
     xy_i, xy_p = inputs.ring_geometry(8000, 12000)
     out = _both(fbc, xy_i, xy_p, 256, 2, 8)
     assert rel_l2(out["fft64"][0], out["fp64"][0]) <= 1e-12
-    assert out["info"]["fft_mx"] == 512 and out["info"]["fft_chunk_items"] < 2 * 129, out["info"]
+    assert out["info"]["fft_mx"] == 320 and out["info"]["fft_chunk_items"] < 2 * 129, out["info"]
 
 
 def test_fft_rejected_for_batches(fbc):
