@@ -115,3 +115,38 @@ def test_fft32_against_fp64(fbc, n_i, n_p, L, R):
     assert rel_l2(out["fft32"], ref) <= 1e-5, rel_l2(out["fft32"], ref)
     # the k = 0 band (the mean along the line) keeps FP64 accuracy
     assert rel_l2(out["fft32"].mean(axis=2), ref.mean(axis=2)) <= 1e-11
+
+
+def test_fft_host_entry_point(fbc):
+    """fbc_apply_host on an FFT plan: the same bits as the device entry point."""
+    xy_i, xy_p = inputs.ring_geometry(150, 220)
+    L, R = 8, 2
+    f = inputs.forces(R, 150, L, seed=3)
+    u0 = np.random.default_rng(4).normal(0, 1, (R, 220, L, 3))
+    with fbc.Plan(xy_i, xy_p, L, CUBIC, precision="fft64", max_rhs=R) as plan:
+        plan.tabulate()
+        ud = torch.from_numpy(u0.copy()).cuda()
+        plan.apply(torch.from_numpy(f).cuda(), ud, alpha=0.5, beta=2.0)
+        torch.cuda.synchronize()
+        uh = u0.copy()
+        plan.apply_host(f, uh, alpha=0.5, beta=2.0)
+        plan.sync_status()
+    np.testing.assert_array_equal(uh, ud.cpu().numpy())
+
+
+@pytest.mark.parametrize("n_i,n_p,L", [(1, 1, 2), (2, 3, 4), (5, 7, 8), (13, 20, 2)])
+def test_fft_degenerate_geometries(fbc, oracle_mod, n_i, n_p, L):
+    """One or a few columns and the shortest lines: grid sides of 2 to 9 points (single passes of
+    radix 2, 3, 5 and mixed lengths), K = 2 modes."""
+    xy_i, xy_p = inputs.ring_geometry(n_i, n_p)
+    f = inputs.forces(1, n_i, L, seed=n_i)
+    ref = oracle_mod.pad_update(xy_i, xy_p, L, 1.0, ISO, f)
+    for prec, tol in (("fft64", 1e-12), ("fft32", 1e-5)):
+        with fbc.Plan(xy_i, xy_p, L, ISO, precision=prec) as plan:
+            plan.tabulate()
+            u = torch.full((1, n_p, L, 3), float("nan"), dtype=torch.float64, device="cuda")
+            plan.apply(torch.from_numpy(f).cuda(), u)
+            torch.cuda.synchronize()
+            plan.sync_status()
+            got = u.cpu().numpy()
+        assert rel_l2(got, ref) <= tol, (prec, rel_l2(got, ref))

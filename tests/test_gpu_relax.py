@@ -93,16 +93,18 @@ def test_two_iterations(fbc, oracle_mod, case):
     assert rel_l2(u, u2) <= 1e-12
 
 
-def test_tensor_plan(fbc, case):
-    """A tensor-core plan: alpha from the same FP64 dot products, ||G f|| from the FP32 transform."""
+@pytest.mark.parametrize("prec,tol", [("bf16x2", 1e-4), ("fft32", 1e-5), ("fft64", 1e-12)])
+def test_other_forms(fbc, case, prec, tol):
+    """Tensor-core and in-plane FFT plans: alpha from the same FP64 dot products, ||G f|| from the form's
+    own inverse transform (FP32 for the tensor-core and FP32 FFT forms)."""
     xy_i, xy_p, f_old, f_new, u0 = case
     out = {}
-    for prec in ("fp64", "bf16x2"):
-        with fbc.Plan(xy_i, xy_p, L, ISO, precision=prec, max_rhs=R) as plan:
+    for p in ("fp64", prec):
+        with fbc.Plan(xy_i, xy_p, L, ISO, precision=p, max_rhs=R) as plan:
             plan.tabulate()
-            out[prec] = _gpu(fbc, plan, f_new, f_old, u0, [1.0, 1.0, 1.0], 1e-2)
-    np.testing.assert_allclose(out["bf16x2"][1], out["fp64"][1], rtol=1e-4)
-    assert rel_l2(out["bf16x2"][0] - u0, out["fp64"][0] - u0) <= 1e-4
+            out[p] = _gpu(fbc, plan, f_new, f_old, u0, [1.0, 1.0, 1.0], 1e-2)
+    np.testing.assert_allclose(out[prec][1], out["fp64"][1], rtol=tol)
+    assert rel_l2(out[prec][0] - u0, out["fp64"][0] - u0) <= tol
 
 
 def test_rejects_bad_arguments(fbc, case):
