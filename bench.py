@@ -120,6 +120,27 @@ def dist_env():
     return rank, world, local
 
 
+def rank_forces(w, rank: int):
+    """Replicas: rank r updates its own instance of the workload, with forces seeded seed + r."""
+    return w.forces(seed=w.seed + rank)
+
+
+def job_step_ms(step_ms: float, world: int, dist=None, device="cuda") -> float:
+    """The whole job's step time: the maximum over ranks of each rank's own CUDA-event time."""
+    if world > 1:
+        import torch
+
+        t = torch.tensor([step_ms], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        step_ms = float(t.item())
+    return step_ms
+
+
+def job_value(pair_modes: float, world: int, step_ms: float) -> float:
+    """Whole-job throughput in Gpair-modes/s: the pair-modes of all ranks over the slowest rank's step."""
+    return world * pair_modes / (step_ms * 1e-3) / 1e9
+
+
 def oracle_sample(w, xy_i, xy_p, f, n_cols: int = 1):
     """The oracle's bounded sample: every repeat of the first n_cols pad columns
     (all of their differences are tabulated first, as setup)."""
@@ -303,7 +324,7 @@ def run_ours(args, w):
     pk = peaks()
     R = w.n_rhs
     xy_i, xy_p = w.geometry()
-    f = w.forces(seed=w.seed + rank)  # replicas: each rank updates its own instance
+    f = rank_forces(w, rank)
     t0 = time.perf_counter()
     plan = fbc.Plan(xy_i, xy_p, w.L, w.material, precision=args.precision, max_rhs=R)
     plan.tabulate()
@@ -359,12 +380,8 @@ def run_ours(args, w):
     with ClockSampler(local) as clk:
         ms, stage = time_device_steps(torch, plan, fd, ud, args.steps, args.warmup, flush_buf)
     torch.cuda.synchronize()
-    step_ms = float(np.sum(ms)) / args.steps
-    if world > 1:
-        t = torch.tensor([step_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        step_ms = float(t.item())
-    value = world * pm / (step_ms * 1e-3) / 1e9
+    step_ms = job_step_ms(float(np.sum(ms)) / args.steps, world, dist if world > 1 else None)
+    value = job_value(pm, world, step_ms)
     outputs["headline"] = snap()
 
     # the other precisions on the same plan and inputs (not after the tables were released); at the
@@ -403,7 +420,7 @@ def run_ours(args, w):
         t1 = time.perf_counter()
         plan.apply_host(fh, uh)
         e2e_t.append(time.perf_counter() - t1)
-    e2e_s = float(np.mean(e2e_t))
+    e2e_s = job_step_ms(float(np.mean(e2e_t)) * 1e3, world, dist if world > 1 else None) * 1e-3
     h2d = f.nbytes
     d2h = uh.numel() * 8
     del fh, uh
@@ -490,7 +507,7 @@ def run_ours(args, w):
                      "frac": achieved / peak, "traffic": traffic, "peak_source": peak_name,
                      "useful_tflops": FLOPS_PER_PAIR_MODE * pm / (contract_ms * 1e-3) / 1e12},
         "variants": variants,
-        "e2e": {"value": world * pm / e2e_s / 1e9, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+        "e2e": {"value": job_value(pm, world, e2e_s * 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "ms_per_step": e2e_s * 1e3},
         "gpu_launches": launches_per_apply(p, info) * args.steps,
         "clocks": clocks,
@@ -530,7 +547,8 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--precision", choices=["fp64", "f32x2", "fp32", "tf32", "bf16x2", "bf16x3"], default=None,
+    ap.add_argument("--precision", choices=["fp64", "f32x2", "fp32", "tf32", "bf16x2", "bf16x3", "fft64", "fft32"],
+                    default=None,
                     help="contraction precision (default: f32x2 for one right-hand side, bf16x2 for several)")
     ap.add_argument("--workload", choices=sorted(inputs.WORKLOADS), default=WORKLOAD)
     ap.add_argument("--surrogate", action="store_true",
