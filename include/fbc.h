@@ -173,7 +173,9 @@ int fbc_plan_create(const fbc_geometry* geom, const fbc_material* mat, const fbc
  * six reals [Re g11, Re g12, Re g22, Re g33, Im g13, Im g23] (the other
  * parts vanish by the mirror symmetry).  Runs once per plan; the table is
  * reused by every apply (Sec. 3.2: the setup is reused across runs).
- * Asynchronous on `stream`. */
+ * Asynchronous on `stream`, except that for the in-plane FFT forms the first
+ * call also builds the grid (host structures and device buffers: synchronous,
+ * allocates) before it queues the grid transform of the table. */
 int fbc_tabulate_kernel(fbc_plan* plan, void* stream);
 
 /* The pad update (see the top of this file) for n_rhs right-hand sides:
@@ -218,7 +220,9 @@ int fbc_apply_host(fbc_plan* plan, const double* f_host, double* u_host, int32_t
 
 /* Switch the contraction precision of an existing plan.  Builds the
  * precision's derived table from the FP64 table on first use (allocates;
- * call outside stream capture).  Synchronous. */
+ * call outside stream capture): the FP32 or double-float table, or for the
+ * in-plane FFT forms the grid and its transformed kernel (K x Mx x My x 6
+ * reals in FP64, plus an FP32 copy for FBC_PREC_FFT32).  Synchronous. */
 int fbc_plan_set_precision(fbc_plan* plan, int32_t precision);
 
 /* Stage timing for profiling.  While enabled, every fbc_apply records CUDA
