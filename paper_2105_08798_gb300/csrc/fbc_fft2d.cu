@@ -62,9 +62,9 @@ struct FftGrid {
     int ny_i = 0, ny_p = 0;
     int Q = 0;                     // (rhs, mode) items per chunk of the workspace
     int* d_row_i = nullptr;        // [ny_i + 1] CSR of the interface rows
-    int2* d_ent_i = nullptr;       // (x position on the grid, fh slot)
+    int2* d_ent_i = nullptr;       // (x position on the grid | row << 12, fh slot)
     int* d_row_p = nullptr;        // [ny_p + 1]
-    int2* d_ent_p = nullptr;       // (x position on the grid, uh slot)
+    int2* d_ent_p = nullptr;       // (x position on the grid | row << 12, uh slot)
     int* d_ypos_i = nullptr;       // [ny_i] y position on the grid of each interface row
     int* d_ypos_p = nullptr;       // [ny_p]
     double2* d_twx = nullptr;      // [Mx] exp(-2 pi i j / Mx)
@@ -325,13 +325,13 @@ __global__ void __launch_bounds__(kFftThreads) k_fft_rows_fwd(FftArgs A, int G) 
     for (int t = threadIdx.x; t < n; t += blockDim.x) s[t] = mkc<C>(0, 0);
     __syncthreads();
     const double* fk = A.fh + ((size_t)r * A.K + k) * A.NIpad * 6;
-    for (int g = 0; g < G && row0 + g < A.ny_i; g++) {
-        const int e0 = A.row_i[row0 + g], e1 = A.row_i[row0 + g + 1];
-        for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
-            const int2 en = A.ent_i[e];
-            const double* v = fk + (size_t)en.y * 6;
-            for (int c = 0; c < 3; c++) s[sx((g * 3 + c) * A.Mx + en.x)] = mkc<C>((R)v[c], (R)v[3 + c]);
-        }
+    // all entries of the block's rows in one loop (each entry carries its row)
+    const int e1 = A.row_i[min(row0 + G, A.ny_i)];
+    for (int e = A.row_i[row0] + threadIdx.x; e < e1; e += blockDim.x) {
+        const int2 en = A.ent_i[e];
+        const int g = (en.x >> 12) - row0, xp = en.x & 4095;
+        const double* v = fk + (size_t)en.y * 6;
+        for (int c = 0; c < 3; c++) s[sx((g * 3 + c) * A.Mx + xp)] = mkc<C>((R)v[c], (R)v[3 + c]);
     }
     __syncthreads();
     const C* res = fft_smem<false>(s, s + n, G * 3, A.fx, (const C*)A.twx);
@@ -396,15 +396,14 @@ __global__ void __launch_bounds__(kFftThreads) k_fft_rows_inv(FftArgs A, int G) 
     __syncthreads();
     const C* res = fft_smem<true>(s, s + n, G * 3, A.fx, (const C*)A.twx);
     double* uk = A.uh + ((size_t)r * A.K + k) * A.NPpad * 6;
-    for (int g = 0; g < gr; g++) {
-        const int e0 = A.row_p[row0 + g], e1 = A.row_p[row0 + g + 1];
-        for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
-            const int2 en = A.ent_p[e];
-            double* o = uk + (size_t)en.y * 6;
-            for (int c = 0; c < 3; c++) {
-                const C v = res[sx((g * 3 + c) * A.Mx + en.x)];
-                o[c] = (double)v.x * A.scale, o[3 + c] = (double)v.y * A.scale;
-            }
+    const int e1 = A.row_p[row0 + gr];
+    for (int e = A.row_p[row0] + threadIdx.x; e < e1; e += blockDim.x) {
+        const int2 en = A.ent_p[e];
+        const int g = (en.x >> 12) - row0, xp = en.x & 4095;
+        double* o = uk + (size_t)en.y * 6;
+        for (int c = 0; c < 3; c++) {
+            const C v = res[sx((g * 3 + c) * A.Mx + xp)];
+            o[c] = (double)v.x * A.scale, o[3 + c] = (double)v.y * A.scale;
         }
     }
 }
@@ -560,7 +559,7 @@ int fft_prepare(Plan& P, int precision) {
             for (const int2& e : kv.second) {
                 const int xr = (((e.x - ox) % Mx) + Mx) % Mx;
                 if (!xres.insert(xr).second) return false;
-                ent.push_back(make_int2(xr, e.y));
+                ent.push_back(make_int2(xr | ((int)ypos.size() << 12), e.y));  // row index in the upper bits
             }
             row.push_back((int)ent.size());
             ypos.push_back(yr);
