@@ -312,11 +312,14 @@ struct FftArgs {
     Fft1D fx, fy;
     int Mx, My, ny_i, ny_p, R, K, NIpad, NPpad, item0;
     double scale;
+    // divisions of the index decodes: by the rows per block of P1 / P3, ny_i, ny_p and My
+    unsigned mG, mNyi, mNyp, mMy;
+    int lG, lNyi, lNyp, lMy;
 };
 
 // P1: rows of interface sites, forward FFT along x.  Block: G rows of one item.
 template <typename R>
-__global__ void __launch_bounds__(kFftThreads) k_fft_rows_fwd(FftArgs A, int G) {
+__global__ void __launch_bounds__(kFftThreads, sizeof(R) == 4 ? 3 : 2) k_fft_rows_fwd(FftArgs A, int G) {
     using C = Cx<R>;
     extern __shared__ __align__(16) unsigned char smraw[];
     C* s = (C*)smraw;  // [G][3][Mx] (padded index), then the same again as scratch
@@ -337,15 +340,15 @@ __global__ void __launch_bounds__(kFftThreads) k_fft_rows_fwd(FftArgs A, int G) 
     const C* res = fft_smem<false>(s, s + n, G * 3, A.fx, (const C*)A.twx);
     const int gr = min(G, A.ny_i - row0);
     C* out = (C*)A.T1 + (size_t)iq * A.Mx * A.ny_i * 3;
-    for (int t = threadIdx.x; t < A.Mx * gr * 3; t += blockDim.x) {
-        const int c = t % 3, g = (t / 3) % gr, xi = t / (3 * gr);
-        out[((size_t)xi * A.ny_i + row0 + g) * 3 + c] = res[sx((g * 3 + c) * A.Mx + xi)];
+    for (int t = threadIdx.x; t < A.Mx * G * 3; t += blockDim.x) {
+        const int q = t / 3, c = t - 3 * q, xi = fdiv(q, A.mG, A.lG), g = q - xi * G;
+        if (g < gr) out[((size_t)xi * A.ny_i + row0 + g) * 3 + c] = res[sx((g * 3 + c) * A.Mx + xi)];
     }
 }
 
 // P2: G grid columns of one item: forward FFT along y, Mhat, inverse FFT along y, pad rows out.
 template <typename R>
-__global__ void __launch_bounds__(kFftThreads) k_fft_cols(FftArgs A, int G) {
+__global__ void __launch_bounds__(kFftThreads, sizeof(R) == 4 ? 3 : 2) k_fft_cols(FftArgs A, int G) {
     using C = Cx<R>;
     extern __shared__ __align__(16) unsigned char smraw[];
     C* s = (C*)smraw;  // [G][3][My] (padded index), then the same again as scratch
@@ -355,13 +358,13 @@ __global__ void __launch_bounds__(kFftThreads) k_fft_cols(FftArgs A, int G) {
     __syncthreads();
     const C* in = (const C*)A.T1 + (size_t)iq * A.Mx * A.ny_i * 3;
     for (int t = threadIdx.x; t < gc * A.ny_i * 3; t += blockDim.x) {
-        const int c = t % 3, row = (t / 3) % A.ny_i, g = t / (3 * A.ny_i);
+        const int q = t / 3, c = t - 3 * q, g = fdiv(q, A.mNyi, A.lNyi), row = q - g * A.ny_i;
         s[sx((g * 3 + c) * A.My + A.ypos_i[row])] = in[((size_t)(xi0 + g) * A.ny_i + row) * 3 + c];
     }
     __syncthreads();
     C* z0p = fft_smem<false>(s, s + n, G * 3, A.fy, (const C*)A.twy);
     for (int t = threadIdx.x; t < gc * A.My; t += blockDim.x) {
-        const int g = t / A.My, et = t - g * A.My;
+        const int g = fdiv(t, A.mMy, A.lMy), et = t - g * A.My;
         const R* m = (const R*)A.mhat + (((size_t)k * A.Mx + xi0 + g) * A.My + et) * 6;
         const R a11 = m[0], a12 = m[1], a22 = m[2], a33 = m[3], b13 = m[4], b23 = m[5];
         const int i0 = sx(g * 3 * A.My + et), i1 = sx((g * 3 + 1) * A.My + et), i2 = sx((g * 3 + 2) * A.My + et);
@@ -375,14 +378,14 @@ __global__ void __launch_bounds__(kFftThreads) k_fft_cols(FftArgs A, int G) {
     const C* res = fft_smem<true>(z0p, z0p == s ? s + n : s, G * 3, A.fy, (const C*)A.twy);
     C* out = (C*)A.T2 + (size_t)iq * A.Mx * A.ny_p * 3;
     for (int t = threadIdx.x; t < gc * A.ny_p * 3; t += blockDim.x) {
-        const int c = t % 3, row = (t / 3) % A.ny_p, g = t / (3 * A.ny_p);
+        const int q = t / 3, c = t - 3 * q, g = fdiv(q, A.mNyp, A.lNyp), row = q - g * A.ny_p;
         out[((size_t)(xi0 + g) * A.ny_p + row) * 3 + c] = res[sx((g * 3 + c) * A.My + A.ypos_p[row])];
     }
 }
 
 // P3: G pad rows of one item: inverse FFT along x, scale, scatter the pad sites into uh.
 template <typename R>
-__global__ void __launch_bounds__(kFftThreads) k_fft_rows_inv(FftArgs A, int G) {
+__global__ void __launch_bounds__(kFftThreads, sizeof(R) == 4 ? 3 : 2) k_fft_rows_inv(FftArgs A, int G) {
     using C = Cx<R>;
     extern __shared__ __align__(16) unsigned char smraw[];
     C* s = (C*)smraw;  // [G][3][Mx] (padded index), then the same again as scratch
@@ -390,7 +393,7 @@ __global__ void __launch_bounds__(kFftThreads) k_fft_rows_inv(FftArgs A, int G) 
     const int row0 = blockIdx.x * G, gr = min(G, A.ny_p - row0), n = padded(G * 3 * A.Mx);
     const C* in = (const C*)A.T2 + (size_t)iq * A.Mx * A.ny_p * 3;
     for (int t = threadIdx.x; t < A.Mx * G * 3; t += blockDim.x) {
-        const int c = t % 3, g = (t / 3) % G, xi = t / (3 * G);
+        const int q = t / 3, c = t - 3 * q, xi = fdiv(q, A.mG, A.lG), g = q - xi * G;
         s[sx((g * 3 + c) * A.Mx + xi)] = g < gr ? in[((size_t)xi * A.ny_p + row0 + g) * 3 + c] : mkc<C>(0, 0);
     }
     __syncthreads();
@@ -673,6 +676,10 @@ template <typename R>
 static cudaError_t run_fft_items(FftArgs A, const FftGrid* F, int i_begin, int i_end, int q_max, cudaStream_t st) {
     const int Gr = std::max(1, kRowElems / F->Mx);
     const int Gc = std::max(1, std::min(F->Mx, kRowElems / F->My));
+    div_magic(Gr, &A.mG, &A.lG);
+    div_magic(F->ny_i, &A.mNyi, &A.lNyi);
+    div_magic(F->ny_p, &A.mNyp, &A.lNyp);
+    div_magic(F->My, &A.mMy, &A.lMy);
     const size_t smem_r = (size_t)2 * padded(Gr * 3 * F->Mx) * sizeof(Cx<R>);  // data and scratch
     const size_t smem_c = (size_t)2 * padded(Gc * 3 * F->My) * sizeof(Cx<R>);
     if (smem_r > 48 * 1024) {
