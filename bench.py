@@ -23,6 +23,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -67,7 +68,8 @@ class ClockSampler:
     def __init__(self, index: int):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+        # raw samples; the JSON line carries their summary
+        self.path = os.path.join(tempfile.gettempdir(), f"fbc_clocks_{os.getpid()}.csv")
 
     def __enter__(self):
         try:
