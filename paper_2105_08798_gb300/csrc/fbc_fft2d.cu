@@ -1,4 +1,6 @@
-// In-plane FFT form of the per-mode contraction (FBC_PREC_FFT64).
+// In-plane FFT forms of the per-mode contraction (FBC_PREC_FFT64: FP64
+// throughout; FBC_PREC_FFT32: FP32 transforms and kernel for k >= 1, the
+// k = 0 mode on the FP64 transforms).
 //
 // The dense contraction evaluates, for every wavenumber k and right-hand side,
 //     U(a) = sum_b M^k(x_a - x_b) z(b),
@@ -11,9 +13,8 @@
 // convolution over the lattice.  It is evaluated exactly by a circular
 // convolution on an Mx x My grid with at least 2 max|d| + 1 points per side
 // (each side 2^a 3^b 5^c, the cheapest such length): every difference d that
-// occurs, and its mirror -d, then has a
-// residue of its own, so the circular sum at a pad site picks up exactly the
-// terms of the direct sum.  The kernel is placed at d with the table values
+// occurs, and its mirror -d, then has a residue of its own, so the circular
+// sum at a pad site picks up exactly the terms of the direct sum.  The kernel is placed at d with the table values
 // and at -d with the exact mirror relations of the Green function (a_ij even
 // and b_i3 odd in d), which makes its 2D DFT the Hermitian matrix
 //     Mhat = [[A11, A12, -i B13], [A12, A22, -i B23], [i B13, i B23, A33]]
