@@ -15,6 +15,9 @@ written from the definitions:
 * ``spring_bonds`` -- the model's bonds: central springs k1 to the neighbours
   with |n|_1 = 1 and k2 to those with |n|_1 = 2 on the lattice with in-plane
   spacing 1 and plane spacing c.
+* ``symbol`` and ``lattice_mode_table`` -- the lattice Green function of the
+  stencil (App., the inverse transform of the inverted Fourier symbol), in
+  the modes of the line-periodic lattice, by the zone grid's trapezoid rule.
 """
 
 from __future__ import annotations
@@ -86,3 +89,45 @@ def spring_incompat_force(xy_i, sources, L: int, c: float, k1: float, k2: float)
             stretch = (u_a - u_b) @ v  # [R][L]: bond elongation times |v|
             f[:, a] += (k / float(v @ v)) * stretch[..., None] * v
     return f
+
+
+def symbol(K, theta) -> np.ndarray:
+    """Fourier symbol of the block stencil, D(theta) = sum_n K(n) exp(-i theta . n), theta [..., 3]
+    (App., the transform of the lattice Green function); returns complex [..., 3, 3]."""
+    K = np.asarray(K, dtype=np.float64).reshape(27, 3, 3)
+    theta = np.asarray(theta, dtype=np.float64)
+    D = np.zeros(theta.shape[:-1] + (3, 3), dtype=np.complex128)
+    for j, (nx, ny, nz) in enumerate(itertools.product((-1, 0, 1), repeat=3)):
+        if K[j].any():
+            ph = np.exp(-1j * (theta[..., 0] * nx + theta[..., 1] * ny + theta[..., 2] * nz))
+            D += ph[..., None, None] * K[j]
+    return D
+
+
+def lattice_mode_table(K, L: int, d_list, ks, n: int) -> np.ndarray:
+    """Lattice Green function of the stencil in the modes of the line-periodic lattice (App., the
+    inverse transform of the inverted symbol), complex [len(d_list)][len(ks)][3][3]:
+
+        g^k(d) = (1 / n^2) sum_{theta in the n x n zone grid} D(theta_x, theta_y, 2 pi k / L)^-1
+                 exp(i theta . d),   theta_x, theta_y = 2 pi j / n.
+
+    This is the trapezoid rule for the zone integral (2 pi)^-2 int D^-1 exp(i theta . d), and the
+    exact Green function of the lattice made n-periodic in the plane.  For k = 0 the symbol is
+    singular at theta = 0; that term is left out (the zero-mean periodic Green function, defined up
+    to the constant every Green function of the plane carries)."""
+    d_list = np.asarray(d_list).reshape(-1, 2)
+    th = 2.0 * np.pi * np.arange(n) / n
+    TX, TY = np.meshgrid(th, th, indexing="ij")
+    out = np.zeros((len(d_list), len(ks), 3, 3), dtype=np.complex128)
+    for ik, k in enumerate(ks):
+        theta = np.stack([TX, TY, np.full_like(TX, 2.0 * np.pi * k / L)], axis=-1)
+        D = symbol(K, theta)
+        if k % L == 0:
+            D[0, 0] = np.eye(3)  # placeholder, its inverse is zeroed below
+        Dinv = np.linalg.inv(D)
+        if k % L == 0:
+            Dinv[0, 0] = 0.0
+        for idd, (dx, dy) in enumerate(d_list):
+            ph = np.exp(1j * (TX * dx + TY * dy))
+            out[idd, ik] = np.einsum("xy,xyij->ij", ph, Dinv) / (n * n)
+    return out
