@@ -249,6 +249,28 @@ int fbc_plan_info_get(const fbc_plan* plan, fbc_plan_info* info);
  * Any output pointer may be NULL. */
 int fbc_plan_layout(const fbc_plan* plan, int32_t* perm_i, int32_t* perm_p, int32_t* xy_i, int32_t* xy_p);
 
+/* Lattice Green function near field (App.: the lattice Green function up to
+ * a cut-off, the continuum one beyond, joined by a blending constant).  For
+ * every difference d of the plan's table with |d| <= r_cut, the mode entries
+ * g^k(d) are replaced by the lattice Green function of the harmonic block
+ * stencil K [27][3][3] (HOST, the layout of fbc_stencil_create):
+ *     g^k(d) = (2 pi)^-2 int D(theta_x, theta_y, 2 pi k / L)^-1 exp(i theta . d),
+ *     D(theta) = sum_n K(n) exp(-i theta . n),
+ * evaluated by the trapezoid rule on an n x n grid of the zone (n = n_zone
+ * rounded up to 2^a 3^b 5^c; 16 <= n_zone <= 2048), i.e. by 2D FFTs.  The
+ * modes k >= 1 are used as computed.  The k = 0 mode (symbol singular at
+ * theta = 0, left out) is defined up to a constant: it is shifted by
+ * C = g_lat^0(d_ref) - g^0(d_ref), d_ref = (ref_dx, ref_dy) a difference of
+ * the plan's table with |d_ref| > r_cut (the paper's r', far enough that C
+ * hardly depends on it).  The stencil must satisfy
+ * K(-n) = K(n) and the mirror symmetry along the line (FBC_ERR_UNSUPPORTED
+ * otherwise); the grid must exceed twice the largest |d_x|, |d_y| involved.
+ * Call after fbc_tabulate_kernel, and again after a later tabulation; the
+ * precision's derived table is rebuilt.  Synchronous; allocates temporary
+ * device memory (about n^2 x 144 B per mode, in chunks of at most 512 MB). */
+int fbc_plan_lattice_near_field(fbc_plan* plan, const double* K, double r_cut, int32_t ref_dx, int32_t ref_dy,
+                                int32_t n_zone);
+
 /* Copy rows of the FP64 mode table to the host (synchronous):
  *   d:   HOST [nd][2] in-plane differences (each must lie in the table box);
  *   out: HOST double [nd][K][6] in the six-real layout of fbc_tabulate_kernel. */

@@ -24,6 +24,11 @@ with ``ctypes``.  Every function cites the passage of the paper it follows:
 * ``relax_alpha``      -- the residual-based relaxation parameter (Sec. 2.3.3,
                           Algorithm 2) and ``relaxed_update``, the pad update of
                           Algorithm 1 that uses it.
+* ``mode_space_update``-- the update evaluated mode by mode with a given mode
+                          table (for tables that are not the continuum one).
+* ``harmonic``         -- the harmonic model: the incompatibility force
+                          (Sec. 2.3.2, Eq. 21) and the lattice Green function
+                          of a block stencil (App.).
 
 Parity is pinned by the ``-m "not gpu"`` tests in ``tests/test_oracle_*.py``.
 """
@@ -360,6 +365,24 @@ def relaxed_update(xy_i, xy_p, L: int, c: float, material: dict, f_new, f_old, u
     if zero_mean_u:
         u = zero_mean(u)
     return u, alpha
+
+
+def mode_space_update(xy_i, xy_p, L: int, f, gk_of_d, project: bool = True) -> np.ndarray:
+    """u = G f evaluated mode by mode with a given mode table (the convolution theorem along the
+    line, Sec. 3.2, Eqs. 37-38): F(b, k) = sum_q f(b, q) exp(-2 pi i k q / L) for k = 0 .. L/2,
+    U(a, k) = sum_b g^k(x_a - x_b) F(b, k), u = the real inverse transform of U.  ``gk_of_d(d)``
+    returns complex [L/2 + 1][3][3] for a difference d.  numpy's real FFT serves as the transform."""
+    f = np.asarray(f, dtype=np.float64)
+    if project:
+        f = project_neutral(f)
+    F = np.fft.rfft(f, axis=2)  # [R][n_i][K][3]
+    R, n_p = f.shape[0], len(xy_p)
+    U = np.zeros((R, n_p, L // 2 + 1, 3), dtype=np.complex128)
+    for a in range(n_p):
+        for b in range(len(xy_i)):
+            g = gk_of_d((int(xy_p[a][0] - xy_i[b][0]), int(xy_p[a][1] - xy_i[b][1])))
+            U[:, a] += np.einsum("kij,rkj->rki", g, F[:, b])
+    return np.fft.irfft(U, n=L, axis=2)
 
 
 def sys_info() -> dict:

@@ -725,3 +725,187 @@ cudaError_t launch_contract_fft(Plan& P, int n_rhs, cudaStream_t st) {
 }
 
 }  // namespace fbc
+
+// ---- lattice Green function near field (App.) ------------------------------------------------------
+//
+// The lattice Green function of a harmonic block stencil K_h is the inverse transform of its inverted
+// Fourier symbol; in mode k of the line-periodic lattice
+//     g^k(d) = (2 pi)^-2 int D(theta_x, theta_y, 2 pi k / L)^-1 exp(i theta . d),
+//     D(theta) = sum_n K(n) exp(-i theta . n) = sum_n K(n) cos(theta . n)   (K(-n) = K(n)).
+// On an n x n zone grid the trapezoid rule is an inverse DFT: the six fields of D^-1, placed at -theta,
+// go through the forward 2D transform above, and g^k(d) is read at d mod n.  The k = 0 mode is
+// singular at theta = 0 (left out: the zero-mean function) and is defined only up to a constant, so
+// it is shifted by the blending constant C = g_lat^0(d_ref) - g_cont^0(d_ref) at a reference
+// difference beyond the cut-off (App.); a constant in real space only touches k = 0.
+
+namespace fbc {
+namespace {
+
+// S [nk][6][n][n]: fields A11 A12 A22 A33 B13 B23 of D^-1 at theta = (-2 pi x / n, -2 pi y / n, 2 pi k / L)
+__global__ void k_zone_fill(const double* __restrict__ Kb, unsigned mask, int L, int k0, int nk, int n,
+                            double2* __restrict__ S) {
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (long long)nk * n * n) return;
+    const int x = (int)(t % n);
+    const long long rem = t / n;
+    const int y = (int)(rem % n), kk = (int)(rem / n), k = k0 + kk;
+    const double tx = -2.0 * M_PI * x / n, ty = -2.0 * M_PI * y / n, tz = 2.0 * M_PI * k / L;
+    double D[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    for (int j = 0; j < 27; j++) {
+        if (!((mask >> j) & 1u)) continue;
+        const int nx = j / 9 - 1, ny = (j / 3) % 3 - 1, nz = j % 3 - 1;
+        const double cs = cos(tx * nx + ty * ny + tz * nz);
+        for (int e = 0; e < 9; e++) D[e] = fma(Kb[9 * j + e], cs, D[e]);
+    }
+    double v[6] = {0, 0, 0, 0, 0, 0};
+    if (!(k == 0 && x == 0 && y == 0)) {
+        // symmetric 3x3 inverse by cofactors
+        const double a = D[0], b = D[1], c = D[2], e = D[4], f = D[5], i = D[8];
+        const double c00 = e * i - f * f, c01 = c * f - b * i, c02 = b * f - c * e;
+        const double det = a * c00 + b * c01 + c * c02;
+        const double r = 1.0 / det;
+        v[0] = c00 * r;                    // (1,1)
+        v[1] = c01 * r;                    // (1,2)
+        v[2] = (a * i - c * c) * r;        // (2,2)
+        v[3] = (a * e - b * b) * r;        // (3,3)
+        v[4] = c02 * r;                    // (1,3)
+        v[5] = (b * c - a * f) * r;        // (2,3)
+    }
+    double2* base = S + (size_t)kk * 6 * n * n + (size_t)y * n + x;
+    for (int fld = 0; fld < 6; fld++) base[(size_t)fld * n * n] = make_double2(v[fld], 0.0);
+}
+
+// table entries of the near differences for modes k0 .. k0 + nk - 1 from the transformed fields
+// Z [nk][n][n][6] (scaled by 1 / n^2); k = 0 minus the blending constant
+__global__ void k_zone_extract(const double* __restrict__ Z, int n, int k0, int nk, const int2* __restrict__ near_d,
+                               const int* __restrict__ near_idx, int n_near, int2 dref, int ref_idx, double* tab,
+                               size_t slice) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nk * n_near * 6) return;
+    const int f = t % 6, e = (t / 6) % n_near, kk = t / (6 * n_near), k = k0 + kk;
+    const double s = 1.0 / ((double)n * (double)n);
+    auto at = [&](int2 d) {
+        const int px = ((d.x % n) + n) % n, py = ((d.y % n) + n) % n;
+        return Z[(((size_t)kk * n + px) * n + py) * 6 + f] * s;
+    };
+    double v = at(near_d[e]);
+    if (k == 0) v -= at(dref) - tab[(size_t)ref_idx * 6 + f];
+    tab[((size_t)k * slice + near_idx[e]) * 6 + f] = v;
+}
+
+}  // namespace
+}  // namespace fbc
+
+extern "C" int fbc_plan_lattice_near_field(fbc_plan* plan, const double* K, double r_cut, int32_t ref_dx,
+                                           int32_t ref_dy, int32_t n_zone) {
+    using namespace fbc;
+    report_error(FBC_OK, "");
+    char msg[256];
+    if (!plan || !K) return report_error(FBC_ERR_INVALID_ARG, "plan or K is NULL");
+    Plan& P = plan->p;
+    if (P.host_only) return report_error(FBC_ERR_INVALID_ARG, "host-only plan");
+    if (!P.tabulated) return report_error(FBC_ERR_NOT_TABULATED, "tabulate the plan first");
+    if (P.sur || P.tables_released || !P.d_table)
+        return report_error(FBC_ERR_UNSUPPORTED, "the plan serves a surrogate; detach it first");
+    if (!(r_cut > 0.0) || !std::isfinite(r_cut)) return report_error(FBC_ERR_INVALID_ARG, "need r_cut > 0");
+    if ((double)ref_dx * ref_dx + (double)ref_dy * ref_dy <= r_cut * r_cut)
+        return report_error(FBC_ERR_INVALID_ARG, "the reference difference must lie beyond r_cut");
+    if (n_zone < 16 || n_zone > 2048) return report_error(FBC_ERR_INVALID_ARG, "n_zone must be in [16, 2048]");
+    // the stencil: finite, K(-n) = K(n), and mirror-symmetric in the line direction (the six-real layout)
+    unsigned mask = 0;
+    for (int j = 0; j < 27; j++) {
+        const int nx = j / 9 - 1, ny = (j / 3) % 3 - 1, nz = j % 3 - 1;
+        const int jm = (1 - nx) * 9 + (1 - ny) * 3 + (1 - nz), jz = (nx + 1) * 9 + (ny + 1) * 3 + (1 - nz);
+        for (int a = 0; a < 3; a++)
+            for (int b = 0; b < 3; b++) {
+                const double v = K[9 * j + 3 * a + b];
+                if (!std::isfinite(v)) return report_error(FBC_ERR_INVALID_ARG, "K has a non-finite entry");
+                if (v != 0.0) mask |= 1u << j;
+                if (std::fabs(v - K[9 * jm + 3 * a + b]) > 1e-14 * (1.0 + std::fabs(v)))
+                    return report_error(FBC_ERR_UNSUPPORTED, "the stencil must satisfy K(-n) = K(n)");
+                const double sg = ((a == 2) != (b == 2)) ? -1.0 : 1.0;  // M K M with M = diag(1, 1, -1)
+                if (std::fabs(v - sg * K[9 * jz + 3 * a + b]) > 1e-14 * (1.0 + std::fabs(v)))
+                    return report_error(FBC_ERR_UNSUPPORTED, "the stencil must be mirror-symmetric along the line");
+            }
+    }
+    // near differences from the plan's difference list; the reference must be one of its differences
+    std::vector<int2> used(P.n_used);
+    if (P.n_used && cudaMemcpy(used.data(), P.d_used, sizeof(int2) * P.n_used, cudaMemcpyDeviceToHost))
+        return report_error(FBC_ERR_CUDA, "copy of the difference list failed");
+    std::vector<int2> near_d;
+    std::vector<int> near_idx;
+    const int2 dref = make_int2(ref_dx, ref_dy);
+    bool ref_found = false;
+    int dmax = 0;
+    for (const int2& d : used) {
+        if ((double)d.x * d.x + (double)d.y * d.y <= r_cut * r_cut) {
+            near_d.push_back(d);
+            near_idx.push_back((d.y - P.box_y0) * P.Dx + (d.x - P.box_x0));
+            dmax = std::max(dmax, std::max(std::abs(d.x), std::abs(d.y)));
+        }
+        ref_found = ref_found || (d.x == dref.x && d.y == dref.y);
+    }
+    if (!ref_found) return report_error(FBC_ERR_INVALID_ARG, "the reference difference is not in the plan's table");
+    if (near_d.empty()) return FBC_OK;  // nothing within the cut-off
+    const int ref_idx = (dref.y - P.box_y0) * P.Dx + (dref.x - P.box_x0);
+    dmax = std::max(dmax, std::max(std::abs(dref.x), std::abs(dref.y)));
+    const Fft1D fz = choose_length(n_zone);
+    const int n = fz.N;
+    if (n < 2 * dmax + 2) {
+        snprintf(msg, sizeof(msg), "zone grid %d too small for differences up to %d", n, dmax);
+        return report_error(FBC_ERR_INVALID_ARG, msg);
+    }
+    std::vector<double2> tw(n);
+    for (int j = 0; j < n; j++) tw[j] = make_double2(cos(2.0 * M_PI * j / n), -sin(2.0 * M_PI * j / n));
+    const size_t per_k = (size_t)n * n * (6 * sizeof(double2) + 6 * sizeof(double));
+    const int nk = (int)std::max<size_t>(1, std::min<size_t>(P.K, ((size_t)512 << 20) / per_k));
+    double* dK = nullptr;
+    double2* dtw = nullptr;
+    double2* S = nullptr;
+    double* Z = nullptr;
+    int2* dnd = nullptr;
+    int* dni = nullptr;
+    cudaError_t e = cudaMalloc((void**)&dK, 27 * 9 * sizeof(double));
+    if (!e) e = cudaMalloc((void**)&dtw, n * sizeof(double2));
+    if (!e) e = cudaMalloc((void**)&S, (size_t)nk * 6 * n * n * sizeof(double2));
+    if (!e) e = cudaMalloc((void**)&Z, (size_t)nk * n * n * 6 * sizeof(double));
+    if (!e) e = cudaMalloc((void**)&dnd, near_d.size() * sizeof(int2));
+    if (!e) e = cudaMalloc((void**)&dni, near_idx.size() * sizeof(int));
+    if (!e) e = cudaMemcpy(dK, K, 27 * 9 * sizeof(double), cudaMemcpyHostToDevice);
+    if (!e) e = cudaMemcpy(dtw, tw.data(), n * sizeof(double2), cudaMemcpyHostToDevice);
+    if (!e) e = cudaMemcpy(dnd, near_d.data(), near_d.size() * sizeof(int2), cudaMemcpyHostToDevice);
+    if (!e) e = cudaMemcpy(dni, near_idx.data(), near_idx.size() * sizeof(int), cudaMemcpyHostToDevice);
+    const int Gr = std::max(1, std::min(n, kRowElems / n));
+    const size_t smem = (size_t)2 * padded(Gr * n) * sizeof(double2);
+    if (!e && smem > 48 * 1024) {
+        e = cudaFuncSetAttribute(k_fft_dense_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (!e) e = cudaFuncSetAttribute(k_fft_dense_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    }
+    const size_t slice = (size_t)P.Dy * P.Dx;
+    for (int k0 = 0; k0 < P.K && !e; k0 += nk) {
+        const int m = std::min(nk, P.K - k0);
+        const long long pts = (long long)m * n * n;
+        k_zone_fill<<<(unsigned)((pts + 255) / 256), 256>>>(dK, mask, P.L, k0, m, n, S);
+        if ((e = cudaGetLastError())) break;
+        k_fft_dense_rows<<<dim3((n + Gr - 1) / Gr, m * 6), kSetupThreads, smem>>>(S, n, n, fz, Gr, dtw);
+        if ((e = cudaGetLastError())) break;
+        k_fft_dense_cols<<<dim3((n + Gr - 1) / Gr, m * 6), kSetupThreads, smem>>>(S, n, n, fz, Gr, 0, dtw, Z);
+        if ((e = cudaGetLastError())) break;
+        const int work = m * (int)near_d.size() * 6;
+        k_zone_extract<<<(work + 255) / 256, 256>>>(Z, n, k0, m, dnd, dni, (int)near_d.size(), dref, ref_idx,
+                                                    P.d_table, slice);
+        e = cudaGetLastError();
+    }
+    if (!e) e = cudaDeviceSynchronize();
+    for (void* b : {(void*)dK, (void*)dtw, (void*)S, (void*)Z, (void*)dnd, (void*)dni})
+        if (b) cudaFree(b);
+    if (!e && P.precision != FBC_PREC_FP64) {
+        e = launch_derive_tables(P, P.precision, 0);
+        if (!e) e = cudaDeviceSynchronize();
+    }
+    if (e) {
+        snprintf(msg, sizeof(msg), "lattice near field: %s", cudaGetErrorString(e));
+        return report_error(e == cudaErrorMemoryAllocation ? FBC_ERR_OOM : FBC_ERR_CUDA, msg);
+    }
+    return FBC_OK;
+}

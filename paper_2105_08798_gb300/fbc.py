@@ -129,6 +129,8 @@ _SIGNATURES = {
                                           _P(ctypes.c_int32), ctypes.c_int32, _P(ctypes.c_double), _P(_vp)]),
     "fbc_incompat_force": (ctypes.c_int, [_vp, _P(_vp), _vp, ctypes.c_int32, _vp]),
     "fbc_stencil_destroy": (ctypes.c_int, [_vp]),
+    "fbc_plan_lattice_near_field": (ctypes.c_int, [_vp, _P(ctypes.c_double), ctypes.c_double, ctypes.c_int32,
+                                                   ctypes.c_int32, ctypes.c_int32]),
     "fbc_batch_create": (ctypes.c_int, [_P(_vp), ctypes.c_int32, _P(_vp), _P(_vp), _P(ctypes.c_int32), _P(_vp)]),
     "fbc_batch_apply": (ctypes.c_int, [_vp, ctypes.c_double, ctypes.c_double, ctypes.c_uint32, _vp]),
     "fbc_batch_autotune": (ctypes.c_int, [_vp, _vp, _P(ctypes.c_double)]),
@@ -299,6 +301,14 @@ def fbc_stencil_create(xy_i: np.ndarray, sources: list[np.ndarray], L: int, K: n
 def fbc_incompat_force(st: int, u_ptrs: list[int | None], f_ptr: int, n_rhs: int, stream=None):
     arr = (_vp * len(u_ptrs))(*u_ptrs)
     _check(load().fbc_incompat_force(st, arr, f_ptr, n_rhs, _stream_handle(stream)), "fbc_incompat_force")
+
+
+def fbc_plan_lattice_near_field(plan: int, K: np.ndarray, r_cut: float, d_ref, n_zone: int):
+    K = np.ascontiguousarray(K, dtype=np.float64)
+    if K.size != 27 * 9:
+        raise ValueError("K must hold 27 blocks of 3x3")
+    _check(load().fbc_plan_lattice_near_field(plan, K.ctypes.data_as(_P(ctypes.c_double)), r_cut, int(d_ref[0]),
+                                              int(d_ref[1]), n_zone), "fbc_plan_lattice_near_field")
 
 
 def fbc_stencil_destroy(st: int):
@@ -521,6 +531,11 @@ class Plan:
 
     def sync_status(self, stream=None):
         fbc_plan_sync_status(self.handle, stream)
+
+    def lattice_near_field(self, K, r_cut: float, d_ref, n_zone: int = 1024):
+        """Replace the table entries with |d| <= r_cut by the lattice Green function of the stencil K; the
+        k = 0 mode joins the continuum one at the table difference d_ref (|d_ref| > r_cut)."""
+        fbc_plan_lattice_near_field(self.handle, K, r_cut, d_ref, n_zone)
 
     def attach_surrogate(self, sur: "Surrogate | None", r_min: float = 8.0, release_tables: bool = False):
         """Serve modes k >= 1 at |d| >= r_min from ``sur`` (None detaches); see fbc_plan_attach_surrogate."""

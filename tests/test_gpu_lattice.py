@@ -1,0 +1,132 @@
+"""Lattice Green function near field (App.) through the C ABI, against the oracle.
+
+The plan's table entries with |d| <= r_cut become the lattice Green function of the synthetic
+spring model, computed on the GPU by 2D FFTs over the zone grid; the oracle computes the same
+zone sums directly.  The k = 0 mode is shifted by the blending constant at the reference
+difference.  Checked: the near entries (1e-12), the far entries unchanged (bit for bit), the
+update with the modified table against the oracle's mode-space update (1e-12), the double-float
+and in-plane FFT forms on the same plan, and the argument checks.
+"""
+
+import numpy as np
+import pytest
+
+from oracle import harmonic
+from paper_2105_08798_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+K1, K2 = 1.0, 0.4
+MAT = {"kind": "cubic", "C11": K1 + 2 * K2, "C12": K2, "C44": K2}  # the spring model's long-wave medium
+N_I, N_P, L, N_ZONE, R_CUT, R_REF = 120, 180, 16, 64, 5.0, 10.0
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm((np.asarray(a) - np.asarray(b)).ravel()) / np.linalg.norm(np.asarray(b).ravel()))
+
+
+def six(g):
+    """complex [..., 3, 3] -> the six-real layout [Re g11, Re g12, Re g22, Re g33, Im g13, Im g23]"""
+    return np.stack([g[..., 0, 0].real, g[..., 0, 1].real, g[..., 1, 1].real, g[..., 2, 2].real,
+                     g[..., 0, 2].imag, g[..., 1, 2].imag], axis=-1)
+
+
+def from_six(v):
+    a11, a12, a22, a33, b13, b23 = (v[..., i] for i in range(6))
+    g = np.zeros(v.shape[:-1] + (3, 3), dtype=np.complex128)
+    g[..., 0, 0], g[..., 0, 1], g[..., 1, 0], g[..., 1, 1], g[..., 2, 2] = a11, a12, a12, a22, a33
+    g[..., 0, 2] = g[..., 2, 0] = 1j * b13
+    g[..., 1, 2] = g[..., 2, 1] = 1j * b23
+    return g
+
+
+@pytest.fixture(scope="module")
+def fbc():
+    from paper_2105_08798_gb300 import build, fbc as binding
+
+    build.build()
+    binding.load()
+    return binding
+
+
+@pytest.fixture(scope="module")
+def geom():
+    xy_i, xy_p = inputs.ring_geometry(N_I, N_P)
+    d = np.unique((xy_p[:, None, :] - xy_i[None, :, :]).reshape(-1, 2), axis=0)
+    r = np.hypot(d[:, 0], d[:, 1])
+    near = d[r <= R_CUT]
+    far = d[r > R_CUT]
+    ref = far[np.argmin(np.abs(np.hypot(far[:, 0], far[:, 1]) - R_REF))]
+    return xy_i, xy_p, d, near, far, ref
+
+
+def test_near_entries_and_far_entries(fbc, geom):
+    xy_i, xy_p, d, near, far, ref = geom
+    K = fbc.fbc_spring_constants(K1, K2, 1.0)
+    K_modes = L // 2 + 1
+    with fbc.Plan(xy_i, xy_p, L, MAT) as plan:
+        plan.tabulate()
+        before = plan.mode_table(d)
+        plan.lattice_near_field(K, R_CUT, ref, N_ZONE)
+        after = plan.mode_table(d)
+    idx = {tuple(x): i for i, x in enumerate(d.tolist())}
+    lat = six(harmonic.lattice_mode_table(K, L, np.vstack([near, ref[None]]), list(range(K_modes)), N_ZONE))
+    C = lat[-1, 0] - before[idx[tuple(ref)], 0]  # blending constant of the k = 0 mode
+    want = lat[:-1].copy()
+    want[:, 0] -= C
+    got = np.array([after[idx[tuple(x)]] for x in near.tolist()])
+    assert len(near) > 0
+    assert np.abs(got - want).max() <= 1e-12 * np.abs(want).max()
+    fi = [idx[tuple(x)] for x in far.tolist()]
+    np.testing.assert_array_equal(after[fi], before[fi])
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("f32x2", 1e-12), ("fft64", 1e-12), ("fft32", 1e-5)])
+def test_update_with_near_field(fbc, oracle_mod, geom, prec, tol):
+    xy_i, xy_p, d, near, far, ref = geom
+    K = fbc.fbc_spring_constants(K1, K2, 1.0)
+    f = inputs.forces(1, N_I, L, seed=31)
+    with fbc.Plan(xy_i, xy_p, L, MAT, precision=prec) as plan:
+        plan.tabulate()
+        table = plan.mode_table(d)  # continuum
+        plan.lattice_near_field(K, R_CUT, ref, N_ZONE)
+        table_near = plan.mode_table(near)
+        u = torch.full((1, N_P, L, 3), float("nan"), dtype=torch.float64, device="cuda")
+        plan.apply(torch.from_numpy(f).cuda(), u)
+        torch.cuda.synchronize()
+        plan.sync_status()
+        got = u.cpu().numpy()
+    # the oracle's table: its own continuum modes, near entries from its own zone sums
+    K_modes = L // 2 + 1
+    cont = oracle_mod.mode_table(oracle_mod.kernel_table(MAT, L, 1.0, d))
+    idx = {tuple(x): i for i, x in enumerate(d.tolist())}
+    lat = harmonic.lattice_mode_table(K, L, np.vstack([near, ref[None]]), list(range(K_modes)), N_ZONE)
+    C = lat[-1, 0] - cont[idx[tuple(ref)], 0]
+    gk = {tuple(x): cont[i] for i, x in enumerate(d.tolist())}
+    for j, x in enumerate(near.tolist()):
+        g = lat[j].copy()
+        g[0] -= C
+        gk[tuple(x)] = g
+    ref_u = oracle_mod.mode_space_update(xy_i, xy_p, L, f, lambda dd: gk[dd])
+    assert rel_l2(got, ref_u) <= tol, (prec, rel_l2(got, ref_u))
+    assert np.abs(from_six(table_near)).max() > 0  # the near field is in use
+
+
+def test_argument_checks(fbc, geom):
+    xy_i, xy_p, d, near, far, ref = geom
+    K = fbc.fbc_spring_constants(K1, K2, 1.0)
+    with fbc.Plan(xy_i, xy_p, L, MAT) as plan:
+        with pytest.raises(fbc.FBCError):
+            plan.lattice_near_field(K, R_CUT, ref, N_ZONE)  # not tabulated
+        plan.tabulate()
+        with pytest.raises(fbc.FBCError):
+            plan.lattice_near_field(K, R_CUT, near[0], N_ZONE)  # reference inside the cut-off
+        bad = K.copy()
+        bad[1, 0, 2] += 0.1  # breaks K(-n) = K(n) and the mirror symmetry
+        with pytest.raises(fbc.FBCError):
+            plan.lattice_near_field(bad, R_CUT, ref, N_ZONE)
+        with pytest.raises(fbc.FBCError):
+            plan.lattice_near_field(K, R_CUT, ref, 16)  # zone grid too small for the reference
+        with pytest.raises(fbc.FBCError):
+            plan.lattice_near_field(K, R_CUT, (1000, 0), N_ZONE)  # not a difference of the table

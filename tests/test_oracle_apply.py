@@ -131,3 +131,20 @@ def test_golden_regression(oracle_mod):
                               n=g["rich_n"], N=g["rich_N"])
     ref = np.asarray(g["u"], dtype=np.float64)
     assert np.abs(u[0] - ref).max() <= 1e-12 * np.abs(ref).max()
+
+
+def test_mode_space_update_matches_real_space_sum(oracle_mod):
+    """The mode-by-mode update with the continuum mode table (convolution theorem along the line)
+    equals the real-space sum over all pairs and repeats."""
+    from conftest import ISO
+    from paper_2105_08798_gb300 import inputs
+
+    xy_i, xy_p = inputs.ring_geometry(60, 90)
+    L = 8
+    f = inputs.forces(2, 60, L, seed=3)
+    d = np.unique((xy_p[:, None, :] - xy_i[None, :, :]).reshape(-1, 2), axis=0)
+    cont = oracle_mod.mode_table(oracle_mod.kernel_table(ISO, L, 1.0, d))
+    gk = {tuple(x): cont[i] for i, x in enumerate(d.tolist())}
+    a = oracle_mod.mode_space_update(xy_i, xy_p, L, f, lambda dd: gk[dd])
+    b = oracle_mod.pad_update(xy_i, xy_p, L, 1.0, ISO, f)
+    assert np.linalg.norm(a - b) / np.linalg.norm(b) <= 1e-13
