@@ -86,6 +86,12 @@ extern "C" {
  * 1.2e-5 for BF16X2 there).  Plans with at most 1024 interface columns are
  * not affected. */
 #define FBC_PLAN_TC_FAST_ACCUMULATE 2
+/* Interface and pad sites may coincide, as in the paper (Lambda^{i+} inside
+ * Lambda^p, self-terms d = 0).  The continuum kernel is singular at d = 0,
+ * so those table entries are zero until fbc_plan_lattice_near_field replaces
+ * them (it always covers d = 0); applies are refused until then, and again
+ * after a new tabulation. */
+#define FBC_PLAN_SELF_TERMS 4
 
 /* ---- fbc_apply flags ------------------------------------------------- */
 #define FBC_APPLY_PROJECT_NEUTRAL 1u /* remove the net interface force first */
@@ -262,7 +268,9 @@ int fbc_plan_layout(const fbc_plan* plan, int32_t* perm_i, int32_t* perm_p, int3
  * theta = 0, left out) is defined up to a constant: it is shifted by
  * C = g_lat^0(d_ref) - g^0(d_ref), d_ref = (ref_dx, ref_dy) a difference of
  * the plan's table with |d_ref| > r_cut (the paper's r', far enough that C
- * hardly depends on it).  The stencil must satisfy
+ * hardly depends on it); d_ref = (0, 0) leaves the k = 0 mode as computed
+ * (the zero-mean function; for a table that is lattice throughout).  The
+ * stencil must satisfy
  * K(-n) = K(n) and the mirror symmetry along the line (FBC_ERR_UNSUPPORTED
  * otherwise); the grid must exceed twice the largest |d_x|, |d_y| involved.
  * Call after fbc_tabulate_kernel, and again after a later tabulation; the

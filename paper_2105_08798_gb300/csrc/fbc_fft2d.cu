@@ -789,12 +789,15 @@ __global__ void k_zone_extract(const double* __restrict__ Z, int n, int k0, int 
         return Z[(((size_t)kk * n + px) * n + py) * 6 + f] * s;
     };
     double v = at(near_d[e]);
-    if (k == 0) v -= at(dref) - tab[(size_t)ref_idx * 6 + f];
+    if (k == 0 && ref_idx >= 0) v -= at(dref) - tab[(size_t)ref_idx * 6 + f];
     tab[((size_t)k * slice + near_idx[e]) * 6 + f] = v;
 }
 
 }  // namespace
 }  // namespace fbc
+
+// set in the plan's options once the near field is in the table (the same bit in fbc_plan.cu)
+static constexpr int kPlanNearFieldSet = 1 << 30;
 
 extern "C" int fbc_plan_lattice_near_field(fbc_plan* plan, const double* K, double r_cut, int32_t ref_dx,
                                            int32_t ref_dy, int32_t n_zone) {
@@ -808,7 +811,8 @@ extern "C" int fbc_plan_lattice_near_field(fbc_plan* plan, const double* K, doub
     if (P.sur || P.tables_released || !P.d_table)
         return report_error(FBC_ERR_UNSUPPORTED, "the plan serves a surrogate; detach it first");
     if (!(r_cut > 0.0) || !std::isfinite(r_cut)) return report_error(FBC_ERR_INVALID_ARG, "need r_cut > 0");
-    if ((double)ref_dx * ref_dx + (double)ref_dy * ref_dy <= r_cut * r_cut)
+    const bool blend = ref_dx != 0 || ref_dy != 0;
+    if (blend && (double)ref_dx * ref_dx + (double)ref_dy * ref_dy <= r_cut * r_cut)
         return report_error(FBC_ERR_INVALID_ARG, "the reference difference must lie beyond r_cut");
     if (n_zone < 16 || n_zone > 2048) return report_error(FBC_ERR_INVALID_ARG, "n_zone must be in [16, 2048]");
     // the stencil: finite, K(-n) = K(n), and mirror-symmetric in the line direction (the six-real layout)
@@ -845,9 +849,13 @@ extern "C" int fbc_plan_lattice_near_field(fbc_plan* plan, const double* K, doub
         }
         ref_found = ref_found || (d.x == dref.x && d.y == dref.y);
     }
-    if (!ref_found) return report_error(FBC_ERR_INVALID_ARG, "the reference difference is not in the plan's table");
-    if (near_d.empty()) return FBC_OK;  // nothing within the cut-off
-    const int ref_idx = (dref.y - P.box_y0) * P.Dx + (dref.x - P.box_x0);
+    if (blend && !ref_found)
+        return report_error(FBC_ERR_INVALID_ARG, "the reference difference is not in the plan's table");
+    if (near_d.empty()) {  // nothing within the cut-off
+        P.opt.flags |= kPlanNearFieldSet;
+        return FBC_OK;
+    }
+    const int ref_idx = blend ? (dref.y - P.box_y0) * P.Dx + (dref.x - P.box_x0) : -1;
     dmax = std::max(dmax, std::max(std::abs(dref.x), std::abs(dref.y)));
     const Fft1D fz = choose_length(n_zone);
     const int n = fz.N;
@@ -907,5 +915,6 @@ extern "C" int fbc_plan_lattice_near_field(fbc_plan* plan, const double* K, doub
         snprintf(msg, sizeof(msg), "lattice near field: %s", cudaGetErrorString(e));
         return report_error(e == cudaErrorMemoryAllocation ? FBC_ERR_OOM : FBC_ERR_CUDA, msg);
     }
+    P.opt.flags |= kPlanNearFieldSet;
     return FBC_OK;
 }

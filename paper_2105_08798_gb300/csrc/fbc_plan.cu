@@ -38,6 +38,9 @@ int cuda_fail(cudaError_t e, const char* what) {
 
 bool is_pow2(int x) { return x > 0 && (x & (x - 1)) == 0; }
 
+// set in the plan's options by fbc_plan_lattice_near_field (the same bit in fbc_fft2d.cu)
+constexpr int kPlanNearFieldSet = 1 << 30;
+
 // Recursive bisection along the longer side of the bounding box.  The left
 // part always holds a multiple of T sites, so every tile is full except the
 // last one.  Ties are broken by the other coordinate and then the index, so
@@ -318,7 +321,7 @@ int fbc_plan_create(const fbc_geometry* geom, const fbc_material* mat, const fbc
     if (opt.max_rhs < 1 || opt.max_rhs > 4096) return fail(FBC_ERR_INVALID_ARG, "max_rhs must be in [1, 4096]");
     if (opt.precision < FBC_PREC_FP64 || opt.precision > FBC_PREC_FFT32)
         return fail(FBC_ERR_INVALID_ARG, "unknown precision %d", opt.precision);
-    if (opt.flags & ~(FBC_PLAN_HOST_ONLY | FBC_PLAN_TC_FAST_ACCUMULATE))
+    if (opt.flags & ~(FBC_PLAN_HOST_ONLY | FBC_PLAN_TC_FAST_ACCUMULATE | FBC_PLAN_SELF_TERMS))
         return fail(FBC_ERR_INVALID_ARG, "unknown options.flags bits 0x%x", opt.flags);
     const int32_t coord_lim = 1 << 20;
     for (int t = 0; t < 2 * n_i; t++)
@@ -392,7 +395,8 @@ int fbc_plan_create(const fbc_geometry* geom, const fbc_material* mat, const fbc
         }
     }
     int zx = -P.box_x0, zy = -P.box_y0;
-    if (zx >= 0 && zx < P.Dx && zy >= 0 && zy < P.Dy && used[(size_t)zy * P.Dx + zx]) {
+    if (!(opt.flags & FBC_PLAN_SELF_TERMS) && zx >= 0 && zx < P.Dx && zy >= 0 && zy < P.Dy &&
+        used[(size_t)zy * P.Dx + zx]) {
         delete plan;
         return fail(FBC_ERR_INVALID_ARG, "an interface site coincides with a pad site (d = 0 is singular)");
     }
@@ -509,6 +513,7 @@ int fbc_tabulate_kernel(fbc_plan* plan, void* stream) {
     cudaError_t e = fbc::launch_tabulate(P, st);
     if (e != cudaSuccess) return cuda_fail(e, "tabulate");
     P.tabulated = true;
+    P.opt.flags &= ~kPlanNearFieldSet;  // a new continuum table: the near field must be set again
     if (fbc::is_fft_precision(P.precision)) {
         if (int s = fbc::fft_prepare(P, P.precision)) return s;
     }
@@ -546,6 +551,8 @@ int fbc_plan_set_precision(fbc_plan* plan, int32_t precision) {
 static int apply_checks(fbc::Plan& P, const double* f, const double* u, int32_t n_rhs, uint32_t flags) {
     if (P.host_only) return fail(FBC_ERR_INVALID_ARG, "host-only plan");
     if (!P.tabulated) return fail(FBC_ERR_NOT_TABULATED, "fbc_apply before fbc_tabulate_kernel");
+    if ((P.opt.flags & FBC_PLAN_SELF_TERMS) && !(P.opt.flags & kPlanNearFieldSet))
+        return fail(FBC_ERR_INVALID_ARG, "a plan with self-terms needs the lattice near field before an apply");
     if (P.tables_released && !P.sur) return fail(FBC_ERR_INVALID_ARG, "tables released without a surrogate");
     if (!f || !u) return fail(FBC_ERR_INVALID_ARG, "f or u is NULL");
     if (n_rhs < 1 || n_rhs > P.opt.max_rhs)

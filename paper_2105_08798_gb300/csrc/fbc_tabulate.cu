@@ -114,6 +114,11 @@ __global__ void k_periodic(const int2* __restrict__ used, int n_used, double* __
     const int di = (int)(tid / (Lh + 1));
     const int s = (int)(tid % (Lh + 1));
     const int2 d = used[di];
+    if (d.x == 0 && d.y == 0) {  // self-terms (FBC_PLAN_SELF_TERMS): filled by the lattice near field
+        double* o0 = gs + ((size_t)di * (Lh + 1) + s) * 6;
+        for (int t = 0; t < 6; t++) o0[t] = 0.0;
+        return;
+    }
     const double rx = (double)d.x, ry = (double)d.y;
     const double l3 = (double)c_tp.L * c_tp.c;
     const double z0 = (double)s * c_tp.c;  // centred representative: s <= L/2

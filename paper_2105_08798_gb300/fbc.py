@@ -45,6 +45,7 @@ PRECISIONS = {"fp64": FBC_PREC_FP64, "fp32": FBC_PREC_FP32, "f32x2": FBC_PREC_F3
               "fft32": FBC_PREC_FFT32}
 
 FBC_PLAN_HOST_ONLY = 1
+FBC_PLAN_SELF_TERMS = 4
 FBC_PLAN_TC_FAST_ACCUMULATE = 2
 
 FBC_APPLY_PROJECT_NEUTRAL = 1
@@ -432,7 +433,7 @@ class Plan:
 
     def __init__(self, xy_i, xy_p, L: int, material: dict, c: float = 1.0, precision: str | int = "fp64",
                  rich_n: int | None = None, rich_N: int | None = None, quad: int | None = None, max_rhs: int = 1,
-                 host_only: bool = False, tc_fast_accumulate: bool = False):
+                 host_only: bool = False, tc_fast_accumulate: bool = False, self_terms: bool = False):
         self._h = None
         self._sur = None
         xy_i = np.ascontiguousarray(xy_i, dtype=np.int32)
@@ -448,7 +449,8 @@ class Plan:
         if quad is not None:
             o.quad = quad
         o.max_rhs = int(max_rhs)
-        o.flags = (FBC_PLAN_HOST_ONLY if host_only else 0) | (FBC_PLAN_TC_FAST_ACCUMULATE if tc_fast_accumulate else 0)
+        o.flags = ((FBC_PLAN_HOST_ONLY if host_only else 0) | (FBC_PLAN_TC_FAST_ACCUMULATE if tc_fast_accumulate else 0)
+                   | (FBC_PLAN_SELF_TERMS if self_terms else 0))
         self._h = fbc_plan_create(g, material_struct(material), o)
         self.n_i, self.n_p, self.L, self.K = len(xy_i), len(xy_p), int(L), int(L) // 2 + 1
         self.max_rhs = int(max_rhs)
