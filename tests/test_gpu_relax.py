@@ -118,3 +118,57 @@ def test_rejects_bad_arguments(fbc, case):
             plan.apply_relaxed(fn, fn, u, a)  # f_old is f_new
         with pytest.raises(fbc.FBCError):
             plan.apply_relaxed(fn, None, u, a, du_max=-1.0)
+
+
+def test_iteration_captured_in_a_cuda_graph(fbc, case):
+    """alpha lives on the device, so an iteration (incompatibility force, then the relaxed update)
+    needs no host round trip: captured once in a CUDA graph and replayed, it gives the same bits as
+    the same calls made directly."""
+    from paper_2105_08798_gb300 import inputs as inp
+
+    xy_i, xy_p, f_old, f_new, u0 = case
+    xy_c = inp.core_sites(N_I)
+    K = fbc.fbc_spring_constants(1.0, 0.4, 1.0)
+    rng = np.random.default_rng(21)
+    u_c = torch.from_numpy(0.05 * rng.normal(0, 1, (R, len(xy_c), L, 3))).cuda()
+    u_i = torch.from_numpy(0.05 * rng.normal(0, 1, (R, N_I, L, 3))).cuda()
+    outs = []
+    with fbc.Plan(xy_i, xy_p, L, ISO, precision="f32x2", max_rhs=R) as plan, \
+            fbc.Stencil(xy_i, [xy_c, xy_i, xy_p], L, K) as st:
+        plan.tabulate()
+        for mode in ("direct", "graph"):
+            up = torch.from_numpy(u0.copy()).cuda()
+            fs = [torch.zeros((R, N_I, L, 3), dtype=torch.float64, device="cuda") for _ in range(2)]
+            a = torch.ones(R, dtype=torch.float64, device="cuda")
+
+            def step(i):
+                st.incompat_force([u_c, u_i, up], f=fs[i % 2])
+                plan.apply_relaxed(fs[i % 2], fs[(i + 1) % 2], up, a, du_max=0.05, zero_mean=True)
+
+            step(0)  # first iteration (no previous residual in fs[1]: zeros, alpha kept) made directly
+            torch.cuda.synchronize()
+            if mode == "direct":
+                for i in range(1, 5):
+                    step(i)
+            else:
+                graphs = []
+                for parity in (1, 2):  # the two residual buffers alternate: one graph per parity
+                    g = torch.cuda.CUDAGraph()
+                    side = torch.cuda.Stream()
+                    side.wait_stream(torch.cuda.current_stream())
+                    with torch.cuda.graph(g, stream=side):
+                        step(parity)
+                    graphs.append(g)
+                # capture does not run the work: replay in order 1, 2, 3, 4
+                up.copy_(torch.from_numpy(u0.copy()).cuda())
+                a.fill_(1.0)
+                for t in fs:
+                    t.zero_()
+                step(0)
+                for i in range(1, 5):
+                    graphs[(i - 1) % 2].replay()
+            torch.cuda.synchronize()
+            plan.sync_status()
+            outs.append((up.cpu().numpy(), a.cpu().numpy()))
+    np.testing.assert_array_equal(outs[0][0], outs[1][0])
+    np.testing.assert_array_equal(outs[0][1], outs[1][1])
