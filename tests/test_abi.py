@@ -60,6 +60,7 @@ int main(void) {
   P(fbc_material, mu) P(fbc_material, C44) P(fbc_material, Q)
   P(fbc_options, max_rhs) P(fbc_options, flags)
   P(fbc_plan_info, pair_modes_per_rhs) P(fbc_plan_info, table_bytes) P(fbc_plan_info, workspace_bytes)
+  P(fbc_plan_info, fft_mx) P(fbc_plan_info, fft_chunk_items) P(fbc_plan_info, reserved2)
   return 0;
 }
 ''')
@@ -118,3 +119,27 @@ def test_null_arguments(lib):
     assert lib.fbc_apply(None, None, None, 1, 1.0, 0.0, 0, None) == fbc.FBC_ERR_INVALID_ARG
     assert lib.fbc_tabulate_kernel(None, None) == fbc.FBC_ERR_INVALID_ARG
     lib.fbc_destroy(None)
+
+
+def test_new_entry_points_validate_before_device_work(lib):
+    """Relaxed apply, stencil and lattice near field: NULL handles, host-only plans and bad scalars are
+    rejected with a status and a message, without any device work (no GPU here)."""
+    assert lib.fbc_apply_relaxed(None, None, None, None, 1, None, 0.0, 0, None) == fbc.FBC_ERR_INVALID_ARG
+    assert lib.fbc_incompat_force(None, None, None, 1, None) == fbc.FBC_ERR_INVALID_ARG
+    assert lib.fbc_stencil_destroy(None) == fbc.FBC_OK
+    K = (ctypes.c_double * 243)()
+    assert lib.fbc_spring_constants(1.0, 0.4, 0.0, K) == fbc.FBC_ERR_INVALID_ARG  # c must be > 0
+    assert lib.fbc_spring_constants(1.0, 0.4, 1.0, None) == fbc.FBC_ERR_INVALID_ARG
+    assert lib.fbc_plan_lattice_near_field(None, K, 5.0, 12, 0, 64) == fbc.FBC_ERR_INVALID_ARG
+    xy_i, xy_p = inputs.ring_geometry(20, 30)
+    with fbc.Plan(xy_i, xy_p, 8, {"kind": "isotropic", "mu": 1.0, "nu": 0.3}, host_only=True) as plan:
+        with pytest.raises(fbc.FBCError, match="host-only"):
+            fbc.fbc_apply_relaxed(plan.handle, 1, None, 2, 1, 3, 0.0, 0, None)
+        with pytest.raises(fbc.FBCError, match="host-only"):
+            fbc.fbc_plan_lattice_near_field(plan.handle, fbc.fbc_spring_constants(1.0, 0.4, 1.0), 5.0, (12, 0), 64)
+    # interface sites inside the pad: accepted only with the self-terms flag
+    pad = np.concatenate([xy_i[:5], xy_p])
+    with fbc.Plan(xy_i, pad, 8, {"kind": "isotropic", "mu": 1.0, "nu": 0.3}, host_only=True, self_terms=True):
+        pass
+    with pytest.raises(fbc.FBCError, match="coincides"):
+        fbc.Plan(xy_i, pad, 8, {"kind": "isotropic", "mu": 1.0, "nu": 0.3}, host_only=True)
