@@ -14,7 +14,8 @@ written from the definitions:
   any block table.
 * ``spring_bonds`` -- the model's bonds: central springs k1 to the neighbours
   with |n|_1 = 1 and k2 to those with |n|_1 = 2 on the lattice with in-plane
-  spacing 1 and plane spacing c.
+  spacing 1 and plane spacing c; ``spring_blocks`` -- the same as a block
+  stencil.
 * ``symbol`` and ``lattice_mode_table`` -- the lattice Green function of the
   stencil (App., the inverse transform of the inverted Fourier symbol), in
   the modes of the line-periodic lattice, by the zone grid's trapezoid rule.
@@ -35,6 +36,17 @@ def spring_bonds(k1: float, k2: float, c: float):
         if l1 in (1, 2):
             out.append((n, k1 if l1 == 1 else k2, np.array([n[0], n[1], c * n[2]], dtype=np.float64)))
     return out
+
+
+def spring_blocks(k1: float, k2: float, c: float) -> np.ndarray:
+    """The spring model as a block stencil K [27][3][3] (offset index (n_x+1)*9 + (n_y+1)*3 + (n_z+1)):
+    K(n) = -k v v^T / |v|^2 for each bond, K(0) = minus the sum of the others."""
+    K = np.zeros((27, 3, 3))
+    for n, k, v in spring_bonds(k1, k2, c):
+        blk = k * np.outer(v, v) / float(v @ v)
+        K[(n[0] + 1) * 9 + (n[1] + 1) * 3 + (n[2] + 1)] -= blk
+        K[13] += blk
+    return K
 
 
 def _site_lookup(sources):

@@ -29,14 +29,14 @@ def fbc():
 
 @pytest.mark.parametrize("prec", ["fp64", "fft64"])
 def test_two_step_convergence_on_device(fbc, oracle_mod, prec):
-    K = fbc.fbc_spring_constants(1.0, 0.4, 1.0)
-    Kb = np.asarray(K).reshape(27, 3, 3)
+    K = fbc.fbc_spring_constants(1.0, 0.4, 1.0)  # the device's blocks
+    Kb = harmonic.spring_blocks(1.0, 0.4, 1.0)  # the oracle's blocks: exact solution and atomistic model
     atoms, ip, pad = fbc_geometry()
     x0 = (0, 0)
     fext = np.zeros((len(atoms), L, 3))
     fext[atoms.index(x0), :, 0] = np.cos(2 * np.pi * np.arange(L) / L)
     need = sorted({(p[0] - q[0], p[1] - q[1]) for p in atoms + pad for q in [x0]})
-    g = harmonic.lattice_mode_table(K, L, need, list(range(L // 2 + 1)), N_ZONE)
+    g = harmonic.lattice_mode_table(Kb, L, need, list(range(L // 2 + 1)), N_ZONE)
     gk = {d: g[i] for i, d in enumerate(need)}
     exact = oracle_mod.mode_space_update(np.array([x0]), np.array(atoms + pad), L,
                                          fext[None, [atoms.index(x0)]], lambda d: gk[d], project=False)[0]

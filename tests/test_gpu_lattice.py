@@ -71,7 +71,8 @@ def test_near_entries_and_far_entries(fbc, geom):
         plan.lattice_near_field(K, R_CUT, ref, N_ZONE)
         after = plan.mode_table(d)
     idx = {tuple(x): i for i, x in enumerate(d.tolist())}
-    lat = six(harmonic.lattice_mode_table(K, L, np.vstack([near, ref[None]]), list(range(K_modes)), N_ZONE))
+    Ko = harmonic.spring_blocks(K1, K2, 1.0)  # the oracle's own blocks
+    lat = six(harmonic.lattice_mode_table(Ko, L, np.vstack([near, ref[None]]), list(range(K_modes)), N_ZONE))
     C = lat[-1, 0] - before[idx[tuple(ref)], 0]  # blending constant of the k = 0 mode
     want = lat[:-1].copy()
     want[:, 0] -= C
@@ -101,7 +102,8 @@ def test_update_with_near_field(fbc, oracle_mod, geom, prec, tol):
     K_modes = L // 2 + 1
     cont = oracle_mod.mode_table(oracle_mod.kernel_table(MAT, L, 1.0, d))
     idx = {tuple(x): i for i, x in enumerate(d.tolist())}
-    lat = harmonic.lattice_mode_table(K, L, np.vstack([near, ref[None]]), list(range(K_modes)), N_ZONE)
+    Ko = harmonic.spring_blocks(K1, K2, 1.0)  # the oracle's own blocks
+    lat = harmonic.lattice_mode_table(Ko, L, np.vstack([near, ref[None]]), list(range(K_modes)), N_ZONE)
     C = lat[-1, 0] - cont[idx[tuple(ref)], 0]
     gk = {tuple(x): cont[i] for i, x in enumerate(d.tolist())}
     for j, x in enumerate(near.tolist()):

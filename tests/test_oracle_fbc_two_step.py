@@ -56,11 +56,7 @@ def atomistic_solve(Kb, atoms, pad, up, fext):
 
 
 def test_two_step_convergence(oracle_mod):
-    from paper_2105_08798_gb300 import build, fbc
-
-    build.build()
-    fbc.load()
-    K = fbc.fbc_spring_constants(1.0, 0.4, 1.0)
+    K = harmonic.spring_blocks(1.0, 0.4, 1.0)
     Kb = np.asarray(K).reshape(27, 3, 3)
     atoms, ip, pad = fbc_geometry()
     x0 = (0, 0)

@@ -111,6 +111,11 @@ def test_library_spring_blocks_match_bond_form(geom):
     a = harmonic.stencil_apply(geom[1], src, L, K)
     b = harmonic.spring_incompat_force(geom[1], src, L, c, k1, k2)
     assert np.abs(a - b).max() <= 1e-13 * np.abs(b).max()
+    # the oracle's own blocks: the same operator as the bond form, and the same numbers as the library's
+    Ko = harmonic.spring_blocks(k1, k2, c)
+    a2 = harmonic.stencil_apply(geom[1], src, L, Ko)
+    assert np.abs(a2 - b).max() <= 1e-13 * np.abs(b).max()
+    np.testing.assert_allclose(K, Ko, rtol=0, atol=1e-15)
 
 
 def test_stencil_builder_rejects_bad_geometry(geom):

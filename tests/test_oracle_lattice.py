@@ -21,11 +21,7 @@ K1, K2, L = 1.0, 0.4, 64
 
 @pytest.fixture(scope="module")
 def K():
-    from paper_2105_08798_gb300 import build, fbc
-
-    build.build()
-    fbc.load()
-    return fbc.fbc_spring_constants(K1, K2, 1.0)
+    return harmonic.spring_blocks(K1, K2, 1.0)
 
 
 @pytest.mark.parametrize("k", [0, 1, 5])
