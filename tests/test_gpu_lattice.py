@@ -61,6 +61,17 @@ def geom():
     return xy_i, xy_p, d, near, far, ref
 
 
+def check_near_entries(got, lat, before_ref_k0):
+    """got, lat: [n_near + 1 (the reference last for lat)][K][6].  Modes k >= 1 equal the oracle's zone
+    sums; the k = 0 entries differ from them by one common constant, C = lat(d_ref) - table(d_ref)."""
+    lat_near = lat[:-1]
+    scale = np.abs(lat_near).max()
+    assert np.abs(got[:, 1:] - lat_near[:, 1:]).max() <= 1e-12 * scale
+    shift = lat_near[:, 0] - got[:, 0]  # [n_near][6]
+    assert np.abs(shift - shift[0]).max() <= 1e-12 * scale  # one constant for every near difference
+    assert np.abs(shift[0] - (lat[-1, 0] - before_ref_k0)).max() <= 1e-12 * scale
+
+
 def test_near_entries_and_far_entries(fbc, geom):
     xy_i, xy_p, d, near, far, ref = geom
     K = fbc.fbc_spring_constants(K1, K2, 1.0)
@@ -73,12 +84,9 @@ def test_near_entries_and_far_entries(fbc, geom):
     idx = {tuple(x): i for i, x in enumerate(d.tolist())}
     Ko = harmonic.spring_blocks(K1, K2, 1.0)  # the oracle's own blocks
     lat = six(harmonic.lattice_mode_table(Ko, L, np.vstack([near, ref[None]]), list(range(K_modes)), N_ZONE))
-    C = lat[-1, 0] - before[idx[tuple(ref)], 0]  # blending constant of the k = 0 mode
-    want = lat[:-1].copy()
-    want[:, 0] -= C
     got = np.array([after[idx[tuple(x)]] for x in near.tolist()])
     assert len(near) > 0
-    assert np.abs(got - want).max() <= 1e-12 * np.abs(want).max()
+    check_near_entries(got, lat, before[idx[tuple(ref)], 0])
     fi = [idx[tuple(x)] for x in far.tolist()]
     np.testing.assert_array_equal(after[fi], before[fi])
 
