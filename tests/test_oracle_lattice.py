@@ -66,3 +66,18 @@ def test_far_field_is_the_continuum_green_function(K, oracle_mod):
         # k = 0: both are defined up to a constant; compare differences to the farthest point
         a, b = gl[i, 0] - gl[3, 0], gc[i, 0] - gc[3, 0]
         assert np.linalg.norm(a - b) / np.linalg.norm(b) < 1e-2, ds[i]
+
+
+def test_golden_regression():
+    """The stored values written by tests/golden/make_golden_lattice.py (oracle only)."""
+    import json
+    import os
+
+    path = os.path.join(os.path.dirname(__file__), "golden", "spring_lattice_modes_L16_n64.json")
+    gold = json.load(open(path))
+    K = harmonic.spring_blocks(gold["k1"], gold["k2"], gold["c"])
+    g = harmonic.lattice_mode_table(K, gold["L"], gold["d"], gold["k"], gold["n_zone"])
+    six = np.stack([g[..., 0, 0].real, g[..., 0, 1].real, g[..., 1, 1].real, g[..., 2, 2].real,
+                    g[..., 0, 2].imag, g[..., 1, 2].imag], axis=-1)
+    ref = np.array(gold["g"])
+    assert np.abs(six - ref).max() <= 1e-13 * np.abs(ref).max()
