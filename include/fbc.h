@@ -164,7 +164,12 @@ typedef struct fbc_plan_info {
 /* Defaults listed in fbc_options. */
 void fbc_default_options(fbc_options* opt);
 
-/* Validate the geometry and medium, sort the columns into spatially compact
+/* The setup of the pad update, done once and reused by every later apply
+ * (Sec. 3.2: the Green matrix is built once per geometry and only applied
+ * afterwards).  The geometry is the line-periodic slab of Sec. 2.1 (columns
+ * of L atoms at in-plane lattice sites, the interface set Lambda^{i+} and the
+ * pad Lambda^p), the medium that of the Green function of Sec. 3.1, Eq. 33.
+ * Validate the geometry and medium, sort the columns into spatially compact
  * tiles and allocate every device buffer the plan will need (tables and the
  * workspace for max_rhs right-hand sides).  Rejects: non-power-of-two L,
  * coincident interface/pad sites (d = 0, where the continuum kernel is
@@ -230,6 +235,16 @@ int fbc_apply_host(fbc_plan* plan, const double* f_host, double* u_host, int32_t
  * in-plane FFT forms the grid and its transformed kernel (K x Mx x My x 6
  * reals in FP64, plus an FP32 copy for FBC_PREC_FFT32).  Synchronous. */
 int fbc_plan_set_precision(fbc_plan* plan, int32_t precision);
+
+/* Bound of the pipeline waits of the tensor-core contraction (the hand-offs
+ * of shared-memory stages between its warps), in polls of the barrier:
+ * 1 <= polls <= 2^24, or 0 for the default 2^24.  A wait that runs out stops
+ * the contraction's work; the next fbc_plan_sync_status then returns
+ * FBC_ERR_TIMEOUT (the results of that apply are not valid).  The waits for
+ * the kernel's own copies and products in flight, before it frees its tensor
+ * memory and exits, always keep the default bound.  Meant for tests of the
+ * timeout path; host only, takes effect at the next apply. */
+int fbc_plan_set_wait_limit(fbc_plan* plan, int32_t polls);
 
 /* Stage timing for profiling.  While enabled, every fbc_apply records CUDA
  * events on its stream before the forward transform, after it, after the
@@ -346,8 +361,8 @@ void fbc_batch_destroy(fbc_batch* batch);
 /* Allocation-free zero-mean step.  The paper has no counterpart of this
  * call: it exists for callers that cannot call cudaMalloc where they need
  * it -- an atomistic engine that owns the whole device through its own
- * memory pool, code running while a CUDA graph is captured, or a relaxation
- * loop that must not take the allocator's device-wide lock.
+ * memory pool, or a relaxation loop that must not take the allocator's
+ * device-wide lock.
  *   u: DEVICE double [n_rhs][n_p][L][3]; for every right-hand side and
  *      component the mean over all n_p * L pad atoms is subtracted in place
  *      (the same result as the FBC_APPLY_ZERO_MEAN_U step of fbc_apply).
@@ -356,7 +371,9 @@ void fbc_batch_destroy(fbc_batch* batch);
  * that every GPU loading the library keeps until the process exits; all
  * calls share it, so calls that overlap on the GPU race.  The first call on
  * a device looks up the array's device address (make it before any stream
- * capture).  Asynchronous on `stream`; allocates nothing. */
+ * capture); calls outside a capture look it up again, so after a
+ * cudaDeviceReset make one call outside a capture first.  Asynchronous on
+ * `stream`; allocates nothing. */
 int fbc_zero_mean_static(double* u, int32_t n_rhs, int32_t n_p, int32_t L, void* stream);
 
 /* ---------------------------------------------------------------------------

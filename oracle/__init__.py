@@ -14,8 +14,9 @@ with ``ctypes``.  Every function cites the passage of the paper it follows:
                           extrapolation, Sec. 3.1, Eqs. 32, 35, 36.
 * ``kernel_table``     -- the periodic kernel on the line lattice (same
                           equations, evaluated at the centred repeat offset).
-* ``project_neutral``  -- removal of the net interface force (a reading of the
-                          workload definition; see the design notes).
+* ``project_neutral``  -- removal of the net interface force: the per-component
+                          mean over all interface atoms (the reading of the
+                          workloads' "zero net force per column set").
 * ``pad_update``       -- the real-space update u = G f (Sec. 1, Eq. 1;
                           Sec. 3.2, Eqs. 37-38) with the relaxation/update
                           form u <- beta u + alpha G f (Sec. 2.3.2, Eq. 22,

@@ -26,11 +26,14 @@
 // pieces h = bf16(x), m = bf16(x - h), l = bf16(x - h - m), all rounded to
 // nearest.  The logarithmic k = 0 mode is left to the double-float kernel.
 //
-// Every wait is bounded and gives up at once when another role has given up;
-// on a timeout the CTA records the status word, stops, waits (bounded) for
-// its own bulk copies and tensor-core work, frees its tensor memory and
-// returns.  Warps that synchronise on a named barrier decide to stop only
-// right after it, so none is left waiting there.
+// Every wait is bounded.  The pipeline waits (stage hand-offs between the
+// roles) give up after the plan's wait limit, or at once when another role has
+// given up; on a timeout the CTA records the status word, stops, waits for its
+// own bulk copies and tensor-core work -- those two waits ignore the stop and
+// keep the full bound, since the CTA may not exit or free its tensor memory
+// while either is in flight -- frees its tensor memory and returns.  Warps that
+// synchronise on a named barrier decide to stop only right after it, so none
+// is left waiting there.
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -127,9 +130,9 @@ __device__ __forceinline__ uint4 pack16(const uint32_t* w) {
     return v;
 }
 
-// Bounded wait that also gives up as soon as another role has set *abort.
-__device__ __forceinline__ bool wait_or_abort(uint64_t* m, uint32_t parity, volatile int* abort) {
-    for (int it = 0; it < tc::kWaitLimit; it++) {
+// Pipeline wait: bounded by `limit` polls, and gives up as soon as another role has set *abort.
+__device__ __forceinline__ bool wait_or_abort(uint64_t* m, uint32_t parity, volatile int* abort, int limit) {
+    for (int it = 0; it < limit; it++) {
         uint32_t ok;
         asm volatile(
             "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
@@ -230,7 +233,7 @@ __global__ void k_prep_b(const double* __restrict__ fh, int K, int NIpad, int n_
 template <int PREC>
 __global__ void __launch_bounds__(kThreads, 1)
     k_contract_tc(ContractArgs A, int n_rhs, int G, int npb, const unsigned char* __restrict__ bprep, int nbuf,
-                  int gs, int* status) {
+                  int gs, int wl, int* status) {
     using C = TcCfg<PREC>;
     using Lt = TcLayout<PREC>;
     constexpr int S = C::S, KPC = Lt::KPC;
@@ -280,7 +283,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             for (; it < n_it; it++) {
                 const int s = it % S;
                 const uint32_t u = (uint32_t)(it / S);
-                if (!wait_or_abort(&empty[s], (u & 1u) ^ 1u, &s_abort)) {
+                if (!wait_or_abort(&empty[s], (u & 1u) ^ 1u, &s_abort, wl)) {
                     s_abort = 1;
                     break;
                 }
@@ -289,8 +292,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                 bulk_g2s(sB + s * Lt::B_STAGE, bprep + bchunk_index(k, g, tB, st, G, A.n_tb) * chunk_bytes,
                          chunk_bytes, &bfull[s]);
             }
-            // copies still in flight land before the CTA may exit (bounded)
-            for (int j = max(0, it - S); j < it; j++) wait_or_abort(&bfull[j % S], (uint32_t)(j / S) & 1u, &s_abort);
+            // copies still in flight land before the CTA may exit: the full bound, whatever the stop flag says
+            for (int j = max(0, it - S); j < it; j++) tc::mbar_wait(&bfull[j % S], (uint32_t)(j / S) & 1u);
         }
     } else if (warp == kMmaWarp) {
         // ---- tensor-core issue ----
@@ -306,7 +309,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const uint32_t par = (uint32_t)(it / S) & 1u;
                 uint64_t* af = C::ATM ? &afull : &full[s];
                 const uint32_t apar = C::ATM ? ((uint32_t)it & 1u) : par;
-                if (!wait_or_abort(af, apar, &s_abort) || !wait_or_abort(&bfull[s], par, &s_abort)) {
+                if (!wait_or_abort(af, apar, &s_abort, wl) || !wait_or_abort(&bfull[s], par, &s_abort, wl)) {
                     s_abort = 1;
                     break;
                 }
@@ -445,7 +448,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             for (int st = 0; st < kStagesPerTile; st++, it++) {
                 const int s = it % S;
                 const uint32_t u = (uint32_t)(it / S);
-                if (!C::ATM && (s_abort || !wait_or_abort(&empty[s], (u & 1u) ^ 1u, &s_abort))) {
+                if (!C::ATM && (s_abort || !wait_or_abort(&empty[s], (u & 1u) ^ 1u, &s_abort, wl))) {
                     s_abort = 1;
                     continue;  // keep the barrier count of the other builders
                 }
@@ -456,7 +459,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const bool boundary = it > 0 && gpos == 0;
                 if (++gpos == gs) gpos = 0;
                 if (boundary) {
-                    if (C::ATM && (s_abort || !wait_or_abort(&aempty, ((uint32_t)it & 1u) ^ 1u, &s_abort))) {
+                    if (C::ATM && (s_abort || !wait_or_abort(&aempty, ((uint32_t)it & 1u) ^ 1u, &s_abort, wl))) {
                         s_abort = 1;
                         continue;
                     }
@@ -504,7 +507,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 }
                 if (C::ATM) {
                     // the tensor-memory A buffer is free once the previous stage's products are complete
-                    if (!drained && (s_abort || !wait_or_abort(&aempty, ((uint32_t)it & 1u) ^ 1u, &s_abort))) {
+                    if (!drained && (s_abort || !wait_or_abort(&aempty, ((uint32_t)it & 1u) ^ 1u, &s_abort, wl))) {
                         s_abort = 1;
                         continue;
                     }
@@ -562,7 +565,10 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         asm volatile("cp.async.wait_all;" ::: "memory");  // a prefetch still in flight after a stop
         // ---- epilogue: accumulators -> uh (FP64) ----
-        const bool ok = wait_or_abort(&done, 0u, &s_abort) && !s_abort;
+        // the MMA thread commits `done` on every path, also after a stop; every product it issued is
+        // complete once `done` fires, so this wait keeps the full bound whatever the stop flag says
+        const bool done_ok = tc::mbar_wait(&done, 0u);
+        const bool ok = done_ok && !s_abort;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         if (ok) drain(n_it > gs);  // the last group; earlier groups were drained in the loop
     }
@@ -615,8 +621,9 @@ cudaError_t launch_tc(const ContractArgs& A, const Plan& P, int n_rhs, cudaStrea
     // accumulation groups of kDrainTiles interface tiles (1024 columns), or one group
     const int n_it = P.n_tb * kStagesPerTile;
     const int gs = (P.opt.flags & FBC_PLAN_TC_FAST_ACCUMULATE) ? n_it : std::min(n_it, kDrainTiles * kStagesPerTile);
+    const int wl = P.wait_limit > 0 ? P.wait_limit : tc::kWaitLimit;
     k_contract_tc<PREC><<<grid, kThreads, smem, st>>>(A, n_rhs, Galloc, npb, (const unsigned char*)P.d_bprep,
-                                                      tc_nbuf<PREC>(P.H * P.W), gs, P.d_status);
+                                                      tc_nbuf<PREC>(P.H * P.W), gs, wl, P.d_status);
     return cudaGetLastError();
 }
 

@@ -796,9 +796,6 @@ __global__ void k_zone_extract(const double* __restrict__ Z, int n, int k0, int 
 }  // namespace
 }  // namespace fbc
 
-// set in the plan's options once the near field is in the table (the same bit in fbc_plan.cu)
-static constexpr int kPlanNearFieldSet = 1 << 30;
-
 extern "C" int fbc_plan_lattice_near_field(fbc_plan* plan, const double* K, double r_cut, int32_t ref_dx,
                                            int32_t ref_dy, int32_t n_zone) {
     using namespace fbc;
@@ -815,7 +812,9 @@ extern "C" int fbc_plan_lattice_near_field(fbc_plan* plan, const double* K, doub
     if (blend && (double)ref_dx * ref_dx + (double)ref_dy * ref_dy <= r_cut * r_cut)
         return report_error(FBC_ERR_INVALID_ARG, "the reference difference must lie beyond r_cut");
     if (n_zone < 16 || n_zone > 2048) return report_error(FBC_ERR_INVALID_ARG, "n_zone must be in [16, 2048]");
-    // the stencil: finite, K(-n) = K(n), and mirror-symmetric in the line direction (the six-real layout)
+    // the stencil: finite, K(-n) = K(n), symmetric blocks K(n) = K(n)^T (with K(-n) = K(n) this makes the
+    // symbol real and symmetric, which the cofactor inverse of k_zone_fill assumes: it reads one triangle),
+    // and mirror-symmetric in the line direction (the six-real layout)
     unsigned mask = 0;
     for (int j = 0; j < 27; j++) {
         const int nx = j / 9 - 1, ny = (j / 3) % 3 - 1, nz = j % 3 - 1;
@@ -827,6 +826,8 @@ extern "C" int fbc_plan_lattice_near_field(fbc_plan* plan, const double* K, doub
                 if (v != 0.0) mask |= 1u << j;
                 if (std::fabs(v - K[9 * jm + 3 * a + b]) > 1e-14 * (1.0 + std::fabs(v)))
                     return report_error(FBC_ERR_UNSUPPORTED, "the stencil must satisfy K(-n) = K(n)");
+                if (std::fabs(v - K[9 * j + 3 * b + a]) > 1e-14 * (1.0 + std::fabs(v)))
+                    return report_error(FBC_ERR_UNSUPPORTED, "the stencil blocks must be symmetric, K(n) = K(n)^T");
                 const double sg = ((a == 2) != (b == 2)) ? -1.0 : 1.0;  // M K M with M = diag(1, 1, -1)
                 if (std::fabs(v - sg * K[9 * jz + 3 * a + b]) > 1e-14 * (1.0 + std::fabs(v)))
                     return report_error(FBC_ERR_UNSUPPORTED, "the stencil must be mirror-symmetric along the line");

@@ -30,6 +30,10 @@ constexpr int kMaxRichImages = 40;  // n + N upper bound
 constexpr int kMaxQuad = 512;       // Barnett nodes on [0, pi)
 constexpr int kTileA = 128;         // pad columns per contraction tile
 constexpr int kTileB = 64;          // interface columns per contraction tile
+// Private bit of Plan::opt.flags, above every FBC_PLAN_* bit: set by
+// fbc_plan_lattice_near_field once the near field is in the table, cleared by
+// a new tabulation; applies of a plan with FBC_PLAN_SELF_TERMS need it.
+constexpr int kPlanNearFieldSet = 1 << 30;
 
 // Material constants as the tabulation kernels read them.
 struct MaterialDev {
@@ -107,6 +111,7 @@ struct Plan {
     void* d_bprep = nullptr;
     size_t bprep_bytes = 0;
     int bprep_prec = -1;
+    int wait_limit = 0;  // polls per pipeline wait of the tensor-core contraction (0: the default bound)
     bool timing = false, timed_once = false;
     size_t table_bytes = 0, workspace_bytes = 0;
     FftGrid* fft = nullptr;  // in-plane FFT form: grid, transformed kernel, workspace

@@ -38,9 +38,6 @@ int cuda_fail(cudaError_t e, const char* what) {
 
 bool is_pow2(int x) { return x > 0 && (x & (x - 1)) == 0; }
 
-// set in the plan's options by fbc_plan_lattice_near_field (the same bit in fbc_fft2d.cu)
-constexpr int kPlanNearFieldSet = 1 << 30;
-
 // Recursive bisection along the longer side of the bounding box.  The left
 // part always holds a multiple of T sites, so every tile is full except the
 // last one.  Ties are broken by the other coordinate and then the index, so
@@ -513,7 +510,7 @@ int fbc_tabulate_kernel(fbc_plan* plan, void* stream) {
     cudaError_t e = fbc::launch_tabulate(P, st);
     if (e != cudaSuccess) return cuda_fail(e, "tabulate");
     P.tabulated = true;
-    P.opt.flags &= ~kPlanNearFieldSet;  // a new continuum table: the near field must be set again
+    P.opt.flags &= ~fbc::kPlanNearFieldSet;  // a new continuum table: the near field must be set again
     if (fbc::is_fft_precision(P.precision)) {
         if (int s = fbc::fft_prepare(P, P.precision)) return s;
     }
@@ -551,7 +548,7 @@ int fbc_plan_set_precision(fbc_plan* plan, int32_t precision) {
 static int apply_checks(fbc::Plan& P, const double* f, const double* u, int32_t n_rhs, uint32_t flags) {
     if (P.host_only) return fail(FBC_ERR_INVALID_ARG, "host-only plan");
     if (!P.tabulated) return fail(FBC_ERR_NOT_TABULATED, "fbc_apply before fbc_tabulate_kernel");
-    if ((P.opt.flags & FBC_PLAN_SELF_TERMS) && !(P.opt.flags & kPlanNearFieldSet))
+    if ((P.opt.flags & FBC_PLAN_SELF_TERMS) && !(P.opt.flags & fbc::kPlanNearFieldSet))
         return fail(FBC_ERR_INVALID_ARG, "a plan with self-terms needs the lattice near field before an apply");
     if (P.tables_released && !P.sur) return fail(FBC_ERR_INVALID_ARG, "tables released without a surrogate");
     if (!f || !u) return fail(FBC_ERR_INVALID_ARG, "f or u is NULL");
@@ -673,6 +670,14 @@ int fbc_apply_host(fbc_plan* plan, const double* f_host, double* u_host, int32_t
     if (s) return s;
     FBC_CUDA(cudaMemcpyAsync(u_host, P.d_stage_u, ub, cudaMemcpyDeviceToHost, st));
     FBC_CUDA(cudaStreamSynchronize(st));
+    return FBC_OK;
+}
+
+int fbc_plan_set_wait_limit(fbc_plan* plan, int32_t polls) {
+    g_last_error.clear();
+    if (!plan) return fail(FBC_ERR_INVALID_ARG, "plan is NULL");
+    if (polls < 0 || polls > (1 << 24)) return fail(FBC_ERR_INVALID_ARG, "polls must be in [0, 2^24]");
+    plan->p.wait_limit = polls;
     return FBC_OK;
 }
 

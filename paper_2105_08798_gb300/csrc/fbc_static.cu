@@ -2,9 +2,8 @@
 //
 // Some callers of the pad update cannot call cudaMalloc at the point where
 // they want to re-centre the pad displacements: an atomistic engine that has
-// handed the whole device to its own memory pool, code that runs while a CUDA
-// graph is being captured (allocation is not a stream operation), or a tight
-// relaxation loop that must not take the allocator's device-wide lock.
+// handed the whole device to its own memory pool, or a tight relaxation loop
+// that must not take the allocator's device-wide lock.
 // fbc_zero_mean_static() gives them the zero-mean step (subtract, per
 // right-hand side and component, the mean displacement over all n_p * L pad
 // atoms) with its reduction scratch in a fixed array of this library, so the
@@ -18,9 +17,13 @@
 // without ordering) race on it.
 //
 // Host code must not pass the array's name to a kernel: on the host it is only
-// a stand-in symbol.  The device address is looked up once per device with
-// cudaGetSymbolAddress, on the first call made while that device is current;
-// make that first call before any stream capture.
+// a stand-in symbol.  Its device address comes from cudaGetSymbolAddress with
+// the device current.  The first call on a device looks it up (make that call
+// before any stream capture); later calls made outside a stream capture look
+// it up again, so that a cudaDeviceReset, after which the module is loaded
+// anew and the array may move, is followed by one such call before the next
+// capture.  A call made while its stream is being captured uses the address of
+// the last lookup on that device.
 #include <mutex>
 
 #include "fbc_internal.cuh"
@@ -98,10 +101,15 @@ int fbc_zero_mean_static(double* u, int32_t n_rhs, int32_t n_p, int32_t L, void*
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices)
         return static_fail(FBC_ERR_CUDA, "cudaGetDevice failed or device index out of range");
+    cudaStream_t st = (cudaStream_t)stream;
+    // outside a capture the address is looked up afresh (it may have moved after a device reset)
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    const bool capturing = cudaStreamIsCapturing(st, &cap) != cudaSuccess || cap != cudaStreamCaptureStatusNone;
+    if (capturing) cudaGetLastError();  // a failed query leaves no sticky error
     void* scratch = nullptr;
     {
         std::lock_guard<std::mutex> lk(g_addr_mu);
-        if (!g_addr[dev]) {
+        if (!g_addr[dev] || !capturing) {
             void* p = nullptr;
             cudaError_t e = cudaGetSymbolAddress(&p, g_zero_mean_scratch);
             if (e != cudaSuccess || !p) return static_fail(FBC_ERR_CUDA, "cudaGetSymbolAddress of the scratch failed");
@@ -110,7 +118,6 @@ int fbc_zero_mean_static(double* u, int32_t n_rhs, int32_t n_p, int32_t L, void*
         scratch = g_addr[dev];
     }
     const size_t n_atoms = (size_t)n_p * (size_t)L;
-    cudaStream_t st = (cudaStream_t)stream;
     dim3 grid(kStaticBlocks, n_rhs);
     k_static_partials<<<grid, kStaticThreads, 0, st>>>(u, (double*)scratch, n_atoms);
     if (cudaGetLastError() != cudaSuccess) return static_fail(FBC_ERR_CUDA, "launch of the partial sums failed");

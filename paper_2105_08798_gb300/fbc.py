@@ -120,6 +120,7 @@ _SIGNATURES = {
                                        _P(ctypes.c_int32)]),
     "fbc_plan_sync_status": (ctypes.c_int, [_vp, _vp]),
     "fbc_plan_set_timing": (ctypes.c_int, [_vp, ctypes.c_int32]),
+    "fbc_plan_set_wait_limit": (ctypes.c_int, [_vp, ctypes.c_int32]),
     "fbc_plan_stage_times": (ctypes.c_int, [_vp, _P(ctypes.c_float)]),
     "fbc_destroy": (None, [_vp]),
     "fbc_last_error": (ctypes.c_char_p, []),
@@ -249,6 +250,10 @@ def fbc_get_mode_table(plan: int, d: np.ndarray, K: int) -> np.ndarray:
 
 def fbc_plan_sync_status(plan: int, stream=None):
     _check(load().fbc_plan_sync_status(plan, _stream_handle(stream)), "fbc_plan_sync_status")
+
+
+def fbc_plan_set_wait_limit(plan: int, polls: int):
+    _check(load().fbc_plan_set_wait_limit(plan, int(polls)), "fbc_plan_set_wait_limit")
 
 
 def fbc_plan_set_timing(plan: int, enable: bool):
@@ -523,6 +528,10 @@ class Plan:
         n_rhs = f.shape[0]
         fbc_apply_host(self.handle, fp, up, n_rhs, alpha, beta, self.flags(project, zero_mean), stream)
         return u
+
+    def set_wait_limit(self, polls: int = 0):
+        """Bound of the tensor-core pipeline waits in polls (0: the default); for tests of the timeout path."""
+        fbc_plan_set_wait_limit(self.handle, polls)
 
     def set_timing(self, enable: bool = True):
         fbc_plan_set_timing(self.handle, enable)

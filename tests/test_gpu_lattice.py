@@ -136,6 +136,12 @@ def test_argument_checks(fbc, geom):
         bad[1, 0, 2] += 0.1  # breaks K(-n) = K(n) and the mirror symmetry
         with pytest.raises(fbc.FBCError):
             plan.lattice_near_field(bad, R_CUT, ref, N_ZONE)
+        # K(-n) = K(n) and the mirror symmetry hold, but the blocks of n = (+-1, 0, 0) are not symmetric
+        skew = K.copy()
+        skew[22, 0, 1] += 0.1
+        skew[4, 0, 1] += 0.1
+        with pytest.raises(fbc.FBCError, match="symmetric"):
+            plan.lattice_near_field(skew, R_CUT, ref, N_ZONE)
         with pytest.raises(fbc.FBCError):
             plan.lattice_near_field(K, R_CUT, ref, 16)  # zone grid too small for the reference
         with pytest.raises(fbc.FBCError):

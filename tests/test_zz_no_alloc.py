@@ -1,9 +1,9 @@
 """The allocation-free zero-mean entry point against the regular apply.
 
 Callers that cannot call cudaMalloc where they re-centre the pad
-displacements (an engine that owns the device through its own pool, code
-running during graph capture, a loop that must not take the allocator lock)
-use fbc_zero_mean_static, whose scratch is a fixed array inside the library.
+displacements (an engine that owns the device through its own pool, a loop
+that must not take the allocator lock) use fbc_zero_mean_static, whose scratch
+is a fixed array inside the library.
 This test calls it through the C ABI twice in a row, on different inputs and
 sizes, and checks each result against fbc_apply's own zero-mean step
 (FBC_APPLY_ZERO_MEAN_U) within the FP64 parity tolerance.  It lives in a file
