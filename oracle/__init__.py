@@ -25,11 +25,13 @@ with ``ctypes``.  Every function cites the passage of the paper it follows:
 * ``relax_alpha``      -- the residual-based relaxation parameter (Sec. 2.3.3,
                           Algorithm 2) and ``relaxed_update``, the pad update of
                           Algorithm 1 that uses it.
+* ``real_space_update``-- the real-space update with a given real-space kernel
+                          table (the lattice Green function's, or a blend).
 * ``mode_space_update``-- the update evaluated mode by mode with a given mode
-                          table (for tables that are not the continuum one).
+                          table (a cross-check of the real-space form).
 * ``harmonic``         -- the harmonic model: the incompatibility force
                           (Sec. 2.3.2, Eq. 21) and the lattice Green function
-                          of a block stencil (App.).
+                          of a block stencil (App.), per mode and in real space.
 
 Parity is pinned by the ``-m "not gpu"`` tests in ``tests/test_oracle_*.py``.
 """
@@ -366,6 +368,22 @@ def relaxed_update(xy_i, xy_p, L: int, c: float, material: dict, f_new, f_old, u
     if zero_mean_u:
         u = zero_mean(u)
     return u, alpha
+
+
+def real_space_update(xy_i, xy_p, L: int, f, table_of_d, project: bool = True) -> np.ndarray:
+    """u(a, p) = sum_{b, q} G~(x_a - x_b, (p - q) mod L) f(b, q) at every pad atom (Eq. 1, Sec. 3.2,
+    Eqs. 37-38) with a given real-space kernel: ``table_of_d(d_list int32 [nd][2])`` returns
+    float64 [nd][L][3][3].  The double sum is the C real-space sum of ``real_space_sum``."""
+    f = np.asarray(f, dtype=np.float64)
+    fp = np.ascontiguousarray(project_neutral(f) if project else f)
+    xy_p = np.asarray(xy_p, dtype=np.int32).reshape(-1, 2)
+    d_list, d_index = difference_index(xy_i, xy_p)
+    table = np.asarray(table_of_d(d_list), dtype=np.float64)
+    n_p = len(xy_p)
+    samp_col = np.repeat(np.arange(n_p, dtype=np.int32), L)
+    samp_p = np.tile(np.arange(L, dtype=np.int32), n_p)
+    u = real_space_sum(d_index, table, fp, samp_col, samp_p)
+    return u.reshape(f.shape[0], n_p, L, 3)
 
 
 def mode_space_update(xy_i, xy_p, L: int, f, gk_of_d, project: bool = True) -> np.ndarray:

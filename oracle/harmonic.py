@@ -143,3 +143,30 @@ def lattice_mode_table(K, L: int, d_list, ks, n: int) -> np.ndarray:
             ph = np.exp(1j * (TX * dx + TY * dy))
             out[idd, ik] = np.einsum("xy,xyij->ij", ph, Dinv) / (n * n)
     return out
+
+
+def lattice_kernel_table(K, L: int, d_list, n: int) -> np.ndarray:
+    """The lattice Green function of the stencil in real space along the line (App.), float64
+    [len(d_list)][L][3][3]:
+
+        G_lat(d, s) = (1 / L) sum_{k = 0}^{L - 1} g^k(d) exp(2 pi i k s / L),
+
+    with g^k(d) the zone sums of ``lattice_mode_table`` and g^{L - k} = conj g^k (the symbol is real
+    and even, so the Green function is real).  This is the Green function of the stencil on the
+    n x n x L periodic lattice with the uniform mode left out: applying the stencil gives the unit
+    impulse minus I / (n^2 L).  The inverse DFT is written out as a plain sum over k."""
+    d_list = np.asarray(d_list).reshape(-1, 2)
+    Kh = L // 2 + 1
+    g = lattice_mode_table(K, L, d_list, list(range(Kh)), n)  # [nd][Kh][3][3]
+    full = np.empty((len(d_list), L, 3, 3), dtype=np.complex128)
+    full[:, :Kh] = g
+    for k in range(Kh, L):
+        full[:, k] = np.conj(g[:, L - k])
+    out = np.zeros((len(d_list), L, 3, 3), dtype=np.complex128)
+    for s in range(L):
+        for k in range(L):
+            out[:, s] += full[:, k] * np.exp(2j * np.pi * k * s / L)
+    out /= L
+    if np.abs(out.imag).max() > 1e-12 * max(np.abs(out.real).max(), 1e-300):
+        raise ValueError("lattice Green function is not real: the stencil's symbol is not real and even")
+    return out.real.copy()

@@ -38,8 +38,13 @@ def test_two_step_convergence_on_device(fbc, oracle_mod, prec):
     need = sorted({(p[0] - q[0], p[1] - q[1]) for p in atoms + pad for q in [x0]})
     g = harmonic.lattice_mode_table(Kb, L, need, list(range(L // 2 + 1)), N_ZONE)
     gk = {d: g[i] for i, d in enumerate(need)}
-    exact = oracle_mod.mode_space_update(np.array([x0]), np.array(atoms + pad), L,
+    # the exact solution u* = G_lat f_ext: the real-space sum with the lattice Green function in real space
+    exact = oracle_mod.real_space_update(np.array([x0]), np.array(atoms + pad), L, fext[None, [atoms.index(x0)]],
+                                         lambda dl: harmonic.lattice_kernel_table(Kb, L, dl, N_ZONE),
+                                         project=False)[0]
+    cross = oracle_mod.mode_space_update(np.array([x0]), np.array(atoms + pad), L,
                                          fext[None, [atoms.index(x0)]], lambda d: gk[d], project=False)[0]
+    assert np.linalg.norm(cross - exact) <= 1e-13 * np.linalg.norm(exact)
     ua_star = exact[:len(atoms)]
     with fbc.Plan(np.array(ip), np.array(pad), L, MAT, precision=prec, self_terms=True) as plan, \
             fbc.Stencil(np.array(ip), [np.array(atoms), np.array(pad)], L, K) as st:

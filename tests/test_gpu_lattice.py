@@ -4,8 +4,9 @@ The plan's table entries with |d| <= r_cut become the lattice Green function of 
 spring model, computed on the GPU by 2D FFTs over the zone grid; the oracle computes the same
 zone sums directly.  The k = 0 mode is shifted by the blending constant at the reference
 difference.  Checked: the near entries (1e-12), the far entries unchanged (bit for bit), the
-update with the modified table against the oracle's mode-space update (1e-12), the double-float
-and in-plane FFT forms on the same plan, and the argument checks.
+update with the modified table against the oracle's real-space sum with the blended real-space
+kernel (1e-12; the oracle's mode-space form as a cross-check), the double-float and in-plane FFT
+forms on the same plan, and the argument checks.
 """
 
 import numpy as np
@@ -118,8 +119,28 @@ def test_update_with_near_field(fbc, oracle_mod, geom, prec, tol):
         g = lat[j].copy()
         g[0] -= C
         gk[tuple(x)] = g
-    ref_u = oracle_mod.mode_space_update(xy_i, xy_p, L, f, lambda dd: gk[dd])
-    assert rel_l2(got, ref_u) <= tol, (prec, rel_l2(got, ref_u))
+    # the real-space oracle: the continuum kernel G~(d, s) beyond r_cut, the lattice Green function in real
+    # space (plain inverse DFT of the zone sums along the line) within, shifted by the blending constant
+    # (C in the k = 0 mode is C / L at every repeat s); then the plain double sum over (b, q)
+    near_set = {tuple(x) for x in near.tolist()}
+    lat_rs = harmonic.lattice_kernel_table(Ko, L, np.vstack([near, ref[None]]), N_ZONE)
+    lat_at = {tuple(x): lat_rs[j] for j, x in enumerate(near.tolist())}
+
+    def blended(d_list):
+        cont_rs = oracle_mod.kernel_table(MAT, L, 1.0, d_list)
+        iref = [j for j, x in enumerate(d_list.tolist()) if tuple(x) == tuple(ref)]
+        C_rs = lat_rs[-1].sum(axis=0) - (cont_rs[iref[0]].sum(axis=0) if iref else
+                                         oracle_mod.kernel_table(MAT, L, 1.0, ref[None])[0].sum(axis=0))
+        for j, x in enumerate(d_list.tolist()):
+            if tuple(x) in near_set:
+                cont_rs[j] = lat_at[tuple(x)] - C_rs / L
+        return cont_rs
+
+    ref_real = oracle_mod.real_space_update(xy_i, xy_p, L, f, blended)
+    assert rel_l2(got, ref_real) <= tol, (prec, rel_l2(got, ref_real))
+    # cross-check: the oracle's mode-by-mode form of the same update
+    ref_modes = oracle_mod.mode_space_update(xy_i, xy_p, L, f, lambda dd: gk[dd])
+    assert rel_l2(ref_modes, ref_real) <= 1e-13
     assert np.abs(from_six(table_near)).max() > 0  # the near field is in use
 
 

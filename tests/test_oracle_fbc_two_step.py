@@ -1,7 +1,8 @@
 """The FBC iteration converges in two steps when the atomistic model is the harmonic one and G is its
 exact lattice Green function (Sec. 2.3.1, Remark 1).  Oracle-level pin of the harmonic pieces
-together: the incompatibility force (Eq. 21), the lattice Green function (App.) and the mode-space
-update (Sec. 3.2), with the interface columns inside the pad as in the paper (self-terms d = 0).
+together: the incompatibility force (Eq. 21), the lattice Green function (App.) in real space along
+the line and the real-space update (Sec. 3.2), with the interface columns inside the pad as in the
+paper (self-terms d = 0).
 
 Set-up: the synthetic spring model on the line-periodic lattice (L = 4); atoms |x|^2 <= 9; the
 interface Lambda^{i+} = continuum sites next to an atom, the pad = Lambda^{i+} and their continuum
@@ -64,10 +65,20 @@ def test_two_step_convergence(oracle_mod):
     fext[atoms.index(x0), :, 0] = np.cos(2 * np.pi * np.arange(L) / L)
     need = sorted({(p[0] - q[0], p[1] - q[1]) for p in pad + atoms for q in ip + [x0]})
     assert (0, 0) in need  # self-terms
+    G = harmonic.lattice_kernel_table(K, L, need, N_ZONE)  # real space along the line
+    Gd = {d: G[i] for i, d in enumerate(need)}
+
+    def table(d_list):
+        return np.stack([Gd[(int(x), int(y))] for x, y in d_list])
+
+    exact = oracle_mod.real_space_update(np.array([x0]), np.array(atoms + pad), L, fext[None, [atoms.index(x0)]],
+                                         table, project=False)[0]
+    # cross-check: the mode-by-mode form of the same sum
     g = harmonic.lattice_mode_table(K, L, need, list(range(L // 2 + 1)), N_ZONE)
     gk = {d: g[i] for i, d in enumerate(need)}
-    exact = oracle_mod.mode_space_update(np.array([x0]), np.array(atoms + pad), L,
+    cross = oracle_mod.mode_space_update(np.array([x0]), np.array(atoms + pad), L,
                                          fext[None, [atoms.index(x0)]], lambda d: gk[d], project=False)[0]
+    assert np.linalg.norm(cross - exact) <= 1e-13 * np.linalg.norm(exact)
     ua_star = exact[:len(atoms)]
     up = np.zeros((len(pad), L, 3))
     errs = []
@@ -75,7 +86,6 @@ def test_two_step_convergence(oracle_mod):
         ua = atomistic_solve(Kb, atoms, pad, up, fext)
         errs.append(np.linalg.norm(ua - ua_star) / np.linalg.norm(ua_star))
         fin = harmonic.stencil_apply(ip, [(np.array(atoms), ua[None]), (np.array(pad), up[None])], L, K)
-        up = up - oracle_mod.mode_space_update(np.array(ip), np.array(pad), L, fin, lambda d: gk[d],
-                                               project=False)[0]
+        up = up - oracle_mod.real_space_update(np.array(ip), np.array(pad), L, fin, table, project=False)[0]
     assert errs[0] > 1e-3  # the first atomistic solve, with the pad at rest, is not the solution
     assert errs[1] <= 1e-12 and errs[2] <= 1e-12, errs

@@ -41,6 +41,49 @@ def test_stencil_applied_to_green_function_is_an_impulse(K, k):
         assert np.abs(acc - want).max() <= 1e-12, (d, k)
 
 
+@pytest.mark.parametrize("L", [4, 8])
+def test_real_space_table_is_the_periodic_lattice_green_function(K, L):
+    """In real space along the line: sum_n K(n) G(d + n_xy, s + n_z) = delta(d) delta(s) I - I / (n^2 L)
+    (the unit impulse on the n x n x L periodic lattice, minus the uniform mode that is left out)."""
+    n = 32
+    Kb = np.asarray(K).reshape(27, 3, 3)
+    targets = [(0, 0), (1, 0), (2, -3)]
+    offs = [o for o in itertools.product((-1, 0, 1), repeat=3)]
+    need = sorted({(dx + nx, dy + ny) for dx, dy in targets for nx, ny, _ in offs})
+    G = harmonic.lattice_kernel_table(K, L, need, n)
+    at = {d: G[i] for i, d in enumerate(need)}
+    for d in targets:
+        for s in range(L):
+            acc = np.zeros((3, 3))
+            for j, (nx, ny, nz) in enumerate(offs):
+                acc += Kb[j] @ at[(d[0] + nx, d[1] + ny)][(s + nz) % L]
+            want = (np.eye(3) if d == (0, 0) and s == 0 else 0.0) - np.eye(3) / (n * n * L)
+            assert np.abs(acc - want).max() <= 1e-12, (d, s)
+    # symmetric blocks, even in (d, s), mirror-symmetric along the line
+    G2 = harmonic.lattice_kernel_table(K, L, [(2, -3), (-2, 3)], n)
+    M = np.diag([1.0, 1.0, -1.0])
+    for s in range(L):
+        assert np.abs(G2[0, s] - G2[0, s].T).max() <= 1e-14
+        assert np.abs(G2[1, (-s) % L] - G2[0, s]).max() <= 1e-14
+        assert np.abs(G2[0, (-s) % L] - M @ G2[0, s] @ M).max() <= 1e-14
+
+
+def test_real_space_update_matches_mode_space_update(K, oracle_mod):
+    """The two oracle forms of the update with the lattice Green function agree (the real-space double
+    sum in C against numpy's real FFTs and per-mode products)."""
+    from paper_2105_08798_gb300 import inputs
+
+    Ls = 8
+    xy_i, xy_p = inputs.ring_geometry(24, 30)
+    f = inputs.forces(2, len(xy_i), Ls, seed=5)
+    d = np.unique((xy_p[:, None, :] - xy_i[None, :, :]).reshape(-1, 2), axis=0)
+    g = harmonic.lattice_mode_table(K, Ls, d, list(range(Ls // 2 + 1)), 48)
+    gk = {tuple(x): g[i] for i, x in enumerate(d.tolist())}
+    u_modes = oracle_mod.mode_space_update(xy_i, xy_p, Ls, f, lambda dd: gk[dd])
+    u_real = oracle_mod.real_space_update(xy_i, xy_p, Ls, f, lambda dl: harmonic.lattice_kernel_table(K, Ls, dl, 48))
+    assert np.linalg.norm(u_real - u_modes) <= 1e-13 * np.linalg.norm(u_modes)
+
+
 def test_mirror_structure(K):
     ds = [(2, 1), (-2, -1), (0, 3), (4, -1)]
     g = harmonic.lattice_mode_table(K, 16, ds, [1, 3], 64)

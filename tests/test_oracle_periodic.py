@@ -65,9 +65,51 @@ def test_richardson_matches_brute_force(oracle_mod, material, l3, r):
     q = oracle_mod.periodic(material, l3, r, n=8, N=8)
     scale = np.abs(lim).max()
     assert np.abs(q - lim).max() < 5e-8 * scale
-    # the default (n, N) = (4, 6) is within the truncation stated in the design notes
-    q0 = oracle_mod.periodic(material, l3, r)
-    assert np.abs(q0 - lim).max() < 1e-5 * scale
+
+
+def _longest_difference(xy_i, xy_p):
+    """The pad-minus-interface difference of largest length (chunked over pad columns)."""
+    best, arg = -1, None
+    xi = xy_i.astype(np.int64)
+    for lo in range(0, len(xy_p), 1000):
+        D = xy_p[lo:lo + 1000, None, :].astype(np.int64) - xi[None, :, :]
+        r2 = (D * D).sum(-1)
+        j = int(np.argmax(r2))
+        if r2.flat[j] > best:
+            best, arg = int(r2.flat[j]), D.reshape(-1, 2)[j]
+    return arg
+
+
+# Truncation of Eq. 36 against the exact image sum of Eq. 32 at each workload's longest difference
+# (the largest |d| / l3, where Richardson's truncation is worst): the default order (n, N) = (4, 6)
+# and (8, 8), the most accurate order at all three sizes (larger n or N amplify the rounding of the
+# image terms more than they remove truncation).  Bounds: the measured values rounded up.
+@pytest.mark.parametrize("name,tol46,tol88", [
+    ("ring200x300_L16_iso", 3.5e-6, 3e-9),
+    ("ring4000x6000_L256_cubic", 6e-8, 1.5e-10),
+    ("ring8000x12000_L1024_rhs64_iso", 1e-8, 1e-11),
+], ids=["L16", "L256-cubic", "L1024"])
+def test_default_order_truncation_at_the_workloads(oracle_mod, name, tol46, tol88):
+    from paper_2105_08798_gb300 import inputs
+
+    w = inputs.WORKLOADS[name]
+    xy_i, xy_p = w.geometry()
+    d = _longest_difference(xy_i, xy_p)
+    l3 = w.L * w.c
+    J = 4000 if w.material["kind"] == "isotropic" else 600
+    worst46 = worst88 = 0.0
+    for s in (0.0, l3 / 4, l3 / 2):
+        r = [float(d[0]), float(d[1]), s]
+        S1 = _brute_force_periodic(oracle_mod, w.material, l3, r, J)
+        S2 = _brute_force_periodic(oracle_mod, w.material, l3, r, 2 * J)
+        lim = S2 + (S2 - S1) / 3.0
+        scale = np.abs(lim).max()
+        worst46 = max(worst46, np.abs(oracle_mod.periodic(w.material, l3, r) - lim).max() / scale)
+        worst88 = max(worst88, np.abs(oracle_mod.periodic(w.material, l3, r, n=8, N=8) - lim).max() / scale)
+    assert worst46 < tol46, worst46
+    assert worst88 < tol88, worst88
+    # the default order is not needlessly loose either: its truncation is visible at this |d| / l3
+    assert worst46 > 10 * worst88
 
 
 def test_richardson_converges_in_n(oracle_mod):
