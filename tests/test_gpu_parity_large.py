@@ -1,0 +1,93 @@
+"""Parity of the reduced-precision and in-plane FFT forms at the size they serve: 8000 interface and
+12000 pad columns, L = 1024, 64 right-hand sides, isotropic medium (the precision-sweep workload).
+
+One plan, one set of device forces; each form is applied in turn and the result is compared with the
+oracle's plain real-space double sum (Eq. 1, Sec. 3.2, Eqs. 37-38) at every repeat of four pad
+columns -- the two innermost (nearest the interface, where the high modes are largest) and the two
+outermost -- for right-hand sides 0 and 63.  Per form: the overall relative L2 error and the error
+per mode band (k = 0, 1..L/8, L/8+1..L/2).  The tensor-core forms drain their accumulators every
+1024 interface columns, so at 8000 columns this covers eight accumulation groups.  Bounds: the
+errors each form is stated to have at this size, with a margin; k = 0 is FP64-accurate in every
+form.
+"""
+
+import numpy as np
+import pytest
+
+from paper_2105_08798_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+W = inputs.WORKLOADS["ring8000x12000_L1024_rhs64_iso"]
+RHS = [0, W.n_rhs - 1]
+# form: (overall bound, k = 0 band bound, low band bound, high band bound)
+BOUNDS = {
+    "bf16x2": (3e-5, 1e-12, 4e-5, 3e-5),
+    "bf16x3": (4e-5, 1e-12, 5e-5, 3e-5),
+    "tf32": (8e-4, 1e-12, 1e-3, 8e-4),
+    "fft32": (6e-7, 1e-12, 1e-6, 3e-6),
+    "fft64": (1e-12, 1e-12, 1e-12, 1e-11),
+}
+
+
+def bands(L):
+    return {"k0": (0, 0), "low": (1, L // 8), "high": (L // 8 + 1, L // 2)}
+
+
+def band_errors(got, ref, L):
+    """got, ref: [n_cols][L][3] lines of pad columns; relative L2 error per mode band."""
+    E = np.fft.rfft(got - ref, axis=1)
+    R = np.fft.rfft(ref, axis=1)
+    return {n: float(np.linalg.norm(E[:, lo:hi + 1]) / np.linalg.norm(R[:, lo:hi + 1]))
+            for n, (lo, hi) in bands(L).items()}
+
+
+@pytest.fixture(scope="module")
+def case(oracle_mod):
+    from paper_2105_08798_gb300 import build, fbc
+
+    build.build()
+    fbc.load()
+    xy_i, xy_p = W.geometry()
+    cols = np.array([0, 1, W.n_p - 2, W.n_p - 1])  # ring order: innermost first, outermost last
+    f = W.forces()
+    # the oracle at all repeats of the sampled columns, right-hand sides 0 and 63
+    fp = oracle_mod.project_neutral(f[RHS])
+    d_list, d_index = oracle_mod.difference_index(xy_i, xy_p[cols])
+    table = oracle_mod.kernel_table(W.material, W.L, W.c, d_list)
+    samp_col = np.repeat(np.arange(len(cols)), W.L).astype(np.int32)
+    samp_p = np.tile(np.arange(W.L), len(cols)).astype(np.int32)
+    ref = oracle_mod.real_space_sum(d_index, table, fp, samp_col, samp_p).reshape(len(RHS), len(cols), W.L, 3)
+    del table
+    fd = torch.from_numpy(f).cuda()
+    del f
+    ud = torch.empty((W.n_rhs, W.n_p, W.L, 3), dtype=torch.float64, device="cuda")
+    plan = fbc.Plan(xy_i, xy_p, W.L, W.material, precision="bf16x2", max_rhs=W.n_rhs)
+    plan.tabulate()
+    yield fbc, plan, fd, ud, cols, ref
+    plan.close()
+    del fd, ud
+    torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("prec", list(BOUNDS))
+def test_form_against_oracle_at_full_size(case, prec):
+    fbc, plan, fd, ud, cols, ref = case
+    plan.set_precision(prec)
+    ud.fill_(float("nan"))
+    plan.apply(fd, ud)
+    torch.cuda.synchronize()
+    plan.sync_status()
+    got = ud[RHS][:, torch.as_tensor(cols, device="cuda")].cpu().numpy()
+    assert np.isfinite(got).all()
+    tot, b0, blo, bhi = BOUNDS[prec]
+    err = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+    assert err <= tot, (prec, err)
+    for j, r in enumerate(RHS):
+        be = band_errors(got[j], ref[j], W.L)
+        assert be["k0"] <= b0, (prec, r, be)
+        assert be["low"] <= blo, (prec, r, be)
+        assert be["high"] <= bhi, (prec, r, be)
+    # the untouched pad columns were written too (every column of every right-hand side)
+    assert torch.isfinite(ud).all().item()
