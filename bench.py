@@ -1,18 +1,22 @@
 """Benchmark of the FBC Green's-function pad update on GB300.
 
 One step = one pad update u <- G f (forward line transform with the neutral
-projection, per-mode contraction, inverse transform) of the paper-scale
-single instance: N_I = 4000 interface and N_P = 6000 pad columns on
-concentric rings, L = 256 repeats, cubic medium C11 = 1.5, C12 = 1.0,
-C44 = 0.9, one right-hand side of N(0, 1) forces (seed 1).  Metric: pad
-updates as Gpair-modes/s, one pair-mode being one (pad column, interface
-column, wavenumber k = 0..L/2, right-hand side) 3x3 block product.
+projection, per-mode contraction, inverse transform) of the largest
+single-GPU workload: N_I = 8000 interface and N_P = 12000 pad columns on
+concentric rings, L = 1024 repeats, 64 right-hand sides of N(0, 1) forces
+(seed 4), isotropic medium (mu = 1, nu = 0.3).  Metric: pad updates as
+Gpair-modes/s, one pair-mode being one (pad column, interface column,
+wavenumber k = 0..L/2, right-hand side) 3x3 block product.  The timed form
+is the dense per-mode contraction in double-float (FP64-accurate); the
+reduced-precision tensor-core forms and the in-plane FFT forms are measured
+beside it, each with its error against the FP64 oracle per mode band.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload NAME] [--precision P] [--surrogate]
 
 Prints ONE JSON line on rank 0.  ``--impl reference`` times the CPU oracle
-(the plain FP64 real-space sum) on the host cores instead; see the design
-notes for how its sample is extrapolated.
+(the plain FP64 real-space sum) on the host cores instead, on a bounded
+sample of the same workload (some repeats of one pad column per step).
 """
 
 from __future__ import annotations
@@ -33,15 +37,19 @@ sys.path.insert(0, ROOT)
 
 from paper_2105_08798_gb300 import inputs  # noqa: E402
 
-WORKLOAD = "ring4000x6000_L256_cubic"
+WORKLOAD = "ring8000x12000_L1024_rhs64_iso"
 METRIC = "FBC pad updates/sec (Gpair-modes/s) at stated error vs FP64 oracle; roofline fraction"
 UNIT = "Gpair-modes/s"
-FLOPS_PER_PAIR_MODE = 36  # two real 3x3 matrix-vector products (x and y' halves)
-X2_INSTR_PER_MAC = 12     # double-float MAC: 1 FMUL + 3 FFMA + 8 FADD (each one FP32-pipe lane slot)
+FLOPS_PER_PAIR_MODE = 36  # useful: two real 3x3 matrix-vector products (x and y' halves) = 18 MACs
+X2_INSTR_PER_MAC = 10     # double-float MAC: 1 FMUL + 3 FFMA + 6 FADD (each one FP32-pipe lane slot)
 L2_BYTES = 129 * 1024 * 1024
+VARIANT_SECONDS = 8.0     # time budget of each beside-measured form (after one untimed step)
 
 
-def peaks():
+def peaks(n_sm: int = 152):
+    """Roofline denominators: the measured copy bandwidth and bf16 rates, and the CUDA-core peaks derived
+    from unit counts (n_sm SMs read from the device, 128 FP32 FMA lanes per SM per clock) and the maximum
+    SM clock; FP64 at the GB300 nominal 1.25 TFLOP/s scaled to that clock."""
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     out = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0, "source": "fallback"}
     if os.path.exists(path):
@@ -49,12 +57,11 @@ def peaks():
             m = json.load(fh)
         out.update({k: m[k] for k in ("hbm_gbs", "bf16_tflops", "bf16_tflops_sustained", "sm_max_mhz") if k in m})
         out["source"] = "measured"
-    # plain-ALU peaks from unit counts and the maximum SM clock: 152 SMs,
-    # 128 FP32 FMA lanes per SM per clock; FP64 at the GB300 nominal 1.25 TFLOP/s
     clk = out["sm_max_mhz"] * 1e6
-    out["fp32_tflops"] = 152 * 128 * 2 * clk / 1e12
-    out["fp32_tinstr"] = 152 * 128 * clk / 1e12
-    out["fp64_tflops"] = 1.25 * clk / 2.07e9
+    out["n_sm"] = n_sm
+    out["fp32_tflops"] = n_sm * 128 * 2 * clk / 1e12
+    out["fp32_tinstr"] = n_sm * 128 * clk / 1e12
+    out["fp64_tflops"] = 1.25 * clk / 2.07e9 * n_sm / 152
     return out
 
 
@@ -143,55 +150,101 @@ def job_value(pair_modes: float, world: int, step_ms: float) -> float:
     return world * pair_modes / (step_ms * 1e-3) / 1e9
 
 
-def oracle_sample(w, xy_i, xy_p, f, n_cols: int = 1):
-    """The oracle's bounded sample: every repeat of the first n_cols pad columns
-    (all of their differences are tabulated first, as setup)."""
+def sample_columns(n_p: int, n: int = 8) -> np.ndarray:
+    """Pad columns at whose every repeat the oracle checks the result: the n/2 innermost and the n/2
+    outermost of the ring order (the innermost carry the largest high-mode terms)."""
+    h = n // 2
+    return np.array(sorted(set(range(min(h, n_p))) | set(range(max(0, n_p - (n - h)), n_p))), dtype=np.int64)
+
+
+def oracle_table(w, xy_i, xy_p_cols, rich=(4, 6)):
+    """The oracle's real-space kernel for the differences of the given pad columns (setup, untimed)."""
     import oracle
 
     oracle.build()
-    cols = np.arange(n_cols)
-    samples = np.array([[a, p] for a in cols for p in range(w.L)], dtype=np.int64)
-    fp = oracle.project_neutral(f)
-    d_list, d_index = oracle.difference_index(xy_i, xy_p[cols])
+    d_list, d_index = oracle.difference_index(xy_i, xy_p_cols)
     t0 = time.perf_counter()
-    table = oracle.kernel_table(w.material, w.L, w.c, d_list, nquad=64)
-    t_table = time.perf_counter() - t0
-    samp_col = np.repeat(np.arange(n_cols), w.L).astype(np.int32)
-    samp_p = np.tile(np.arange(w.L), n_cols).astype(np.int32)
-    return samples, fp, d_index, table, samp_col, samp_p, t_table
+    table = oracle.kernel_table(w.material, w.L, w.c, d_list, n=rich[0], N=rich[1], nquad=64)
+    return d_index, table, time.perf_counter() - t0
+
+
+def oracle_check(w, xy_i, xy_p, f, cols, rows, out):
+    """The oracle's side of the error check (into ``out``): the real-space sum at every repeat of the
+    sampled pad columns for the sampled right-hand sides, and the Richardson truncation of the kernel
+    itself -- Eq. 36 at the plan's (n, N) = (4, 6) against (8, 8), the most accurate order (pinned against
+    the brute-force image sum of Eq. 32 in the oracle tests) -- at the innermost sampled column."""
+    try:
+        import oracle
+
+        nt = max(1, oracle.n_threads() - 2)
+        fp = oracle.project_neutral(f[rows])
+        oracle.build()
+        d_list, d_index = oracle.difference_index(xy_i, xy_p[cols])
+        t0 = time.perf_counter()
+        table = oracle.kernel_table(w.material, w.L, w.c, d_list, nquad=64, nthreads=nt)
+        out["t_table"] = time.perf_counter() - t0
+        samp_col = np.repeat(np.arange(len(cols)), w.L).astype(np.int32)
+        samp_p = np.tile(np.arange(w.L), len(cols)).astype(np.int32)
+        t0 = time.perf_counter()
+        out["ref"] = oracle.real_space_sum(d_index, table, fp, samp_col, samp_p, nthreads=nt).reshape(
+            len(rows), len(cols), w.L, 3)
+        out["t_check"] = time.perf_counter() - t0
+        out["threads"] = nt
+        del table
+        d1, di1 = oracle.difference_index(xy_i, xy_p[cols[:1]])
+        sc, sp = np.zeros(w.L, np.int32), np.arange(w.L, dtype=np.int32)
+        u = {}
+        for nN in ((4, 6), (8, 8)):
+            t = oracle.kernel_table(w.material, w.L, w.c, d1, n=nN[0], N=nN[1], nquad=64, nthreads=nt)
+            u[nN] = oracle.real_space_sum(di1, t, fp[:1], sc, sp, nthreads=nt)
+        out["trunc"] = {"rich": [4, 6], "vs_rich": [8, 8],
+                        "rel_l2": float(np.linalg.norm(u[(4, 6)] - u[(8, 8)]) / np.linalg.norm(u[(8, 8)])),
+                        "sample": f"every repeat of pad column {int(cols[0])}, right-hand side {rows[0]}",
+                        "note": "the error of the tabulated kernel itself against the periodic Green function "
+                                "of Eq. 32 (rel_l2_vs_oracle compares with the oracle's own (4, 6) kernel)"}
+    except Exception as e:  # reported by the main thread
+        out["error"] = repr(e)
+
+
+def cpu_sample(w):
+    """The bounded sample both CPU measurements time: repeats 0..n-1 (n = min(L, 128)) of pad column 0,
+    right-hand side 0, as a share of the whole update's N_P L n_rhs pad atoms."""
+    n_rep = min(w.L, 128)
+    return n_rep, n_rep / float(w.n_p * w.L * w.n_rhs)
 
 
 def run_reference(args, w):
-    """CPU oracle arm: time the plain real-space sum on a bounded sample."""
+    """CPU oracle arm: time the plain real-space sum on a bounded sample of the workload."""
     import oracle
 
     rank, world, _ = dist_env()
     if rank != 0:
         return 0
     xy_i, xy_p = w.geometry()
-    f = w.forces()[:1]  # one right-hand side per sampled step; extrapolated over all of them below
-    samples, fp, d_index, table, samp_col, samp_p, t_table = oracle_sample(w, xy_i, xy_p, f)
+    # right-hand side 0 alone: the generator fills [n_rhs][n_i][L][3] in order, so this is forces()[:1]
+    fp = oracle.project_neutral(inputs.forces(1, w.n_i, w.L, w.seed))
+    n_rep, share = cpu_sample(w)
+    d_index, table, t_table = oracle_table(w, xy_i, xy_p[:1])
+    samp_col = np.zeros(n_rep, dtype=np.int32)
+    samp_p = np.arange(n_rep, dtype=np.int32)
     for _ in range(args.warmup):
         oracle.real_space_sum(d_index, table, fp, samp_col, samp_p)
     t0 = time.perf_counter()
     for _ in range(args.steps):
         oracle.real_space_sum(d_index, table, fp, samp_col, samp_p)
-    dt = (time.perf_counter() - t0) / args.steps
-    # extrapolate one sampled step (len(samples) pad atoms, one right-hand side) to the whole update
-    # (N_P L pad atoms for each of the n_rhs right-hand sides)
-    t_full = dt * (w.n_p * w.L * w.n_rhs) / len(samples)
-    value = w.pair_modes / t_full / 1e9
+    dt = (time.perf_counter() - t0) / max(1, args.steps)
+    value = w.pair_modes * share / dt / 1e9
     info = oracle.sys_info()
-    sample = (f"{len(samples)} pad atoms (all {w.L} repeats of 1 pad column, 1 right-hand side) per step, full "
-              f"real-space sum over {w.n_i} x {w.L} interface atoms; extrapolated "
-              f"x{w.n_p * w.L * w.n_rhs // len(samples)} to the whole update; "
-              f"kernel tabulation for the sample ({t_table:.1f} s) is setup and untimed")
+    sample = (f"{n_rep} pad atoms (repeats 0..{n_rep - 1} of pad column 0, right-hand side 0) per step: the full "
+              f"real-space sum over {w.n_i} x {w.L} interface atoms each, {share:.3g} of the update; kernel "
+              f"tabulation for the sample ({t_table:.1f} s) is setup and untimed")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": t_full * 1e3, "higher_is_better": True, "scaling": "weak",
+        "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": w.name, "n_i": w.n_i, "n_p": w.n_p, "L": w.L, "n_rhs": w.n_rhs,
                    "material": w.material.get("kind"), "sampled": True},
+        "extrapolated_full_update_ms": dt / share * 1e3,
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": info["cores"], "kind": "oracle", "sample": sample,
                          "cpu": info["cpu"]},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -273,6 +326,7 @@ DTYPE = {"fp64": "f64", "f32x2": "f32x2 (double-float, FP64-accurate)", "fp32": 
          "bf16x3": "bf16 3-term split x f32-accumulate (k = 0 in double-float)",
          "fft64": "f64 (in-plane FFT form)",
          "fft32": "f32 (in-plane FFT form; k = 0 in f64)"}
+FFT = ("fft64", "fft32")
 
 
 def mode_bands(L):
@@ -281,20 +335,21 @@ def mode_bands(L):
 
 
 def band_errors(got, ref, L):
-    """Relative L2 error per mode band of one pad column's line (got, ref: [L][3])."""
-    E = np.fft.rfft(got - ref, axis=0)
-    R = np.fft.rfft(ref, axis=0)
+    """Relative L2 error per mode band of pad-column lines (got, ref: [..., L, 3], the line on axis -2)."""
+    E = np.fft.rfft(got - ref, axis=-2)
+    R = np.fft.rfft(ref, axis=-2)
     out = {}
     for name, (lo, hi) in mode_bands(L).items():
-        out[name] = float(np.linalg.norm(E[lo:hi + 1]) / max(np.linalg.norm(R[lo:hi + 1]), 1e-300))
+        out[name] = float(np.linalg.norm(E[..., lo:hi + 1, :]) / max(np.linalg.norm(R[..., lo:hi + 1, :]), 1e-300))
     return out
 
 
 def launches_per_apply(precision, info):
     """Kernels one apply launches: forward, projection, contraction (k = 0 separately for the FP32 and
-    tensor forms; per streamed chunk: network, near copy, contraction), inverse."""
+    tensor forms, plus the tensor forms' split of the force operand; per streamed chunk: network, near
+    copy, contraction), inverse."""
     K = info["K"]
-    if precision in ("fft64", "fft32"):
+    if precision in FFT:
         R, Q = info["max_rhs"], max(1, info["fft_chunk_items"])
         if precision == "fft64":
             return 2 + 3 * -(-(R * K) // Q) + 1
@@ -304,9 +359,47 @@ def launches_per_apply(precision, info):
         contract = 1 + 3 * chunks
     elif precision in ("fp64", "f32x2"):
         contract = 1
+    elif precision in TENSOR:
+        contract = 3
     else:
         contract = 2
     return 2 + contract + 1
+
+
+def contraction_roofline(p, pm, contract_ms, pk):
+    """Roofline of the per-mode contraction stage: ALGORITHMIC work = 36 useful flops per pair-mode (two
+    real 3x3 matrix-vector products) over the stage's time, against the peak of the arithmetic the form
+    runs on; what the form actually issues (split products, double-float instructions) is reported beside."""
+    t = contract_ms * 1e-3
+    useful = FLOPS_PER_PAIR_MODE * pm / t / 1e12
+    if p in TENSOR:
+        base = pk.get("bf16_tflops_sustained", pk["bf16_tflops"])
+        peak = base * (1.1 / 2.25 if p == "tf32" else 1.0)
+        src = ("measured sustained bf16 dense" + (" x nominal tf32/bf16 ratio 1.1/2.25" if p == "tf32" else "")
+               + f" ({pk['source']})")
+        issued = {"what": f"{TENSOR[p]} {'tf32' if p == 'tf32' else 'bf16'} products per useful product",
+                  "tflops": TENSOR[p] * useful, "frac": TENSOR[p] * useful / peak}
+        return {"bound": "tensor", "achieved": useful, "peak": peak, "unit": "TFLOP/s", "frac": useful / peak,
+                "peak_source": src, "issued": issued}
+    if p == "fp64":
+        return {"bound": "alu", "achieved": useful, "peak": pk["fp64_tflops"], "unit": "TFLOP/s",
+                "frac": useful / pk["fp64_tflops"],
+                "peak_source": "FP64 nominal 1.25 TFLOP/s scaled to the maximum SM clock (not measured)"}
+    peak = pk["fp32_tflops"]
+    src = (f"FP32 FMA: {pk['n_sm']} SMs x 128 lanes x 2 flops x maximum SM clock (derived from unit counts, "
+           "not measured)")
+    out = {"bound": "alu", "achieved": useful, "peak": peak, "unit": "TFLOP/s", "frac": useful / peak,
+           "peak_source": src}
+    if p == "f32x2":
+        per_pm = (FLOPS_PER_PAIR_MODE // 2) * X2_INSTR_PER_MAC
+        ti = per_pm * pm / t / 1e12
+        out["issued"] = {"what": f"FP32-pipe lane instructions, {X2_INSTR_PER_MAC} per double-float MAC "
+                                 f"({per_pm} per pair-mode)", "t_instr_per_s": ti, "peak_t_instr_per_s":
+                         pk["fp32_tinstr"], "frac": ti / pk["fp32_tinstr"]}
+    elif p in FFT:
+        out["effective"] = ("the in-plane FFT form does O(M log M) work per mode, not 36 flops per pair-mode: "
+                            "achieved counts the dense form's useful flops (an effective rate)")
+    return out
 
 
 def run_ours(args, w):
@@ -323,7 +416,7 @@ def run_ours(args, w):
     torch.cuda.set_device(local)
     fbc_build.build()
     fbc.load()
-    pk = peaks()
+    pk = peaks(torch.cuda.get_device_properties(local).multi_processor_count)
     R = w.n_rhs
     xy_i, xy_p = w.geometry()
     f = rank_forces(w, rank)
@@ -336,25 +429,49 @@ def run_ours(args, w):
     ud = torch.zeros((R, w.n_p, w.L, 3), dtype=torch.float64, device="cuda")
     flush_buf = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
     pm = w.pair_modes
-    keep = 2  # pad columns whose outputs are kept for the error check (all rhs 0 and R-1 repeats)
+    cols = sample_columns(w.n_p, 8)
     rows = sorted({0, R - 1})
+    cols_d = torch.as_tensor(cols, device="cuda")
+    # the oracle's side of the error check needs only f and the geometry: it runs on the host cores (all
+    # but two, left to the launching thread) while the device is timed, and is joined before the end-to-end
+    # measurement, whose copies share the host's memory bandwidth
+    check_thread, check_out = None, {}
+    if rank == 0 and not args.skip_oracle:
+        import threading
+
+        check_thread = threading.Thread(target=oracle_check, args=(w, xy_i, xy_p, f, cols, rows, check_out),
+                                        daemon=True)
+        check_thread.start()
 
     def snap():
-        return ud[rows, :keep].cpu().numpy()
+        return ud.index_select(0, torch.as_tensor(rows, device="cuda")).index_select(1, cols_d).cpu().numpy()
 
     variants, outputs = {}, {}
 
-    def variant(prec, steps):
+    def time_capped(p1, budget_s, cap):
+        """One untimed step, then as many timed steps as fit the budget (at least 1, at most cap)."""
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        flush_buf.zero_()
+        p1.apply(fd, ud)
+        torch.cuda.synchronize()
+        one = time.perf_counter() - t1
+        n = int(max(1, min(cap, budget_s // max(one, 1e-3))))
+        return time_device_steps(torch, p1, fd, ud, n, 0, flush_buf) + (n,)
+
+    def variant(prec):
         plan.set_precision(prec)
-        vms, vstage = time_device_steps(torch, plan, fd, ud, steps, 2, flush_buf)
+        vms, vstage, n = time_capped(plan, VARIANT_SECONDS, max(2, args.steps // 2))
         outputs[prec] = snap()
         variants[prec] = {"ms_per_step": float(np.mean(vms)), "value": pm / (np.mean(vms) * 1e-3) / 1e9,
-                          "contract_ms": float(vstage[1])}
+                          "contract_ms": float(vstage[1]), "steps": n, "dtype": DTYPE[prec]}
+        if prec in FFT:
+            variants[prec]["note"] = "effective rate: pair-modes of the dense form per second"
 
     surrogate = None
     if args.surrogate:
         # ablation: the same plan with its exact tables first, then with the learned far field
-        variant(args.precision, max(2, args.steps // 2))
+        variant(args.precision)
         variants["exact_table"] = variants.pop(args.precision)
         outputs["exact_table"] = outputs.pop(args.precision)
         t1 = time.perf_counter()
@@ -386,37 +503,40 @@ def run_ours(args, w):
     value = job_value(pm, world, step_ms)
     outputs["headline"] = snap()
 
-    # the other precisions on the same plan and inputs (not after the tables were released); at the
-    # multi-rhs sizes the FP64 and double-float forms (tens of seconds per step) are left out
+    # the other forms on the same plan and inputs (not after the tables were released); the dense FP64
+    # form, several times slower than double-float at the same accuracy, only at one right-hand side
     if not args.surrogate:
         others = (("fp64", "f32x2", "fp32", "fft64", "fft32") if R == 1
-                  else ("fp32", "tf32", "bf16x2", "bf16x3", "fft64", "fft32"))
+                  else ("f32x2", "fp32", "tf32", "bf16x2", "bf16x3", "fft64", "fft32"))
         for prec in others:
             if prec != args.precision:
-                variant(prec, max(2, args.steps // 2))
+                variant(prec)
         plan.set_precision(args.precision)
         if R == 1:
             variants["harmonic_step"] = time_harmonic_step(torch, fbc, plan, w, xy_i, xy_p, ud,
                                                            max(3, args.steps // 2), flush_buf)
-        if args.precision in TENSOR and w.n_i > 1024:
-            # the same precision with the whole interface sum in one tensor-memory accumulation group
-            with fbc.Plan(xy_i, xy_p, w.L, w.material, precision=args.precision, max_rhs=R,
+        if R > 1 and w.n_i > 1024:
+            # BF16x2 with the whole interface sum in one tensor-memory accumulation group
+            with fbc.Plan(xy_i, xy_p, w.L, w.material, precision="bf16x2", max_rhs=R,
                           tc_fast_accumulate=True) as p1:
                 p1.tabulate()
-                vms, vstage = time_device_steps(torch, p1, fd, ud, max(2, args.steps // 2), 2, flush_buf)
+                vms, vstage, n = time_capped(p1, VARIANT_SECONDS, max(2, args.steps // 2))
                 outputs["fast_accumulate"] = snap()
-                variants["fast_accumulate"] = {"precision": args.precision, "ms_per_step": float(np.mean(vms)),
+                variants["fast_accumulate"] = {"precision": "bf16x2", "ms_per_step": float(np.mean(vms)),
                                                "value": pm / (np.mean(vms) * 1e-3) / 1e9,
-                                               "contract_ms": float(vstage[1])}
+                                               "contract_ms": float(vstage[1]), "steps": n}
 
-    # end-to-end through the host entry point: pinned host f in, host u out
+    # end-to-end through the host entry point: pinned host f in, host u out, in the headline form
+    if check_thread is not None:
+        check_thread.join()
     fh = torch.from_numpy(f).pin_memory()
     uh = torch.zeros((R, w.n_p, w.L, 3), dtype=torch.float64).pin_memory()
-    for _ in range(2):
-        plan.apply_host(fh, uh)
     torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    plan.apply_host(fh, uh)
+    one = time.perf_counter() - t1
     e2e_t = []
-    for _ in range(max(3, args.steps // 2)):
+    for _ in range(int(max(2, min(max(3, args.steps // 2), 2 * VARIANT_SECONDS // max(one, 1e-3))))):
         flush_buf.zero_()
         torch.cuda.synchronize()
         t1 = time.perf_counter()
@@ -427,61 +547,52 @@ def run_ours(args, w):
     d2h = uh.numel() * 8
     del fh, uh
 
-    # error against the FP64 oracle at the sampled pad atoms (all repeats of the first pad column, right-hand
-    # sides 0 and R-1), per mode band, and the CPU baseline
-    errors, bands, cpu = {}, {}, None
+    # error against the FP64 oracle at every repeat of the sampled pad columns for right-hand sides 0 and
+    # R - 1, per mode band; the Richardson truncation of the kernel; the CPU baseline
+    errors, bands, cpu, trunc = {}, {}, None, None
     if rank == 0 and not args.skip_oracle:
         import oracle
 
-        samples, fp, d_index, table, samp_col, samp_p, t_table = oracle_sample(w, xy_i, xy_p, f[rows])
-        ref = oracle.real_space_sum(d_index, table, fp, samp_col, samp_p)  # [len(rows)][L][3]
+        if "error" in check_out:
+            raise RuntimeError(f"oracle check failed: {check_out['error']}")
+        ref = check_out["ref"]
         for name, u in outputs.items():
-            got = u[:, samples[:, 0], samples[:, 1]]
-            errors[name] = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
-            bands[name] = band_errors(got[0], ref[0], w.L)
-        # timed oracle sum on the same sample (one right-hand side), repeated to ~10 s of CPU work
-        fp1 = np.ascontiguousarray(fp[:1])
+            errors[name] = float(np.linalg.norm(u - ref) / np.linalg.norm(ref))
+            bands[name] = band_errors(u, ref, w.L)
+        trunc = check_out["trunc"]
+        fp = oracle.project_neutral(f[:1])
+        # timed oracle on the bounded sample of the reference arm, repeated to ~10 s of CPU work
+        n_rep, share = cpu_sample(w)
+        d0, t0_, _ = oracle_table(w, xy_i, xy_p[:1])
+        sc0, sp0 = np.zeros(n_rep, np.int32), np.arange(n_rep, dtype=np.int32)
         reps, t_cpu = 0, 0.0
         while t_cpu < 10.0 and reps < 200:
             t1 = time.perf_counter()
-            oracle.real_space_sum(d_index, table, fp1, samp_col, samp_p)
+            oracle.real_space_sum(d0, t0_, fp[:1], sc0, sp0)
             t_cpu += time.perf_counter() - t1
             reps += 1
-        t_full = (t_cpu / reps) * (w.n_p * w.L * R) / len(samples)
         sinfo = oracle.sys_info()
-        cpu = {"value": pm / t_full / 1e9, "unit": UNIT, "cores": sinfo["cores"], "kind": "oracle",
-               "sample": (f"real-space sum at {len(samples)} pad atoms (1 pad column, all repeats, 1 right-hand "
-                          f"side) x {reps} repetitions ({t_cpu:.1f} s), extrapolated to N_P L n_rhs = "
-                          f"{w.n_p * w.L * R} pad-atom updates; kernel tabulation for the sample ({t_table:.1f} s) "
-                          f"untimed"),
+        cpu = {"value": pm * share / (t_cpu / reps) / 1e9, "unit": UNIT, "cores": sinfo["cores"], "kind": "oracle",
+               "sample": (f"real-space sum at {n_rep} pad atoms (repeats 0..{n_rep - 1} of pad column 0, right-hand "
+                          f"side 0) x {reps} repetitions ({t_cpu:.1f} s): {share:.3g} of the update per repetition; "
+                          "kernel tabulation for the sample untimed"),
                "cpu": sinfo["cpu"]}
         for name in variants:
-            variants[name]["rel_l2_vs_oracle"] = errors.get(name)
-            variants[name]["rel_l2_by_band"] = bands.get(name)
-
-    # roofline of the dominant kernel (the per-mode contraction stage, timed by the plan's events on the
-    # launching stream over the timed steps)
-    contract_ms = float(stage[1])
-    p = args.precision
-    if p in TENSOR:
-        # issued split products (TENSOR[p] bf16/tf32 products per block product), 36 flops each
-        achieved = TENSOR[p] * FLOPS_PER_PAIR_MODE * pm / (contract_ms * 1e-3) / 1e12
-        base = pk.get("bf16_tflops_sustained", pk["bf16_tflops"])
-        peak = base * (1.1 / 2.25 if p == "tf32" else 1.0)
-        peak_name = ("measured sustained bf16 dense" + (" x nominal tf32/bf16 ratio 1.1/2.25" if p == "tf32" else "")
-                     + f" ({pk['source']})")
-        bound = "tensor"
-    elif p == "fp64":
-        achieved = FLOPS_PER_PAIR_MODE * pm / (contract_ms * 1e-3) / 1e12
-        peak, peak_name, bound = pk["fp64_tflops"], "fp64 nominal 1.25 TFLOP/s scaled to max SM clock", "alu"
+            if name in errors:
+                variants[name]["rel_l2_vs_oracle"] = errors[name]
+                variants[name]["rel_l2_by_band"] = bands[name]
+        check = {"pad_columns": [int(c) for c in cols], "rhs": rows, "repeats": "all",
+                 "oracle_s": check_out["t_check"], "oracle_table_s": check_out["t_table"],
+                 "oracle_threads": check_out["threads"]}
     else:
-        # CUDA-core FP32-pipe work: FFMA, FMUL and FADD each take one lane-slot of the FMA pipes, so the
-        # ceiling is an instruction rate: 152 SMs x 128 lanes x max SM clock
-        per_pm = (FLOPS_PER_PAIR_MODE // 2) * (X2_INSTR_PER_MAC if p == "f32x2" else 1)
-        achieved = per_pm * pm / (contract_ms * 1e-3) / 1e12
-        peak, bound = pk["fp32_tinstr"], "alu"
-        peak_name = ("FP32-pipe lane instructions: 152 SM x 128 lanes x max SM clock; "
-                     f"{per_pm} per pair-mode ({'12 per double-float MAC' if p == 'f32x2' else '1 FFMA per MAC'})")
+        check = None
+
+    p = args.precision
+    contract_ms = float(stage[1])
+    roof = contraction_roofline(p, pm, contract_ms, pk)
+    roof["kernel"] = {"f32x2": "k_contract_x2_rb" if R > 1 else "k_contract_x2", "fp64": "k_contract_fp64",
+                      "fp32": "k_contract_fp32_rb" if R > 1 else "k_contract_fp32"}.get(
+        p, "k_contract_tc" if p in TENSOR else "k_fft_* (in-plane FFT contraction)")
     traffic = None
     tpath = os.path.join(ROOT, "profiles", "contract_traffic.json")
     if os.path.exists(tpath) and not args.surrogate:
@@ -490,6 +601,7 @@ def run_ours(args, w):
         ent = tr.get(f"{w.name}/{p}")
         if ent and ent.get("source_sha256") == source_digest(ent.get("sources", [])):
             traffic = ent.get("dram_bytes_per_apply_contraction")
+    roof["traffic"] = traffic
     clocks = clk.summary()
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -502,15 +614,14 @@ def run_ours(args, w):
                    "parallelism": "replicas" if world > 1 else "single"},
         "rel_l2_vs_oracle": errors.get("headline"),
         "rel_l2_by_band": bands.get("headline"),
+        "error_check": check,
+        "kernel_truncation": trunc,
         "setup_s": setup_s,
         "stage_ms": {"forward": float(stage[0]), "contract": contract_ms, "inverse": float(stage[2])},
-        "roofline": {"bound": bound, "achieved": achieved, "peak": peak,
-                     "unit": "TFLOP/s" if p in TENSOR or p == "fp64" else "T FP32-pipe instr/s",
-                     "frac": achieved / peak, "traffic": traffic, "peak_source": peak_name,
-                     "useful_tflops": FLOPS_PER_PAIR_MODE * pm / (contract_ms * 1e-3) / 1e12},
+        "roofline": roof,
         "variants": variants,
-        "e2e": {"value": job_value(pm, world, e2e_s * 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                "ms_per_step": e2e_s * 1e3},
+        "e2e": {"value": job_value(pm, world, e2e_s * 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h, "ms_per_step": e2e_s * 1e3, "steps": len(e2e_t)},
         "gpu_launches": launches_per_apply(p, info) * args.steps,
         "clocks": clocks,
         "plan": {k: info[k] for k in ("n_tiles_a", "n_tiles_b", "sub_w", "sub_h", "n_used_d", "table_bytes",
@@ -526,6 +637,139 @@ def run_ours(args, w):
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
+    return 0
+
+
+def run_batch(args):
+    """The batched workload: 64 uneven instances (N_I ~ U[500, 8000], N_P = 1.5 N_I, L in {32, ..., 512}),
+    16 right-hand sides each, rhs j scaled by 0.5^j.  One step = one update of every instance by the batch:
+    batched line transforms and one persistent contraction launch over all instances' work items, replayed
+    from a CUDA graph (the autotuned configuration).  Beside it: the same update as a loop of per-plan
+    applies, and other precisions.  Error: every repeat of pad column 0 of every instance, right-hand side
+    0, against the oracle."""
+    import torch
+
+    from paper_2105_08798_gb300 import build as fbc_build
+    from paper_2105_08798_gb300 import fbc
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    fbc_build.build()
+    fbc.load()
+    pk = peaks(torch.cuda.get_device_properties(local).multi_processor_count)
+    specs = inputs.batch_instances()
+    prec = args.precision
+    t0 = time.perf_counter()
+    plans, fs, us, geo, pm = [], [], [], [], 0.0
+    for sp in specs:
+        xy_i, xy_p = inputs.ring_geometry(sp["n_i"], sp["n_p"])
+        f = inputs.forces(sp["n_rhs"], sp["n_i"], sp["L"], sp["seed"], decay=0.5)
+        p = fbc.Plan(xy_i, xy_p, sp["L"], sp["material"], precision=prec, max_rhs=sp["n_rhs"])
+        p.tabulate()
+        plans.append(p)
+        fs.append(torch.from_numpy(f).cuda())
+        us.append(torch.zeros((sp["n_rhs"], sp["n_p"], sp["L"], 3), dtype=torch.float64, device="cuda"))
+        geo.append((xy_i, xy_p, f[:1]))
+        pm += sp["n_p"] * sp["n_i"] * (sp["L"] // 2 + 1) * sp["n_rhs"]
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t0
+    check_out = {}
+    if not args.skip_oracle:
+        import threading
+
+        def check():
+            try:
+                import oracle
+
+                nt = max(1, oracle.n_threads() - 2)
+                out = []
+                for sp, (xy_i, xy_p, f0) in zip(specs, geo):
+                    L = sp["L"]
+                    d_list, d_index = oracle.difference_index(xy_i, xy_p[:1])
+                    table = oracle.kernel_table(sp["material"], L, 1.0, d_list, nthreads=nt)
+                    out.append(oracle.real_space_sum(d_index, table, oracle.project_neutral(f0),
+                                                     np.zeros(L, np.int32), np.arange(L, dtype=np.int32),
+                                                     nthreads=nt)[0])
+                check_out["ref"] = out
+            except Exception as e:  # reported by the main thread
+                check_out["error"] = repr(e)
+
+        th = threading.Thread(target=check, daemon=True)
+        th.start()
+    else:
+        th = None
+    flush_buf = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def time_it(fn, steps, warmup):
+        for _ in range(warmup):
+            flush_buf.zero_()
+            fn()
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for a, b in ev:
+            flush_buf.zero_()
+            a.record(stream)
+            fn()
+            b.record(stream)
+        torch.cuda.synchronize()
+        return [a.elapsed_time(b) for a, b in ev]
+
+    batch = fbc.Batch(plans, fs, us)
+    batch.apply()
+    tune_ms = batch.autotune()
+    info = batch.info()
+    with ClockSampler(local) as clk:
+        ms = time_it(lambda: batch.apply(stream=stream), args.steps, args.warmup)
+    plans[0].sync_status()
+    outs = [u[0, 0].cpu().numpy() for u in us]
+    step_ms = float(np.mean(ms))
+    variants = {}
+
+    def loop():
+        for p, f, u in zip(plans, fs, us):
+            p.apply(f, u, stream=stream)
+
+    lms = time_it(loop, max(2, args.steps // 2), 1)
+    variants["per_plan_loop"] = {"precision": prec, "ms_per_step": float(np.mean(lms)),
+                                 "value": pm / (np.mean(lms) * 1e-3) / 1e9,
+                                 "note": "the same update as one fbc_apply per instance (each with its own launches)"}
+    batch.close()
+    for other in ("fp32", "bf16x2", "tf32"):
+        if other == prec:
+            continue
+        for p in plans:
+            p.set_precision(other)
+        with fbc.Batch(plans, fs, us) as b2:
+            b2.apply()
+            b2.autotune()
+            vms = time_it(lambda: b2.apply(stream=stream), max(2, args.steps // 2), 1)
+        variants[f"batch_{other}"] = {"ms_per_step": float(np.mean(vms)), "value": pm / (np.mean(vms) * 1e-3) / 1e9}
+    errors = None
+    if th is not None:
+        th.join()
+        if "error" in check_out:
+            raise RuntimeError(f"oracle check failed: {check_out['error']}")
+        per = [float(np.linalg.norm(o - r) / np.linalg.norm(r)) for o, r in zip(outs, check_out["ref"])]
+        errors = {"max": max(per), "median": float(np.median(per)), "per_instance": per,
+                  "sample": "every repeat of pad column 0 of each instance, right-hand side 0"}
+    for p in plans:
+        p.close()
+    line = {
+        "metric": METRIC, "value": pm / (step_ms * 1e-3) / 1e9, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": DTYPE[prec], "data": "synthetic",
+        "config": {"workload": "batch64_rhs16_iso", "instances": len(specs), "n_rhs": 16,
+                   "pair_modes": pm, "precision": prec, "l2": "flushed between steps (256 MB write)",
+                   "graph": True, "parallelism": "single"},
+        "batch": {"autotuned_contract_ms": tune_ms, "rhs_per_cta": info.get("rhs_per_cta"),
+                  "grid": info["grid"], "lpt_order": info["lpt_order"], "work_items": info["n_contract_items"],
+                  "kernel_launches": info["kernel_launches"]},
+        "rel_l2_vs_oracle": errors, "setup_s": setup_s, "variants": variants,
+        "gpu_launches": info["kernel_launches"] * args.steps, "clocks": clk.summary(),
+        "peaks": {"bf16_tflops_sustained": pk.get("bf16_tflops_sustained")},
+    }
+    print(json.dumps(line), flush=True)
     return 0
 
 
@@ -551,16 +795,25 @@ def main(argv=None):
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--precision", choices=["fp64", "f32x2", "fp32", "tf32", "bf16x2", "bf16x3", "fft64", "fft32"],
                     default=None,
-                    help="contraction precision (default: f32x2 for one right-hand side, bf16x2 for several)")
-    ap.add_argument("--workload", choices=sorted(inputs.WORKLOADS), default=WORKLOAD)
+                    help="contraction form of the timed steps (default: f32x2, the dense FP64-accurate form)")
+    ap.add_argument("--workload", choices=sorted(inputs.WORKLOADS) + ["batch"], default=WORKLOAD,
+                    help="a named single instance, or 'batch': 64 uneven instances with 16 right-hand sides each")
     ap.add_argument("--surrogate", action="store_true",
                     help="train the learned far field (width 128, 2^20 samples, 50 epochs), attach it with "
                          "r_min = 8 and release the K-slice tables; the exact-table path is timed first")
     ap.add_argument("--skip-oracle", action="store_true", help="no oracle error check / CPU baseline")
     args = ap.parse_args(argv)
+    if args.workload == "batch":
+        if args.impl == "reference":
+            print(json.dumps({"impl": "reference", "unavailable": "the batched workload has no reference arm; "
+                              "run the single-instance workloads"}), flush=True)
+            return 0
+        if args.precision is None:
+            args.precision = "bf16x2"
+        return run_batch(args)
     w = inputs.WORKLOADS[args.workload]
     if args.precision is None:
-        args.precision = "f32x2" if w.n_rhs == 1 else "bf16x2"
+        args.precision = "f32x2"
     if args.surrogate and args.precision not in ("fp32", "tf32", "bf16x2", "bf16x3"):
         ap.error("--surrogate serves the FP32 and tensor-core precisions")
     if args.impl == "reference":

@@ -332,12 +332,18 @@ typedef struct fbc_batch_info {
     int32_t kernel_launches;    /* launches per apply (with both flags) */
     size_t smem_contract;       /* dynamic shared memory of the contraction CTAs */
     double pair_modes;          /* sum over instances of n_p n_i K n_rhs */
+    int32_t rhs_per_cta;        /* right-hand sides per contraction work item (tensor forms: the tuned group) */
+    int32_t reserved;
 } fbc_batch_info;
 
 /* Bind n_plans tabulated plans (same precision, each at most once) to their
  * DEVICE buffers: f[i] [n_rhs[i]][n_i][L][3], u[i] [n_rhs[i]][n_p][L][3].
  * The buffers are fixed for the batch's lifetime (the graph refers to them).
- * Allocates the work lists; synchronous. */
+ * Precisions: FP64, FP32, double-float and the tensor-core forms (TF32,
+ * BF16X2, BF16X3: the modes k >= 1 of every instance run in one persistent
+ * tensor-core launch, k = 0 in double-float; a timeout of that launch is
+ * reported through the first plan's status word, fbc_plan_sync_status).  Not
+ * the in-plane FFT forms.  Allocates the work lists; synchronous. */
 int fbc_batch_create(fbc_plan* const* plans, int32_t n_plans, const double* const* f, double* const* u,
                      const int32_t* n_rhs, fbc_batch** out);
 
@@ -348,9 +354,13 @@ int fbc_batch_create(fbc_plan* const* plans, int32_t n_plans, const double* cons
  * one batch, or of batches sharing a plan, concurrently. */
 int fbc_batch_apply(fbc_batch* batch, double alpha, double beta, uint32_t flags, void* stream);
 
-/* Time the contraction launch for a few persistent grid sizes and both queue
- * orders and keep the fastest (synchronous; reallocates the queue).  *best_ms
- * (may be NULL) receives the chosen configuration's contraction time. */
+/* Time the contraction launch for each candidate configuration and keep the
+ * fastest (synchronous; reallocates the queue): both queue orders (longest
+ * first, instance-major) and, for the CUDA-core forms, a few persistent grid
+ * sizes; for the tensor-core forms the rhs group (right-hand sides per work
+ * item, i.e. the N = 2 rhs of the tensor-core tile: the plans' largest, then
+ * halves down to 8).  No candidate changes the results.  *best_ms (may be
+ * NULL) receives the chosen configuration's contraction time. */
 int fbc_batch_autotune(fbc_batch* batch, void* stream, double* best_ms);
 
 int fbc_batch_info_get(const fbc_batch* batch, fbc_batch_info* info);

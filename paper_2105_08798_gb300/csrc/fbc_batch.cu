@@ -8,9 +8,19 @@
 // The persistent kernel's CTAs take work with atomicAdd on a counter that is
 // reset by the graph; no CTA waits for another, so nothing can spin.
 //
-// Autotuning: the persistent grid size (resident CTAs per SM times the SM
-// count, or fewer) and the order of the contraction queue (LPT or the natural
-// instance-major order) are chosen by timing the contraction launch.
+// Tensor-core batches (TF32, BF16x2, BF16x3): the k = 0 items run on the
+// double-float tile (as in a single plan), each instance's force operand is
+// split into its plan's buffer, and the modes k >= 1 of all instances run in
+// one persistent tensor-core launch (one CTA per SM) over a queue of items
+// (instance, mode, pad tile, rhs group).
+//
+// Autotuning: the order of the contraction queue (LPT or the natural
+// instance-major order) and, for the CUDA-core forms, the persistent grid
+// size (resident CTAs per SM times the SM count, or fewer); for the tensor
+// forms the rhs group -- right-hand sides per CTA, i.e. the N of the
+// tensor-core tile (N = 2 x rhs) -- which trades the table gathers (once per
+// group) against the number of items and their balance.  Each candidate is
+// timed on the contraction launch; none changes the results.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -37,6 +47,11 @@ struct fbc_batch {
     std::vector<int> n_rhs;
     std::vector<Item> con_items[2];  // natural order; [0]: k = 0 items of an FP32 batch, [1]: the rest
     std::vector<int4> fwd, proj, inv, zm;
+    // tensor-core forms: rhs per CTA (one value for the batch, capped per instance), jobs and their items
+    int rpc = 0;
+    std::vector<fbc::TcJob> tc_jobs;
+    fbc::TcJob* d_tc_jobs = nullptr;
+    size_t smem_tc = 0;
     fbc::LineArgs* d_largs = nullptr;
     fbc::ContractArgs* d_cargs = nullptr;
     int* d_nrhs = nullptr;
@@ -72,8 +87,8 @@ void free_batch(fbc_batch* b) {
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->graph) cudaGraphDestroy(b->graph);
     if (b->cap) cudaStreamDestroy(b->cap);
-    void* bufs[] = {b->d_largs, b->d_cargs, b->d_nrhs, b->d_fwd, b->d_proj, b->d_con[0], b->d_con[1], b->d_inv, b->d_zm,
-                    b->d_counter};
+    void* bufs[] = {b->d_largs, b->d_cargs, b->d_nrhs, b->d_fwd,   b->d_proj,   b->d_con[0],
+                    b->d_con[1], b->d_inv,   b->d_zm,   b->d_counter, b->d_tc_jobs};
     for (void* p : bufs)
         if (p) cudaFree(p);
 }
@@ -86,6 +101,37 @@ cudaError_t upload(T** dst, const std::vector<T>& src) {
     if (e) return e;
     if (!src.empty()) e = cudaMemcpy(*dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice);
     return e;
+}
+
+bool tensor(const fbc_batch* b) { return fbc::is_tensor_precision(b->precision); }
+
+// rhs per CTA of instance i for the batch's choice (capped by what its plan's operand buffer holds)
+int inst_rpc(const fbc_batch* b, int i) {
+    const fbc::Plan& P = b->plans[i]->p;
+    int r = std::min(b->rpc, fbc::contract_tc_max_rpc(P));
+    while (r > 1 && !fbc::contract_tc_rpc_fits(P, r)) r--;
+    return r;
+}
+
+// Tensor-core items (instance, k >= 1, pad tile, rhs group) and jobs for the batch's rhs group; the cost of
+// an item is its stages (interface tiles) times the rows of its force operand (the tile's N).
+void build_tc_items(fbc_batch* b) {
+    b->con_items[1].clear();
+    b->tc_jobs.resize(b->n);
+    b->smem_tc = 0;
+    for (int i = 0; i < b->n; i++) {
+        const fbc::Plan& P = b->plans[i]->p;
+        const int rpc = inst_rpc(b, i), R = b->n_rhs[i], HW = P.H * P.W;
+        const int nbuf = fbc::contract_tc_nbuf_smem(b->precision, HW, 2) <= 227 * 1024 ? 2 : 1;
+        b->smem_tc = std::max(b->smem_tc, fbc::contract_tc_nbuf_smem(b->precision, HW, nbuf));
+        b->tc_jobs[i] = fbc::contract_tc_job(P, R, rpc, nbuf);
+        for (int k = 1; k < P.K; k++)
+            for (int tA = 0; tA < P.n_ta; tA++)
+                for (int g = 0; g < (R + rpc - 1) / rpc; g++) {
+                    const int rg = std::min(rpc, R - g * rpc);
+                    b->con_items[1].push_back({make_int4(i, k, tA, g), (double)P.n_tb * (16 + ((2 * rg + 15) / 16) * 16)});
+                }
+    }
 }
 
 std::vector<int4> ordered_items(const fbc_batch* b, int phase, bool lpt) {
@@ -103,11 +149,26 @@ cudaError_t enqueue(fbc_batch* b, double alpha, double beta, uint32_t flags, cud
     if ((e = fbc::launch_batch_line(0, b->d_largs, b->d_fwd, (int)b->fwd.size(), b->smem_line, 0, 0, 0, st, fbc::line_fp32(b->precision)))) return e;
     if (project && (e = fbc::launch_batch_line(1, b->d_largs, b->d_proj, (int)b->proj.size(), 0, 0, 0, 0, st, fbc::line_fp32(b->precision)))) return e;
     if ((e = cudaMemsetAsync(b->d_counter, 0, 2 * sizeof(int), st))) return e;
-    for (int ph = 0; ph < 2; ph++)
+    for (int ph = 0; ph < 2; ph++) {
+        if (ph == 1 && tensor(b)) {
+            // each instance's force operand split once for its rhs group, then one launch over all items
+            for (int i = 0; i < b->n; i++) {
+                const fbc::Plan& P = b->plans[i]->p;
+                if (P.K < 2) continue;
+                if ((e = fbc::contract_tc_prep(P, P.d_fh, inst_rpc(b, i), b->n_rhs[i], 1, P.K - 1, st))) return e;
+            }
+            const fbc::Plan& P0 = b->plans[0]->p;
+            const int wl = P0.wait_limit > 0 ? P0.wait_limit : (1 << 24);
+            if ((e = fbc::launch_contract_tc_batch(b->precision, b->d_tc_jobs, b->d_con[1], (int)b->con_items[1].size(),
+                                                   b->d_counter + 1, b->grid[1], b->smem_tc, wl, P0.d_status, st)))
+                return e;
+            continue;
+        }
         if ((e = fbc::launch_batch_contract(b->precision, ph, b->d_cargs, b->d_nrhs, b->d_con[ph],
                                             (int)b->con_items[ph].size(), b->d_counter + ph, b->grid[ph],
                                             b->smem_con[ph], st)))
             return e;
+    }
     if ((e = fbc::launch_batch_line(2, b->d_largs, b->d_inv, (int)b->inv.size(), b->smem_line, alpha, beta,
                                     zmean ? 1 : 0, st, fbc::line_fp32(b->precision))))
         return e;
@@ -136,8 +197,8 @@ int fbc_batch_create(fbc_plan* const* plans, int32_t n_plans, const double* cons
         if (P.precision != prec) return bfail(FBC_ERR_INVALID_ARG, "all plans of a batch need the same precision");
         if (fbc::is_fft_precision(prec))
             return bfail(FBC_ERR_UNSUPPORTED, "batches run the dense per-mode contraction, not the in-plane FFT form");
-        if (fbc::is_tensor_precision(prec))
-            return bfail(FBC_ERR_UNSUPPORTED, "batches run the CUDA-core precisions (FP64, FP32, double-float)");
+        if (fbc::is_tensor_precision(prec) && fbc::contract_tc_smem(prec, P.W * P.H) > 227 * 1024)
+            return bfail(FBC_ERR_UNSUPPORTED, "tensor-core contraction: an instance's sub-box exceeds shared memory");
         if (n_rhs[i] < 1 || n_rhs[i] > P.opt.max_rhs) return bfail(FBC_ERR_INVALID_ARG, "n_rhs outside [1, max_rhs]");
         if (!f[i] || !u[i]) return bfail(FBC_ERR_INVALID_ARG, "f or u of an instance is NULL");
         for (int j = 0; j < i; j++)
@@ -176,7 +237,11 @@ int fbc_batch_create(fbc_plan* const* plans, int32_t n_plans, const double* cons
         const double per_tile = (double)P.n_tb * P.TA * P.TB;
         for (int k = 0; k < P.K; k++)
             for (int tA = 0; tA < P.n_ta; tA++) {
-                if (prec == FBC_PREC_FP32 && k > 0) {
+                if (fbc::is_tensor_precision(prec) && k > 0) {
+                    continue;  // the tensor-core items are built below for the batch's rhs group
+                } else if (fbc::is_tensor_precision(prec)) {  // k = 0 in double-float, as in a single plan
+                    for (int r = 0; r < R; r++) b->con_items[0].push_back({make_int4(i, k, tA, r), per_tile / 130.0});
+                } else if (prec == FBC_PREC_FP32 && k > 0) {
                     for (int rb = 0; rb < (R + RB - 1) / RB; rb++) {
                         const int cnt = std::min(RB, R - rb * RB);
                         b->con_items[1].push_back({make_int4(i, k, tA, rb), per_tile * cnt / 1500.0});
@@ -189,6 +254,10 @@ int fbc_batch_create(fbc_plan* const* plans, int32_t n_plans, const double* cons
                 }
             }
         b->pair_modes += (double)P.n_p * P.n_i * P.K * R;
+    }
+    if (fbc::is_tensor_precision(prec)) {
+        b->rpc = 64;
+        build_tc_items(b);
     }
     if (std::max(b->smem_con[0], b->smem_con[1]) > 227 * 1024) {
         free_batch(b);
@@ -207,6 +276,7 @@ int fbc_batch_create(fbc_plan* const* plans, int32_t n_plans, const double* cons
     if (!e) e = upload(&b->d_zm, b->zm);
     if (!e) e = upload(&b->d_con[0], ordered_items(b, 0, true));
     if (!e) e = upload(&b->d_con[1], ordered_items(b, 1, true));
+    if (!e && tensor(b)) e = upload(&b->d_tc_jobs, b->tc_jobs);
     if (!e) e = cudaMalloc((void**)&b->d_counter, 2 * sizeof(int));
     if (!e) e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
     if (e) {
@@ -216,7 +286,8 @@ int fbc_batch_create(fbc_plan* const* plans, int32_t n_plans, const double* cons
         return st;
     }
     for (int ph = 0; ph < 2; ph++) {
-        b->occupancy[ph] = fbc::batch_contract_occupancy_phase(prec, ph, b->smem_con[ph]);
+        // the tensor-core launch holds all of an SM's tensor memory: one CTA per SM
+        b->occupancy[ph] = (ph == 1 && tensor(b)) ? 1 : fbc::batch_contract_occupancy_phase(prec, ph, b->smem_con[ph]);
         b->grid[ph] = b->occupancy[ph] * b->sm_count;
     }
     *out = b;
@@ -265,6 +336,57 @@ int fbc_batch_autotune(fbc_batch* b, void* stream, double* best_ms) {
     // the transforms run once so the contraction sees real inputs; the dominant launch (phase 1) is tuned
     cudaError_t e = fbc::launch_batch_line(0, b->d_largs, b->d_fwd, (int)b->fwd.size(), b->smem_line, 0, 0, 0, st, fbc::line_fp32(b->precision));
     const int ph = 1;
+    if (!e && tensor(b)) {
+        // rhs group (largest first, then halves that keep N = 2 rhs a multiple of 16) x queue order
+        int max_rpc = 1;
+        for (int i = 0; i < b->n; i++) max_rpc = std::max(max_rpc, fbc::contract_tc_max_rpc(b->plans[i]->p));
+        std::vector<int> cands;
+        for (int r = max_rpc; r >= 8; r /= 2) cands.push_back(r);
+        double best = 1e300;
+        int best_rpc = b->rpc, best_lpt = b->lpt;
+        const fbc::Plan& P0 = b->plans[0]->p;
+        const int wl = P0.wait_limit > 0 ? P0.wait_limit : (1 << 24);
+        for (int rpc : cands) {
+            b->rpc = rpc;
+            build_tc_items(b);
+            if ((e = upload(&b->d_tc_jobs, b->tc_jobs))) break;
+            for (int i = 0; i < b->n && !e; i++) {
+                const fbc::Plan& P = b->plans[i]->p;
+                if (P.K > 1) e = fbc::contract_tc_prep(P, P.d_fh, inst_rpc(b, i), b->n_rhs[i], 1, P.K - 1, st);
+            }
+            for (int lpt = 1; lpt >= 0 && !e; lpt--) {
+                if ((e = upload(&b->d_con[ph], ordered_items(b, ph, lpt == 1)))) break;
+                float ms_sum = 0.0f;
+                for (int rep = 0; rep < 2 && !e; rep++) {
+                    if ((e = cudaMemsetAsync(b->d_counter + ph, 0, sizeof(int), st))) break;
+                    cudaEventRecord(e0, st);
+                    e = fbc::launch_contract_tc_batch(b->precision, b->d_tc_jobs, b->d_con[ph],
+                                                      (int)b->con_items[ph].size(), b->d_counter + ph, b->grid[ph],
+                                                      b->smem_tc, wl, P0.d_status, st);
+                    cudaEventRecord(e1, st);
+                    if (!e) e = cudaEventSynchronize(e1);
+                    float ms = 0.0f;
+                    cudaEventElapsedTime(&ms, e0, e1);
+                    if (rep == 1) ms_sum += ms;  // the first repetition warms caches
+                }
+                if (!e && ms_sum < best) best = ms_sum, best_rpc = rpc, best_lpt = lpt;
+            }
+            if (e) break;
+        }
+        if (!e) {
+            b->rpc = best_rpc;
+            b->lpt = best_lpt;
+            build_tc_items(b);
+            e = upload(&b->d_tc_jobs, b->tc_jobs);
+            if (!e) e = upload(&b->d_con[ph], ordered_items(b, ph, best_lpt == 1));
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        if (e) return bcuda(e, "autotune");
+        b->graph_valid = false;
+        if (best_ms) *best_ms = best;
+        return FBC_OK;
+    }
     double best = 1e300;
     int best_grid = b->grid[ph], best_lpt = b->lpt;
     const int occ = b->occupancy[ph];
@@ -309,8 +431,11 @@ int fbc_batch_info_get(const fbc_batch* b, fbc_batch_info* info) {
     info->lpt_order = b->lpt;
     // forward, projection, contraction (one launch per non-empty phase), inverse, zero mean (when flagged)
     info->kernel_launches = 4 + (b->con_items[0].empty() ? 0 : 1) + (b->con_items[1].empty() ? 0 : 1);
-    info->smem_contract = b->smem_con[1];
+    if (tensor(b))
+        for (const fbc_plan* pl : b->plans) info->kernel_launches += pl->p.K > 1 ? 1 : 0;  // the force splits
+    info->smem_contract = tensor(b) ? b->smem_tc : b->smem_con[1];
     info->pair_modes = b->pair_modes;
+    info->rhs_per_cta = tensor(b) ? b->rpc : (b->precision == FBC_PREC_FP32 ? fbc::batch_rhs_block() : 1);
     return FBC_OK;
 }
 

@@ -223,19 +223,25 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
     e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
 }
 
-// Accumulate the product (ah + al)(xh + xl) into the running pair (S, E):
-// the leading product ah*xh is split exactly into p + e with one FMA, the
-// cross terms (relative size 2^-24) are folded into e, p is added to S with
-// an exact two-sum and every low-order piece lands in E.
+// Accumulate the product (ah + al)(xh + xl) into the running pair (S, E),
+// 10 FP32-pipe instructions.  The leading product p = fl(ah xh) is added to
+// S as in Knuth's two-sum: s = S + p, bb = s - S is the part of p that s
+// took up and S - (s - bb) the part of S it lost (exact).  What is left of
+// the exact product, ah xh - bb, comes from one FMA (a single rounding of a
+// quantity of order ulp(s)); it replaces both the two-sum's p - bb and the
+// product's own rounding error ah xh - p.  The cross terms ah xl + al xh
+// (relative size 2^-24) are added to it with two more FMAs, and everything
+// low-order lands in E.
 __device__ __forceinline__ void df_mac(float ah, float al, float xh, float xl, float& S, float& E) {
     const float p = __fmul_rn(ah, xh);
-    float e = __fmaf_rn(ah, xh, -p);
-    e = __fmaf_rn(ah, xl, e);
-    e = __fmaf_rn(al, xh, e);
-    float s, err;
-    two_sum(S, p, s, err);
+    const float s = __fadd_rn(S, p);
+    const float bb = __fsub_rn(s, S);
+    const float lost = __fsub_rn(S, __fsub_rn(s, bb));
+    float rest = __fmaf_rn(ah, xh, -bb);
+    rest = __fmaf_rn(ah, xl, rest);
+    rest = __fmaf_rn(al, xh, rest);
     S = s;
-    E = __fadd_rn(E, __fadd_rn(err, e));
+    E = __fadd_rn(E, __fadd_rn(lost, rest));
 }
 
 // T += (S + E) in double-float arithmetic (accurate sum of two pairs).
@@ -353,6 +359,136 @@ __device__ __forceinline__ void tile_x2(const ContractArgs& A, int tA, int k, in
 }
 
 
+// Double-float for plans with several right-hand sides.  The CTA has NG
+// groups of TA threads (thread = pad column a of the tile, group g) and covers
+// NG * RB right-hand sides; thread (a, g) carries RB of them.  The staged
+// table sub-box is shared by all groups, the three table records of a
+// (pad column, interface column) pair are read once per thread and applied to
+// its RB force columns, and each thread carries 6 RB independent running pairs
+// (S, E): independent work for the FP32 pipes between the dependent adds of
+// the two-sums.  The sums, their order and the fold per interface tile are
+// those of tile_x2, so each right-hand side gets the same bits as from the
+// one-rhs tile.  grid.z = ceil(n_rhs / (NG RB)); force records [NG RB][TB][3]
+// (hi/lo pairs of x and y').
+template <int TA, int TB, int NG, int RB, bool K0>
+__device__ __forceinline__ void tile_x2_rb(const ContractArgs& A, int tA, int k, int rb, int n_rhs, void* smem_raw) {
+    constexpr int NT = TA * NG, NR = NG * RB;
+    float4* smemx2 = (float4*)smem_raw;
+    const int HW = A.H * A.W;
+    float4* s_tab = smemx2;                   // [HW][3]
+    float4* s_f = s_tab + 3 * HW;             // [NR][TB][3]
+    int* s_off = (int*)(s_f + 3 * NR * TB);   // [TB]
+    const int r0 = rb * NR;
+    const int a_loc = threadIdx.x % TA, g = threadIdx.x / TA;
+    const int a = tA * TA + a_loc;
+    const int2 xa = A.xy_p[a];
+    const int4 bA = A.bbox_a[tA];
+    float Th[RB][6], Tl[RB][6];
+#pragma unroll
+    for (int q = 0; q < RB; q++)
+#pragma unroll
+        for (int c = 0; c < 6; c++) Th[q][c] = Tl[q][c] = 0.f;
+    const float* tk = A.tabx2 + (size_t)(k - A.kbase) * A.Dy * A.Dx * 12;
+    for (int tB = 0; tB < A.n_tb; tB++) {
+        const int4 bB = A.bbox_b[tB];
+        const int ox = bA.x - bB.y, oy = bA.z - bB.w;
+        __syncthreads();
+        for (int e = threadIdx.x; e < HW; e += NT) {
+            const int iy = e / A.W, ix = e - iy * A.W;
+            const int gx = ox + ix - A.box_x0, gy = oy + iy - A.box_y0;
+            float4 q0 = make_float4(0, 0, 0, 0), q1 = q0, q2 = q0;
+            if (gx < A.Dx && gy < A.Dy) {
+                const float2* src = (const float2*)(tk + ((size_t)gy * A.Dx + gx) * 12);
+                const float2 h01 = __ldg(src), h23 = __ldg(src + 1), h45 = __ldg(src + 2);
+                const float2 l01 = __ldg(src + 3), l23 = __ldg(src + 4), l45 = __ldg(src + 5);
+                q0 = make_float4(h01.x, l01.x, h01.y, l01.y);
+                q1 = make_float4(h23.x, l23.x, h23.y, l23.y);
+                q2 = make_float4(h45.x, l45.x, h45.y, l45.y);
+            }
+            s_tab[3 * e] = q0, s_tab[3 * e + 1] = q1, s_tab[3 * e + 2] = q2;
+        }
+        for (int e = threadIdx.x; e < NR * TB; e += NT) {
+            const int q = e / TB, j = e - q * TB;
+            float h[6] = {0, 0, 0, 0, 0, 0}, l[6] = {0, 0, 0, 0, 0, 0};
+            if (r0 + q < n_rhs) {
+                const double* src = A.fh + (((size_t)(r0 + q) * A.K + k) * A.NIpad + (size_t)tB * TB + j) * 6;
+#pragma unroll
+                for (int c = 0; c < 6; c++) {
+                    const double v = src[c];
+                    h[c] = (float)v;
+                    l[c] = (float)(v - (double)h[c]);
+                }
+            }
+            s_f[3 * e + 0] = make_float4(h[0], l[0], h[1], l[1]);
+            s_f[3 * e + 1] = make_float4(h[2], l[2], h[3], l[3]);
+            s_f[3 * e + 2] = make_float4(h[4], l[4], h[5], l[5]);
+        }
+        for (int e = threadIdx.x; e < TB; e += NT) s_off[e] = A.off_i[tB * TB + e];
+        __syncthreads();
+        const int base = (xa.x - ox) + A.W * (xa.y - oy);
+        float S[RB][6], E[RB][6];
+#pragma unroll
+        for (int q = 0; q < RB; q++)
+#pragma unroll
+            for (int c = 0; c < 6; c++) S[q][c] = E[q][c] = 0.f;
+        const float4* fg = s_f + 3 * (g * RB) * TB;  // this group's right-hand sides
+#pragma unroll 2
+        for (int j = 0; j < TB; j++) {
+            const int idx = base - s_off[j];
+            const float4 t0 = s_tab[3 * idx], t1 = s_tab[3 * idx + 1];
+            const float4 t2 = K0 ? make_float4(0, 0, 0, 0) : s_tab[3 * idx + 2];
+#pragma unroll
+            for (int q = 0; q < RB; q++) {
+                const float4* fq = fg + 3 * (q * TB + j);
+                const float4 f0 = fq[0], f2 = fq[2];
+                if (K0) {
+                    // k = 0: the five non-zero products of tile_x2's k = 0 branch, in its order
+                    df_mac(t0.x, t0.y, f0.x, f0.y, S[q][0], E[q][0]);
+                    df_mac(t0.z, t0.w, f0.z, f0.w, S[q][0], E[q][0]);
+                    df_mac(t0.z, t0.w, f0.x, f0.y, S[q][1], E[q][1]);
+                    df_mac(t1.x, t1.y, f0.z, f0.w, S[q][1], E[q][1]);
+                    df_mac(t1.z, t1.w, f2.z, f2.w, S[q][5], E[q][5]);
+                    continue;
+                }
+                const float4 f1 = fq[1];
+                // x = (f0.x, f0.y) (f0.z, f0.w) (f1.x, f1.y); y' = (f1.z, f1.w) (f2.x, f2.y) (f2.z, f2.w)
+                df_mac(t0.x, t0.y, f0.x, f0.y, S[q][0], E[q][0]);
+                df_mac(t0.z, t0.w, f0.z, f0.w, S[q][0], E[q][0]);
+                df_mac(-t2.x, -t2.y, f1.x, f1.y, S[q][0], E[q][0]);
+                df_mac(t0.z, t0.w, f0.x, f0.y, S[q][1], E[q][1]);
+                df_mac(t1.x, t1.y, f0.z, f0.w, S[q][1], E[q][1]);
+                df_mac(-t2.z, -t2.w, f1.x, f1.y, S[q][1], E[q][1]);
+                df_mac(t2.x, t2.y, f0.x, f0.y, S[q][2], E[q][2]);
+                df_mac(t2.z, t2.w, f0.z, f0.w, S[q][2], E[q][2]);
+                df_mac(t1.z, t1.w, f1.x, f1.y, S[q][2], E[q][2]);
+                df_mac(t0.x, t0.y, f1.z, f1.w, S[q][3], E[q][3]);
+                df_mac(t0.z, t0.w, f2.x, f2.y, S[q][3], E[q][3]);
+                df_mac(-t2.x, -t2.y, f2.z, f2.w, S[q][3], E[q][3]);
+                df_mac(t0.z, t0.w, f1.z, f1.w, S[q][4], E[q][4]);
+                df_mac(t1.x, t1.y, f2.x, f2.y, S[q][4], E[q][4]);
+                df_mac(-t2.z, -t2.w, f2.z, f2.w, S[q][4], E[q][4]);
+                df_mac(t2.x, t2.y, f1.z, f1.w, S[q][5], E[q][5]);
+                df_mac(t2.z, t2.w, f2.x, f2.y, S[q][5], E[q][5]);
+                df_mac(t1.z, t1.w, f2.z, f2.w, S[q][5], E[q][5]);
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < RB; q++)
+#pragma unroll
+            for (int c = 0; c < 6; c++) df_fold(Th[q][c], Tl[q][c], S[q][c], E[q][c]);
+    }
+#pragma unroll
+    for (int q = 0; q < RB; q++) {
+        const int r = r0 + g * RB + q;
+        if (r >= n_rhs) break;
+        double* o = A.uh + (((size_t)r * A.K + k) * A.NPpad + a) * 6;
+#pragma unroll
+        for (int c = 0; c < 6; c++) o[c] = (double)Th[q][c] + (double)Tl[q][c];
+        if (K0) o[2] = o[3] = o[4] = 0.0;
+    }
+}
+
+
 // ---- one launch per plan: grid (pad tiles, modes, right-hand sides) ----------
 template <int TA, int TB>
 __global__ void __launch_bounds__(TA) k_contract_fp64(ContractArgs A) {
@@ -373,6 +509,13 @@ template <int TA, int TB, bool K0>
 __global__ void __launch_bounds__(TA) k_contract_x2(ContractArgs A) {
     extern __shared__ float4 smem_raw[];
     tile_x2<TA, TB, K0>(A, blockIdx.x, A.k0 + blockIdx.y, blockIdx.z, smem_raw);
+}
+// grid (pad tiles, rhs groups, modes): the modes outermost, so the CTAs of all rhs groups of one mode run
+// together and read that mode's table slice from L2
+template <int TA, int TB, int NG, int RB, bool K0>
+__global__ void __launch_bounds__(TA * NG) k_contract_x2_rb(ContractArgs A, int n_rhs) {
+    extern __shared__ float4 smem_raw[];
+    tile_x2_rb<TA, TB, NG, RB, K0>(A, blockIdx.x, A.k0 + blockIdx.z, blockIdx.y, n_rhs, smem_raw);
 }
 
 // ---- batched: one persistent launch drains a cost-sorted work list ----------
@@ -407,6 +550,12 @@ __global__ void __launch_bounds__(TA) k_batch_contract(const ContractArgs* __res
     }
 }
 
+// multi-rhs double-float tile: kX2NG groups of kTileA threads, kX2RB right-hand sides per thread
+constexpr int kX2NG = 2, kX2RB = 2, kX2R = kX2NG * kX2RB;
+size_t x2_rb_smem(const Plan& P) {
+    return (size_t)P.H * P.W * 48 + (size_t)kX2R * kTileB * 48 + (size_t)kTileB * 4 + 16;
+}
+
 template <class T>
 size_t contract_smem(const Plan& P, int TB, int per_entry) {
     return (size_t)6 * P.H * P.W * per_entry + (size_t)TB * 6 * per_entry + (size_t)TB * sizeof(int) + 16;
@@ -436,7 +585,7 @@ cudaError_t launch_contract(Plan& P, int n_rhs, cudaStream_t st) {
     }
     if (P.precision == FBC_PREC_FP32) {
         // logarithmic k = 0 mode in double-float (FP64-accurate), the rest in FP32
-        cudaError_t e = launch_one(k_contract_x2<kTileA, kTileB, true>, A, dim3(P.n_ta, 1, n_rhs), kTileA, sx2, st);
+        cudaError_t e = launch_contract_x2_k0(P, A, n_rhs, st);
         if (e || P.K < 2) return e;
         A.k0 = 1;
         if (n_rhs >= 2) {
@@ -450,12 +599,16 @@ cudaError_t launch_contract(Plan& P, int n_rhs, cudaStream_t st) {
     }
     if (is_tensor_precision(P.precision)) {
         // logarithmic k = 0 mode in double-float (FP64-accurate) on the CUDA cores, k >= 1 on the tensor cores
-        cudaError_t e = launch_one(k_contract_x2<kTileA, kTileB, true>, A, dim3(P.n_ta, 1, n_rhs), kTileA, sx2, st);
+        cudaError_t e = launch_contract_x2_k0(P, A, n_rhs, st);
         if (e || P.K < 2) return e;
         A.k0 = 1;
         return launch_contract_tc(A, P, n_rhs, st);
     }
     if (P.precision == FBC_PREC_F32X2) {
+        if (n_rhs >= 2) {
+            return launch_one(k_contract_x2_rb<kTileA, kTileB, kX2NG, kX2RB, false>, A,
+                              dim3(P.n_ta, (n_rhs + kX2R - 1) / kX2R, P.K), kTileA * kX2NG, x2_rb_smem(P), st, n_rhs);
+        }
         return launch_one(k_contract_x2<kTileA, kTileB, false>, A, dim3(P.n_ta, P.K, n_rhs), kTileA, sx2, st);
     }
     if (is_fft_precision(P.precision)) return launch_contract_fft(P, n_rhs, st);
@@ -475,6 +628,10 @@ ContractArgs make_contract_args(const Plan& P) {
 }
 
 cudaError_t launch_contract_x2_k0(Plan& P, const ContractArgs& A, int n_rhs, cudaStream_t st) {
+    if (n_rhs >= 2) {
+        return launch_one(k_contract_x2_rb<kTileA, kTileB, kX2NG, kX2RB, true>, A,
+                          dim3(P.n_ta, (n_rhs + kX2R - 1) / kX2R, 1), kTileA * kX2NG, x2_rb_smem(P), st, n_rhs);
+    }
     const size_t sx2 = (size_t)P.H * P.W * 48 + (size_t)kTileB * 64 + 16;
     return launch_one(k_contract_x2<kTileA, kTileB, true>, A, dim3(P.n_ta, 1, n_rhs), kTileA, sx2, st);
 }

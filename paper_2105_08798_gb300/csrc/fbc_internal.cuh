@@ -132,6 +132,18 @@ struct ContractArgs {
     int kbase;  // the tables hold mode slices kbase, kbase + 1, ... (0: all K; else a streamed chunk)
 };
 
+// One instance's share of a tensor-core contraction launch (fbc_contract_tc.cu).
+struct TcJob {
+    ContractArgs A;
+    const unsigned char* bprep;  // split force operand: chunks (mode, rhs group, interface tile, stage)
+    int n_rhs;                   // right-hand sides applied
+    int rpc;                     // right-hand sides per CTA (one rhs group)
+    int G;                       // rhs groups in the operand buffer's layout
+    int npb;                     // force-operand rows per chunk: 2 rpc rounded up to 16
+    int gs;                      // stages per tensor-memory accumulation group
+    int nbuf;                    // table sub-box buffers in shared memory (2: the next tile prefetched)
+};
+
 // Everything the line transforms need about one plan (one instance of a batch).
 struct LineArgs {
     const double* f;   // caller forces [n_rhs][n_i][L][3]
@@ -178,7 +190,16 @@ cudaError_t launch_contract_x2_k0(Plan& P, const ContractArgs& A, int n_rhs, cud
 cudaError_t launch_contract_streamed(Plan& P, int n_rhs, cudaStream_t st);
 void release_surrogate_buffers(Plan& P);
 size_t contract_tc_smem(int precision, int HW);
+size_t contract_tc_nbuf_smem(int precision, int HW, int nbuf);
 size_t contract_tc_prep_bytes(const Plan& P, int precision);
+// tensor-core batches: rhs groups a plan's operand buffer holds, the split of one instance's forces, its job
+// record, and the persistent launch over a queue of items (job, k, pad tile, rhs group)
+int contract_tc_max_rpc(const Plan& P);
+bool contract_tc_rpc_fits(const Plan& P, int rpc);
+cudaError_t contract_tc_prep(const Plan& P, const double* fh, int rpc, int n_rhs, int k0, int n_modes, cudaStream_t st);
+TcJob contract_tc_job(const Plan& P, int n_rhs, int rpc, int nbuf);
+cudaError_t launch_contract_tc_batch(int precision, const TcJob* d_jobs, const int4* d_items, int n_items,
+                                     int* d_counter, int grid, size_t smem, int wl, int* status, cudaStream_t st);
 inline bool is_tensor_precision(int p) { return p == FBC_PREC_TF32 || p == FBC_PREC_BF16X2 || p == FBC_PREC_BF16X3; }
 int batch_rhs_block();
 LineArgs make_line_args(const Plan& P, const double* f, double* u);

@@ -1,11 +1,13 @@
 """Run one configuration of the pad update (or of the surrogate network) a
 few times, for a profiler to capture.
 
-    python -m paper_2105_08798_gb300.profile_case --workload NAME --precision P [--applies N]
+    python -m paper_2105_08798_gb300.profile_case --workload NAME --precision P [--applies N] [--rhs R] [--L L]
     python -m paper_2105_08798_gb300.profile_case --mlp-rows N [--width H] [--applies N]
 
 The first form builds a plan for a named workload, tabulates it and runs
-``--applies`` pad updates at the given precision on device-resident inputs;
+``--applies`` pad updates at the given precision on device-resident inputs
+(``--rhs R``, ``--L L``: the workload's ring geometry with R right-hand sides
+and L repeats, for a capture that holds fewer bytes on the device);
 the second runs the fused surrogate network on N rows of random features.
 Exits non-zero on any error; prints one line of timings.
 """
@@ -22,6 +24,8 @@ def main(argv=None) -> int:
     ap.add_argument("--workload", default="ring4000x6000_L256_rhs64_iso")
     ap.add_argument("--precision", default="bf16x2")
     ap.add_argument("--applies", type=int, default=2)
+    ap.add_argument("--rhs", type=int, default=0, help="right-hand sides (default: the workload's)")
+    ap.add_argument("--L", type=int, default=0, help="repeats along the line (default: the workload's)")
     ap.add_argument("--mlp-rows", type=int, default=0)
     ap.add_argument("--width", type=int, default=128)
     args = ap.parse_args(argv)
@@ -41,11 +45,13 @@ def main(argv=None) -> int:
         print(f"surrogate forward: {args.applies} x {args.mlp_rows} rows, width {args.width}")
         return 0
     w = inputs.WORKLOADS[args.workload]
+    R = args.rhs if args.rhs > 0 else w.n_rhs
+    L = args.L if args.L > 0 else w.L
     xy_i, xy_p = w.geometry()
-    with fbc.Plan(xy_i, xy_p, w.L, w.material, precision=args.precision, max_rhs=w.n_rhs) as plan:
+    with fbc.Plan(xy_i, xy_p, L, w.material, precision=args.precision, max_rhs=R) as plan:
         plan.tabulate()
-        fd = torch.from_numpy(w.forces()).cuda()
-        ud = torch.zeros((w.n_rhs, w.n_p, w.L, 3), dtype=torch.float64, device="cuda")
+        fd = torch.from_numpy(inputs.forces(R, w.n_i, L, w.seed)).cuda()
+        ud = torch.zeros((R, w.n_p, L, 3), dtype=torch.float64, device="cuda")
         torch.cuda.synchronize()
         times = []
         for _ in range(args.applies):
@@ -54,7 +60,7 @@ def main(argv=None) -> int:
             torch.cuda.synchronize()
             times.append(time.perf_counter() - t0)
         plan.sync_status()
-    print(f"{w.name} {args.precision}: applies " + " ".join(f"{t * 1e3:.1f} ms" for t in times))
+    print(f"{w.name} L {L} rhs {R} {args.precision}: applies " + " ".join(f"{t * 1e3:.1f} ms" for t in times))
     return 0
 
 

@@ -54,8 +54,10 @@ def test_struct_layout_matches_header(tmp_path):
 #include "fbc.h"
 #define P(T, f) printf("%s.%s %zu\n", #T, #f, offsetof(T, f));
 int main(void) {
-  printf("fbc_geometry %zu\nfbc_material %zu\nfbc_options %zu\nfbc_plan_info %zu\n",
-         sizeof(fbc_geometry), sizeof(fbc_material), sizeof(fbc_options), sizeof(fbc_plan_info));
+  printf("fbc_geometry %zu\nfbc_material %zu\nfbc_options %zu\nfbc_plan_info %zu\nfbc_batch_info %zu\n",
+         sizeof(fbc_geometry), sizeof(fbc_material), sizeof(fbc_options), sizeof(fbc_plan_info),
+         sizeof(fbc_batch_info));
+  P(fbc_batch_info, smem_contract) P(fbc_batch_info, pair_modes) P(fbc_batch_info, rhs_per_cta)
   P(fbc_geometry, c) P(fbc_geometry, xy_i) P(fbc_geometry, xy_p)
   P(fbc_material, mu) P(fbc_material, C44) P(fbc_material, Q)
   P(fbc_options, max_rhs) P(fbc_options, flags)
@@ -72,6 +74,7 @@ int main(void) {
     assert int(vals["fbc_material"]) == ctypes.sizeof(fbc.fbc_material)
     assert int(vals["fbc_options"]) == ctypes.sizeof(fbc.fbc_options)
     assert int(vals["fbc_plan_info"]) == ctypes.sizeof(fbc.fbc_plan_info)
+    assert int(vals["fbc_batch_info"]) == ctypes.sizeof(fbc.fbc_batch_info)
     for key, v in vals.items():
         if "." in key:
             t, f = key.split(".")

@@ -7,6 +7,9 @@
   (directly and replayed from a CUDA graph), reproduces each plan's own
   fbc_apply bit for bit, and the oracle within the FP64 tolerance; graph
   replays are deterministic; the autotuner keeps results unchanged.
+* The same for the tensor-core forms (one persistent tcgen05 launch over the
+  items of all instances, k = 0 in double-float), including the autotuner's
+  choice of the rhs group (right-hand sides per work item).
 """
 
 import numpy as np
@@ -70,7 +73,7 @@ def _make(fbc, prec):
     return plans, fs, us, ref_u
 
 
-@pytest.mark.parametrize("prec", ["fp64", "f32x2", "fp32"])
+@pytest.mark.parametrize("prec", ["fp64", "f32x2", "fp32", "bf16x2", "tf32", "bf16x3"])
 def test_batch_matches_per_plan_apply(fbc, prec):
     plans, fs, us, ref_u = _make(fbc, prec)
     for p, f, u in zip(plans, fs, ref_u):
@@ -123,5 +126,41 @@ def test_batch_rejects_bad_input(fbc):
     plans[1].set_precision("fp32")
     with pytest.raises(fbc.FBCError):
         fbc.Batch(plans[:2], fs[:2], us[:2])  # mixed precisions
+    for p in plans:
+        p.close()
+
+
+def test_tensor_batch_autotune_and_oracle(fbc, oracle_mod):
+    cases = [(200, 300, 32, 16), (120, 180, 16, 16), (260, 390, 64, 16)]
+    plans, fs, outs = [], [], []
+    for idx, (n_i, n_p, L, R) in enumerate(cases):
+        xy_i, xy_p = inputs.ring_geometry(n_i, n_p)
+        p = fbc.Plan(xy_i, xy_p, L, ISO, precision="bf16x2", max_rhs=R)
+        p.tabulate()
+        plans.append(p)
+        fs.append(torch.from_numpy(inputs.forces(R, n_i, L, seed=200 + idx, decay=0.5)).cuda())
+        outs.append(torch.zeros((R, n_p, L, 3), dtype=torch.float64, device="cuda"))
+    with fbc.Batch(plans, fs, outs) as b:
+        b.apply()
+        torch.cuda.synchronize()
+        first = [o.clone() for o in outs]
+        ms = b.autotune()
+        assert ms > 0
+        info = b.info()
+        assert info["rhs_per_cta"] in (16, 8)
+        b.apply()
+        torch.cuda.synchronize()
+        assert all(torch.equal(a, o) for a, o in zip(first, outs))
+        plans[0].sync_status()
+    # each instance against its own apply, and one against the oracle (BF16x2 level; k = 0 FP64-accurate)
+    for p, f, o in zip(plans, fs, first):
+        u = torch.zeros_like(o)
+        p.apply(f, u)
+        torch.cuda.synchronize()
+        assert torch.equal(u, o)
+    n_i, n_p, L, R = cases[0]
+    xy_i, xy_p = inputs.ring_geometry(n_i, n_p)
+    ref = oracle_mod.pad_update(xy_i, xy_p, L, 1.0, ISO, fs[0][:2].cpu().numpy())
+    assert rel_l2(first[0][:2].cpu().numpy(), ref) <= 1e-4
     for p in plans:
         p.close()

@@ -201,3 +201,39 @@ def test_paper_scale_cubic_sampled(fbc, oracle_mod):
         sel = got[0, samples[:, 0], samples[:, 1]]
         assert rel_l2(sel, ref) <= TOL_FP64, prec
     plan.close()
+
+
+@pytest.mark.parametrize("R,n_i,n_p,L", [(7, 200, 300, 16), (64, 130, 260, 8)], ids=["R7-ragged", "R64"])
+def test_multi_rhs_double_float_tile_bits(fbc, oracle_mod, R, n_i, n_p, L):
+    """The multi-rhs double-float tile (several right-hand sides per thread, used for n_rhs >= 2) gives every
+    right-hand side the same bits as an apply of that right-hand side alone (one-rhs tile): the products,
+    their order and the fold per interface tile are the same.  Also for the k = 0 one-mode launch of the
+    FP32 and tensor-core forms.  Right-hand side 0 against the oracle at 1e-12; a ragged last group."""
+    torch_ = pytest.importorskip("torch")
+    xy_i, xy_p = inputs.ring_geometry(n_i, n_p)
+    f = inputs.forces(R, n_i, L, seed=41)
+    fd = torch_.from_numpy(f).cuda()
+    for prec in ("f32x2", "bf16x2"):
+        with fbc.Plan(xy_i, xy_p, L, ISO, precision=prec, max_rhs=R) as plan:
+            plan.tabulate()
+            u = torch_.zeros((R, n_p, L, 3), dtype=torch_.float64, device="cuda")
+            plan.apply(fd, u)
+            torch_.cuda.synchronize()
+            plan.sync_status()
+            many = u.cpu().numpy()
+            one = np.empty_like(many)
+            for r in range(R):
+                u1 = torch_.zeros((1, n_p, L, 3), dtype=torch_.float64, device="cuda")
+                plan.apply(fd[r:r + 1].contiguous(), u1)
+                torch_.cuda.synchronize()
+                one[r] = u1[0].cpu().numpy()
+            plan.sync_status()
+        if prec == "f32x2":
+            assert np.array_equal(many, one)
+            ref = oracle_mod.pad_update(xy_i, xy_p, L, 1.0, ISO, f[:1])
+            assert rel_l2(many[:1], ref) <= 1e-12
+        else:
+            # the k = 0 mode comes from the double-float tile in both cases: equal bits in that band
+            k0_many = many.sum(axis=2)
+            k0_one = one.sum(axis=2)
+            assert np.abs(k0_many - k0_one).max() <= 1e-12 * np.abs(k0_one).max()
