@@ -763,6 +763,8 @@ def run_batch(args):
                    "pair_modes": pm, "precision": prec, "l2": "flushed between steps (256 MB write)",
                    "graph": True, "parallelism": "single"},
         "batch": {"autotuned_contract_ms": tune_ms, "rhs_per_cta": info.get("rhs_per_cta"),
+                  "launch_form": ["one persistent launch over all items", "per-instance launches in the graph"][
+                      info.get("launch_form", 0)],
                   "grid": info["grid"], "lpt_order": info["lpt_order"], "work_items": info["n_contract_items"],
                   "kernel_launches": info["kernel_launches"]},
         "rel_l2_vs_oracle": errors, "setup_s": setup_s, "variants": variants,

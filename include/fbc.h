@@ -333,7 +333,7 @@ typedef struct fbc_batch_info {
     size_t smem_contract;       /* dynamic shared memory of the contraction CTAs */
     double pair_modes;          /* sum over instances of n_p n_i K n_rhs */
     int32_t rhs_per_cta;        /* right-hand sides per contraction work item (tensor forms: the tuned group) */
-    int32_t reserved;
+    int32_t launch_form;        /* tensor forms: 0 one persistent launch over all items, 1 per-instance launches */
 } fbc_batch_info;
 
 /* Bind n_plans tabulated plans (same precision, each at most once) to their
@@ -354,13 +354,15 @@ int fbc_batch_create(fbc_plan* const* plans, int32_t n_plans, const double* cons
  * one batch, or of batches sharing a plan, concurrently. */
 int fbc_batch_apply(fbc_batch* batch, double alpha, double beta, uint32_t flags, void* stream);
 
-/* Time the contraction launch for each candidate configuration and keep the
- * fastest (synchronous; reallocates the queue): both queue orders (longest
- * first, instance-major) and, for the CUDA-core forms, a few persistent grid
- * sizes; for the tensor-core forms the rhs group (right-hand sides per work
- * item, i.e. the N = 2 rhs of the tensor-core tile: the plans' largest, then
- * halves down to 8).  No candidate changes the results.  *best_ms (may be
- * NULL) receives the chosen configuration's contraction time. */
+/* Time the contraction for each candidate configuration and keep the fastest
+ * (synchronous; reallocates the queue): both queue orders (longest first,
+ * instance-major) and, for the CUDA-core forms, a few persistent grid sizes;
+ * for the tensor-core forms the launch form (one persistent launch over the
+ * items of all instances, or each instance's own launches inside the graph)
+ * and the queue's rhs group (right-hand sides per work item, i.e. the N = 2
+ * rhs of the tensor-core tile: the plans' largest, then halves down to 8).
+ * No candidate changes the results.  *best_ms (may be NULL) receives the
+ * chosen configuration's contraction time. */
 int fbc_batch_autotune(fbc_batch* batch, void* stream, double* best_ms);
 
 int fbc_batch_info_get(const fbc_batch* batch, fbc_batch_info* info);

@@ -8,19 +8,24 @@
 // The persistent kernel's CTAs take work with atomicAdd on a counter that is
 // reset by the graph; no CTA waits for another, so nothing can spin.
 //
-// Tensor-core batches (TF32, BF16x2, BF16x3): the k = 0 items run on the
-// double-float tile (as in a single plan), each instance's force operand is
-// split into its plan's buffer, and the modes k >= 1 of all instances run in
-// one persistent tensor-core launch (one CTA per SM) over a queue of items
-// (instance, mode, pad tile, rhs group).
+// Tensor-core batches (TF32, BF16x2, BF16x3) have two launch forms for the
+// contraction.  Queue: the k = 0 items run on the double-float tile in the
+// persistent CUDA-core launch, each instance's force operand is split into its
+// plan's buffer, and the modes k >= 1 of all instances run in one persistent
+// tensor-core launch (one CTA per SM) over a queue of items (instance, mode,
+// pad tile, rhs group).  Per instance: the graph holds, for each instance, the
+// launches of its own apply (k = 0 multi-rhs double-float tile, force split,
+// tensor-core grid) -- when every instance fills the GPU by itself, this
+// avoids the queue's per-item overhead.  Both give each instance's own bits.
 //
 // Autotuning: the order of the contraction queue (LPT or the natural
 // instance-major order) and, for the CUDA-core forms, the persistent grid
 // size (resident CTAs per SM times the SM count, or fewer); for the tensor
-// forms the rhs group -- right-hand sides per CTA, i.e. the N of the
-// tensor-core tile (N = 2 x rhs) -- which trades the table gathers (once per
-// group) against the number of items and their balance.  Each candidate is
-// timed on the contraction launch; none changes the results.
+// forms the launch form and, for the queue, the rhs group -- right-hand sides
+// per CTA, i.e. the N of the tensor-core tile (N = 2 x rhs) -- which trades
+// the table gathers (once per group) against the number of items and their
+// balance.  Each candidate is timed on the contraction; none changes the
+// results.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -47,7 +52,9 @@ struct fbc_batch {
     std::vector<int> n_rhs;
     std::vector<Item> con_items[2];  // natural order; [0]: k = 0 items of an FP32 batch, [1]: the rest
     std::vector<int4> fwd, proj, inv, zm;
-    // tensor-core forms: rhs per CTA (one value for the batch, capped per instance), jobs and their items
+    // tensor-core forms: launch form (0: persistent queue, 1: per-instance launches), rhs per CTA of the queue
+    // (one value for the batch, capped per instance), jobs and their items
+    int tc_form = 0;
     int rpc = 0;
     std::vector<fbc::TcJob> tc_jobs;
     fbc::TcJob* d_tc_jobs = nullptr;
@@ -142,12 +149,30 @@ std::vector<int4> ordered_items(const fbc_batch* b, int phase, bool lpt) {
     return out;
 }
 
+cudaError_t enqueue_contract(fbc_batch* b, cudaStream_t st);
+
 // Enqueue the whole batched update on `st` (direct launches, no graph).
 cudaError_t enqueue(fbc_batch* b, double alpha, double beta, uint32_t flags, cudaStream_t st) {
     cudaError_t e;
     const bool project = flags & FBC_APPLY_PROJECT_NEUTRAL, zmean = flags & FBC_APPLY_ZERO_MEAN_U;
     if ((e = fbc::launch_batch_line(0, b->d_largs, b->d_fwd, (int)b->fwd.size(), b->smem_line, 0, 0, 0, st, fbc::line_fp32(b->precision)))) return e;
     if (project && (e = fbc::launch_batch_line(1, b->d_largs, b->d_proj, (int)b->proj.size(), 0, 0, 0, 0, st, fbc::line_fp32(b->precision)))) return e;
+    if ((e = enqueue_contract(b, st))) return e;
+    if ((e = fbc::launch_batch_line(2, b->d_largs, b->d_inv, (int)b->inv.size(), b->smem_line, alpha, beta,
+                                    zmean ? 1 : 0, st, fbc::line_fp32(b->precision))))
+        return e;
+    if (zmean && (e = fbc::launch_batch_line(3, b->d_largs, b->d_zm, (int)b->zm.size(), 0, 0, 0, 0, st, fbc::line_fp32(b->precision)))) return e;
+    return cudaSuccess;
+}
+
+// The contraction of every instance (after the forward transforms, before the inverse ones).
+cudaError_t enqueue_contract(fbc_batch* b, cudaStream_t st) {
+    cudaError_t e;
+    if (tensor(b) && b->tc_form == 1) {
+        for (int i = 0; i < b->n; i++)
+            if ((e = fbc::launch_contract(b->plans[i]->p, b->n_rhs[i], st))) return e;
+        return cudaSuccess;
+    }
     if ((e = cudaMemsetAsync(b->d_counter, 0, 2 * sizeof(int), st))) return e;
     for (int ph = 0; ph < 2; ph++) {
         if (ph == 1 && tensor(b)) {
@@ -169,10 +194,6 @@ cudaError_t enqueue(fbc_batch* b, double alpha, double beta, uint32_t flags, cud
                                             b->smem_con[ph], st)))
             return e;
     }
-    if ((e = fbc::launch_batch_line(2, b->d_largs, b->d_inv, (int)b->inv.size(), b->smem_line, alpha, beta,
-                                    zmean ? 1 : 0, st, fbc::line_fp32(b->precision))))
-        return e;
-    if (zmean && (e = fbc::launch_batch_line(3, b->d_largs, b->d_zm, (int)b->zm.size(), 0, 0, 0, 0, st, fbc::line_fp32(b->precision)))) return e;
     return cudaSuccess;
 }
 
@@ -264,7 +285,9 @@ int fbc_batch_create(fbc_plan* const* plans, int32_t n_plans, const double* cons
         delete b;
         return bfail(FBC_ERR_UNSUPPORTED, "an instance's staged sub-box exceeds shared memory");
     }
-    b->smem_line = fbc::batch_line_smem(max_L);
+    b->smem_line = 0;
+    for (int i = 0; i < n_plans; i++)
+        b->smem_line = std::max(b->smem_line, fbc::line_args_smem(la[i], fbc::line_fp32(prec)));
     std::vector<int> nr(b->n_rhs);
     cudaError_t e = cudaSuccess;
     if (!e) e = upload(&b->d_largs, la);
@@ -337,48 +360,41 @@ int fbc_batch_autotune(fbc_batch* b, void* stream, double* best_ms) {
     cudaError_t e = fbc::launch_batch_line(0, b->d_largs, b->d_fwd, (int)b->fwd.size(), b->smem_line, 0, 0, 0, st, fbc::line_fp32(b->precision));
     const int ph = 1;
     if (!e && tensor(b)) {
-        // rhs group (largest first, then halves that keep N = 2 rhs a multiple of 16) x queue order
+        // candidates: per-instance launches, and the queue with each rhs group (largest first, then halves
+        // that keep N = 2 rhs a multiple of 16) in both orders; each timed on the whole contraction
         int max_rpc = 1;
         for (int i = 0; i < b->n; i++) max_rpc = std::max(max_rpc, fbc::contract_tc_max_rpc(b->plans[i]->p));
-        std::vector<int> cands;
-        for (int r = max_rpc; r >= 8; r /= 2) cands.push_back(r);
+        struct Cand { int form, rpc, lpt; };
+        std::vector<Cand> cands = {{1, b->rpc, b->lpt}};
+        for (int r = max_rpc; r >= 8; r /= 2)
+            for (int lpt = 1; lpt >= 0; lpt--) cands.push_back({0, r, lpt});
         double best = 1e300;
-        int best_rpc = b->rpc, best_lpt = b->lpt;
-        const fbc::Plan& P0 = b->plans[0]->p;
-        const int wl = P0.wait_limit > 0 ? P0.wait_limit : (1 << 24);
-        for (int rpc : cands) {
-            b->rpc = rpc;
-            build_tc_items(b);
-            if ((e = upload(&b->d_tc_jobs, b->tc_jobs))) break;
-            for (int i = 0; i < b->n && !e; i++) {
-                const fbc::Plan& P = b->plans[i]->p;
-                if (P.K > 1) e = fbc::contract_tc_prep(P, P.d_fh, inst_rpc(b, i), b->n_rhs[i], 1, P.K - 1, st);
+        Cand bestc = cands[0];
+        for (const Cand& c : cands) {
+            b->tc_form = c.form, b->rpc = c.rpc, b->lpt = c.lpt;
+            if (c.form == 0) {
+                build_tc_items(b);
+                if ((e = upload(&b->d_tc_jobs, b->tc_jobs))) break;
+                if ((e = upload(&b->d_con[1], ordered_items(b, 1, c.lpt == 1)))) break;
             }
-            for (int lpt = 1; lpt >= 0 && !e; lpt--) {
-                if ((e = upload(&b->d_con[ph], ordered_items(b, ph, lpt == 1)))) break;
-                float ms_sum = 0.0f;
-                for (int rep = 0; rep < 2 && !e; rep++) {
-                    if ((e = cudaMemsetAsync(b->d_counter + ph, 0, sizeof(int), st))) break;
-                    cudaEventRecord(e0, st);
-                    e = fbc::launch_contract_tc_batch(b->precision, b->d_tc_jobs, b->d_con[ph],
-                                                      (int)b->con_items[ph].size(), b->d_counter + ph, b->grid[ph],
-                                                      b->smem_tc, wl, P0.d_status, st);
-                    cudaEventRecord(e1, st);
-                    if (!e) e = cudaEventSynchronize(e1);
-                    float ms = 0.0f;
-                    cudaEventElapsedTime(&ms, e0, e1);
-                    if (rep == 1) ms_sum += ms;  // the first repetition warms caches
-                }
-                if (!e && ms_sum < best) best = ms_sum, best_rpc = rpc, best_lpt = lpt;
+            float ms_sum = 0.0f;
+            for (int rep = 0; rep < 2 && !e; rep++) {
+                cudaEventRecord(e0, st);
+                e = enqueue_contract(b, st);
+                cudaEventRecord(e1, st);
+                if (!e) e = cudaEventSynchronize(e1);
+                float ms = 0.0f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (rep == 1) ms_sum += ms;  // the first repetition warms caches
             }
             if (e) break;
+            if (ms_sum < best) best = ms_sum, bestc = c;
         }
         if (!e) {
-            b->rpc = best_rpc;
-            b->lpt = best_lpt;
+            b->tc_form = bestc.form, b->rpc = bestc.rpc, b->lpt = bestc.lpt;
             build_tc_items(b);
             e = upload(&b->d_tc_jobs, b->tc_jobs);
-            if (!e) e = upload(&b->d_con[ph], ordered_items(b, ph, best_lpt == 1));
+            if (!e) e = upload(&b->d_con[1], ordered_items(b, 1, bestc.lpt == 1));
         }
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
@@ -431,11 +447,16 @@ int fbc_batch_info_get(const fbc_batch* b, fbc_batch_info* info) {
     info->lpt_order = b->lpt;
     // forward, projection, contraction (one launch per non-empty phase), inverse, zero mean (when flagged)
     info->kernel_launches = 4 + (b->con_items[0].empty() ? 0 : 1) + (b->con_items[1].empty() ? 0 : 1);
-    if (tensor(b))
+    if (tensor(b) && b->tc_form == 1) {
+        info->kernel_launches = 4;  // forward, projection, inverse, zero mean; per instance k = 0, split, tensor
+        for (const fbc_plan* pl : b->plans) info->kernel_launches += pl->p.K > 1 ? 3 : 1;
+    } else if (tensor(b)) {
         for (const fbc_plan* pl : b->plans) info->kernel_launches += pl->p.K > 1 ? 1 : 0;  // the force splits
+    }
     info->smem_contract = tensor(b) ? b->smem_tc : b->smem_con[1];
     info->pair_modes = b->pair_modes;
-    info->rhs_per_cta = tensor(b) ? b->rpc : (b->precision == FBC_PREC_FP32 ? fbc::batch_rhs_block() : 1);
+    info->rhs_per_cta = tensor(b) ? inst_rpc(b, 0) : (b->precision == FBC_PREC_FP32 ? fbc::batch_rhs_block() : 1);
+    info->launch_form = tensor(b) ? b->tc_form : 0;
     return FBC_OK;
 }
 

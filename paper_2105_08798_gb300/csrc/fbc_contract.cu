@@ -620,7 +620,7 @@ ContractArgs make_contract_args(const Plan& P) {
     A.tab = P.d_table, A.tab32 = P.d_table32;
     // the double-float kernel of an FP32 or tensor-core plan only reads k = 0: the k = 0 slice suffices
     A.tabx2 = P.d_table_x2 ? P.d_table_x2 : P.d_table_x2_k0;
-    A.fh = P.d_fh, A.uh = P.d_uh, A.xy_p = P.d_xy_p, A.off_i = P.d_off_i;
+    A.fh = P.d_fh, A.uh = P.d_uh, A.uh32 = P.d_uh32, A.xy_p = P.d_xy_p, A.off_i = P.d_off_i;
     A.bbox_a = P.d_bbox_a, A.bbox_b = P.d_bbox_b;
     A.n_tb = P.n_tb, A.K = P.K, A.Dx = P.Dx, A.Dy = P.Dy, A.box_x0 = P.box_x0, A.box_y0 = P.box_y0;
     A.W = P.W, A.H = P.H, A.NIpad = P.NIpad, A.NPpad = P.NPpad, A.k0 = 0, A.kbase = 0;

@@ -392,10 +392,10 @@ __device__ __forceinline__ void tc_item(const TcJob& J, const int4 wk, const uin
                 if (tid < kTileB / 4) cp_async16(s_off + buf * kTileB + 4 * tid, A.off_i + tB * kTileB + 4 * tid);
                 asm volatile("cp.async.commit_group;" ::: "memory");
             };
-            // Accumulators -> uh.  The FP32 accumulation in tensor memory truncates at every
-            // step, so the interface sum is split into groups of gs stages whose partial sums
-            // are added here with round-to-nearest FP32 adds (conversions on the integer
-            // pipes); the first group writes, the later ones add.
+            // Accumulators -> uh32 (the modes k >= 1 in FP32).  The FP32 accumulation in tensor
+            // memory truncates at every step, so the interface sum is split into groups of gs
+            // stages whose partial sums are added here with round-to-nearest FP32 adds; the first
+            // group writes, the later ones add.  The sums are FP32 values, kept in FP32.
             const uint32_t tacc = tmem + ((uint32_t)((warp & 3) * 32) << 16);
             auto drain = [&](bool add) {
                 for (int c0 = hb * 16; c0 < NP; c0 += 32) {
@@ -406,12 +406,12 @@ __device__ __forceinline__ void tc_item(const TcJob& J, const int4 wk, const uin
 #pragma unroll
                     for (int h = 0; h < 2; h++) {
                         // four right-hand sides at a time: every load issued before any store
-                        double2 q[4][3];
-                        double2* o[4];
+                        float2 q[4][3];
+                        float2* o[4];
 #pragma unroll
                         for (int jj = 0; jj < 4; jj++) {
                             const int r = c0 / 2 + h * 4 + jj;
-                            o[jj] = (double2*)(A.uh + (((size_t)(r0 + min(r, RG - 1)) * A.K + k) * A.NPpad + a) * 6);
+                            o[jj] = (float2*)(A.uh32 + (((size_t)(r0 + min(r, RG - 1)) * A.K + k) * A.NPpad + a) * 6);
                             if (add && r < RG) q[jj][0] = o[jj][0], q[jj][1] = o[jj][1], q[jj][2] = o[jj][2];
                         }
 #pragma unroll
@@ -420,12 +420,12 @@ __device__ __forceinline__ void tc_item(const TcJob& J, const int4 wk, const uin
                             if (r >= RG) continue;
                             float w[6] = {v0[2 * j], v1[2 * j], v2[2 * j], v0[2 * j + 1], v1[2 * j + 1], v2[2 * j + 1]};
                             if (add) {
-                                w[0] += d2f_int(q[jj][0].x), w[1] += d2f_int(q[jj][0].y), w[2] += d2f_int(q[jj][1].x);
-                                w[3] += d2f_int(q[jj][1].y), w[4] += d2f_int(q[jj][2].x), w[5] += d2f_int(q[jj][2].y);
+                                w[0] += q[jj][0].x, w[1] += q[jj][0].y, w[2] += q[jj][1].x;
+                                w[3] += q[jj][1].y, w[4] += q[jj][2].x, w[5] += q[jj][2].y;
                             }
-                            o[jj][0] = make_double2(f2d_int(w[0]), f2d_int(w[1]));
-                            o[jj][1] = make_double2(f2d_int(w[2]), f2d_int(w[3]));
-                            o[jj][2] = make_double2(f2d_int(w[4]), f2d_int(w[5]));
+                            o[jj][0] = make_float2(w[0], w[1]);
+                            o[jj][1] = make_float2(w[2], w[3]);
+                            o[jj][2] = make_float2(w[4], w[5]);
                         }
                     }
                 }

@@ -23,6 +23,7 @@
 #include <vector>
 
 #include "fbc.h"
+#include "fbc_fft.cuh"
 
 namespace fbc {
 
@@ -84,12 +85,15 @@ struct Plan {
     int2* d_used = nullptr;      // [n_used] differences that occur
     double2* d_tw = nullptr;     // [L/2] exp(-2 pi i t / L), then the same as [L/2] float2
     double2* d_twL = nullptr;    // [L] (cos, sin)(2 pi t / L) for the table DFT
+    float2* d_twl = nullptr;     // [L] exp(-2 pi i t / L) in FP32: the Stockham FP32 line transforms
+    Fft1D line_fft;              // their passes (length L)
     double* d_table = nullptr;   // [K][Dy][Dx][6] FP64
     float* d_table32 = nullptr;  // [K][Dy][Dx][6] FP32 (FBC_PREC_FP32)
     float* d_table_x2 = nullptr; // [K][Dy][Dx][12] hi/lo pairs (FBC_PREC_F32X2)
     float* d_table_x2_k0 = nullptr; // [Dy][Dx][12]: the k = 0 slice as hi/lo pairs (FP32 and tensor-core plans)
     double* d_fh = nullptr;      // [max_rhs][K][NIpad][6]
     double* d_uh = nullptr;      // [max_rhs][K][NPpad][6]
+    float* d_uh32 = nullptr;     // [max_rhs][K][NPpad][6]: the modes k >= 1 of the tensor-core forms (FP32 sums)
     double* d_part = nullptr;    // [max_rhs][n_line_blocks_p][3] zero-mean partial sums
     double* d_relax = nullptr;   // [max_rhs][kRelaxBlocks][2] dot products, then [max_rhs][n_line_blocks_p] maxima
     double* d_stage_f = nullptr; // host-apply staging
@@ -124,6 +128,7 @@ struct ContractArgs {
     const float* tabx2;  // [K][Dy][Dx][12] (hi[6], lo[6])
     const double* fh;    // [rhs][K][NIpad][6]
     double* uh;          // [rhs][K][NPpad][6]
+    float* uh32;         // [rhs][K][NPpad][6] the tensor-core forms' modes k >= 1
     const int2* xy_p;
     const int* off_i;
     const int4* bbox_a;
@@ -146,6 +151,10 @@ struct TcJob {
 
 // Everything the line transforms need about one plan (one instance of a batch).
 struct LineArgs {
+    Fft1D F;           // Stockham passes of length L (FP32 forms)
+    const float2* twl; // their twiddles
+    int stockham;      // 1: FP32 transforms in the Stockham form (L <= kLineStockhamMaxL, 16-byte aligned arrays)
+    const float* uh32; // the tensor-core forms' modes k >= 1 in FP32 (nullptr: every mode in uh)
     const double* f;   // caller forces [n_rhs][n_i][L][3]
     double* u;         // caller displacements [n_rhs][n_p][L][3]
     double* fh;
@@ -203,7 +212,9 @@ cudaError_t launch_contract_tc_batch(int precision, const TcJob* d_jobs, const i
 inline bool is_tensor_precision(int p) { return p == FBC_PREC_TF32 || p == FBC_PREC_BF16X2 || p == FBC_PREC_BF16X3; }
 int batch_rhs_block();
 LineArgs make_line_args(const Plan& P, const double* f, double* u);
-size_t batch_line_smem(int max_L);
+// dynamic shared memory of one instance's batched line transforms (FP64 or FP32 form; a batch launches
+// with the largest over its instances)
+size_t line_args_smem(const LineArgs& A, bool fp32);
 // stage 0 forward, 1 projection, 2 inverse, 3 zero mean; items as documented in fbc_line.cu
 cudaError_t launch_batch_line(int stage, const LineArgs* d_args, const int4* d_items, int n_items, size_t smem,
                               double alpha, double beta, int want_part, cudaStream_t st, bool fp32);
@@ -288,6 +299,11 @@ __device__ __forceinline__ double f2d_int(float x) {
 }
 // Record the message fbc_last_error() returns for this thread; returns code.
 int report_error(int code, const char* msg);
+
+// The FP32 line transforms run in the Stockham form up to this L (two padded buffers of 1.5 NC L FP32
+// complex numbers: 110 KB at L = 2048), when the caller's arrays are 16-byte aligned; else radix-2.
+constexpr int kLineStockhamMaxL = 2048;
+bool line_stockham(int L, const void* a, const void* b);
 
 // line-transform blocking: columns per CTA so that a CTA holds 2048 complex points
 inline int line_cols(int L) {

@@ -27,6 +27,7 @@
 // FP64 rate, while the k = 0 mode stays FP64: the forward k = 0 entries are
 // FP64 column sums, and the inverse adds the k = 0 term (a constant along the
 // line) in FP64 after an FP32 transform of the k >= 1 modes.
+#include "fbc_fft.cuh"
 #include "fbc_internal.cuh"
 
 namespace fbc {
@@ -243,7 +244,8 @@ __device__ __forceinline__ void inv_block(const double* __restrict__ uh, const i
                                           double* __restrict__ part, int n_p, int L, int logL, int K, int NPpad,
                                           int NC, double alpha_over_L, double beta, int want_part, int blk, int n_blk,
                                           int r, void* sraw, const double* __restrict__ alpha_dev = nullptr,
-                                          double alpha_dev_scale = 0.0, double* __restrict__ gmax_part = nullptr) {
+                                          double alpha_dev_scale = 0.0, double* __restrict__ gmax_part = nullptr,
+                                          const float* __restrict__ uh32 = nullptr) {
     using T2 = typename Cx<R>::T;
     constexpr bool kF32 = sizeof(R) == 4;
     const int logNC = __ffs(NC) - 1;  // NC and L are powers of two: shifts, no integer division
@@ -268,6 +270,11 @@ __device__ __forceinline__ void inv_block(const double* __restrict__ uh, const i
             if (k == 0) {
                 u0[j][0] = src[0], u0[j][1] = src[1];
                 U1r = U2r = U1i = U2i = 0.f;
+            } else if (uh32) {  // the tensor-core forms' modes k >= 1, kept in FP32
+                const float* s32 = uh32 + (((size_t)r * K + k) * NPpad + a0 + j) * 6;
+                U1r = s32[0], U2r = s32[1];
+                U1i = k == Lh ? 0.f : s32[3];
+                U2i = k == Lh ? 0.f : s32[4];
             } else {
                 const long long* sb = (const long long*)src;  // raw FP64 words
                 U1r = d2f_bits(sb[0]), U2r = d2f_bits(sb[1]);
@@ -297,6 +304,12 @@ __device__ __forceinline__ void inv_block(const double* __restrict__ uh, const i
             if (k == 0) {
                 u0[2 * jp][2] = -se[5], u0[2 * jp + 1][2] = -so[5];
                 Er = Ei = Or = Oi = 0.f;
+            } else if (uh32) {
+                const float* e32 = uh32 + (((size_t)r * K + k) * NPpad + a0 + 2 * jp) * 6;
+                const float* o32 = e32 + 6;
+                Er = -e32[5], Or = -o32[5];
+                Ei = k == Lh ? 0.f : e32[2];
+                Oi = k == Lh ? 0.f : o32[2];
             } else {
                 const long long *eb = (const long long*)se, *ob = (const long long*)so;
                 Er = -d2f_bits(eb[5]), Or = -d2f_bits(ob[5]);
@@ -424,6 +437,251 @@ __device__ __forceinline__ void inv_block(const double* __restrict__ uh, const i
     }
 }
 
+// ---- FP32 line transforms in the Stockham form ---------------------------------
+// The FP32 forms' transforms when L <= 2048 and the caller's arrays are 16-byte
+// aligned: natural order in and out, radix-8 passes in shared memory (4 passes
+// at L = 1024 instead of 10 radix-2 stages; padded index, no bank conflicts),
+// each lane of a warp moving two rows of a column [L][3] as three 16-byte
+// words, the FP64 k = 0 sums taken from the same loads, 16-byte stores of the
+// six-vectors.  The arithmetic per element is that of the radix-2 form: FP32
+// transform, k = 0 in FP64.  twl[m] = exp(-2 pi i m / L), m < L, in FP32.
+__device__ __forceinline__ void fwd_block_s(const double* __restrict__ f, const int* __restrict__ perm,
+                                            const float2* __restrict__ twl, const Fft1D& F, double* __restrict__ fh,
+                                            int n_i, int L, int K, int NIpad, int NC, int blk, int r, void* sraw) {
+    const int nseq = NC + NC / 2, logNC = __ffs(NC) - 1, Lh = L >> 1;
+    float2* A = (float2*)sraw;
+    float2* B = A + fft::padded(nseq * L);
+    __shared__ double s0[64][3];  // FP64 column sums = the k = 0 mode
+    const int b0 = blk * NC;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    // wpc warps share a column (all warps busy when the CTA holds fewer columns than warps)
+    const int wpc = nw > NC ? nw / NC : 1, sub = warp % wpc;
+    __shared__ double s0p[8][3];  // per-warp partial sums when a column is shared
+    for (int j = warp / wpc; j < NC; j += nw / wpc) {
+        const int ob = perm[b0 + j];
+        const double2* src = ob >= 0 ? (const double2*)(f + ((size_t)r * n_i + ob) * L * 3) : nullptr;
+        const int zb = j * L, wb = (NC + (j >> 1)) * L, half = j & 1;
+        double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+        for (int m = lane + 32 * sub; m < Lh; m += 32 * wpc) {
+            double2 v0 = make_double2(0.0, 0.0), v1 = v0, v2 = v0;
+            if (src) v0 = src[3 * m], v1 = src[3 * m + 1], v2 = src[3 * m + 2];
+            // row 2m: (v0.x, v0.y, v1.x); row 2m + 1: (v1.y, v2.x, v2.y)
+            a0 += v0.x, a0 += v1.y, a1 += v0.y, a1 += v2.x, a2 += v1.x, a2 += v2.y;
+            A[fft::sx(zb + 2 * m)] = make_float2(d2f_int(v0.x), d2f_int(v0.y));
+            A[fft::sx(zb + 2 * m + 1)] = make_float2(d2f_int(v1.y), d2f_int(v2.x));
+            ((float*)&A[fft::sx(wb + 2 * m)])[half] = d2f_int(v1.x);
+            ((float*)&A[fft::sx(wb + 2 * m + 1)])[half] = d2f_int(v2.y);
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            a0 += __shfl_xor_sync(0xffffffffu, a0, o);
+            a1 += __shfl_xor_sync(0xffffffffu, a1, o);
+            a2 += __shfl_xor_sync(0xffffffffu, a2, o);
+        }
+        if (lane == 0) {
+            if (wpc == 1) s0[j][0] = a0, s0[j][1] = a1, s0[j][2] = a2;
+            else s0p[warp][0] = a0, s0p[warp][1] = a1, s0p[warp][2] = a2;
+        }
+    }
+    __syncthreads();
+    if (wpc > 1 && threadIdx.x < NC * 3) {  // the warps of a column in a fixed order (deterministic)
+        const int j = threadIdx.x / 3, c = threadIdx.x % 3;
+        double a = 0.0;
+        for (int w = 0; w < wpc; w++) a += s0p[j * wpc + w][c];
+        s0[j][c] = a;
+    }
+    const float2* Y = fft::fft_smem<false>(A, B, nseq, F, twl);
+    for (int t = threadIdx.x; t < NC * K; t += blockDim.x) {
+        const int k = t >> logNC, j = t & (NC - 1);
+        double2* o = (double2*)(fh + (((size_t)r * K + k) * NIpad + b0 + j) * 6);
+        if (perm[b0 + j] < 0) {
+            o[0] = o[1] = o[2] = make_double2(0.0, 0.0);
+            continue;
+        }
+        const int km = (L - k) & (L - 1), wb = (NC + (j >> 1)) * L;
+        const float2 Z = Y[fft::sx(j * L + k)], Zm = Y[fft::sx(j * L + km)];
+        const float2 Wv = Y[fft::sx(wb + k)], Wm = Y[fft::sx(wb + km)];
+        // F1 = (Z + conj Zm) / 2, F2 = (Z - conj Zm) / (2i); F3 from W the same way (x part or y part)
+        double F1r = f2d_int(0.5f * (Z.x + Zm.x)), F1i = f2d_int(0.5f * (Z.y - Zm.y));
+        double F2r = f2d_int(0.5f * (Z.y + Zm.y)), F2i = f2d_int(-0.5f * (Z.x - Zm.x));
+        double F3r, F3i;
+        if ((j & 1) == 0) {
+            F3r = f2d_int(0.5f * (Wv.x + Wm.x)), F3i = f2d_int(0.5f * (Wv.y - Wm.y));
+        } else {
+            F3r = f2d_int(0.5f * (Wv.y + Wm.y)), F3i = f2d_int(-0.5f * (Wv.x - Wm.x));
+        }
+        if (k == 0) F1r = s0[j][0], F2r = s0[j][1], F3r = s0[j][2], F1i = F2i = F3i = 0.0;
+        o[0] = make_double2(F1r, F2r);
+        o[1] = make_double2(F3i, F1i);
+        o[2] = make_double2(F2i, -F3r);
+    }
+}
+
+__device__ __forceinline__ void inv_block_s(const double* __restrict__ uh, const int* __restrict__ perm,
+                                            const float2* __restrict__ twl, const Fft1D& F, double* __restrict__ u,
+                                            double* __restrict__ part, int n_p, int L, int K, int NPpad, int NC,
+                                            double alpha_over_L, double beta, int want_part, int blk, int n_blk,
+                                            int r, void* sraw, const double* __restrict__ alpha_dev = nullptr,
+                                            double alpha_dev_scale = 0.0, double* __restrict__ gmax_part = nullptr,
+                                            const float* __restrict__ uh32 = nullptr) {
+    const int nseq = NC + NC / 2, logNC = __ffs(NC) - 1, Lh = L >> 1;
+    float2* A = (float2*)sraw;
+    float2* B = A + fft::padded(nseq * L);
+    const int a0 = blk * NC;
+    if (alpha_dev) alpha_over_L = alpha_dev_scale * alpha_dev[r];
+    const bool max_only = gmax_part != nullptr;
+    const bool has_beta = beta != 0.0;
+    __shared__ double u0[64][3];  // FP64 k = 0 term per column
+    __shared__ double uk[64][3];
+    // Z = U1 + i U2 per column: Z(k) and Z(L - k) = conj U1 + i conj U2
+    for (int t = threadIdx.x; t < NC * K; t += blockDim.x) {
+        const int k = t >> logNC, j = t & (NC - 1);
+        const double2* src = (const double2*)(uh + (((size_t)r * K + k) * NPpad + a0 + j) * 6);
+        if (k == 0) {
+            const double2 p0 = src[0];
+            u0[j][0] = p0.x, u0[j][1] = p0.y;
+            A[fft::sx(j * L)] = make_float2(0.f, 0.f);
+            continue;
+        }
+        float U1r, U2r, U1i, U2i;
+        if (uh32) {  // the tensor-core forms' modes k >= 1, kept in FP32: (Re V1, Re V2) (Im V3, Im V1) (Im V2, -Re V3)
+            const float2* s32 = (const float2*)(uh32 + (((size_t)r * K + k) * NPpad + a0 + j) * 6);
+            const float2 q0 = s32[0], q1 = s32[1], q2 = s32[2];
+            U1r = q0.x, U2r = q0.y, U1i = k == Lh ? 0.f : q1.y, U2i = k == Lh ? 0.f : q2.x;
+        } else {
+            const double2 p0 = src[0], p1 = src[1], p2 = src[2];  // (Re V1, Re V2) (Im V3, Im V1) (Im V2, -Re V3)
+            U1r = d2f_int(p0.x), U2r = d2f_int(p0.y);
+            U1i = k == Lh ? 0.f : d2f_int(p1.y), U2i = k == Lh ? 0.f : d2f_int(p2.x);
+        }
+        A[fft::sx(j * L + k)] = make_float2(U1r - U2i, U1i + U2r);
+        if (k != Lh) A[fft::sx(j * L + L - k)] = make_float2(U1r + U2i, U2r - U1i);
+    }
+    // W = U3(even column) + i U3(odd column), with U3 = -y2 + i x2
+    for (int t = threadIdx.x; t < (NC / 2) * K; t += blockDim.x) {
+        const int k = t >> (logNC - 1), jp = t & ((NC >> 1) - 1);
+        const double* se = uh + (((size_t)r * K + k) * NPpad + a0 + 2 * jp) * 6;
+        const double* so = se + 6;
+        const int wb = (NC + jp) * L;
+        if (k == 0) {
+            u0[2 * jp][2] = -se[5], u0[2 * jp + 1][2] = -so[5];
+            A[fft::sx(wb)] = make_float2(0.f, 0.f);
+            continue;
+        }
+        float Er, Or, Ei, Oi;
+        if (uh32) {
+            const float* e32 = uh32 + (((size_t)r * K + k) * NPpad + a0 + 2 * jp) * 6;
+            Er = -e32[5], Or = -e32[11], Ei = k == Lh ? 0.f : e32[2], Oi = k == Lh ? 0.f : e32[8];
+        } else {
+            Er = -d2f_int(se[5]), Or = -d2f_int(so[5]);
+            Ei = k == Lh ? 0.f : d2f_int(se[2]), Oi = k == Lh ? 0.f : d2f_int(so[2]);
+        }
+        A[fft::sx(wb + k)] = make_float2(Er - Oi, Ei + Or);
+        if (k != Lh) A[fft::sx(wb + L - k)] = make_float2(Er + Oi, Or - Ei);
+    }
+    __syncthreads();
+    const float2* Y = fft::fft_smem<true>(A, B, nseq, F, twl);
+    // the k >= 1 modes sum to zero along the line: remove the mean their FP32 transform picked up (summed in
+    // double-float), so the k = 0 band keeps FP64 accuracy; uk[j][c] = (alpha / L) (U_c(0) - mean) in FP64
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    const int wpc = nw > NC ? nw / NC : 1, sub = warp % wpc;  // warps per column
+    // per-warp partial sums when warps share a column (wpc > 1: each warp then has exactly one column):
+    // 3 doubles per warp in the transform's other buffer, free once Y holds the result (at least
+    // 1.5 NC L = 192 FP32 complex numbers, 1536 bytes, for L = 2)
+    double* scr = (double*)(Y == A ? B : A);
+    for (int j = warp / wpc; j < NC; j += nw / wpc) {
+        const int wb = (NC + (j >> 1)) * L;
+        float h0 = 0.f, l0 = 0.f, h1 = 0.f, l1 = 0.f, h2 = 0.f, l2 = 0.f;
+        for (int p = lane + 32 * sub; p < L; p += 32 * wpc) {
+            const float2 z = Y[fft::sx(j * L + p)];
+            const float2 w = Y[fft::sx(wb + p)];
+            df_acc(z.x, h0, l0), df_acc(z.y, h1, l1), df_acc((j & 1) ? w.y : w.x, h2, l2);
+        }
+        double a0_ = f2d_int(h0) + f2d_int(l0), a1_ = f2d_int(h1) + f2d_int(l1), a2_ = f2d_int(h2) + f2d_int(l2);
+        for (int o = 16; o > 0; o >>= 1) {
+            a0_ += __shfl_xor_sync(0xffffffffu, a0_, o);
+            a1_ += __shfl_xor_sync(0xffffffffu, a1_, o);
+            a2_ += __shfl_xor_sync(0xffffffffu, a2_, o);
+        }
+        if (lane == 0) {
+            if (wpc == 1) {
+                uk[j][0] = alpha_over_L * (u0[j][0] - a0_ / L);
+                uk[j][1] = alpha_over_L * (u0[j][1] - a1_ / L);
+                uk[j][2] = alpha_over_L * (u0[j][2] - a2_ / L);
+            } else {
+                scr[3 * warp] = a0_, scr[3 * warp + 1] = a1_, scr[3 * warp + 2] = a2_;
+            }
+        }
+    }
+    __syncthreads();
+    if (wpc > 1 && threadIdx.x < NC * 3) {  // the warps of a column in a fixed order (deterministic)
+        const int j = threadIdx.x / 3, c = threadIdx.x % 3;
+        double a = 0.0;
+        for (int w = 0; w < wpc; w++) a += scr[3 * (j * wpc + w) + c];
+        uk[j][c] = alpha_over_L * (u0[j][c] - a / L);
+    }
+    __syncthreads();
+    const float af = (float)alpha_over_L;
+    float mx32 = 0.f;
+    double ps0 = 0.0, ps1 = 0.0, ps2 = 0.0;
+    for (int j = warp / wpc; j < NC; j += nw / wpc) {
+        const int oa = perm[a0 + j];
+        if (oa < 0) continue;
+        const int zb = j * L, wb = (NC + (j >> 1)) * L, half = j & 1;
+        const double k0 = uk[j][0], k1 = uk[j][1], k2 = uk[j][2];
+        double2* dst = (double2*)(u + ((size_t)r * n_p + oa) * L * 3);
+        for (int m = lane + 32 * sub; m < Lh; m += 32 * wpc) {
+            const float2 z0 = Y[fft::sx(zb + 2 * m)], z1 = Y[fft::sx(zb + 2 * m + 1)];
+            const float2 w0 = Y[fft::sx(wb + 2 * m)], w1 = Y[fft::sx(wb + 2 * m + 1)];
+            const float w0h = half ? w0.y : w0.x, w1h = half ? w1.y : w1.x;
+            if (max_only) {
+                // the cap needs |g| to FP32 accuracy: sum in FP32, no FP64 work per element
+                const float g[6] = {af * z0.x + (float)k0, af * z0.y + (float)k1, af * w0h + (float)k2,
+                                    af * z1.x + (float)k0, af * z1.y + (float)k1, af * w1h + (float)k2};
+#pragma unroll
+                for (int c = 0; c < 6; c++) mx32 = fmaxf(mx32, fabsf(g[c]));
+                continue;
+            }
+            double o[6] = {f2d_int(af * z0.x) + k0, f2d_int(af * z0.y) + k1, f2d_int(af * w0h) + k2,
+                           f2d_int(af * z1.x) + k0, f2d_int(af * z1.y) + k1, f2d_int(af * w1h) + k2};
+            if (has_beta) {
+                const double2 d0 = dst[3 * m], d1 = dst[3 * m + 1], d2 = dst[3 * m + 2];
+                o[0] = fma(beta, d0.x, o[0]), o[1] = fma(beta, d0.y, o[1]), o[2] = fma(beta, d1.x, o[2]);
+                o[3] = fma(beta, d1.y, o[3]), o[4] = fma(beta, d2.x, o[4]), o[5] = fma(beta, d2.y, o[5]);
+            }
+            dst[3 * m] = make_double2(o[0], o[1]);
+            dst[3 * m + 1] = make_double2(o[2], o[3]);
+            dst[3 * m + 2] = make_double2(o[4], o[5]);
+            if (want_part) ps0 += o[0], ps0 += o[3], ps1 += o[1], ps1 += o[4], ps2 += o[2], ps2 += o[5];
+        }
+    }
+    __shared__ double red[3 * 256];  // block reductions (the maximum, or the three partial sums)
+    if (max_only) {
+        double* redm = red;
+        redm[threadIdx.x] = (double)mx32;
+        __syncthreads();
+        for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+            if ((int)threadIdx.x < w) redm[threadIdx.x] = fmax(redm[threadIdx.x], redm[threadIdx.x + w]);
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) gmax_part[(size_t)r * n_blk + blk] = redm[0];
+        return;
+    }
+    if (want_part) {
+        red[threadIdx.x] = ps0;
+        red[256 + threadIdx.x] = ps1;
+        red[512 + threadIdx.x] = ps2;
+        __syncthreads();
+        for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+            if ((int)threadIdx.x < w)
+                for (int c = 0; c < 3; c++) red[256 * c + threadIdx.x] += red[256 * c + threadIdx.x + w];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) {
+            double* pp = part + ((size_t)r * n_blk + blk) * 3;
+            pp[0] = red[0], pp[1] = red[256], pp[2] = red[512];
+        }
+    }
+}
+
 // Zero mean of the pad displacements (Eq. 23): every CTA reduces the per-CTA
 // partial sums in the same fixed order, then subtracts from chunk c of n_chunk.
 __device__ __forceinline__ void zero_mean_chunk(double* __restrict__ u, const double* __restrict__ part, int n_part,
@@ -457,10 +715,23 @@ template <typename R>
 __global__ void k_inverse(const double* __restrict__ uh, const int* __restrict__ perm, const double2* __restrict__ tw,
                           double* __restrict__ u, double* __restrict__ part, int n_p, int L, int logL, int K, int NPpad,
                           int NC, double alpha_over_L, double beta, int want_part, const double* __restrict__ alpha_dev,
-                          double alpha_dev_scale, double* __restrict__ gmax_part) {
+                          double alpha_dev_scale, double* __restrict__ gmax_part, const float* __restrict__ uh32) {
     extern __shared__ double2 sbuf[];
     inv_block<R>(uh, perm, tw, u, part, n_p, L, logL, K, NPpad, NC, alpha_over_L, beta, want_part, blockIdx.x,
-                 gridDim.x, blockIdx.y, sbuf, alpha_dev, alpha_dev_scale, gmax_part);
+                 gridDim.x, blockIdx.y, sbuf, alpha_dev, alpha_dev_scale, gmax_part, uh32);
+}
+__global__ void k_forward_s(const double* __restrict__ f, const int* __restrict__ perm, const float2* __restrict__ twl,
+                            Fft1D F, double* __restrict__ fh, int n_i, int L, int K, int NIpad, int NC) {
+    extern __shared__ double2 sbuf[];
+    fwd_block_s(f, perm, twl, F, fh, n_i, L, K, NIpad, NC, blockIdx.x, blockIdx.y, sbuf);
+}
+__global__ void k_inverse_s(const double* __restrict__ uh, const int* __restrict__ perm, const float2* __restrict__ twl,
+                            Fft1D F, double* __restrict__ u, double* __restrict__ part, int n_p, int L, int K, int NPpad,
+                            int NC, double alpha_over_L, double beta, int want_part, const double* __restrict__ alpha_dev,
+                            double alpha_dev_scale, double* __restrict__ gmax_part, const float* __restrict__ uh32) {
+    extern __shared__ double2 sbuf[];
+    inv_block_s(uh, perm, twl, F, u, part, n_p, L, K, NPpad, NC, alpha_over_L, beta, want_part, blockIdx.x, gridDim.x,
+                blockIdx.y, sbuf, alpha_dev, alpha_dev_scale, gmax_part, uh32);
 }
 __global__ void k_zero_mean(double* __restrict__ u, const double* __restrict__ part, int n_part, int n_p, int L) {
     zero_mean_chunk(u, part, n_part, n_p, L, blockIdx.y, blockIdx.x, gridDim.x);
@@ -472,7 +743,10 @@ __global__ void k_batch_forward(const LineArgs* __restrict__ la, const int4* __r
     extern __shared__ double2 sbuf[];
     const int4 w = items[blockIdx.x];
     const LineArgs A = la[w.x];
-    fwd_block<R>(A.f, A.perm_i, A.tw, A.fh, A.n_i, A.L, A.logL, A.K, A.NIpad, A.NC, w.y, w.z, sbuf);
+    if (sizeof(R) == 4 && A.stockham)
+        fwd_block_s(A.f, A.perm_i, A.twl, A.F, A.fh, A.n_i, A.L, A.K, A.NIpad, A.NC, w.y, w.z, sbuf);
+    else
+        fwd_block<R>(A.f, A.perm_i, A.tw, A.fh, A.n_i, A.L, A.logL, A.K, A.NIpad, A.NC, w.y, w.z, sbuf);
 }
 __global__ void k_batch_project(const LineArgs* __restrict__ la, const int4* __restrict__ items) {
     const int4 w = items[blockIdx.x];
@@ -485,8 +759,12 @@ __global__ void k_batch_inverse(const LineArgs* __restrict__ la, const int4* __r
     extern __shared__ double2 sbuf[];
     const int4 w = items[blockIdx.x];
     const LineArgs A = la[w.x];
-    inv_block<R>(A.uh, A.perm_p, A.tw, A.u, A.part, A.n_p, A.L, A.logL, A.K, A.NPpad, A.NC, alpha / (double)A.L, beta,
-              want_part, w.y, A.NPpad / A.NC, w.z, sbuf);
+    if (sizeof(R) == 4 && A.stockham)
+        inv_block_s(A.uh, A.perm_p, A.twl, A.F, A.u, A.part, A.n_p, A.L, A.K, A.NPpad, A.NC, alpha / (double)A.L,
+                    beta, want_part, w.y, A.NPpad / A.NC, w.z, sbuf, nullptr, 0.0, nullptr, A.uh32);
+    else
+        inv_block<R>(A.uh, A.perm_p, A.tw, A.u, A.part, A.n_p, A.L, A.logL, A.K, A.NPpad, A.NC, alpha / (double)A.L,
+                     beta, want_part, w.y, A.NPpad / A.NC, w.z, sbuf, nullptr, 0.0, nullptr, A.uh32);
 }
 __global__ void k_batch_zero_mean(const LineArgs* __restrict__ la, const int4* __restrict__ items) {
     const int4 w = items[blockIdx.x];  // (instance, chunk, r, n_chunk)
@@ -495,8 +773,14 @@ __global__ void k_batch_zero_mean(const LineArgs* __restrict__ la, const int4* _
 }
 
 size_t line_smem(int L, int NC) { return (size_t)(NC + NC / 2) * L * sizeof(double2); }
+// the Stockham FP32 form: two padded buffers of FP32 complex numbers
+size_t line_smem_s(int L, int NC) { return (size_t)2 * fft::padded((NC + NC / 2) * L) * sizeof(float2); }
 
 }  // namespace
+
+bool line_stockham(int L, const void* a, const void* b) {
+    return L >= 2 && L <= kLineStockhamMaxL && ((uintptr_t)a & 15) == 0 && ((uintptr_t)b & 15) == 0;
+}
 
 cudaError_t launch_forward(Plan& P, const double* f, int n_rhs, bool project, cudaStream_t st) {
     const int NC = line_cols(P.L);
@@ -504,7 +788,11 @@ cudaError_t launch_forward(Plan& P, const double* f, int n_rhs, bool project, cu
     cudaError_t e;
     // opt in above the default dynamic limit (the kernel's static arrays count towards 48 KB)
     dim3 grid(P.NIpad / NC, n_rhs);
-    if (line_fp32(P.precision)) {
+    if (line_fp32(P.precision) && line_stockham(P.L, f, P.d_fh)) {
+        const size_t ss = line_smem_s(P.L, NC);
+        if ((e = cudaFuncSetAttribute(k_forward_s, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ss))) return e;
+        k_forward_s<<<grid, 256, ss, st>>>(f, P.d_perm_i, P.d_twl, P.line_fft, P.d_fh, P.n_i, P.L, P.K, P.NIpad, NC);
+    } else if (line_fp32(P.precision)) {
         if ((e = cudaFuncSetAttribute(k_forward<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem))) return e;
         k_forward<float><<<grid, 256, smem / 2, st>>>(f, P.d_perm_i, P.d_tw, P.d_fh, P.n_i, P.L, P.logL, P.K, P.NIpad, NC);
     } else {
@@ -526,16 +814,24 @@ cudaError_t launch_inverse(Plan& P, double* u, int n_rhs, double alpha, double b
     cudaError_t e;
     const int nb = P.NPpad / NC;
     dim3 grid(nb, n_rhs);
-    if (line_fp32(P.precision)) {
+    // the tensor-core forms leave their modes k >= 1 in FP32 (k = 0 in the FP64 buffer)
+    const float* uh32 = is_tensor_precision(P.precision) ? P.d_uh32 : nullptr;
+    if (line_fp32(P.precision) && line_stockham(P.L, u, P.d_uh)) {
+        const size_t ss = line_smem_s(P.L, NC);
+        if ((e = cudaFuncSetAttribute(k_inverse_s, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ss))) return e;
+        k_inverse_s<<<grid, 256, ss, st>>>(P.d_uh, P.d_perm_p, P.d_twl, P.line_fft, u, P.d_part, P.n_p, P.L, P.K, P.NPpad,
+                                           NC, alpha / (double)P.L, beta, zero_mean ? 1 : 0, alpha_dev, alpha_dev_scale,
+                                           gmax_part, uh32);
+    } else if (line_fp32(P.precision)) {
         if ((e = cudaFuncSetAttribute(k_inverse<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem))) return e;
         k_inverse<float><<<grid, 256, smem / 2, st>>>(P.d_uh, P.d_perm_p, P.d_tw, u, P.d_part, P.n_p, P.L, P.logL, P.K,
                                                       P.NPpad, NC, alpha / (double)P.L, beta, zero_mean ? 1 : 0,
-                                                      alpha_dev, alpha_dev_scale, gmax_part);
+                                                      alpha_dev, alpha_dev_scale, gmax_part, uh32);
     } else {
         if ((e = cudaFuncSetAttribute(k_inverse<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem))) return e;
         k_inverse<double><<<grid, 256, smem, st>>>(P.d_uh, P.d_perm_p, P.d_tw, u, P.d_part, P.n_p, P.L, P.logL, P.K,
                                                    P.NPpad, NC, alpha / (double)P.L, beta, zero_mean ? 1 : 0,
-                                                   alpha_dev, alpha_dev_scale, gmax_part);
+                                                   alpha_dev, alpha_dev_scale, gmax_part, nullptr);
     }
     if ((e = cudaGetLastError())) return e;
     if (zero_mean && !gmax_part) {
@@ -553,10 +849,18 @@ LineArgs make_line_args(const Plan& P, const double* f, double* u) {
     A.part = P.d_part;
     A.n_i = P.n_i, A.n_p = P.n_p, A.L = P.L, A.logL = P.logL, A.K = P.K, A.NIpad = P.NIpad, A.NPpad = P.NPpad;
     A.NC = line_cols(P.L);
+    A.F = P.line_fft;
+    A.twl = P.d_twl;
+    A.uh32 = is_tensor_precision(P.precision) ? P.d_uh32 : nullptr;
+    A.stockham = line_fp32(P.precision) && line_stockham(P.L, f, P.d_fh) && line_stockham(P.L, u, P.d_uh) ? 1 : 0;
     return A;
 }
 
-size_t batch_line_smem(int max_L) { return line_smem(max_L, line_cols(max_L)); }
+// Dynamic shared memory one instance's line transforms need in its form (the batch launches with the largest).
+size_t line_args_smem(const LineArgs& A, bool fp32) {
+    if (!fp32) return line_smem(A.L, A.NC);
+    return A.stockham ? line_smem_s(A.L, A.NC) : line_smem(A.L, A.NC) / 2;
+}
 
 cudaError_t launch_batch_line(int stage, const LineArgs* d_args, const int4* d_items, int n_items, size_t smem,
                               double alpha, double beta, int want_part, cudaStream_t st, bool fp32) {
@@ -568,7 +872,7 @@ cudaError_t launch_batch_line(int stage, const LineArgs* d_args, const int4* d_i
                 if ((e = cudaFuncSetAttribute(k_batch_forward<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                               (int)smem)))
                     return e;
-                k_batch_forward<float><<<n_items, 256, smem / 2, st>>>(d_args, d_items);
+                k_batch_forward<float><<<n_items, 256, smem, st>>>(d_args, d_items);
             } else {
                 if ((e = cudaFuncSetAttribute(k_batch_forward<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                               (int)smem)))
@@ -584,7 +888,7 @@ cudaError_t launch_batch_line(int stage, const LineArgs* d_args, const int4* d_i
                 if ((e = cudaFuncSetAttribute(k_batch_inverse<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                               (int)smem)))
                     return e;
-                k_batch_inverse<float><<<n_items, 256, smem / 2, st>>>(d_args, d_items, alpha, beta, want_part);
+                k_batch_inverse<float><<<n_items, 256, smem, st>>>(d_args, d_items, alpha, beta, want_part);
             } else {
                 if ((e = cudaFuncSetAttribute(k_batch_inverse<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                               (int)smem)))

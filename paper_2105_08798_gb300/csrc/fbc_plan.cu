@@ -192,9 +192,9 @@ int dev_alloc(T** p, size_t count, size_t& acc, const char* what) {
 
 void free_plan(fbc::Plan& P) {
     void* bufs[] = {P.d_xy_p,  P.d_off_i,    P.d_bbox_a, P.d_bbox_b, P.d_perm_i, P.d_perm_p,
-                    P.d_used,  P.d_tw,       P.d_twL,    P.d_table,  P.d_table32, P.d_table_x2, P.d_table_x2_k0,
+                    P.d_used,  P.d_tw,       P.d_twL,    P.d_twl,    P.d_table,  P.d_table32, P.d_table_x2, P.d_table_x2_k0,
                     P.d_fh,    P.d_uh,       P.d_part,   P.d_stage_f, P.d_stage_u, P.d_status, P.d_bprep,
-                    P.d_relax};
+                    P.d_relax, P.d_uh32};
     for (void* b : bufs)
         if (b) cudaFree(b);
     for (auto& e : P.ev)
@@ -226,6 +226,11 @@ int ensure_derived(fbc::Plan& P, int precision) {
             P.d_bprep = q, P.bprep_bytes = want;
         }
         P.bprep_prec = precision;
+    }
+    // the tensor-core forms' modes k >= 1: their group partials are FP32 sums, kept in FP32
+    if (fbc::is_tensor_precision(precision) && !P.d_uh32) {
+        int s = dev_alloc(&P.d_uh32, (size_t)P.opt.max_rhs * P.K * P.NPpad * 6, acc, "uh32");
+        if (s) return s;
     }
     if (precision == FBC_PREC_F32X2 && !P.d_table_x2) {
         int s = dev_alloc(&P.d_table_x2, cells * 12, acc, "table_x2");
@@ -446,6 +451,7 @@ int fbc_plan_create(const fbc_geometry* geom, const fbc_material* mat, const fbc
     ALLOC(P.d_used, P.n_used, "used");
     ALLOC(P.d_tw, L / 2 + L / 4 + 1, "twiddles");  // L/2 double2, then L/2 float2
     ALLOC(P.d_twL, L, "table_twiddles");
+    ALLOC(P.d_twl, L, "line_twiddles");
     size_t ws_before_table = acc;
     ALLOC(P.d_table, cells * 6, "table");
     P.table_bytes = acc - ws_before_table;
@@ -463,6 +469,8 @@ int fbc_plan_create(const fbc_geometry* geom, const fbc_material* mat, const fbc
     }
 
     std::vector<double2> tw(L / 2 + L / 4 + 1), twL(L);
+    std::vector<float2> twl(L);
+    P.line_fft = fbc::fft::make_fft(L);
     float2* tw32 = (float2*)(tw.data() + L / 2);  // the FP32 transforms' copy, rounded from FP64
     for (int t = 0; t < L / 2; t++) {
         double ang = 2.0 * M_PI * (double)t / (double)L;
@@ -472,6 +480,7 @@ int fbc_plan_create(const fbc_geometry* geom, const fbc_material* mat, const fbc
     for (int t = 0; t < L; t++) {
         double ang = 2.0 * M_PI * (double)t / (double)L;
         twL[t] = make_double2(cos(ang), sin(ang));
+        twl[t] = make_float2((float)cos(ang), (float)-sin(ang));
     }
     cudaError_t e = cudaSuccess;
 #define UP(dst, src, n)                                                                   \
@@ -485,6 +494,7 @@ int fbc_plan_create(const fbc_geometry* geom, const fbc_material* mat, const fbc
     if (P.n_used) UP(P.d_used, used_list.data(), P.n_used);
     UP(P.d_tw, tw.data(), L / 2 + L / 4 + 1);
     UP(P.d_twL, twL.data(), L);
+    UP(P.d_twl, twl.data(), L);
 #undef UP
     if (e == cudaSuccess) e = cudaMemset(P.d_table, 0, cells * 6 * sizeof(double));
     // padding columns of fh stay zero for ever: the forward transform never writes them

@@ -93,7 +93,7 @@ class fbc_batch_info(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int32) for n in ("n_plans", "precision", "n_contract_items", "grid", "occupancy",
                                               "lpt_order", "kernel_launches")] + [
         ("smem_contract", ctypes.c_size_t), ("pair_modes", ctypes.c_double), ("rhs_per_cta", ctypes.c_int32),
-        ("reserved", ctypes.c_int32)]
+        ("launch_form", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
         return {name: getattr(self, name) for name, _ in self._fields_}

@@ -148,6 +148,7 @@ def test_tensor_batch_autotune_and_oracle(fbc, oracle_mod):
         assert ms > 0
         info = b.info()
         assert info["rhs_per_cta"] in (16, 8)
+        assert info["launch_form"] in (0, 1)
         b.apply()
         torch.cuda.synchronize()
         assert all(torch.equal(a, o) for a, o in zip(first, outs))

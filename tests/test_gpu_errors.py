@@ -75,8 +75,10 @@ def test_wait_limit_argument_checks(fbc):
 
 # (allocation name, precision whose plan allocates it)
 ALLOCS = [(n, "fp64") for n in ("xy_p", "off_i", "bbox_a", "bbox_b", "perm_i", "perm_p", "used", "twiddles",
-                                "table_twiddles", "table", "fh", "uh", "partials", "relaxation", "status")] + [
-    ("table32", "fp32"), ("table_x2_k0", "fp32"), ("tensor force operand", "bf16x2"), ("table_x2", "f32x2")]
+                                "table_twiddles", "line_twiddles", "table", "fh", "uh", "partials", "relaxation",
+                                "status")] + [
+    ("table32", "fp32"), ("table_x2_k0", "fp32"), ("tensor force operand", "bf16x2"), ("uh32", "bf16x2"),
+    ("table_x2", "f32x2")]
 
 
 def _create(fbc, xy_i, xy_p, L, prec, max_rhs):
