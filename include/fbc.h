@@ -524,6 +524,92 @@ int fbc_plan_attach_surrogate(fbc_plan* plan, fbc_surrogate* s, double r_min, in
 /* Release the surrogate.  NULL is ignored. */
 void fbc_surrogate_destroy(fbc_surrogate* s);
 
+
+/* ---------------------------------------------------------------------------
+ * H-matrix form of the pad update (Sec. 3.2; App., the construction of the
+ * H-matrix approximation of the Green matrix): the comparison form.  The
+ * Green matrix G~^{p|i+} has 3 x 3 blocks G~(x_a - x_b, (p - q) c) for pad atoms
+ * (a, p) and interface atoms (b, q).  It is approximated by
+ *   Step 1: cluster trees of each atom set by geometric bisection: split at
+ *           the midpoint of the bounding box's longest side until at most
+ *           b_min atoms;
+ *   Step 2: the admissible partition: t x s is low rank when
+ *           min(diam t, diam s') <= gamma dist(t, s') for s' in {s, s+, s-},
+ *           where s+- are the same cluster one period L c up and down, diam
+ *           is the bounding-box diagonal and dist the centroid distance;
+ *           inadmissible pairs of leaves are dense;
+ *   Step 3: adaptive cross approximation with partial pivoting on atoms
+ *           (3 x 3 pivots), stopping after three consecutive steps whose
+ *           terms have Frobenius norm <= eps times the approximation's.
+ * The entries come from the plan's periodic kernel (Sec. 3.1, Eqs. 32-36) in
+ * real space, the same kernel that the per-mode forms transform.  The build
+ * runs on the device in FP32 (residuals, terms) with FP64 norms; the factors
+ * are stored in FP32.  The paper's settings are eps = 1e-5, gamma = 2,
+ * b_min = 20.
+ * ------------------------------------------------------------------------- */
+typedef struct fbc_hmat fbc_hmat;
+
+typedef struct {
+    double eps;            /* ACA tolerance, 1e-6 <= eps < 1 (paper: 1e-5) */
+    double gamma;          /* admissibility constant, > 0 (paper: 2) */
+    int32_t b_min;         /* leaf size of the cluster trees in atoms, 1..64 (paper: 20) */
+    int32_t max_rank;      /* terms per block at most: 0 = 2046, else 1..3069 */
+    int64_t scratch_bytes; /* device scratch per build wave: 0 = 40 % of the free memory */
+} fbc_hmat_options;
+
+typedef struct {
+    int64_t n_rows, n_cols;      /* 3 n_p L and 3 n_i L */
+    int64_t n_lowrank, n_dense;  /* blocks of the partition */
+    int64_t rank_sum;            /* sum of the low-rank blocks' ranks (terms) */
+    int32_t rank_max;            /* the largest rank */
+    int32_t n_capped;            /* blocks that stopped at max_rank before the rule held */
+    int64_t factor_bytes;        /* FP32 factors U, V of the low-rank blocks */
+    int64_t dense_bytes;         /* FP32 dense blocks */
+    int32_t n_row_leaves, n_col_leaves;
+    int32_t n_waves;             /* build waves (groups of blocks that share the scratch) */
+    int32_t reserved;
+    double build_ms;             /* wall time of fbc_hmat_create */
+} fbc_hmat_info;
+
+/* Steps 1 and 2 on the host only (no device use): the partition for the
+ * column sites xy_i [n_i][2], xy_p [n_p][2] (host int32) with L repeats of
+ * spacing c.  *n_blocks receives the number of blocks.  blocks (host int64
+ * [cap][5], may be NULL) receives the blocks sorted by (row start, row count,
+ * col start, col count): (row start, row count, col start, col count,
+ * low rank) in atoms of cluster order, when cap >= *n_blocks
+ * (FBC_ERR_INVALID_ARG otherwise).  perm_p [n_p L], perm_i [n_i L] (host
+ * int64, may be NULL) receive the atom id (column * L + repeat) at each
+ * cluster-order position. */
+int fbc_hmat_partition(const int32_t* xy_i, int32_t n_i, const int32_t* xy_p, int32_t n_p, int32_t L, double c,
+                       double gamma, int32_t b_min, int64_t* n_blocks, int64_t* blocks, int64_t cap, int64_t* perm_p,
+                       int64_t* perm_i);
+
+/* Build the H-matrix of a plan's Green matrix (the plan's geometry, medium and
+ * Richardson order; its precision is not used).  Plans with interface sites
+ * inside the pad (FBC_PLAN_SELF_TERMS) or a lattice near field are refused
+ * (FBC_ERR_UNSUPPORTED): their kernel is not the periodic continuum one.
+ * Blocks until done; allocates.  opt == NULL takes the paper's settings. */
+int fbc_hmat_create(fbc_plan* plan, const fbc_hmat_options* opt, void* stream, fbc_hmat** out);
+
+/* u <- beta u + alpha G_H f' with f' = f, or f minus its per-component mean
+ * over all n_i L interface atoms (FBC_APPLY_PROJECT_NEUTRAL), then the optional
+ * zero mean of u (FBC_APPLY_ZERO_MEAN_U).  f: DEVICE const double
+ * [n_rhs][n_i][L][3]; u: DEVICE double [n_rhs][n_p][L][3] (read only when
+ * beta != 0); n_rhs >= 1, applied four at a time.  Asynchronous on `stream`,
+ * deterministic; concurrent applies of one H-matrix race on its workspace. */
+int fbc_hmat_apply(fbc_hmat* h, const double* f, double* u, int32_t n_rhs, double alpha, double beta, uint32_t flags,
+                   void* stream);
+
+/* Sizes, ranks and build time. */
+int fbc_hmat_get_info(const fbc_hmat* h, fbc_hmat_info* info);
+
+/* The partition as in fbc_hmat_partition and each block's rank (ranks
+ * [cap], host int32; 0 for a dense block); either may be NULL. */
+int fbc_hmat_blocks(const fbc_hmat* h, int64_t* blocks, int32_t* ranks, int64_t cap);
+
+/* Free the H-matrix (NULL is ignored). */
+void fbc_hmat_destroy(fbc_hmat* h);
+
 #ifdef __cplusplus
 }
 #endif

@@ -168,6 +168,10 @@ struct LineArgs {
 
 // ---- launchers (each returns the launch's cudaError_t) ---------------------
 cudaError_t launch_tabulate(Plan& P, cudaStream_t st);
+// The periodic kernel in real space, G~(d, s) for s = 0..L/2 (the stage before the line DFT), as
+// FP32 six-entry records at every cell of the difference box: out[Dy * Dx][L/2 + 1][6] (11, 12, 22,
+// 33, 13, 23); cells of differences that do not occur are zero.  The H-matrix build reads it.
+cudaError_t launch_real_space_table(Plan& P, float* out, cudaStream_t st);
 cudaError_t launch_forward(Plan& P, const double* f, int n_rhs, bool project, cudaStream_t st);
 cudaError_t launch_contract(Plan& P, int n_rhs, cudaStream_t st);
 // alpha_dev (optional): per-rhs multiplier alpha_dev_scale * alpha_dev[r] in place of alpha / L;

@@ -219,7 +219,9 @@ __global__ void k_derive_x2(const double* __restrict__ t64, float* __restrict__ 
 
 }  // namespace
 
-cudaError_t launch_tabulate(Plan& P, cudaStream_t st) {
+// The plan's medium and tabulation parameters into this file's constant memory (shared by every
+// plan: uploaded again before each use).
+static cudaError_t upload_tabulate_constants(Plan& P, cudaStream_t st) {
     cudaError_t e;
     if ((e = cudaMemcpyToSymbolAsync(c_mat, &P.mat, sizeof(MaterialDev), 0, cudaMemcpyHostToDevice, st))) return e;
     if ((e = cudaMemcpyToSymbolAsync(c_tp, &P.tp, sizeof(TabulateParams), 0, cudaMemcpyHostToDevice, st))) return e;
@@ -239,6 +241,12 @@ cudaError_t launch_tabulate(Plan& P, cudaStream_t st) {
         // the host vectors must outlive the asynchronous copies
         if ((e = cudaStreamSynchronize(st))) return e;
     }
+    return cudaSuccess;
+}
+
+cudaError_t launch_tabulate(Plan& P, cudaStream_t st) {
+    cudaError_t e;
+    if ((e = upload_tabulate_constants(P, st))) return e;
     if (P.n_used == 0) return cudaSuccess;
     const int Lh = P.L / 2;
     // process the differences in chunks so the stage-1 buffer stays bounded
@@ -262,6 +270,47 @@ cudaError_t launch_tabulate(Plan& P, cudaStream_t st) {
         if ((e = cudaGetLastError())) break;
         const int bt = std::min(256, std::max(32, ((P.K + 31) / 32) * 32));
         k_line_dft<<<nd, bt, smem, st>>>(P.d_used + d0, gs, P.d_twL, P.d_table);
+        if ((e = cudaGetLastError())) break;
+    }
+    cudaError_t e2 = cudaFreeAsync(gs, st);
+    return e ? e : e2;
+}
+
+// Stage-1 output of a chunk of used differences, rounded to FP32 and placed at each difference's
+// cell of the box: out[cell][s][6] for s = 0..L/2.
+__global__ void k_real_space_scatter(const int2* __restrict__ used, int n_used, const double* __restrict__ gs,
+                                     float* __restrict__ out) {
+    const int Lh = c_tp.Lh;
+    const long long per = (long long)(Lh + 1) * 6;
+    const long long total = (long long)n_used * per;
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int di = (int)(t / per);
+        const long long r = t - (long long)di * per;
+        const int2 d = used[di];
+        const long long cell = (long long)(d.y - c_tp.box_y0) * c_tp.Dx + (d.x - c_tp.box_x0);
+        out[cell * per + r] = (float)gs[t];
+    }
+}
+
+cudaError_t launch_real_space_table(Plan& P, float* out, cudaStream_t st) {
+    cudaError_t e;
+    if ((e = upload_tabulate_constants(P, st))) return e;
+    const int Lh = P.L / 2;
+    const size_t cells = (size_t)P.Dx * P.Dy;
+    if ((e = cudaMemsetAsync(out, 0, cells * (Lh + 1) * 6 * sizeof(float), st))) return e;
+    if (P.n_used == 0) return cudaSuccess;
+    const size_t per_d = (size_t)(Lh + 1) * 6 * sizeof(double);
+    int chunk = (int)std::min<size_t>((size_t)P.n_used, std::max<size_t>(1, (size_t)256 << 20) / per_d);
+    if (chunk < 1) chunk = 1;
+    double* gs = nullptr;
+    if ((e = cudaMallocAsync((void**)&gs, per_d * chunk, st))) return e;
+    for (int d0 = 0; d0 < P.n_used; d0 += chunk) {
+        const int nd = std::min(chunk, P.n_used - d0);
+        const long long threads = (long long)nd * (Lh + 1);
+        k_periodic<<<(unsigned)((threads + 127) / 128), 128, 0, st>>>(P.d_used + d0, nd, gs);
+        if ((e = cudaGetLastError())) break;
+        k_real_space_scatter<<<1216, 256, 0, st>>>(P.d_used + d0, nd, gs, out);
         if ((e = cudaGetLastError())) break;
     }
     cudaError_t e2 = cudaFreeAsync(gs, st);

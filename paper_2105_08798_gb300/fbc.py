@@ -99,6 +99,22 @@ class fbc_batch_info(ctypes.Structure):
         return {name: getattr(self, name) for name, _ in self._fields_}
 
 
+class fbc_hmat_options(ctypes.Structure):
+    _fields_ = [("eps", ctypes.c_double), ("gamma", ctypes.c_double), ("b_min", ctypes.c_int32),
+                ("max_rank", ctypes.c_int32), ("scratch_bytes", ctypes.c_int64)]
+
+
+class fbc_hmat_info(ctypes.Structure):
+    _fields_ = [("n_rows", ctypes.c_int64), ("n_cols", ctypes.c_int64), ("n_lowrank", ctypes.c_int64),
+                ("n_dense", ctypes.c_int64), ("rank_sum", ctypes.c_int64), ("rank_max", ctypes.c_int32),
+                ("n_capped", ctypes.c_int32), ("factor_bytes", ctypes.c_int64), ("dense_bytes", ctypes.c_int64),
+                ("n_row_leaves", ctypes.c_int32), ("n_col_leaves", ctypes.c_int32), ("n_waves", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("build_ms", ctypes.c_double)]
+
+    def as_dict(self) -> dict:
+        return {name: getattr(self, name) for name, _ in self._fields_ if name != "reserved"}
+
+
 _lock = threading.Lock()
 _lib = None
 
@@ -151,6 +167,16 @@ _SIGNATURES = {
     "fbc_plan_attach_surrogate": (ctypes.c_int, [_vp, _vp, ctypes.c_double, ctypes.c_int32]),
     "fbc_surrogate_sync_status": (ctypes.c_int, [_vp, _vp]),
     "fbc_surrogate_destroy": (None, [_vp]),
+    "fbc_hmat_partition": (ctypes.c_int, [_P(ctypes.c_int32), ctypes.c_int32, _P(ctypes.c_int32), ctypes.c_int32,
+                                          ctypes.c_int32, ctypes.c_double, ctypes.c_double, ctypes.c_int32,
+                                          _P(ctypes.c_int64), _P(ctypes.c_int64), ctypes.c_int64, _P(ctypes.c_int64),
+                                          _P(ctypes.c_int64)]),
+    "fbc_hmat_create": (ctypes.c_int, [_vp, _P(fbc_hmat_options), _vp, _P(_vp)]),
+    "fbc_hmat_apply": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int32, ctypes.c_double, ctypes.c_double,
+                                      ctypes.c_uint32, _vp]),
+    "fbc_hmat_get_info": (ctypes.c_int, [_vp, _P(fbc_hmat_info)]),
+    "fbc_hmat_blocks": (ctypes.c_int, [_vp, _P(ctypes.c_int64), _P(ctypes.c_int32), ctypes.c_int64]),
+    "fbc_hmat_destroy": (None, [_vp]),
 }
 
 
@@ -417,6 +443,56 @@ def fbc_surrogate_destroy(sur: int):
 
 
 # ---- convenience wrapper -----------------------------------------------------
+def fbc_hmat_partition(xy_i: np.ndarray, xy_p: np.ndarray, L: int, c: float = 1.0, gamma: float = 2.0,
+                       b_min: int = 20) -> tuple[np.ndarray, np.ndarray, np.ndarray]:
+    """Steps 1-2 of the H-matrix construction on the host: (blocks [n][5], perm_p, perm_i)."""
+    lib = load()
+    xi = np.ascontiguousarray(xy_i, dtype=np.int32).reshape(-1, 2)
+    xp = np.ascontiguousarray(xy_p, dtype=np.int32).reshape(-1, 2)
+    n = ctypes.c_int64(0)
+    i32 = _P(ctypes.c_int32)
+    i64 = _P(ctypes.c_int64)
+    _check(lib.fbc_hmat_partition(xi.ctypes.data_as(i32), len(xi), xp.ctypes.data_as(i32), len(xp), L, c, gamma, b_min,
+                                  ctypes.byref(n), None, 0, None, None), "fbc_hmat_partition")
+    blocks = np.zeros((n.value, 5), dtype=np.int64)
+    perm_p = np.zeros(len(xp) * L, dtype=np.int64)
+    perm_i = np.zeros(len(xi) * L, dtype=np.int64)
+    _check(lib.fbc_hmat_partition(xi.ctypes.data_as(i32), len(xi), xp.ctypes.data_as(i32), len(xp), L, c, gamma, b_min,
+                                  ctypes.byref(n), blocks.ctypes.data_as(i64), n.value, perm_p.ctypes.data_as(i64),
+                                  perm_i.ctypes.data_as(i64)), "fbc_hmat_partition")
+    return blocks, perm_p, perm_i
+
+
+def fbc_hmat_create(plan: int, eps: float, gamma: float, b_min: int, max_rank: int, scratch_bytes: int,
+                    stream=None) -> int:
+    h = _vp()
+    opt = fbc_hmat_options(eps, gamma, b_min, max_rank, scratch_bytes)
+    _check(load().fbc_hmat_create(plan, ctypes.byref(opt), _stream_handle(stream), ctypes.byref(h)), "fbc_hmat_create")
+    return h.value
+
+
+def fbc_hmat_apply(h: int, f_ptr: int, u_ptr: int, n_rhs: int, alpha: float, beta: float, flags: int, stream=None):
+    _check(load().fbc_hmat_apply(h, f_ptr, u_ptr, n_rhs, alpha, beta, flags, _stream_handle(stream)), "fbc_hmat_apply")
+
+
+def fbc_hmat_get_info(h: int) -> dict:
+    info = fbc_hmat_info()
+    _check(load().fbc_hmat_get_info(h, ctypes.byref(info)), "fbc_hmat_get_info")
+    return info.as_dict()
+
+
+def fbc_hmat_blocks(h: int, n_blocks: int) -> tuple[np.ndarray, np.ndarray]:
+    blocks = np.zeros((n_blocks, 5), dtype=np.int64)
+    ranks = np.zeros(n_blocks, dtype=np.int32)
+    _check(load().fbc_hmat_blocks(h, blocks.ctypes.data_as(_P(ctypes.c_int64)), ranks.ctypes.data_as(_P(ctypes.c_int32)),
+                                  n_blocks), "fbc_hmat_blocks")
+    return blocks, ranks
+
+
+def fbc_hmat_destroy(h: int):
+    load().fbc_hmat_destroy(h)
+
+
 def material_struct(material: dict) -> fbc_material:
     m = fbc_material()
     kind = material.get("kind", "isotropic")
@@ -734,6 +810,66 @@ class Batch:
     def close(self):
         if self._h is not None:
             fbc_batch_destroy(self._h)
+            self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class HMatrix:
+    """Owning handle of one ``fbc_hmat``: the H-matrix approximation of a plan's Green matrix
+    (Sec. 3.2; App., the H-matrix construction).  Defaults are the paper's settings."""
+
+    def __init__(self, plan: Plan, eps: float = 1e-5, gamma: float = 2.0, b_min: int = 20, max_rank: int = 0,
+                 scratch_bytes: int = 0, stream=None):
+        self._h = None
+        self.n_i, self.n_p, self.L = plan.n_i, plan.n_p, plan.L
+        self._h = fbc_hmat_create(plan.handle, eps, gamma, b_min, max_rank, scratch_bytes, stream)
+
+    @property
+    def handle(self) -> int:
+        if self._h is None:
+            raise ValueError("H-matrix is closed")
+        return self._h
+
+    def info(self) -> dict:
+        return fbc_hmat_get_info(self.handle)
+
+    def blocks(self) -> tuple[np.ndarray, np.ndarray]:
+        """The partition (rows of (row start, row count, col start, col count, low rank)) and the ranks."""
+        i = self.info()
+        return fbc_hmat_blocks(self.handle, int(i["n_lowrank"] + i["n_dense"]))
+
+    def apply(self, f, u, alpha: float = 1.0, beta: float = 0.0, project: bool = True, zero_mean: bool = False,
+              stream=None):
+        """u <- beta u + alpha G_H f on float64 CUDA tensors f [n_rhs][n_i][L][3], u [n_rhs][n_p][L][3]."""
+        import torch
+
+        n_rhs = f.shape[0]
+        if f.dtype != torch.float64 or u.dtype != torch.float64 or not f.is_cuda or not u.is_cuda:
+            raise TypeError("f and u must be float64 CUDA tensors")
+        if tuple(f.shape) != (n_rhs, self.n_i, self.L, 3) or tuple(u.shape) != (n_rhs, self.n_p, self.L, 3):
+            raise ValueError(f"shape mismatch: f {tuple(f.shape)}, u {tuple(u.shape)}")
+        if not f.is_contiguous() or not u.is_contiguous():
+            raise ValueError("f and u must be contiguous")
+        if stream is None:
+            stream = torch.cuda.current_stream(f.device)
+        fbc_hmat_apply(self.handle, f.data_ptr(), u.data_ptr(), n_rhs, alpha, beta, Plan.flags(project, zero_mean),
+                       stream)
+        return u
+
+    def close(self):
+        if self._h is not None:
+            fbc_hmat_destroy(self._h)
             self._h = None
 
     def __enter__(self):

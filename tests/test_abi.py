@@ -57,6 +57,9 @@ int main(void) {
   printf("fbc_geometry %zu\nfbc_material %zu\nfbc_options %zu\nfbc_plan_info %zu\nfbc_batch_info %zu\n",
          sizeof(fbc_geometry), sizeof(fbc_material), sizeof(fbc_options), sizeof(fbc_plan_info),
          sizeof(fbc_batch_info));
+  printf("fbc_hmat_options %zu\nfbc_hmat_info %zu\n", sizeof(fbc_hmat_options), sizeof(fbc_hmat_info));
+  P(fbc_hmat_options, b_min) P(fbc_hmat_options, scratch_bytes)
+  P(fbc_hmat_info, rank_max) P(fbc_hmat_info, factor_bytes) P(fbc_hmat_info, n_waves) P(fbc_hmat_info, build_ms)
   P(fbc_batch_info, smem_contract) P(fbc_batch_info, pair_modes) P(fbc_batch_info, rhs_per_cta)
   P(fbc_geometry, c) P(fbc_geometry, xy_i) P(fbc_geometry, xy_p)
   P(fbc_material, mu) P(fbc_material, C44) P(fbc_material, Q)
@@ -75,6 +78,8 @@ int main(void) {
     assert int(vals["fbc_options"]) == ctypes.sizeof(fbc.fbc_options)
     assert int(vals["fbc_plan_info"]) == ctypes.sizeof(fbc.fbc_plan_info)
     assert int(vals["fbc_batch_info"]) == ctypes.sizeof(fbc.fbc_batch_info)
+    assert int(vals["fbc_hmat_options"]) == ctypes.sizeof(fbc.fbc_hmat_options)
+    assert int(vals["fbc_hmat_info"]) == ctypes.sizeof(fbc.fbc_hmat_info)
     for key, v in vals.items():
         if "." in key:
             t, f = key.split(".")
@@ -146,3 +151,34 @@ def test_new_entry_points_validate_before_device_work(lib):
         pass
     with pytest.raises(fbc.FBCError, match="coincides"):
         fbc.Plan(xy_i, pad, 8, {"kind": "isotropic", "mu": 1.0, "nu": 0.3}, host_only=True)
+
+
+def test_hmat_entry_points_validate_before_device_work(lib):
+    """H-matrix: bad options, NULL handles and host-only plans are rejected without device work."""
+    h = ctypes.c_void_p()
+    bad = [fbc.fbc_hmat_options(1e-7, 2.0, 20, 0, 0), fbc.fbc_hmat_options(1e-5, 0.0, 20, 0, 0),
+           fbc.fbc_hmat_options(1e-5, 2.0, 0, 0, 0), fbc.fbc_hmat_options(1e-5, 2.0, 20, 5000, 0),
+           fbc.fbc_hmat_options(1e-5, 2.0, 20, 0, -1)]
+    for opt in bad:
+        assert lib.fbc_hmat_create(None, ctypes.byref(opt), None, ctypes.byref(h)) == fbc.FBC_ERR_INVALID_ARG
+        assert h.value is None
+    assert lib.fbc_hmat_create(None, None, None, ctypes.byref(h)) == fbc.FBC_ERR_INVALID_ARG
+    assert lib.fbc_hmat_apply(None, None, None, 1, 1.0, 0.0, 0, None) == fbc.FBC_ERR_INVALID_ARG
+    assert lib.fbc_hmat_get_info(None, None) == fbc.FBC_ERR_INVALID_ARG
+    lib.fbc_hmat_destroy(None)
+    xy_i, xy_p = inputs.ring_geometry(20, 30)
+    with fbc.Plan(xy_i, xy_p, 8, {"kind": "isotropic", "mu": 1.0, "nu": 0.3}, host_only=True) as plan:
+        with pytest.raises(fbc.FBCError, match="host-only"):
+            fbc.fbc_hmat_create(plan.handle, 1e-5, 2.0, 20, 0, 0)
+    n = ctypes.c_int64(0)
+    xi = np.ascontiguousarray(xy_i, dtype=np.int32)
+    xp = np.ascontiguousarray(xy_p, dtype=np.int32)
+    i32 = ctypes.POINTER(ctypes.c_int32)
+    assert lib.fbc_hmat_partition(xi.ctypes.data_as(i32), len(xi), xp.ctypes.data_as(i32), len(xp), 8, 1.0, 2.0, 0,
+                                  ctypes.byref(n), None, 0, None, None) == fbc.FBC_ERR_INVALID_ARG
+    assert lib.fbc_hmat_partition(xi.ctypes.data_as(i32), len(xi), xp.ctypes.data_as(i32), len(xp), 8, 1.0, 2.0, 20,
+                                  ctypes.byref(n), None, 0, None, None) == fbc.FBC_OK
+    blk = (ctypes.c_int64 * 5)()
+    if n.value > 1:
+        assert lib.fbc_hmat_partition(xi.ctypes.data_as(i32), len(xi), xp.ctypes.data_as(i32), len(xp), 8, 1.0, 2.0, 20,
+                                      ctypes.byref(n), blk, 1, None, None) == fbc.FBC_ERR_INVALID_ARG
