@@ -526,6 +526,43 @@ def run_ours(args, w):
                                                "value": pm / (np.mean(vms) * 1e-3) / 1e9,
                                                "contract_ms": float(vstage[1]), "steps": n}
 
+    if args.hmatrix:
+        # the paper's comparison form (Sec. 3.2, App.): the H-matrix of the same Green matrix at the paper's
+        # settings, built once (setup), applied like the plan
+        t1 = time.perf_counter()
+        H = fbc.HMatrix(plan, eps=1e-5, gamma=2.0, b_min=20)
+        torch.cuda.synchronize()
+        build_s = time.perf_counter() - t1
+        hi = H.info()
+
+        class _HApply:  # the interface time_device_steps uses; the H-matrix has no stage events
+            def apply(self, f_, u_, **kw):
+                return H.apply(f_, u_, **kw)
+
+            def set_timing(self, on):
+                pass
+
+            def stage_times(self):
+                return [0.0, 0.0, 0.0]
+
+            def sync_status(self):
+                pass
+
+        vms, _, n = time_capped(_HApply(), VARIANT_SECONDS, max(2, args.steps // 2))
+        outputs["hmatrix"] = snap()
+        dense_bytes = 9.0 * w.n_p * w.n_i * w.L * w.L * 4
+        variants["hmatrix"] = {"ms_per_step": float(np.mean(vms)), "value": pm / (np.mean(vms) * 1e-3) / 1e9,
+                               "steps": n, "dtype": "f32 factors, double-float sums",
+                               "note": "effective rate: pair-modes of the dense form per second",
+                               "eps": 1e-5, "gamma": 2.0, "b_min": 20, "build_s": build_s,
+                               "factor_bytes": hi["factor_bytes"] + hi["dense_bytes"],
+                               "dense_matrix_fp32_bytes": dense_bytes,
+                               "factor_gbs": (hi["factor_bytes"] + hi["dense_bytes"]) / (np.mean(vms) * 1e-3) / 1e9,
+                               "n_lowrank": hi["n_lowrank"], "n_dense": hi["n_dense"], "rank_sum": hi["rank_sum"],
+                               "rank_max": hi["rank_max"], "n_capped": hi["n_capped"], "n_waves": hi["n_waves"]}
+        H.close()
+        torch.cuda.empty_cache()
+
     # end-to-end through the host entry point: pinned host f in, host u out, in the headline form
     if check_thread is not None:
         check_thread.join()
@@ -804,6 +841,9 @@ def main(argv=None):
                     help="train the learned far field (width 128, 2^20 samples, 50 epochs), attach it with "
                          "r_min = 8 and release the K-slice tables; the exact-table path is timed first")
     ap.add_argument("--skip-oracle", action="store_true", help="no oracle error check / CPU baseline")
+    ap.add_argument("--hmatrix", action="store_true",
+                    help="also build the H-matrix of the same Green matrix (eps 1e-5, gamma 2, b_min 20) and time "
+                         "its apply as a variant")
     args = ap.parse_args(argv)
     if args.workload == "batch":
         if args.impl == "reference":

@@ -553,7 +553,7 @@ typedef struct {
     double eps;            /* ACA tolerance, 1e-6 <= eps < 1 (paper: 1e-5) */
     double gamma;          /* admissibility constant, > 0 (paper: 2) */
     int32_t b_min;         /* leaf size of the cluster trees in atoms, 1..64 (paper: 20) */
-    int32_t max_rank;      /* terms per block at most: 0 = 2046, else 1..3069 */
+    int32_t max_rank;      /* terms per block at most: 0 = 6141 (the build's limit), else 1..6141 */
     int64_t scratch_bytes; /* device scratch per build wave: 0 = 40 % of the free memory */
 } fbc_hmat_options;
 

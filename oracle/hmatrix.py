@@ -26,7 +26,9 @@ Readings, where the paper leaves a choice to its library:
 1. Pivots are atoms, not single rows.  The residual rows of the pivot atom are computed.  The
    column atom is the one whose 3 x 3 residual block has the largest Frobenius norm.  Up to
    three rank-1 terms are then taken from that 3 x 3 block by elimination with full pivoting.
-   A further pivot smaller than ``PIVOT_DROP`` times the first one ends the step.  Scalar
+   A pivot smaller than ``PIVOT_DROP`` times the block's first pivot ends the step: that is the
+   scale of the rounding left in the residual by the stored terms (FP32 on the device), and a
+   pivot at that level adds noise and can fill the rank of a small block.  Scalar
    pivoting stalls on this kernel: the z rows decouple from the in-plane rows at s = 0 and
    s = L/2, and the partial search then misses whole components.
 2. The stopping rule is the paper's "norm of R^k - R^(k-1) below eps", taken relative.  The
@@ -167,6 +169,7 @@ def aca(rows, cols, n_t: int, n_s: int, eps: float, max_rank: int | None = None)
     V = np.zeros((0, ns3))
     used = np.zeros(n_t, dtype=bool)
     ia, S2, small, capped = 0, 0.0, 0, False
+    p0 = None  # the block's first pivot: the scale of the drop rule
     while True:
         R = rows(ia) - U[3 * ia:3 * ia + 3] @ V  # residual rows of the pivot atom
         used[ia] = True
@@ -179,14 +182,13 @@ def aca(rows, cols, n_t: int, n_s: int, eps: float, max_rank: int | None = None)
             continue
         C = cols(ja) - U @ V[:, 3 * ja:3 * ja + 3]  # residual columns of the pivot column atom
         new_u, new_v = [], []
-        first = None
         for _ in range(3):
             P = R[:, 3 * ja:3 * ja + 3]
             a, b = np.unravel_index(int(np.argmax(np.abs(P))), P.shape)
             piv = P[a, b]
-            if first is None:
-                first = abs(piv)
-            elif not (abs(piv) > PIVOT_DROP * first):
+            if p0 is None:
+                p0 = abs(piv)
+            if not (abs(piv) > PIVOT_DROP * p0):
                 break
             u = C[:, b] / piv
             v = R[a, :].copy()
@@ -194,8 +196,8 @@ def aca(rows, cols, n_t: int, n_s: int, eps: float, max_rank: int | None = None)
             new_v.append(v)
             R = R - np.outer(u[3 * ia:3 * ia + 3], v)
             C = C - np.outer(u, v[3 * ja:3 * ja + 3])
-        Un = np.array(new_u).T
-        Vn = np.array(new_v)
+        Un = np.array(new_u).reshape(len(new_u), nt3).T
+        Vn = np.array(new_v).reshape(len(new_v), ns3)
         cross = float(np.sum((U.T @ Un) * (V @ Vn.T)))
         step2 = float(np.sum((Un.T @ Un) * (Vn @ Vn.T)))
         S2 += 2.0 * cross + step2
@@ -207,6 +209,9 @@ def aca(rows, cols, n_t: int, n_s: int, eps: float, max_rank: int | None = None)
         if U.shape[1] >= max_rank:
             capped = max_rank < full  # a full-rank factorisation is exact
             break
+        if not new_u:  # nothing above the drop level in this row atom: the first unused one next
+            ia = int(np.argmin(used))
+            continue
         w = (Un.reshape(n_t, 3, -1) ** 2).sum(axis=(1, 2))
         w[used] = -1.0
         ia = int(np.argmax(w))

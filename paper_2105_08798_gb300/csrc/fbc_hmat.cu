@@ -19,7 +19,7 @@
 //          row atom the three residual rows are computed.  The column atom with the largest 3 x 3
 //          residual block is chosen and its three residual columns computed.  Up to three rank-1
 //          terms are taken from that 3 x 3 block by elimination with full pivoting; a pivot below
-//          1e-6 of the first ends the step.  The step's terms are then written as combinations of
+//          1e-6 of the block's first pivot ends the step.  The step's terms are then written as combinations of
 //          the raw rows and columns.  A block stops after three consecutive steps whose terms have
 //          Frobenius norm <= eps ||S||_F.  ||S||_F is kept exactly with the cross terms
 //          2 sum_{l,m} (u_l . u_m)(v_l . v_m).  The next pivot atom is the unused row atom where the
@@ -30,15 +30,18 @@
 //          and column halves), and the stopping test.  The work of a step is O(k (n_t + n_s)) and
 //          is spread over the whole GPU whatever the blocks' sizes.  Entries come from the plan's
 //          periodic kernel, evaluated once in real space and stored as an FP32 box table.  The
-//          residuals and terms are FP32: their rounding (about 1e-7 relative) is far below the
-//          tolerances the approximation is used at (the paper's eps = 1e-5; eps >= 1e-6).  The
-//          running norms are FP64.
+//          terms are stored in FP32, but the residual entries G - sum_l u_l v_l are summed in
+//          double-float: the terms of a cross approximation cancel strongly, and plain FP32 sums
+//          leave a noise floor near 5e-5 that the approximation then fits (measured: 5.4e-5 on
+//          the small ring at eps = 1e-5, against 6e-6 with FP64 arithmetic).  The running norms
+//          are FP64; the paper's eps = 1e-5 is inside the range accepted (eps >= 1e-6).
 // Apply, u <- beta u + alpha G_H (f - mean f):
 //   gather: f in cluster order, FP32, after the neutral projection;
 //   z_b = V_b^T x_s for every low-rank block (items of 256 column dofs, then a fixed-order sum);
 //   one CTA per row leaf: y = sum over the blocks that cover the leaf's rows of U_b z_b (and
 //   D_b x_s for dense blocks), in the blocks' order.  Warps own rows and sums are FP64, so the result
 //   is deterministic.  The epilogue writes u in the caller's layout; an optional zero mean follows.
+//   For the same cancellation, z and U_b z_b are summed in double-float (z kept as an FP32 pair).
 // Storage for the apply is FP32: U_b [3 n_t][k] and V_b [3 n_s][k], row-major (a row's k
 // coefficients contiguous), and D_b [3 n_t][3 n_s].  The apply reads each factor once per group
 // of up to four right-hand sides.
@@ -56,14 +59,15 @@
 
 namespace {
 
-constexpr float kPivotDrop = 1e-6f;  // a further pivot below this fraction of the first ends a step
+constexpr float kPivotDrop = 1e-6f;  // a pivot below this fraction of the block's first ends a step
 constexpr int kStopSteps = 3;        // consecutive small steps that stop a block
 constexpr int kChunk = 256;          // atoms per CTA item of the build (rows or columns)
 constexpr int kDotChunk = 4096;      // dofs per CTA item of the dot products
 constexpr int kRG = 4;               // right-hand sides per pass of the apply
 constexpr int kZCols = 256;          // column dofs per item of z = V^T x
-constexpr int kDefaultMaxRank = 2046;
-constexpr int kMaxRank = 3069;       // the build's slots (rank + 3) stay <= 3072
+constexpr int kMaxRank = 6141;       // the build's slots (rank + 3) stay <= 6144
+constexpr int kDefaultMaxRank = kMaxRank;
+constexpr size_t kBuildSmemMax = sizeof(float) * 3 * (kMaxRank + 3);  // k_aca_rows / k_aca_cols
 
 // ------------------------------------------------------------------------------------- host side
 
@@ -257,10 +261,30 @@ struct BuildState {
     int small;     // consecutive small steps
     int capped;    // stopped at kcap before the rule held
     double S2;     // ||S||_F^2
+    double p0;     // the block's first pivot (0 until the first step): the scale of the drop rule
     float P[9];    // the 3 x 3 residual pivot block
-    float au[9];   // u_m = sum_b au[3 m + b] C_b
-    float bv[9];   // v_m = sum_a bv[3 m + a] R_a
+    // the step's elimination, replayed by the emit kernel on every row and column:
+    // u_q = C'_{pb[q]} / piv[q], v_q = R'_{pa[q]}; then C'_b -= u_q rowv[q][b], R'_a -= colv[q][a] v_q
+    int pa[3], pb[3];
+    float piv[3];
+    float rowv[9];  // P'_q[pa[q]][b]: v_q at the pivot column atom's columns
+    float colv[9];  // P'_q[a][pb[q]] / piv[q]: u_q at the pivot row atom's rows
 };
+
+// (S, E) <- (S, E) + a b, a double-float sum of FP32 products: Knuth's two-sum on S, and the
+// product's own rounding error carried by one FMA (a b - bb is formed exactly and rounded once).
+// The terms of a cross approximation cancel strongly (their sum is far smaller than the largest
+// term), so plain FP32 sums of them lose the accuracy that eps asks for.  The round-to-nearest
+// intrinsics keep the compiler from fusing a b + S into one FMA, which would break the two-sum.
+__device__ __forceinline__ void df_mac(float& S, float& E, float a, float b) {
+    const float p = __fmul_rn(a, b);
+    const float s = __fadd_rn(S, p);
+    const float bb = __fsub_rn(s, S);
+    const float lost = __fsub_rn(S, __fsub_rn(s, bb));
+    const float rest = __fmaf_rn(a, b, -bb);
+    S = s;
+    E = __fadd_rn(E, __fadd_rn(lost, rest));
+}
 
 __device__ __forceinline__ void argmax_merge(float& v, int& i, float v2, int i2) {
     if (v2 > v || (v2 == v && i2 < i)) v = v2, i = i2;
@@ -303,19 +327,23 @@ __global__ void __launch_bounds__(256) k_aca_rows(const BuildBlk* __restrict__ B
     float best = -1.0f;
     int barg = 0x7fffffff;
     if (ca < b.nc) {
-        float acc[9];
+        float acc[9], err[9];
         entry9(g, g.ra[b.r0 + ia], g.ca[b.c0 + ca], acc);
+#pragma unroll
+        for (int t = 0; t < 9; t++) err[t] = 0.0f;
         const float* v = V + 3LL * ca;
         for (int l = 0; l < k; l++, v += nc3) {
             const float v0 = v[0], v1 = v[1], v2 = v[2];
 #pragma unroll
             for (int i = 0; i < 3; i++) {
-                const float u = su[3 * l + i];
-                acc[3 * i + 0] = fmaf(-u, v0, acc[3 * i + 0]);
-                acc[3 * i + 1] = fmaf(-u, v1, acc[3 * i + 1]);
-                acc[3 * i + 2] = fmaf(-u, v2, acc[3 * i + 2]);
+                const float u = -su[3 * l + i];
+                df_mac(acc[3 * i + 0], err[3 * i + 0], u, v0);
+                df_mac(acc[3 * i + 1], err[3 * i + 1], u, v1);
+                df_mac(acc[3 * i + 2], err[3 * i + 2], u, v2);
             }
         }
+#pragma unroll
+        for (int t = 0; t < 9; t++) acc[t] += err[t];
         float n2 = 0.0f;
 #pragma unroll
         for (int i = 0; i < 3; i++)
@@ -398,36 +426,40 @@ __global__ void __launch_bounds__(256) k_aca_cols(const BuildBlk* __restrict__ B
     __syncthreads();
     const int ra = it.y + threadIdx.x;
     if (ra >= b.nr) return;
-    float acc[9];
+    float acc[9], err[9];
     entry9(g, g.ra[b.r0 + ra], g.ca[b.c0 + ja], acc);
+#pragma unroll
+    for (int t = 0; t < 9; t++) err[t] = 0.0f;
     const float* u = U + 3LL * ra;
     for (int l = 0; l < k; l++, u += nr3) {
-        const float u0 = u[0], u1 = u[1], u2 = u[2];
+        const float u0 = -u[0], u1 = -u[1], u2 = -u[2];
 #pragma unroll
         for (int jj = 0; jj < 3; jj++) {
             const float v = sv[3 * l + jj];
-            acc[0 + jj] = fmaf(-u0, v, acc[0 + jj]);
-            acc[3 + jj] = fmaf(-u1, v, acc[3 + jj]);
-            acc[6 + jj] = fmaf(-u2, v, acc[6 + jj]);
+            df_mac(acc[0 + jj], err[0 + jj], u0, v);
+            df_mac(acc[3 + jj], err[3 + jj], u1, v);
+            df_mac(acc[6 + jj], err[6 + jj], u2, v);
         }
     }
+#pragma unroll
+    for (int t = 0; t < 9; t++) acc[t] += err[t];
 #pragma unroll
     for (int ii = 0; ii < 3; ii++)
 #pragma unroll
         for (int jj = 0; jj < 3; jj++) U[(long long)(k + jj) * nr3 + 3LL * ra + ii] = acc[3 * ii + jj];
 }
 
-// Step (d), one thread per block: elimination with full pivoting on the 3 x 3 pivot block.  The
-// current rows and columns are tracked as combinations of the raw ones: R'_a = sum Rc[a][.] R,
-// C'_b = sum Cc[b][.] C.
+// Step (d), one thread per block: elimination with full pivoting on the 3 x 3 pivot block (FP64 from
+// the FP32 block).  The pivot sequence and the factors that update the other rows and columns are
+// kept for the emit kernel, which repeats the same elimination on every row and column of the block.
 __global__ void k_aca_pivot(BuildState* __restrict__ S, int n) {
     const int bi = blockIdx.x * blockDim.x + threadIdx.x;
     if (bi >= n) return;
     BuildState& st = S[bi];
     if (!st.active || st.skip) return;
-    double P[9], Rc[9], Cc[9];
-    for (int t = 0; t < 9; t++) P[t] = st.P[t], Rc[t] = (t % 4 == 0), Cc[t] = (t % 4 == 0);
-    double first = 0.0;
+    double P[9];
+    for (int t = 0; t < 9; t++) P[t] = st.P[t];
+    double p0 = st.p0;
     int m = 0;
     for (int step = 0; step < 3; step++) {
         int a = 0, bcol = 0;
@@ -435,37 +467,33 @@ __global__ void k_aca_pivot(BuildState* __restrict__ S, int n) {
         for (int t = 0; t < 9; t++)
             if (fabs(P[t]) > amax) amax = fabs(P[t]), a = t / 3, bcol = t % 3;
         const double piv = P[3 * a + bcol];
-        if (step == 0) first = fabs(piv);
-        if (!(fabs(piv) > 0.0) || (step > 0 && !(fabs(piv) > (double)kPivotDrop * first))) break;
+        if (p0 == 0.0) p0 = fabs(piv);
+        // pivots at the rounding level that the FP32 terms leave in the residual (about 6e-8 of
+        // the block's scale) would add noise and could fill a small block's rank
+        if (!(fabs(piv) > (double)kPivotDrop * p0)) break;
+        st.pa[m] = a, st.pb[m] = bcol, st.piv[m] = (float)piv;
         for (int t = 0; t < 3; t++) {
-            st.au[3 * m + t] = (float)(Cc[3 * bcol + t] / piv);
-            st.bv[3 * m + t] = (float)Rc[3 * a + t];
+            st.rowv[3 * m + t] = (float)P[3 * a + t];
+            st.colv[3 * m + t] = (float)(P[3 * t + bcol] / piv);
         }
         m++;
-        double Po[9], ra[3], cb[3];
+        double Po[9];
         for (int t = 0; t < 9; t++) Po[t] = P[t];
-        for (int t = 0; t < 3; t++) ra[t] = Rc[3 * a + t], cb[t] = Cc[3 * bcol + t];
-        for (int a2 = 0; a2 < 3; a2++) {
-            const double fr = Po[3 * a2 + bcol] / piv;
-            for (int t = 0; t < 3; t++) Rc[3 * a2 + t] -= fr * ra[t];
-        }
-        for (int b2 = 0; b2 < 3; b2++) {
-            const double fc = Po[3 * a + b2] / piv;
-            for (int t = 0; t < 3; t++) Cc[3 * b2 + t] -= fc * cb[t];
-        }
         for (int a2 = 0; a2 < 3; a2++)
             for (int b2 = 0; b2 < 3; b2++) P[3 * a2 + b2] = Po[3 * a2 + b2] - Po[3 * a2 + bcol] * Po[3 * a + b2] / piv;
     }
+    st.p0 = p0;
     st.m = m;
 }
 
-// Step (e): the step's terms from the raw rows and columns, in place in slots k..k+m-1.  Row items
+// Step (e): the step's terms from the raw rows and columns, in place in slots k..k+m-1, by the pivot
+// kernel's elimination repeated on each atom's rows (or columns) in FP32.  Row items
 // also give the Gram partials of the new u and the unused row atom where they are largest; column
 // items give the Gram partials of the new v.
 template <bool ROWS>
 __global__ void __launch_bounds__(256) k_aca_emit(const BuildBlk* __restrict__ B, const BuildState* __restrict__ S,
                                                    const int2* __restrict__ items, const unsigned* __restrict__ used,
-                                                   float* __restrict__ w, float* __restrict__ gram,
+                                                   float* __restrict__ w, double* __restrict__ gram,
                                                    float2* __restrict__ rmax) {
     const int2 it = items[blockIdx.x];
     const BuildBlk b = B[it.x];
@@ -475,23 +503,41 @@ __global__ void __launch_bounds__(256) k_aca_emit(const BuildBlk* __restrict__ B
     const int n = ROWS ? b.nr : b.nc;
     const long long n3 = 3LL * n;
     float* X = w + (ROWS ? b.offU : b.offV);
-    const float* co = ROWS ? st.au : st.bv;
     const int at = it.y + threadIdx.x;
-    float g6[6] = {0, 0, 0, 0, 0, 0};
+    double g6[6] = {0, 0, 0, 0, 0, 0};
     float best = -1.0f;
     int barg = 0x7fffffff;
     if (at < n) {
-        float raw[3][3], out[3][3];
+        float raw[3][3], out[3][3];  // raw[s][e]: raw column (rows) or row (columns) s at dof e
 #pragma unroll
-        for (int s = 0; s < 3; s++)
+        for (int s2 = 0; s2 < 3; s2++)
 #pragma unroll
-            for (int e = 0; e < 3; e++) raw[s][e] = X[(long long)(k + s) * n3 + 3LL * at + e];
+            for (int e = 0; e < 3; e++) raw[s2][e] = X[(long long)(k + s2) * n3 + 3LL * at + e];
 #pragma unroll
-        for (int q = 0; q < 3; q++)
+        for (int q = 0; q < 3; q++) {
 #pragma unroll
-            for (int e = 0; e < 3; e++)
-                out[q][e] = q < m ? fmaf(co[3 * q + 0], raw[0][e], fmaf(co[3 * q + 1], raw[1][e], co[3 * q + 2] * raw[2][e]))
-                                  : 0.0f;
+            for (int e = 0; e < 3; e++) out[q][e] = 0.0f;
+            if (q < m) {
+                if (ROWS) {  // u_q = C'_b / piv, then C'_b2 -= u_q rowv[q][b2]
+                    const int bq = st.pb[q];
+                    const float pv = st.piv[q];
+#pragma unroll
+                    for (int e = 0; e < 3; e++) out[q][e] = (bq == 0 ? raw[0][e] : bq == 1 ? raw[1][e] : raw[2][e]) / pv;
+#pragma unroll
+                    for (int b2 = 0; b2 < 3; b2++)
+#pragma unroll
+                        for (int e = 0; e < 3; e++) raw[b2][e] = fmaf(-out[q][e], st.rowv[3 * q + b2], raw[b2][e]);
+                } else {  // v_q = R'_a, then R'_a2 -= colv[q][a2] v_q
+                    const int aq = st.pa[q];
+#pragma unroll
+                    for (int e = 0; e < 3; e++) out[q][e] = aq == 0 ? raw[0][e] : aq == 1 ? raw[1][e] : raw[2][e];
+#pragma unroll
+                    for (int a2 = 0; a2 < 3; a2++)
+#pragma unroll
+                        for (int e = 0; e < 3; e++) raw[a2][e] = fmaf(-st.colv[3 * q + a2], out[q][e], raw[a2][e]);
+                }
+            }
+        }
 #pragma unroll
         for (int q = 0; q < 3; q++)
             if (q < m) {
@@ -503,15 +549,15 @@ __global__ void __launch_bounds__(256) k_aca_emit(const BuildBlk* __restrict__ B
         for (int q = 0; q < 3; q++)
 #pragma unroll
             for (int q2 = q; q2 < 3; q2++, t++)
-                g6[t] = fmaf(out[q][0], out[q2][0], fmaf(out[q][1], out[q2][1], out[q][2] * out[q2][2]));
+                g6[t] = (double)out[q][0] * out[q2][0] + (double)out[q][1] * out[q2][1] + (double)out[q][2] * out[q2][2];
         if (ROWS) {
             const unsigned* bits = used + b.used;
-            if (!((bits[at >> 5] >> (at & 31)) & 1u)) best = g6[0] + g6[3] + g6[5], barg = at;
+            if (!((bits[at >> 5] >> (at & 31)) & 1u)) best = (float)(g6[0] + g6[3] + g6[5]), barg = at;
         }
     }
-    __shared__ float sg[8][6];
+    __shared__ double sg[8][6];
     for (int t = 0; t < 6; t++) {
-        float v = g6[t];
+        double v = g6[t];
         for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
         g6[t] = v;
     }
@@ -521,7 +567,7 @@ __global__ void __launch_bounds__(256) k_aca_emit(const BuildBlk* __restrict__ B
     else __syncthreads();
     if (threadIdx.x == 0) {
         for (int t = 0; t < 6; t++) {
-            float v = 0.0f;
+            double v = 0.0;
             for (int ww = 0; ww < (int)(blockDim.x >> 5); ww++) v += sg[ww][t];
             gram[6LL * blockIdx.x + t] = v;
         }
@@ -530,11 +576,14 @@ __global__ void __launch_bounds__(256) k_aca_emit(const BuildBlk* __restrict__ B
 }
 
 // Step (f): partial dot products of the step's terms with the earlier ones over a chunk of dofs:
-// part[item][q][l] = sum_{i in chunk} X_l[i] X_{k+q}[i], l < k.  Warps over l, lanes over dofs.
+// part[item][q][l] = sum_{i in chunk} X_l[i] X_{k+q}[i], l < k.  Warps over l, lanes over dofs.  The
+// terms of a cross approximation are much larger than their sum and cancel, so ||S||_F^2 built from
+// plain FP32 dot products drifts by more than S itself (it went negative on a 720 x 480-atom block,
+// and the stopping rule then never held): double-float per lane, FP64 across lanes and chunks.
 template <bool ROWS>
 __global__ void __launch_bounds__(256) k_aca_dots(const BuildBlk* __restrict__ B, const BuildState* __restrict__ S,
                                                    const int2* __restrict__ items, const float* __restrict__ w,
-                                                   float* __restrict__ part) {
+                                                   double* __restrict__ part) {
     __shared__ float snew[3][kDotChunk];
     const int2 it = items[blockIdx.x];
     const BuildBlk b = B[it.x];
@@ -548,17 +597,18 @@ __global__ void __launch_bounds__(256) k_aca_dots(const BuildBlk* __restrict__ B
     for (int q = 0; q < 3; q++)
         for (int t = threadIdx.x; t < cnt; t += blockDim.x) snew[q][t] = q < m ? X[(long long)(k + q) * n3 + i0 + t] : 0.0f;
     __syncthreads();
-    float* out = part + (ROWS ? b.offDU : b.offDV) + (long long)(it.y) * 3 * b.slots;
+    double* out = part + (ROWS ? b.offDU : b.offDV) + (long long)(it.y) * 3 * b.slots;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (int l = warp; l < k; l += (int)(blockDim.x >> 5)) {
         const float* xl = X + (long long)l * n3 + i0;
-        float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f;
+        float s0 = 0.0f, s1 = 0.0f, s2 = 0.0f, e0 = 0.0f, e1 = 0.0f, e2 = 0.0f;
         for (int t = lane; t < cnt; t += 32) {
             const float x = xl[t];
-            a0 = fmaf(x, snew[0][t], a0);
-            a1 = fmaf(x, snew[1][t], a1);
-            a2 = fmaf(x, snew[2][t], a2);
+            df_mac(s0, e0, x, snew[0][t]);
+            df_mac(s1, e1, x, snew[1][t]);
+            df_mac(s2, e2, x, snew[2][t]);
         }
+        double a0 = (double)s0 + (double)e0, a1 = (double)s1 + (double)e1, a2 = (double)s2 + (double)e2;
         for (int o = 16; o > 0; o >>= 1) {
             a0 += __shfl_xor_sync(0xffffffffu, a0, o);
             a1 += __shfl_xor_sync(0xffffffffu, a1, o);
@@ -570,8 +620,8 @@ __global__ void __launch_bounds__(256) k_aca_dots(const BuildBlk* __restrict__ B
 
 // Step (g), one CTA per block: ||S||_F^2 += 2 <S, dS> + ||dS||^2, the stopping rule, the next pivot row.
 __global__ void __launch_bounds__(256) k_aca_finish(const BuildBlk* __restrict__ B, BuildState* __restrict__ S,
-                                                     const float* __restrict__ part, const float* __restrict__ gram_r,
-                                                     const float* __restrict__ gram_c, const float2* __restrict__ rmax,
+                                                     const double* __restrict__ part, const double* __restrict__ gram_r,
+                                                     const double* __restrict__ gram_c, const float2* __restrict__ rmax,
                                                      double eps, int* __restrict__ n_active) {
     const BuildBlk b = B[blockIdx.x];
     BuildState& st = S[blockIdx.x];
@@ -587,8 +637,8 @@ __global__ void __launch_bounds__(256) k_aca_finish(const BuildBlk* __restrict__
     for (int l = threadIdx.x; l < k; l += blockDim.x) {
         for (int q = 0; q < m; q++) {
             double du = 0.0, dv = 0.0;
-            for (int t = 0; t < b.n_dt_r; t++) du += (double)part[b.offDU + (long long)t * 3 * b.slots + q * b.slots + l];
-            for (int t = 0; t < b.n_dt_c; t++) dv += (double)part[b.offDV + (long long)t * 3 * b.slots + q * b.slots + l];
+            for (int t = 0; t < b.n_dt_r; t++) du += part[b.offDU + (long long)t * 3 * b.slots + q * b.slots + l];
+            for (int t = 0; t < b.n_dt_c; t++) dv += part[b.offDV + (long long)t * 3 * b.slots + q * b.slots + l];
             cross += du * dv;
         }
     }
@@ -609,9 +659,9 @@ __global__ void __launch_bounds__(256) k_aca_finish(const BuildBlk* __restrict__
     if (threadIdx.x == 0) {
         double gu[6] = {0, 0, 0, 0, 0, 0}, gv[6] = {0, 0, 0, 0, 0, 0};
         for (int t = 0; t < b.n_it_r; t++)
-            for (int e = 0; e < 6; e++) gu[e] += (double)gram_r[6LL * (b.it_r0 + t) + e];
+            for (int e = 0; e < 6; e++) gu[e] += gram_r[6LL * (b.it_r0 + t) + e];
         for (int t = 0; t < b.n_it_c; t++)
-            for (int e = 0; e < 6; e++) gv[e] += (double)gram_c[6LL * (b.it_c0 + t) + e];
+            for (int e = 0; e < 6; e++) gv[e] += gram_c[6LL * (b.it_c0 + t) + e];
         // ||dS||^2 = sum_{q,q2} (u_q . u_q2)(v_q . v_q2); the 6 entries are the upper triangle
         const double step2 = gu[0] * gv[0] + gu[3] * gv[3] + gu[5] * gv[5] +
                              2.0 * (gu[1] * gv[1] + gu[2] * gv[2] + gu[4] * gv[4]);
@@ -709,97 +759,118 @@ __global__ void k_hm_gather(const double* __restrict__ f, const int* __restrict_
     x[t] = (float)v;
 }
 
-// z partials: for an item (block, 256 column dofs), zp[item][r][l] = sum_j V[j][l] x[r][c0 3 + j].
+// z partials: for an item (block, 256 column dofs), zp[item][r][l] = sum_j V[j][l] x[r][c0 3 + j],
+// summed in double-float and stored in FP64.
+template <int RG>  // right-hand sides of this pass (1..kRG)
 __global__ void __launch_bounds__(256) k_hm_z(const ApplyBlk* __restrict__ A, const int2* __restrict__ items,
-                                               const float* __restrict__ x, long long ncol3, int rg,
-                                               float* __restrict__ zp, const long long* __restrict__ zp_off) {
+                                               const float* __restrict__ x, long long ncol3,
+                                               double* __restrict__ zp, const long long* __restrict__ zp_off) {
+    constexpr int rg = RG;
     __shared__ float sx[kRG][kZCols];
     const int2 it = items[blockIdx.x];
     const ApplyBlk b = A[it.x];
     const long long j0 = (long long)it.y * kZCols;
     const int cnt = (int)min((long long)kZCols, 3LL * b.nc - j0);
-    for (int t = threadIdx.x; t < rg * kZCols; t += blockDim.x) {
+    for (int t = threadIdx.x; t < kRG * kZCols; t += blockDim.x) {
         const int r = t / kZCols, j = t % kZCols;
-        sx[r][j] = j < cnt ? x[(long long)r * ncol3 + 3LL * b.c0 + j0 + j] : 0.0f;
+        sx[r][j] = (j < cnt && r < rg) ? x[(long long)r * ncol3 + 3LL * b.c0 + j0 + j] : 0.0f;
     }
     __syncthreads();
-    float* out = zp + zp_off[blockIdx.x];
+    double* out = zp + zp_off[blockIdx.x];
     const float* V = b.V + j0 * b.k;
     for (int l = threadIdx.x; l < b.k; l += blockDim.x) {
-        float acc[kRG] = {0.0f, 0.0f, 0.0f, 0.0f};
+        float acc[RG], err[RG];
+#pragma unroll
+        for (int r = 0; r < RG; r++) acc[r] = 0.0f, err[r] = 0.0f;
         const float* v = V + l;
         for (int j = 0; j < cnt; j++, v += b.k) {
             const float vv = *v;
 #pragma unroll
-            for (int r = 0; r < kRG; r++) acc[r] = fmaf(vv, sx[r][j], acc[r]);
+            for (int r = 0; r < RG; r++) df_mac(acc[r], err[r], vv, sx[r][j]);
         }
-        for (int r = 0; r < rg; r++) out[(long long)r * b.k + l] = acc[r];
+#pragma unroll
+        for (int r = 0; r < RG; r++) out[(long long)r * b.k + l] = (double)acc[r] + (double)err[r];
     }
 }
 
-// z[b][r][l] = sum over the block's items of the partials, in item order.
-__global__ void k_hm_zsum(const ApplyBlk* __restrict__ A, const float* __restrict__ zp,
-                          const long long* __restrict__ zp_off, int rg, float* __restrict__ z) {
+// z[b][r][l] = sum over the block's items of the partials, in item order (FP64), kept as an FP32
+// pair (hi, lo) with hi + lo = z to about 48 bits.
+__global__ void k_hm_zsum(const ApplyBlk* __restrict__ A, const double* __restrict__ zp,
+                          const long long* __restrict__ zp_off, int rg, float2* __restrict__ z) {
     const ApplyBlk b = A[blockIdx.x];
     if (!b.lowrank) return;
     for (int t = threadIdx.x; t < rg * b.k; t += blockDim.x) {
-        float s = 0.0f;
+        double s = 0.0;
         for (int i = 0; i < b.n_zit; i++) s += zp[zp_off[b.zit0 + i] + t];
-        z[b.offZ + t] = s;
+        const float hi = (float)s;
+        z[b.offZ + t] = make_float2(hi, (float)(s - (double)hi));
     }
 }
 
 // One CTA per row leaf: y = sum over the covering blocks of U z (or D x); then the epilogue
 // u = beta u + alpha y in the caller's layout, and the leaf's sums of the new u (zero mean).
+template <int RG>  // right-hand sides of this pass (1..kRG)
 __global__ void __launch_bounds__(256) k_hm_y(const ApplyBlk* __restrict__ A, const int* __restrict__ leaf_r0,
                                                const int* __restrict__ leaf_nr, const int* __restrict__ cover_off,
-                                               const int* __restrict__ cover, const float* __restrict__ z,
+                                               const int* __restrict__ cover, const float2* __restrict__ z,
                                                const float* __restrict__ x, long long ncol3, const int* __restrict__ perm_p,
-                                               long long n_pat, int rg, double alpha, double beta,
+                                               long long n_pat, double alpha, double beta,
                                                double* __restrict__ u, double* __restrict__ usum, int max_rows) {
+    constexpr int rg = RG;
     extern __shared__ unsigned char smem_raw[];
-    double* y = reinterpret_cast<double*>(smem_raw);            // [rows][kRG]
-    float* sz = reinterpret_cast<float*>(y + (size_t)max_rows * kRG);  // [kRG][k] of the current block
+    double* y = reinterpret_cast<double*>(smem_raw);  // [rows][kRG]
     const int lf = blockIdx.x;
     const int R0 = leaf_r0[lf], NR = leaf_nr[lf];
     const int rows = 3 * NR;
     for (int t = threadIdx.x; t < rows * kRG; t += blockDim.x) y[t] = 0.0;
+    __syncthreads();  // from here on each row's sums belong to one warp
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
     for (int c = cover_off[lf]; c < cover_off[lf + 1]; c++) {
         const ApplyBlk b = A[cover[c]];
-        __syncthreads();  // the previous block's z is no longer read
         const long long row0 = 3LL * (R0 - b.r0);  // the leaf's first row within the block
         if (b.lowrank) {
-            for (int t = threadIdx.x; t < rg * b.k; t += blockDim.x) sz[t] = z[b.offZ + t];
-            __syncthreads();
+            const float2* zb = z + b.offZ;  // read by every row of the leaf: from L1
             for (int i = warp; i < rows; i += nw) {
                 const float* ur = b.U + (row0 + i) * b.k;
-                float acc[kRG] = {0.0f, 0.0f, 0.0f, 0.0f};
+                float acc[RG], err[RG];
+#pragma unroll
+                for (int r = 0; r < RG; r++) acc[r] = 0.0f, err[r] = 0.0f;
                 for (int l = lane; l < b.k; l += 32) {
                     const float uv = ur[l];
 #pragma unroll
-                    for (int r = 0; r < kRG; r++) acc[r] = fmaf(uv, r < rg ? sz[r * b.k + l] : 0.0f, acc[r]);
+                    for (int r = 0; r < RG; r++) {
+                        const float2 zz = __ldg(zb + r * b.k + l);
+                        df_mac(acc[r], err[r], uv, zz.x);
+                        err[r] = __fmaf_rn(uv, zz.y, err[r]);
+                    }
                 }
+                // the lanes' double-float sums meet in FP64
 #pragma unroll
-                for (int r = 0; r < kRG; r++)
-                    for (int o = 16; o > 0; o >>= 1) acc[r] += __shfl_xor_sync(0xffffffffu, acc[r], o);
-                if (lane == 0)
-                    for (int r = 0; r < rg; r++) y[i * kRG + r] += (double)acc[r];
+                for (int r = 0; r < RG; r++) {
+                    double d = (double)acc[r] + (double)err[r];
+                    for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+                    if (lane == 0) y[i * kRG + r] += d;
+                }
             }
         } else {
             const long long nc3 = 3LL * b.nc;
             for (int i = warp; i < rows; i += nw) {
                 const float* dr = b.U + (row0 + i) * nc3;
-                float acc[kRG] = {0.0f, 0.0f, 0.0f, 0.0f};
+                float acc[RG];
+#pragma unroll
+                for (int r = 0; r < RG; r++) acc[r] = 0.0f;
                 for (long long j = lane; j < nc3; j += 32) {
                     const float dv = dr[j];
-                    for (int r = 0; r < rg; r++) acc[r] = fmaf(dv, x[(long long)r * ncol3 + 3LL * b.c0 + j], acc[r]);
+#pragma unroll
+                    for (int r = 0; r < RG; r++) acc[r] = fmaf(dv, x[(long long)r * ncol3 + 3LL * b.c0 + j], acc[r]);
                 }
 #pragma unroll
-                for (int r = 0; r < kRG; r++)
+                for (int r = 0; r < RG; r++)
                     for (int o = 16; o > 0; o >>= 1) acc[r] += __shfl_xor_sync(0xffffffffu, acc[r], o);
-                if (lane == 0)
-                    for (int r = 0; r < rg; r++) y[i * kRG + r] += (double)acc[r];
+                if (lane == 0) {
+#pragma unroll
+                    for (int r = 0; r < RG; r++) y[i * kRG + r] += (double)acc[r];
+                }
             }
         }
     }
@@ -862,8 +933,8 @@ struct fbc_hmat {
     long long* d_zp_off = nullptr;
     int n_zitems = 0;
     float* d_x = nullptr;            // [kRG][3 n_i L]
-    float* d_zp = nullptr;
-    float* d_z = nullptr;
+    double* d_zp = nullptr;          // z partials per item (FP64)
+    float2* d_z = nullptr;           // z of each low-rank block as (hi, lo)
     double* d_fpart = nullptr;       // [kRG][kFParts][3]
     double* d_mean = nullptr;        // [kRG][3]
     double* d_usum = nullptr;        // [kRG][n_leaves][3]
@@ -964,9 +1035,9 @@ int build_wave(fbc_hmat* h, const std::vector<int>& wave, const Geom& g, cudaStr
         max_k = std::max(max_k, slots);
     }
     float* d_w = nullptr;
-    float* d_part = nullptr;
-    float* d_gr = nullptr;
-    float* d_gc = nullptr;
+    double* d_part = nullptr;
+    double* d_gr = nullptr;
+    double* d_gc = nullptr;
     float2* d_pmax = nullptr;
     float2* d_rmax = nullptr;
     unsigned* d_used = nullptr;
@@ -1023,11 +1094,8 @@ int build_wave(fbc_hmat* h, const std::vector<int>& wave, const Geom& g, cudaStr
     WCHK(cudaMemcpyAsync(d_dtc, dt_c.data(), sizeof(int2) * dt_c.size(), cudaMemcpyHostToDevice, st));
     WCHK(cudaMemsetAsync(d_used, 0, sizeof(unsigned) * (size_t)used_words, st));
     WCHK(cudaMemcpyAsync(d_nact, &nb, sizeof(int), cudaMemcpyHostToDevice, st));
+    // at most 3 x 6144 floats (kMaxRank + 3 slots); the kernels' limit is raised once per create
     const size_t smem_k = sizeof(float) * 3 * (size_t)max_k;
-    if (smem_k > 48 * 1024) {
-        WCHK(cudaFuncSetAttribute(k_aca_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_k));
-        WCHK(cudaFuncSetAttribute(k_aca_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_k));
-    }
     // every iteration adds a term or uses up a row atom
     long long max_iter = 0;
     for (const auto& b : bb) max_iter = std::max<long long>(max_iter, (long long)b.slots + b.nr + 8);
@@ -1132,7 +1200,7 @@ int fbc_hmat_create(fbc_plan* plan, const fbc_hmat_options* opt_in, void* stream
     if (!(opt.eps >= 1e-6 && opt.eps < 1.0)) return hfail(FBC_ERR_INVALID_ARG, "eps must be in [1e-6, 1)");
     if (!(opt.gamma > 0.0) || !std::isfinite(opt.gamma)) return hfail(FBC_ERR_INVALID_ARG, "gamma must be positive");
     if (opt.b_min < 1 || opt.b_min > 64) return hfail(FBC_ERR_INVALID_ARG, "b_min must be in 1..64");
-    if (opt.max_rank < 1 || opt.max_rank > kMaxRank) return hfail(FBC_ERR_INVALID_ARG, "max_rank must be in 0..3069");
+    if (opt.max_rank < 1 || opt.max_rank > kMaxRank) return hfail(FBC_ERR_INVALID_ARG, "max_rank must be in 0..6141");
     if (opt.scratch_bytes < 0) return hfail(FBC_ERR_INVALID_ARG, "scratch_bytes must be >= 0");
     if (!plan) return hfail(FBC_ERR_INVALID_ARG, "plan is NULL");
     fbc::Plan& P = plan->p;
@@ -1253,6 +1321,9 @@ int fbc_hmat_create(fbc_plan* plan, const fbc_hmat_options* opt_in, void* stream
             TCHK(cudaGetLastError());
             I.dense_bytes = (long long)(sizeof(float) * dense_n);
         }
+        // one limit for every build (the attribute belongs to the kernels, not to this object)
+        TCHK(cudaFuncSetAttribute(k_aca_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBuildSmemMax));
+        TCHK(cudaFuncSetAttribute(k_aca_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBuildSmemMax));
         // low-rank blocks in waves that share the build scratch
         size_t free_b = 0, total_b = 0;
         TCHK(cudaMemGetInfo(&free_b, &total_b));
@@ -1355,14 +1426,7 @@ int fbc_hmat_create(fbc_plan* plan, const fbc_hmat_options* opt_in, void* stream
         CCHK(cudaMemcpyAsync(h->d_zitems, zit.data(), sizeof(int2) * zit.size(), cudaMemcpyHostToDevice, st));
         CCHK(cudaMemcpyAsync(h->d_zp_off, zoff.data(), sizeof(long long) * zoff.size(), cudaMemcpyHostToDevice, st));
     }
-    h->apply_smem = sizeof(double) * (size_t)h->max_leaf_rows * kRG + sizeof(float) * (size_t)kRG * h->max_k;
-    if (h->apply_smem > 48 * 1024) {
-        if (h->apply_smem > 200 * 1024) {
-            free_hmat(h);
-            return hfail(FBC_ERR_UNSUPPORTED, "H-matrix: rank too large for the apply's shared memory");
-        }
-        CCHK(cudaFuncSetAttribute(k_hm_y, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)h->apply_smem));
-    }
+    h->apply_smem = sizeof(double) * (size_t)h->max_leaf_rows * kRG;  // at most 64 atoms: 6 KB
     CCHK(cudaStreamSynchronize(st));
     cudaGetDevice(&h->device);
     I.build_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
@@ -1381,31 +1445,42 @@ int fbc_hmat_apply(fbc_hmat* h, const double* f, double* u, int32_t n_rhs, doubl
     cudaStream_t st = (cudaStream_t)stream;
     const long long n_iat = (long long)h->n_i * h->L, n_pat = (long long)h->n_p * h->L;
     const bool project = flags & FBC_APPLY_PROJECT_NEUTRAL, zmean = flags & FBC_APPLY_ZERO_MEAN_U;
+    cudaError_t e;
+#define HLAUNCH(name, ...)                                     \
+    do {                                                       \
+        __VA_ARGS__;                                           \
+        if ((e = cudaGetLastError()) != cudaSuccess) return hcuda(e, "fbc_hmat_apply: " name); \
+    } while (0)
     for (int g0 = 0; g0 < n_rhs; g0 += kRG) {
         const int rg = std::min(kRG, n_rhs - g0);
         const double* fg = f + (long long)g0 * n_iat * 3;
         double* ug = u + (long long)g0 * n_pat * 3;
         if (project) {
-            k_hm_fsum<<<dim3(kFParts, rg), 256, 0, st>>>(fg, n_iat, h->d_fpart);
-            k_hm_mean<<<rg, 32, 0, st>>>(h->d_fpart, kFParts, n_iat, h->d_mean);
+            HLAUNCH("k_hm_fsum", k_hm_fsum<<<dim3(kFParts, rg), 256, 0, st>>>(fg, n_iat, h->d_fpart));
+            HLAUNCH("k_hm_mean", k_hm_mean<<<rg, 32, 0, st>>>(h->d_fpart, kFParts, n_iat, h->d_mean));
         }
         const long long nx = (long long)rg * n_iat * 3;
-        k_hm_gather<<<(unsigned)((nx + 255) / 256), 256, 0, st>>>(fg, h->d_perm_i, n_iat, rg, project ? h->d_mean : nullptr,
-                                                                 h->d_x);
+        HLAUNCH("k_hm_gather", k_hm_gather<<<(unsigned)((nx + 255) / 256), 256, 0, st>>>(
+                                   fg, h->d_perm_i, n_iat, rg, project ? h->d_mean : nullptr, h->d_x));
         if (h->n_zitems) {
-            k_hm_z<<<h->n_zitems, 256, 0, st>>>(h->d_blocks, h->d_zitems, h->d_x, 3 * n_iat, rg, h->d_zp, h->d_zp_off);
-            k_hm_zsum<<<(unsigned)h->blocks.size(), 256, 0, st>>>(h->d_blocks, h->d_zp, h->d_zp_off, rg, h->d_z);
+#define HZ(R) k_hm_z<R><<<h->n_zitems, 256, 0, st>>>(h->d_blocks, h->d_zitems, h->d_x, 3 * n_iat, h->d_zp, h->d_zp_off)
+            HLAUNCH("k_hm_z", if (rg == 1) HZ(1); else if (rg == 2) HZ(2); else if (rg == 3) HZ(3); else HZ(4));
+#undef HZ
+            HLAUNCH("k_hm_zsum", k_hm_zsum<<<(unsigned)h->blocks.size(), 256, 0, st>>>(h->d_blocks, h->d_zp,
+                                                                                      h->d_zp_off, rg, h->d_z));
         }
-        k_hm_y<<<h->n_leaves, 256, h->apply_smem, st>>>(h->d_blocks, h->d_leaf_r0, h->d_leaf_nr, h->d_cover_off, h->d_cover,
-                                                        h->d_z, h->d_x, 3 * n_iat, h->d_perm_p, n_pat, rg, alpha, beta, ug,
-                                                        zmean ? h->d_usum : nullptr, h->max_leaf_rows);
+#define HY(R)                                                                                                  \
+    k_hm_y<R><<<h->n_leaves, 256, h->apply_smem, st>>>(h->d_blocks, h->d_leaf_r0, h->d_leaf_nr, h->d_cover_off,     \
+                                                       h->d_cover, h->d_z, h->d_x, 3 * n_iat, h->d_perm_p, n_pat,    \
+                                                       alpha, beta, ug, zmean ? h->d_usum : nullptr, h->max_leaf_rows)
+        HLAUNCH("k_hm_y", if (rg == 1) HY(1); else if (rg == 2) HY(2); else if (rg == 3) HY(3); else HY(4));
+#undef HY
         if (zmean) {
-            k_hm_mean<<<rg, 32, 0, st>>>(h->d_usum, h->n_leaves, n_pat, h->d_mean);
-            k_hm_usub<<<dim3(kFParts, rg), 256, 0, st>>>(ug, n_pat, h->d_mean);
+            HLAUNCH("k_hm_mean", k_hm_mean<<<rg, 32, 0, st>>>(h->d_usum, h->n_leaves, n_pat, h->d_mean));
+            HLAUNCH("k_hm_usub", k_hm_usub<<<dim3(kFParts, rg), 256, 0, st>>>(ug, n_pat, h->d_mean));
         }
-        cudaError_t e = cudaGetLastError();
-        if (e != cudaSuccess) return hcuda(e, "fbc_hmat_apply launch");
     }
+#undef HLAUNCH
     return FBC_OK;
 }
 

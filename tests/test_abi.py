@@ -157,7 +157,7 @@ def test_hmat_entry_points_validate_before_device_work(lib):
     """H-matrix: bad options, NULL handles and host-only plans are rejected without device work."""
     h = ctypes.c_void_p()
     bad = [fbc.fbc_hmat_options(1e-7, 2.0, 20, 0, 0), fbc.fbc_hmat_options(1e-5, 0.0, 20, 0, 0),
-           fbc.fbc_hmat_options(1e-5, 2.0, 0, 0, 0), fbc.fbc_hmat_options(1e-5, 2.0, 20, 5000, 0),
+           fbc.fbc_hmat_options(1e-5, 2.0, 0, 0, 0), fbc.fbc_hmat_options(1e-5, 2.0, 20, 7000, 0),
            fbc.fbc_hmat_options(1e-5, 2.0, 20, 0, -1)]
     for opt in bad:
         assert lib.fbc_hmat_create(None, ctypes.byref(opt), None, ctypes.byref(h)) == fbc.FBC_ERR_INVALID_ARG
