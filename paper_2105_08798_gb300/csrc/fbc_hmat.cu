@@ -286,6 +286,23 @@ __device__ __forceinline__ void df_mac(float& S, float& E, float a, float b) {
     E = __fadd_rn(E, __fadd_rn(lost, rest));
 }
 
+// (S, E) <- (S, E) + (S2, E2): two-sum of the leading parts, the rest added to the trailing part.
+__device__ __forceinline__ void df_add(float& S, float& E, float S2, float E2) {
+    const float s = __fadd_rn(S, S2);
+    const float bb = __fsub_rn(s, S);
+    const float err = __fadd_rn(__fsub_rn(S, __fsub_rn(s, bb)), __fsub_rn(S2, bb));
+    E = __fadd_rn(__fadd_rn(E, E2), err);
+    S = s;
+}
+
+// The warp's double-float sum, in FP32 operations (no FP64 pipe work per row); every lane gets it.
+__device__ __forceinline__ void df_warp_sum(float& S, float& E) {
+    for (int o = 16; o > 0; o >>= 1) {
+        const float s2 = __shfl_xor_sync(0xffffffffu, S, o), e2 = __shfl_xor_sync(0xffffffffu, E, o);
+        df_add(S, E, s2, e2);
+    }
+}
+
 __device__ __forceinline__ void argmax_merge(float& v, int& i, float v2, int i2) {
     if (v2 > v || (v2 == v && i2 < i)) v = v2, i = i2;
 }
@@ -779,17 +796,35 @@ __global__ void __launch_bounds__(256) k_hm_z(const ApplyBlk* __restrict__ A, co
     double* out = zp + zp_off[blockIdx.x];
     const float* V = b.V + j0 * b.k;
     for (int l = threadIdx.x; l < b.k; l += blockDim.x) {
-        float acc[RG], err[RG];
+        // four interleaved chains over j (columns j = c mod 4), joined in a fixed order
+        float acc[4][RG], err[4][RG];
 #pragma unroll
-        for (int r = 0; r < RG; r++) acc[r] = 0.0f, err[r] = 0.0f;
+        for (int c = 0; c < 4; c++)
+#pragma unroll
+            for (int r = 0; r < RG; r++) acc[c][r] = 0.0f, err[c][r] = 0.0f;
         const float* v = V + l;
-        for (int j = 0; j < cnt; j++, v += b.k) {
+        int j = 0;
+        for (; j + 4 <= cnt; j += 4, v += 4LL * b.k) {
+            float vv[4];
+#pragma unroll
+            for (int c = 0; c < 4; c++) vv[c] = v[(long long)c * b.k];
+#pragma unroll
+            for (int c = 0; c < 4; c++)
+#pragma unroll
+                for (int r = 0; r < RG; r++) df_mac(acc[c][r], err[c][r], vv[c], sx[r][j + c]);
+        }
+        for (int c = 0; j < cnt; j++, c++, v += b.k) {
             const float vv = *v;
 #pragma unroll
-            for (int r = 0; r < RG; r++) df_mac(acc[r], err[r], vv, sx[r][j]);
+            for (int r = 0; r < RG; r++) df_mac(acc[0][r], err[0][r], vv, sx[r][j]);
         }
 #pragma unroll
-        for (int r = 0; r < RG; r++) out[(long long)r * b.k + l] = (double)acc[r] + (double)err[r];
+        for (int r = 0; r < RG; r++) {
+            df_add(acc[0][r], err[0][r], acc[1][r], err[1][r]);
+            df_add(acc[2][r], err[2][r], acc[3][r], err[3][r]);
+            df_add(acc[0][r], err[0][r], acc[2][r], err[2][r]);
+            out[(long long)r * b.k + l] = (double)acc[0][r] + (double)err[0][r];
+        }
     }
 }
 
@@ -830,26 +865,39 @@ __global__ void __launch_bounds__(256) k_hm_y(const ApplyBlk* __restrict__ A, co
         const long long row0 = 3LL * (R0 - b.r0);  // the leaf's first row within the block
         if (b.lowrank) {
             const float2* zb = z + b.offZ;  // read by every row of the leaf: from L1
-            for (int i = warp; i < rows; i += nw) {
-                const float* ur = b.U + (row0 + i) * b.k;
-                float acc[RG], err[RG];
+            constexpr int RR = 4;            // rows per warp at a time: each z load serves four rows
+            for (int i0 = warp; i0 < rows; i0 += nw * RR) {
+                float acc[RR][RG], err[RR][RG];
+                const float* ur[RR];
 #pragma unroll
-                for (int r = 0; r < RG; r++) acc[r] = 0.0f, err[r] = 0.0f;
+                for (int q = 0; q < RR; q++) {
+                    const int i = min(i0 + q * nw, rows - 1);  // rows past the leaf repeat its last row
+                    ur[q] = b.U + (row0 + i) * b.k;
+#pragma unroll
+                    for (int r = 0; r < RG; r++) acc[q][r] = 0.0f, err[q][r] = 0.0f;
+                }
                 for (int l = lane; l < b.k; l += 32) {
-                    const float uv = ur[l];
+                    float2 zz[RG];
 #pragma unroll
-                    for (int r = 0; r < RG; r++) {
-                        const float2 zz = __ldg(zb + r * b.k + l);
-                        df_mac(acc[r], err[r], uv, zz.x);
-                        err[r] = __fmaf_rn(uv, zz.y, err[r]);
+                    for (int r = 0; r < RG; r++) zz[r] = __ldg(zb + r * b.k + l);
+#pragma unroll
+                    for (int q = 0; q < RR; q++) {
+                        const float uv = ur[q][l];
+#pragma unroll
+                        for (int r = 0; r < RG; r++) {
+                            df_mac(acc[q][r], err[q][r], uv, zz[r].x);
+                            err[q][r] = __fmaf_rn(uv, zz[r].y, err[q][r]);
+                        }
                     }
                 }
-                // the lanes' double-float sums meet in FP64
 #pragma unroll
-                for (int r = 0; r < RG; r++) {
-                    double d = (double)acc[r] + (double)err[r];
-                    for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
-                    if (lane == 0) y[i * kRG + r] += d;
+                for (int q = 0; q < RR; q++) {
+                    const int i = i0 + q * nw;
+#pragma unroll
+                    for (int r = 0; r < RG; r++) {
+                        df_warp_sum(acc[q][r], err[q][r]);
+                        if (lane == 0 && i < rows) y[i * kRG + r] += (double)acc[q][r] + (double)err[q][r];
+                    }
                 }
             }
         } else {

@@ -144,6 +144,9 @@ WORKLOADS = {
     "ring8000x12000_L1024_rhs64_iso": Workload("ring8000x12000_L1024_rhs64_iso", 8000, 12000, 1024, 64, ISO, 4),
     # the same kind of case at a size a profiler capture can hold (a few GB on the device)
     "ring4000x6000_L256_rhs64_iso": Workload("ring4000x6000_L256_rhs64_iso", 4000, 6000, 256, 64, ISO, 5),
+    # the H-matrix comparison: 96 000 pad atoms, where the H-matrix at eps = 1e-5 (about 19 GB of
+    # FP32 factors) fits on one GPU; at 4000 x 6000, L = 256 it does not
+    "ring1000x1500_L64_iso": Workload("ring1000x1500_L64_iso", 1000, 1500, 64, 1, ISO, 6),
 }
 
 
