@@ -828,15 +828,27 @@ __global__ void __launch_bounds__(256) k_hm_z(const ApplyBlk* __restrict__ A, co
     }
 }
 
-// z[b][r][l] = sum over the block's items of the partials, in item order (FP64), kept as an FP32
-// pair (hi, lo) with hi + lo = z to about 48 bits.
-__global__ void k_hm_zsum(const ApplyBlk* __restrict__ A, const double* __restrict__ zp,
-                          const long long* __restrict__ zp_off, int rg, float2* __restrict__ z) {
+// z[b][r][l] = sum over the block's items of the partials, in a fixed order, kept as an FP32 pair
+// (hi, lo) with hi + lo = z to about 48 bits.  CTA (b, tile): 32 entries t of z_b times 8 subsets
+// of the items (item i in subset i mod 8); the subsets meet in order.  A block's items are
+// consecutive in the partial buffer, kRG k numbers apart.
+__global__ void __launch_bounds__(256) k_hm_zsum(const ApplyBlk* __restrict__ A, const double* __restrict__ zp,
+                                                  const long long* __restrict__ zp_off, int rg, float2* __restrict__ z) {
+    __shared__ double red[8][32];
     const ApplyBlk b = A[blockIdx.x];
-    if (!b.lowrank) return;
-    for (int t = threadIdx.x; t < rg * b.k; t += blockDim.x) {
+    if (!b.lowrank || b.n_zit == 0) return;
+    const int n = rg * b.k;
+    const int t = blockIdx.y * 32 + (threadIdx.x & 31), sub = threadIdx.x >> 5;
+    if (blockIdx.y * 32 >= n) return;
+    const long long base = zp_off[b.zit0], stride = (long long)kRG * b.k;
+    double c = 0.0;
+    if (t < n)
+        for (int i = sub; i < b.n_zit; i += 8) c += zp[base + (long long)i * stride + t];
+    red[sub][threadIdx.x & 31] = c;
+    __syncthreads();
+    if (sub == 0 && t < n) {
         double s = 0.0;
-        for (int i = 0; i < b.n_zit; i++) s += zp[zp_off[b.zit0 + i] + t];
+        for (int q = 0; q < 8; q++) s += red[q][threadIdx.x];
         const float hi = (float)s;
         z[b.offZ + t] = make_float2(hi, (float)(s - (double)hi));
     }
@@ -1514,8 +1526,9 @@ int fbc_hmat_apply(fbc_hmat* h, const double* f, double* u, int32_t n_rhs, doubl
 #define HZ(R) k_hm_z<R><<<h->n_zitems, 256, 0, st>>>(h->d_blocks, h->d_zitems, h->d_x, 3 * n_iat, h->d_zp, h->d_zp_off)
             HLAUNCH("k_hm_z", if (rg == 1) HZ(1); else if (rg == 2) HZ(2); else if (rg == 3) HZ(3); else HZ(4));
 #undef HZ
-            HLAUNCH("k_hm_zsum", k_hm_zsum<<<(unsigned)h->blocks.size(), 256, 0, st>>>(h->d_blocks, h->d_zp,
-                                                                                      h->d_zp_off, rg, h->d_z));
+            const unsigned tiles = (unsigned)((rg * h->max_k + 31) / 32);
+            HLAUNCH("k_hm_zsum", k_hm_zsum<<<dim3((unsigned)h->blocks.size(), tiles), 256, 0, st>>>(
+                                     h->d_blocks, h->d_zp, h->d_zp_off, rg, h->d_z));
         }
 #define HY(R)                                                                                                  \
     k_hm_y<R><<<h->n_leaves, 256, h->apply_smem, st>>>(h->d_blocks, h->d_leaf_r0, h->d_leaf_nr, h->d_cover_off,     \
