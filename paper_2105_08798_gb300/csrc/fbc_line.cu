@@ -526,12 +526,15 @@ __device__ __forceinline__ void inv_block_s(const double* __restrict__ uh, const
     const int nseq = NC + NC / 2, logNC = __ffs(NC) - 1, Lh = L >> 1;
     float2* A = (float2*)sraw;
     float2* B = A + fft::padded(nseq * L);
+    // FP64 k = 0 term per column, and the column's final k = 0 value: after the two FFT buffers in
+    // the dynamic shared memory (sized for this launch's NC, not the largest), so that at L = 1024
+    // four CTAs fit on an SM
+    double (*u0)[3] = reinterpret_cast<double (*)[3]>(B + fft::padded(nseq * L));
+    double (*uk)[3] = u0 + NC;
     const int a0 = blk * NC;
     if (alpha_dev) alpha_over_L = alpha_dev_scale * alpha_dev[r];
     const bool max_only = gmax_part != nullptr;
     const bool has_beta = beta != 0.0;
-    __shared__ double u0[64][3];  // FP64 k = 0 term per column
-    __shared__ double uk[64][3];
     // Z = U1 + i U2 per column: Z(k) and Z(L - k) = conj U1 + i conj U2
     for (int t = threadIdx.x; t < NC * K; t += blockDim.x) {
         const int k = t >> logNC, j = t & (NC - 1);
@@ -653,31 +656,34 @@ __device__ __forceinline__ void inv_block_s(const double* __restrict__ uh, const
             if (want_part) ps0 += o[0], ps0 += o[3], ps1 += o[1], ps1 += o[4], ps2 += o[2], ps2 += o[5];
         }
     }
-    __shared__ double red[3 * 256];  // block reductions (the maximum, or the three partial sums)
+    // block reductions (the maximum, or the three partial sums): a fixed shuffle tree per warp, then
+    // the warps in order; 192 bytes of static shared memory, so shared memory allows a fourth CTA
+    __shared__ double red[8][3];
     if (max_only) {
-        double* redm = red;
-        redm[threadIdx.x] = (double)mx32;
+        float m = mx32;
+        for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+        if (lane == 0) red[warp][0] = (double)m;
         __syncthreads();
-        for (int w = blockDim.x / 2; w > 0; w >>= 1) {
-            if ((int)threadIdx.x < w) redm[threadIdx.x] = fmax(redm[threadIdx.x], redm[threadIdx.x + w]);
-            __syncthreads();
+        if (threadIdx.x == 0) {
+            double mm = red[0][0];
+            for (int w = 1; w < nw; w++) mm = fmax(mm, red[w][0]);
+            gmax_part[(size_t)r * n_blk + blk] = mm;
         }
-        if (threadIdx.x == 0) gmax_part[(size_t)r * n_blk + blk] = redm[0];
         return;
     }
     if (want_part) {
-        red[threadIdx.x] = ps0;
-        red[256 + threadIdx.x] = ps1;
-        red[512 + threadIdx.x] = ps2;
-        __syncthreads();
-        for (int w = blockDim.x / 2; w > 0; w >>= 1) {
-            if ((int)threadIdx.x < w)
-                for (int c = 0; c < 3; c++) red[256 * c + threadIdx.x] += red[256 * c + threadIdx.x + w];
-            __syncthreads();
+        for (int o = 16; o > 0; o >>= 1) {
+            ps0 += __shfl_xor_sync(0xffffffffu, ps0, o);
+            ps1 += __shfl_xor_sync(0xffffffffu, ps1, o);
+            ps2 += __shfl_xor_sync(0xffffffffu, ps2, o);
         }
+        if (lane == 0) red[warp][0] = ps0, red[warp][1] = ps1, red[warp][2] = ps2;
+        __syncthreads();
         if (threadIdx.x == 0) {
+            double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+            for (int w = 0; w < nw; w++) s0 += red[w][0], s1 += red[w][1], s2 += red[w][2];
             double* pp = part + ((size_t)r * n_blk + blk) * 3;
-            pp[0] = red[0], pp[1] = red[256], pp[2] = red[512];
+            pp[0] = s0, pp[1] = s1, pp[2] = s2;
         }
     }
 }
@@ -774,7 +780,9 @@ __global__ void k_batch_zero_mean(const LineArgs* __restrict__ la, const int4* _
 
 size_t line_smem(int L, int NC) { return (size_t)(NC + NC / 2) * L * sizeof(double2); }
 // the Stockham FP32 form: two padded buffers of FP32 complex numbers
-size_t line_smem_s(int L, int NC) { return (size_t)2 * fft::padded((NC + NC / 2) * L) * sizeof(float2); }
+size_t line_smem_s(int L, int NC) {
+    return (size_t)2 * fft::padded((NC + NC / 2) * L) * sizeof(float2) + (size_t)2 * NC * 3 * sizeof(double);
+}
 
 }  // namespace
 
