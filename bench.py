@@ -234,6 +234,11 @@ def run_reference(args, w):
         oracle.real_space_sum(d_index, table, fp, samp_col, samp_p)
     dt = (time.perf_counter() - t0) / max(1, args.steps)
     value = w.pair_modes * share / dt / 1e9
+    # the same sum on one core, over a quarter of the sample's pad atoms (after the timed steps)
+    m1 = max(1, n_rep // 4)
+    t1 = time.perf_counter()
+    oracle.real_space_sum(d_index, table, fp, samp_col[:m1], samp_p[:m1], nthreads=1)
+    t_one = time.perf_counter() - t1
     info = oracle.sys_info()
     sample = (f"{n_rep} pad atoms (repeats 0..{n_rep - 1} of pad column 0, right-hand side 0) per step: the full "
               f"real-space sum over {w.n_i} x {w.L} interface atoms each, {share:.3g} of the update; kernel "
@@ -246,7 +251,9 @@ def run_reference(args, w):
                    "material": w.material.get("kind"), "sampled": True},
         "extrapolated_full_update_ms": dt / share * 1e3,
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": info["cores"], "kind": "oracle", "sample": sample,
-                         "cpu": info["cpu"]},
+                         "cpu": info["cpu"],
+                         "one_core": {"value": w.pair_modes * share * (m1 / n_rep) / t_one / 1e9, "unit": UNIT,
+                                      "cores": 1, "sample": f"repeats 0..{m1 - 1} of pad column 0, once ({t_one:.1f} s)"}},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -615,8 +622,15 @@ def run_ours(args, w):
             oracle.real_space_sum(d0, t0_, fp[:1], sc0, sp0)
             t_cpu += time.perf_counter() - t1
             reps += 1
+        # the same sum on one core, over a quarter of the sample's pad atoms
+        m1 = max(1, n_rep // 4)
+        t1 = time.perf_counter()
+        oracle.real_space_sum(d0, t0_, fp[:1], sc0[:m1], sp0[:m1], nthreads=1)
+        t_one = time.perf_counter() - t1
         sinfo = oracle.sys_info()
         cpu = {"value": pm * share / (t_cpu / reps) / 1e9, "unit": UNIT, "cores": sinfo["cores"], "kind": "oracle",
+               "one_core": {"value": pm * share * (m1 / n_rep) / t_one / 1e9, "unit": UNIT, "cores": 1,
+                            "sample": f"repeats 0..{m1 - 1} of pad column 0, right-hand side 0, once ({t_one:.1f} s)"},
                "sample": (f"real-space sum at {n_rep} pad atoms (repeats 0..{n_rep - 1} of pad column 0, right-hand "
                           f"side 0) x {reps} repetitions ({t_cpu:.1f} s): {share:.3g} of the update per repetition; "
                           "kernel tabulation for the sample untimed"),
