@@ -525,6 +525,12 @@ int fbc_plan_attach_surrogate(fbc_plan* plan, fbc_surrogate* s, double r_min, in
 void fbc_surrogate_destroy(fbc_surrogate* s);
 
 
+/* Measured rate of fused multiply-adds on this GPU, for the rooflines of the CUDA-core forms:
+ * FP32 (fp64 = 0) or FP64 (fp64 = 1), 2 flops per FMA.  8 CTAs of 256 threads per SM run 8
+ * independent chains per thread; the second of two launches is timed with events on `stream`.
+ * *tflops receives TFLOP/s.  Blocks until done; allocates a small buffer. */
+int fbc_measure_fma_peak(int32_t fp64, double* tflops, void* stream);
+
 /* ---------------------------------------------------------------------------
  * H-matrix form of the pad update (Sec. 3.2; App., the construction of the
  * H-matrix approximation of the Green matrix): the comparison form.  The

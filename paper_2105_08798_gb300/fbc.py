@@ -177,6 +177,7 @@ _SIGNATURES = {
     "fbc_hmat_get_info": (ctypes.c_int, [_vp, _P(fbc_hmat_info)]),
     "fbc_hmat_blocks": (ctypes.c_int, [_vp, _P(ctypes.c_int64), _P(ctypes.c_int32), ctypes.c_int64]),
     "fbc_hmat_destroy": (None, [_vp]),
+    "fbc_measure_fma_peak": (ctypes.c_int, [ctypes.c_int32, _P(ctypes.c_double), _vp]),
 }
 
 
@@ -443,6 +444,14 @@ def fbc_surrogate_destroy(sur: int):
 
 
 # ---- convenience wrapper -----------------------------------------------------
+def fbc_measure_fma_peak(fp64: bool, stream=None) -> float:
+    """Measured FP32 (or FP64) fused multiply-add rate of this GPU in TFLOP/s."""
+    t = ctypes.c_double(0.0)
+    _check(load().fbc_measure_fma_peak(1 if fp64 else 0, ctypes.byref(t), _stream_handle(stream)),
+           "fbc_measure_fma_peak")
+    return t.value
+
+
 def fbc_hmat_partition(xy_i: np.ndarray, xy_p: np.ndarray, L: int, c: float = 1.0, gamma: float = 2.0,
                        b_min: int = 20) -> tuple[np.ndarray, np.ndarray, np.ndarray]:
     """Steps 1-2 of the H-matrix construction on the host: (blocks [n][5], perm_p, perm_i)."""

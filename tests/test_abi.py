@@ -163,6 +163,7 @@ def test_hmat_entry_points_validate_before_device_work(lib):
         assert lib.fbc_hmat_create(None, ctypes.byref(opt), None, ctypes.byref(h)) == fbc.FBC_ERR_INVALID_ARG
         assert h.value is None
     assert lib.fbc_hmat_create(None, None, None, ctypes.byref(h)) == fbc.FBC_ERR_INVALID_ARG
+    assert lib.fbc_measure_fma_peak(0, None, None) == fbc.FBC_ERR_INVALID_ARG
     assert lib.fbc_hmat_apply(None, None, None, 1, 1.0, 0.0, 0, None) == fbc.FBC_ERR_INVALID_ARG
     assert lib.fbc_hmat_get_info(None, None) == fbc.FBC_ERR_INVALID_ARG
     lib.fbc_hmat_destroy(None)
