@@ -19,7 +19,10 @@
 // unevaluated pair of FP32 numbers -- Dekker's exact product via FMA, Knuth's
 // two-sum -- and each interface tile's partial folded into a double-float
 // running total, FP64-accurate on the FP32 pipes).
+#include <cuda.h>  // CUtensorMap and its encoder's types (the encoder is reached through the runtime)
+
 #include "fbc_internal.cuh"
+#include "fbc_tc.cuh"
 
 namespace fbc {
 namespace {
@@ -253,13 +256,63 @@ __device__ __forceinline__ void df_fold(float& Thi, float& Tlo, float S, float E
     Tlo = __fsub_rn(e, __fsub_rn(Thi, s));
 }
 
-// Double-float: each table entry is staged as three 16-byte records
-// (a11h, a11l, a12h, a12l), (a22h, a22l, a33h, a33l), (b13h, b13l, b23h, b23l)
-// and each interface column as four: the (hi, lo) pairs of x and y' and off_b.
+// Double-float sub-box staging.  The table holds each entry as three 16-byte
+// records (a11h, a11l, a12h, a12l), (a22h, a22l, a33h, a33l), (b13h, b13l,
+// b23h, b23l), the layout kept in shared memory, so the W x H sub-box of a
+// tile pair is a box of a three-dimensional tensor of 8-byte elements (6 Dx
+// per table row, Dy rows, modes): H lines of 48 W contiguous bytes.  With a
+// tensor map (tmap != nullptr) thread 0 fetches it with one TMA copy that
+// completes on the barrier `bar` and zero-fills the part outside the table;
+// without one (the persistent batch kernel, or a box line over the copy
+// engine's 256 elements, W > 42) the CTA's threads copy it entry by entry.
+__device__ __forceinline__ void x2_box_issue(const ContractArgs& A, int k, int ox, int oy, float4* s_tab,
+                                             const void* tmap, uint64_t* bar, int nthreads) {
+    if (tmap) {
+        if (threadIdx.x == 0) {
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // after the last tile's reads
+            tc::mbar_expect_tx(bar, (uint32_t)(A.H * A.W) * 48u);
+            tc::tma_load_3d(s_tab, tmap, bar, 6 * (ox - A.box_x0), oy - A.box_y0, k - A.kbase);
+        }
+        return;
+    }
+    const float* tk = A.tabx2 + (size_t)(k - A.kbase) * A.Dy * A.Dx * 12;
+    const int HW = A.H * A.W;
+    for (int e = threadIdx.x; e < HW; e += nthreads) {
+        const int iy = e / A.W, ix = e - iy * A.W;
+        const int gx = ox + ix - A.box_x0, gy = oy + iy - A.box_y0;
+        float4 q0 = make_float4(0, 0, 0, 0), q1 = q0, q2 = q0;
+        if (gx < A.Dx && gy < A.Dy) {
+            const float4* src = (const float4*)(tk + ((size_t)gy * A.Dx + gx) * 12);
+            q0 = __ldg(src), q1 = __ldg(src + 1), q2 = __ldg(src + 2);
+        }
+        s_tab[3 * e] = q0, s_tab[3 * e + 1] = q1, s_tab[3 * e + 2] = q2;
+    }
+}
+
+// The barrier before a tile's products.  With TMA staging every thread first
+// waits (bounded) for the sub-box of interface tile tB, the barrier's phase
+// tB.  Returns true for every thread of the CTA when a wait gave up: the CTA
+// has then recorded the status word and waited once more (bounded) for its
+// copy in flight, and leaves the tile without writing results.
+__device__ __forceinline__ bool x2_box_wait(const ContractArgs& A, const void* tmap, uint64_t* bar, int tB) {
+    if (!tmap) {
+        __syncthreads();
+        return false;
+    }
+    const bool late = !tc::mbar_wait(bar, (uint32_t)tB & 1u);
+    if (!__syncthreads_or(late)) return false;
+    if (threadIdx.x == 0) atomicExch(A.status, FBC_ERR_TIMEOUT);
+    if (late) tc::mbar_wait(bar, (uint32_t)tB & 1u);
+    return true;
+}
+
+// Double-float: the table sub-box staged as above and each interface column as
+// four records: the (hi, lo) pairs of x and y' and off_b.
 // K0: the tile of the one-mode k = 0 launches (a separate instance, so that the
 // all-modes loop keeps its own code).
 template <int TA, int TB, bool K0>
-__device__ __forceinline__ void tile_x2(const ContractArgs& A, int tA, int k, int r, void* smem_raw) {
+__device__ __forceinline__ void tile_x2(const ContractArgs& A, int tA, int k, int r, void* smem_raw,
+                                        const void* tmap = nullptr, uint64_t* bar = nullptr) {
     float4* smemx2 = (float4*)smem_raw;
     const int HW = A.H * A.W;
     float4* s_tab = smemx2;            // [HW][3]
@@ -269,25 +322,11 @@ __device__ __forceinline__ void tile_x2(const ContractArgs& A, int tA, int k, in
     const int4 bA = A.bbox_a[tA];
     float Th[6] = {0, 0, 0, 0, 0, 0}, Tl[6] = {0, 0, 0, 0, 0, 0};
     const double* fk = A.fh + ((size_t)r * A.K + k) * A.NIpad * 6;
-    const float* tk = A.tabx2 + (size_t)(k - A.kbase) * A.Dy * A.Dx * 12;
     for (int tB = 0; tB < A.n_tb; tB++) {
         const int4 bB = A.bbox_b[tB];
         const int ox = bA.x - bB.y, oy = bA.z - bB.w;
         __syncthreads();
-        for (int e = threadIdx.x; e < HW; e += TA) {
-            const int iy = e / A.W, ix = e - iy * A.W;
-            const int gx = ox + ix - A.box_x0, gy = oy + iy - A.box_y0;
-            float4 q0 = make_float4(0, 0, 0, 0), q1 = q0, q2 = q0;
-            if (gx < A.Dx && gy < A.Dy) {
-                const float2* src = (const float2*)(tk + ((size_t)gy * A.Dx + gx) * 12);
-                const float2 h01 = __ldg(src), h23 = __ldg(src + 1), h45 = __ldg(src + 2);
-                const float2 l01 = __ldg(src + 3), l23 = __ldg(src + 4), l45 = __ldg(src + 5);
-                q0 = make_float4(h01.x, l01.x, h01.y, l01.y);
-                q1 = make_float4(h23.x, l23.x, h23.y, l23.y);
-                q2 = make_float4(h45.x, l45.x, h45.y, l45.y);
-            }
-            s_tab[3 * e] = q0, s_tab[3 * e + 1] = q1, s_tab[3 * e + 2] = q2;
-        }
+        x2_box_issue(A, k, ox, oy, s_tab, tmap, bar, TA);
         for (int j = threadIdx.x; j < TB; j += TA) {
             float h[6], l[6];
 #pragma unroll
@@ -301,7 +340,7 @@ __device__ __forceinline__ void tile_x2(const ContractArgs& A, int tA, int k, in
             s_f[4 * j + 2] = make_float4(h[4], l[4], h[5], l[5]);
             s_f[4 * j + 3] = make_float4(__int_as_float(A.off_i[tB * TB + j]), 0.f, 0.f, 0.f);
         }
-        __syncthreads();
+        if (x2_box_wait(A, tmap, bar, tB)) return;
         const int base = (xa.x - ox) + A.W * (xa.y - oy);
         float S[6] = {0, 0, 0, 0, 0, 0}, E[6] = {0, 0, 0, 0, 0, 0};
         if (K0) {
@@ -371,7 +410,8 @@ __device__ __forceinline__ void tile_x2(const ContractArgs& A, int tA, int k, in
 // one-rhs tile.  grid.z = ceil(n_rhs / (NG RB)); force records [NG RB][TB][3]
 // (hi/lo pairs of x and y').
 template <int TA, int TB, int NG, int RB, bool K0>
-__device__ __forceinline__ void tile_x2_rb(const ContractArgs& A, int tA, int k, int rb, int n_rhs, void* smem_raw) {
+__device__ __forceinline__ void tile_x2_rb(const ContractArgs& A, int tA, int k, int rb, int n_rhs, void* smem_raw,
+                                           const void* tmap, uint64_t* bar) {
     constexpr int NT = TA * NG, NR = NG * RB;
     float4* smemx2 = (float4*)smem_raw;
     const int HW = A.H * A.W;
@@ -388,25 +428,11 @@ __device__ __forceinline__ void tile_x2_rb(const ContractArgs& A, int tA, int k,
     for (int q = 0; q < RB; q++)
 #pragma unroll
         for (int c = 0; c < 6; c++) Th[q][c] = Tl[q][c] = 0.f;
-    const float* tk = A.tabx2 + (size_t)(k - A.kbase) * A.Dy * A.Dx * 12;
     for (int tB = 0; tB < A.n_tb; tB++) {
         const int4 bB = A.bbox_b[tB];
         const int ox = bA.x - bB.y, oy = bA.z - bB.w;
         __syncthreads();
-        for (int e = threadIdx.x; e < HW; e += NT) {
-            const int iy = e / A.W, ix = e - iy * A.W;
-            const int gx = ox + ix - A.box_x0, gy = oy + iy - A.box_y0;
-            float4 q0 = make_float4(0, 0, 0, 0), q1 = q0, q2 = q0;
-            if (gx < A.Dx && gy < A.Dy) {
-                const float2* src = (const float2*)(tk + ((size_t)gy * A.Dx + gx) * 12);
-                const float2 h01 = __ldg(src), h23 = __ldg(src + 1), h45 = __ldg(src + 2);
-                const float2 l01 = __ldg(src + 3), l23 = __ldg(src + 4), l45 = __ldg(src + 5);
-                q0 = make_float4(h01.x, l01.x, h01.y, l01.y);
-                q1 = make_float4(h23.x, l23.x, h23.y, l23.y);
-                q2 = make_float4(h45.x, l45.x, h45.y, l45.y);
-            }
-            s_tab[3 * e] = q0, s_tab[3 * e + 1] = q1, s_tab[3 * e + 2] = q2;
-        }
+        x2_box_issue(A, k, ox, oy, s_tab, tmap, bar, NT);
         for (int e = threadIdx.x; e < NR * TB; e += NT) {
             const int q = e / TB, j = e - q * TB;
             float h[6] = {0, 0, 0, 0, 0, 0}, l[6] = {0, 0, 0, 0, 0, 0};
@@ -424,7 +450,7 @@ __device__ __forceinline__ void tile_x2_rb(const ContractArgs& A, int tA, int k,
             s_f[3 * e + 2] = make_float4(h[4], l[4], h[5], l[5]);
         }
         for (int e = threadIdx.x; e < TB; e += NT) s_off[e] = A.off_i[tB * TB + e];
-        __syncthreads();
+        if (x2_box_wait(A, tmap, bar, tB)) return;
         const int base = (xa.x - ox) + A.W * (xa.y - oy);
         float S[RB][6], E[RB][6];
 #pragma unroll
@@ -505,17 +531,35 @@ __global__ void __launch_bounds__(TA) k_contract_fp32_rb(ContractArgs A, int n_r
     extern __shared__ float4 smem_raw[];
     tile_fp32_rb<TA, TB, RB>(A, blockIdx.x, A.k0 + blockIdx.y, blockIdx.z, n_rhs, smem_raw);
 }
-template <int TA, int TB, bool K0>
-__global__ void __launch_bounds__(TA) k_contract_x2(ContractArgs A) {
+// The double-float kernels' shared memory: the sub-box at the first 128-byte boundary (the TMA
+// destination's alignment; launches add 128 bytes), and the staging barrier, initialised by thread 0
+// (the tile's first __syncthreads orders it before any use).  TMA: the sub-box comes by one tensor
+// copy per tile (a compiled-in choice; the thread-staged instance serves boxes the copy cannot take).
+__device__ __forceinline__ float4* x2_smem_setup(float4* smem_raw, uint64_t* bar, bool use_tma) {
+    if (use_tma && threadIdx.x == 0) {
+        tc::mbar_init(bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    const uint32_t pad = (128u - (tc::smem_u32(smem_raw) & 127u)) & 127u;
+    return (float4*)((char*)smem_raw + pad);
+}
+template <int TA, int TB, bool K0, bool TMA>
+__global__ void __launch_bounds__(TA) k_contract_x2(ContractArgs A, const __grid_constant__ CUtensorMap tm) {
     extern __shared__ float4 smem_raw[];
-    tile_x2<TA, TB, K0>(A, blockIdx.x, A.k0 + blockIdx.y, blockIdx.z, smem_raw);
+    __shared__ uint64_t bar;
+    float4* smem = x2_smem_setup(smem_raw, &bar, TMA);
+    tile_x2<TA, TB, K0>(A, blockIdx.x, A.k0 + blockIdx.y, blockIdx.z, smem, TMA ? &tm : nullptr, &bar);
 }
 // grid (pad tiles, rhs groups, modes): the modes outermost, so the CTAs of all rhs groups of one mode run
 // together and read that mode's table slice from L2
-template <int TA, int TB, int NG, int RB, bool K0>
-__global__ void __launch_bounds__(TA * NG) k_contract_x2_rb(ContractArgs A, int n_rhs) {
+template <int TA, int TB, int NG, int RB, bool K0, bool TMA>
+__global__ void __launch_bounds__(TA * NG) k_contract_x2_rb(ContractArgs A, const __grid_constant__ CUtensorMap tm,
+                                                            int n_rhs) {
     extern __shared__ float4 smem_raw[];
-    tile_x2_rb<TA, TB, NG, RB, K0>(A, blockIdx.x, A.k0 + blockIdx.z, blockIdx.y, n_rhs, smem_raw);
+    __shared__ uint64_t bar;
+    float4* smem = x2_smem_setup(smem_raw, &bar, TMA);
+    tile_x2_rb<TA, TB, NG, RB, K0>(A, blockIdx.x, A.k0 + blockIdx.z, blockIdx.y, n_rhs, smem, TMA ? &tm : nullptr,
+                                   &bar);
 }
 
 // ---- batched: one persistent launch drains a cost-sorted work list ----------
@@ -553,7 +597,43 @@ __global__ void __launch_bounds__(TA) k_batch_contract(const ContractArgs* __res
 // multi-rhs double-float tile: kX2NG groups of kTileA threads, kX2RB right-hand sides per thread
 constexpr int kX2NG = 2, kX2RB = 2, kX2R = kX2NG * kX2RB;
 size_t x2_rb_smem(const Plan& P) {
-    return (size_t)P.H * P.W * 48 + (size_t)kX2R * kTileB * 48 + (size_t)kTileB * 4 + 16;
+    return (size_t)P.H * P.W * 48 + (size_t)kX2R * kTileB * 48 + (size_t)kTileB * 4 + 16 + 128;
+}
+size_t x2_smem(const Plan& P) { return (size_t)P.H * P.W * 48 + (size_t)kTileB * 64 + 16 + 128; }
+
+// cuTensorMapEncodeTiled, reached through the runtime (no link against the driver library).
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeTiledFn encode_tiled_fn() {
+    static const EncodeTiledFn fn = [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess) {
+            cudaGetLastError();
+            return (EncodeTiledFn) nullptr;
+        }
+        return (EncodeTiledFn)p;
+    }();
+    return fn;
+}
+
+// Tensor map of the double-float table for the TMA staging of a tile pair's sub-box: 8-byte
+// elements in three dimensions (6 Dx per table row, Dy rows, n_slices mode slices), box (6 W, H, 1),
+// zero outside the table.  A box starts at x = 6 (ox - box_x0): 48 bytes per entry, so on a
+// 16-byte boundary.  Returns 0 (thread staging) when a box line is over the copy engine's 256
+// elements (W > 42), H > 256, or the map cannot be made.
+int encode_x2_map(const ContractArgs& A, int n_slices, CUtensorMap* m) {
+    const EncodeTiledFn fn = encode_tiled_fn();
+    if (!fn || !A.tabx2 || 6 * A.W > 256 || A.H > 256 || ((uintptr_t)A.tabx2 & 15u)) return 0;
+    const cuuint64_t dims[3] = {6ull * A.Dx, (cuuint64_t)A.Dy, (cuuint64_t)n_slices};
+    const cuuint64_t strides[2] = {48ull * A.Dx, 48ull * A.Dx * A.Dy};
+    const cuuint32_t box[3] = {6u * (cuuint32_t)A.W, (cuuint32_t)A.H, 1};
+    const cuuint32_t unit[3] = {1, 1, 1};
+    return fn(m, CU_TENSOR_MAP_DATA_TYPE_UINT64, 3, (void*)A.tabx2, dims, strides, box, unit,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 template <class T>
@@ -572,6 +652,30 @@ cudaError_t launch_one(KernelT kern, const ContractArgs& A, dim3 grid, int threa
     return cudaGetLastError();
 }
 
+// The double-float contraction of every mode (n_modes = K) or of the k = 0 mode alone (n_modes = 0:
+// the one-mode instances).  Both tiles take the sub-box by TMA where the map can be made (measured
+// faster than thread staging in each); otherwise the thread-staged instances run.
+template <bool K0, bool TMA>
+cudaError_t launch_x2_instance(Plan& P, const ContractArgs& A, int n_modes, int n_rhs, const CUtensorMap& tm,
+                               cudaStream_t st) {
+    if (n_rhs >= 2) {
+        return launch_one(k_contract_x2_rb<kTileA, kTileB, kX2NG, kX2RB, K0, TMA>, A,
+                          dim3(P.n_ta, (n_rhs + kX2R - 1) / kX2R, n_modes), kTileA * kX2NG, x2_rb_smem(P), st, tm,
+                          n_rhs);
+    }
+    return launch_one(k_contract_x2<kTileA, kTileB, K0, TMA>, A, dim3(P.n_ta, n_modes, n_rhs), kTileA, x2_smem(P), st,
+                      tm);
+}
+cudaError_t launch_contract_x2(Plan& P, const ContractArgs& A, int n_modes, int n_rhs, cudaStream_t st) {
+    CUtensorMap tm{};
+    const bool tma = encode_x2_map(A, A.tabx2 == P.d_table_x2 ? P.K : 1, &tm);
+    if (n_modes == 0)
+        return tma ? launch_x2_instance<true, true>(P, A, 1, n_rhs, tm, st)
+                   : launch_x2_instance<true, false>(P, A, 1, n_rhs, tm, st);
+    return tma ? launch_x2_instance<false, true>(P, A, n_modes, n_rhs, tm, st)
+               : launch_x2_instance<false, false>(P, A, n_modes, n_rhs, tm, st);
+}
+
 }  // namespace
 
 cudaError_t launch_contract(Plan& P, int n_rhs, cudaStream_t st) {
@@ -579,7 +683,6 @@ cudaError_t launch_contract(Plan& P, int n_rhs, cudaStream_t st) {
     ContractArgs A = make_contract_args(P);
     const size_t s64 = contract_smem<double>(P, kTileB, 8);
     if (s64 > 220 * 1024) return cudaErrorInvalidConfiguration;
-    const size_t sx2 = (size_t)P.H * P.W * 48 + (size_t)kTileB * 64 + 16;
     if (P.precision == FBC_PREC_FP64) {
         return launch_one(k_contract_fp64<kTileA, kTileB>, A, dim3(P.n_ta, P.K, n_rhs), kTileA, s64, st);
     }
@@ -604,13 +707,7 @@ cudaError_t launch_contract(Plan& P, int n_rhs, cudaStream_t st) {
         A.k0 = 1;
         return launch_contract_tc(A, P, n_rhs, st);
     }
-    if (P.precision == FBC_PREC_F32X2) {
-        if (n_rhs >= 2) {
-            return launch_one(k_contract_x2_rb<kTileA, kTileB, kX2NG, kX2RB, false>, A,
-                              dim3(P.n_ta, (n_rhs + kX2R - 1) / kX2R, P.K), kTileA * kX2NG, x2_rb_smem(P), st, n_rhs);
-        }
-        return launch_one(k_contract_x2<kTileA, kTileB, false>, A, dim3(P.n_ta, P.K, n_rhs), kTileA, sx2, st);
-    }
+    if (P.precision == FBC_PREC_F32X2) return launch_contract_x2(P, A, P.K, n_rhs, st);
     if (is_fft_precision(P.precision)) return launch_contract_fft(P, n_rhs, st);
     return cudaErrorInvalidValue;
 }
@@ -624,16 +721,12 @@ ContractArgs make_contract_args(const Plan& P) {
     A.bbox_a = P.d_bbox_a, A.bbox_b = P.d_bbox_b;
     A.n_tb = P.n_tb, A.K = P.K, A.Dx = P.Dx, A.Dy = P.Dy, A.box_x0 = P.box_x0, A.box_y0 = P.box_y0;
     A.W = P.W, A.H = P.H, A.NIpad = P.NIpad, A.NPpad = P.NPpad, A.k0 = 0, A.kbase = 0;
+    A.status = P.d_status;
     return A;
 }
 
 cudaError_t launch_contract_x2_k0(Plan& P, const ContractArgs& A, int n_rhs, cudaStream_t st) {
-    if (n_rhs >= 2) {
-        return launch_one(k_contract_x2_rb<kTileA, kTileB, kX2NG, kX2RB, true>, A,
-                          dim3(P.n_ta, (n_rhs + kX2R - 1) / kX2R, 1), kTileA * kX2NG, x2_rb_smem(P), st, n_rhs);
-    }
-    const size_t sx2 = (size_t)P.H * P.W * 48 + (size_t)kTileB * 64 + 16;
-    return launch_one(k_contract_x2<kTileA, kTileB, true>, A, dim3(P.n_ta, 1, n_rhs), kTileA, sx2, st);
+    return launch_contract_x2(P, A, 0, n_rhs, st);
 }
 
 cudaError_t launch_contract_modes(Plan& P, const ContractArgs& A0, int k0, int n_modes, int n_rhs, cudaStream_t st) {

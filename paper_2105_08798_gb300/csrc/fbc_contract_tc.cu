@@ -58,6 +58,8 @@ constexpr int kDrainTiles = 16;  // interface tiles per tensor-memory accumulati
 constexpr uint32_t kAcol = 384;  // first TMEM column of the A operand (after 3 x 128 accumulator columns)
 
 using tc::idesc;
+using tc::mbar_expect_tx;
+using tc::mbar_init;
 using tc::sdesc;
 using tc::smem_u32;
 
@@ -165,16 +167,8 @@ __device__ __forceinline__ void cp_async16(void* dst, const void* src) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
 }
 
-__device__ __forceinline__ void mbar_init(uint64_t* m, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(m)), "r"(count));
-}
 __device__ __forceinline__ void mbar_arrive(uint64_t* m) {
     asm volatile("{\n.reg .b64 st;\nmbarrier.arrive.shared::cta.b64 st, [%0];\n}\n" ::"r"(smem_u32(m)) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* m, uint32_t bytes) {
-    asm volatile("{\n.reg .b64 st;\nmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n}\n" ::"r"(smem_u32(m)),
-                 "r"(bytes)
-                 : "memory");
 }
 __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* m) {
     asm volatile(

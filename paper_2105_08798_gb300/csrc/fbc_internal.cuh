@@ -125,7 +125,7 @@ struct Plan {
 struct ContractArgs {
     const double* tab;   // [K][Dy][Dx][6]
     const float* tab32;  // [K][Dy][Dx][6]
-    const float* tabx2;  // [K][Dy][Dx][12] (hi[6], lo[6])
+    const float* tabx2;  // [K][Dy][Dx][12] (hi, lo) pairs of the six reals
     const double* fh;    // [rhs][K][NIpad][6]
     double* uh;          // [rhs][K][NPpad][6]
     float* uh32;         // [rhs][K][NPpad][6] the tensor-core forms' modes k >= 1
@@ -135,6 +135,7 @@ struct ContractArgs {
     const int4* bbox_b;
     int n_tb, K, Dx, Dy, box_x0, box_y0, W, H, NIpad, NPpad, k0;
     int kbase;  // the tables hold mode slices kbase, kbase + 1, ... (0: all K; else a streamed chunk)
+    int* status;  // device error word (a bounded wait that gave up)
 };
 
 // One instance's share of a tensor-core contraction launch (fbc_contract_tc.cu).

@@ -201,7 +201,9 @@ __global__ void k_derive_fp32(const double* __restrict__ t64, float* __restrict_
 }
 
 // Double-float split: v = hi + lo with hi = fl32(v), lo = fl32(v - hi).  Stored
-// per entry as (hi0..hi5, lo0..lo5) so that the two halves load as vectors.
+// per entry as the pairs (hi0, lo0, hi1, lo1, ..., hi5, lo5): three 16-byte
+// records, the layout the contraction keeps in shared memory, so that a tile's
+// sub-box is one tensor copy.
 __global__ void k_derive_x2(const double* __restrict__ t64, float* __restrict__ tx2, size_t n_entries) {
     size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     size_t stride = (size_t)gridDim.x * blockDim.x;
@@ -211,8 +213,8 @@ __global__ void k_derive_x2(const double* __restrict__ t64, float* __restrict__ 
             const double v = t64[e * 6 + c];
             const float hi = (float)v;
             const float lo = (float)(v - (double)hi);
-            tx2[e * 12 + c] = hi;
-            tx2[e * 12 + 6 + c] = lo;
+            tx2[e * 12 + 2 * c] = hi;
+            tx2[e * 12 + 2 * c + 1] = lo;
         }
     }
 }

@@ -1,6 +1,7 @@
-// Small tcgen05 helpers shared by the tensor-core kernels: shared-memory
-// matrix descriptors (K-major, no swizzle), instruction descriptors, and a
-// bounded mbarrier wait.
+// Small tcgen05, mbarrier and TMA helpers shared by the tensor-core kernels and
+// the double-float contraction: shared-memory matrix descriptors (K-major, no
+// swizzle), instruction descriptors, barrier set-up and a bounded wait, and a
+// three-dimensional tensor-map load.
 #pragma once
 #include <cstdint>
 
@@ -35,6 +36,31 @@ __device__ __forceinline__ uint32_t idesc(int fmt, int M, int N) {
 // along K 128 bytes apart (LBO), 8-row groups sbo bytes apart (SBO).
 __device__ __forceinline__ uint32_t canon_bf16(int row, int k, uint32_t sbo) {
     return (uint32_t)(row >> 3) * sbo + (uint32_t)(k >> 3) * 128u + (uint32_t)(row & 7) * 16u + (uint32_t)(k & 7) * 2u;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* m, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(m)), "r"(count));
+}
+
+// One arrival that also announces `bytes` of asynchronous copies to come.
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* m, uint32_t bytes) {
+    asm volatile("{\n.reg .b64 st;\nmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n}\n" ::"r"(smem_u32(m)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+// Tiled tensor-map load of one box at coordinates (c0, c1, c2), innermost
+// first, into shared memory at `dst` (128-byte aligned); completion is counted
+// on the barrier `m` in bytes.  `map` is the generic address of a tensor map in
+// kernel-parameter (__grid_constant__), constant or global memory.  Coordinates
+// outside the tensor read the map's fill value (zero).  c0 times the element
+// size must be a multiple of 16 bytes.
+__device__ __forceinline__ void tma_load_3d(void* dst, const void* map, uint64_t* m, int c0, int c1, int c2) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+        "[%5];" ::"r"(smem_u32(dst)),
+        "l"((uint64_t)map), "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(m))
+        : "memory");
 }
 
 __device__ __forceinline__ bool mbar_wait(uint64_t* m, uint32_t phase) {

@@ -237,3 +237,22 @@ def test_multi_rhs_double_float_tile_bits(fbc, oracle_mod, R, n_i, n_p, L):
             k0_many = many.sum(axis=2)
             k0_one = one.sum(axis=2)
             assert np.abs(k0_many - k0_one).max() <= 1e-12 * np.abs(k0_one).max()
+
+
+def test_double_float_wide_sub_box(fbc, oracle_mod):
+    """Two rows of columns, the pad row three sites apart: the sub-box of a tile pair is 445 x 1 table
+    entries, a line of 445 x 48 bytes, over the 256 8-byte elements of a tensor copy's box line, so the
+    double-float tile stages it with its threads instead of one TMA copy.  That staging against the
+    oracle at 1e-12 (the ring geometries of the other tests take the TMA copy)."""
+    n_i, n_p, L, R = 200, 300, 8, 3
+    xy_i = np.stack([np.arange(n_i), np.zeros(n_i, dtype=np.int64)], axis=1).astype(np.int32)
+    xy_p = np.stack([3 * np.arange(n_p), np.full(n_p, 2)], axis=1).astype(np.int32)
+    f = inputs.forces(R, n_i, L, seed=23)
+    ref = oracle_mod.pad_update(xy_i, xy_p, L, 1.0, ISO, f)
+    with fbc.Plan(xy_i, xy_p, L, ISO, precision="f32x2", max_rhs=R) as plan:
+        info = plan.info()
+        assert 6 * info["sub_w"] > 256
+        plan.tabulate()
+        for n in (1, R):  # the one-rhs and the multi-rhs tiles
+            got = gpu_update(fbc, xy_i, xy_p, L, ISO, f[:n], plan=plan)
+            assert rel_l2(got, ref[:n]) <= TOL_FP64, n
