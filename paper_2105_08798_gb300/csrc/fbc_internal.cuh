@@ -29,6 +29,8 @@ namespace fbc {
 
 constexpr int kMaxRichImages = 40;  // n + N upper bound
 constexpr int kMaxQuad = 512;       // Barnett nodes on [0, pi)
+constexpr int kHostChunks = 8;      // host-memory apply: right-hand-side chunks at most
+constexpr int kHostChunkRhs = 4;    // ... and right-hand sides per chunk at least
 constexpr int kTileA = 128;         // pad columns per contraction tile
 constexpr int kTileB = 64;          // interface columns per contraction tile
 // Private bit of Plan::opt.flags, above every FBC_PLAN_* bit: set by
@@ -100,6 +102,9 @@ struct Plan {
     double* d_stage_u = nullptr;
     int* d_status = nullptr;     // device error word
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};  // stage timing (optional)
+    // host-memory apply: copy-in and copy-out streams and their events (created on first use)
+    cudaStream_t host_st[2] = {nullptr, nullptr};
+    cudaEvent_t host_ev[2 * kHostChunks + 2] = {};
     // learned far field (fbc_plan_attach_surrogate): streamed per-mode slices
     fbc_surrogate* sur = nullptr;
     double sur_rmin = 0.0;

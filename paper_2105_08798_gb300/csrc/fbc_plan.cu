@@ -199,6 +199,10 @@ void free_plan(fbc::Plan& P) {
         if (b) cudaFree(b);
     for (auto& e : P.ev)
         if (e) cudaEventDestroy(e), e = nullptr;
+    for (auto& e : P.host_ev)
+        if (e) cudaEventDestroy(e), e = nullptr;
+    for (auto& h : P.host_st)
+        if (h) cudaStreamDestroy(h), h = nullptr;
     fbc::release_surrogate_buffers(P);
     fbc::fft_free(P);
 }
@@ -672,14 +676,52 @@ int fbc_apply_host(fbc_plan* plan, const double* f_host, double* u_host, int32_t
         if (s) return s;
     }
     P.workspace_bytes += acc;
-    const size_t fb = (size_t)n_rhs * P.n_i * P.L * 3 * sizeof(double);
-    const size_t ub = (size_t)n_rhs * P.n_p * P.L * 3 * sizeof(double);
-    FBC_CUDA(cudaMemcpyAsync(P.d_stage_f, f_host, fb, cudaMemcpyHostToDevice, st));
-    if (beta != 0.0) FBC_CUDA(cudaMemcpyAsync(P.d_stage_u, u_host, ub, cudaMemcpyHostToDevice, st));
-    int s = apply_common(P, P.d_stage_f, P.d_stage_u, n_rhs, alpha, beta, flags, st);
+    if (!P.host_st[0]) {
+        for (auto& h : P.host_st) FBC_CUDA(cudaStreamCreateWithFlags(&h, cudaStreamNonBlocking));
+        for (auto& e : P.host_ev) FBC_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    }
+    // The right-hand sides go through in chunks (at least kHostChunkRhs each, at most kHostChunks):
+    // chunk c is copied in on one stream, applied on the caller's stream once it has arrived, and
+    // copied out on a third stream once applied, so copies overlap the applies of other chunks.
+    // Each right-hand side is computed as in one apply of all of them.
+    const int n_chunks = std::max(1, std::min(fbc::kHostChunks, n_rhs / fbc::kHostChunkRhs));
+    const int per = (n_rhs + n_chunks - 1) / n_chunks;
+    const size_t fr = (size_t)P.n_i * P.L * 3, ur = (size_t)P.n_p * P.L * 3;  // doubles per right-hand side
+    cudaStream_t cin = P.host_st[0], cout = P.host_st[1];
+    cudaEvent_t* ev = P.host_ev;  // [0] start, [1 + c] chunk c in, [1 + kHostChunks + c] chunk c applied, [last] end
+    cudaEvent_t ev_end = ev[2 * fbc::kHostChunks + 1];
+    int s = FBC_OK;
+    cudaError_t e = cudaEventRecord(ev[0], st);  // after the work already queued on the caller's stream
+    if (!e) e = cudaStreamWaitEvent(cin, ev[0], 0);
+    if (!e) e = cudaStreamWaitEvent(cout, ev[0], 0);
+    for (int c = 0; c < n_chunks && !e; c++) {
+        const int r0 = c * per, nr = std::min(per, n_rhs - r0);
+        if (nr <= 0) break;
+        e = cudaMemcpyAsync(P.d_stage_f + r0 * fr, f_host + r0 * fr, nr * fr * sizeof(double), cudaMemcpyHostToDevice,
+                            cin);
+        if (!e && beta != 0.0)
+            e = cudaMemcpyAsync(P.d_stage_u + r0 * ur, u_host + r0 * ur, nr * ur * sizeof(double),
+                                cudaMemcpyHostToDevice, cin);
+        if (!e) e = cudaEventRecord(ev[1 + c], cin);
+    }
+    for (int c = 0; c < n_chunks && !e && !s; c++) {
+        const int r0 = c * per, nr = std::min(per, n_rhs - r0);
+        if (nr <= 0) break;
+        if ((e = cudaStreamWaitEvent(st, ev[1 + c], 0))) break;
+        if ((s = apply_common(P, P.d_stage_f + r0 * fr, P.d_stage_u + r0 * ur, nr, alpha, beta, flags, st))) break;
+        if ((e = cudaEventRecord(ev[1 + fbc::kHostChunks + c], st))) break;
+        if ((e = cudaStreamWaitEvent(cout, ev[1 + fbc::kHostChunks + c], 0))) break;
+        e = cudaMemcpyAsync(u_host + r0 * ur, P.d_stage_u + r0 * ur, nr * ur * sizeof(double), cudaMemcpyDeviceToHost,
+                            cout);
+    }
+    if (!e && !s) e = cudaEventRecord(ev_end, cout);
+    if (!e && !s) e = cudaStreamWaitEvent(st, ev_end, 0);  // the caller's stream ends after the last copy out
+    // the host buffers stay in use until every copy has finished, on the error paths too
+    const cudaError_t e_in = cudaStreamSynchronize(cin), e_out = cudaStreamSynchronize(cout);
+    const cudaError_t e_st = cudaStreamSynchronize(st);
     if (s) return s;
-    FBC_CUDA(cudaMemcpyAsync(u_host, P.d_stage_u, ub, cudaMemcpyDeviceToHost, st));
-    FBC_CUDA(cudaStreamSynchronize(st));
+    if (!e) e = e_in ? e_in : (e_out ? e_out : e_st);
+    if (e) return cuda_fail(e, "host-memory apply");
     return FBC_OK;
 }
 

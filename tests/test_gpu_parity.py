@@ -165,6 +165,28 @@ def test_host_entry_point_matches_device(fbc):
     assert np.array_equal(dev, host_u)
 
 
+def test_host_entry_point_in_chunks(fbc):
+    """fbc_apply_host with 22 right-hand sides runs them in chunks (5 of 5, 5, 5, 5, 2) whose copies
+    overlap the applies of the others.  Every right-hand side gets the bits of one device apply of all
+    22 (the CUDA-core forms; the tensor-core form within 1e-14), with beta u0, the zero mean and the
+    ragged last chunk."""
+    xy_i, xy_p = inputs.ring_geometry(80, 100)
+    L, R = 16, 22
+    f = inputs.forces(R, 80, L, seed=16)
+    u0 = np.random.default_rng(5).standard_normal((R, 100, L, 3))
+    for prec in ("f32x2", "fp64", "bf16x2"):
+        with fbc.Plan(xy_i, xy_p, L, ISO, precision=prec, max_rhs=R) as plan:
+            plan.tabulate()
+            dev = gpu_update(fbc, xy_i, xy_p, L, ISO, f, plan=plan, alpha=-1.0, beta=0.5, u0=u0, zero_mean=True)
+            host_u = u0.copy()
+            plan.apply_host(np.ascontiguousarray(f), host_u, alpha=-1.0, beta=0.5, zero_mean=True)
+            plan.sync_status()
+        if prec == "bf16x2":
+            assert rel_l2(host_u, dev) <= 1e-14
+        else:
+            assert np.array_equal(dev, host_u), prec
+
+
 def test_errors_are_reported(fbc):
     xy_i, xy_p = inputs.ring_geometry(10, 12)
     plan = fbc.Plan(xy_i, xy_p, 8, ISO, max_rhs=1)
