@@ -326,13 +326,15 @@ def time_harmonic_step(torch, fbc, plan, w, xy_i, xy_p, ud, steps, flush_buf):
             "model": "spring k1 = 1, k2 = 0.4, c = 1; du_max = 0.02; zero mean"}
 
 
-TENSOR = {"tf32": 1, "bf16x2": 3, "bf16x3": 6}  # tensor-core products per block product (split terms)
+# tensor-core products per block product (split terms; bf16x6: the 26 fixed-point slice products)
+TENSOR = {"tf32": 1, "bf16x2": 3, "bf16x3": 6, "bf16x6": 26}
 DTYPE = {"fp64": "f64", "f32x2": "f32x2 (double-float, FP64-accurate)", "fp32": "f32",
          "tf32": "tf32 x f32-accumulate (k = 0 in double-float)",
          "bf16x2": "bf16 2-term split x f32-accumulate (k = 0 in double-float)",
          "bf16x3": "bf16 3-term split x f32-accumulate (k = 0 in double-float)",
          "fft64": "f64 (in-plane FFT form)",
-         "fft32": "f32 (in-plane FFT form; k = 0 in f64)"}
+         "fft32": "f32 (in-plane FFT form; k = 0 in f64)",
+         "bf16x6": "bf16 6-slice fixed-point split x exact f32 accumulation (FP64-accurate; k = 0 in double-float)"}
 FFT = ("fft64", "fft32")
 
 
@@ -366,6 +368,8 @@ def launches_per_apply(precision, info):
         contract = 1 + 3 * chunks
     elif precision in ("fp64", "f32x2"):
         contract = 1
+    elif precision == "bf16x6":
+        contract = 4  # k = 0, force scales, force slices, contraction
     elif precision in TENSOR:
         contract = 3
     else:
@@ -516,7 +520,7 @@ def run_ours(args, w):
     # form, several times slower than double-float at the same accuracy, only at one right-hand side
     if not args.surrogate:
         others = (("fp64", "f32x2", "fp32", "fft64", "fft32") if R == 1
-                  else ("f32x2", "fp32", "tf32", "bf16x2", "bf16x3", "fft64", "fft32"))
+                  else ("f32x2", "bf16x6", "fp32", "tf32", "bf16x2", "bf16x3", "fft64", "fft32"))
         for prec in others:
             if prec != args.precision:
                 variant(prec)
@@ -864,7 +868,8 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--precision", choices=["fp64", "f32x2", "fp32", "tf32", "bf16x2", "bf16x3", "fft64", "fft32"],
+    ap.add_argument("--precision", choices=["fp64", "f32x2", "fp32", "tf32", "bf16x2", "bf16x3", "fft64", "fft32",
+                                                "bf16x6"],
                     default=None,
                     help="contraction form of the timed steps (default: f32x2, the dense FP64-accurate form)")
     ap.add_argument("--workload", choices=sorted(inputs.WORKLOADS) + ["batch"], default=WORKLOAD,

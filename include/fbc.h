@@ -74,6 +74,18 @@ extern "C" {
  * and FP32 line transforms; the logarithmic k = 0 mode stays on the FP64
  * grid transforms (as the other FP32 forms keep it FP64-accurate). */
 #define FBC_PREC_FFT32 7
+/* Tensor cores, FP64-accurate (Ozaki's error-free splitting of the dot
+ * product; Sec. 3.2, Eqs. 37-38 as the other forms): every table entry and
+ * force value, scaled by a power of two (per pad row and interface tile, per
+ * force column and mode), is cut into six fixed-point bf16 slices of 8 bits;
+ * the 26 slice products with i + j <= 8 are summed exactly in FP32 tensor
+ * memory, one accumulator per diagonal i + j, and the groups are combined in
+ * double-float.  Error about 1e-14 relative to the largest operand products
+ * (unit roundoff near 2^-47).  Needs the double-float table, FP64 line
+ * transforms and a sliced force operand of 18 KB per (mode, group of 16 rhs,
+ * stage of 16 interface columns); k = 0 in double-float.  Not for batches or
+ * plans with a surrogate. */
+#define FBC_PREC_BF16X6 8
 
 /* ---- plan flags (fbc_options.flags) ----------------------------------- */
 #define FBC_PLAN_HOST_ONLY 1 /* validate and lay out on the host only: no device memory,

@@ -218,6 +218,8 @@ int fbc_batch_create(fbc_plan* const* plans, int32_t n_plans, const double* cons
         if (P.precision != prec) return bfail(FBC_ERR_INVALID_ARG, "all plans of a batch need the same precision");
         if (fbc::is_fft_precision(prec))
             return bfail(FBC_ERR_UNSUPPORTED, "batches run the dense per-mode contraction, not the in-plane FFT form");
+        if (prec == FBC_PREC_BF16X6)
+            return bfail(FBC_ERR_UNSUPPORTED, "BF16X6 plans run on their own, not in a batch");
         if (fbc::is_tensor_precision(prec) && fbc::contract_tc_smem(prec, P.W * P.H) > 227 * 1024)
             return bfail(FBC_ERR_UNSUPPORTED, "tensor-core contraction: an instance's sub-box exceeds shared memory");
         if (n_rhs[i] < 1 || n_rhs[i] > P.opt.max_rhs) return bfail(FBC_ERR_INVALID_ARG, "n_rhs outside [1, max_rhs]");

@@ -708,6 +708,13 @@ cudaError_t launch_contract(Plan& P, int n_rhs, cudaStream_t st) {
         return launch_contract_tc(A, P, n_rhs, st);
     }
     if (P.precision == FBC_PREC_F32X2) return launch_contract_x2(P, A, P.K, n_rhs, st);
+    if (P.precision == FBC_PREC_BF16X6) {
+        // k = 0 in double-float, k >= 1 in fixed-point slices on the tensor cores
+        cudaError_t e = launch_contract_x2_k0(P, A, n_rhs, st);
+        if (e || P.K < 2) return e;
+        A.k0 = 1;
+        return launch_contract_oz(A, P, n_rhs, st);
+    }
     if (is_fft_precision(P.precision)) return launch_contract_fft(P, n_rhs, st);
     return cudaErrorInvalidValue;
 }

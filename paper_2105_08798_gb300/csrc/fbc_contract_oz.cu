@@ -1,0 +1,551 @@
+// FP64-accurate per-mode contraction on the tensor cores: fixed-point bf16
+// slices with exact FP32 accumulation (Ozaki's error-free splitting of a dot
+// product), for plans with several right-hand sides.
+//
+// The operation is the one of the other forms (Sec. 3.2, Eqs. 37-38 in the mode
+// domain): for every mode k >= 1, pad column a and output component co,
+//     U_co(a, n) = sum_{ci, b} M_{co ci}(x_a - x_b) X_ci(b, n),
+// n over the x and y' halves of the right-hand sides.  Exactness comes from
+// three facts:
+//   * every operand value v is scaled by a power of two to |v'| < 1/2 and cut
+//     into six slices t_1 .. t_6, t_i an integer of at most 8 bits times
+//     2^(-8 i) (round to nearest, so the slices after the first are at most 128
+//     units); six slices hold v' to 2^-49;
+//   * the product of two slices is exact in FP32 (16 significant bits), and all
+//     products t_i s_j with the same i + j = q lie on the grid 2^(-8 q);
+//   * an FP32 accumulator that only ever adds values of one grid is exact while
+//     the sum stays below 2^24 grid units.  With 192 terms per group (64
+//     interface columns x 3 components) and at most q - 1 products of at most
+//     2^14 units per term, q <= 6 stays exact in the worst case, and the sums of
+//     q = 7, 8 are far below the result's last bit when they round.
+// So each diagonal q = 2 .. 8 (26 slice products: i, j <= 6, i + j <= 8) has an
+// accumulator of its own in tensor memory, the products of a group are summed
+// exactly there, and the group's seven sums are combined in double-float
+// arithmetic, scaled back and added to a running double-float sum per output.
+// What is left out -- slices beyond the sixth and products with i + j > 8 -- is
+// below 2^-47 of the largest operand product, per term.
+//
+// Scales: the table entries of pad row a and interface tile tB (64 columns, one
+// accumulation group) share 2^E(a, tB), the largest power of two with |entry| <
+// 2^(E-1) over the row's entries in the tile, found on the fly; the force column
+// n of mode k shares 2^F(k, n), found by a reduction before the split.  Rows and
+// columns scale the GEMM independently, so both are exact.
+//
+// A CTA owns 128 pad columns (the GEMM rows, one tensor-memory lane each), one
+// output component co, one mode and 16 right-hand sides (N = 32), and walks the
+// interface columns in stages of 16:
+//   * eight builder warps gather the co-th row of M, (M_{co 0}, M_{co 1},
+//     M_{co 2}), from the staged double-float table sub-box, split it into six
+//     slices and store the 3 x 6 blocks of 128 x 16 bf16 into tensor memory;
+//   * one thread streams the force operand, split once per apply (3 x 6 blocks
+//     of 32 x 16 bf16 per stage, 18 KB), with bulk copies into a ring of stages;
+//   * one thread issues 3 x 26 tcgen05.mma (M = 128, N = 32, K = 16) per stage
+//     into the seven diagonal accumulators;
+//   * at the end of every interface tile the builders drain the accumulators
+//     into their running double-float sums.
+// Tensor memory: 7 x 32 accumulator columns and 18 x 8 columns of A: 368 of 512.
+// The mode k = 0 stays with the double-float kernel, as in the other tensor forms.
+//
+// Every wait is bounded as in the other tensor-core kernel: pipeline waits give
+// up after the plan's wait limit or once another role gave up; the waits for a
+// CTA's own bulk copies and products in flight keep the full bound; a stopped CTA
+// records the status word, frees its tensor memory and returns.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+
+#include "fbc_internal.cuh"
+#include "fbc_tc.cuh"
+
+namespace fbc {
+namespace {
+
+constexpr int kTmemCols = 512;
+constexpr int kRows = kTileA;        // GEMM rows (pad columns) per CTA
+constexpr int kRhs = 16;             // right-hand sides per CTA
+constexpr int kN = 2 * kRhs;         // GEMM columns: (x, y') of each right-hand side
+constexpr int kKC = 16;              // interface columns per stage (the bf16 MMA's K)
+constexpr int kStages = kTileB / kKC;  // stages per interface tile = per accumulation group
+constexpr int kNS = 6;               // slices per operand value
+constexpr int kNQ = 7;               // diagonals q = 2 .. 8
+constexpr int kNPair = 26;           // slice products with i, j <= 6 and i + j <= 8
+constexpr int kBuilderWarps = 8;
+constexpr int kBuilders = kBuilderWarps * 32;
+constexpr int kMmaWarp = 8, kCopyWarp = 9;
+constexpr int kThreads = 10 * 32;
+constexpr int kS = 3;                // force-operand ring stages
+constexpr uint32_t kAcol = 256;      // first TMEM column of the A blocks
+constexpr uint32_t kBBlk = (uint32_t)kN * kKC * 2;       // one (ci, slice) block of a force chunk: 1 KB
+constexpr uint32_t kChunk = 3u * kNS * kBBlk;            // one stage of the force operand: 18 KB
+constexpr uint32_t kSBO = (kKC / 8) * 128;               // 8-row group stride of a [rows][16] bf16 block
+constexpr int kEmin = -120, kEmax = 120;                 // clamp of the scale exponents (2^E a normal float)
+
+// Entry of M(d) in row co, column ci, as (index into the six table reals, sign):
+// M = [[A11, A12, -B13], [A12, A22, -B23], [B13, B23, A33]], reals (A11, A12, A22, A33, B13, B23).
+__host__ __device__ constexpr int oz_real(int co, int ci) {
+    return co == 0 ? (ci == 0 ? 0 : ci == 1 ? 1 : 4) : co == 1 ? (ci == 0 ? 1 : ci == 1 ? 2 : 5) : (ci == 0 ? 4 : ci == 1 ? 5 : 3);
+}
+__host__ __device__ constexpr bool oz_neg(int co, int ci) { return ci == 2 && co < 2; }
+
+// Slice products by diagonal: pair p multiplies A slice oz_pi(p) with B slice oz_pj(p) (1-based) into
+// accumulator q = oz_pi(p) + oz_pj(p); oz_first(p) marks the first product of its diagonal.
+__host__ __device__ constexpr int oz_pi(int p) {
+    constexpr int v[kNPair] = {1, 1, 2, 1, 2, 3, 1, 2, 3, 4, 1, 2, 3, 4, 5, 1, 2, 3, 4, 5, 6, 2, 3, 4, 5, 6};
+    return v[p];
+}
+__host__ __device__ constexpr int oz_pj(int p) {
+    constexpr int v[kNPair] = {1, 2, 1, 3, 2, 1, 4, 3, 2, 1, 5, 4, 3, 2, 1, 6, 5, 4, 3, 2, 1, 6, 5, 4, 3, 2};
+    return v[p];
+}
+__host__ __device__ constexpr bool oz_first(int p) {
+    return p == 0 || oz_pi(p) + oz_pj(p) != oz_pi(p - 1) + oz_pj(p - 1);
+}
+static_assert(oz_pi(kNPair - 1) + oz_pj(kNPair - 1) == 8 && oz_first(21) && !oz_first(25), "pair table");
+
+// Six fixed-point slices of v' = (hi + lo) s, |v'| < 1/2, s a power of two: t_i is v's remainder
+// rounded to the grid 2^(-8 i) (add and subtract 1.5 x 2^(23 - 8 i)).  hi s - t_1 and the later
+// remainders are exact; only lo s joins with a rounding, of at most 2^-49.
+__device__ __forceinline__ void oz_split(float hi, float lo, float s, float (&t)[kNS]) {
+    const float C1 = 49152.0f, C2 = 192.0f, C3 = 0.75f;
+    const float C4 = 0.0029296875f, C5 = 1.1444091796875e-05f, C6 = 4.470348358154297e-08f;
+    t[0] = __fsub_rn(__fmaf_rn(hi, s, C1), C1);
+    float r = __fmaf_rn(hi, s, -t[0]);
+    t[1] = __fsub_rn(__fadd_rn(r, C2), C2);
+    r = __fsub_rn(r, t[1]);
+    t[2] = __fsub_rn(__fadd_rn(r, C3), C3);
+    r = __fsub_rn(r, t[2]);
+    r = __fmaf_rn(lo, s, r);
+    t[3] = __fsub_rn(__fadd_rn(r, C4), C4);
+    r = __fsub_rn(r, t[3]);
+    t[4] = __fsub_rn(__fadd_rn(r, C5), C5);
+    r = __fsub_rn(r, t[4]);
+    t[5] = __fsub_rn(__fadd_rn(r, C6), C6);
+}
+
+// 2^-E as a float and the exponent E of a magnitude bound m: the smallest power of two above 2 m
+// (|v| <= m gives |v 2^-E| < 1/2), clamped to [kEmin, kEmax].
+__device__ __forceinline__ int oz_exp_of(float m) {
+    const int e = (int)((__float_as_uint(m) >> 23) & 0xffu) - 127;  // floor(log2 m) (m = 0: -127)
+    return min(max(e + 2, kEmin), kEmax);
+}
+__device__ __forceinline__ float oz_pow2(int e) { return __uint_as_float((uint32_t)(127 + e) << 23); }
+
+// Two-sum (Knuth): s + e == a + b exactly.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// ---- force operand: scales and slices (once per apply) ----------------------
+
+// Scale exponent F(k, n) of every force column (right-hand side r, half h) of modes k0 .. k0 + n_modes - 1:
+// one block per (mode, rhs), the largest |fh| of the half over the interface columns and its three
+// components, compared as the integer bits of the magnitudes.  fexp[(r K + k) 2 + h].
+__global__ void __launch_bounds__(256) k_oz_fscale(const double* __restrict__ fh, int K, int NIpad, int k0,
+                                                   int* __restrict__ fexp) {
+    const int k = k0 + (int)blockIdx.x, r = (int)blockIdx.y;
+    const double* src = fh + ((size_t)r * K + k) * NIpad * 6;
+    unsigned long long m0 = 0ull, m1 = 0ull;  // halves x (entries 0..2) and y' (3..5)
+    for (int i = threadIdx.x; i < NIpad * 3; i += blockDim.x) {  // one double2 per step: entries 2j, 2j + 1
+        const double2 v = ((const double2*)src)[i];
+        const int j = i % 3;
+        const unsigned long long a = (unsigned long long)__double_as_longlong(v.x) & 0x7fffffffffffffffull;
+        const unsigned long long b = (unsigned long long)__double_as_longlong(v.y) & 0x7fffffffffffffffull;
+        if (j == 0) m0 = max(m0, max(a, b));
+        else if (j == 1) m0 = max(m0, a), m1 = max(m1, b);
+        else m1 = max(m1, max(a, b));
+    }
+    const unsigned long long m[2] = {m0, m1};
+    __shared__ unsigned long long s_m[2][8];
+#pragma unroll
+    for (int h = 0; h < 2; h++) {
+        unsigned long long v = m[h];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+        if (threadIdx.x % 32 == 0) s_m[h][threadIdx.x / 32] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 2) {
+        const int h = threadIdx.x;
+        unsigned long long v = 0ull;
+        for (int w = 0; w < (int)blockDim.x / 32; w++) v = max(v, s_m[h][w]);
+        const int e = (int)((v >> 52) & 0x7ffull) - 1023;  // floor(log2 max) (max = 0: -1023)
+        fexp[((size_t)r * K + k) * 2 + h] = min(max(e + 2, kEmin), kEmax);
+    }
+}
+
+// Chunk of the sliced force operand for (k, rhs group g, interface tile tB, stage st).
+__host__ __device__ __forceinline__ size_t oz_chunk(int k, int g, int tB, int st, int G, int n_tb) {
+    return (((size_t)k * G + g) * n_tb + tB) * kStages + st;
+}
+
+// One thread per (mode, rhs group g < Gu, tile, stage, rhs r of the group, core column kc): the eight interface
+// columns b0 .. b0 + 7 of both halves and all three components of right-hand side r, each cut into six
+// slices at its column's scale, stored as 16-byte core rows of the K-major blocks (ci, slice) of the
+// chunk, GEMM column n = 2 r + h.  Right-hand sides at or beyond n_rhs are zero.
+__global__ void __launch_bounds__(256) k_oz_prep(const double* __restrict__ fh, const int* __restrict__ fexp, int K,
+                                                 int NIpad, int n_tb, int G, int Gu, int n_rhs, int k0, int n_modes,
+                                                 unsigned char* __restrict__ out) {
+    const size_t total = (size_t)n_modes * Gu * n_tb * kStages * kRhs * 2;
+    for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
+        const int kc = (int)(t & 1), rl = (int)((t >> 1) % kRhs);
+        size_t q = t / (2 * kRhs);
+        const int st = (int)(q % kStages);
+        q /= kStages;
+        const int tB = (int)(q % n_tb);
+        q /= n_tb;
+        const int g = (int)(q % Gu);
+        const int k = k0 + (int)(q / Gu);
+        const int r = g * kRhs + rl;
+        const int b0 = tB * kTileB + st * kKC + kc * 8;
+        unsigned char* chunk = out + oz_chunk(k, g, tB, st, G, n_tb) * kChunk;
+        const double* src = fh + (((size_t)r * K + k) * NIpad + b0) * 6;
+#pragma unroll
+        for (int h = 0; h < 2; h++) {
+            const int n = 2 * rl + h;
+            const float s = r < n_rhs ? oz_pow2(-fexp[((size_t)r * K + k) * 2 + h]) : 0.0f;
+            const uint32_t off = (uint32_t)(n / 8) * kSBO + (uint32_t)kc * 128u + (uint32_t)(n % 8) * 16u;
+#pragma unroll
+            for (int ci = 0; ci < 3; ci++) {
+                uint32_t w[kNS][4];
+#pragma unroll
+                for (int i = 0; i < 4; i++) {
+                    float t2[2][kNS];
+#pragma unroll
+                    for (int u = 0; u < 2; u++) {
+                        const double x = r < n_rhs ? src[(size_t)(2 * i + u) * 6 + 3 * h + ci] : 0.0;
+                        const float hi = d2f_int(x);
+                        const float lo = d2f_int(x - f2d_int(hi));
+                        oz_split(hi, lo, s, t2[u]);
+                    }
+#pragma unroll
+                    for (int p = 0; p < kNS; p++)
+                        asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(w[p][i]) : "f"(t2[1][p]), "f"(t2[0][p]));
+                }
+#pragma unroll
+                for (int p = 0; p < kNS; p++)
+                    *(uint4*)(chunk + (size_t)(ci * kNS + p) * kBBlk + off) = make_uint4(w[p][0], w[p][1], w[p][2], w[p][3]);
+            }
+        }
+    }
+}
+
+// ---- the contraction --------------------------------------------------------
+
+struct OzArgs {
+    ContractArgs A;              // table (double-float), uh, geometry; A.k0 = first mode of the launch
+    const unsigned char* bprep;  // sliced force operand, chunks oz_chunk(k, g, tB, st)
+    const int* fexp;             // force column scale exponents [rhs][K][2]
+    int n_rhs, G, nbuf;          // rhs applied, rhs groups of the buffer's layout, table sub-box buffers
+};
+
+struct OzSync {
+    uint64_t bfull[kS], empty[kS], done, afull, aempty;
+    uint32_t tbase;
+    volatile int abort;
+};
+
+// Running double-float sum of one output: (H, L) += the seven diagonal sums d[0..6] of a group, at
+// the group's row scale sc.  d2 + d3 + d4 by two-sums (they differ by about 2^8 each and are exact);
+// the rest, below 2^-23 of the total, joins the low word.
+__device__ __forceinline__ void oz_accumulate(const float (&d)[kNQ], float sc, float& H, float& L) {
+    float s, e, s2, e2;
+    two_sum(d[0], d[1], s, e);
+    two_sum(s, d[2], s2, e2);
+    float l = __fadd_rn(__fadd_rn(__fadd_rn(__fadd_rn(__fadd_rn(e, e2), d[3]), d[4]), d[5]), d[6]);
+    s2 = __fmul_rn(s2, sc);
+    l = __fmul_rn(l, sc);
+    float t;
+    two_sum(H, s2, H, t);
+    L = __fadd_rn(L, __fadd_rn(t, l));
+}
+
+__global__ void __launch_bounds__(kThreads, 1) k_contract_oz(OzArgs O, int wl, int* status) {
+    extern __shared__ __align__(1024) unsigned char smem[];
+    __shared__ OzSync sy;
+    const ContractArgs& A = O.A;
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const int co = (int)blockIdx.x % 3, tA = (int)blockIdx.x / 3;
+    const int k = A.k0 + (int)blockIdx.y, g = (int)blockIdx.z;
+    const int n_it = A.n_tb * kStages;
+    const int HW = A.H * A.W, nbuf = O.nbuf;
+    unsigned char* sB = smem;                                      // [kS][kChunk]
+    float* s_tab = (float*)(smem + kS * kChunk);                   // [nbuf][HW][12]
+    int* s_off = (int*)(s_tab + (size_t)nbuf * HW * 12);           // [nbuf][kTileB]
+    float* s_rmax = (float*)(s_off + nbuf * kTileB);               // [2][kRows]
+    volatile int& s_abort = sy.abort;
+
+    if (threadIdx.x == 0) {
+        sy.abort = 0;
+        for (int s = 0; s < kS; s++) tc::mbar_init(&sy.bfull[s], 1), tc::mbar_init(&sy.empty[s], 1);
+        tc::mbar_init(&sy.done, 1);
+        tc::mbar_init(&sy.afull, kBuilderWarps), tc::mbar_init(&sy.aempty, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(tc::smem_u32(&sy.tbase)),
+                     "r"(kTmemCols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = sy.tbase;
+
+    if (warp == kCopyWarp) {
+        // ---- force operand: one bulk copy per stage ----
+        if (lane == 0) {
+            int il = 0;
+            for (; il < n_it; il++) {
+                const int s = il % kS;
+                const uint32_t u = (uint32_t)(il / kS);
+                if (!tc::wait_or_abort(&sy.empty[s], (u & 1u) ^ 1u, &s_abort, wl)) {
+                    s_abort = 1;
+                    break;
+                }
+                const int tB = il / kStages, st = il % kStages;
+                tc::mbar_expect_tx(&sy.bfull[s], kChunk);
+                tc::bulk_g2s(sB + (size_t)s * kChunk, O.bprep + oz_chunk(k, g, tB, st, O.G, A.n_tb) * kChunk, kChunk,
+                             &sy.bfull[s]);
+            }
+            // copies still in flight land before the CTA may go on or exit: the full bound, whatever the stop flag
+            for (int j = max(0, il - kS); j < il; j++) tc::mbar_wait(&sy.bfull[j % kS], (uint32_t)(j / kS) & 1u);
+        }
+    } else if (warp == kMmaWarp) {
+        // ---- tensor-core issue: 3 x 26 products per stage ----
+        if (lane == 0) {
+            const uint32_t id = tc::idesc(1, kRows, kN);
+            const uint64_t dB0 = tc::sdesc(tc::smem_u32(sB), 128, kSBO);
+            for (int il = 0; il < n_it; il++) {
+                const int s = il % kS;
+                const uint32_t par = (uint32_t)(il / kS) & 1u;
+                if (!tc::wait_or_abort(&sy.afull, (uint32_t)il & 1u, &s_abort, wl) ||
+                    !tc::wait_or_abort(&sy.bfull[s], par, &s_abort, wl)) {
+                    s_abort = 1;
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint64_t dBs = dB0 + (uint64_t)(((size_t)s * kChunk) >> 4);
+                const bool first = (il % kStages) == 0;  // a new group overwrites the accumulators
+#pragma unroll
+                for (int ci = 0; ci < 3; ci++)
+#pragma unroll
+                    for (int p = 0; p < kNPair; p++) {
+                        const uint32_t ta = tmem + kAcol + (uint32_t)(ci * kNS + oz_pi(p) - 1) * 8u;
+                        const uint64_t db = dBs + (uint64_t)(((uint32_t)(ci * kNS + oz_pj(p) - 1) * kBBlk) >> 4);
+                        const uint32_t dt = tmem + (uint32_t)(oz_pi(p) + oz_pj(p) - 2) * (uint32_t)kN;
+                        const uint32_t en = (first && ci == 0 && oz_first(p)) ? 0u : 1u;
+                        asm volatile(
+                            "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                            "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}\n" ::"r"(dt),
+                            "r"(ta), "l"(db), "r"(id), "r"(en));
+                    }
+                tc::commit(&sy.aempty);
+                tc::commit(&sy.empty[s]);
+            }
+            tc::commit(&sy.done);  // also after a stop: fires once the issued products are complete
+        }
+    } else {
+        // ---- builders (warps 0..7): table slices into tensor memory, drains, output ----
+        const int tid = threadIdx.x;               // 0 .. 255
+        const int a_loc = (warp & 3) * 32 + lane;  // TMEM lane = GEMM row
+        const int hb = warp >> 2;                  // which 8 of a stage's 16 columns, which 16 of the 32 GEMM columns
+        const int a = tA * kRows + a_loc;
+        const int2 xa = A.xy_p[a];
+        const int4 bA = A.bbox_a[tA];
+        const float* tk = A.tabx2 + (size_t)k * A.Dy * A.Dx * 12;
+        const int rl0 = oz_real(co, 0), rl1 = oz_real(co, 1), rl2 = oz_real(co, 2);
+        const float sg2 = oz_neg(co, 2) ? -1.0f : 1.0f;
+        // double-float sub-box of tile tB and its interface offsets into buffer buf, by asynchronous copies
+        auto stage_async = [&](int buf, int tB) {
+            const int4 bB = A.bbox_b[tB];
+            const int ox = bA.x - bB.y, oy = bA.z - bB.w;
+            float* dt = s_tab + (size_t)buf * HW * 12;
+            for (int e = tid; e < HW * 3; e += kBuilders) {
+                const int ent = e / 3, part = e - 3 * ent;
+                const int iy = ent / A.W, ix = ent - iy * A.W;
+                const int gx = ox + ix - A.box_x0, gy = oy + iy - A.box_y0;
+                const bool in = gx < A.Dx && gy < A.Dy;
+                const float* src = in ? tk + ((size_t)gy * A.Dx + gx) * 12 + 4 * part : tk;  // zero outside the box
+                tc::cp_async16z(dt + (size_t)ent * 12 + 4 * part, src, in ? 16 : 0);
+            }
+            if (tid < kTileB / 4) tc::cp_async16(s_off + buf * kTileB + 4 * tid, A.off_i + tB * kTileB + 4 * tid);
+            asm volatile("cp.async.commit_group;" ::: "memory");
+        };
+        // running double-float sums of this thread's row and GEMM columns hb * 16 .. + 15
+        float H[16], L[16];
+#pragma unroll
+        for (int j = 0; j < 16; j++) H[j] = 0.0f, L[j] = 0.0f;
+        const uint32_t tacc = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(hb * 16);
+        auto drain = [&](float sc) {
+#pragma unroll
+            for (int c = 0; c < 2; c++) {
+                uint32_t u[kNQ][8];
+#pragma unroll
+                for (int q = 0; q < kNQ; q++) tc::ld8_nowait(tacc + (uint32_t)(q * kN + c * 8), u[q]);
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+                for (int j = 0; j < 8; j++) {
+                    float d[kNQ];
+#pragma unroll
+                    for (int q = 0; q < kNQ; q++) d[q] = __uint_as_float(u[q][j]);
+                    oz_accumulate(d, sc, H[c * 8 + j], L[c * 8 + j]);
+                }
+            }
+        };
+        const uint32_t trow = tmem + ((uint32_t)((warp & 3) * 32) << 16) + kAcol + 4u * (uint32_t)hb;
+        float sc_prev = 0.0f;  // 2^E of the tile whose group is drained next
+        int il = 0;
+        if (nbuf == 2) stage_async(0, 0);
+        for (int tB = 0; tB < A.n_tb; tB++) {
+            if (nbuf == 1) {
+                if (tc::builders_sync_any(s_abort)) break;  // everyone is done with the previous tile
+                stage_async(0, tB);
+            }
+            asm volatile("cp.async.wait_all;" ::: "memory");
+            // this tile's copies are visible to every builder, the previous tile is done; one stop decision
+            if (tc::builders_sync_any(s_abort)) break;
+            if (nbuf == 2 && tB + 1 < A.n_tb) stage_async((tB + 1) & 1, tB + 1);
+            const int buf = nbuf == 2 ? (tB & 1) : 0;
+            const float* tab_b = s_tab + (size_t)buf * HW * 12;
+            const int* off_b = s_off + buf * kTileB;
+            const int4 bB = A.bbox_b[tB];
+            const int ox = bA.x - bB.y, oy = bA.z - bB.w;
+            const int base = (xa.x - ox) + A.W * (xa.y - oy);
+            // the row's scale for this tile: its largest entry over both halves' 64 columns
+            float m = 0.0f;
+            for (int st = 0; st < kStages; st++)
+#pragma unroll
+                for (int i = 0; i < 8; i++) {
+                    const float* e = tab_b + (size_t)(base - off_b[st * kKC + hb * 8 + i]) * 12;
+                    m = fmaxf(m, fmaxf(fabsf(e[2 * rl0]), fmaxf(fabsf(e[2 * rl1]), fabsf(e[2 * rl2]))));
+                }
+            s_rmax[hb * kRows + a_loc] = m;
+            if (tc::builders_sync_any(s_abort)) break;
+            const int E = oz_exp_of(fmaxf(s_rmax[a_loc], s_rmax[kRows + a_loc]));
+            const float s_in = oz_pow2(-E), sc = oz_pow2(E);
+            for (int st = 0; st < kStages; st++, il++) {
+                // row a_loc, interface columns st * 16 + hb * 8 .. + 7: the row's three entries, six slices
+                // each, two columns per 32-bit word
+                uint32_t w[3][kNS][4];
+#pragma unroll
+                for (int i2 = 0; i2 < 4; i2++) {
+                    float t[2][3][kNS];
+#pragma unroll
+                    for (int u = 0; u < 2; u++) {
+                        const float* e = tab_b + (size_t)(base - off_b[st * kKC + hb * 8 + 2 * i2 + u]) * 12;
+                        const float2 p0 = *(const float2*)(e + 2 * rl0), p1 = *(const float2*)(e + 2 * rl1);
+                        const float2 p2 = *(const float2*)(e + 2 * rl2);
+                        oz_split(p0.x, p0.y, s_in, t[u][0]);
+                        oz_split(p1.x, p1.y, s_in, t[u][1]);
+                        oz_split(sg2 * p2.x, sg2 * p2.y, s_in, t[u][2]);
+                    }
+#pragma unroll
+                    for (int ci = 0; ci < 3; ci++)
+#pragma unroll
+                        for (int p = 0; p < kNS; p++)
+                            asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(w[ci][p][i2]) : "f"(t[1][ci][p]), "f"(t[0][ci][p]));
+                }
+                // the tensor-memory A blocks are free once the previous stage's products are complete; the
+                // warp decides as one (the stores below are warp-wide)
+                bool ok = !s_abort && tc::wait_or_abort(&sy.aempty, ((uint32_t)il & 1u) ^ 1u, &s_abort, wl);
+                ok = __all_sync(0xffffffffu, ok);
+                if (!ok) {
+                    s_abort = 1;
+                    continue;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                if (st == 0 && tB > 0) drain(sc_prev);  // the previous tile's group is complete
+#pragma unroll
+                for (int ci = 0; ci < 3; ci++)
+#pragma unroll
+                    for (int p = 0; p < kNS; p++)
+                        asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1, %2, %3, %4};" ::"r"(
+                                         trow + (uint32_t)(ci * kNS + p) * 8u),
+                                     "r"(w[ci][p][0]), "r"(w[ci][p][1]), "r"(w[ci][p][2]), "r"(w[ci][p][3])
+                                     : "memory");
+                asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+                asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                __syncwarp();
+                if (lane == 0) tc::mbar_arrive(&sy.afull);
+            }
+            sc_prev = sc;
+        }
+        asm volatile("cp.async.wait_all;" ::: "memory");  // a prefetch still in flight after a stop
+        // every product the MMA thread issued is complete once `done` fires (it commits on every path), so
+        // this wait keeps the full bound whatever the stop flag says
+        const bool done_ok = tc::mbar_wait(&sy.done, 0u);
+        const bool ok = __all_sync(0xffffffffu, done_ok && !s_abort);
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (ok) {
+            drain(sc_prev);  // the last tile's group
+#pragma unroll
+            for (int j = 0; j < 16; j++) {
+                const int n = hb * 16 + j, r = g * kRhs + n / 2, h = n & 1;
+                if (r < O.n_rhs) {
+                    const float sF = oz_pow2(O.fexp[((size_t)r * A.K + k) * 2 + h]);
+                    A.uh[(((size_t)r * A.K + k) * A.NPpad + a) * 6 + 3 * h + co] =
+                        f2d_int(__fmul_rn(H[j], sF)) + f2d_int(__fmul_rn(L[j], sF));
+                }
+            }
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && sy.abort) atomicExch(status, FBC_ERR_TIMEOUT);
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols));
+}
+
+size_t oz_smem(int HW, int nbuf) {
+    return (size_t)kS * kChunk + (size_t)nbuf * ((size_t)HW * 48 + kTileB * 4) + 2 * kRows * 4 + 1024;
+}
+// two table buffers (the next tile prefetched) when they fit, else one
+int oz_nbuf(int HW) { return oz_smem(HW, 2) <= 227 * 1024 ? 2 : 1; }
+int oz_groups(const Plan& P) { return (P.opt.max_rhs + kRhs - 1) / kRhs; }
+size_t oz_chunk_bytes(const Plan& P) { return (size_t)P.K * oz_groups(P) * P.n_tb * kStages * kChunk; }
+
+}  // namespace
+
+size_t contract_oz_smem(int HW) { return oz_smem(HW, oz_nbuf(HW)); }
+
+// the sliced force operand of every mode and rhs group, then the scale exponents [max_rhs][K][2]
+size_t contract_oz_prep_bytes(const Plan& P) {
+    return oz_chunk_bytes(P) + (size_t)P.opt.max_rhs * P.K * 2 * sizeof(int);
+}
+
+// Modes A.k0 .. K - 1 (A.k0 >= 1) of an FBC_PREC_BF16X6 plan: scales and slices of the forces, then the
+// contraction, one CTA per (pad tile, output component) x mode x group of 16 right-hand sides.
+cudaError_t launch_contract_oz(const ContractArgs& A, const Plan& P, int n_rhs, cudaStream_t st) {
+    const int n_modes = P.K - A.k0;
+    if (n_modes <= 0 || n_rhs < 1) return cudaSuccess;
+    const int HW = P.H * P.W;
+    const size_t smem = oz_smem(HW, oz_nbuf(HW));
+    if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
+    if (!P.d_bprep || P.bprep_prec != FBC_PREC_BF16X6 || P.bprep_bytes < contract_oz_prep_bytes(P) ||
+        n_rhs > P.opt.max_rhs || !A.tabx2 || A.tabx2 != P.d_table_x2)
+        return cudaErrorInvalidValue;
+    OzArgs O;
+    O.A = A;
+    O.bprep = (const unsigned char*)P.d_bprep;
+    O.fexp = (const int*)((const unsigned char*)P.d_bprep + oz_chunk_bytes(P));
+    O.n_rhs = n_rhs;
+    O.G = oz_groups(P);
+    O.nbuf = oz_nbuf(HW);
+    k_oz_fscale<<<dim3(n_modes, n_rhs), 256, 0, st>>>(A.fh, P.K, P.NIpad, A.k0, (int*)O.fexp);
+    if (cudaError_t e = cudaGetLastError()) return e;
+    const int gu = (n_rhs + kRhs - 1) / kRhs;  // rhs groups of this apply
+    const size_t total = (size_t)n_modes * gu * P.n_tb * kStages * kRhs * 2;
+    const int grid = (int)std::min<size_t>((total + 255) / 256, (size_t)152 * 32);
+    k_oz_prep<<<grid, 256, 0, st>>>(A.fh, O.fexp, P.K, P.NIpad, P.n_tb, O.G, gu, n_rhs, A.k0, n_modes,
+                                    (unsigned char*)P.d_bprep);
+    if (cudaError_t e = cudaGetLastError()) return e;
+    cudaError_t e = cudaFuncSetAttribute(k_contract_oz, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e) return e;
+    const int wl = P.wait_limit > 0 ? P.wait_limit : tc::kWaitLimit;
+    k_contract_oz<<<dim3(3 * P.n_ta, n_modes, gu), kThreads, smem, st>>>(O, wl, P.d_status);
+    return cudaGetLastError();
+}
+
+}  // namespace fbc

@@ -132,50 +132,12 @@ __device__ __forceinline__ uint4 pack16(const uint32_t* w) {
     return v;
 }
 
-// Pipeline wait: bounded by `limit` polls, and gives up as soon as another role has set *abort.
-__device__ __forceinline__ bool wait_or_abort(uint64_t* m, uint32_t parity, volatile int* abort, int limit) {
-    for (int it = 0; it < limit; it++) {
-        uint32_t ok;
-        asm volatile(
-            "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
-            : "=r"(ok)
-            : "r"(smem_u32(m)), "r"(parity)
-            : "memory");
-        if (ok) return true;
-        if ((it & 255) == 255 && *abort) return false;
-    }
-    return false;
-}
-
-// Named barrier among the builder warps that also returns, to every one of
-// them, whether any passed flag != 0: a decision all of them take alike.
-__device__ __forceinline__ bool builders_sync_any(int flag) {
-    uint32_t r;
-    asm volatile(
-        "{\n.reg .pred p, q;\nsetp.ne.s32 p, %1, 0;\nbar.red.or.pred q, 1, %2, p;\nselp.u32 %0, 1, 0, q;\n}\n"
-        : "=r"(r)
-        : "r"(flag), "n"(kBuilders)
-        : "memory");
-    return r != 0;
-}
-
-__device__ __forceinline__ void cp_async8(void* dst, const void* src, int src_bytes) {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(smem_u32(dst)), "l"(src), "r"(src_bytes)
-                 : "memory");
-}
-__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive(uint64_t* m) {
-    asm volatile("{\n.reg .b64 st;\nmbarrier.arrive.shared::cta.b64 st, [%0];\n}\n" ::"r"(smem_u32(m)) : "memory");
-}
-__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* m) {
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_u32(dst)),
-        "l"(src), "r"(bytes), "r"(smem_u32(m))
-        : "memory");
-}
+using tc::builders_sync_any;
+using tc::bulk_g2s;
+using tc::cp_async16;
+using tc::cp_async8;
+using tc::mbar_arrive;
+using tc::wait_or_abort;
 
 // Chunk of the split force operand for (k, rhs group g, interface tile tB, stage st).
 __host__ __device__ __forceinline__ size_t bchunk_index(int k, int g, int tB, int st, int G, int n_tb) {

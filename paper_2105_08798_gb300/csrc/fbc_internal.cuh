@@ -219,6 +219,11 @@ cudaError_t contract_tc_prep(const Plan& P, const double* fh, int rpc, int n_rhs
 TcJob contract_tc_job(const Plan& P, int n_rhs, int rpc, int nbuf);
 cudaError_t launch_contract_tc_batch(int precision, const TcJob* d_jobs, const int4* d_items, int n_items,
                                      int* d_counter, int grid, size_t smem, int wl, int* status, cudaStream_t st);
+// FBC_PREC_BF16X6 (fbc_contract_oz.cu): shared memory of the contraction, bytes of the sliced force
+// operand and scales (the plan's d_bprep), and the launch of modes A.k0 .. K - 1
+size_t contract_oz_smem(int HW);
+size_t contract_oz_prep_bytes(const Plan& P);
+cudaError_t launch_contract_oz(const ContractArgs& A, const Plan& P, int n_rhs, cudaStream_t st);
 inline bool is_tensor_precision(int p) { return p == FBC_PREC_TF32 || p == FBC_PREC_BF16X2 || p == FBC_PREC_BF16X3; }
 int batch_rhs_block();
 LineArgs make_line_args(const Plan& P, const double* f, double* u);

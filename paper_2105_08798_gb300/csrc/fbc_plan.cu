@@ -236,7 +236,23 @@ int ensure_derived(fbc::Plan& P, int precision) {
         int s = dev_alloc(&P.d_uh32, (size_t)P.opt.max_rhs * P.K * P.NPpad * 6, acc, "uh32");
         if (s) return s;
     }
-    if (precision == FBC_PREC_F32X2 && !P.d_table_x2) {
+    // FBC_PREC_BF16X6: the double-float table and the sliced force operand with its scales
+    if (precision == FBC_PREC_BF16X6 && P.bprep_prec != precision) {
+        const size_t want = fbc::contract_oz_prep_bytes(P);
+        if (P.d_bprep && P.bprep_bytes < want) {
+            cudaFree(P.d_bprep);
+            P.workspace_bytes -= P.bprep_bytes;
+            P.d_bprep = nullptr, P.bprep_bytes = 0;
+        }
+        if (!P.d_bprep) {
+            unsigned char* q = nullptr;
+            int s = dev_alloc(&q, want, acc, "sliced force operand");
+            if (s) return s;
+            P.d_bprep = q, P.bprep_bytes = want;
+        }
+        P.bprep_prec = precision;
+    }
+    if ((precision == FBC_PREC_F32X2 || precision == FBC_PREC_BF16X6) && !P.d_table_x2) {
         int s = dev_alloc(&P.d_table_x2, cells * 12, acc, "table_x2");
         if (s) return s;
     }
@@ -325,7 +341,7 @@ int fbc_plan_create(const fbc_geometry* geom, const fbc_material* mat, const fbc
         return fail(FBC_ERR_INVALID_ARG, "Richardson needs n >= 1, 0 <= N <= 12, n + N <= %d", fbc::kMaxRichImages);
     if (opt.quad < 8 || opt.quad > fbc::kMaxQuad) return fail(FBC_ERR_INVALID_ARG, "quad must be in [8, %d]", fbc::kMaxQuad);
     if (opt.max_rhs < 1 || opt.max_rhs > 4096) return fail(FBC_ERR_INVALID_ARG, "max_rhs must be in [1, 4096]");
-    if (opt.precision < FBC_PREC_FP64 || opt.precision > FBC_PREC_FFT32)
+    if (opt.precision < FBC_PREC_FP64 || opt.precision > FBC_PREC_BF16X6)
         return fail(FBC_ERR_INVALID_ARG, "unknown precision %d", opt.precision);
     if (opt.flags & ~(FBC_PLAN_HOST_ONLY | FBC_PLAN_TC_FAST_ACCUMULATE | FBC_PLAN_SELF_TERMS))
         return fail(FBC_ERR_INVALID_ARG, "unknown options.flags bits 0x%x", opt.flags);
@@ -538,7 +554,7 @@ int fbc_tabulate_kernel(fbc_plan* plan, void* stream) {
 int fbc_plan_set_precision(fbc_plan* plan, int32_t precision) {
     g_last_error.clear();
     if (!plan) return fail(FBC_ERR_INVALID_ARG, "plan is NULL");
-    if (precision < FBC_PREC_FP64 || precision > FBC_PREC_FFT32)
+    if (precision < FBC_PREC_FP64 || precision > FBC_PREC_BF16X6)
         return fail(FBC_ERR_INVALID_ARG, "unknown precision %d", precision);
     fbc::Plan& P = plan->p;
     if (P.host_only) return fail(FBC_ERR_INVALID_ARG, "host-only plan");
@@ -579,7 +595,10 @@ static int apply_checks(fbc::Plan& P, const double* f, const double* u, int32_t 
         return fail(FBC_ERR_INVALID_ARG, "FP32 table missing");
     if (fbc::is_tensor_precision(P.precision) && fbc::contract_tc_smem(P.precision, P.W * P.H) > 227 * 1024)
         return fail(FBC_ERR_UNSUPPORTED, "tensor-core contraction: staged sub-box too large for shared memory");
-    if (P.precision == FBC_PREC_F32X2 && !P.d_table_x2) return fail(FBC_ERR_INVALID_ARG, "F32X2 table missing");
+    if ((P.precision == FBC_PREC_F32X2 || P.precision == FBC_PREC_BF16X6) && !P.d_table_x2)
+        return fail(FBC_ERR_INVALID_ARG, "double-float table missing");
+    if (P.precision == FBC_PREC_BF16X6 && fbc::contract_oz_smem(P.W * P.H) > 227 * 1024)
+        return fail(FBC_ERR_UNSUPPORTED, "BF16X6 contraction: staged sub-box too large for shared memory");
     if (fbc::is_fft_precision(P.precision) && !fbc::fft_ready(P, P.precision))
         return fail(FBC_ERR_INVALID_ARG, "in-plane FFT grid missing");
     return FBC_OK;

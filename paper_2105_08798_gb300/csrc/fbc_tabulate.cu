@@ -330,7 +330,7 @@ cudaError_t launch_derive_tables(Plan& P, int precision, cudaStream_t st) {
         return cudaGetLastError();
     }
     if (is_fft_precision(precision)) return launch_fft_tables(P, precision, st);
-    if (precision == FBC_PREC_F32X2) {
+    if (precision == FBC_PREC_F32X2 || precision == FBC_PREC_BF16X6) {
         if (!P.d_table_x2) return cudaErrorInvalidValue;
         k_derive_x2<<<1216, 256, 0, st>>>(P.d_table, P.d_table_x2, cells);
         return cudaGetLastError();

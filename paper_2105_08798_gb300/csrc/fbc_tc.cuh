@@ -100,5 +100,65 @@ __device__ __forceinline__ void ld16(uint32_t taddr, float (&v)[16]) {
     for (int i = 0; i < 16; i++) v[i] = __uint_as_float(u[i]);
 }
 
+// Pipeline wait: bounded by `limit` polls, and gives up as soon as another role has set *abort.
+__device__ __forceinline__ bool wait_or_abort(uint64_t* m, uint32_t parity, volatile int* abort, int limit) {
+    for (int it = 0; it < limit; it++) {
+        uint32_t ok;
+        asm volatile(
+            "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(ok)
+            : "r"(smem_u32(m)), "r"(parity)
+            : "memory");
+        if (ok) return true;
+        if ((it & 255) == 255 && *abort) return false;
+    }
+    return false;
+}
+
+// Named barrier 1 among the NT threads of the builder warps that also returns,
+// to every one of them, whether any passed flag != 0: a decision all of them
+// take alike.
+template <int NT = 256>
+__device__ __forceinline__ bool builders_sync_any(int flag) {
+    uint32_t r;
+    asm volatile(
+        "{\n.reg .pred p, q;\nsetp.ne.s32 p, %1, 0;\nbar.red.or.pred q, 1, %2, p;\nselp.u32 %0, 1, 0, q;\n}\n"
+        : "=r"(r)
+        : "r"(flag), "n"(NT)
+        : "memory");
+    return r != 0;
+}
+
+__device__ __forceinline__ void cp_async8(void* dst, const void* src, int src_bytes) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(smem_u32(dst)), "l"(src), "r"(src_bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+
+// 16 bytes, of which the first src_bytes (0 or 16) come from global memory and the rest are zero
+__device__ __forceinline__ void cp_async16z(void* dst, const void* src, int src_bytes) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(dst)), "l"(src), "r"(src_bytes)
+                 : "memory");
+}
+
+// 8 consecutive FP32 accumulator columns of this thread's TMEM lane (no wait: follow with tcgen05.wait::ld)
+__device__ __forceinline__ void ld8_nowait(uint32_t taddr, uint32_t (&u)[8]) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(u[0]), "=r"(u[1]), "=r"(u[2]), "=r"(u[3]), "=r"(u[4]), "=r"(u[5]), "=r"(u[6]), "=r"(u[7])
+                 : "r"(taddr));
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* m) {
+    asm volatile("{\n.reg .b64 st;\nmbarrier.arrive.shared::cta.b64 st, [%0];\n}\n" ::"r"(smem_u32(m)) : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* m) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(m))
+        : "memory");
+}
+
 }  // namespace tc
 }  // namespace fbc

@@ -40,9 +40,10 @@ FBC_PREC_BF16X2 = 4
 FBC_PREC_BF16X3 = 5
 FBC_PREC_FFT64 = 6
 FBC_PREC_FFT32 = 7
+FBC_PREC_BF16X6 = 8
 PRECISIONS = {"fp64": FBC_PREC_FP64, "fp32": FBC_PREC_FP32, "f32x2": FBC_PREC_F32X2, "tf32": FBC_PREC_TF32,
               "bf16x2": FBC_PREC_BF16X2, "bf16x3": FBC_PREC_BF16X3, "fft64": FBC_PREC_FFT64,
-              "fft32": FBC_PREC_FFT32}
+              "fft32": FBC_PREC_FFT32, "bf16x6": FBC_PREC_BF16X6}
 
 FBC_PLAN_HOST_ONLY = 1
 FBC_PLAN_SELF_TERMS = 4

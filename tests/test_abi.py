@@ -116,7 +116,7 @@ def test_validation_rejects_bad_input(lib):
         fbc.FBC_ERR_UNSUPPORTED
     assert _try_create(xy_i, xy_p, 16, ISO, max_rhs=0) == fbc.FBC_ERR_INVALID_ARG
     assert _try_create(xy_i, xy_p, 16, ISO, rich_n=0) == fbc.FBC_ERR_INVALID_ARG
-    assert _try_create(xy_i, xy_p, 16, ISO, precision=fbc.FBC_PREC_FFT32 + 1) == fbc.FBC_ERR_INVALID_ARG
+    assert _try_create(xy_i, xy_p, 16, ISO, precision=fbc.FBC_PREC_BF16X6 + 1) == fbc.FBC_ERR_INVALID_ARG
     assert "power of two" in fbc.fbc_last_error() or fbc.fbc_last_error() != ""
 
 

@@ -36,7 +36,7 @@ def fbc():
     return fbc_mod
 
 
-@pytest.mark.parametrize("prec", ["bf16x2", "tf32", "bf16x3"])
+@pytest.mark.parametrize("prec", ["bf16x2", "tf32", "bf16x3", "bf16x6"])
 def test_wait_limit_timeout_then_recovery(fbc, prec):
     xy_i, xy_p = inputs.ring_geometry(200, 300)
     L, R = 16, 16

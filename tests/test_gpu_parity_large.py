@@ -28,6 +28,7 @@ BOUNDS = {
     "tf32": (8e-4, 1e-12, 1e-3, 8e-4),
     "fft32": (6e-7, 1e-12, 1e-6, 3e-6),
     "fft64": (1e-12, 1e-12, 1e-12, 1e-11),
+    "bf16x6": (1e-12, 1e-12, 1e-12, 1e-11),
 }
 
 
