@@ -237,13 +237,14 @@ int fbc_apply_relaxed(fbc_plan* plan, const double* f_new, const double* f_old, 
 
 /* Same as fbc_apply with f and u in HOST memory (pinned memory makes the
  * copies asynchronous): copies f (and u when beta != 0) to the plan's device
- * staging buffers, applies, copies u back and synchronises `stream`.  With
- * 8 or more right-hand sides they go through in chunks of at least 4 (at
- * most 8 chunks): each chunk is copied in on a stream of the plan, applied on
- * `stream`, and copied out on a second stream of the plan, so the copies of
- * one chunk overlap the applies of the others.  Each right-hand side is
- * computed as in one fbc_apply of all of them (for the CUDA-core forms with
- * the same bits).  The first call allocates the staging buffers and creates
+ * staging buffers, applies, copies u back and synchronises `stream`.  The
+ * right-hand sides go through in at most 8 chunks of at least 4 (for the
+ * tensor-core forms: of whole right-hand-side groups, 32 for FBC_PREC_BF16X6
+ * and up to 64 for the others): each chunk is copied in on a stream of the
+ * plan, applied on `stream`, and copied out on a second stream of the plan,
+ * so the copies of one chunk overlap the applies of the others.  Each
+ * right-hand side is computed as in one fbc_apply of all of them (for the
+ * CUDA-core forms and FBC_PREC_BF16X6 with the same bits).  The first call allocates the staging buffers and creates
  * the two streams. */
 int fbc_apply_host(fbc_plan* plan, const double* f_host, double* u_host, int32_t n_rhs, double alpha,
                    double beta, uint32_t flags, void* stream);

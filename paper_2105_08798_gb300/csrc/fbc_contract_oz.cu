@@ -62,22 +62,25 @@ namespace {
 
 constexpr int kTmemCols = 512;
 constexpr int kRows = kTileA;        // GEMM rows (pad columns) per CTA
-constexpr int kRhs = 16;             // right-hand sides per CTA
+constexpr int kRhs = 32;             // right-hand sides per CTA
 constexpr int kN = 2 * kRhs;         // GEMM columns: (x, y') of each right-hand side
 constexpr int kKC = 16;              // interface columns per stage (the bf16 MMA's K)
 constexpr int kStages = kTileB / kKC;  // stages per interface tile = per accumulation group
 constexpr int kNS = 6;               // slices per operand value
-constexpr int kNQ = 7;               // diagonals q = 2 .. 8
+constexpr int kNQ = 5;               // accumulators: diagonals q = 2, 3, 4, 5 and q >= 6 together
 constexpr int kNPair = 26;           // slice products with i, j <= 6 and i + j <= 8
 constexpr int kBuilderWarps = 8;
 constexpr int kBuilders = kBuilderWarps * 32;
 constexpr int kMmaWarp = 8, kCopyWarp = 9;
 constexpr int kThreads = 10 * 32;
 constexpr int kS = 3;                // force-operand ring stages
-constexpr uint32_t kAcol = 256;      // first TMEM column of the A blocks
-constexpr uint32_t kBBlk = (uint32_t)kN * kKC * 2;       // one (ci, slice) block of a force chunk: 1 KB
-constexpr uint32_t kChunk = 3u * kNS * kBBlk;            // one stage of the force operand: 18 KB
+constexpr uint32_t kAcol = kNQ * kN;                     // first TMEM column of the A blocks (after 5 x 64)
+constexpr uint32_t kAcols = 3 * kNS * 8;                 // TMEM columns of the A blocks (18 blocks of 128 x 16 bf16)
+static_assert(kAcol + kAcols <= kTmemCols, "tensor memory");
+constexpr uint32_t kBBlk = (uint32_t)kN * kKC * 2;       // one (ci, slice) block of a force chunk: 2 KB
+constexpr uint32_t kChunk = 3u * kNS * kBBlk;            // one stage of the force operand: 36 KB
 constexpr uint32_t kSBO = (kKC / 8) * 128;               // 8-row group stride of a [rows][16] bf16 block
+constexpr uint32_t kSleepNs = 200;  // suspend hint of the copy and MMA threads' waits
 constexpr int kEmin = -120, kEmax = 120;                 // clamp of the scale exponents (2^E a normal float)
 
 // Entry of M(d) in row co, column ci, as (index into the six table reals, sign):
@@ -88,7 +91,8 @@ __host__ __device__ constexpr int oz_real(int co, int ci) {
 __host__ __device__ constexpr bool oz_neg(int co, int ci) { return ci == 2 && co < 2; }
 
 // Slice products by diagonal: pair p multiplies A slice oz_pi(p) with B slice oz_pj(p) (1-based) into
-// accumulator q = oz_pi(p) + oz_pj(p); oz_first(p) marks the first product of its diagonal.
+// diagonal q = oz_pi(p) + oz_pj(p), accumulator oz_acc(p) (q = 6, 7, 8 share the last); oz_first(p) marks
+// the first product into its accumulator.
 __host__ __device__ constexpr int oz_pi(int p) {
     constexpr int v[kNPair] = {1, 1, 2, 1, 2, 3, 1, 2, 3, 4, 1, 2, 3, 4, 5, 1, 2, 3, 4, 5, 6, 2, 3, 4, 5, 6};
     return v[p];
@@ -97,10 +101,11 @@ __host__ __device__ constexpr int oz_pj(int p) {
     constexpr int v[kNPair] = {1, 2, 1, 3, 2, 1, 4, 3, 2, 1, 5, 4, 3, 2, 1, 6, 5, 4, 3, 2, 1, 6, 5, 4, 3, 2};
     return v[p];
 }
-__host__ __device__ constexpr bool oz_first(int p) {
-    return p == 0 || oz_pi(p) + oz_pj(p) != oz_pi(p - 1) + oz_pj(p - 1);
-}
-static_assert(oz_pi(kNPair - 1) + oz_pj(kNPair - 1) == 8 && oz_first(21) && !oz_first(25), "pair table");
+__host__ __device__ constexpr int oz_acc(int p) { return (oz_pi(p) + oz_pj(p) < 6 ? oz_pi(p) + oz_pj(p) : 6) - 2; }
+__host__ __device__ constexpr bool oz_first(int p) { return p == 0 || oz_acc(p) != oz_acc(p - 1); }
+static_assert(oz_pi(kNPair - 1) + oz_pj(kNPair - 1) == 8 && oz_first(10) && !oz_first(15) && !oz_first(21) &&
+                  oz_acc(kNPair - 1) == kNQ - 1,
+              "pair table");
 
 // Six fixed-point slices of v' = (hi + lo) s, |v'| < 1/2, s a power of two: t_i is v's remainder
 // rounded to the grid 2^(-8 i) (add and subtract 1.5 x 2^(23 - 8 i)).  hi s - t_1 and the later
@@ -130,12 +135,6 @@ __device__ __forceinline__ int oz_exp_of(float m) {
 }
 __device__ __forceinline__ float oz_pow2(int e) { return __uint_as_float((uint32_t)(127 + e) << 23); }
 
-// Two-sum (Knuth): s + e == a + b exactly.
-__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
-    s = __fadd_rn(a, b);
-    const float bb = __fsub_rn(s, a);
-    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
-}
 
 // ---- force operand: scales and slices (once per apply) ----------------------
 
@@ -237,7 +236,7 @@ struct OzArgs {
     ContractArgs A;              // table (double-float), uh, geometry; A.k0 = first mode of the launch
     const unsigned char* bprep;  // sliced force operand, chunks oz_chunk(k, g, tB, st)
     const int* fexp;             // force column scale exponents [rhs][K][2]
-    int n_rhs, G, nbuf;          // rhs applied, rhs groups of the buffer's layout, table sub-box buffers
+    int n_rhs, G;                // rhs applied, rhs groups of the buffer's layout
 };
 
 struct OzSync {
@@ -246,20 +245,84 @@ struct OzSync {
     volatile int abort;
 };
 
-// Running double-float sum of one output: (H, L) += the seven diagonal sums d[0..6] of a group, at
-// the group's row scale sc.  d2 + d3 + d4 by two-sums (they differ by about 2^8 each and are exact);
-// the rest, below 2^-23 of the total, joins the low word.
-__device__ __forceinline__ void oz_accumulate(const float (&d)[kNQ], float sc, float& H, float& L) {
-    float s, e, s2, e2;
-    two_sum(d[0], d[1], s, e);
-    two_sum(s, d[2], s2, e2);
-    float l = __fadd_rn(__fadd_rn(__fadd_rn(__fadd_rn(__fadd_rn(e, e2), d[3]), d[4]), d[5]), d[6]);
-    s2 = __fmul_rn(s2, sc);
-    l = __fmul_rn(l, sc);
-    float t;
-    two_sum(H, s2, H, t);
-    L = __fadd_rn(L, __fadd_rn(t, l));
+// Packed FP32 pairs (two lanes per instruction, each rounded to nearest as the scalar operation).
+__device__ __forceinline__ uint64_t pk2(float a, float b) {
+    uint64_t r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
 }
+__device__ __forceinline__ void upk2(uint64_t r, float& a, float& b) { asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(r)); }
+__device__ __forceinline__ uint64_t add2(uint64_t a, uint64_t b) {
+    uint64_t r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ uint64_t sub2(uint64_t a, uint64_t b) {
+    uint64_t r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ uint64_t mul2(uint64_t a, uint64_t b) {
+    uint64_t r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ uint64_t fma2(uint64_t a, uint64_t b, uint64_t c) {
+    uint64_t r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+    return r;
+}
+
+// oz_split on two values at once: (hi, lo) pairs of two values, s a pair of powers of two.
+__device__ __forceinline__ void oz_split2(uint64_t hi, uint64_t lo, uint64_t s, uint64_t (&t)[kNS]) {
+    const uint64_t C1 = pk2(49152.0f, 49152.0f), C2 = pk2(192.0f, 192.0f), C3 = pk2(0.75f, 0.75f);
+    const uint64_t C4 = pk2(0.0029296875f, 0.0029296875f), C5 = pk2(1.1444091796875e-05f, 1.1444091796875e-05f);
+    const uint64_t C6 = pk2(4.470348358154297e-08f, 4.470348358154297e-08f);
+    const uint64_t m = mul2(hi, s);  // exact: s is a power of two
+    t[0] = sub2(add2(m, C1), C1);
+    uint64_t r = sub2(m, t[0]);
+    t[1] = sub2(add2(r, C2), C2);
+    r = sub2(r, t[1]);
+    t[2] = sub2(add2(r, C3), C3);
+    r = sub2(r, t[2]);
+    r = fma2(lo, s, r);
+    t[3] = sub2(add2(r, C4), C4);
+    r = sub2(r, t[3]);
+    t[4] = sub2(add2(r, C5), C5);
+    r = sub2(r, t[4]);
+    t[5] = sub2(add2(r, C6), C6);
+}
+
+__device__ __forceinline__ uint32_t cvt_bf16x2(float hi, float lo) {
+    uint32_t r;
+    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
+    return r;
+}
+
+// Two-sum (Knuth) on pairs: s + e == a + b exactly, per lane.
+__device__ __forceinline__ void two_sum2(uint64_t a, uint64_t b, uint64_t& s, uint64_t& e) {
+    s = add2(a, b);
+    const uint64_t bb = sub2(s, a);
+    e = add2(sub2(a, sub2(s, bb)), sub2(b, bb));
+}
+
+// Running double-float sums of two outputs: (H, L) += the five accumulator sums d[0..4] of a group (pairs:
+// diagonals 2, 3, 4, 5 and 6-8), at the group's scale sc.  d2 + d3 + d4 by two-sums (they differ by about
+// 2^8 each and are exact); the rest, below 2^-23 of the total, joins the low word.
+__device__ __forceinline__ void oz_accumulate2(const uint64_t (&d)[kNQ], uint64_t sc, uint64_t& H, uint64_t& L) {
+    uint64_t s, e, s2, e2, t;
+    two_sum2(d[0], d[1], s, e);
+    two_sum2(s, d[2], s2, e2);
+    uint64_t l = add2(add2(add2(e, e2), d[3]), d[4]);
+    s2 = mul2(s2, sc);
+    l = mul2(l, sc);
+    two_sum2(H, s2, H, t);
+    L = add2(L, add2(t, l));
+}
+
+// Shared-memory bytes of one staged table sub-box: the CTA's three reals as (hi, lo) of the first two
+// (packed pairs), hi and lo of the third, and the largest |hi| of the three per entry.
+__host__ __device__ inline size_t oz_tab_bytes(int HW) { return ((size_t)HW * 28 + 15) / 16 * 16; }
 
 __global__ void __launch_bounds__(kThreads, 1) k_contract_oz(OzArgs O, int wl, int* status) {
     extern __shared__ __align__(1024) unsigned char smem[];
@@ -269,11 +332,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_contract_oz(OzArgs O, int wl, i
     const int co = (int)blockIdx.x % 3, tA = (int)blockIdx.x / 3;
     const int k = A.k0 + (int)blockIdx.y, g = (int)blockIdx.z;
     const int n_it = A.n_tb * kStages;
-    const int HW = A.H * A.W, nbuf = O.nbuf;
-    unsigned char* sB = smem;                                      // [kS][kChunk]
-    float* s_tab = (float*)(smem + kS * kChunk);                   // [nbuf][HW][12]
-    int* s_off = (int*)(s_tab + (size_t)nbuf * HW * 12);           // [nbuf][kTileB]
-    float* s_rmax = (float*)(s_off + nbuf * kTileB);               // [2][kRows]
+    const int HW = A.H * A.W;
+    const size_t tb = oz_tab_bytes(HW);
+    unsigned char* sB = smem;                                     // [kS][kChunk]
+    unsigned char* s_tabs = smem + kS * kChunk;                   // [tb]: the staged double-float sub-box
+    int* s_off = (int*)(s_tabs + tb);                             // [2][kTileB]: interface offsets of two tiles
+    uint32_t* s_sl = (uint32_t*)(s_off + 2 * kTileB);             // [HW][9]: the sub-box cut into slices
+    __shared__ uint32_t s_wmax[kBuilderWarps];
     volatile int& s_abort = sy.abort;
 
     if (threadIdx.x == 0) {
@@ -300,7 +365,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_contract_oz(OzArgs O, int wl, i
             for (; il < n_it; il++) {
                 const int s = il % kS;
                 const uint32_t u = (uint32_t)(il / kS);
-                if (!tc::wait_or_abort(&sy.empty[s], (u & 1u) ^ 1u, &s_abort, wl)) {
+                if (!tc::wait_or_abort_sleep(&sy.empty[s], (u & 1u) ^ 1u, &s_abort, wl, kSleepNs)) {
                     s_abort = 1;
                     break;
                 }
@@ -320,21 +385,22 @@ __global__ void __launch_bounds__(kThreads, 1) k_contract_oz(OzArgs O, int wl, i
             for (int il = 0; il < n_it; il++) {
                 const int s = il % kS;
                 const uint32_t par = (uint32_t)(il / kS) & 1u;
-                if (!tc::wait_or_abort(&sy.afull, (uint32_t)il & 1u, &s_abort, wl) ||
-                    !tc::wait_or_abort(&sy.bfull[s], par, &s_abort, wl)) {
+                if (!tc::wait_or_abort_sleep(&sy.afull, (uint32_t)il & 1u, &s_abort, wl, kSleepNs) ||
+                    !tc::wait_or_abort_sleep(&sy.bfull[s], par, &s_abort, wl, kSleepNs)) {
                     s_abort = 1;
                     break;
                 }
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 const uint64_t dBs = dB0 + (uint64_t)(((size_t)s * kChunk) >> 4);
+                const uint32_t ta0 = tmem + kAcol;
                 const bool first = (il % kStages) == 0;  // a new group overwrites the accumulators
 #pragma unroll
                 for (int ci = 0; ci < 3; ci++)
 #pragma unroll
                     for (int p = 0; p < kNPair; p++) {
-                        const uint32_t ta = tmem + kAcol + (uint32_t)(ci * kNS + oz_pi(p) - 1) * 8u;
+                        const uint32_t ta = ta0 + (uint32_t)(ci * kNS + oz_pi(p) - 1) * 8u;
                         const uint64_t db = dBs + (uint64_t)(((uint32_t)(ci * kNS + oz_pj(p) - 1) * kBBlk) >> 4);
-                        const uint32_t dt = tmem + (uint32_t)(oz_pi(p) + oz_pj(p) - 2) * (uint32_t)kN;
+                        const uint32_t dt = tmem + (uint32_t)oz_acc(p) * (uint32_t)kN;
                         const uint32_t en = (first && ci == 0 && oz_first(p)) ? 0u : 1u;
                         asm volatile(
                             "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
@@ -357,98 +423,140 @@ __global__ void __launch_bounds__(kThreads, 1) k_contract_oz(OzArgs O, int wl, i
         const float* tk = A.tabx2 + (size_t)k * A.Dy * A.Dx * 12;
         const int rl0 = oz_real(co, 0), rl1 = oz_real(co, 1), rl2 = oz_real(co, 2);
         const float sg2 = oz_neg(co, 2) ? -1.0f : 1.0f;
-        // double-float sub-box of tile tB and its interface offsets into buffer buf, by asynchronous copies
-        auto stage_async = [&](int buf, int tB) {
+        // the CTA's three reals of every entry of tile tB's sub-box into the staging buffer (hi/lo pairs of
+        // the first two, hi and lo of the third), and the tile's interface offsets into offset buffer tB & 1,
+        // by asynchronous 4-byte copies
+        auto stage_async = [&](int tB) {
             const int4 bB = A.bbox_b[tB];
             const int ox = bA.x - bB.y, oy = bA.z - bB.w;
-            float* dt = s_tab + (size_t)buf * HW * 12;
-            for (int e = tid; e < HW * 3; e += kBuilders) {
-                const int ent = e / 3, part = e - 3 * ent;
-                const int iy = ent / A.W, ix = ent - iy * A.W;
+            float* h01 = (float*)s_tabs;
+            float* l01 = h01 + 2 * HW;
+            float* h2 = l01 + 2 * HW;
+            float* l2 = h2 + HW;
+            for (int e = tid; e < HW; e += kBuilders) {
+                const int iy = e / A.W, ix = e - iy * A.W;
                 const int gx = ox + ix - A.box_x0, gy = oy + iy - A.box_y0;
                 const bool in = gx < A.Dx && gy < A.Dy;
-                const float* src = in ? tk + ((size_t)gy * A.Dx + gx) * 12 + 4 * part : tk;  // zero outside the box
-                tc::cp_async16z(dt + (size_t)ent * 12 + 4 * part, src, in ? 16 : 0);
+                const float* src = in ? tk + ((size_t)gy * A.Dx + gx) * 12 : tk;  // zero outside the box
+                const int nb = in ? 4 : 0;
+                tc::cp_async4(h01 + 2 * e, src + 2 * rl0, nb);
+                tc::cp_async4(h01 + 2 * e + 1, src + 2 * rl1, nb);
+                tc::cp_async4(l01 + 2 * e, src + 2 * rl0 + 1, nb);
+                tc::cp_async4(l01 + 2 * e + 1, src + 2 * rl1 + 1, nb);
+                tc::cp_async4(h2 + e, src + 2 * rl2, nb);
+                tc::cp_async4(l2 + e, src + 2 * rl2 + 1, nb);
             }
-            if (tid < kTileB / 4) tc::cp_async16(s_off + buf * kTileB + 4 * tid, A.off_i + tB * kTileB + 4 * tid);
+            if (tid < kTileB / 4) tc::cp_async16(s_off + (tB & 1) * kTileB + 4 * tid, A.off_i + tB * kTileB + 4 * tid);
             asm volatile("cp.async.commit_group;" ::: "memory");
         };
-        // running double-float sums of this thread's row and GEMM columns hb * 16 .. + 15
-        float H[16], L[16];
+        // running double-float sums of this thread's row and GEMM columns hb * 32 .. + 31, as pairs of columns
+        uint64_t H[16], L[16];
 #pragma unroll
-        for (int j = 0; j < 16; j++) H[j] = 0.0f, L[j] = 0.0f;
-        const uint32_t tacc = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(hb * 16);
+        for (int j = 0; j < 16; j++) H[j] = 0ull, L[j] = 0ull;
+        const uint32_t tacc = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(hb * 32);
         auto drain = [&](float sc) {
+            const uint64_t sc2 = pk2(sc, sc);
 #pragma unroll
-            for (int c = 0; c < 2; c++) {
+            for (int c = 0; c < 4; c++) {
                 uint32_t u[kNQ][8];
 #pragma unroll
                 for (int q = 0; q < kNQ; q++) tc::ld8_nowait(tacc + (uint32_t)(q * kN + c * 8), u[q]);
                 asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-                for (int j = 0; j < 8; j++) {
-                    float d[kNQ];
+                for (int j = 0; j < 4; j++) {
+                    uint64_t d[kNQ];
 #pragma unroll
-                    for (int q = 0; q < kNQ; q++) d[q] = __uint_as_float(u[q][j]);
-                    oz_accumulate(d, sc, H[c * 8 + j], L[c * 8 + j]);
+                    for (int q = 0; q < kNQ; q++) d[q] = pk2(__uint_as_float(u[q][2 * j]), __uint_as_float(u[q][2 * j + 1]));
+                    oz_accumulate2(d, sc2, H[c * 4 + j], L[c * 4 + j]);
                 }
             }
         };
         const uint32_t trow = tmem + ((uint32_t)((warp & 3) * 32) << 16) + kAcol + 4u * (uint32_t)hb;
         float sc_prev = 0.0f;  // 2^E of the tile whose group is drained next
         int il = 0;
-        if (nbuf == 2) stage_async(0, 0);
+        stage_async(0);
         for (int tB = 0; tB < A.n_tb; tB++) {
-            if (nbuf == 1) {
-                if (tc::builders_sync_any(s_abort)) break;  // everyone is done with the previous tile
-                stage_async(0, tB);
-            }
             asm volatile("cp.async.wait_all;" ::: "memory");
-            // this tile's copies are visible to every builder, the previous tile is done; one stop decision
+            // this tile's copies are visible to every builder, and every builder is done with the previous
+            // tile's slices; one stop decision
             if (tc::builders_sync_any(s_abort)) break;
-            if (nbuf == 2 && tB + 1 < A.n_tb) stage_async((tB + 1) & 1, tB + 1);
-            const int buf = nbuf == 2 ? (tB & 1) : 0;
-            const float* tab_b = s_tab + (size_t)buf * HW * 12;
-            const int* off_b = s_off + buf * kTileB;
+            const uint64_t* h01 = (const uint64_t*)s_tabs;
+            const uint64_t* l01 = h01 + HW;
+            const float* h2 = (const float*)(l01 + HW);
+            const float* l2 = h2 + HW;
+            float* me = (float*)(l2 + HW);
+            for (int e = tid; e < HW; e += kBuilders) {
+                float x0, x1;
+                upk2(h01[e], x0, x1);
+                me[e] = fmaxf(fabsf(h2[e]), fmaxf(fabsf(x0), fabsf(x1)));
+            }
+            if (tc::builders_sync_any(s_abort)) break;
+            const int* off_b = s_off + (tB & 1) * kTileB;
             const int4 bB = A.bbox_b[tB];
             const int ox = bA.x - bB.y, oy = bA.z - bB.w;
             const int base = (xa.x - ox) + A.W * (xa.y - oy);
-            // the row's scale for this tile: its largest entry over both halves' 64 columns
+            // the tile pair's scale: the largest entry over its 128 x 64 pairs (each thread: its row and half
+            // the columns; magnitudes compare as integers)
             float m = 0.0f;
-            for (int st = 0; st < kStages; st++)
-#pragma unroll
-                for (int i = 0; i < 8; i++) {
-                    const float* e = tab_b + (size_t)(base - off_b[st * kKC + hb * 8 + i]) * 12;
-                    m = fmaxf(m, fmaxf(fabsf(e[2 * rl0]), fmaxf(fabsf(e[2 * rl1]), fabsf(e[2 * rl2]))));
-                }
-            s_rmax[hb * kRows + a_loc] = m;
+#pragma unroll 8
+            for (int j = hb * 32; j < hb * 32 + 32; j++) m = fmaxf(m, me[base - off_b[j]]);
+            const uint32_t mw = __reduce_max_sync(0xffffffffu, __float_as_uint(m));
+            if (lane == 0) s_wmax[warp] = mw;
             if (tc::builders_sync_any(s_abort)) break;
-            const int E = oz_exp_of(fmaxf(s_rmax[a_loc], s_rmax[kRows + a_loc]));
+            uint32_t mb = s_wmax[0];
+#pragma unroll
+            for (int w8 = 1; w8 < kBuilderWarps; w8++) mb = max(mb, s_wmax[w8]);
+            const int E = oz_exp_of(__uint_as_float(mb));
             const float s_in = oz_pow2(-E), sc = oz_pow2(E);
+            const uint64_t s01 = pk2(s_in, s_in), s22 = pk2(sg2 * s_in, sg2 * s_in);
+            // every cell of the sub-box cut once at that scale: 18 bf16 slices (real, slice) in 9 words; cells
+            // e0 and e0 + 256 go together (the third real split as a pair of cells; past the end, the last
+            // cell again, written twice with the same bits)
+            for (int e0 = tid; e0 < HW; e0 += 2 * kBuilders) {
+                const int e1 = min(e0 + kBuilders, HW - 1);
+                uint64_t t0[kNS], t1[kNS], t2[kNS];
+                oz_split2(h01[e0], l01[e0], s01, t0);
+                oz_split2(h01[e1], l01[e1], s01, t1);
+                oz_split2(pk2(h2[e0], h2[e1]), pk2(l2[e0], l2[e1]), s22, t2);
+                uint32_t* c0 = s_sl + 9 * e0;
+                uint32_t* c1 = s_sl + 9 * e1;
+#pragma unroll
+                for (int q = 0; q < 3; q++) {  // word q of a real: slices 2q (low half) and 2q + 1
+                    float a0, b0, a1, b1, x0, x1, y0, y1;
+                    upk2(t0[2 * q], a0, b0);
+                    upk2(t0[2 * q + 1], a1, b1);
+                    c0[q] = cvt_bf16x2(a1, a0), c0[3 + q] = cvt_bf16x2(b1, b0);
+                    upk2(t1[2 * q], a0, b0);
+                    upk2(t1[2 * q + 1], a1, b1);
+                    c1[q] = cvt_bf16x2(a1, a0), c1[3 + q] = cvt_bf16x2(b1, b0);
+                    upk2(t2[2 * q], x0, x1);
+                    upk2(t2[2 * q + 1], y0, y1);
+                    c0[6 + q] = cvt_bf16x2(y0, x0), c1[6 + q] = cvt_bf16x2(y1, x1);
+                }
+            }
+            if (tc::builders_sync_any(s_abort)) break;
+            // the staging buffer is free: the next tile's sub-box loads while this tile's stages run
+            if (tB + 1 < A.n_tb) stage_async(tB + 1);
             for (int st = 0; st < kStages; st++, il++) {
-                // row a_loc, interface columns st * 16 + hb * 8 .. + 7: the row's three entries, six slices
-                // each, two columns per 32-bit word
+                // row a_loc, interface columns st * 16 + hb * 8 .. + 7: the 18 slices of each entry, two
+                // columns per 32-bit word
                 uint32_t w[3][kNS][4];
 #pragma unroll
                 for (int i2 = 0; i2 < 4; i2++) {
-                    float t[2][3][kNS];
+                    const int c = st * kKC + hb * 8 + 2 * i2;
+                    const uint32_t* p0 = s_sl + 9 * (base - off_b[c]);
+                    const uint32_t* p1 = s_sl + 9 * (base - off_b[c + 1]);
 #pragma unroll
-                    for (int u = 0; u < 2; u++) {
-                        const float* e = tab_b + (size_t)(base - off_b[st * kKC + hb * 8 + 2 * i2 + u]) * 12;
-                        const float2 p0 = *(const float2*)(e + 2 * rl0), p1 = *(const float2*)(e + 2 * rl1);
-                        const float2 p2 = *(const float2*)(e + 2 * rl2);
-                        oz_split(p0.x, p0.y, s_in, t[u][0]);
-                        oz_split(p1.x, p1.y, s_in, t[u][1]);
-                        oz_split(sg2 * p2.x, sg2 * p2.y, s_in, t[u][2]);
+                    for (int q = 0; q < 9; q++) {
+                        const uint32_t u0 = p0[q], u1 = p1[q];
+                        const int s0 = 2 * q, s1 = 2 * q + 1;  // slots (real, slice) = (s / 6, s % 6)
+                        w[s0 / kNS][s0 % kNS][i2] = __byte_perm(u0, u1, 0x5410);
+                        w[s1 / kNS][s1 % kNS][i2] = __byte_perm(u0, u1, 0x7632);
                     }
-#pragma unroll
-                    for (int ci = 0; ci < 3; ci++)
-#pragma unroll
-                        for (int p = 0; p < kNS; p++)
-                            asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(w[ci][p][i2]) : "f"(t[1][ci][p]), "f"(t[0][ci][p]));
                 }
-                // the tensor-memory A blocks are free once the previous stage's products are complete; the
-                // warp decides as one (the stores below are warp-wide)
+                // the A blocks are free once the previous stage's products are complete (at a tile's first
+                // stage: the previous tile's whole group, drained next).  The warp decides as one (the stores
+                // below are warp-wide).
                 bool ok = !s_abort && tc::wait_or_abort(&sy.aempty, ((uint32_t)il & 1u) ^ 1u, &s_abort, wl);
                 ok = __all_sync(0xffffffffu, ok);
                 if (!ok) {
@@ -456,13 +564,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_contract_oz(OzArgs O, int wl, i
                     continue;
                 }
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                if (st == 0 && tB > 0) drain(sc_prev);  // the previous tile's group is complete
+                if (st == 0 && tB > 0) drain(sc_prev);
+                const uint32_t tbase_a = trow;
 #pragma unroll
                 for (int ci = 0; ci < 3; ci++)
 #pragma unroll
                     for (int p = 0; p < kNS; p++)
                         asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1, %2, %3, %4};" ::"r"(
-                                         trow + (uint32_t)(ci * kNS + p) * 8u),
+                                         tbase_a + (uint32_t)(ci * kNS + p) * 8u),
                                      "r"(w[ci][p][0]), "r"(w[ci][p][1]), "r"(w[ci][p][2]), "r"(w[ci][p][3])
                                      : "memory");
                 asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
@@ -481,12 +590,16 @@ __global__ void __launch_bounds__(kThreads, 1) k_contract_oz(OzArgs O, int wl, i
         if (ok) {
             drain(sc_prev);  // the last tile's group
 #pragma unroll
-            for (int j = 0; j < 16; j++) {
-                const int n = hb * 16 + j, r = g * kRhs + n / 2, h = n & 1;
+            for (int j = 0; j < 32; j++) {
+                const int n = hb * 32 + j, r = g * kRhs + n / 2, h = n & 1;
                 if (r < O.n_rhs) {
+                    float hv0, hv1, lv0, lv1;
+                    upk2(H[j / 2], hv0, hv1);
+                    upk2(L[j / 2], lv0, lv1);
+                    const float hv = (j & 1) ? hv1 : hv0, lv = (j & 1) ? lv1 : lv0;
                     const float sF = oz_pow2(O.fexp[((size_t)r * A.K + k) * 2 + h]);
                     A.uh[(((size_t)r * A.K + k) * A.NPpad + a) * 6 + 3 * h + co] =
-                        f2d_int(__fmul_rn(H[j], sF)) + f2d_int(__fmul_rn(L[j], sF));
+                        f2d_int(__fmul_rn(hv, sF)) + f2d_int(__fmul_rn(lv, sF));
                 }
             }
         }
@@ -498,17 +611,16 @@ __global__ void __launch_bounds__(kThreads, 1) k_contract_oz(OzArgs O, int wl, i
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols));
 }
 
-size_t oz_smem(int HW, int nbuf) {
-    return (size_t)kS * kChunk + (size_t)nbuf * ((size_t)HW * 48 + kTileB * 4) + 2 * kRows * 4 + 1024;
+size_t oz_smem(int HW) {
+    return (size_t)kS * kChunk + oz_tab_bytes(HW) + 2 * kTileB * 4 + (size_t)HW * 36 + 1024;
 }
-// two table buffers (the next tile prefetched) when they fit, else one
-int oz_nbuf(int HW) { return oz_smem(HW, 2) <= 227 * 1024 ? 2 : 1; }
 int oz_groups(const Plan& P) { return (P.opt.max_rhs + kRhs - 1) / kRhs; }
 size_t oz_chunk_bytes(const Plan& P) { return (size_t)P.K * oz_groups(P) * P.n_tb * kStages * kChunk; }
 
 }  // namespace
 
-size_t contract_oz_smem(int HW) { return oz_smem(HW, oz_nbuf(HW)); }
+size_t contract_oz_smem(int HW) { return oz_smem(HW); }
+int contract_oz_rhs_group() { return kRhs; }
 
 // the sliced force operand of every mode and rhs group, then the scale exponents [max_rhs][K][2]
 size_t contract_oz_prep_bytes(const Plan& P) {
@@ -521,7 +633,7 @@ cudaError_t launch_contract_oz(const ContractArgs& A, const Plan& P, int n_rhs, 
     const int n_modes = P.K - A.k0;
     if (n_modes <= 0 || n_rhs < 1) return cudaSuccess;
     const int HW = P.H * P.W;
-    const size_t smem = oz_smem(HW, oz_nbuf(HW));
+    const size_t smem = oz_smem(HW);
     if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
     if (!P.d_bprep || P.bprep_prec != FBC_PREC_BF16X6 || P.bprep_bytes < contract_oz_prep_bytes(P) ||
         n_rhs > P.opt.max_rhs || !A.tabx2 || A.tabx2 != P.d_table_x2)
@@ -532,7 +644,6 @@ cudaError_t launch_contract_oz(const ContractArgs& A, const Plan& P, int n_rhs, 
     O.fexp = (const int*)((const unsigned char*)P.d_bprep + oz_chunk_bytes(P));
     O.n_rhs = n_rhs;
     O.G = oz_groups(P);
-    O.nbuf = oz_nbuf(HW);
     k_oz_fscale<<<dim3(n_modes, n_rhs), 256, 0, st>>>(A.fh, P.K, P.NIpad, A.k0, (int*)O.fexp);
     if (cudaError_t e = cudaGetLastError()) return e;
     const int gu = (n_rhs + kRhs - 1) / kRhs;  // rhs groups of this apply

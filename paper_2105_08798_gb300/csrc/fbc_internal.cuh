@@ -223,6 +223,7 @@ cudaError_t launch_contract_tc_batch(int precision, const TcJob* d_jobs, const i
 // operand and scales (the plan's d_bprep), and the launch of modes A.k0 .. K - 1
 size_t contract_oz_smem(int HW);
 size_t contract_oz_prep_bytes(const Plan& P);
+int contract_oz_rhs_group();  // right-hand sides per CTA
 cudaError_t launch_contract_oz(const ContractArgs& A, const Plan& P, int n_rhs, cudaStream_t st);
 inline bool is_tensor_precision(int p) { return p == FBC_PREC_TF32 || p == FBC_PREC_BF16X2 || p == FBC_PREC_BF16X3; }
 int batch_rhs_block();

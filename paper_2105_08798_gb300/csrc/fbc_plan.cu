@@ -699,12 +699,18 @@ int fbc_apply_host(fbc_plan* plan, const double* f_host, double* u_host, int32_t
         for (auto& h : P.host_st) FBC_CUDA(cudaStreamCreateWithFlags(&h, cudaStreamNonBlocking));
         for (auto& e : P.host_ev) FBC_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
     }
-    // The right-hand sides go through in chunks (at least kHostChunkRhs each, at most kHostChunks):
+    // The right-hand sides go through in chunks (at least gran each, at most kHostChunks):
     // chunk c is copied in on one stream, applied on the caller's stream once it has arrived, and
     // copied out on a third stream once applied, so copies overlap the applies of other chunks.
     // Each right-hand side is computed as in one apply of all of them.
-    const int n_chunks = std::max(1, std::min(fbc::kHostChunks, n_rhs / fbc::kHostChunkRhs));
-    const int per = (n_rhs + n_chunks - 1) / n_chunks;
+    // A chunk holds whole right-hand-side groups of the tensor-core forms (their CTAs compute a group's
+    // width whatever its fill).
+    const int gran = P.precision == FBC_PREC_BF16X6  ? fbc::contract_oz_rhs_group()
+                     : fbc::is_tensor_precision(P.precision) ? fbc::contract_tc_max_rpc(P)
+                                                             : fbc::kHostChunkRhs;
+    const int n_chunks = std::max(1, std::min(fbc::kHostChunks, n_rhs / gran));
+    int per = (n_rhs + n_chunks - 1) / n_chunks;
+    if (gran > fbc::kHostChunkRhs) per = (per + gran - 1) / gran * gran;
     const size_t fr = (size_t)P.n_i * P.L * 3, ur = (size_t)P.n_p * P.L * 3;  // doubles per right-hand side
     cudaStream_t cin = P.host_st[0], cout = P.host_st[1];
     cudaEvent_t* ev = P.host_ev;  // [0] start, [1 + c] chunk c in, [1 + kHostChunks + c] chunk c applied, [last] end

@@ -115,6 +115,24 @@ __device__ __forceinline__ bool wait_or_abort(uint64_t* m, uint32_t parity, vola
     return false;
 }
 
+// wait_or_abort for a role thread that has nothing else to do meanwhile: each poll may suspend the
+// thread for up to about hint_ns nanoseconds (it resumes as soon as the phase completes), so a waiting
+// thread takes no issue slots from the warps that work.  Bounded by `limit` polls.
+__device__ __forceinline__ bool wait_or_abort_sleep(uint64_t* m, uint32_t parity, volatile int* abort, int limit,
+                                                    uint32_t hint_ns) {
+    for (int it = 0; it < limit; it++) {
+        uint32_t ok;
+        asm volatile(
+            "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\nselp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(ok)
+            : "r"(smem_u32(m)), "r"(parity), "r"(hint_ns)
+            : "memory");
+        if (ok) return true;
+        if ((it & 15) == 15 && *abort) return false;
+    }
+    return false;
+}
+
 // Named barrier 1 among the NT threads of the builder warps that also returns,
 // to every one of them, whether any passed flag != 0: a decision all of them
 // take alike.
@@ -137,6 +155,11 @@ __device__ __forceinline__ void cp_async16(void* dst, const void* src) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
 }
 
+// 4 bytes, or zero when src_bytes is 0
+__device__ __forceinline__ void cp_async4(void* dst, const void* src, int src_bytes) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(smem_u32(dst)), "l"(src), "r"(src_bytes)
+                 : "memory");
+}
 // 16 bytes, of which the first src_bytes (0 or 16) come from global memory and the rest are zero
 __device__ __forceinline__ void cp_async16z(void* dst, const void* src, int src_bytes) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(dst)), "l"(src), "r"(src_bytes)

@@ -166,15 +166,16 @@ def test_host_entry_point_matches_device(fbc):
 
 
 def test_host_entry_point_in_chunks(fbc):
-    """fbc_apply_host with 22 right-hand sides runs them in chunks (5 of 5, 5, 5, 5, 2) whose copies
-    overlap the applies of the others.  Every right-hand side gets the bits of one device apply of all
-    22 (the CUDA-core forms; the tensor-core form within 1e-14), with beta u0, the zero mean and the
+    """fbc_apply_host with 22 right-hand sides runs the CUDA-core forms in chunks (5 of 5, 5, 5, 5, 2)
+    whose copies overlap the applies of the others, and the tensor-core forms in chunks of whole
+    right-hand-side groups (here one).  Every right-hand side gets the bits of one device apply of all
+    22 (the CUDA-core forms and BF16X6; BF16X2 within 1e-14), with beta u0, the zero mean and the
     ragged last chunk."""
     xy_i, xy_p = inputs.ring_geometry(80, 100)
     L, R = 16, 22
     f = inputs.forces(R, 80, L, seed=16)
     u0 = np.random.default_rng(5).standard_normal((R, 100, L, 3))
-    for prec in ("f32x2", "fp64", "bf16x2"):
+    for prec in ("f32x2", "fp64", "bf16x2", "bf16x6"):
         with fbc.Plan(xy_i, xy_p, L, ISO, precision=prec, max_rhs=R) as plan:
             plan.tabulate()
             dev = gpu_update(fbc, xy_i, xy_p, L, ISO, f, plan=plan, alpha=-1.0, beta=0.5, u0=u0, zero_mean=True)
