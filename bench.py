@@ -521,7 +521,7 @@ def run_ours(args, w):
 
     # the other forms on the same plan and inputs (not after the tables were released); the dense FP64
     # form, several times slower than double-float at the same accuracy, only at one right-hand side
-    if not args.surrogate:
+    if not args.surrogate and not args.no_variants:
         others = (("fp64", "f32x2", "fp32", "fft64", "fft32") if R == 1
                   else ("f32x2", "bf16x6", "fp32", "tf32", "bf16x2", "bf16x3", "fft64", "fft32"))
         for prec in others:
@@ -883,6 +883,8 @@ def main(argv=None):
                     help="train the learned far field (width 128, 2^20 samples, 50 epochs), attach it with "
                          "r_min = 8 and release the K-slice tables; the exact-table path is timed first")
     ap.add_argument("--skip-oracle", action="store_true", help="no oracle error check / CPU baseline")
+    ap.add_argument("--no-variants", action="store_true",
+                    help="time the headline form only (no other forms beside it), e.g. for a launch list")
     ap.add_argument("--hmatrix", action="store_true",
                     help="also build the H-matrix of the same Green matrix (eps 1e-5, gamma 2, b_min 20) and time "
                          "its apply as a variant")

@@ -240,7 +240,7 @@ struct OzArgs {
 };
 
 struct OzSync {
-    uint64_t bfull[kS], empty[kS], done, afull, aempty;
+    uint64_t bfull[kS], empty[kS], done, afull[3], aempty[3];  // A: one barrier pair per input component
     uint32_t tbase;
     volatile int abort;
 };
@@ -345,7 +345,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_contract_oz(OzArgs O, int wl, i
         sy.abort = 0;
         for (int s = 0; s < kS; s++) tc::mbar_init(&sy.bfull[s], 1), tc::mbar_init(&sy.empty[s], 1);
         tc::mbar_init(&sy.done, 1);
-        tc::mbar_init(&sy.afull, kBuilderWarps), tc::mbar_init(&sy.aempty, 1);
+        for (int c = 0; c < 3; c++) tc::mbar_init(&sy.afull[c], kBuilderWarps), tc::mbar_init(&sy.aempty[c], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 0) {
@@ -385,17 +385,22 @@ __global__ void __launch_bounds__(kThreads, 1) k_contract_oz(OzArgs O, int wl, i
             for (int il = 0; il < n_it; il++) {
                 const int s = il % kS;
                 const uint32_t par = (uint32_t)(il / kS) & 1u;
-                if (!tc::wait_or_abort_sleep(&sy.afull, (uint32_t)il & 1u, &s_abort, wl, kSleepNs) ||
-                    !tc::wait_or_abort_sleep(&sy.bfull[s], par, &s_abort, wl, kSleepNs)) {
+                if (!tc::wait_or_abort_sleep(&sy.bfull[s], par, &s_abort, wl, kSleepNs)) {
                     s_abort = 1;
                     break;
                 }
-                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 const uint64_t dBs = dB0 + (uint64_t)(((size_t)s * kChunk) >> 4);
                 const uint32_t ta0 = tmem + kAcol;
                 const bool first = (il % kStages) == 0;  // a new group overwrites the accumulators
+                bool stop = false;
 #pragma unroll
-                for (int ci = 0; ci < 3; ci++)
+                for (int ci = 0; ci < 3; ci++) {
+                    // the A blocks of input component ci, stored by the builders while the others' products run
+                    if (!tc::wait_or_abort_sleep(&sy.afull[ci], (uint32_t)il & 1u, &s_abort, wl, kSleepNs)) {
+                        stop = true;
+                        break;
+                    }
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 #pragma unroll
                     for (int p = 0; p < kNPair; p++) {
                         const uint32_t ta = ta0 + (uint32_t)(ci * kNS + oz_pi(p) - 1) * 8u;
@@ -407,7 +412,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_contract_oz(OzArgs O, int wl, i
                             "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}\n" ::"r"(dt),
                             "r"(ta), "l"(db), "r"(id), "r"(en));
                     }
-                tc::commit(&sy.aempty);
+                    tc::commit(&sy.aempty[ci]);
+                }
+                if (stop) {
+                    s_abort = 1;
+                    break;
+                }
                 tc::commit(&sy.empty[s]);
             }
             tc::commit(&sy.done);  // also after a stop: fires once the issued products are complete
@@ -538,46 +548,47 @@ __global__ void __launch_bounds__(kThreads, 1) k_contract_oz(OzArgs O, int wl, i
             // the staging buffer is free: the next tile's sub-box loads while this tile's stages run
             if (tB + 1 < A.n_tb) stage_async(tB + 1);
             for (int st = 0; st < kStages; st++, il++) {
-                // row a_loc, interface columns st * 16 + hb * 8 .. + 7: the 18 slices of each entry, two
-                // columns per 32-bit word
-                uint32_t w[3][kNS][4];
+                const uint32_t ph = ((uint32_t)il & 1u) ^ 1u;  // parity of stage il - 1's phase
+                int cell[8];  // row a_loc, interface columns st * 16 + hb * 8 .. + 7
 #pragma unroll
-                for (int i2 = 0; i2 < 4; i2++) {
-                    const int c = st * kKC + hb * 8 + 2 * i2;
-                    const uint32_t* p0 = s_sl + 9 * (base - off_b[c]);
-                    const uint32_t* p1 = s_sl + 9 * (base - off_b[c + 1]);
+                for (int i = 0; i < 8; i++) cell[i] = 9 * (base - off_b[st * kKC + hb * 8 + i]);
 #pragma unroll
-                    for (int q = 0; q < 9; q++) {
-                        const uint32_t u0 = p0[q], u1 = p1[q];
-                        const int s0 = 2 * q, s1 = 2 * q + 1;  // slots (real, slice) = (s / 6, s % 6)
-                        w[s0 / kNS][s0 % kNS][i2] = __byte_perm(u0, u1, 0x5410);
-                        w[s1 / kNS][s1 % kNS][i2] = __byte_perm(u0, u1, 0x7632);
+                for (int ci = 0; ci < 3; ci++) {
+                    // the six slices of component ci, two columns per 32-bit word (words 3 ci .. 3 ci + 2 of
+                    // a cell hold its slices 0 .. 5)
+                    uint32_t w[kNS][4];
+#pragma unroll
+                    for (int i2 = 0; i2 < 4; i2++)
+#pragma unroll
+                        for (int q = 0; q < 3; q++) {
+                            const uint32_t u0 = s_sl[cell[2 * i2] + 3 * ci + q], u1 = s_sl[cell[2 * i2 + 1] + 3 * ci + q];
+                            w[2 * q][i2] = __byte_perm(u0, u1, 0x5410);
+                            w[2 * q + 1][i2] = __byte_perm(u0, u1, 0x7632);
+                        }
+                    // component ci's blocks are free once stage il - 1's products of ci are complete; at a
+                    // tile's first stage the whole of stage il - 1 (its last component) first, since the
+                    // previous tile's group is drained before these stores.  The warp decides as one (the
+                    // stores are warp-wide).
+                    const bool tile_start = ci == 0 && st == 0 && tB > 0;
+                    bool ok = !s_abort && tc::wait_or_abort(&sy.aempty[tile_start ? 2 : ci], ph, &s_abort, wl);
+                    ok = __all_sync(0xffffffffu, ok);
+                    if (!ok) {
+                        s_abort = 1;
+                        break;
                     }
-                }
-                // the A blocks are free once the previous stage's products are complete (at a tile's first
-                // stage: the previous tile's whole group, drained next).  The warp decides as one (the stores
-                // below are warp-wide).
-                bool ok = !s_abort && tc::wait_or_abort(&sy.aempty, ((uint32_t)il & 1u) ^ 1u, &s_abort, wl);
-                ok = __all_sync(0xffffffffu, ok);
-                if (!ok) {
-                    s_abort = 1;
-                    continue;
-                }
-                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                if (st == 0 && tB > 0) drain(sc_prev);
-                const uint32_t tbase_a = trow;
-#pragma unroll
-                for (int ci = 0; ci < 3; ci++)
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    if (tile_start) drain(sc_prev);
 #pragma unroll
                     for (int p = 0; p < kNS; p++)
                         asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1, %2, %3, %4};" ::"r"(
-                                         tbase_a + (uint32_t)(ci * kNS + p) * 8u),
-                                     "r"(w[ci][p][0]), "r"(w[ci][p][1]), "r"(w[ci][p][2]), "r"(w[ci][p][3])
+                                         trow + (uint32_t)(ci * kNS + p) * 8u),
+                                     "r"(w[p][0]), "r"(w[p][1]), "r"(w[p][2]), "r"(w[p][3])
                                      : "memory");
-                asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
-                asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-                __syncwarp();
-                if (lane == 0) tc::mbar_arrive(&sy.afull);
+                    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+                    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                    __syncwarp();
+                    if (lane == 0) tc::mbar_arrive(&sy.afull[ci]);
+                }
             }
             sc_prev = sc;
         }
