@@ -396,7 +396,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_contract_oz(OzArgs O, int wl, i
 #pragma unroll
                 for (int ci = 0; ci < 3; ci++) {
                     // the A blocks of input component ci, stored by the builders while the others' products run
-                    if (!tc::wait_or_abort_sleep(&sy.afull[ci], (uint32_t)il & 1u, &s_abort, wl, kSleepNs)) {
+                    if (!tc::wait_or_abort(&sy.afull[ci], (uint32_t)il & 1u, &s_abort, wl)) {
                         stop = true;
                         break;
                     }
