@@ -16,34 +16,41 @@
 //   * an FP32 accumulator that only ever adds values of one grid is exact while
 //     the sum stays below 2^24 grid units.  With 192 terms per group (64
 //     interface columns x 3 components) and at most q - 1 products of at most
-//     2^14 units per term, q <= 6 stays exact in the worst case, and the sums of
-//     q = 7, 8 are far below the result's last bit when they round.
-// So each diagonal q = 2 .. 8 (26 slice products: i, j <= 6, i + j <= 8) has an
-// accumulator of its own in tensor memory, the products of a group are summed
-// exactly there, and the group's seven sums are combined in double-float
-// arithmetic, scaled back and added to a running double-float sum per output.
-// What is left out -- slices beyond the sixth and products with i + j > 8 -- is
-// below 2^-47 of the largest operand product, per term.
+//     2^14 units per term, the diagonals q = 2 .. 5 stay exact in the worst case.
+// The 26 slice products with i, j <= 6 and i + j <= 8 are kept.  Diagonals 2, 3,
+// 4 and 5 have an accumulator each in tensor memory; 6, 7 and 8 (about 2^-31 of
+// the result) share a fifth, whose rounding stays near 2^-54 of the result.  The
+// group's five sums are combined in double-float arithmetic, scaled back and
+// added to a running double-float sum per output.  What is left out -- slices
+// beyond the sixth and products with i + j > 8 -- is about 2^-47 of the largest
+// operand product, per term.
 //
-// Scales: the table entries of pad row a and interface tile tB (64 columns, one
-// accumulation group) share 2^E(a, tB), the largest power of two with |entry| <
-// 2^(E-1) over the row's entries in the tile, found on the fly; the force column
-// n of mode k shares 2^F(k, n), found by a reduction before the split.  Rows and
-// columns scale the GEMM independently, so both are exact.
+// Scales: all table entries of a (pad tile, interface tile) pair share 2^E, the
+// smallest power of two above twice their largest magnitude over the pair's
+// 128 x 64 entries (of the CTA's three reals), so every cell of the pair's table
+// sub-box is cut into slices once; the force column n of mode k shares 2^F(k, n),
+// found by a reduction before the split.  Row and column scales factor out of the
+// GEMM exactly.
 //
 // A CTA owns 128 pad columns (the GEMM rows, one tensor-memory lane each), one
-// output component co, one mode and 16 right-hand sides (N = 32), and walks the
-// interface columns in stages of 16:
-//   * eight builder warps gather the co-th row of M, (M_{co 0}, M_{co 1},
-//     M_{co 2}), from the staged double-float table sub-box, split it into six
-//     slices and store the 3 x 6 blocks of 128 x 16 bf16 into tensor memory;
+// output component co, one mode and 32 right-hand sides (N = 64), and walks the
+// interface columns tile by tile (64 columns, one accumulation group), in stages
+// of 16:
+//   * per tile, the eight builder warps stage the CTA's three reals of the
+//     double-float sub-box (prefetched during the previous tile), find the
+//     pair's scale and cut each cell into 18 bf16 slices in shared memory;
+//   * per stage, they gather the slices of the co-th row of M, (M_{co 0},
+//     M_{co 1}, M_{co 2}), and store them into tensor memory one input component
+//     at a time (3 x 6 blocks of 128 x 16 bf16), each handed over by its own
+//     barrier pair, so the stores of one component overlap the products of the
+//     others;
 //   * one thread streams the force operand, split once per apply (3 x 6 blocks
-//     of 32 x 16 bf16 per stage, 18 KB), with bulk copies into a ring of stages;
-//   * one thread issues 3 x 26 tcgen05.mma (M = 128, N = 32, K = 16) per stage
-//     into the seven diagonal accumulators;
-//   * at the end of every interface tile the builders drain the accumulators
+//     of 64 x 16 bf16 per stage, 36 KB), with bulk copies into a ring of stages;
+//   * one thread issues 3 x 26 tcgen05.mma (M = 128, N = 64, K = 16) per stage
+//     into the five accumulators;
+//   * at the start of every tile the builders drain the previous tile's group
 //     into their running double-float sums.
-// Tensor memory: 7 x 32 accumulator columns and 18 x 8 columns of A: 368 of 512.
+// Tensor memory: 5 x 64 accumulator columns and 18 x 8 columns of A: 464 of 512.
 // The mode k = 0 stays with the double-float kernel, as in the other tensor forms.
 //
 // Every wait is bounded as in the other tensor-core kernel: pipeline waits give
@@ -80,7 +87,7 @@ static_assert(kAcol + kAcols <= kTmemCols, "tensor memory");
 constexpr uint32_t kBBlk = (uint32_t)kN * kKC * 2;       // one (ci, slice) block of a force chunk: 2 KB
 constexpr uint32_t kChunk = 3u * kNS * kBBlk;            // one stage of the force operand: 36 KB
 constexpr uint32_t kSBO = (kKC / 8) * 128;               // 8-row group stride of a [rows][16] bf16 block
-constexpr uint32_t kSleepNs = 200;  // suspend hint of the copy and MMA threads' waits
+constexpr uint32_t kSleepNs = 200;  // suspend hint of the copy thread's waits and the MMA thread's force waits
 constexpr int kEmin = -120, kEmax = 120;                 // clamp of the scale exponents (2^E a normal float)
 
 // Entry of M(d) in row co, column ci, as (index into the six table reals, sign):
