@@ -1,12 +1,14 @@
-"""Parity of the reduced-precision and in-plane FFT forms at the size they serve: 8000 interface and
+"""Parity of the tensor-core, reduced-precision and in-plane FFT forms at the size they serve: 8000 interface and
 12000 pad columns, L = 1024, 64 right-hand sides, isotropic medium (the precision-sweep workload).
 
 One plan, one set of device forces; each form is applied in turn and the result is compared with the
 oracle's plain real-space double sum (Eq. 1, Sec. 3.2, Eqs. 37-38) at every repeat of four pad
 columns -- the two innermost (nearest the interface, where the high modes are largest) and the two
 outermost -- for right-hand sides 0 and 63.  Per form: the overall relative L2 error and the error
-per mode band (k = 0, 1..L/8, L/8+1..L/2).  The tensor-core forms drain their accumulators every
-1024 interface columns, so at 8000 columns this covers eight accumulation groups.  Bounds: the
+per mode band (k = 0, 1..L/8, L/8+1..L/2).  The reduced-precision tensor-core forms drain their
+accumulators every 1024 interface columns, so at 8000 columns this covers eight accumulation
+groups; the FP64-accurate BF16X6 form drains every 64 columns (125 groups, 125 scales per pad tile)
+and runs two groups of 32 right-hand sides.  Bounds: the
 errors each form is stated to have at this size, with a margin; k = 0 is FP64-accurate in every
 form.
 """
